@@ -1,0 +1,303 @@
+/*
+ * bp_oracle.c -- CPU oracle for the DFF-based feasibility check of the
+ * bin_packing constraint (Tardivo, Michel, Pontelli, "Constraint Propagation
+ * on GPU: A Case Study for the Bin Packing Constraint", arXiv 2402.14821).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct
+ * definition that the CUDA path is checked against.  Only the test suite,
+ * the smoke check and the benchmark's CPU-baseline leg may load it.  It shares
+ * no code, header, table or helper with the CUDA library, and the CUDA
+ * library never calls it.
+ *
+ * Style rules followed here, so that a reader can check it against the paper
+ * by eye:
+ *   - int64_t everywhere; native '/' and '%' on non-negative operands;
+ *   - every dual-feasible function (DFF) is the literal case analysis printed
+ *     in Sec. 3.1 ("Lower bounds"), cases tested in the printed order;
+ *   - the bound is Alg. 2 without its early exit: the full maximum over every
+ *     DFF and every integer parameter, first (DFF, lambda) in the paper's
+ *     order wins ties;
+ *   - no blocking, fusion, reordering, magic numbers or precomputation.
+ *
+ * Readings of the paper taken here:
+ *   R1  lambda is an integer (Sec. 3.1 says so for f_MT).  Real end points of
+ *       the printed ranges become: MT [0, c/2], RAD2 [c/4 + 1, c/3],
+ *       FS1 [1, 100], CCM1 [1, c/2], VB2 [2, c], BJ1 [1, c] (integer floors).
+ *   R2  "w = c/2" and "w > c/2" are tested as 2w == c and 2w > c.
+ *   R3  The returned bound is the full maximum (Alg. 2 early exit dropped);
+ *       the verdict is bound <= k.
+ *   R4  Argmax tie-break: first (DFF, lambda) in the order MT, RAD2, FS1,
+ *       CCM1, VB2, BJ1 and ascending lambda.
+ *   R5  VB2's range is [2, c] by default.  With vb2_cap != 0 the upper end is
+ *       min(c, floor(UINT_MAX / (r * max w'))) as in Sec. 4 ("Implementation
+ *       details").
+ *   R6  The reduction (Sec. 3 "Feasibility check", Fig. 3) keeps the unpacked
+ *       items in index order and then one virtual item per bin whose size is
+ *       the bin's packed load, bins in index order; empty bins (load 0) are
+ *       dropped because f(0) = 0 for every DFF.
+ *   R7  L2 (Sec. 3.1) is evaluated over integer lambda in [0, c/2].
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { ORC_MT = 0, ORC_RAD2 = 1, ORC_FS1 = 2, ORC_CCM1 = 3, ORC_VB2 = 4,
+       ORC_BJ1 = 5, ORC_NDFF = 6 };
+
+/* ceil(a / b) for a >= 0, b > 0. */
+static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+static int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
+
+/* Parameter range of each DFF (Sec. 3.1; reading R1).  Returns the number of
+ * parameters; *lo > *hi means the range is empty. */
+int64_t orc_param_range(int d, int64_t c, int64_t *lo, int64_t *hi)
+{
+    switch (d) {
+    case ORC_MT:   *lo = 0;         *hi = c / 2; break;   /* 0 <= l <= c/2   */
+    case ORC_RAD2: *lo = c / 4 + 1; *hi = c / 3; break;   /* c/4 < l <= c/3  */
+    case ORC_FS1:  *lo = 1;         *hi = 100;   break;   /* 1 <= l <= 100   */
+    case ORC_CCM1: *lo = 1;         *hi = c / 2; break;   /* 1 <= l <= c/2   */
+    case ORC_VB2:  *lo = 2;         *hi = c;     break;   /* 2 <= l <= c     */
+    case ORC_BJ1:  *lo = 1;         *hi = c;     break;   /* 1 <= l <= c     */
+    default:       *lo = 1;         *hi = 0;     break;
+    }
+    return *hi >= *lo ? *hi - *lo + 1 : 0;
+}
+
+/* f_MT (Sec. 3.1, Fig. 4). */
+static int64_t f_mt(int64_t w, int64_t l, int64_t c)
+{
+    if (c - l < w) return c;
+    if (l <= w && w <= c - l) return w;
+    return 0;                                   /* w < l */
+}
+
+/* f_RAD2 (Sec. 3.1).  The last case recurses on c - w <= c - 2l, which lands
+ * in one of the first two cases, so the recursion is one level deep. */
+static int64_t f_rad2(int64_t w, int64_t l, int64_t c)
+{
+    if (w < l) return 0;
+    if (l <= w && w <= c - 2 * l) return c / 3;
+    if (c - 2 * l < w && w < 2 * l) return c / 2;
+    return c - f_rad2(c - w, l, c);             /* 2l <= w */
+}
+
+/* f_FS1 (Sec. 3.1): "w(l+1)/c is a natural number" is (w(l+1)) mod c == 0. */
+static int64_t f_fs1(int64_t w, int64_t l, int64_t c)
+{
+    if ((w * (l + 1)) % c == 0) return w * l;
+    return (w * (l + 1)) / c * c;
+}
+
+/* f_CCM1 (Sec. 3.1). */
+static int64_t f_ccm1(int64_t w, int64_t l, int64_t c)
+{
+    if (2 * w > c) return 2 * (c / l) - 2 * ((c - w) / l);
+    if (2 * w == c) return c / l;
+    return 2 * (w / l);                         /* 2w < c */
+}
+
+/* f_VB2 (Sec. 3.1), including the unsimplified ceil(c*l / c). */
+static int64_t f_vb2(int64_t w, int64_t l, int64_t c)
+{
+    if (2 * w > c)
+        return 2 * max64(0, ceil_div(c * l, c) - 1)
+             - 2 * max64(0, ceil_div(c * l - w * l, c) - 1);
+    if (2 * w == c) return max64(0, ceil_div(c * l, c) - 1);
+    return 2 * max64(0, ceil_div(w * l, c) - 1); /* 2w < c */
+}
+
+/* f_BJ1 (Sec. 3.1). */
+static int64_t f_bj1(int64_t w, int64_t l, int64_t c)
+{
+    if (w % l <= c % l) return (w / l) * (l - c % l);
+    return (w / l) * (l - c % l) + w % l - c % l;
+}
+
+int64_t orc_dff(int d, int64_t w, int64_t l, int64_t c)
+{
+    switch (d) {
+    case ORC_MT:   return f_mt(w, l, c);
+    case ORC_RAD2: return f_rad2(w, l, c);
+    case ORC_FS1:  return f_fs1(w, l, c);
+    case ORC_CCM1: return f_ccm1(w, l, c);
+    case ORC_VB2:  return f_vb2(w, l, c);
+    case ORC_BJ1:  return f_bj1(w, l, c);
+    }
+    return -1;
+}
+
+/* One "L1-like" bound of Alg. 2: ceil(sum_w f(w, l) / f(c, l)). */
+int64_t orc_lb_param(int d, int64_t l, const int64_t *wr, int64_t r, int64_t c)
+{
+    int64_t sum = 0;
+    for (int64_t i = 0; i < r; i++) sum += orc_dff(d, wr[i], l, c);
+    return ceil_div(sum, orc_dff(d, c, l, c));
+}
+
+/* Upper end of the VB2 range under the paper's 32-bit overflow cap (R5). */
+static int64_t vb2_cap_hi(const int64_t *wr, int64_t r, int64_t c)
+{
+    int64_t wmax = 0;
+    for (int64_t i = 0; i < r; i++) if (wr[i] > wmax) wmax = wr[i];
+    if (r == 0 || wmax == 0) return c;
+    int64_t cap = (int64_t)4294967295LL / (r * wmax);
+    return cap < c ? cap : c;
+}
+
+/* L_f of Alg. 2 for one DFF: the largest bound over its parameter range and
+ * the first lambda attaining it; -1 when the range is empty (reading R5 for
+ * vb2_cap). */
+int64_t orc_lb_dff(int d, const int64_t *wr, int64_t r, int64_t c, int vb2_cap,
+                   int64_t *out_lambda)
+{
+    int64_t lo, hi, best = -1, best_l = 0;
+    orc_param_range(d, c, &lo, &hi);
+    if (d == ORC_VB2 && vb2_cap) hi = vb2_cap_hi(wr, r, c);
+    for (int64_t l = lo; l <= hi; l++) {
+        int64_t lb = orc_lb_param(d, l, wr, r, c);
+        if (lb > best) { best = lb; best_l = l; }
+    }
+    if (out_lambda) *out_lambda = best_l;
+    return best;
+}
+
+/* The collection of DFF bounds (Alg. 2, full maximum; readings R3, R4, R5).
+ * Writes the bound and its first attaining (DFF, lambda); returns 1 when
+ * bound <= k (feasible), 0 otherwise, -1 on invalid input. */
+int orc_lb(const int64_t *wr, int64_t r, int64_t c, int64_t k, int vb2_cap,
+           int64_t *out_bound, int32_t *out_dff, int64_t *out_lambda)
+{
+    if (c < 1 || r < 0) return -1;
+    for (int64_t i = 0; i < r; i++) if (wr[i] < 0 || wr[i] > c) return -1;
+    int64_t best = -1, best_l = 0;
+    int32_t best_d = 0;
+    for (int d = 0; d < ORC_NDFF; d++) {
+        int64_t l;
+        int64_t lf = orc_lb_dff(d, wr, r, c, vb2_cap, &l);
+        if (lf > best) { best = lf; best_d = d; best_l = l; }
+    }
+    *out_bound = best;
+    *out_dff = best_d;
+    *out_lambda = best_l;
+    return best <= k ? 1 : 0;
+}
+
+/* getReduction (Sec. 3 "Feasibility check", Fig. 3; reading R6).
+ * assign[i] = -1 for an unpacked item, else the bin 0..k-1 it is packed in.
+ * Writes at most n + k sizes to out and returns their count, or -1 when an
+ * assignment is out of range or a bin's load exceeds c. */
+int64_t orc_reduce(const int64_t *w, const int32_t *assign, int64_t n,
+                   int64_t k, int64_t c, int64_t *out)
+{
+    int64_t *load = (int64_t *)calloc((size_t)(k > 0 ? k : 1), sizeof(int64_t));
+    if (!load) return -1;
+    int64_t r = 0;
+    for (int64_t i = 0; i < n; i++) {
+        if (assign[i] < -1 || assign[i] >= k) { free(load); return -1; }
+        if (assign[i] == -1) out[r++] = w[i];
+        else load[assign[i]] += w[i];
+    }
+    for (int64_t j = 0; j < k; j++) {
+        if (load[j] > c) { free(load); return -1; }
+        if (load[j] > 0) out[r++] = load[j];
+    }
+    free(load);
+    return r;
+}
+
+/* L1 (Sec. 3.1). */
+int64_t orc_l1(const int64_t *w, int64_t n, int64_t c)
+{
+    int64_t s = 0;
+    for (int64_t i = 0; i < n; i++) s += w[i];
+    return ceil_div(s, c);
+}
+
+/* L2 (Sec. 3.1), straight from its definition over integer lambda (R7). */
+int64_t orc_l2(const int64_t *w, int64_t n, int64_t c)
+{
+    int64_t best = 0;
+    for (int64_t l = 0; 2 * l <= c; l++) {
+        int64_t n1 = 0, n2 = 0, s2 = 0, s3 = 0;
+        for (int64_t i = 0; i < n; i++) {
+            if (c - l < w[i]) n1++;                               /* W1 */
+            else if (2 * w[i] > c && w[i] <= c - l) { n2++; s2 += w[i]; } /* W2 */
+            else if (l <= w[i] && 2 * w[i] <= c) s3 += w[i];     /* W3 */
+        }
+        int64_t num = s3 - (c * n2 - s2);
+        int64_t v = n1 + n2 + (num > 0 ? ceil_div(num, c) : 0);
+        if (v > best) best = v;
+    }
+    return best;
+}
+
+/* Brute-force optimum number of bins for tiny instances: depth-first search
+ * over item-to-bin assignments (items in the given order, a new bin is opened
+ * only as the next unused one), pruned by the best solution found so far. */
+static void opt_dfs(const int64_t *w, int64_t n, int64_t c, int64_t i,
+                    int64_t *load, int64_t used, int64_t *best)
+{
+    if (used >= *best) return;
+    if (i == n) { *best = used; return; }
+    for (int64_t j = 0; j < used; j++) {
+        if (load[j] + w[i] <= c) {
+            load[j] += w[i];
+            opt_dfs(w, n, c, i + 1, load, used, best);
+            load[j] -= w[i];
+        }
+    }
+    load[used] = w[i];
+    opt_dfs(w, n, c, i + 1, load, used + 1, best);
+    load[used] = 0;
+}
+
+int64_t orc_opt_bins(const int64_t *w, int64_t n, int64_t c)
+{
+    for (int64_t i = 0; i < n; i++) if (w[i] > c || w[i] < 0) return -1;
+    int64_t *load = (int64_t *)calloc((size_t)(n + 1), sizeof(int64_t));
+    if (!load) return -1;
+    int64_t best = n + 1;
+    opt_dfs(w, n, c, 0, load, 0, &best);
+    free(load);
+    return n == 0 ? 0 : best;
+}
+
+/* Largest sum of f(x_i, l) over all multisets of integer sizes x_i in [1, c]
+ * with sum x_i <= c (an unbounded knapsack solved exactly by dynamic
+ * programming).  f is dual feasible (Sec. 3.1) iff this is <= f(c, l) and
+ * f(0, l) == 0. */
+int64_t orc_dff_knapsack_max(int d, int64_t l, int64_t c)
+{
+    int64_t *best = (int64_t *)calloc((size_t)(c + 1), sizeof(int64_t));
+    if (!best) return -1;
+    for (int64_t s = 1; s <= c; s++) {
+        int64_t b = best[s - 1];
+        for (int64_t x = 1; x <= s; x++) {
+            int64_t v = best[s - x] + orc_dff(d, x, l, c);
+            if (v > b) b = v;
+        }
+        best[s] = b;
+    }
+    int64_t out = best[c];
+    free(best);
+    return out;
+}
+
+/* Batch helper for timing and sampling: runs orc_lb on B instances given as
+ * ragged (offsets[B+1], sizes) with per-instance capacity and bins. */
+int orc_lb_batch(int64_t B, const int64_t *offsets, const int64_t *sizes,
+                 const int64_t *cap, const int64_t *bins, int vb2_cap,
+                 int64_t *out_bound, int32_t *out_dff, int64_t *out_lambda,
+                 uint8_t *out_feasible)
+{
+    for (int64_t b = 0; b < B; b++) {
+        int ok = orc_lb(sizes + offsets[b], offsets[b + 1] - offsets[b], cap[b],
+                        bins[b], vb2_cap, &out_bound[b], &out_dff[b],
+                        &out_lambda[b]);
+        if (ok < 0) return -1;
+        out_feasible[b] = (uint8_t)ok;
+    }
+    return 0;
+}
