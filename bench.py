@@ -1,0 +1,370 @@
+#!/usr/bin/env python3
+"""Benchmark of the DFF lower-bound feasibility check on GB300.
+
+Workload (one step): the search-node batch -- one base instance of n = 500
+items with sizes uniform in [1, c/2], c = 10^4, k = ceil(sum/c) + 1 bins, and
+4096 partial packings of it (a uniform 0..60% of the items committed to random
+bins without overflow).  A step reduces every node on the device (Sec. 3,
+Fig. 3) and evaluates the full collection of DFF bounds (Alg. 2, all six DFFs
+and all their integer parameters) for each of them: one bp_lb_eval_nodes call.
+
+Reported: batched feasibility checks/s (value), item-parameter evals/s, the
+plain one-check-per-launch path (bp_lb_eval_node: H2D, one launch, D2H, sync)
+with its p50/p99 latency, the end-to-end rate with host buffers, the roofline
+of the evaluation kernel against the integer issue rate, and the CPU oracle on
+a bounded sample of the same workload.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+(N > 1 under torch.distributed.run: every rank runs its own batch; weak scaling.)
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "feasibility checks/s and item-param evals/s, batched vs plain; p50/p99 ms"
+UNIT = "checks/s"
+WORKLOAD = "search-node batch: 4096 partial packings of n=500 items, sizes U[1,c/2], c=10000"
+NODES, N_ITEMS, CAP = 4096, 500, 10_000
+
+# Integer operations per (item, parameter) pair in the kernel's formulation of
+# each DFF (compare/select/add for MT and RAD2; multiply-high division for the
+# others); see the evaluators in csrc/bp_lb_eval.cuh.
+OPS_PER_EVAL = {0: 2, 1: 4, 2: 7, 3: 3, 4: 4, 5: 6}
+OPS_PER_EVAL_VB2_FLOAT = 5
+SM_COUNT_NOMINAL = 152
+
+
+def param_counts(c):
+    from paper_2402_14821_gb300 import binding as B
+    return [B.bp_lb_param_count(d, c)[0] for d in range(6)]
+
+
+def reduced_sizes(nd):
+    """r of each node: unpacked items + non-empty bins (all sizes are >= 1)."""
+    r = np.empty(nd.count, dtype=np.int64)
+    for j in range(nd.count):
+        a = nd.assign[nd.assign_offsets[j]:nd.assign_offsets[j + 1]]
+        r[j] = int(np.sum(a == -1)) + len(np.unique(a[a >= 0]))
+    return r
+
+
+def algorithmic_work(nd):
+    """(item-parameter evals, integer ops) of one batch."""
+    r = reduced_sizes(nd)
+    evals = ops = 0
+    for j in range(nd.count):
+        c = int(nd.base.capacity[nd.node_base[j]])
+        cnt = param_counts(c)
+        for d in range(6):
+            per = OPS_PER_EVAL[d]
+            if d == 4 and c > 65535:
+                per = OPS_PER_EVAL_VB2_FLOAT
+            evals += int(r[j]) * cnt[d]
+            ops += int(r[j]) * cnt[d] * per
+    return evals, ops
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self._t.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg
+# ---------------------------------------------------------------------------
+def oracle_rate(nd, budget_s: float, threads: int):
+    """Checks/s of the oracle (reduction + full bound) over a bounded sample of
+    the nodes, run on `threads` host threads (ctypes releases the GIL)."""
+    import oracle
+    orc = oracle.load()
+
+    def one(j):
+        w, a, c, k = nd.node(j)
+        orc.lb(orc.reduce(w, a, k, c), c, k)
+
+    t0 = time.perf_counter()
+    one(0)
+    t_one = max(time.perf_counter() - t0, 1e-4)
+    m = int(max(threads, min(nd.count, budget_s / t_one)))
+    m = min(m, nd.count)
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(one, range(m)))
+    wall = time.perf_counter() - t0
+    return m / wall, m, wall
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--plain-sample", type=int, default=1024)
+    ap.add_argument("--cpu-budget", type=float, default=15.0,
+                    help="CPU-seconds of oracle work for the cpu_baseline sample")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    from paper_2402_14821_gb300 import instances as I
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        nd = I.search_nodes(seed=1, n=N_ITEMS, c=CAP, nodes=NODES)
+        threads = os.cpu_count() or 1
+        budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+        for _ in range(args.warmup):
+            oracle_rate(nd, budget * 0.25, threads)
+        rates, walls, sample = [], [], 0
+        for _ in range(args.steps):
+            rate, m, wall = oracle_rate(nd, budget * threads, threads)
+            rates.append(rate)
+            walls.append(wall / m)
+            sample = m
+        value = float(np.mean(rates))
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": float(np.mean(walls)) * 1e3 * NODES, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "nodes": NODES, "n": N_ITEMS, "c": CAP},
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                 "sample": f"{sample} of the {NODES} nodes per step, reduction + "
+                                           f"full bound, {threads} host threads"},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    from paper_2402_14821_gb300 import binding as B
+    from paper_2402_14821_gb300 import build
+
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    build.build()
+    dev = torch.device("cuda")
+    stream = torch.cuda.current_stream()
+
+    nd = I.search_nodes(seed=1 + rank, n=N_ITEMS, c=CAP, nodes=NODES)
+    evals, ops = algorithmic_work(nd)
+
+    def d(x, dt):
+        return torch.from_numpy(np.ascontiguousarray(x)).to(dt).to(dev)
+
+    t_in = dict(base_offsets=d(nd.base.offsets, torch.int64), base_sizes=d(nd.base.sizes, torch.int32),
+                base_capacity=d(nd.base.capacity, torch.int64), node_base=d(nd.node_base, torch.int32),
+                assign_offsets=d(nd.assign_offsets, torch.int64), assign=d(nd.assign, torch.int32),
+                bins=d(nd.bins, torch.int64))
+    max_bins = int(nd.bins.max())
+    out_b = torch.empty(NODES, dtype=torch.int64, device=dev)
+    out_a = B.argmax_tensor(NODES)
+    out_f = torch.empty(NODES, dtype=torch.uint8, device=dev)
+    h = B.bp_lb_create(CAP, 1 << 16)
+    B.bp_lb_reserve(h, NODES)
+
+    def step():
+        B.bp_lb_eval_nodes(h, max_bins=max_bins, out_bound=out_b, out_argmax=out_a,
+                           out_feasible=out_f, stream=stream, **t_in)
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident batched path ---------------------------------------
+    for _ in range(max(3, args.warmup)):
+        step()
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        barrier()
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record(stream)
+            step()
+            e1.record(stream)
+        barrier()
+    step_ms = np.array([e0.elapsed_time(e1) for e0, e1 in ev])
+    t_step = float(step_ms.mean())
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step = float(t.item())
+    value = NODES * world / (t_step / 1e3)
+
+    # ---- end to end through the C ABI with host buffers ---------------------
+    pin = {k: v.cpu().pin_memory() for k, v in t_in.items()}
+    h_b = torch.empty(NODES, dtype=torch.int64).pin_memory()
+    h_a = torch.empty((NODES, 2), dtype=torch.int64).pin_memory()
+    h_f = torch.empty(NODES, dtype=torch.uint8).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in pin.values())
+    d2h = h_b.numel() * 8 + h_a.numel() * 8 + h_f.numel()
+
+    def e2e_step():
+        for k2, v in pin.items():
+            t_in[k2].copy_(v, non_blocking=True)
+        step()
+        h_b.copy_(out_b, non_blocking=True)
+        h_a.copy_(out_a, non_blocking=True)
+        h_f.copy_(out_f, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    t_e2e = e0.elapsed_time(e1) / args.steps
+    e2e_value = NODES * world / (t_e2e / 1e3)
+
+    # ---- plain path: one check per launch ------------------------------------
+    lat = []
+    for j in range(min(args.plain_sample, NODES)):
+        w, a, c, k = nd.node(j)
+        t0 = time.perf_counter()
+        B.bp_lb_eval_node(h, w, a, k)
+        lat.append(time.perf_counter() - t0)
+    lat = np.array(lat[8:]) * 1e3  # drop the first calls (warm-up)
+    plain_rate = 1e3 / float(lat.mean())
+
+    # correctness spot check of the timed batch against the plain path
+    torch.cuda.synchronize()
+    for j in (0, NODES // 2, NODES - 1):
+        w, a, c, k = nd.node(j)
+        assert B.bp_lb_eval_node(h, w, a, k)[0] == int(out_b[j].item())
+
+    B.bp_lb_destroy(h)
+    if rank != 0:
+        return
+
+    # ---- CPU oracle baseline ---------------------------------------------------
+    threads = os.cpu_count() or 1
+    cpu_rate, cpu_m, cpu_wall = oracle_rate(nd, args.cpu_budget, threads)
+
+    peaks = measured_peaks()
+    sm_mhz_max = float(peaks.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak_ops = sms * 4 * 32 * sm_mhz_max * 1e6        # one warp instruction / clk / SMSP
+    achieved = ops / (t_step / 1e3)
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nodes": NODES, "n": N_ITEMS, "c": CAP,
+                   "evals_per_step": evals, "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": f"independent batches per rank x{world}"},
+        "evals_per_s": evals * world / (t_step / 1e3),
+        "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+        "plain": {"value": plain_rate, "unit": UNIT, "p50_ms": float(np.percentile(lat, 50)),
+                  "p99_ms": float(np.percentile(lat, 99)), "sample": len(lat),
+                  "call": "bp_lb_eval_node (H2D, 1 launch, D2H, sync)"},
+        "batched_over_plain": value / world / plain_rate,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9,
+                     "unit": "Gop/s", "frac": achieved / peak_ops, "traffic": None,
+                     "peak_basis": f"{sms} SMs x 4 SMSP x 32 lanes x {sm_mhz_max:.0f} MHz "
+                                   "(integer issue, one warp instruction per clock per SMSP)",
+                     "kernel": "eval_kernel (plan_kernel included in the timed step)"},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+        "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{cpu_m} of the {NODES} nodes (reduction + full bound), "
+                                   f"{cpu_wall:.1f} s wall on {threads} threads"},
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,235 @@
+/*
+ * bp_lb.h -- C ABI of the GB300 (sm_103a) DFF lower-bound feasibility check
+ * for the bin_packing constraint.
+ *
+ * Method: Tardivo, Michel, Pontelli, "Constraint Propagation on GPU: A Case
+ * Study for the Bin Packing Constraint" (arXiv 2402.14821).
+ *
+ * What one check computes (Sec. 3 "Feasibility check", Sec. 3.1, Alg. 2):
+ *   given the reduced instance W_R = [w'_1 .. w'_r] of a partial packing
+ *   (unpacked items plus one virtual item per bin holding that bin's packed
+ *   load, Fig. 3), a capacity c and a bin count k,
+ *     for each DFF f in (MT, RAD2, FS1, CCM1, VB2, BJ1) and each integer
+ *     parameter lambda in its range,
+ *       lb(f, lambda) = ceil( sum_i f(w'_i, lambda) / f(c, lambda) )
+ *     LB = max over all (f, lambda) of lb(f, lambda)
+ *     the partial packing is infeasible iff LB > k.
+ *   Parameter ranges (integer lambda): MT [0, c/2], RAD2 [c/4 + 1, c/3],
+ *   FS1 [1, 100], CCM1 [1, c/2], VB2 [2, c], BJ1 [1, c] (integer division).
+ *   The returned LB is always the full maximum (the early exit of Alg. 2 is
+ *   not taken), so it does not depend on evaluation order.  The argmax is the
+ *   first (f, lambda) attaining LB in the order above, lambda ascending.
+ *   All arithmetic is exact integer arithmetic; results are bit-exact.
+ *
+ * Limits: 1 <= c <= 2^30; 0 <= every size <= c; r <= 2^20 per instance.
+ *
+ * Conventions
+ *   - Every function returns a status code (BP_OK = 0 or a BP_E* value).
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory of the device current when the handle was created.
+ *   - The caller owns every input and output buffer.  A handle owns only its
+ *     own scratch (per-instance result slots, tile tables, staging buffers).
+ *   - Calls taking a `stream` (a cudaStream_t passed as void*; NULL = legacy
+ *     default stream) are asynchronous and stream-ordered: outputs are valid
+ *     once the stream has reached the call.  Inputs must stay valid and
+ *     unchanged until then.
+ *   - Per-instance domain errors found on the device (a size < 0 or > c, a
+ *     capacity outside [1, 2^30], a negative bin count, a bad assignment or an
+ *     overfull bin) do not fail the call: that instance's out_bound is set to
+ *     -BP_ERANGE, its argmax to {-1, 0, -1} and its out_feasible to 0.
+ *   - A handle is not thread-safe: calls on one handle must not overlap on
+ *     the host, and asynchronous calls on one handle must be ordered on one
+ *     stream (they share the handle's scratch).
+ */
+#ifndef BP_LB_H
+#define BP_LB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define BP_OK        0
+#define BP_EINVAL    1  /* bad argument (NULL pointer, negative count, ...)     */
+#define BP_ERANGE    2  /* a value outside the limits above                      */
+#define BP_ENOMEM    3  /* a device or pinned-host allocation failed            */
+#define BP_ECUDA     4  /* a CUDA runtime call failed                             */
+#define BP_ETIMEOUT  5  /* a bounded wait ran out (serving layer)                 */
+#define BP_EBUSY     6  /* admission refused: not enough memory budget or slots  */
+
+/* DFF indices, in the paper's order (Alg. 2). */
+#define BP_DFF_MT    0
+#define BP_DFF_RAD2  1
+#define BP_DFF_FS1   2
+#define BP_DFF_CCM1  3
+#define BP_DFF_VB2   4
+#define BP_DFF_BJ1   5
+
+typedef struct bp_lb bp_lb_t;            /* opaque handle */
+
+/* The (DFF, lambda) pair attaining the bound: dff in 0..5, lambda its
+ * integer parameter.  16 bytes, naturally aligned. */
+typedef struct {
+    int32_t dff;
+    int32_t pad;      /* always 0 */
+    int64_t lambda;
+} bp_argmax_t;
+
+/* Human-readable name of a status code (static storage). */
+const char *bp_lb_strerror(int status);
+
+/* ---- handle ---------------------------------------------------------- */
+
+/* Creates a handle on the current CUDA device.
+ *   capacity   default bin capacity c of bp_lb_eval / bp_lb_eval_node,
+ *              1 <= capacity <= 2^30;
+ *   max_items  largest reduced instance (and largest assignment) the plain
+ *              single-check calls accept, 1 <= max_items <= 2^20; the handle
+ *              allocates device and pinned staging of this size up front.
+ * On success *out receives the handle.  Errors: BP_EINVAL (out NULL),
+ * BP_ERANGE, BP_ENOMEM, BP_ECUDA. */
+int bp_lb_create(int64_t capacity, int64_t max_items, bp_lb_t **out);
+
+/* Releases the handle and its scratch.  Synchronises the device first.
+ * NULL is accepted and ignored. */
+int bp_lb_destroy(bp_lb_t *h);
+
+/* Grows the handle's batch scratch to hold at least max_batch instances or
+ * nodes, so that later batch calls with B <= max_batch allocate nothing
+ * (required before capturing batch calls into a CUDA graph).
+ * Errors: BP_EINVAL, BP_ENOMEM. */
+int bp_lb_reserve(bp_lb_t *h, int32_t max_batch);
+
+/* ---- plain path: one check, one launch (Alg. 3 shape) ------------------ */
+
+/* One feasibility check of a reduced instance held in HOST memory, against
+ * the handle's capacity.  Copies sizes[0..n) host->device, runs one kernel
+ * launch for all six DFFs, copies the result back and synchronises (so the
+ * call returns with the answer).
+ *   sizes      host, n int32 item sizes of W_R, each in [0, c]; any order;
+ *   n          0 <= n <= max_items (n = 0 gives LB = 0, argmax {MT, 0});
+ *   bins       k >= 0;
+ *   out_bound  host, receives LB;
+ *   out_argmax host, receives the first attaining (DFF, lambda); may be NULL.
+ * Returns BP_OK, or BP_EINVAL / BP_ERANGE (checked on the host before any
+ * copy), BP_ECUDA.  The verdict is (*out_bound <= bins). */
+int bp_lb_eval(bp_lb_t *h, const int32_t *sizes, int64_t n, int64_t bins,
+               int64_t *out_bound, bp_argmax_t *out_argmax);
+
+/* Plain check of one search node given as a partial packing in HOST memory:
+ * base item sizes w[0..n) and assign[0..n) (-1 = unpacked, else the bin in
+ * [0, bins)).  The reduction (Sec. 3, Fig. 3) runs on the device inside the
+ * same single launch.  n <= max_items, bins <= max_items.  Same outputs and
+ * errors as bp_lb_eval (an overfull bin gives BP_ERANGE). */
+int bp_lb_eval_node(bp_lb_t *h, const int32_t *w, const int32_t *assign,
+                    int64_t n, int64_t bins, int64_t *out_bound,
+                    bp_argmax_t *out_argmax);
+
+/* ---- batched path: device pointers, stream-ordered --------------------- */
+
+/* B independent checks of reduced instances in DEVICE memory, all in one
+ * stream-ordered pass (a planning launch and one persistent evaluation launch
+ * over a ragged (instance, DFF, lambda-tile) grid; capturable in a CUDA graph
+ * once bp_lb_reserve(h, B) has been called).
+ *   B            number of instances, 0 <= B (B = 0 is a no-op);
+ *   d_offsets    device int64[B+1]: instance b is d_sizes[d_offsets[b] ..
+ *                d_offsets[b+1]), non-decreasing;
+ *   d_sizes      device int32 sizes (bp_lb_eval_batch_i64: int64);
+ *   d_capacity   device int64[B], c of each instance;
+ *   d_bins       device int64[B], k of each instance;
+ *   d_out_bound  device int64[B], receives LB (or -BP_ERANGE, see above);
+ *   d_out_argmax device bp_argmax_t[B], may be NULL;
+ *   d_out_feasible device uint8[B] (1 iff LB <= k), may be NULL;
+ *   stream       cudaStream_t or NULL.
+ * Errors: BP_EINVAL (NULL required pointer, B < 0), BP_ENOMEM, BP_ECUDA. */
+int bp_lb_eval_batch(bp_lb_t *h, int32_t B, const int64_t *d_offsets,
+                     const int32_t *d_sizes, const int64_t *d_capacity,
+                     const int64_t *d_bins, int64_t *d_out_bound,
+                     bp_argmax_t *d_out_argmax, uint8_t *d_out_feasible,
+                     void *stream);
+
+int bp_lb_eval_batch_i64(bp_lb_t *h, int32_t B, const int64_t *d_offsets,
+                         const int64_t *d_sizes, const int64_t *d_capacity,
+                         const int64_t *d_bins, int64_t *d_out_bound,
+                         bp_argmax_t *d_out_argmax, uint8_t *d_out_feasible,
+                         void *stream);
+
+/* B search nodes in DEVICE memory: each node is a partial packing of one of
+ * the base instances; its reduced instance (Sec. 3 "Feasibility check",
+ * Fig. 3: unpacked items plus one virtual item of size equal to the packed
+ * load per non-empty bin) is built on the device inside the evaluation launch
+ * and checked as in bp_lb_eval_batch.
+ *   num_base         I, the number of base instances;
+ *   d_base_offsets   device int64[I+1] ragged offsets of the base instances;
+ *   d_base_sizes     device int32 base item sizes;
+ *   d_base_capacity  device int64[I], c of each base instance;
+ *   d_node_base      device int32[B], base instance of each node (0..I-1);
+ *   d_assign_offsets device int64[B+1]: node b's assignment is
+ *                    d_assign[d_assign_offsets[b] ..) with exactly n = size of
+ *                    its base instance entries;
+ *   d_assign         device int32: -1 unpacked, else bin index in [0, bins);
+ *   d_bins           device int64[B], k of each node, 0 <= k <= max_bins;
+ *   max_bins         host bound on every d_bins[b], 0 <= max_bins <= 16384
+ *                    (sizes the on-chip load table; BP_ERANGE above it);
+ *   outputs as for bp_lb_eval_batch.
+ * A node with an out-of-range bin index or an overfull bin gets the
+ * per-instance error described above. */
+int bp_lb_eval_nodes(bp_lb_t *h, int32_t B, int32_t num_base,
+                     const int64_t *d_base_offsets,
+                     const int32_t *d_base_sizes, const int64_t *d_base_capacity,
+                     const int32_t *d_node_base, const int64_t *d_assign_offsets,
+                     const int32_t *d_assign, const int64_t *d_bins,
+                     int64_t max_bins, int64_t *d_out_bound,
+                     bp_argmax_t *d_out_argmax, uint8_t *d_out_feasible,
+                     void *stream);
+
+/* The reduction alone (Sec. 3 "Feasibility check", Fig. 3), for B nodes laid
+ * out as in bp_lb_eval_nodes.  Node b's reduced instance is written to
+ * d_out_sizes[d_out_offsets[b] ..) -- the caller reserves n + bins entries
+ * there -- as the unpacked items in index order followed by the loads of the
+ * non-empty bins in bin order; d_out_count[b] receives its length r, or
+ * -BP_ERANGE for a node with a bad assignment or an overfull bin.
+ * Errors: BP_EINVAL, BP_ERANGE (max_bins), BP_ECUDA. */
+int bp_lb_reduce_nodes(bp_lb_t *h, int32_t B, int32_t num_base,
+                       const int64_t *d_base_offsets,
+                       const int32_t *d_base_sizes,
+                       const int64_t *d_base_capacity,
+                       const int32_t *d_node_base,
+                       const int64_t *d_assign_offsets,
+                       const int32_t *d_assign, const int64_t *d_bins,
+                       int64_t max_bins, const int64_t *d_out_offsets,
+                       int32_t *d_out_sizes, int64_t *d_out_count,
+                       void *stream);
+
+/* ---- inspection -------------------------------------------------------- */
+
+/* Per-parameter bounds for spot checks of very long sweeps: for j < m,
+ * d_out_lb[j] = lb(d_dff[j], d_lambda[j]) of the single reduced instance
+ * d_sizes[0..n) with capacity c, computed by the same device code as the
+ * batched path (one lambda per lane).  A lambda outside its DFF's range
+ * gives -BP_ERANGE.  Device pointers; stream-ordered. */
+int bp_lb_debug_params(bp_lb_t *h, const int32_t *d_sizes, int64_t n,
+                       int64_t c, const int32_t *d_dff,
+                       const int64_t *d_lambda, int64_t m, int64_t *d_out_lb,
+                       void *stream);
+
+/* Number of integer parameters of DFF d at capacity c (0 for an empty
+ * range), and the range itself; host-only helper, no device work.
+ * Returns -1 for a bad d or c. */
+int64_t bp_lb_param_count(int32_t d, int64_t c, int64_t *lo, int64_t *hi);
+
+/* Host-side exhaustive self-check of the exact division used by the kernels
+ * (Granlund-Montgomery multiply-high division by invariant integers):
+ * compares it with '/' for every divisor in [d_lo, d_hi] on every numerator
+ * in [0, n_hi] and on `samples` pseudo-random numerators in [0, 2^31).
+ * Returns the number of mismatches (0 expected), -1 on bad arguments. */
+int64_t bp_lb_selfcheck_division(uint32_t d_lo, uint32_t d_hi, uint32_t n_hi,
+                                 int64_t samples);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BP_LB_H */

@@ -1,0 +1,234 @@
+"""Thin Python binding of the C ABI in include/bp_lb.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls.  Device
+buffers are torch CUDA tensors (only their data pointers are passed); the
+stream defaults to torch's current stream.  The CUDA library must have been
+built (``paper_2402_14821_gb300.build.build()``); there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbp_lb.so")
+
+BP_OK, BP_EINVAL, BP_ERANGE, BP_ENOMEM, BP_ECUDA, BP_ETIMEOUT, BP_EBUSY = range(7)
+DFF_NAMES = ("MT", "RAD2", "FS1", "CCM1", "VB2", "BJ1")
+
+_c_i64 = ctypes.c_int64
+_c_i32 = ctypes.c_int32
+_vp = ctypes.c_void_p
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+class BpArgmax(ctypes.Structure):
+    _fields_ = [("dff", ctypes.c_int32), ("pad", ctypes.c_int32), ("lam", ctypes.c_int64)]
+
+
+class BpLbError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {strerror(status)} ({status})")
+
+
+_lib = None
+
+
+def _bind(lib):
+    P = ctypes.POINTER
+    sig = {
+        "bp_lb_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "bp_lb_create": (ctypes.c_int, [_c_i64, _c_i64, P(_vp)]),
+        "bp_lb_destroy": (ctypes.c_int, [_vp]),
+        "bp_lb_reserve": (ctypes.c_int, [_vp, _c_i32]),
+        "bp_lb_eval": (ctypes.c_int, [_vp, _vp, _c_i64, _c_i64, _i64p, P(BpArgmax)]),
+        "bp_lb_eval_node": (ctypes.c_int, [_vp, _vp, _vp, _c_i64, _c_i64, _i64p, P(BpArgmax)]),
+        "bp_lb_eval_batch": (ctypes.c_int, [_vp, _c_i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+        "bp_lb_eval_batch_i64": (ctypes.c_int, [_vp, _c_i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+        "bp_lb_eval_nodes": (ctypes.c_int, [_vp, _c_i32, _c_i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                            _c_i64, _vp, _vp, _vp, _vp]),
+        "bp_lb_reduce_nodes": (ctypes.c_int, [_vp, _c_i32, _c_i32, _vp, _vp, _vp, _vp, _vp, _vp,
+                                              _vp, _c_i64, _vp, _vp, _vp, _vp]),
+        "bp_lb_debug_params": (ctypes.c_int, [_vp, _vp, _c_i64, _c_i64, _vp, _vp, _c_i64, _vp, _vp]),
+        "bp_lb_param_count": (_c_i64, [_c_i32, _c_i64, _i64p, _i64p]),
+        "bp_lb_selfcheck_division": (_c_i64, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                              _c_i64]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+def lib():
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "paper_2402_14821_gb300.build.build()")
+        _lib = _bind(ctypes.CDLL(LIB_PATH))
+    return _lib
+
+
+EXPORTED = ("bp_lb_strerror", "bp_lb_create", "bp_lb_destroy", "bp_lb_reserve", "bp_lb_eval",
+            "bp_lb_eval_node", "bp_lb_eval_batch", "bp_lb_eval_batch_i64", "bp_lb_eval_nodes",
+            "bp_lb_reduce_nodes", "bp_lb_debug_params", "bp_lb_param_count",
+            "bp_lb_selfcheck_division")
+
+
+def strerror(status: int) -> str:
+    return lib().bp_lb_strerror(status).decode()
+
+
+def _check(status: int, where: str):
+    if status != BP_OK:
+        raise BpLbError(status, where)
+
+
+# -- tensor marshalling --------------------------------------------------------
+def _ptr(t, dtype=None, name="tensor"):
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def argmax_tensor(B: int, device="cuda"):
+    """A [B, 2] int64 tensor laid out as B bp_argmax_t records."""
+    import torch
+    return torch.empty((B, 2), dtype=torch.int64, device=device)
+
+
+def decode_argmax(t):
+    """(dff int32 array, lambda int64 array) from an argmax tensor / array."""
+    a = t.cpu().numpy() if hasattr(t, "cpu") else np.asarray(t)
+    a = np.ascontiguousarray(a, dtype=np.int64)
+    return (a[:, 0] & 0xFFFFFFFF).astype(np.int64).astype(np.int32), a[:, 1].copy()
+
+
+# -- handle ----------------------------------------------------------------------
+def bp_lb_create(capacity: int, max_items: int):
+    h = _vp()
+    _check(lib().bp_lb_create(int(capacity), int(max_items), ctypes.byref(h)), "bp_lb_create")
+    return h
+
+
+def bp_lb_destroy(h):
+    _check(lib().bp_lb_destroy(h), "bp_lb_destroy")
+
+
+def bp_lb_reserve(h, max_batch: int):
+    _check(lib().bp_lb_reserve(h, int(max_batch)), "bp_lb_reserve")
+
+
+# -- plain path ------------------------------------------------------------------
+def bp_lb_eval(h, sizes, bins: int):
+    """Host sizes (int32) -> (bound, dff, lambda)."""
+    a = np.ascontiguousarray(np.asarray(sizes, dtype=np.int32))
+    b = ctypes.c_int64()
+    am = BpArgmax()
+    _check(lib().bp_lb_eval(h, a.ctypes.data, len(a), int(bins), ctypes.byref(b), ctypes.byref(am)),
+           "bp_lb_eval")
+    return b.value, am.dff, am.lam
+
+
+def bp_lb_eval_node(h, w, assign, bins: int):
+    """Host base sizes + assignment -> (bound, dff, lambda)."""
+    wa = np.ascontiguousarray(np.asarray(w, dtype=np.int32))
+    aa = np.ascontiguousarray(np.asarray(assign, dtype=np.int32))
+    if len(wa) != len(aa):
+        raise ValueError("w and assign differ in length")
+    b = ctypes.c_int64()
+    am = BpArgmax()
+    _check(lib().bp_lb_eval_node(h, wa.ctypes.data, aa.ctypes.data, len(wa), int(bins),
+                                 ctypes.byref(b), ctypes.byref(am)), "bp_lb_eval_node")
+    return b.value, am.dff, am.lam
+
+
+# -- batched path ------------------------------------------------------------------
+def bp_lb_eval_batch(h, offsets, sizes, capacity, bins, out_bound, out_argmax=None,
+                     out_feasible=None, stream=None):
+    import torch
+    B = offsets.numel() - 1
+    fn = lib().bp_lb_eval_batch if sizes.dtype == torch.int32 else lib().bp_lb_eval_batch_i64
+    if sizes.dtype not in (torch.int32, torch.int64):
+        raise TypeError("sizes must be int32 or int64")
+    _check(fn(h, B, _ptr(offsets, torch.int64, "offsets"), _ptr(sizes, None, "sizes"),
+              _ptr(capacity, torch.int64, "capacity"), _ptr(bins, torch.int64, "bins"),
+              _ptr(out_bound, torch.int64, "out_bound"), _ptr(out_argmax, torch.int64, "out_argmax"),
+              _ptr(out_feasible, torch.uint8, "out_feasible"), _stream(stream)), "bp_lb_eval_batch")
+
+
+def bp_lb_eval_batch_i64(h, offsets, sizes, capacity, bins, out_bound, out_argmax=None,
+                         out_feasible=None, stream=None):
+    import torch
+    if sizes.dtype != torch.int64:
+        raise TypeError("sizes must be int64")
+    bp_lb_eval_batch(h, offsets, sizes, capacity, bins, out_bound, out_argmax, out_feasible, stream)
+
+
+def bp_lb_eval_nodes(h, base_offsets, base_sizes, base_capacity, node_base, assign_offsets,
+                     assign, bins, max_bins: int, out_bound, out_argmax=None, out_feasible=None,
+                     stream=None):
+    import torch
+    B = node_base.numel()
+    I = base_offsets.numel() - 1
+    _check(lib().bp_lb_eval_nodes(
+        h, B, I, _ptr(base_offsets, torch.int64, "base_offsets"),
+        _ptr(base_sizes, torch.int32, "base_sizes"), _ptr(base_capacity, torch.int64, "base_capacity"),
+        _ptr(node_base, torch.int32, "node_base"), _ptr(assign_offsets, torch.int64, "assign_offsets"),
+        _ptr(assign, torch.int32, "assign"), _ptr(bins, torch.int64, "bins"), int(max_bins),
+        _ptr(out_bound, torch.int64, "out_bound"), _ptr(out_argmax, torch.int64, "out_argmax"),
+        _ptr(out_feasible, torch.uint8, "out_feasible"), _stream(stream)), "bp_lb_eval_nodes")
+
+
+def bp_lb_reduce_nodes(h, base_offsets, base_sizes, base_capacity, node_base, assign_offsets,
+                       assign, bins, max_bins: int, out_offsets, out_sizes, out_count, stream=None):
+    import torch
+    B = node_base.numel()
+    I = base_offsets.numel() - 1
+    _check(lib().bp_lb_reduce_nodes(
+        h, B, I, _ptr(base_offsets, torch.int64, "base_offsets"),
+        _ptr(base_sizes, torch.int32, "base_sizes"), _ptr(base_capacity, torch.int64, "base_capacity"),
+        _ptr(node_base, torch.int32, "node_base"), _ptr(assign_offsets, torch.int64, "assign_offsets"),
+        _ptr(assign, torch.int32, "assign"), _ptr(bins, torch.int64, "bins"), int(max_bins),
+        _ptr(out_offsets, torch.int64, "out_offsets"), _ptr(out_sizes, torch.int32, "out_sizes"),
+        _ptr(out_count, torch.int64, "out_count"), _stream(stream)), "bp_lb_reduce_nodes")
+
+
+def bp_lb_debug_params(h, sizes, c: int, dff, lam, out_lb, stream=None):
+    import torch
+    _check(lib().bp_lb_debug_params(h, _ptr(sizes, torch.int32, "sizes"), sizes.numel(), int(c),
+                                    _ptr(dff, torch.int32, "dff"), _ptr(lam, torch.int64, "lam"),
+                                    dff.numel(), _ptr(out_lb, torch.int64, "out_lb"),
+                                    _stream(stream)), "bp_lb_debug_params")
+
+
+def bp_lb_param_count(d: int, c: int):
+    lo, hi = ctypes.c_int64(), ctypes.c_int64()
+    n = lib().bp_lb_param_count(int(d), int(c), ctypes.byref(lo), ctypes.byref(hi))
+    return n, lo.value, hi.value
+
+
+def bp_lb_selfcheck_division(d_lo: int, d_hi: int, n_hi: int, samples: int) -> int:
+    return lib().bp_lb_selfcheck_division(d_lo, d_hi, n_hi, samples)

@@ -1,0 +1,447 @@
+// bp_lb.cu -- C ABI of the DFF lower-bound feasibility check (include/bp_lb.h).
+//
+// Host side: argument checks, handle-owned scratch, launch configuration and
+// the plain single-check path (one H2D copy, one kernel launch, one D2H copy,
+// one synchronisation -- the shape of Alg. 3 with the six per-DFF launches
+// merged into one).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/bp_lb.h"
+#include "bp_lb_core.cuh"
+#include "bp_lb_eval.cuh"
+#include "bp_lb_kernels.cuh"
+
+using namespace bplb;
+
+namespace {
+
+constexpr int kNT = 256;
+constexpr int kT = 4;
+constexpr int kLPT = kNT * kT;
+constexpr size_t kListBytes = 2 * sizeof(uint32_t) * kListTop;  // items + fp32 quotients
+
+struct PlainOut {  // device and pinned-host layout of one plain result
+  int64_t bound;
+  int64_t pad;
+  bp_argmax_t arg;
+  uint8_t feasible;
+  uint8_t pad2[15];
+};
+
+}  // namespace
+
+struct bp_lb {
+  int device = 0;
+  int num_sms = 0;
+  int64_t capacity = 0;
+  int64_t max_items = 0;
+  cudaStream_t stream = nullptr;  // plain path
+  // plain path
+  int32_t *d_items = nullptr;
+  int32_t *d_assign = nullptr;
+  int32_t *h_items = nullptr;   // pinned
+  int32_t *h_assign = nullptr;  // pinned
+  PlainOut *d_out = nullptr;
+  PlainOut *h_out = nullptr;    // pinned
+  unsigned long long *d_key1 = nullptr;
+  unsigned int *d_done1 = nullptr;
+  // batch scratch
+  int32_t cap_batch = 0;
+  int64_t *d_tile_start = nullptr;
+  unsigned long long *d_keys = nullptr;
+  unsigned int *d_done = nullptr;
+  unsigned long long *d_work = nullptr;
+  // occupancy cache
+  int occ_ragged32 = 0, occ_ragged64 = 0, occ_nodes = 0;
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return BP_OK;
+  if (e == cudaErrorMemoryAllocation) return BP_ENOMEM;
+  return BP_ECUDA;
+}
+
+#define BP_CHECK(call)                        \
+  do {                                        \
+    const int _s = cuda_status(call);         \
+    if (_s != BP_OK) return _s;               \
+  } while (0)
+
+template <int MODE>
+size_t eval_smem(int64_t max_bins) {
+  return kListBytes + (MODE == kSrcNodes ? sizeof(uint32_t) * (size_t)max_bins : 0);
+}
+
+template <int MODE>
+int occupancy(bp_lb *h, size_t smem) {
+  auto kern = eval_kernel<kNT, kT, MODE>;
+  int blocks = 0;
+  if (smem > 48 * 1024) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return 0;
+  }
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kNT, smem) != cudaSuccess)
+    return 0;
+  return blocks;
+}
+
+int grow_batch(bp_lb *h, int32_t B) {
+  if (B <= h->cap_batch) return BP_OK;
+  int32_t cap = std::max<int32_t>(B, 1024);
+  cudaFree(h->d_tile_start);
+  cudaFree(h->d_keys);
+  cudaFree(h->d_done);
+  h->d_tile_start = nullptr;
+  h->d_keys = nullptr;
+  h->d_done = nullptr;
+  h->cap_batch = 0;
+  BP_CHECK(cudaMalloc(&h->d_tile_start, sizeof(int64_t) * ((size_t)cap + 1)));
+  BP_CHECK(cudaMalloc(&h->d_keys, sizeof(unsigned long long) * (size_t)cap));
+  BP_CHECK(cudaMalloc(&h->d_done, sizeof(unsigned int) * (size_t)cap));
+  BP_CHECK(cudaMemset(h->d_keys, 0, sizeof(unsigned long long) * (size_t)cap));
+  BP_CHECK(cudaMemset(h->d_done, 0, sizeof(unsigned int) * (size_t)cap));
+  h->cap_batch = cap;
+  return BP_OK;
+}
+
+EvalArgs blank_args() {
+  EvalArgs A;
+  std::memset(&A, 0, sizeof(A));
+  return A;
+}
+
+template <int MODE>
+int launch_batch(bp_lb *h, EvalArgs A, size_t smem, cudaStream_t st) {
+  if (A.B == 0) return BP_OK;
+  const int s = grow_batch(h, A.B);
+  if (s != BP_OK) return s;
+  A.tile_start = h->d_tile_start;
+  A.keys = h->d_keys;
+  A.done = h->d_done;
+  A.work = h->d_work;
+  int occ = occupancy<MODE>(h, smem);
+  if (occ <= 0) return BP_ECUDA;
+  plan_kernel<MODE><<<1, 1024, 0, st>>>(A, (int64_t)kLPT, h->d_tile_start);
+  BP_CHECK(cudaGetLastError());
+  const int grid = h->num_sms * occ;
+  eval_kernel<kNT, kT, MODE><<<grid, kNT, smem, st>>>(A);
+  BP_CHECK(cudaGetLastError());
+  return BP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *bp_lb_strerror(int status) {
+  switch (status) {
+    case BP_OK: return "ok";
+    case BP_EINVAL: return "invalid argument";
+    case BP_ERANGE: return "value out of range";
+    case BP_ENOMEM: return "out of memory";
+    case BP_ECUDA: return "CUDA error";
+    case BP_ETIMEOUT: return "timed out";
+    case BP_EBUSY: return "busy: admission refused";
+    default: return "unknown status";
+  }
+}
+
+int bp_lb_create(int64_t capacity, int64_t max_items, bp_lb_t **out) {
+  if (!out) return BP_EINVAL;
+  *out = nullptr;
+  if (capacity < 1 || capacity > kMaxCapacity || max_items < 1 || max_items > kMaxItems)
+    return BP_ERANGE;
+  bp_lb *h = new (std::nothrow) bp_lb();
+  if (!h) return BP_ENOMEM;
+  h->capacity = capacity;
+  h->max_items = max_items;
+  int st = BP_OK;
+  do {
+    if ((st = cuda_status(cudaGetDevice(&h->device))) != BP_OK) break;
+    if ((st = cuda_status(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount,
+                                                 h->device))) != BP_OK)
+      break;
+    if ((st = cuda_status(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking))) != BP_OK)
+      break;
+    const size_t nb = sizeof(int32_t) * (size_t)max_items;
+    if ((st = cuda_status(cudaMalloc(&h->d_items, nb))) != BP_OK) break;
+    if ((st = cuda_status(cudaMalloc(&h->d_assign, nb))) != BP_OK) break;
+    if ((st = cuda_status(cudaMallocHost(&h->h_items, nb))) != BP_OK) break;
+    if ((st = cuda_status(cudaMallocHost(&h->h_assign, nb))) != BP_OK) break;
+    if ((st = cuda_status(cudaMalloc(&h->d_out, sizeof(PlainOut)))) != BP_OK) break;
+    if ((st = cuda_status(cudaMallocHost(&h->h_out, sizeof(PlainOut)))) != BP_OK) break;
+    if ((st = cuda_status(cudaMalloc(&h->d_key1, sizeof(unsigned long long)))) != BP_OK) break;
+    if ((st = cuda_status(cudaMalloc(&h->d_done1, sizeof(unsigned int)))) != BP_OK) break;
+    if ((st = cuda_status(cudaMalloc(&h->d_work, sizeof(unsigned long long)))) != BP_OK) break;
+    if ((st = cuda_status(cudaMemset(h->d_key1, 0, sizeof(unsigned long long)))) != BP_OK) break;
+    if ((st = cuda_status(cudaMemset(h->d_done1, 0, sizeof(unsigned int)))) != BP_OK) break;
+    if ((st = cuda_status(cudaMemset(h->d_work, 0, sizeof(unsigned long long)))) != BP_OK) break;
+    // the plain node path may use the full on-chip bin table
+    const size_t smem_nodes = eval_smem<kSrcNodes>(kMaxNodeBins);
+    if ((st = cuda_status(cudaFuncSetAttribute(eval_kernel<kNT, kT, kSrcNodes>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem_nodes))) != BP_OK)
+      break;
+    if ((st = cuda_status(cudaFuncSetAttribute(reduce_kernel<256>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)(sizeof(uint32_t) * kMaxNodeBins)))) != BP_OK)
+      break;
+    if ((st = cuda_status(cudaDeviceSynchronize())) != BP_OK) break;
+  } while (0);
+  if (st != BP_OK) {
+    bp_lb_destroy(h);
+    return st;
+  }
+  *out = h;
+  return BP_OK;
+}
+
+int bp_lb_destroy(bp_lb_t *h) {
+  if (!h) return BP_OK;
+  cudaDeviceSynchronize();
+  cudaFree(h->d_items);
+  cudaFree(h->d_assign);
+  cudaFreeHost(h->h_items);
+  cudaFreeHost(h->h_assign);
+  cudaFree(h->d_out);
+  cudaFreeHost(h->h_out);
+  cudaFree(h->d_key1);
+  cudaFree(h->d_done1);
+  cudaFree(h->d_work);
+  cudaFree(h->d_tile_start);
+  cudaFree(h->d_keys);
+  cudaFree(h->d_done);
+  if (h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return BP_OK;
+}
+
+int bp_lb_reserve(bp_lb_t *h, int32_t max_batch) {
+  if (!h || max_batch < 0) return BP_EINVAL;
+  return grow_batch(h, max_batch);
+}
+
+static int plain_finish(bp_lb *h, int64_t *out_bound, bp_argmax_t *out_argmax) {
+  BP_CHECK(cudaMemcpyAsync(h->h_out, h->d_out, sizeof(PlainOut), cudaMemcpyDeviceToHost, h->stream));
+  BP_CHECK(cudaStreamSynchronize(h->stream));
+  if (h->h_out->bound < 0) return BP_ERANGE;
+  *out_bound = h->h_out->bound;
+  if (out_argmax) *out_argmax = h->h_out->arg;
+  return BP_OK;
+}
+
+static EvalArgs plain_args(bp_lb *h, int64_t n, int64_t bins) {
+  EvalArgs A = blank_args();
+  A.B = 1;
+  A.out_bound = &h->d_out->bound;
+  A.out_argmax = &h->d_out->arg;
+  A.out_feasible = &h->d_out->feasible;
+  A.tile_start = nullptr;
+  A.single_tiles = tiles_for(h->capacity, kLPT);
+  A.single_c = h->capacity;
+  A.single_k = bins;
+  A.single_n = n;
+  A.keys = h->d_key1;
+  A.done = h->d_done1;
+  A.work = nullptr;
+  return A;
+}
+
+int bp_lb_eval(bp_lb_t *h, const int32_t *sizes, int64_t n, int64_t bins, int64_t *out_bound,
+               bp_argmax_t *out_argmax) {
+  if (!h || !out_bound || (n > 0 && !sizes) || n < 0 || bins < 0) return BP_EINVAL;
+  if (n > h->max_items) return BP_ERANGE;
+  const int64_t c = h->capacity;
+  for (int64_t i = 0; i < n; ++i)
+    if (sizes[i] < 0 || (int64_t)sizes[i] > c) return BP_ERANGE;
+  if (n > 0) {
+    std::memcpy(h->h_items, sizes, sizeof(int32_t) * (size_t)n);
+    BP_CHECK(cudaMemcpyAsync(h->d_items, h->h_items, sizeof(int32_t) * (size_t)n,
+                             cudaMemcpyHostToDevice, h->stream));
+  }
+  EvalArgs A = plain_args(h, n, bins);
+  A.sizes = h->d_items;
+  eval_kernel<kNT, kT, kSrcRaggedI32>
+      <<<(unsigned)A.single_tiles, kNT, eval_smem<kSrcRaggedI32>(0), h->stream>>>(A);
+  BP_CHECK(cudaGetLastError());
+  return plain_finish(h, out_bound, out_argmax);
+}
+
+int bp_lb_eval_node(bp_lb_t *h, const int32_t *w, const int32_t *assign, int64_t n, int64_t bins,
+                    int64_t *out_bound, bp_argmax_t *out_argmax) {
+  if (!h || !out_bound || (n > 0 && (!w || !assign)) || n < 0 || bins < 0) return BP_EINVAL;
+  if (n > h->max_items || bins > h->max_items || bins > kMaxNodeBins) return BP_ERANGE;
+  if (n > 0) {
+    std::memcpy(h->h_items, w, sizeof(int32_t) * (size_t)n);
+    std::memcpy(h->h_assign, assign, sizeof(int32_t) * (size_t)n);
+    BP_CHECK(cudaMemcpyAsync(h->d_items, h->h_items, sizeof(int32_t) * (size_t)n,
+                             cudaMemcpyHostToDevice, h->stream));
+    BP_CHECK(cudaMemcpyAsync(h->d_assign, h->h_assign, sizeof(int32_t) * (size_t)n,
+                             cudaMemcpyHostToDevice, h->stream));
+  }
+  EvalArgs A = plain_args(h, n, bins);
+  A.base_sizes = h->d_items;
+  A.assign = h->d_assign;
+  A.max_bins = (int32_t)bins;
+  eval_kernel<kNT, kT, kSrcNodes>
+      <<<(unsigned)A.single_tiles, kNT, eval_smem<kSrcNodes>(bins), h->stream>>>(A);
+  BP_CHECK(cudaGetLastError());
+  return plain_finish(h, out_bound, out_argmax);
+}
+
+int bp_lb_eval_batch(bp_lb_t *h, int32_t B, const int64_t *d_offsets, const int32_t *d_sizes,
+                     const int64_t *d_capacity, const int64_t *d_bins, int64_t *d_out_bound,
+                     bp_argmax_t *d_out_argmax, uint8_t *d_out_feasible, void *stream) {
+  if (!h || B < 0) return BP_EINVAL;
+  if (B == 0) return BP_OK;
+  if (!d_offsets || !d_sizes || !d_capacity || !d_bins || !d_out_bound) return BP_EINVAL;
+  EvalArgs A = blank_args();
+  A.B = B;
+  A.offsets = d_offsets;
+  A.sizes = d_sizes;
+  A.capacity = d_capacity;
+  A.bins = d_bins;
+  A.out_bound = d_out_bound;
+  A.out_argmax = d_out_argmax;
+  A.out_feasible = d_out_feasible;
+  return launch_batch<kSrcRaggedI32>(h, A, eval_smem<kSrcRaggedI32>(0), (cudaStream_t)stream);
+}
+
+int bp_lb_eval_batch_i64(bp_lb_t *h, int32_t B, const int64_t *d_offsets, const int64_t *d_sizes,
+                         const int64_t *d_capacity, const int64_t *d_bins, int64_t *d_out_bound,
+                         bp_argmax_t *d_out_argmax, uint8_t *d_out_feasible, void *stream) {
+  if (!h || B < 0) return BP_EINVAL;
+  if (B == 0) return BP_OK;
+  if (!d_offsets || !d_sizes || !d_capacity || !d_bins || !d_out_bound) return BP_EINVAL;
+  EvalArgs A = blank_args();
+  A.B = B;
+  A.offsets = d_offsets;
+  A.sizes = d_sizes;
+  A.capacity = d_capacity;
+  A.bins = d_bins;
+  A.out_bound = d_out_bound;
+  A.out_argmax = d_out_argmax;
+  A.out_feasible = d_out_feasible;
+  return launch_batch<kSrcRaggedI64>(h, A, eval_smem<kSrcRaggedI64>(0), (cudaStream_t)stream);
+}
+
+int bp_lb_eval_nodes(bp_lb_t *h, int32_t B, int32_t num_base, const int64_t *d_base_offsets,
+                     const int32_t *d_base_sizes, const int64_t *d_base_capacity,
+                     const int32_t *d_node_base, const int64_t *d_assign_offsets,
+                     const int32_t *d_assign, const int64_t *d_bins, int64_t max_bins,
+                     int64_t *d_out_bound, bp_argmax_t *d_out_argmax, uint8_t *d_out_feasible,
+                     void *stream) {
+  if (!h || B < 0 || num_base < 0) return BP_EINVAL;
+  if (max_bins < 0 || max_bins > kMaxNodeBins) return BP_ERANGE;
+  if (B == 0) return BP_OK;
+  if (!d_base_offsets || !d_base_sizes || !d_base_capacity || !d_node_base || !d_assign_offsets ||
+      !d_assign || !d_bins || !d_out_bound)
+    return BP_EINVAL;
+  EvalArgs A = blank_args();
+  A.B = B;
+  A.num_base = num_base;
+  A.base_offsets = d_base_offsets;
+  A.base_sizes = d_base_sizes;
+  A.base_capacity = d_base_capacity;
+  A.node_base = d_node_base;
+  A.assign_offsets = d_assign_offsets;
+  A.assign = d_assign;
+  A.bins = d_bins;
+  A.max_bins = (int32_t)max_bins;
+  A.out_bound = d_out_bound;
+  A.out_argmax = d_out_argmax;
+  A.out_feasible = d_out_feasible;
+  return launch_batch<kSrcNodes>(h, A, eval_smem<kSrcNodes>(max_bins), (cudaStream_t)stream);
+}
+
+int bp_lb_reduce_nodes(bp_lb_t *h, int32_t B, int32_t num_base, const int64_t *d_base_offsets,
+                       const int32_t *d_base_sizes, const int64_t *d_base_capacity,
+                       const int32_t *d_node_base, const int64_t *d_assign_offsets,
+                       const int32_t *d_assign, const int64_t *d_bins, int64_t max_bins,
+                       const int64_t *d_out_offsets, int32_t *d_out_sizes, int64_t *d_out_count,
+                       void *stream) {
+  if (!h || B < 0 || num_base < 0) return BP_EINVAL;
+  if (max_bins < 0 || max_bins > kMaxNodeBins) return BP_ERANGE;
+  if (B == 0) return BP_OK;
+  if (!d_base_offsets || !d_base_sizes || !d_base_capacity || !d_node_base || !d_assign_offsets ||
+      !d_assign || !d_bins || !d_out_offsets || !d_out_sizes || !d_out_count)
+    return BP_EINVAL;
+  EvalArgs A = blank_args();
+  A.B = B;
+  A.num_base = num_base;
+  A.base_offsets = d_base_offsets;
+  A.base_sizes = d_base_sizes;
+  A.base_capacity = d_base_capacity;
+  A.node_base = d_node_base;
+  A.assign_offsets = d_assign_offsets;
+  A.assign = d_assign;
+  A.bins = d_bins;
+  A.max_bins = (int32_t)max_bins;
+  const int grid = (int)std::min<int64_t>(B, (int64_t)h->num_sms * 8);
+  reduce_kernel<256><<<grid, 256, sizeof(uint32_t) * (size_t)max_bins, (cudaStream_t)stream>>>(
+      A, d_out_offsets, d_out_sizes, d_out_count);
+  BP_CHECK(cudaGetLastError());
+  return BP_OK;
+}
+
+int bp_lb_debug_params(bp_lb_t *h, const int32_t *d_sizes, int64_t n, int64_t c,
+                       const int32_t *d_dff, const int64_t *d_lambda, int64_t m, int64_t *d_out_lb,
+                       void *stream) {
+  if (!h || n < 0 || m < 0 || (n > 0 && !d_sizes)) return BP_EINVAL;
+  if (c < 1 || c > kMaxCapacity || n > kMaxItems) return BP_ERANGE;
+  if (m == 0) return BP_OK;
+  if (!d_dff || !d_lambda || !d_out_lb) return BP_EINVAL;
+  EvalArgs A = blank_args();
+  A.B = 1;
+  A.sizes = d_sizes;
+  A.single_c = c;
+  A.single_k = 0;
+  A.single_n = n;
+  A.single_tiles = 1;
+  const dim3 grid((unsigned)((m + 255) / 256), kNumDff);
+  debug_kernel<256><<<grid, 256, kListBytes, (cudaStream_t)stream>>>(A, d_dff, d_lambda, m,
+                                                                     d_out_lb);
+  BP_CHECK(cudaGetLastError());
+  return BP_OK;
+}
+
+int64_t bp_lb_param_count(int32_t d, int64_t c, int64_t *lo, int64_t *hi) {
+  if (d < 0 || d >= kNumDff || c < 1 || c > kMaxCapacity) return -1;
+  int64_t l, u;
+  param_range(d, c, l, u);
+  if (lo) *lo = l;
+  if (hi) *hi = u;
+  return u >= l ? u - l + 1 : 0;
+}
+
+int64_t bp_lb_selfcheck_division(uint32_t d_lo, uint32_t d_hi, uint32_t n_hi, int64_t samples) {
+  if (d_lo < 1 || d_hi < d_lo || d_hi >= (1u << 31) || n_hi >= (1u << 31) || samples < 0) return -1;
+  int64_t bad = 0;
+  uint64_t x = 0x9E3779B97F4A7C15ull;  // splitmix64 state
+  for (uint64_t d = d_lo; d <= d_hi; ++d) {
+    const Div31 D = div31_make((uint32_t)d);
+    for (uint64_t n = 0; n <= n_hi; ++n)
+      bad += div31((uint32_t)(2 * n), D) != (uint32_t)(n / d);
+    for (int64_t s = 0; s < samples; ++s) {
+      x += 0x9E3779B97F4A7C15ull;
+      uint64_t z = x;
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z ^= z >> 31;
+      const uint32_t n = (uint32_t)(z & 0x7FFFFFFFu);
+      bad += div31(2u * n, D) != n / (uint32_t)d;
+    }
+  }
+  return bad;
+}
+
+}  // extern "C"

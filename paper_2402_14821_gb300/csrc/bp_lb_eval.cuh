@@ -1,0 +1,269 @@
+// bp_lb_eval.cuh -- per-DFF evaluation of one staged item list for T
+// parameters per thread (Alg. 4's "one parameter per thread", with T
+// parameters per thread so that every item read from shared memory feeds T
+// independent evaluations).
+//
+// Lists live in shared memory as uint32 values, padded with zeros to a
+// multiple of 4 so that each step reads four items with one 16-byte
+// broadcast load.  A zero pad contributes 0 to every list sum below.
+//
+// Partial sums are 32-bit within a group of K items, chosen so that the
+// group's true sum stays below 2^32, then added into 64-bit accumulators
+// (the WIDE variants accumulate in 64 bits directly; they serve capacities
+// above the fast-path limits).
+#pragma once
+
+#include "bp_lb_core.cuh"
+
+namespace bplb {
+
+// Largest multiple of 4 not above floor((2^32 - 1) / max_term), at least 4.
+BPLB_HD int group_len(int64_t max_term) {
+  if (max_term < 1) max_term = 1;
+  int64_t k = (int64_t)0xFFFFFFFFu / max_term;
+  if (k > (int64_t(1) << 30)) k = int64_t(1) << 30;
+  k &= ~int64_t(3);
+  return k < 4 ? 4 : (int)k;
+}
+
+BPLB_D uint4 lds4(const uint32_t *s, int i) { return *reinterpret_cast<const uint4 *>(s + i); }
+BPLB_D float4 lds4f(const float *s, int i) { return *reinterpret_cast<const float4 *>(s + i); }
+
+// ---- MT: sum_small u2*[u2 >= 2l] and sum_big u2*[u2 < 2l] -------------------
+template <int T>
+BPLB_D void mt_list(const uint32_t *s, int beg, int end, int K, const uint32_t (&thr)[T],
+                    bool big, uint64_t (&acc)[T]) {
+  for (int g0 = beg; g0 < end; g0 += K) {
+    const int g1 = min(end, g0 + K);
+    uint32_t a[T];
+#pragma unroll
+    for (int j = 0; j < T; ++j) a[j] = 0;
+    for (int i = g0; i < g1; i += 4) {
+      const uint4 v = lds4(s, i);
+#pragma unroll
+      for (int j = 0; j < T; ++j) {
+        if (!big) {
+          a[j] += (v.x >= thr[j] ? v.x : 0u) + (v.y >= thr[j] ? v.y : 0u);
+          a[j] += (v.z >= thr[j] ? v.z : 0u) + (v.w >= thr[j] ? v.w : 0u);
+        } else {
+          a[j] += (v.x < thr[j] ? v.x : 0u) + (v.y < thr[j] ? v.y : 0u);
+          a[j] += (v.z < thr[j] ? v.z : 0u) + (v.w < thr[j] ? v.w : 0u);
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < T; ++j) acc[j] += a[j];
+  }
+}
+
+// ---- RAD2: counts #[u2 >= 2l] (low half) and #[u2 > 2c - 4l] (high half) ----
+template <int T>
+BPLB_D void rad2_list(const uint32_t *s, int beg, int end, const uint32_t (&t1)[T],
+                      const uint32_t (&t2)[T], uint64_t (&acc)[T]) {
+  uint32_t n1[T], n2[T];
+#pragma unroll
+  for (int j = 0; j < T; ++j) n1[j] = n2[j] = 0;
+  for (int i = beg; i < end; i += 4) {
+    const uint4 v = lds4(s, i);
+#pragma unroll
+    for (int j = 0; j < T; ++j) {
+      n1[j] += (uint32_t)(v.x >= t1[j]) + (uint32_t)(v.y >= t1[j]) + (uint32_t)(v.z >= t1[j]) +
+               (uint32_t)(v.w >= t1[j]);
+      n2[j] += (uint32_t)(v.x > t2[j]) + (uint32_t)(v.y > t2[j]) + (uint32_t)(v.z > t2[j]) +
+               (uint32_t)(v.w > t2[j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < T; ++j) acc[j] += (uint64_t)n1[j] | ((uint64_t)n2[j] << 32);
+}
+
+// ---- FS1 (raw w): sum floor(w(l+1)/c) and sum w*[c | w(l+1)] -----------------
+template <int T>
+BPLB_D void fs1_list(const uint32_t *s, int beg, int end, int K, const uint32_t (&mul2)[T],
+                     Div31 Dc, uint32_t c2, uint64_t (&acc0)[T], uint64_t (&acc1)[T]) {
+  for (int g0 = beg; g0 < end; g0 += K) {
+    const int g1 = min(end, g0 + K);
+    uint32_t a0[T], a1[T];
+#pragma unroll
+    for (int j = 0; j < T; ++j) a0[j] = a1[j] = 0;
+    for (int i = g0; i < g1; i += 4) {
+      const uint4 v = lds4(s, i);
+      const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+#pragma unroll
+        for (int j = 0; j < T; ++j) {
+          const uint32_t x2 = w4[e] * mul2[j];  // 2 w (l + 1) < 2^32
+          const uint32_t q = div31(x2, Dc);     // floor(w (l + 1) / c)
+          a0[j] += q;
+          a1[j] += (q * c2 == x2) ? w4[e] : 0u;
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < T; ++j) {
+      acc0[j] += a0[j];
+      acc1[j] += a1[j];
+    }
+  }
+}
+
+template <int T>
+BPLB_D void fs1_list_wide(const uint32_t *s, int beg, int end, const int64_t (&lam)[T], int64_t c,
+                          uint64_t (&acc0)[T], uint64_t (&acc1)[T]) {
+  for (int i = beg; i < end; ++i) {
+    const int64_t w = s[i];
+#pragma unroll
+    for (int j = 0; j < T; ++j) {
+      const int64_t x = w * (lam[j] + 1);
+      acc0[j] += (uint64_t)(x / c);
+      acc1[j] += (x % c == 0) ? (uint64_t)w : 0u;
+    }
+  }
+}
+
+// ---- CCM1 (u2 = 2u): sum floor(u / l) ----------------------------------------
+template <int T>
+BPLB_D void ccm1_list(const uint32_t *s, int beg, int end, int K, const Div31 (&D)[T],
+                      uint64_t (&acc)[T]) {
+  for (int g0 = beg; g0 < end; g0 += K) {
+    const int g1 = min(end, g0 + K);
+    uint32_t a[T];
+#pragma unroll
+    for (int j = 0; j < T; ++j) a[j] = 0;
+    for (int i = g0; i < g1; i += 4) {
+      const uint4 v = lds4(s, i);
+#pragma unroll
+      for (int j = 0; j < T; ++j) {
+        a[j] += div31(v.x, D[j]) + div31(v.y, D[j]);
+        a[j] += div31(v.z, D[j]) + div31(v.w, D[j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < T; ++j) acc[j] += a[j];
+  }
+}
+
+// ---- VB2 (u2 = 2u): sum ceil(u l / c) -----------------------------------------
+// c <= 65535: ceil(u l / c) = floor((u l + c - 1) / c), numerator < 2^31, exact
+// multiply-high division by c.
+template <int T>
+BPLB_D void vb2_list_magic(const uint32_t *s, int beg, int end, int K, const uint32_t (&lam)[T],
+                           Div31 Dc, uint32_t add2, uint64_t (&acc)[T]) {
+  for (int g0 = beg; g0 < end; g0 += K) {
+    const int g1 = min(end, g0 + K);
+    uint32_t a[T];
+#pragma unroll
+    for (int j = 0; j < T; ++j) a[j] = 0;
+    for (int i = g0; i < g1; i += 4) {
+      const uint4 v = lds4(s, i);
+#pragma unroll
+      for (int j = 0; j < T; ++j) {
+        // 2 (u l + c - 1) = u2 * l + (2c - 2)
+        a[j] += div31(v.x * lam[j] + add2, Dc) + div31(v.y * lam[j] + add2, Dc);
+        a[j] += div31(v.z * lam[j] + add2, Dc) + div31(v.w * lam[j] + add2, Dc);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < T; ++j) acc[j] += a[j];
+  }
+}
+
+// 65535 < c <= 2^22: an fp32 estimate of the quotient, corrected exactly.
+//   a = fl(u / c) (correctly rounded, staged with the list), relative error
+//   <= 2^-24.  fmaf(l, a, 1.5 * 2^23) rounds l*a + 1.5*2^23 to an integer
+//   since the sum lies in [2^23, 2^24); its bit pattern is 0x4B400000 + q~
+//   with q~ = round(l * a), and |q~ - u l / c| <= 1/2 + (c/2) 2^-24 < 1.
+//   The residual 2 rho = u2 l - 2c q~ is then in (-2c, 2c), so it is exact in
+//   wrapping 32-bit arithmetic, and ceil(u l / c) = q~ + [rho > 0].
+//   The loop accumulates bits + [rho > 0] modulo 2^32 and removes
+//   0x4B400000 per list slot at the end of each group.
+constexpr uint32_t kF32RoundBits = 0x4B400000u;  // bit pattern of 1.5 * 2^23
+
+template <int T>
+BPLB_D void vb2_list_float(const uint32_t *s, const float *sa, int beg, int end, int K,
+                           const uint32_t (&lam)[T], const float (&lamf)[T], uint32_t c2,
+                           uint32_t K2, uint64_t (&acc)[T]) {
+  for (int g0 = beg; g0 < end; g0 += K) {
+    const int g1 = min(end, g0 + K);
+    uint32_t a[T];
+#pragma unroll
+    for (int j = 0; j < T; ++j) a[j] = 0;
+    for (int i = g0; i < g1; i += 4) {
+      const uint4 v = lds4(s, i);
+      const float4 f = lds4f(sa, i);
+      const uint32_t u4[4] = {v.x, v.y, v.z, v.w};
+      const float f4[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+#pragma unroll
+        for (int j = 0; j < T; ++j) {
+          const uint32_t bits = __float_as_uint(__fmaf_rn(lamf[j], f4[e], 12582912.0f));
+          const uint32_t neg2rho = bits * c2 + K2 - u4[e] * lam[j];  // = -2 rho (mod 2^32)
+          a[j] += bits + (neg2rho >> 31);
+        }
+      }
+    }
+    const uint32_t slots = (uint32_t)(g1 - g0);
+#pragma unroll
+    for (int j = 0; j < T; ++j) acc[j] += (uint32_t)(a[j] - slots * kF32RoundBits);
+  }
+}
+
+template <int T>
+BPLB_D void vb2_list_wide(const uint32_t *s, int beg, int end, const int64_t (&lam)[T], int64_t c,
+                          uint64_t (&acc)[T]) {
+  for (int i = beg; i < end; ++i) {
+    const int64_t u = s[i] >> 1;
+#pragma unroll
+    for (int j = 0; j < T; ++j) acc[j] += (uint64_t)((u * lam[j] + c - 1) / c);
+  }
+}
+
+// ---- BJ1 (w2 = 2w): sum floor(w / l) and sum min(2 (w mod l), 2 (c mod l)) ----
+template <int T>
+BPLB_D void bj1_list(const uint32_t *s, int beg, int end, int K, const Div31 (&D)[T],
+                     const uint32_t (&l2)[T], const uint32_t (&cm2)[T], uint64_t (&acc0)[T],
+                     uint64_t (&acc1)[T]) {
+  for (int g0 = beg; g0 < end; g0 += K) {
+    const int g1 = min(end, g0 + K);
+    uint32_t a0[T], a1[T];
+#pragma unroll
+    for (int j = 0; j < T; ++j) a0[j] = a1[j] = 0;
+    for (int i = g0; i < g1; i += 4) {
+      const uint4 v = lds4(s, i);
+      const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+#pragma unroll
+        for (int j = 0; j < T; ++j) {
+          const uint32_t q = div31(w4[e], D[j]);
+          const uint32_t r2 = w4[e] - q * l2[j];  // 2 (w mod l)
+          a0[j] += q;
+          a1[j] += min(r2, cm2[j]);
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < T; ++j) {
+      acc0[j] += a0[j];
+      acc1[j] += a1[j];
+    }
+  }
+}
+
+template <int T>
+BPLB_D void bj1_list_wide(const uint32_t *s, int beg, int end, const int64_t (&lam)[T], int64_t c,
+                          uint64_t (&acc0)[T], uint64_t (&acc1)[T]) {
+  for (int i = beg; i < end; ++i) {
+    const int64_t w = s[i] >> 1;
+#pragma unroll
+    for (int j = 0; j < T; ++j) {
+      const int64_t q = w / lam[j], rho = w % lam[j], cm = c % lam[j];
+      acc0[j] += (uint64_t)q;
+      acc1[j] += (uint64_t)(2 * (rho < cm ? rho : cm));
+    }
+  }
+}
+
+}  // namespace bplb

@@ -1,0 +1,701 @@
+// bp_lb_kernels.cuh -- the kernels of the DFF lower-bound check.
+//
+//   plan_kernel     per instance: validate, count (DFF, lambda-tile) tiles,
+//                   exclusive scan into a tile table; resets the work counter.
+//   eval_kernel     persistent CTAs pull tiles from an atomic counter; a tile
+//                   is (instance, DFF, NT*T consecutive lambdas).  The CTA
+//                   stages the instance's items into shared memory (building
+//                   the reduced instance on the fly for search nodes),
+//                   evaluates T lambdas per thread, reduces a packed
+//                   (bound, -index) key over the block and folds it into the
+//                   instance's slot with one 64-bit atomicMax; the last tile
+//                   of an instance writes its outputs and clears the slot.
+//   reduce_kernel   the reduction alone (one CTA per search node).
+//   debug_kernel    per-(DFF, lambda) bounds for spot checks.
+//
+// Paper: Alg. 2 (what is computed), Alg. 4 and Sec. 4 "Implementation
+// details" (parameters across threads, items in shared memory, block-level
+// max then one global atomic max) and Sec. 3 / Fig. 3 (the reduction).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../../include/bp_lb.h"
+#include "bp_lb_core.cuh"
+#include "bp_lb_eval.cuh"
+
+namespace bplb {
+
+constexpr int kChunk = 2048;          // stream positions staged per pass
+constexpr int kListTop = kChunk + 8;  // list buffer length (small up, big down)
+constexpr int kMaxNodeBins = 16384;   // on-chip bin-load table limit
+
+enum SrcMode : int { kSrcRaggedI32 = 0, kSrcRaggedI64 = 1, kSrcNodes = 2 };
+
+struct EvalArgs {
+  int32_t B;
+  // ragged reduced instances
+  const int64_t *offsets;
+  const void *sizes;
+  const int64_t *capacity;
+  const int64_t *bins;
+  // search nodes
+  int32_t num_base;
+  const int64_t *base_offsets;
+  const int32_t *base_sizes;
+  const int64_t *base_capacity;
+  const int32_t *node_base;
+  const int64_t *assign_offsets;
+  const int32_t *assign;
+  int32_t max_bins;
+  // outputs
+  int64_t *out_bound;
+  bp_argmax_t *out_argmax;
+  uint8_t *out_feasible;
+  // schedule / scratch
+  const int64_t *tile_start;  // [B+1]; nullptr: one instance with single_tiles tiles
+  int64_t single_tiles;
+  int64_t single_c;
+  int64_t single_k;
+  int64_t single_n;
+  unsigned long long *keys;   // [B] packed (bound, -index) maxima, zero between calls
+  unsigned int *done;         // [B] finished-tile counters, zero between calls
+  unsigned long long *work;   // [1] next tile (persistent mode), nullptr otherwise
+};
+
+// Instance view resolved per tile.
+struct InstView {
+  int64_t c, k;
+  int64_t n;        // base items (nodes) or items (ragged)
+  int64_t begin;    // ragged: offset of the first item
+  const int32_t *w; // nodes: base sizes
+  const int32_t *a; // nodes: assignment
+};
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+// Warp-aggregated append to a shared-memory list counter; returns the slot.
+__device__ __forceinline__ int warp_append(bool pred, int *counter) {
+  const unsigned mask = __ballot_sync(0xFFFFFFFFu, pred);
+  if (mask == 0) return -1;
+  const int leader = __ffs(mask) - 1;
+  int base = 0;
+  if ((int)lane_id() == leader) base = atomicAdd(counter, __popc(mask));
+  base = __shfl_sync(0xFFFFFFFFu, base, leader);
+  return base + __popc(mask & ((1u << lane_id()) - 1u));
+}
+
+template <class V>
+__device__ __forceinline__ V warp_sum(V v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long x = __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    v = x > v ? x : v;
+  }
+  return v;
+}
+
+__device__ __forceinline__ void write_error(const EvalArgs &A, int64_t b) {
+  A.out_bound[b] = -BP_ERANGE;
+  if (A.out_argmax) {
+    bp_argmax_t e;
+    e.dff = -1;
+    e.pad = 0;
+    e.lambda = -1;
+    A.out_argmax[b] = e;
+  }
+  if (A.out_feasible) A.out_feasible[b] = 0;
+}
+
+__device__ __forceinline__ void write_result(const EvalArgs &A, int64_t b, unsigned long long key,
+                                             int64_t c, int64_t k) {
+  const int64_t lb = (int64_t)(key >> 32);
+  const uint32_t g = 0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull);
+  A.out_bound[b] = lb;
+  if (A.out_argmax) {
+    bp_argmax_t r;
+    unflatten(g, c, r.dff, r.lambda);
+    r.pad = 0;
+    A.out_argmax[b] = r;
+  }
+  if (A.out_feasible) A.out_feasible[b] = (uint8_t)(lb <= k);
+}
+
+// ---------------------------------------------------------------------------
+// plan_kernel: one block.  Validates every instance, writes tile_start[0..B]
+// (exclusive scan of tiles per instance; 0 tiles and an error result for an
+// invalid one), clears keys/done and resets the work counter.
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(1024) plan_kernel(EvalArgs A, int64_t lpt, int64_t *tile_start) {
+  __shared__ int64_t s_warp[32];
+  __shared__ int64_t s_carry;
+  if (threadIdx.x == 0) {
+    s_carry = 0;
+    *A.work = 0ull;
+  }
+  __syncthreads();
+  for (int64_t b0 = 0; b0 < A.B; b0 += blockDim.x) {
+    const int64_t b = b0 + threadIdx.x;
+    int64_t tiles = 0;
+    if (b < A.B) {
+      A.keys[b] = 0ull;
+      A.done[b] = 0u;
+      bool ok;
+      int64_t c;
+      if (MODE == kSrcNodes) {
+        const int32_t base = A.node_base[b];
+        ok = base >= 0 && base < A.num_base;
+        c = ok ? A.base_capacity[base] : 0;
+        const int64_t n = ok ? A.base_offsets[base + 1] - A.base_offsets[base] : 0;
+        const int64_t na = A.assign_offsets[b + 1] - A.assign_offsets[b];
+        const int64_t k = A.bins[b];
+        ok = ok && c >= 1 && c <= kMaxCapacity && n >= 0 && n <= kMaxItems && na == n && k >= 0 &&
+             k <= A.max_bins;
+      } else {
+        c = A.capacity[b];
+        const int64_t r = A.offsets[b + 1] - A.offsets[b];
+        ok = c >= 1 && c <= kMaxCapacity && r >= 0 && r <= kMaxItems && A.bins[b] >= 0;
+      }
+      if (ok) tiles = tiles_for(c, lpt);
+      else write_error(A, b);
+    }
+    // block-wide inclusive scan of `tiles`
+    int64_t v = tiles;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t x = __shfl_up_sync(0xFFFFFFFFu, v, o);
+      if ((int)lane_id() >= o) v += x;
+    }
+    if (lane_id() == 31) s_warp[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const int nw = blockDim.x >> 5;
+      int64_t wv = (int)threadIdx.x < nw ? s_warp[threadIdx.x] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t x = __shfl_up_sync(0xFFFFFFFFu, wv, o);
+        if ((int)threadIdx.x >= o) wv += x;
+      }
+      s_warp[threadIdx.x] = wv;  // inclusive warp prefix
+    }
+    __syncthreads();
+    const int64_t warp_excl = (threadIdx.x >> 5) ? s_warp[(threadIdx.x >> 5) - 1] : 0;
+    const int64_t incl = s_carry + warp_excl + v;
+    if (b < A.B) tile_start[b] = incl - tiles;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) s_carry = incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) tile_start[A.B] = s_carry;
+}
+
+// ---------------------------------------------------------------------------
+// Tile processing.
+// ---------------------------------------------------------------------------
+struct TileShared {
+  int ns, nb, err;
+  int pad_;
+  unsigned long long warp_key[32];
+  long long sums[6];
+};
+
+// Fetches stream position q: returns true and the size when q is an item of
+// the (reduced) instance, false for a filtered position (a packed item).
+template <int MODE>
+__device__ __forceinline__ bool fetch_item(const EvalArgs &A, const InstView &I, const uint32_t *s_load,
+                                           int64_t q, int64_t &w) {
+  if (MODE == kSrcRaggedI32) {
+    w = reinterpret_cast<const int32_t *>(A.sizes)[I.begin + q];
+    return true;
+  } else if (MODE == kSrcRaggedI64) {
+    w = reinterpret_cast<const int64_t *>(A.sizes)[I.begin + q];
+    return true;
+  } else {
+    if (q < I.n) {
+      w = I.w[q];
+      return I.a[q] == -1;
+    }
+    w = s_load[q - I.n];
+    return true;
+  }
+}
+
+template <int NT, int T, int MODE>
+__device__ void process_tile(const EvalArgs &A, int64_t b, int64_t lt, int64_t ntiles,
+                             const InstView &I, uint32_t *s_items, float *s_a, uint32_t *s_load,
+                             TileShared &S, const int32_t *req_dff = nullptr,
+                             const int64_t *req_lam = nullptr, int64_t req_m = 0,
+                             int64_t *req_out = nullptr, int req_d = -1) {
+  constexpr int LPT = NT * T;
+  const int tid = threadIdx.x;
+  const int64_t c = I.c;
+
+  // ---- which DFF and which lambdas -------------------------------------
+  int d = 0;
+  int64_t lam0 = 0, lam_end = 0;
+  int64_t lam[T];
+  bool valid[T];
+  int64_t lo_d, hi_d;
+  if (req_d < 0) {
+    int64_t rem = lt;
+    for (d = 0; d < kNumDff; ++d) {
+      const int64_t nt = (param_count(d, c) + LPT - 1) / LPT;
+      if (rem < nt) break;
+      rem -= nt;
+    }
+    param_range(d, c, lo_d, hi_d);
+    lam0 = lo_d + rem * LPT;
+    lam_end = min(hi_d + 1, lam0 + LPT);
+#pragma unroll
+    for (int j = 0; j < T; ++j) {
+      const int64_t l = lam0 + (int64_t)j * NT + tid;
+      valid[j] = l < lam_end;
+      lam[j] = valid[j] ? l : lo_d;
+    }
+  } else {
+    d = req_d;
+    param_range(d, c, lo_d, hi_d);
+    const int64_t r = (int64_t)blockIdx.x * NT + tid;
+    if (d == 0 && r < req_m && (req_dff[r] < 0 || req_dff[r] >= kNumDff)) req_out[r] = -BP_ERANGE;
+    const bool mine = r < req_m && req_dff[r] == d;
+    const int64_t l = mine ? req_lam[r] : lo_d;
+    valid[0] = mine && l >= lo_d && l <= hi_d;
+    lam[0] = valid[0] ? l : lo_d;
+    if (mine && !valid[0]) req_out[r] = -BP_ERANGE;
+#pragma unroll
+    for (int j = 1; j < T; ++j) {
+      valid[j] = false;
+      lam[j] = lo_d;
+    }
+  }
+
+  // ---- per-lambda constants ------------------------------------------------
+  const bool ulist = (d == kMT || d == kRAD2 || d == kCCM1 || d == kVB2);
+  const bool narrow = c <= kNarrowCap;  // BJ1: terms < 2c stay below 2^30
+  const bool vb2_magic = c <= kVb2MagicCap;
+  const bool vb2_float = !vb2_magic && c <= kVb2FloatCap;
+  const bool fs1_fast = c <= kFs1FastCap;
+  const bool stage_a = (d == kVB2) && vb2_float;
+
+  uint32_t p0[T], p1[T], p2[T];
+  float pf[T];
+  Div31 Dl[T];
+#pragma unroll
+  for (int j = 0; j < T; ++j) {
+    p0[j] = p1[j] = p2[j] = 0;
+    pf[j] = 0.f;
+    Dl[j].m = 0;
+    Dl[j].l = 0;
+    const uint32_t l32 = (uint32_t)lam[j];
+    switch (d) {
+      case kMT: p0[j] = 2u * l32; break;
+      case kRAD2:
+        p0[j] = 2u * l32;
+        p1[j] = (uint32_t)(2 * c - 4 * lam[j]);
+        break;
+      case kFS1: p0[j] = 2u * l32 + 2u; break;
+      case kCCM1: Dl[j] = div31_make(l32); break;
+      case kVB2:
+        p0[j] = l32;
+        pf[j] = (float)l32;
+        break;
+      default: {  // BJ1
+        Dl[j] = div31_make(l32);
+        p0[j] = 2u * l32;
+        const uint32_t q = div31((uint32_t)(2 * c), Dl[j]);
+        p1[j] = 2u * ((uint32_t)c - q * l32);  // 2 (c mod l)
+      }
+    }
+  }
+  const Div31 Dc = div31_make((uint32_t)c);
+  const uint32_t c2 = (uint32_t)(2 * c);
+  const uint32_t vb2_add2 = (uint32_t)(2 * c - 2);
+  const uint32_t vb2_K2 = 0u - c2 * kF32RoundBits;
+
+  uint64_t acc0[T], acc1[T];
+#pragma unroll
+  for (int j = 0; j < T; ++j) acc0[j] = acc1[j] = 0;
+  int64_t ls_small = 0, ls_big = 0, ls_half = 0, ls_full = 0, ls_sbig = 0, ls_sum = 0;
+
+  if (tid == 0) S.err = 0;
+
+  // ---- node mode: bin loads of the partial packing -----------------------
+  if (MODE == kSrcNodes) {
+    for (int64_t j = tid; j < I.k; j += NT) s_load[j] = 0u;
+    __syncthreads();
+    for (int64_t i = tid; i < I.n; i += NT) {
+      const int32_t a = I.a[i];
+      const int32_t w = I.w[i];
+      if (w < 0 || (int64_t)w > c || a < -1 || (int64_t)a >= I.k) {
+        S.err = 1;
+      } else if (a >= 0) {
+        const uint32_t old = atomicAdd(&s_load[a], (uint32_t)w);
+        if ((int64_t)old + w > c) S.err = 1;
+      }
+    }
+  }
+  __syncthreads();
+
+  const int64_t L = (MODE == kSrcNodes) ? I.n + I.k : I.n;
+  for (int64_t p = 0; p < L; p += kChunk) {
+    if (tid == 0) {
+      S.ns = 0;
+      S.nb = 0;
+    }
+    __syncthreads();
+    // ---- stage one chunk ---------------------------------------------------
+    for (int o = 0; o < kChunk; o += NT) {
+      const int64_t q = p + o + tid;
+      int64_t w = 0;
+      bool have = false;
+      if (q < L) have = fetch_item<MODE>(A, I, s_load, q, w);
+      if (have && (w < 0 || w > c)) {
+        S.err = 1;
+        have = false;
+      }
+      if (have && w == 0) have = false;
+      if (ulist) {
+        const bool full = have && w == c;
+        const bool small = have && !full && 2 * w < c;
+        const bool big = have && !full && 2 * w > c;
+        const bool half = have && 2 * w == c;
+        ls_full += full;
+        ls_half += half;
+        ls_small += small;
+        ls_big += big;
+        if (big) ls_sbig += w;
+        ls_sum += have ? w : 0;
+        const int ps = warp_append(small, &S.ns);
+        const int pb = warp_append(big, &S.nb);
+        if (small) {
+          s_items[ps] = (uint32_t)(2 * w);
+          if (stage_a) s_a[ps] = __fdiv_rn((float)w, (float)c);
+        }
+        if (big) {
+          const int slot = kListTop - 1 - pb;
+          s_items[slot] = (uint32_t)(2 * (c - w));
+          if (stage_a) s_a[slot] = __fdiv_rn((float)(c - w), (float)c);
+        }
+      } else {
+        ls_sum += have ? w : 0;
+        const int ps = warp_append(have, &S.ns);
+        if (have) s_items[ps] = (d == kBJ1) ? (uint32_t)(2 * w) : (uint32_t)w;
+      }
+    }
+    __syncthreads();
+    const int ns = S.ns, nb = S.nb;
+    const int ns_pad = (ns + 3) & ~3;
+    const int bstart = (kListTop - nb) & ~3;
+    if (tid < 4) {
+      if (ns + tid < ns_pad) {
+        s_items[ns + tid] = 0u;
+        if (stage_a) s_a[ns + tid] = 0.f;
+      }
+      if (ulist && bstart + tid < kListTop - nb) {
+        s_items[bstart + tid] = 0u;
+        if (stage_a) s_a[bstart + tid] = 0.f;
+      }
+    }
+    __syncthreads();
+    if (!S.err) {
+      // ---- evaluate the staged lists --------------------------------------
+      switch (d) {
+        case kMT: {
+          // terms u2 < c <= 2^30, so groups of >= 4 never overflow 32 bits
+          const int K = group_len(c - 1);
+          mt_list<T>(s_items, 0, ns_pad, K, p0, false, acc0);
+          mt_list<T>(s_items, bstart, kListTop, K, p0, true, acc1);
+          break;
+        }
+        case kRAD2:
+          rad2_list<T>(s_items, 0, ns_pad, p0, p1, acc0);
+          rad2_list<T>(s_items, bstart, kListTop, p0, p1, acc1);
+          break;
+        case kFS1:
+          if (fs1_fast) {
+            fs1_list<T>(s_items, 0, ns_pad, group_len(c), p0, Dc, c2, acc0, acc1);
+          } else {
+            fs1_list_wide<T>(s_items, 0, ns_pad, lam, c, acc0, acc1);
+          }
+          break;
+        case kCCM1: {
+          // terms floor(u / l) <= c / 2 <= 2^29: groups of >= 8 items
+          const int K = group_len(c / 2);
+          ccm1_list<T>(s_items, 0, ns_pad, K, Dl, acc0);
+          ccm1_list<T>(s_items, bstart, kListTop, K, Dl, acc1);
+          break;
+        }
+        case kVB2:
+          if (vb2_magic) {
+            const int K = group_len(c / 2 + 1);
+            vb2_list_magic<T>(s_items, 0, ns_pad, K, p0, Dc, vb2_add2, acc0);
+            vb2_list_magic<T>(s_items, bstart, kListTop, K, p0, Dc, vb2_add2, acc1);
+          } else if (vb2_float) {
+            const int K = group_len(c / 2 + 1);
+            vb2_list_float<T>(s_items, s_a, 0, ns_pad, K, p0, pf, c2, vb2_K2, acc0);
+            vb2_list_float<T>(s_items, s_a, bstart, kListTop, K, p0, pf, c2, vb2_K2, acc1);
+          } else {
+            vb2_list_wide<T>(s_items, 0, ns_pad, lam, c, acc0);
+            vb2_list_wide<T>(s_items, bstart, kListTop, lam, c, acc1);
+          }
+          break;
+        default:  // BJ1
+          if (narrow) {
+            bj1_list<T>(s_items, 0, ns_pad, group_len(2 * c), Dl, p0, p1, acc0, acc1);
+          } else {
+            bj1_list_wide<T>(s_items, 0, ns_pad, lam, c, acc0, acc1);
+          }
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- instance constants: block sums -------------------------------------
+  if (tid < 6) S.sums[tid] = 0;
+  __syncthreads();
+  {
+    long long v[6] = {ls_small, ls_big, ls_half, ls_full, ls_sbig, ls_sum};
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+      const long long x = warp_sum(v[e]);
+      if (lane_id() == 0 && x != 0) atomicAdd((unsigned long long *)&S.sums[e], (unsigned long long)x);
+    }
+  }
+  __syncthreads();
+  InstSums sums;
+  sums.n_small = S.sums[0];
+  sums.n_big = S.sums[1];
+  sums.n_half = S.sums[2];
+  sums.n_full = S.sums[3];
+  sums.sumw_big = S.sums[4];
+  sums.sumw = S.sums[5];
+  const bool err = S.err != 0;
+
+  // ---- bounds, keys, block max ---------------------------------------------
+  unsigned long long best = 0ull;
+  if (!err) {
+    const uint32_t g0 = flat_index(d, lo_d, c);
+#pragma unroll
+    for (int j = 0; j < T; ++j) {
+      if (!valid[j]) continue;
+      const int64_t l = lam[j];
+      int64_t Ssum;
+      switch (d) {
+        case kMT: Ssum = mt_sum(sums, c, acc0[j], acc1[j]); break;
+        case kRAD2:
+          Ssum = rad2_sum(sums, c, (int64_t)(acc0[j] & 0xFFFFFFFFull), (int64_t)(acc0[j] >> 32),
+                          (int64_t)(acc1[j] & 0xFFFFFFFFull), (int64_t)(acc1[j] >> 32));
+          break;
+        case kFS1: Ssum = fs1_sum(c, acc0[j], acc1[j]); break;
+        case kCCM1: Ssum = ccm1_sum(sums, c / l, acc0[j], acc1[j]); break;
+        case kVB2: Ssum = vb2_sum(sums, l, acc0[j], acc1[j]); break;
+        default: Ssum = bj1_sum(sums, c % l, acc0[j], acc1[j]);
+      }
+      const int64_t den = dff_at_c(d, l, c);
+      const int64_t lb = ceil_div_i64(Ssum, den);
+      if (req_d >= 0) {
+        req_out[(int64_t)blockIdx.x * NT + tid] = lb;
+      } else {
+        const unsigned long long key = make_key(lb, g0 + (uint32_t)(l - lo_d));
+        best = key > best ? key : best;
+      }
+    }
+  }
+  if (req_d >= 0) return;
+  best = warp_max_u64(best);
+  if (lane_id() == 0) S.warp_key[tid >> 5] = best;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long m = 0ull;
+    for (int w = 0; w < NT / 32; ++w) m = S.warp_key[w] > m ? S.warp_key[w] : m;
+    if (m) atomicMax(&A.keys[b], m);
+    __threadfence();
+    const unsigned int ticket = atomicAdd(&A.done[b], 1u);
+    if ((int64_t)ticket == ntiles - 1) {
+      __threadfence();
+      const unsigned long long key = atomicExch(&A.keys[b], 0ull);
+      A.done[b] = 0u;
+      if (err) write_error(A, b);
+      else write_result(A, b, key, c, I.k);
+    }
+  }
+  __syncthreads();
+}
+
+template <int MODE>
+__device__ __forceinline__ InstView resolve_instance(const EvalArgs &A, int64_t b) {
+  InstView I;
+  I.w = nullptr;
+  I.a = nullptr;
+  I.begin = 0;
+  if (A.tile_start == nullptr) {
+    I.c = A.single_c;
+    I.k = A.single_k;
+    I.n = A.single_n;
+    if (MODE == kSrcNodes) {
+      I.w = A.base_sizes;
+      I.a = A.assign;
+    }
+    return I;
+  }
+  if (MODE == kSrcNodes) {
+    const int32_t base = A.node_base[b];
+    I.c = A.base_capacity[base];
+    I.k = A.bins[b];
+    const int64_t bo = A.base_offsets[base];
+    I.n = A.base_offsets[base + 1] - bo;
+    I.w = A.base_sizes + bo;
+    I.a = A.assign + A.assign_offsets[b];
+  } else {
+    I.c = A.capacity[b];
+    I.k = A.bins[b];
+    I.begin = A.offsets[b];
+    I.n = A.offsets[b + 1] - I.begin;
+  }
+  return I;
+}
+
+template <int NT, int T, int MODE>
+__global__ void __launch_bounds__(NT) eval_kernel(EvalArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ TileShared S;
+  __shared__ long long s_tile;
+  __shared__ long long s_inst;
+  uint32_t *s_items = reinterpret_cast<uint32_t *>(smem_raw);
+  float *s_a = reinterpret_cast<float *>(smem_raw + sizeof(uint32_t) * kListTop);
+  uint32_t *s_load = reinterpret_cast<uint32_t *>(smem_raw + 2 * sizeof(uint32_t) * kListTop);
+
+  const int64_t total = A.tile_start ? A.tile_start[A.B] : A.single_tiles;
+  int64_t t = blockIdx.x;
+  if (A.work) {
+    if (threadIdx.x == 0) s_tile = (long long)atomicAdd(A.work, 1ull);
+    __syncthreads();
+    t = s_tile;
+  }
+  while (t < total) {
+    if (threadIdx.x == 0) {
+      int64_t b = 0;
+      if (A.tile_start) {
+        int64_t lo = 0, hi = A.B - 1;  // largest b with tile_start[b] <= t
+        while (lo < hi) {
+          const int64_t mid = (lo + hi + 1) >> 1;
+          if (A.tile_start[mid] <= t) lo = mid;
+          else hi = mid - 1;
+        }
+        b = lo;
+      }
+      s_inst = b;
+    }
+    __syncthreads();
+    const int64_t b = s_inst;
+    const int64_t t0 = A.tile_start ? A.tile_start[b] : 0;
+    const int64_t nt = A.tile_start ? A.tile_start[b + 1] - t0 : A.single_tiles;
+    const InstView I = resolve_instance<MODE>(A, b);
+    process_tile<NT, T, MODE>(A, b, t - t0, nt, I, s_items, s_a, s_load, S);
+    if (!A.work) break;
+    if (threadIdx.x == 0) s_tile = (long long)atomicAdd(A.work, 1ull);
+    __syncthreads();
+    t = s_tile;
+  }
+}
+
+// Per-(DFF, lambda) bounds of one instance: grid (ceil(m / NT), 6).
+template <int NT>
+__global__ void __launch_bounds__(NT)
+    debug_kernel(EvalArgs A, const int32_t *req_dff, const int64_t *req_lam, int64_t m,
+                 int64_t *req_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ TileShared S;
+  uint32_t *s_items = reinterpret_cast<uint32_t *>(smem_raw);
+  float *s_a = reinterpret_cast<float *>(smem_raw + sizeof(uint32_t) * kListTop);
+  const InstView I = resolve_instance<kSrcRaggedI32>(A, 0);
+  process_tile<NT, 1, kSrcRaggedI32>(A, 0, 0, 1, I, s_items, s_a, nullptr, S, req_dff, req_lam, m,
+                                     req_out, (int)blockIdx.y);
+}
+
+// ---------------------------------------------------------------------------
+// reduce_kernel: one CTA per node; order-preserving compaction.
+// ---------------------------------------------------------------------------
+template <int NT>
+__global__ void __launch_bounds__(NT)
+    reduce_kernel(EvalArgs A, const int64_t *out_offsets, int32_t *out_sizes, int64_t *out_count) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint32_t *s_load = reinterpret_cast<uint32_t *>(smem_raw);
+  __shared__ int s_err;
+  __shared__ int s_warp[NT / 32];
+  __shared__ long long s_base;
+  for (int64_t b = blockIdx.x; b < A.B; b += gridDim.x) {
+    const int tid = threadIdx.x;
+    const int32_t base = A.node_base[b];
+    bool ok = base >= 0 && base < A.num_base;
+    const int64_t c = ok ? A.base_capacity[base] : 0;
+    const int64_t bo = ok ? A.base_offsets[base] : 0;
+    const int64_t n = ok ? A.base_offsets[base + 1] - bo : 0;
+    const int64_t k = A.bins[b];
+    ok = ok && c >= 1 && c <= kMaxCapacity && n >= 0 && n <= kMaxItems &&
+         A.assign_offsets[b + 1] - A.assign_offsets[b] == n && k >= 0 && k <= A.max_bins;
+    if (!ok) {
+      if (tid == 0) out_count[b] = -BP_ERANGE;
+      continue;
+    }
+    const int32_t *w = A.base_sizes + bo;
+    const int32_t *a = A.assign + A.assign_offsets[b];
+    if (tid == 0) {
+      s_err = 0;
+      s_base = 0;
+    }
+    for (int64_t j = tid; j < k; j += NT) s_load[j] = 0u;
+    __syncthreads();
+    for (int64_t i = tid; i < n; i += NT) {
+      const int32_t ai = a[i], wi = w[i];
+      if (wi < 0 || (int64_t)wi > c || ai < -1 || (int64_t)ai >= k) s_err = 1;
+      else if (ai >= 0) {
+        const uint32_t old = atomicAdd(&s_load[ai], (uint32_t)wi);
+        if ((int64_t)old + wi > c) s_err = 1;
+      }
+    }
+    __syncthreads();
+    if (s_err) {
+      if (tid == 0) out_count[b] = -BP_ERANGE;
+      __syncthreads();
+      continue;
+    }
+    int32_t *dst = out_sizes + out_offsets[b];
+    // unpacked items, index order; then non-empty bins, bin order
+    for (int64_t p = 0; p < n + k; p += NT) {
+      const int64_t q = p + tid;
+      bool keep = false;
+      int32_t v = 0;
+      if (q < n) {
+        keep = a[q] == -1;
+        v = w[q];
+      } else if (q < n + k) {
+        v = (int32_t)s_load[q - n];
+        keep = v > 0;
+      }
+      const unsigned mask = __ballot_sync(0xFFFFFFFFu, keep);
+      if (lane_id() == 0) s_warp[tid >> 5] = __popc(mask);
+      __syncthreads();
+      int before = 0, total = 0;
+      for (int e = 0; e < NT / 32; ++e) {
+        before += (e < (tid >> 5)) ? s_warp[e] : 0;
+        total += s_warp[e];
+      }
+      if (keep) dst[s_base + before + __popc(mask & ((1u << lane_id()) - 1u))] = v;
+      __syncthreads();
+      if (tid == 0) s_base += total;
+      __syncthreads();
+    }
+    if (tid == 0) out_count[b] = s_base;
+    __syncthreads();
+  }
+}
+
+}  // namespace bplb

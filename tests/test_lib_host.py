@@ -1,0 +1,70 @@
+"""CPU-only checks of the CUDA library: it builds, loads, exports every entry
+point include/bp_lb.h declares, and its host-side helpers (parameter ranges,
+exact division by invariant integers) are right.  No kernel runs here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2402_14821_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return binding.lib()
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "bp_lb.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(bp_lb_\w+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_symbols()
+    assert len(names) >= 12
+    cdll = ctypes.CDLL(binding.LIB_PATH)
+    for n in names:
+        assert hasattr(cdll, n), n
+    assert set(names) == set(binding.EXPORTED)
+
+
+def test_strerror(lib):
+    assert binding.strerror(0) == "ok"
+    assert "range" in binding.strerror(2)
+
+
+def test_param_count_matches_oracle(lib, orc):
+    for c in list(range(1, 64)) + [150, 1000, 65535, 65536, 10 ** 6, 2 ** 30]:
+        for d in range(6):
+            n, lo, hi = binding.bp_lb_param_count(d, c)
+            olo, ohi, on = orc.param_range(d, c)
+            assert n == on, (d, c)
+            if n:
+                assert (lo, hi) == (olo, ohi)
+    assert binding.bp_lb_param_count(6, 10)[0] == -1
+    assert binding.bp_lb_param_count(0, 0)[0] == -1
+    assert binding.bp_lb_param_count(0, 2 ** 30 + 1)[0] == -1
+
+
+def test_exact_division_small_exhaustive(lib):
+    # every divisor up to 2^11 on every numerator up to 2^12
+    assert binding.bp_lb_selfcheck_division(1, 2048, 4096, 64) == 0
+
+
+def test_exact_division_wide(lib):
+    # divisors near powers of two and at the top of the range, random numerators < 2^31
+    for lo in (2 ** 15 - 8, 2 ** 16 - 8, 2 ** 20 - 8, 2 ** 24 - 8, 2 ** 30 - 8, 2 ** 31 - 64):
+        assert binding.bp_lb_selfcheck_division(lo, lo + 63, 64, 4000) == 0
+    assert binding.bp_lb_selfcheck_division(0, 5, 5, 0) == -1
+
+
+def test_create_rejects_bad_arguments(lib):
+    for cap, items in ((0, 10), (2 ** 30 + 1, 10), (10, 0), (10, 2 ** 20 + 1)):
+        with pytest.raises(binding.BpLbError) as e:
+            binding.bp_lb_create(cap, items)
+        assert e.value.status == binding.BP_ERANGE
