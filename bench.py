@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "feasibility checks/s and item-param evals/s, batched vs plain; p50/p99 ms"
 UNIT = "checks/s"
-WORKLOAD = "search-node batch: 4096 partial packings of n=500 items, sizes U[1,c/2], c=10000"
+WORKLOAD = "search-node batch: {} partial packings of n=500 items, sizes U[1,c/2], c=10000"
 NODES, N_ITEMS, CAP = 4096, 500, 10_000
 
 # Integer operations per (item, parameter) pair in the kernel's formulation of
@@ -169,16 +169,20 @@ def oracle_rate(nd, budget_s: float, threads: int):
 
 # ---------------------------------------------------------------------------
 def main():
+    global NODES
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=150)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--nodes", type=int, default=NODES,
+                    help="search nodes per batch (4096 is the benchmark workload)")
     ap.add_argument("--plain-sample", type=int, default=1024)
     ap.add_argument("--cpu-budget", type=float, default=15.0,
                     help="CPU-seconds of oracle work for the cpu_baseline sample")
     args = ap.parse_args()
 
+    NODES = args.nodes
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -204,7 +208,7 @@ def main():
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": float(np.mean(walls)) * 1e3 * NODES, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "nodes": NODES, "n": N_ITEMS, "c": CAP},
+                "config": {"workload": WORKLOAD.format(NODES), "nodes": NODES, "n": N_ITEMS, "c": CAP},
                 "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                                  "sample": f"{sample} of the {NODES} nodes per step, reduction + "
                                            f"full bound, {threads} host threads"},
@@ -243,6 +247,10 @@ def main():
     out_f = torch.empty(NODES, dtype=torch.uint8, device=dev)
     h = B.bp_lb_create(CAP, 1 << 16)
     B.bp_lb_reserve(h, NODES)
+    # autotuner: pick the launch shape on this batch (not timed)
+    shape, shape_ms = B.bp_lb_autotune_nodes(h, max_bins=max_bins, out_bound=out_b,
+                                             out_argmax=out_a, out_feasible=out_f, reps=2,
+                                             stream=stream, **t_in)
 
     def step():
         B.bp_lb_eval_nodes(h, max_bins=max_bins, out_bound=out_b, out_argmax=out_a,
@@ -341,7 +349,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nodes": NODES, "n": N_ITEMS, "c": CAP,
+        "config": {"workload": WORKLOAD.format(NODES), "nodes": NODES, "n": N_ITEMS, "c": CAP,
                    "evals_per_step": evals, "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"independent batches per rank x{world}"},
         "evals_per_s": evals * world / (t_step / 1e3),
@@ -357,6 +365,8 @@ def main():
                      "peak_basis": f"{sms} SMs x 4 SMSP x 32 lanes x {sm_mhz_max:.0f} MHz "
                                    "(integer issue, one warp instruction per clock per SMSP)",
                      "kernel": "eval_kernel (plan_kernel included in the timed step)"},
+        "launch_shape": {"chosen": shape, "nt_t_g_minb": list(B.bp_lb_launch_shape_info(shape)),
+                         "autotune_ms": [round(x, 4) for x in shape_ms]},
         "gpu_launches": 2 * args.steps,
         "clocks": clocks,
         "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": threads, "kind": "oracle",

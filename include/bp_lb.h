@@ -203,6 +203,61 @@ int bp_lb_reduce_nodes(bp_lb_t *h, int32_t B, int32_t num_base,
                        int32_t *d_out_sizes, int64_t *d_out_count,
                        void *stream);
 
+/* ---- launch shapes and autotuning ---------------------------------------- */
+
+/* Input modes of the evaluation kernel, for the launch-shape calls below. */
+#define BP_MODE_RAGGED_I32 0   /* bp_lb_eval, bp_lb_eval_batch     */
+#define BP_MODE_RAGGED_I64 1   /* bp_lb_eval_batch_i64             */
+#define BP_MODE_NODES      2   /* bp_lb_eval_node, bp_lb_eval_nodes */
+
+/* The evaluation kernel is compiled for a small table of launch shapes:
+ * nt threads per CTA, t parameters per thread and pass, g passes per tile
+ * (so a tile covers nt*t*g consecutive parameters of one DFF), and a floor of
+ * min_blocks resident CTAs per SM (which caps registers per thread).  This is
+ * the implementation's own tuning space; the paper uses one parameter per
+ * thread and blocks of one SM's core count (Sec. 4, "Parallelization"). */
+int bp_lb_num_launch_shapes(void);
+
+/* Describes shape `id` (0 <= id < bp_lb_num_launch_shapes()); any output
+ * pointer may be NULL.  Errors: BP_ERANGE. */
+int bp_lb_launch_shape_info(int32_t id, int32_t *nt, int32_t *t, int32_t *g,
+                            int32_t *min_blocks);
+
+/* Selects the shape the handle uses for one input mode (default 0).
+ * Errors: BP_EINVAL (bad handle or mode), BP_ERANGE (bad id). */
+int bp_lb_set_launch_shape(bp_lb_t *h, int32_t mode, int32_t id);
+
+/* The shape the handle uses for `mode`, or -1 for a bad handle or mode. */
+int bp_lb_get_launch_shape(bp_lb_t *h, int32_t mode);
+
+/* Autotuner: runs the given batch once per launch shape to warm up, then
+ * `reps` times, timed with CUDA events on `stream`; keeps the fastest shape
+ * for the mode and writes it to *best_shape (may be NULL), and the mean
+ * milliseconds per call of every shape to ms_per_shape[0 .. num shapes) (may
+ * be NULL).  The output buffers receive the batch's results.  Synchronises
+ * the stream (not capturable).  Arguments as for bp_lb_eval_batch(_i64)
+ * (sizes_are_i64 selects the size type) and bp_lb_eval_nodes.
+ * Errors: as those calls, and BP_EINVAL for B < 1 or reps < 1. */
+int bp_lb_autotune_batch(bp_lb_t *h, int32_t B, const int64_t *d_offsets,
+                         const void *d_sizes, int32_t sizes_are_i64,
+                         const int64_t *d_capacity, const int64_t *d_bins,
+                         int64_t *d_out_bound, bp_argmax_t *d_out_argmax,
+                         uint8_t *d_out_feasible, int32_t reps,
+                         float *ms_per_shape, int32_t *best_shape,
+                         void *stream);
+
+int bp_lb_autotune_nodes(bp_lb_t *h, int32_t B, int32_t num_base,
+                         const int64_t *d_base_offsets,
+                         const int32_t *d_base_sizes,
+                         const int64_t *d_base_capacity,
+                         const int32_t *d_node_base,
+                         const int64_t *d_assign_offsets,
+                         const int32_t *d_assign, const int64_t *d_bins,
+                         int64_t max_bins, int64_t *d_out_bound,
+                         bp_argmax_t *d_out_argmax, uint8_t *d_out_feasible,
+                         int32_t reps, float *ms_per_shape,
+                         int32_t *best_shape, void *stream);
+
 /* ---- inspection -------------------------------------------------------- */
 
 /* Per-parameter bounds for spot checks of very long sweeps: for j < m,

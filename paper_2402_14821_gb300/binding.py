@@ -54,6 +54,16 @@ def _bind(lib):
                                               _vp, _c_i64, _vp, _vp, _vp, _vp]),
         "bp_lb_debug_params": (ctypes.c_int, [_vp, _vp, _c_i64, _c_i64, _vp, _vp, _c_i64, _vp, _vp]),
         "bp_lb_param_count": (_c_i64, [_c_i32, _c_i64, _i64p, _i64p]),
+        "bp_lb_num_launch_shapes": (ctypes.c_int, []),
+        "bp_lb_launch_shape_info": (ctypes.c_int, [_c_i32, P(_c_i32), P(_c_i32), P(_c_i32),
+                                                   P(_c_i32)]),
+        "bp_lb_set_launch_shape": (ctypes.c_int, [_vp, _c_i32, _c_i32]),
+        "bp_lb_get_launch_shape": (ctypes.c_int, [_vp, _c_i32]),
+        "bp_lb_autotune_batch": (ctypes.c_int, [_vp, _c_i32, _vp, _vp, _c_i32, _vp, _vp, _vp, _vp,
+                                                _vp, _c_i32, _vp, P(_c_i32), _vp]),
+        "bp_lb_autotune_nodes": (ctypes.c_int, [_vp, _c_i32, _c_i32, _vp, _vp, _vp, _vp, _vp, _vp,
+                                                _vp, _c_i64, _vp, _vp, _vp, _c_i32, _vp, P(_c_i32),
+                                                _vp]),
         "bp_lb_selfcheck_division": (_c_i64, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                               _c_i64]),
     }
@@ -78,7 +88,11 @@ def lib():
 EXPORTED = ("bp_lb_strerror", "bp_lb_create", "bp_lb_destroy", "bp_lb_reserve", "bp_lb_eval",
             "bp_lb_eval_node", "bp_lb_eval_batch", "bp_lb_eval_batch_i64", "bp_lb_eval_nodes",
             "bp_lb_reduce_nodes", "bp_lb_debug_params", "bp_lb_param_count",
-            "bp_lb_selfcheck_division")
+            "bp_lb_selfcheck_division", "bp_lb_num_launch_shapes", "bp_lb_launch_shape_info",
+            "bp_lb_set_launch_shape", "bp_lb_get_launch_shape", "bp_lb_autotune_batch",
+            "bp_lb_autotune_nodes")
+
+MODE_RAGGED_I32, MODE_RAGGED_I64, MODE_NODES = 0, 1, 2
 
 
 def strerror(status: int) -> str:
@@ -228,6 +242,63 @@ def bp_lb_param_count(d: int, c: int):
     lo, hi = ctypes.c_int64(), ctypes.c_int64()
     n = lib().bp_lb_param_count(int(d), int(c), ctypes.byref(lo), ctypes.byref(hi))
     return n, lo.value, hi.value
+
+
+def bp_lb_num_launch_shapes() -> int:
+    return lib().bp_lb_num_launch_shapes()
+
+
+def bp_lb_launch_shape_info(shape: int):
+    """(nt, t, g, min_blocks) of one compiled launch shape."""
+    v = [ctypes.c_int32() for _ in range(4)]
+    _check(lib().bp_lb_launch_shape_info(int(shape), *[ctypes.byref(x) for x in v]),
+           "bp_lb_launch_shape_info")
+    return tuple(x.value for x in v)
+
+
+def bp_lb_set_launch_shape(h, mode: int, shape: int):
+    _check(lib().bp_lb_set_launch_shape(h, int(mode), int(shape)), "bp_lb_set_launch_shape")
+
+
+def bp_lb_get_launch_shape(h, mode: int) -> int:
+    return lib().bp_lb_get_launch_shape(h, int(mode))
+
+
+def bp_lb_autotune_batch(h, offsets, sizes, capacity, bins, out_bound, out_argmax=None,
+                         out_feasible=None, reps: int = 3, stream=None):
+    """Times every launch shape on this batch; keeps the fastest.  Returns
+    (best shape, [ms per shape])."""
+    import torch
+    n = bp_lb_num_launch_shapes()
+    ms = (ctypes.c_float * n)()
+    best = ctypes.c_int32()
+    _check(lib().bp_lb_autotune_batch(
+        h, offsets.numel() - 1, _ptr(offsets, torch.int64, "offsets"), _ptr(sizes, None, "sizes"),
+        int(sizes.dtype == torch.int64), _ptr(capacity, torch.int64, "capacity"),
+        _ptr(bins, torch.int64, "bins"), _ptr(out_bound, torch.int64, "out_bound"),
+        _ptr(out_argmax, torch.int64, "out_argmax"), _ptr(out_feasible, torch.uint8, "out_feasible"),
+        int(reps), ms, ctypes.byref(best), _stream(stream)), "bp_lb_autotune_batch")
+    return best.value, list(ms)
+
+
+def bp_lb_autotune_nodes(h, base_offsets, base_sizes, base_capacity, node_base, assign_offsets,
+                         assign, bins, max_bins: int, out_bound, out_argmax=None, out_feasible=None,
+                         reps: int = 3, stream=None):
+    """Times every launch shape on this node batch; keeps the fastest.  Returns
+    (best shape, [ms per shape])."""
+    import torch
+    n = bp_lb_num_launch_shapes()
+    ms = (ctypes.c_float * n)()
+    best = ctypes.c_int32()
+    _check(lib().bp_lb_autotune_nodes(
+        h, node_base.numel(), base_offsets.numel() - 1, _ptr(base_offsets, torch.int64, "base_offsets"),
+        _ptr(base_sizes, torch.int32, "base_sizes"), _ptr(base_capacity, torch.int64, "base_capacity"),
+        _ptr(node_base, torch.int32, "node_base"), _ptr(assign_offsets, torch.int64, "assign_offsets"),
+        _ptr(assign, torch.int32, "assign"), _ptr(bins, torch.int64, "bins"), int(max_bins),
+        _ptr(out_bound, torch.int64, "out_bound"), _ptr(out_argmax, torch.int64, "out_argmax"),
+        _ptr(out_feasible, torch.uint8, "out_feasible"), int(reps), ms, ctypes.byref(best),
+        _stream(stream)), "bp_lb_autotune_nodes")
+    return best.value, list(ms)
 
 
 def bp_lb_selfcheck_division(d_lo: int, d_hi: int, n_hi: int, samples: int) -> int:

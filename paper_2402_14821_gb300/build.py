@@ -7,8 +7,9 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libbp_lb.so")
-SOURCES = ("bp_lb.cu",)
-DEPS = ("bp_lb.cu", "bp_lb_core.cuh", "bp_lb_eval.cuh", "bp_lb_kernels.cuh")
+SOURCES = ("bp_lb.cu", "bp_lb_inst_ragged_i32.cu", "bp_lb_inst_ragged_i64.cu",
+           "bp_lb_inst_nodes.cu")
+DEPS = SOURCES + ("bp_lb_core.cuh", "bp_lb_eval.cuh", "bp_lb_kernels.cuh", "bp_lb_launch.cuh")
 ARCH = ("-gencode", "arch=compute_103a,code=sm_103a")
 
 
@@ -22,14 +23,25 @@ def _stale(out: str) -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile libbp_lb.so (no-op when it is newer than every source)."""
+    """Compile libbp_lb.so (no-op when it is newer than every source).  The
+    translation units compile in parallel, then link into one shared library."""
     if not force and not _stale(LIB):
         return LIB
-    cmd = ["nvcc", *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-o", LIB + ".tmp", *[os.path.join(CSRC, s) for s in SOURCES]]
+    objdir = os.path.join(HERE, "_build")
+    os.makedirs(objdir, exist_ok=True)
+    flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.run(cmd, check=True)
+        flags.append("-Xptxas=-v")
+    procs, objs = [], []
+    for src in SOURCES:
+        obj = os.path.join(objdir, src.replace(".cu", ".o"))
+        objs.append(obj)
+        procs.append((src, subprocess.Popen(["nvcc", *flags, "-c", os.path.join(CSRC, src),
+                                              "-o", obj])))
+    failed = [src for src, p in procs if p.wait() != 0]
+    if failed:
+        raise RuntimeError(f"nvcc failed on {failed}")
+    subprocess.run(["nvcc", *ARCH, "-shared", "-o", LIB + ".tmp", *objs], check=True)
     os.replace(LIB + ".tmp", LIB)
     return LIB
 

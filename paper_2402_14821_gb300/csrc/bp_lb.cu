@@ -16,14 +16,12 @@
 #include "bp_lb_core.cuh"
 #include "bp_lb_eval.cuh"
 #include "bp_lb_kernels.cuh"
+#include "bp_lb_launch.cuh"
 
 using namespace bplb;
 
 namespace {
 
-constexpr int kNT = 256;
-constexpr int kT = 4;
-constexpr int kLPT = kNT * kT;
 constexpr size_t kListBytes = 2 * sizeof(uint32_t) * kListTop;  // items + fp32 quotients
 
 struct PlainOut {  // device and pinned-host layout of one plain result
@@ -57,8 +55,11 @@ struct bp_lb {
   unsigned long long *d_keys = nullptr;
   unsigned int *d_done = nullptr;
   unsigned long long *d_work = nullptr;
-  // occupancy cache
-  int occ_ragged32 = 0, occ_ragged64 = 0, occ_nodes = 0;
+  // launch shape per input mode (index into kShapes) and occupancy cache
+  int shape[3] = {0, 0, 0};
+  int occ_shape[3] = {-1, -1, -1};
+  size_t occ_smem[3] = {0, 0, 0};
+  int occ_blocks[3] = {0, 0, 0};
 };
 
 namespace {
@@ -75,23 +76,35 @@ int cuda_status(cudaError_t e) {
     if (_s != BP_OK) return _s;               \
   } while (0)
 
+#define BP_CHECK_STATUS(expr)                 \
+  do {                                        \
+    const int _s = (expr);                    \
+    if (_s != BP_OK) return _s;               \
+  } while (0)
+
 template <int MODE>
 size_t eval_smem(int64_t max_bins) {
   return kListBytes + (MODE == kSrcNodes ? sizeof(uint32_t) * (size_t)max_bins : 0);
 }
 
-template <int MODE>
-int occupancy(bp_lb *h, size_t smem) {
-  auto kern = eval_kernel<kNT, kT, MODE>;
+// Resident CTAs per SM of the handle's shape for `mode` at `smem` bytes.
+int occupancy(bp_lb *h, int mode, size_t smem) {
+  const int s = h->shape[mode];
+  if (h->occ_shape[mode] == s && h->occ_smem[mode] == smem) return h->occ_blocks[mode];
   int blocks = 0;
-  if (smem > 48 * 1024) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return 0;
-  }
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kNT, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, (const void *)eval_fn(s, mode),
+                                                    kShapes[s].nt, smem) != cudaSuccess)
     return 0;
+  h->occ_shape[mode] = s;
+  h->occ_smem[mode] = smem;
+  h->occ_blocks[mode] = blocks;
   return blocks;
+}
+
+int launch_eval(int shape, int mode, unsigned grid, size_t smem, cudaStream_t st, EvalArgs &A) {
+  void *args[] = {&A};
+  return cuda_status(cudaLaunchKernel((const void *)eval_fn(shape, mode), dim3(grid),
+                                      dim3(kShapes[shape].nt), args, smem, st));
 }
 
 int grow_batch(bp_lb *h, int32_t B) {
@@ -128,14 +141,50 @@ int launch_batch(bp_lb *h, EvalArgs A, size_t smem, cudaStream_t st) {
   A.keys = h->d_keys;
   A.done = h->d_done;
   A.work = h->d_work;
-  int occ = occupancy<MODE>(h, smem);
+  const int shape = h->shape[MODE];
+  const int occ = occupancy(h, MODE, smem);
   if (occ <= 0) return BP_ECUDA;
-  plan_kernel<MODE><<<1, 1024, 0, st>>>(A, (int64_t)kLPT, h->d_tile_start);
+  plan_kernel<MODE><<<1, 1024, 0, st>>>(A, shape_lpt(shape), h->d_tile_start);
   BP_CHECK(cudaGetLastError());
-  const int grid = h->num_sms * occ;
-  eval_kernel<kNT, kT, MODE><<<grid, kNT, smem, st>>>(A);
-  BP_CHECK(cudaGetLastError());
-  return BP_OK;
+  return launch_eval(shape, MODE, (unsigned)(h->num_sms * occ), smem, st, A);
+}
+
+// Times `reps` calls of `call` per launch shape with CUDA events on `st`,
+// leaves the fastest shape set for `mode`.
+template <class F>
+int autotune(bp_lb *h, int mode, int32_t reps, cudaStream_t st, float *ms_out,
+                    int32_t *best_out, F call) {
+  if (reps < 1) return BP_EINVAL;
+  cudaEvent_t e0, e1;
+  BP_CHECK(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return BP_ECUDA;
+  }
+  int best = 0, st_all = BP_OK;
+  float best_ms = 0.f;
+  for (int s = 0; s < kNumShapes && st_all == BP_OK; ++s) {
+    h->shape[mode] = s;
+    st_all = call();  // warm-up (also sets up occupancy)
+    if (st_all != BP_OK) break;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < reps && st_all == BP_OK; ++r) st_all = call();
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) st_all = BP_ECUDA;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= reps;
+    if (ms_out) ms_out[s] = ms;
+    if (s == 0 || ms < best_ms) {
+      best_ms = ms;
+      best = s;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->shape[mode] = best;
+  if (best_out) *best_out = best;
+  return st_all;
 }
 
 }  // namespace
@@ -187,10 +236,11 @@ int bp_lb_create(int64_t capacity, int64_t max_items, bp_lb_t **out) {
     if ((st = cuda_status(cudaMemset(h->d_work, 0, sizeof(unsigned long long)))) != BP_OK) break;
     // the plain node path may use the full on-chip bin table
     const size_t smem_nodes = eval_smem<kSrcNodes>(kMaxNodeBins);
-    if ((st = cuda_status(cudaFuncSetAttribute(eval_kernel<kNT, kT, kSrcNodes>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem_nodes))) != BP_OK)
-      break;
+    for (int sh = 0; sh < kNumShapes && st == BP_OK; ++sh)
+      st = cuda_status(cudaFuncSetAttribute((const void *)eval_fn(sh, kSrcNodes),
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem_nodes));
+    if (st != BP_OK) break;
     if ((st = cuda_status(cudaFuncSetAttribute(reduce_kernel<256>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)(sizeof(uint32_t) * kMaxNodeBins)))) != BP_OK)
@@ -239,14 +289,14 @@ static int plain_finish(bp_lb *h, int64_t *out_bound, bp_argmax_t *out_argmax) {
   return BP_OK;
 }
 
-static EvalArgs plain_args(bp_lb *h, int64_t n, int64_t bins) {
+static EvalArgs plain_args(bp_lb *h, int64_t n, int64_t bins, int mode) {
   EvalArgs A = blank_args();
   A.B = 1;
   A.out_bound = &h->d_out->bound;
   A.out_argmax = &h->d_out->arg;
   A.out_feasible = &h->d_out->feasible;
   A.tile_start = nullptr;
-  A.single_tiles = tiles_for(h->capacity, kLPT);
+  A.single_tiles = tiles_for(h->capacity, shape_lpt(h->shape[mode]));
   A.single_c = h->capacity;
   A.single_k = bins;
   A.single_n = n;
@@ -268,11 +318,10 @@ int bp_lb_eval(bp_lb_t *h, const int32_t *sizes, int64_t n, int64_t bins, int64_
     BP_CHECK(cudaMemcpyAsync(h->d_items, h->h_items, sizeof(int32_t) * (size_t)n,
                              cudaMemcpyHostToDevice, h->stream));
   }
-  EvalArgs A = plain_args(h, n, bins);
+  EvalArgs A = plain_args(h, n, bins, kSrcRaggedI32);
   A.sizes = h->d_items;
-  eval_kernel<kNT, kT, kSrcRaggedI32>
-      <<<(unsigned)A.single_tiles, kNT, eval_smem<kSrcRaggedI32>(0), h->stream>>>(A);
-  BP_CHECK(cudaGetLastError());
+  BP_CHECK_STATUS(launch_eval(h->shape[kSrcRaggedI32], kSrcRaggedI32, (unsigned)A.single_tiles,
+                              eval_smem<kSrcRaggedI32>(0), h->stream, A));
   return plain_finish(h, out_bound, out_argmax);
 }
 
@@ -288,13 +337,12 @@ int bp_lb_eval_node(bp_lb_t *h, const int32_t *w, const int32_t *assign, int64_t
     BP_CHECK(cudaMemcpyAsync(h->d_assign, h->h_assign, sizeof(int32_t) * (size_t)n,
                              cudaMemcpyHostToDevice, h->stream));
   }
-  EvalArgs A = plain_args(h, n, bins);
+  EvalArgs A = plain_args(h, n, bins, kSrcNodes);
   A.base_sizes = h->d_items;
   A.assign = h->d_assign;
   A.max_bins = (int32_t)bins;
-  eval_kernel<kNT, kT, kSrcNodes>
-      <<<(unsigned)A.single_tiles, kNT, eval_smem<kSrcNodes>(bins), h->stream>>>(A);
-  BP_CHECK(cudaGetLastError());
+  BP_CHECK_STATUS(launch_eval(h->shape[kSrcNodes], kSrcNodes, (unsigned)A.single_tiles,
+                              eval_smem<kSrcNodes>(bins), h->stream, A));
   return plain_finish(h, out_bound, out_argmax);
 }
 
@@ -412,6 +460,58 @@ int bp_lb_debug_params(bp_lb_t *h, const int32_t *d_sizes, int64_t n, int64_t c,
                                                                      d_out_lb);
   BP_CHECK(cudaGetLastError());
   return BP_OK;
+}
+
+int bp_lb_num_launch_shapes(void) { return kNumShapes; }
+
+int bp_lb_launch_shape_info(int32_t id, int32_t *nt, int32_t *t, int32_t *g, int32_t *min_blocks) {
+  if (id < 0 || id >= kNumShapes) return BP_ERANGE;
+  if (nt) *nt = kShapes[id].nt;
+  if (t) *t = kShapes[id].t;
+  if (g) *g = kShapes[id].g;
+  if (min_blocks) *min_blocks = kShapes[id].minb;
+  return BP_OK;
+}
+
+int bp_lb_set_launch_shape(bp_lb_t *h, int32_t mode, int32_t id) {
+  if (!h || mode < 0 || mode > 2) return BP_EINVAL;
+  if (id < 0 || id >= kNumShapes) return BP_ERANGE;
+  h->shape[mode] = id;
+  return BP_OK;
+}
+
+int bp_lb_get_launch_shape(bp_lb_t *h, int32_t mode) {
+  if (!h || mode < 0 || mode > 2) return -1;
+  return h->shape[mode];
+}
+
+int bp_lb_autotune_batch(bp_lb_t *h, int32_t B, const int64_t *d_offsets, const void *d_sizes,
+                         int32_t sizes_are_i64, const int64_t *d_capacity, const int64_t *d_bins,
+                         int64_t *d_out_bound, bp_argmax_t *d_out_argmax, uint8_t *d_out_feasible,
+                         int32_t reps, float *ms_per_shape, int32_t *best_shape, void *stream) {
+  if (!h || B < 1) return BP_EINVAL;
+  const int mode = sizes_are_i64 ? kSrcRaggedI64 : kSrcRaggedI32;
+  return autotune(h, mode, reps, (cudaStream_t)stream, ms_per_shape, best_shape, [&]() {
+    return sizes_are_i64
+               ? bp_lb_eval_batch_i64(h, B, d_offsets, (const int64_t *)d_sizes, d_capacity, d_bins,
+                                      d_out_bound, d_out_argmax, d_out_feasible, stream)
+               : bp_lb_eval_batch(h, B, d_offsets, (const int32_t *)d_sizes, d_capacity, d_bins,
+                                  d_out_bound, d_out_argmax, d_out_feasible, stream);
+  });
+}
+
+int bp_lb_autotune_nodes(bp_lb_t *h, int32_t B, int32_t num_base, const int64_t *d_base_offsets,
+                         const int32_t *d_base_sizes, const int64_t *d_base_capacity,
+                         const int32_t *d_node_base, const int64_t *d_assign_offsets,
+                         const int32_t *d_assign, const int64_t *d_bins, int64_t max_bins,
+                         int64_t *d_out_bound, bp_argmax_t *d_out_argmax, uint8_t *d_out_feasible,
+                         int32_t reps, float *ms_per_shape, int32_t *best_shape, void *stream) {
+  if (!h || B < 1) return BP_EINVAL;
+  return autotune(h, kSrcNodes, reps, (cudaStream_t)stream, ms_per_shape, best_shape, [&]() {
+    return bp_lb_eval_nodes(h, B, num_base, d_base_offsets, d_base_sizes, d_base_capacity,
+                            d_node_base, d_assign_offsets, d_assign, d_bins, max_bins, d_out_bound,
+                            d_out_argmax, d_out_feasible, stream);
+  });
 }
 
 int64_t bp_lb_param_count(int32_t d, int64_t c, int64_t *lo, int64_t *hi) {

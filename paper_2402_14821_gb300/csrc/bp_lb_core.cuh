@@ -129,8 +129,10 @@ struct InstSums {
 BPLB_HD int64_t ceil_div_i64(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // ---------------------------------------------------------------------------
-// S(d, lambda) assembly from the lambda-dependent list sums, and f(c, lambda).
-// The list sums are defined next to each evaluator below.
+// S(d, lambda) = sum_i f_d(w_i, lambda) assembled from one lambda-dependent
+// list accumulator (defined next to each evaluator in bp_lb_eval.cuh) and the
+// lambda-independent instance sums.  Each identity below is an exact
+// rearrangement of the printed case analysis (Sec. 3.1).
 // ---------------------------------------------------------------------------
 
 // f_MT(w, l) = c if w > c - l; w if l <= w <= c - l; 0 if w < l (l <= c/2).
@@ -138,10 +140,9 @@ BPLB_HD int64_t ceil_div_i64(int64_t a, int64_t b) { return (a + b - 1) / b; }
 //   big   (w > c/2 >= l):          w + u * [u < l]   (u = c - w; w > c - l <=> u < l)
 //   half  (w = c/2):               c/2
 //   full:                          c = f(c)
-// acc0 = sum_small u2*[u2 >= 2l], acc1 = sum_big u2*[u2 < 2l]  (u2 = 2u).
-BPLB_HD int64_t mt_sum(const InstSums &s, int64_t c, uint64_t acc0, uint64_t acc1) {
-  return (int64_t)(acc0 >> 1) + s.sumw_big + (int64_t)(acc1 >> 1) + s.n_half * (c / 2) +
-         s.n_full * c;
+// acc = sum_small u2*[u2 >= 2l] + sum_big u2*[u2 < 2l]   (u2 = 2u).
+BPLB_HD int64_t mt_sum(const InstSums &s, int64_t c, uint64_t acc) {
+  return (int64_t)(acc >> 1) + s.sumw_big + s.n_half * (c / 2) + s.n_full * c;
 }
 
 // f_RAD2, c/4 < l <= c/3, A = floor(c/3), B = floor(c/2):
@@ -150,41 +151,34 @@ BPLB_HD int64_t mt_sum(const InstSums &s, int64_t c, uint64_t acc0, uint64_t acc
 //   big:   w < 2l <=> u > c - 2l: B;  else c - f(u): c - A (u >= l) or c (u < l)
 //        = c - A*[u >= l] - (c - A - B)*[u > c - 2l]
 //   half:  B;  full: c.
-// Counts N1 = #[u2 >= 2l], N2 = #[u2 > 2c - 4l] per list.
-BPLB_HD int64_t rad2_sum(const InstSums &s, int64_t c, int64_t n1s, int64_t n2s, int64_t n1b,
-                         int64_t n2b) {
+// n1 = #small[u >= l] - #big[u >= l]; n2s, n2b = #[u > c - 2l] per list.
+BPLB_HD int64_t rad2_sum(const InstSums &s, int64_t c, int64_t n1, int64_t n2s, int64_t n2b) {
   const int64_t A = c / 3, B = c / 2;
-  return A * n1s + (B - A) * n2s + s.n_big * c - A * n1b - (c - A - B) * n2b + s.n_half * B +
-         s.n_full * c;
+  return A * n1 + (B - A) * n2s + s.n_big * c - (c - A - B) * n2b + s.n_half * B + s.n_full * c;
 }
 
 // f_FS1(w, l) = w*l if c | w(l+1), else c*floor(w(l+1)/c)
 //            = c*floor(w(l+1)/c) - w*[c | w(l+1)]   (raw sizes, all items).
-// acc0 = sum floor(w(l+1)/c), acc1 = sum w*[c | w(l+1)].
-BPLB_HD int64_t fs1_sum(int64_t c, uint64_t acc0, uint64_t acc1) {
-  return c * (int64_t)acc0 - (int64_t)acc1;
-}
+// acc = sum of that expression.
+BPLB_HD int64_t fs1_sum(int64_t acc) { return acc; }
 
 // f_CCM1, Q = floor(c/l): big 2Q - 2 floor(u/l); half Q; small 2 floor(u/l); full 2Q.
-// acc0 = sum_small floor(u/l), acc1 = sum_big floor(u/l).
-BPLB_HD int64_t ccm1_sum(const InstSums &s, int64_t Q, uint64_t acc0, uint64_t acc1) {
-  return 2 * ((int64_t)acc0 - (int64_t)acc1) + Q * (2 * s.n_big + s.n_half + 2 * s.n_full);
+// acc = sum_small floor(u/l) - sum_big floor(u/l).
+BPLB_HD int64_t ccm1_sum(const InstSums &s, int64_t Q, int64_t acc) {
+  return 2 * acc + Q * (2 * s.n_big + s.n_half + 2 * s.n_full);
 }
 
 // f_VB2 with ceil(c*l/c) = l and g(u) = max(0, ceil(u*l/c) - 1) = ceil(u*l/c) - 1 for u >= 1:
 //   small 2 g(u); big 2(l-1) - 2 g(u); half l - 1; full 2(l-1) = f(c).
-// acc0 = sum_small ceil(u*l/c), acc1 = sum_big ceil(u*l/c)  (every listed u >= 1).
-BPLB_HD int64_t vb2_sum(const InstSums &s, int64_t l, uint64_t acc0, uint64_t acc1) {
-  return 2 * ((int64_t)acc0 - s.n_small) - 2 * ((int64_t)acc1 - s.n_big) +
-         (l - 1) * (2 * s.n_big + s.n_half + 2 * s.n_full);
+// acc = sum_small ceil(u*l/c) - sum_big ceil(u*l/c)  (every listed u >= 1).
+BPLB_HD int64_t vb2_sum(const InstSums &s, int64_t l, int64_t acc) {
+  return 2 * (acc - s.n_small + s.n_big) + (l - 1) * (2 * s.n_big + s.n_half + 2 * s.n_full);
 }
 
 // f_BJ1 with q = floor(w/l), rho = w mod l, cm = c mod l:
-//   q(l - cm) + max(0, rho - cm) = w - cm*q - min(rho, cm)      (w = q l + rho).
-// acc0 = sum q, acc1 = sum min(2 rho, 2 cm)  (raw sizes, all items).
-BPLB_HD int64_t bj1_sum(const InstSums &s, int64_t cm, uint64_t acc0, uint64_t acc1) {
-  return s.sumw - cm * (int64_t)acc0 - (int64_t)(acc1 >> 1);
-}
+//   q(l - cm) + max(0, rho - cm) = w - (cm*q + min(rho, cm))    (w = q l + rho).
+// acc = sum (cm*q + min(rho, cm))  (raw sizes, all items).
+BPLB_HD int64_t bj1_sum(const InstSums &s, int64_t acc) { return s.sumw - acc; }
 
 // f(c, lambda) of each DFF (Sec. 3.1): the denominator of the bound.  > 0 on
 // every parameter range: MT c, RAD2 c, FS1 c*l, CCM1 2 floor(c/l) >= 4,

@@ -1,23 +1,26 @@
-// bp_lb_eval.cuh -- per-DFF evaluation of one staged item list for T
-// parameters per thread (Alg. 4's "one parameter per thread", with T
-// parameters per thread so that every item read from shared memory feeds T
+// bp_lb_eval.cuh -- per-DFF inner loops over one staged item list, for T
+// parameters per thread (Alg. 4 gives each GPU thread one parameter; here a
+// thread carries T of them so that every item read from shared memory feeds T
 // independent evaluations).
 //
 // Lists live in shared memory as uint32 values, padded with zeros to a
-// multiple of 4 so that each step reads four items with one 16-byte
-// broadcast load.  A zero pad contributes 0 to every list sum below.
+// multiple of 4 so that each step reads four items with one 16-byte broadcast
+// load (all lanes of a warp read the same address).  A zero pad contributes 0
+// to every list sum below.
 //
-// Partial sums are 32-bit within a group of K items, chosen so that the
-// group's true sum stays below 2^32, then added into 64-bit accumulators
-// (the WIDE variants accumulate in 64 bits directly; they serve capacities
-// above the fast-path limits).
+// Partial sums are 32-bit within a group of K items, K chosen so that the
+// group's true sum stays below 2^32, then folded into one 64-bit accumulator
+// per parameter with the sign (+1 small list, -1 big list) or weight the DFF's
+// sum needs.  The *_wide variants accumulate in 64 bits directly; they serve
+// capacities above the fast-path limits.
 #pragma once
 
 #include "bp_lb_core.cuh"
 
 namespace bplb {
 
-// Largest multiple of 4 not above floor((2^32 - 1) / max_term), at least 4.
+// Largest multiple of 4 not above floor((2^32 - 1) / max_term), capped at 2^30.
+// Callers guarantee max_term <= 2^30 - 1 so that the result is >= 4.
 BPLB_HD int group_len(int64_t max_term) {
   if (max_term < 1) max_term = 1;
   int64_t k = (int64_t)0xFFFFFFFFu / max_term;
@@ -29,10 +32,10 @@ BPLB_HD int group_len(int64_t max_term) {
 BPLB_D uint4 lds4(const uint32_t *s, int i) { return *reinterpret_cast<const uint4 *>(s + i); }
 BPLB_D float4 lds4f(const float *s, int i) { return *reinterpret_cast<const float4 *>(s + i); }
 
-// ---- MT: sum_small u2*[u2 >= 2l] and sum_big u2*[u2 < 2l] -------------------
-template <int T>
+// ---- MT: acc += sum_small u2*[u2 >= 2l]  (BIG: sum_big u2*[u2 < 2l]) ---------
+template <int T, bool BIG>
 BPLB_D void mt_list(const uint32_t *s, int beg, int end, int K, const uint32_t (&thr)[T],
-                    bool big, uint64_t (&acc)[T]) {
+                    uint64_t (&acc)[T]) {
   for (int g0 = beg; g0 < end; g0 += K) {
     const int g1 = min(end, g0 + K);
     uint32_t a[T];
@@ -42,7 +45,7 @@ BPLB_D void mt_list(const uint32_t *s, int beg, int end, int K, const uint32_t (
       const uint4 v = lds4(s, i);
 #pragma unroll
       for (int j = 0; j < T; ++j) {
-        if (!big) {
+        if (!BIG) {
           a[j] += (v.x >= thr[j] ? v.x : 0u) + (v.y >= thr[j] ? v.y : 0u);
           a[j] += (v.z >= thr[j] ? v.z : 0u) + (v.w >= thr[j] ? v.w : 0u);
         } else {
@@ -56,31 +59,26 @@ BPLB_D void mt_list(const uint32_t *s, int beg, int end, int K, const uint32_t (
   }
 }
 
-// ---- RAD2: counts #[u2 >= 2l] (low half) and #[u2 > 2c - 4l] (high half) ----
-template <int T>
+// ---- RAD2: n1 += #[u2 >= 2l] (SIGN), n2 += #[u2 > 2c - 4l] ---------------------
+template <int T, int SIGN>
 BPLB_D void rad2_list(const uint32_t *s, int beg, int end, const uint32_t (&t1)[T],
-                      const uint32_t (&t2)[T], uint64_t (&acc)[T]) {
-  uint32_t n1[T], n2[T];
-#pragma unroll
-  for (int j = 0; j < T; ++j) n1[j] = n2[j] = 0;
+                      const uint32_t (&t2)[T], int32_t (&n1)[T], uint32_t (&n2)[T]) {
   for (int i = beg; i < end; i += 4) {
     const uint4 v = lds4(s, i);
 #pragma unroll
     for (int j = 0; j < T; ++j) {
-      n1[j] += (uint32_t)(v.x >= t1[j]) + (uint32_t)(v.y >= t1[j]) + (uint32_t)(v.z >= t1[j]) +
-               (uint32_t)(v.w >= t1[j]);
+      const int32_t c1 = (int32_t)((v.x >= t1[j]) + (v.y >= t1[j]) + (v.z >= t1[j]) + (v.w >= t1[j]));
+      n1[j] += SIGN * c1;
       n2[j] += (uint32_t)(v.x > t2[j]) + (uint32_t)(v.y > t2[j]) + (uint32_t)(v.z > t2[j]) +
                (uint32_t)(v.w > t2[j]);
     }
   }
-#pragma unroll
-  for (int j = 0; j < T; ++j) acc[j] += (uint64_t)n1[j] | ((uint64_t)n2[j] << 32);
 }
 
-// ---- FS1 (raw w): sum floor(w(l+1)/c) and sum w*[c | w(l+1)] -----------------
+// ---- FS1 (raw w): acc += c * floor(w(l+1)/c) - w*[c | w(l+1)] ----------------
 template <int T>
 BPLB_D void fs1_list(const uint32_t *s, int beg, int end, int K, const uint32_t (&mul2)[T],
-                     Div31 Dc, uint32_t c2, uint64_t (&acc0)[T], uint64_t (&acc1)[T]) {
+                     Div31 Dc, uint32_t c2, int64_t c, int64_t (&acc)[T]) {
   for (int g0 = beg; g0 < end; g0 += K) {
     const int g1 = min(end, g0 + K);
     uint32_t a0[T], a1[T];
@@ -101,31 +99,27 @@ BPLB_D void fs1_list(const uint32_t *s, int beg, int end, int K, const uint32_t 
       }
     }
 #pragma unroll
-    for (int j = 0; j < T; ++j) {
-      acc0[j] += a0[j];
-      acc1[j] += a1[j];
-    }
+    for (int j = 0; j < T; ++j) acc[j] += c * (int64_t)a0[j] - (int64_t)a1[j];
   }
 }
 
 template <int T>
 BPLB_D void fs1_list_wide(const uint32_t *s, int beg, int end, const int64_t (&lam)[T], int64_t c,
-                          uint64_t (&acc0)[T], uint64_t (&acc1)[T]) {
+                          int64_t (&acc)[T]) {
   for (int i = beg; i < end; ++i) {
     const int64_t w = s[i];
 #pragma unroll
     for (int j = 0; j < T; ++j) {
       const int64_t x = w * (lam[j] + 1);
-      acc0[j] += (uint64_t)(x / c);
-      acc1[j] += (x % c == 0) ? (uint64_t)w : 0u;
+      acc[j] += c * (x / c) - ((x % c == 0) ? w : 0);
     }
   }
 }
 
-// ---- CCM1 (u2 = 2u): sum floor(u / l) ----------------------------------------
-template <int T>
+// ---- CCM1 (u2 = 2u): acc += SIGN * floor(u / l) ---------------------------------
+template <int T, int SIGN>
 BPLB_D void ccm1_list(const uint32_t *s, int beg, int end, int K, const Div31 (&D)[T],
-                      uint64_t (&acc)[T]) {
+                      int64_t (&acc)[T]) {
   for (int g0 = beg; g0 < end; g0 += K) {
     const int g1 = min(end, g0 + K);
     uint32_t a[T];
@@ -140,16 +134,16 @@ BPLB_D void ccm1_list(const uint32_t *s, int beg, int end, int K, const Div31 (&
       }
     }
 #pragma unroll
-    for (int j = 0; j < T; ++j) acc[j] += a[j];
+    for (int j = 0; j < T; ++j) acc[j] += SIGN * (int64_t)a[j];
   }
 }
 
-// ---- VB2 (u2 = 2u): sum ceil(u l / c) -----------------------------------------
+// ---- VB2 (u2 = 2u): acc += SIGN * ceil(u l / c) ---------------------------------
 // c <= 65535: ceil(u l / c) = floor((u l + c - 1) / c), numerator < 2^31, exact
 // multiply-high division by c.
-template <int T>
+template <int T, int SIGN>
 BPLB_D void vb2_list_magic(const uint32_t *s, int beg, int end, int K, const uint32_t (&lam)[T],
-                           Div31 Dc, uint32_t add2, uint64_t (&acc)[T]) {
+                           Div31 Dc, uint32_t add2, int64_t (&acc)[T]) {
   for (int g0 = beg; g0 < end; g0 += K) {
     const int g1 = min(end, g0 + K);
     uint32_t a[T];
@@ -165,7 +159,7 @@ BPLB_D void vb2_list_magic(const uint32_t *s, int beg, int end, int K, const uin
       }
     }
 #pragma unroll
-    for (int j = 0; j < T; ++j) acc[j] += a[j];
+    for (int j = 0; j < T; ++j) acc[j] += SIGN * (int64_t)a[j];
   }
 }
 
@@ -180,10 +174,10 @@ BPLB_D void vb2_list_magic(const uint32_t *s, int beg, int end, int K, const uin
 //   0x4B400000 per list slot at the end of each group.
 constexpr uint32_t kF32RoundBits = 0x4B400000u;  // bit pattern of 1.5 * 2^23
 
-template <int T>
+template <int T, int SIGN>
 BPLB_D void vb2_list_float(const uint32_t *s, const float *sa, int beg, int end, int K,
                            const uint32_t (&lam)[T], const float (&lamf)[T], uint32_t c2,
-                           uint32_t K2, uint64_t (&acc)[T]) {
+                           uint32_t K2, int64_t (&acc)[T]) {
   for (int g0 = beg; g0 < end; g0 += K) {
     const int g1 = min(end, g0 + K);
     uint32_t a[T];
@@ -206,25 +200,24 @@ BPLB_D void vb2_list_float(const uint32_t *s, const float *sa, int beg, int end,
     }
     const uint32_t slots = (uint32_t)(g1 - g0);
 #pragma unroll
-    for (int j = 0; j < T; ++j) acc[j] += (uint32_t)(a[j] - slots * kF32RoundBits);
+    for (int j = 0; j < T; ++j) acc[j] += SIGN * (int64_t)(uint32_t)(a[j] - slots * kF32RoundBits);
   }
 }
 
-template <int T>
+template <int T, int SIGN>
 BPLB_D void vb2_list_wide(const uint32_t *s, int beg, int end, const int64_t (&lam)[T], int64_t c,
-                          uint64_t (&acc)[T]) {
+                          int64_t (&acc)[T]) {
   for (int i = beg; i < end; ++i) {
     const int64_t u = s[i] >> 1;
 #pragma unroll
-    for (int j = 0; j < T; ++j) acc[j] += (uint64_t)((u * lam[j] + c - 1) / c);
+    for (int j = 0; j < T; ++j) acc[j] += SIGN * ((u * lam[j] + c - 1) / c);
   }
 }
 
-// ---- BJ1 (w2 = 2w): sum floor(w / l) and sum min(2 (w mod l), 2 (c mod l)) ----
+// ---- BJ1 (w2 = 2w): acc += cm * floor(w / l) + min(w mod l, cm) ---------------
 template <int T>
 BPLB_D void bj1_list(const uint32_t *s, int beg, int end, int K, const Div31 (&D)[T],
-                     const uint32_t (&l2)[T], const uint32_t (&cm2)[T], uint64_t (&acc0)[T],
-                     uint64_t (&acc1)[T]) {
+                     const uint32_t (&l2)[T], const uint32_t (&cm2)[T], int64_t (&acc)[T]) {
   for (int g0 = beg; g0 < end; g0 += K) {
     const int g1 = min(end, g0 + K);
     uint32_t a0[T], a1[T];
@@ -245,23 +238,20 @@ BPLB_D void bj1_list(const uint32_t *s, int beg, int end, int K, const Div31 (&D
       }
     }
 #pragma unroll
-    for (int j = 0; j < T; ++j) {
-      acc0[j] += a0[j];
-      acc1[j] += a1[j];
-    }
+    for (int j = 0; j < T; ++j)
+      acc[j] += (int64_t)(cm2[j] >> 1) * (int64_t)a0[j] + (int64_t)(a1[j] >> 1);
   }
 }
 
 template <int T>
 BPLB_D void bj1_list_wide(const uint32_t *s, int beg, int end, const int64_t (&lam)[T], int64_t c,
-                          uint64_t (&acc0)[T], uint64_t (&acc1)[T]) {
+                          int64_t (&acc)[T]) {
   for (int i = beg; i < end; ++i) {
     const int64_t w = s[i] >> 1;
 #pragma unroll
     for (int j = 0; j < T; ++j) {
       const int64_t q = w / lam[j], rho = w % lam[j], cm = c % lam[j];
-      acc0[j] += (uint64_t)q;
-      acc1[j] += (uint64_t)(2 * (rho < cm ? rho : cm));
+      acc[j] += cm * q + (rho < cm ? rho : cm);
     }
   }
 }

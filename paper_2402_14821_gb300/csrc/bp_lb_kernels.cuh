@@ -227,106 +227,296 @@ __device__ __forceinline__ bool fetch_item(const EvalArgs &A, const InstView &I,
   }
 }
 
-template <int NT, int T, int MODE>
-__device__ void process_tile(const EvalArgs &A, int64_t b, int64_t lt, int64_t ntiles,
-                             const InstView &I, uint32_t *s_items, float *s_a, uint32_t *s_load,
-                             TileShared &S, const int32_t *req_dff = nullptr,
-                             const int64_t *req_lam = nullptr, int64_t req_m = 0,
-                             int64_t *req_out = nullptr, int req_d = -1) {
-  constexpr int LPT = NT * T;
-  const int tid = threadIdx.x;
-  const int64_t c = I.c;
+// Stream length of an instance: its items, or for a search node its base
+// items (packed ones are filtered out) followed by its bin loads.
+template <int MODE>
+__device__ __forceinline__ int64_t stream_len(const InstView &I) {
+  return MODE == kSrcNodes ? I.n + I.k : I.n;
+}
 
-  // ---- which DFF and which lambdas -------------------------------------
-  int d = 0;
-  int64_t lam0 = 0, lam_end = 0;
-  int64_t lam[T];
-  bool valid[T];
-  int64_t lo_d, hi_d;
-  if (req_d < 0) {
-    int64_t rem = lt;
-    for (d = 0; d < kNumDff; ++d) {
-      const int64_t nt = (param_count(d, c) + LPT - 1) / LPT;
-      if (rem < nt) break;
-      rem -= nt;
+// Local (per-thread) instance sums, reduced over the block once per tile.
+struct LocalSums {
+  int64_t v[6];  // n_small, n_big, n_half, n_full, sumw_big, sumw
+};
+
+// Stages stream positions [p, p + len) into the shared lists:
+//   ULIST: small items as 2w from index 0 up, big items as 2(c - w) from
+//          kListTop - 1 down (plus fl(u / c) in s_a when stage_a);
+//   else:  every nonzero item as w (or 2w when WDOUBLE) from index 0 up.
+// Sizes outside [0, c] set S.err.  COUNT adds the instance sums.
+template <int NT, int MODE, bool ULIST, bool WDOUBLE>
+__device__ __forceinline__ void stage_chunk(const EvalArgs &A, const InstView &I, const uint32_t *s_load,
+                                            int64_t p, int len, bool stage_a, bool count,
+                                            uint32_t *s_items, float *s_a, TileShared &S,
+                                            LocalSums &ls) {
+  const int64_t c = I.c;
+  for (int o = 0; o < len; o += NT) {
+    const int64_t q = p + o + threadIdx.x;
+    int64_t w = 0;
+    bool have = false;
+    if (o + (int)threadIdx.x < len) have = fetch_item<MODE>(A, I, s_load, q, w);
+    if (have && (w < 0 || w > c)) {
+      S.err = 1;
+      have = false;
     }
-    param_range(d, c, lo_d, hi_d);
-    lam0 = lo_d + rem * LPT;
-    lam_end = min(hi_d + 1, lam0 + LPT);
-#pragma unroll
-    for (int j = 0; j < T; ++j) {
-      const int64_t l = lam0 + (int64_t)j * NT + tid;
-      valid[j] = l < lam_end;
-      lam[j] = valid[j] ? l : lo_d;
-    }
-  } else {
-    d = req_d;
-    param_range(d, c, lo_d, hi_d);
-    const int64_t r = (int64_t)blockIdx.x * NT + tid;
-    if (d == 0 && r < req_m && (req_dff[r] < 0 || req_dff[r] >= kNumDff)) req_out[r] = -BP_ERANGE;
-    const bool mine = r < req_m && req_dff[r] == d;
-    const int64_t l = mine ? req_lam[r] : lo_d;
-    valid[0] = mine && l >= lo_d && l <= hi_d;
-    lam[0] = valid[0] ? l : lo_d;
-    if (mine && !valid[0]) req_out[r] = -BP_ERANGE;
-#pragma unroll
-    for (int j = 1; j < T; ++j) {
-      valid[j] = false;
-      lam[j] = lo_d;
+    if (have && w == 0) have = false;
+    if (count && have) ls.v[5] += w;
+    if (ULIST) {
+      const bool full = have && w == c;
+      const bool small = have && !full && 2 * w < c;
+      const bool big = have && !full && 2 * w > c;
+      if (count) {
+        ls.v[0] += small;
+        ls.v[1] += big;
+        ls.v[2] += have && 2 * w == c;
+        ls.v[3] += full;
+        if (big) ls.v[4] += w;
+      }
+      const int ps = warp_append(small, &S.ns);
+      const int pb = warp_append(big, &S.nb);
+      if (small) {
+        s_items[ps] = (uint32_t)(2 * w);
+        if (stage_a) s_a[ps] = __fdiv_rn((float)w, (float)c);
+      }
+      if (big) {
+        const int slot = kListTop - 1 - pb;
+        s_items[slot] = (uint32_t)(2 * (c - w));
+        if (stage_a) s_a[slot] = __fdiv_rn((float)(c - w), (float)c);
+      }
+    } else {
+      const int ps = warp_append(have, &S.ns);
+      if (have) s_items[ps] = WDOUBLE ? (uint32_t)(2 * w) : (uint32_t)w;
     }
   }
+}
 
-  // ---- per-lambda constants ------------------------------------------------
-  const bool ulist = (d == kMT || d == kRAD2 || d == kCCM1 || d == kVB2);
-  const bool narrow = c <= kNarrowCap;  // BJ1: terms < 2c stay below 2^30
+// Evaluates one tile of DFF D: lambdas [lam0, lam_end) in groups of NT * T,
+// thread t taking lam_g + j * NT + t (j < T) in group g.  Returns the
+// thread's largest key make_key(lb, flat index); 0 if it had no parameter.
+// With DEBUG the thread's single parameter comes from a request list and its
+// bound is written to req_out instead.
+template <int NT, int T, int D, int MODE, bool DEBUG>
+__device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int64_t lam0,
+                                       int64_t lam_end, uint32_t *s_items, float *s_a,
+                                       const uint32_t *s_load, TileShared &S,
+                                       const int64_t *req_lam = nullptr, int64_t *req_out = nullptr,
+                                       int64_t req_idx = -1) {
+  constexpr bool ULIST = (D == kMT || D == kRAD2 || D == kCCM1 || D == kVB2);
+  constexpr int GW = NT * T;
+  const int tid = threadIdx.x;
+  const int64_t c = I.c;
+  int64_t lo_d, hi_d;
+  param_range(D, c, lo_d, hi_d);
+  const uint32_t gbase = flat_index(D, lo_d, c);
   const bool vb2_magic = c <= kVb2MagicCap;
-  const bool vb2_float = !vb2_magic && c <= kVb2FloatCap;
+  const bool stage_a = (D == kVB2) && !vb2_magic && c <= kVb2FloatCap;
+  const bool narrow = c <= kNarrowCap;  // BJ1: terms < 2c stay below 2^30
   const bool fs1_fast = c <= kFs1FastCap;
-  const bool stage_a = (d == kVB2) && vb2_float;
+  const Div31 Dc = div31_make((uint32_t)c);
+  const uint32_t c2 = (uint32_t)(2 * c);
 
-  uint32_t p0[T], p1[T], p2[T];
-  float pf[T];
-  Div31 Dl[T];
+  const int64_t L = stream_len<MODE>(I);
+  const bool one_chunk = L <= kChunk;
+  const int ngroups = DEBUG ? 1 : (int)((lam_end - lam0 + GW - 1) / GW);
+  LocalSums ls;
 #pragma unroll
-  for (int j = 0; j < T; ++j) {
-    p0[j] = p1[j] = p2[j] = 0;
-    pf[j] = 0.f;
-    Dl[j].m = 0;
-    Dl[j].l = 0;
-    const uint32_t l32 = (uint32_t)lam[j];
-    switch (d) {
-      case kMT: p0[j] = 2u * l32; break;
-      case kRAD2:
-        p0[j] = 2u * l32;
-        p1[j] = (uint32_t)(2 * c - 4 * lam[j]);
-        break;
-      case kFS1: p0[j] = 2u * l32 + 2u; break;
-      case kCCM1: Dl[j] = div31_make(l32); break;
-      case kVB2:
-        p0[j] = l32;
-        pf[j] = (float)l32;
-        break;
-      default: {  // BJ1
+  for (int e = 0; e < 6; ++e) ls.v[e] = 0;
+  unsigned long long best = 0ull;
+
+  for (int g = 0; g < ngroups; ++g) {
+    // ---- this group's parameters and their constants -------------------------
+    int64_t lam[T];
+    bool valid[T];
+#pragma unroll
+    for (int j = 0; j < T; ++j) {
+      int64_t l;
+      if (DEBUG) {
+        l = (j == 0 && req_idx >= 0) ? req_lam[req_idx] : lo_d;
+      } else {
+        l = lam0 + (int64_t)g * GW + (int64_t)j * NT + tid;
+      }
+      valid[j] = DEBUG ? (j == 0 && req_idx >= 0 && l >= lo_d && l <= hi_d) : (l < lam_end);
+      lam[j] = valid[j] ? l : lo_d;
+    }
+    uint32_t k0[T], k1[T], k2[T];
+    float kf[T];
+    Div31 Dl[T];
+#pragma unroll
+    for (int j = 0; j < T; ++j) {
+      const uint32_t l32 = (uint32_t)lam[j];
+      k0[j] = k1[j] = k2[j] = 0;
+      kf[j] = 0.f;
+      Dl[j].m = Dl[j].l = 0;
+      if (D == kMT) {
+        k0[j] = 2u * l32;
+      } else if (D == kRAD2) {
+        k0[j] = 2u * l32;
+        k1[j] = (uint32_t)(2 * c - 4 * lam[j]);
+      } else if (D == kFS1) {
+        k0[j] = 2u * l32 + 2u;
+      } else if (D == kCCM1) {
         Dl[j] = div31_make(l32);
-        p0[j] = 2u * l32;
-        const uint32_t q = div31((uint32_t)(2 * c), Dl[j]);
-        p1[j] = 2u * ((uint32_t)c - q * l32);  // 2 (c mod l)
+      } else if (D == kVB2) {
+        k0[j] = l32;
+        kf[j] = (float)l32;
+      } else {  // BJ1
+        Dl[j] = div31_make(l32);
+        k0[j] = 2u * l32;
+        const uint32_t q = div31(c2, Dl[j]);       // floor(c / l)
+        k1[j] = 2u * ((uint32_t)c - q * l32);      // 2 (c mod l)
+      }
+    }
+    int64_t acc[T];
+    int32_t n1[T];
+    uint32_t n2s[T], n2b[T];
+#pragma unroll
+    for (int j = 0; j < T; ++j) {
+      acc[j] = 0;
+      n1[j] = 0;
+      n2s[j] = n2b[j] = 0;
+    }
+
+    // ---- stream the instance through shared memory ---------------------------
+    for (int64_t p = 0; p < L || (p == 0 && L == 0); p += kChunk) {
+      const bool stage = (g == 0) || !one_chunk;
+      if (stage) {
+        if (tid == 0) {
+          S.ns = 0;
+          S.nb = 0;
+        }
+        __syncthreads();
+        const int len = (int)min((int64_t)kChunk, L - p);
+        stage_chunk<NT, MODE, ULIST, D == kBJ1>(A, I, s_load, p, len, stage_a, g == 0, s_items,
+                                                s_a, S, ls);
+        __syncthreads();
+        const int ns = S.ns, nb = S.nb;
+        const int ns_pad = (ns + 3) & ~3;
+        const int bstart = (kListTop - nb) & ~3;
+        if (tid < 4) {
+          if (ns + tid < ns_pad) {
+            s_items[ns + tid] = 0u;
+            if (stage_a) s_a[ns + tid] = 0.f;
+          }
+          if (ULIST && bstart + tid < kListTop - nb) {
+            s_items[bstart + tid] = 0u;
+            if (stage_a) s_a[bstart + tid] = 0.f;
+          }
+        }
+        __syncthreads();
+      }
+      if (!S.err) {
+        const int ns_pad = (S.ns + 3) & ~3;
+        const int bstart = (kListTop - S.nb) & ~3;
+        if (D == kMT) {
+          const int K = group_len(c - 1);  // terms u2 < c
+          uint64_t a64[T];
+#pragma unroll
+          for (int j = 0; j < T; ++j) a64[j] = 0;
+          mt_list<T, false>(s_items, 0, ns_pad, K, k0, a64);
+          mt_list<T, true>(s_items, bstart, kListTop, K, k0, a64);
+#pragma unroll
+          for (int j = 0; j < T; ++j) acc[j] += (int64_t)a64[j];
+        } else if (D == kRAD2) {
+          rad2_list<T, 1>(s_items, 0, ns_pad, k0, k1, n1, n2s);
+          rad2_list<T, -1>(s_items, bstart, kListTop, k0, k1, n1, n2b);
+        } else if (D == kFS1) {
+          if (fs1_fast) fs1_list<T>(s_items, 0, ns_pad, group_len(c), k0, Dc, c2, c, acc);
+          else fs1_list_wide<T>(s_items, 0, ns_pad, lam, c, acc);
+        } else if (D == kCCM1) {
+          const int K = group_len(c / 2);  // terms floor(u / l) <= c / 2
+          ccm1_list<T, 1>(s_items, 0, ns_pad, K, Dl, acc);
+          ccm1_list<T, -1>(s_items, bstart, kListTop, K, Dl, acc);
+        } else if (D == kVB2) {
+          const int K = group_len(c / 2 + 1);
+          if (vb2_magic) {
+            const uint32_t add2 = (uint32_t)(2 * c - 2);
+            vb2_list_magic<T, 1>(s_items, 0, ns_pad, K, k0, Dc, add2, acc);
+            vb2_list_magic<T, -1>(s_items, bstart, kListTop, K, k0, Dc, add2, acc);
+          } else if (stage_a) {
+            const uint32_t K2 = 0u - c2 * kF32RoundBits;
+            vb2_list_float<T, 1>(s_items, s_a, 0, ns_pad, K, k0, kf, c2, K2, acc);
+            vb2_list_float<T, -1>(s_items, s_a, bstart, kListTop, K, k0, kf, c2, K2, acc);
+          } else {
+            vb2_list_wide<T, 1>(s_items, 0, ns_pad, lam, c, acc);
+            vb2_list_wide<T, -1>(s_items, bstart, kListTop, lam, c, acc);
+          }
+        } else {  // BJ1
+          if (narrow) bj1_list<T>(s_items, 0, ns_pad, group_len(2 * c), Dl, k0, k1, acc);
+          else bj1_list_wide<T>(s_items, 0, ns_pad, lam, c, acc);
+        }
+      }
+      if (!one_chunk) __syncthreads();
+      if (L == 0) break;
+    }
+
+    // ---- instance sums (once, after the first pass over the stream) ------------
+    if (g == 0) {
+      if (tid < 6) S.sums[tid] = 0;
+      __syncthreads();
+#pragma unroll
+      for (int e = 0; e < 6; ++e) {
+        const long long x = warp_sum((long long)ls.v[e]);
+        if (lane_id() == 0 && x != 0)
+          atomicAdd((unsigned long long *)&S.sums[e], (unsigned long long)x);
+      }
+      __syncthreads();
+    }
+    if (S.err) break;
+    InstSums sums;
+    sums.n_small = S.sums[0];
+    sums.n_big = S.sums[1];
+    sums.n_half = S.sums[2];
+    sums.n_full = S.sums[3];
+    sums.sumw_big = S.sums[4];
+    sums.sumw = S.sums[5];
+
+    // ---- bounds of this group's parameters -----------------------------------------
+#pragma unroll
+    for (int j = 0; j < T; ++j) {
+      if (!valid[j]) continue;
+      const int64_t l = lam[j];
+      int64_t Ssum;
+      if (D == kMT) Ssum = mt_sum(sums, c, (uint64_t)acc[j]);
+      else if (D == kRAD2) Ssum = rad2_sum(sums, c, n1[j], n2s[j], n2b[j]);
+      else if (D == kFS1) Ssum = fs1_sum(acc[j]);
+      else if (D == kCCM1) Ssum = ccm1_sum(sums, c / l, acc[j]);
+      else if (D == kVB2) Ssum = vb2_sum(sums, l, acc[j]);
+      else Ssum = bj1_sum(sums, acc[j]);
+      const int64_t lb = ceil_div_i64(Ssum, dff_at_c(D, l, c));
+      if (DEBUG) {
+        req_out[req_idx] = lb;
+      } else {
+        const unsigned long long key = make_key(lb, gbase + (uint32_t)(l - lo_d));
+        best = key > best ? key : best;
       }
     }
   }
-  const Div31 Dc = div31_make((uint32_t)c);
-  const uint32_t c2 = (uint32_t)(2 * c);
-  const uint32_t vb2_add2 = (uint32_t)(2 * c - 2);
-  const uint32_t vb2_K2 = 0u - c2 * kF32RoundBits;
+  return best;
+}
 
-  uint64_t acc0[T], acc1[T];
-#pragma unroll
-  for (int j = 0; j < T; ++j) acc0[j] = acc1[j] = 0;
-  int64_t ls_small = 0, ls_big = 0, ls_half = 0, ls_full = 0, ls_sbig = 0, ls_sum = 0;
+// One tile: resolves its DFF and lambda range, computes the bin loads of a
+// search node, runs tile_dff, then folds the block's best key into the
+// instance slot; the last tile of the instance writes the outputs.
+template <int NT, int T, int G, int MODE>
+__device__ void process_tile(const EvalArgs &A, int64_t b, int64_t lt, int64_t ntiles,
+                             const InstView &I, uint32_t *s_items, float *s_a, uint32_t *s_load,
+                             TileShared &S) {
+  constexpr int64_t LPT = (int64_t)NT * T * G;
+  const int tid = threadIdx.x;
+  const int64_t c = I.c;
+  int d = 0;
+  int64_t rem = lt;
+  for (d = 0; d < kNumDff; ++d) {
+    const int64_t nt = (param_count(d, c) + LPT - 1) / LPT;
+    if (rem < nt) break;
+    rem -= nt;
+  }
+  int64_t lo_d, hi_d;
+  param_range(d, c, lo_d, hi_d);
+  const int64_t lam0 = lo_d + rem * LPT;
+  const int64_t lam_end = min(hi_d + 1, lam0 + LPT);
 
   if (tid == 0) S.err = 0;
-
-  // ---- node mode: bin loads of the partial packing -----------------------
   if (MODE == kSrcNodes) {
     for (int64_t j = tid; j < I.k; j += NT) s_load[j] = 0u;
     __syncthreads();
@@ -343,179 +533,23 @@ __device__ void process_tile(const EvalArgs &A, int64_t b, int64_t lt, int64_t n
   }
   __syncthreads();
 
-  const int64_t L = (MODE == kSrcNodes) ? I.n + I.k : I.n;
-  for (int64_t p = 0; p < L; p += kChunk) {
-    if (tid == 0) {
-      S.ns = 0;
-      S.nb = 0;
-    }
-    __syncthreads();
-    // ---- stage one chunk ---------------------------------------------------
-    for (int o = 0; o < kChunk; o += NT) {
-      const int64_t q = p + o + tid;
-      int64_t w = 0;
-      bool have = false;
-      if (q < L) have = fetch_item<MODE>(A, I, s_load, q, w);
-      if (have && (w < 0 || w > c)) {
-        S.err = 1;
-        have = false;
-      }
-      if (have && w == 0) have = false;
-      if (ulist) {
-        const bool full = have && w == c;
-        const bool small = have && !full && 2 * w < c;
-        const bool big = have && !full && 2 * w > c;
-        const bool half = have && 2 * w == c;
-        ls_full += full;
-        ls_half += half;
-        ls_small += small;
-        ls_big += big;
-        if (big) ls_sbig += w;
-        ls_sum += have ? w : 0;
-        const int ps = warp_append(small, &S.ns);
-        const int pb = warp_append(big, &S.nb);
-        if (small) {
-          s_items[ps] = (uint32_t)(2 * w);
-          if (stage_a) s_a[ps] = __fdiv_rn((float)w, (float)c);
-        }
-        if (big) {
-          const int slot = kListTop - 1 - pb;
-          s_items[slot] = (uint32_t)(2 * (c - w));
-          if (stage_a) s_a[slot] = __fdiv_rn((float)(c - w), (float)c);
-        }
-      } else {
-        ls_sum += have ? w : 0;
-        const int ps = warp_append(have, &S.ns);
-        if (have) s_items[ps] = (d == kBJ1) ? (uint32_t)(2 * w) : (uint32_t)w;
-      }
-    }
-    __syncthreads();
-    const int ns = S.ns, nb = S.nb;
-    const int ns_pad = (ns + 3) & ~3;
-    const int bstart = (kListTop - nb) & ~3;
-    if (tid < 4) {
-      if (ns + tid < ns_pad) {
-        s_items[ns + tid] = 0u;
-        if (stage_a) s_a[ns + tid] = 0.f;
-      }
-      if (ulist && bstart + tid < kListTop - nb) {
-        s_items[bstart + tid] = 0u;
-        if (stage_a) s_a[bstart + tid] = 0.f;
-      }
-    }
-    __syncthreads();
-    if (!S.err) {
-      // ---- evaluate the staged lists --------------------------------------
-      switch (d) {
-        case kMT: {
-          // terms u2 < c <= 2^30, so groups of >= 4 never overflow 32 bits
-          const int K = group_len(c - 1);
-          mt_list<T>(s_items, 0, ns_pad, K, p0, false, acc0);
-          mt_list<T>(s_items, bstart, kListTop, K, p0, true, acc1);
-          break;
-        }
-        case kRAD2:
-          rad2_list<T>(s_items, 0, ns_pad, p0, p1, acc0);
-          rad2_list<T>(s_items, bstart, kListTop, p0, p1, acc1);
-          break;
-        case kFS1:
-          if (fs1_fast) {
-            fs1_list<T>(s_items, 0, ns_pad, group_len(c), p0, Dc, c2, acc0, acc1);
-          } else {
-            fs1_list_wide<T>(s_items, 0, ns_pad, lam, c, acc0, acc1);
-          }
-          break;
-        case kCCM1: {
-          // terms floor(u / l) <= c / 2 <= 2^29: groups of >= 8 items
-          const int K = group_len(c / 2);
-          ccm1_list<T>(s_items, 0, ns_pad, K, Dl, acc0);
-          ccm1_list<T>(s_items, bstart, kListTop, K, Dl, acc1);
-          break;
-        }
-        case kVB2:
-          if (vb2_magic) {
-            const int K = group_len(c / 2 + 1);
-            vb2_list_magic<T>(s_items, 0, ns_pad, K, p0, Dc, vb2_add2, acc0);
-            vb2_list_magic<T>(s_items, bstart, kListTop, K, p0, Dc, vb2_add2, acc1);
-          } else if (vb2_float) {
-            const int K = group_len(c / 2 + 1);
-            vb2_list_float<T>(s_items, s_a, 0, ns_pad, K, p0, pf, c2, vb2_K2, acc0);
-            vb2_list_float<T>(s_items, s_a, bstart, kListTop, K, p0, pf, c2, vb2_K2, acc1);
-          } else {
-            vb2_list_wide<T>(s_items, 0, ns_pad, lam, c, acc0);
-            vb2_list_wide<T>(s_items, bstart, kListTop, lam, c, acc1);
-          }
-          break;
-        default:  // BJ1
-          if (narrow) {
-            bj1_list<T>(s_items, 0, ns_pad, group_len(2 * c), Dl, p0, p1, acc0, acc1);
-          } else {
-            bj1_list_wide<T>(s_items, 0, ns_pad, lam, c, acc0, acc1);
-          }
-      }
-    }
-    __syncthreads();
+  unsigned long long best;
+  switch (d) {
+    case kMT: best = tile_dff<NT, T, kMT, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S); break;
+    case kRAD2: best = tile_dff<NT, T, kRAD2, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S); break;
+    case kFS1: best = tile_dff<NT, T, kFS1, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S); break;
+    case kCCM1: best = tile_dff<NT, T, kCCM1, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S); break;
+    case kVB2: best = tile_dff<NT, T, kVB2, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S); break;
+    default: best = tile_dff<NT, T, kBJ1, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S); break;
   }
-
-  // ---- instance constants: block sums -------------------------------------
-  if (tid < 6) S.sums[tid] = 0;
-  __syncthreads();
-  {
-    long long v[6] = {ls_small, ls_big, ls_half, ls_full, ls_sbig, ls_sum};
-#pragma unroll
-    for (int e = 0; e < 6; ++e) {
-      const long long x = warp_sum(v[e]);
-      if (lane_id() == 0 && x != 0) atomicAdd((unsigned long long *)&S.sums[e], (unsigned long long)x);
-    }
-  }
-  __syncthreads();
-  InstSums sums;
-  sums.n_small = S.sums[0];
-  sums.n_big = S.sums[1];
-  sums.n_half = S.sums[2];
-  sums.n_full = S.sums[3];
-  sums.sumw_big = S.sums[4];
-  sums.sumw = S.sums[5];
   const bool err = S.err != 0;
-
-  // ---- bounds, keys, block max ---------------------------------------------
-  unsigned long long best = 0ull;
-  if (!err) {
-    const uint32_t g0 = flat_index(d, lo_d, c);
-#pragma unroll
-    for (int j = 0; j < T; ++j) {
-      if (!valid[j]) continue;
-      const int64_t l = lam[j];
-      int64_t Ssum;
-      switch (d) {
-        case kMT: Ssum = mt_sum(sums, c, acc0[j], acc1[j]); break;
-        case kRAD2:
-          Ssum = rad2_sum(sums, c, (int64_t)(acc0[j] & 0xFFFFFFFFull), (int64_t)(acc0[j] >> 32),
-                          (int64_t)(acc1[j] & 0xFFFFFFFFull), (int64_t)(acc1[j] >> 32));
-          break;
-        case kFS1: Ssum = fs1_sum(c, acc0[j], acc1[j]); break;
-        case kCCM1: Ssum = ccm1_sum(sums, c / l, acc0[j], acc1[j]); break;
-        case kVB2: Ssum = vb2_sum(sums, l, acc0[j], acc1[j]); break;
-        default: Ssum = bj1_sum(sums, c % l, acc0[j], acc1[j]);
-      }
-      const int64_t den = dff_at_c(d, l, c);
-      const int64_t lb = ceil_div_i64(Ssum, den);
-      if (req_d >= 0) {
-        req_out[(int64_t)blockIdx.x * NT + tid] = lb;
-      } else {
-        const unsigned long long key = make_key(lb, g0 + (uint32_t)(l - lo_d));
-        best = key > best ? key : best;
-      }
-    }
-  }
-  if (req_d >= 0) return;
   best = warp_max_u64(best);
   if (lane_id() == 0) S.warp_key[tid >> 5] = best;
   __syncthreads();
   if (tid == 0) {
     unsigned long long m = 0ull;
     for (int w = 0; w < NT / 32; ++w) m = S.warp_key[w] > m ? S.warp_key[w] : m;
-    if (m) atomicMax(&A.keys[b], m);
+    if (m && !err) atomicMax(&A.keys[b], m);
     __threadfence();
     const unsigned int ticket = atomicAdd(&A.done[b], 1u);
     if ((int64_t)ticket == ntiles - 1) {
@@ -562,8 +596,8 @@ __device__ __forceinline__ InstView resolve_instance(const EvalArgs &A, int64_t 
   return I;
 }
 
-template <int NT, int T, int MODE>
-__global__ void __launch_bounds__(NT) eval_kernel(EvalArgs A) {
+template <int NT, int T, int G, int MODE, int MINB>
+__global__ void __launch_bounds__(NT, MINB) eval_kernel(EvalArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ TileShared S;
   __shared__ long long s_tile;
@@ -598,7 +632,7 @@ __global__ void __launch_bounds__(NT) eval_kernel(EvalArgs A) {
     const int64_t t0 = A.tile_start ? A.tile_start[b] : 0;
     const int64_t nt = A.tile_start ? A.tile_start[b + 1] - t0 : A.single_tiles;
     const InstView I = resolve_instance<MODE>(A, b);
-    process_tile<NT, T, MODE>(A, b, t - t0, nt, I, s_items, s_a, s_load, S);
+    process_tile<NT, T, G, MODE>(A, b, t - t0, nt, I, s_items, s_a, s_load, S);
     if (!A.work) break;
     if (threadIdx.x == 0) s_tile = (long long)atomicAdd(A.work, 1ull);
     __syncthreads();
@@ -606,7 +640,8 @@ __global__ void __launch_bounds__(NT) eval_kernel(EvalArgs A) {
   }
 }
 
-// Per-(DFF, lambda) bounds of one instance: grid (ceil(m / NT), 6).
+// Per-(DFF, lambda) bounds of one instance: grid (ceil(m / NT), 6); block
+// (x, d) serves the requests of its index range that name DFF d.
 template <int NT>
 __global__ void __launch_bounds__(NT)
     debug_kernel(EvalArgs A, const int32_t *req_dff, const int64_t *req_lam, int64_t m,
@@ -616,8 +651,31 @@ __global__ void __launch_bounds__(NT)
   uint32_t *s_items = reinterpret_cast<uint32_t *>(smem_raw);
   float *s_a = reinterpret_cast<float *>(smem_raw + sizeof(uint32_t) * kListTop);
   const InstView I = resolve_instance<kSrcRaggedI32>(A, 0);
-  process_tile<NT, 1, kSrcRaggedI32>(A, 0, 0, 1, I, s_items, s_a, nullptr, S, req_dff, req_lam, m,
-                                     req_out, (int)blockIdx.y);
+  const int d = blockIdx.y;
+  const int64_t r = (int64_t)blockIdx.x * NT + threadIdx.x;
+  int64_t idx = -1;
+  if (r < m) {
+    const int32_t rd = req_dff[r];
+    if (d == 0 && (rd < 0 || rd >= kNumDff)) req_out[r] = -BP_ERANGE;
+    if (rd == d) {
+      int64_t lo, hi;
+      param_range(d, I.c, lo, hi);
+      const int64_t l = req_lam[r];
+      if (l < lo || l > hi) req_out[r] = -BP_ERANGE;
+      else idx = r;
+    }
+  }
+  if (threadIdx.x == 0) S.err = 0;
+  __syncthreads();
+  switch (d) {
+    case kMT: tile_dff<NT, 1, kMT, kSrcRaggedI32, true>(A, I, 0, 0, s_items, s_a, nullptr, S, req_lam, req_out, idx); break;
+    case kRAD2: tile_dff<NT, 1, kRAD2, kSrcRaggedI32, true>(A, I, 0, 0, s_items, s_a, nullptr, S, req_lam, req_out, idx); break;
+    case kFS1: tile_dff<NT, 1, kFS1, kSrcRaggedI32, true>(A, I, 0, 0, s_items, s_a, nullptr, S, req_lam, req_out, idx); break;
+    case kCCM1: tile_dff<NT, 1, kCCM1, kSrcRaggedI32, true>(A, I, 0, 0, s_items, s_a, nullptr, S, req_lam, req_out, idx); break;
+    case kVB2: tile_dff<NT, 1, kVB2, kSrcRaggedI32, true>(A, I, 0, 0, s_items, s_a, nullptr, S, req_lam, req_out, idx); break;
+    default: tile_dff<NT, 1, kBJ1, kSrcRaggedI32, true>(A, I, 0, 0, s_items, s_a, nullptr, S, req_lam, req_out, idx); break;
+  }
+  if (S.err && idx >= 0) req_out[idx] = -BP_ERANGE;  // a size outside [0, c]
 }
 
 // ---------------------------------------------------------------------------

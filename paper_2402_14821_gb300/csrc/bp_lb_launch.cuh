@@ -1,0 +1,62 @@
+// bp_lb_launch.cuh -- the table of compiled launch shapes of eval_kernel.
+//
+// Each shape is (NT threads per CTA, T parameters per thread per group, G
+// groups per tile, MINB resident CTAs per SM -- which caps registers at
+// 65536 / (NT * MINB)).  Every shape is instantiated for the three input modes
+// in its own translation unit (bp_lb_inst_<mode>.cu) and picked at run time
+// per handle, by default or by the autotuner.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "bp_lb_kernels.cuh"
+
+namespace bplb {
+
+struct LaunchShape {
+  int nt, t, g, minb;
+};
+
+constexpr int kNumShapes = 4;
+constexpr LaunchShape kShapes[kNumShapes] = {
+    {256, 4, 2, 3},  // 0: default
+    {256, 2, 4, 4},  // 1: fewer registers, more resident warps
+    {128, 4, 2, 6},  // 2: smaller CTAs
+    {256, 4, 4, 3},  // 3: longer tiles (less staging per parameter)
+};
+
+constexpr int64_t shape_lpt(int s) { return (int64_t)kShapes[s].nt * kShapes[s].t * kShapes[s].g; }
+
+using EvalFn = void (*)(EvalArgs);
+
+// Host stubs of the instantiated kernels, one table per input mode.
+EvalFn eval_fn_ragged_i32(int shape);
+EvalFn eval_fn_ragged_i64(int shape);
+EvalFn eval_fn_nodes(int shape);
+
+inline EvalFn eval_fn(int shape, int mode) {
+  switch (mode) {
+    case kSrcRaggedI32: return eval_fn_ragged_i32(shape);
+    case kSrcRaggedI64: return eval_fn_ragged_i64(shape);
+    default: return eval_fn_nodes(shape);
+  }
+}
+
+}  // namespace bplb
+
+// Instantiates every shape of one mode (used once per translation unit).
+#define BPLB_INSTANTIATE_MODE(NAME, MODE)                                          \
+  namespace bplb {                                                                 \
+  EvalFn NAME(int shape) {                                                         \
+    switch (shape) {                                                               \
+      case 0: return eval_kernel<kShapes[0].nt, kShapes[0].t, kShapes[0].g, MODE,  \
+                                 kShapes[0].minb>;                                 \
+      case 1: return eval_kernel<kShapes[1].nt, kShapes[1].t, kShapes[1].g, MODE,  \
+                                 kShapes[1].minb>;                                 \
+      case 2: return eval_kernel<kShapes[2].nt, kShapes[2].t, kShapes[2].g, MODE,  \
+                                 kShapes[2].minb>;                                 \
+      default: return eval_kernel<kShapes[3].nt, kShapes[3].t, kShapes[3].g, MODE, \
+                                  kShapes[3].minb>;                                \
+    }                                                                              \
+  }                                                                                \
+  }

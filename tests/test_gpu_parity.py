@@ -313,3 +313,42 @@ def test_reduce_nodes_exact(cudalib, handle, orc):
         want = orc.reduce(w, a, k, c)
         assert cnt[j] == len(want), j
         assert np.array_equal(sz[out_off[j]:out_off[j] + cnt[j]], want), j
+
+
+# ---------------------------------------------------------------------------
+# every compiled launch shape, and the autotuner
+# ---------------------------------------------------------------------------
+def test_every_launch_shape_is_exact(cudalib, orc):
+    rng = np.random.default_rng(11)
+    rg = random_ragged(rng, 120, 1, 5000, 300)
+    rg.sizes = rg.sizes.astype(np.int64)
+    want = oracle_batch(orc, rg)
+    nd = I.ragged_nodes(seed=12, count=60, n_lo=1, n_hi=2600, caps=(150, 1000, 9000))
+    want_nodes = tuple(np.array(x) for x in zip(*[oracle_node(orc, nd, j) for j in range(nd.count)]))
+    h = cudalib.bp_lb_create(150, 4096)
+    try:
+        for shape in range(cudalib.bp_lb_num_launch_shapes()):
+            for mode in (cudalib.MODE_RAGGED_I32, cudalib.MODE_RAGGED_I64, cudalib.MODE_NODES):
+                cudalib.bp_lb_set_launch_shape(h, mode, shape)
+            assert_same(run_batch(cudalib, h, rg), want, f"shape {shape} i32")
+            assert_same(run_batch(cudalib, h, rg, i64=True), want, f"shape {shape} i64")
+            assert_same(run_nodes(cudalib, h, nd), want_nodes, f"shape {shape} nodes")
+            w = rg.instance(3)
+            assert cudalib.bp_lb_eval(h, w[w <= 150], 7)[0] == orc.lb(w[w <= 150], 150, 7)[0]
+    finally:
+        cudalib.bp_lb_destroy(h)
+
+
+def test_autotune_nodes(cudalib, handle, orc):
+    import torch
+    nd = I.search_nodes(nodes=256)
+    t = node_tensors(nd)
+    out_b = torch.empty(nd.count, dtype=torch.int64, device="cuda")
+    out_a = cudalib.argmax_tensor(nd.count)
+    best, ms = cudalib.bp_lb_autotune_nodes(handle, max_bins=int(nd.bins.max()), out_bound=out_b,
+                                            out_argmax=out_a, reps=2, **t)
+    assert 0 <= best < cudalib.bp_lb_num_launch_shapes()
+    assert all(x > 0 for x in ms) and ms[best] == min(ms)
+    assert cudalib.bp_lb_get_launch_shape(handle, cudalib.MODE_NODES) == best
+    for j in (0, 100, 255):
+        assert (int(out_b[j]),) == (oracle_node(orc, nd, j)[0],)
