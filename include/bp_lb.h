@@ -203,6 +203,38 @@ int bp_lb_reduce_nodes(bp_lb_t *h, int32_t B, int32_t num_base,
                        int32_t *d_out_sizes, int64_t *d_out_count,
                        void *stream);
 
+/* ---- batched path without a handle and without allocation ---------------- */
+
+/* Largest B bp_lb_eval_batch_noalloc accepts. */
+#define BP_NOALLOC_MAX_BATCH 4096
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory where they check: code whose device
+ * memory belongs to another allocator (e.g. a framework pool that reserved
+ * the whole device), search loops that must not take the device-wide
+ * synchronisation of cudaFree between their own kernels, and solvers with a
+ * device-memory budget fixed at start-up.  It computes exactly what
+ * bp_lb_eval_batch computes, with the same arguments and per-instance error
+ * convention, but needs no handle and calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *   Its scratch (tile table, result slots, counters: about 82 KB) is one
+ *   fixed __device__ array in the library, held by every GPU that loads the
+ *   library until the process exits.
+ *   The first call on a device looks up that array's device address
+ *   (cudaGetSymbolAddress) with the device current; make that first call
+ *   before any stream capture on the device.
+ *   All calls share the one array: calls whose work overlaps on the GPU (on
+ *   different streams, or from different host threads) race and give wrong
+ *   results; order them on one stream.  Each call clears the parts it uses.
+ *   It always uses launch shape 0 (no autotuning: that needs a handle).
+ * Errors: BP_EINVAL (NULL required pointer, B < 0), BP_ERANGE
+ * (B > BP_NOALLOC_MAX_BATCH, checked before any launch), BP_ECUDA. */
+int bp_lb_eval_batch_noalloc(int32_t B, const int64_t *d_offsets,
+                             const int32_t *d_sizes, const int64_t *d_capacity,
+                             const int64_t *d_bins, int64_t *d_out_bound,
+                             bp_argmax_t *d_out_argmax,
+                             uint8_t *d_out_feasible, void *stream);
+
 /* ---- launch shapes and autotuning ---------------------------------------- */
 
 /* Input modes of the evaluation kernel, for the launch-shape calls below. */

@@ -66,6 +66,7 @@ def _bind(lib):
                                                 _vp]),
         "bp_lb_selfcheck_division": (_c_i64, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                               _c_i64]),
+        "bp_lb_eval_batch_noalloc": (ctypes.c_int, [_c_i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -90,7 +91,9 @@ EXPORTED = ("bp_lb_strerror", "bp_lb_create", "bp_lb_destroy", "bp_lb_reserve", 
             "bp_lb_reduce_nodes", "bp_lb_debug_params", "bp_lb_param_count",
             "bp_lb_selfcheck_division", "bp_lb_num_launch_shapes", "bp_lb_launch_shape_info",
             "bp_lb_set_launch_shape", "bp_lb_get_launch_shape", "bp_lb_autotune_batch",
-            "bp_lb_autotune_nodes")
+            "bp_lb_autotune_nodes", "bp_lb_eval_batch_noalloc")
+
+NOALLOC_MAX_BATCH = 4096
 
 MODE_RAGGED_I32, MODE_RAGGED_I64, MODE_NODES = 0, 1, 2
 
@@ -191,6 +194,20 @@ def bp_lb_eval_batch(h, offsets, sizes, capacity, bins, out_bound, out_argmax=No
               _ptr(capacity, torch.int64, "capacity"), _ptr(bins, torch.int64, "bins"),
               _ptr(out_bound, torch.int64, "out_bound"), _ptr(out_argmax, torch.int64, "out_argmax"),
               _ptr(out_feasible, torch.uint8, "out_feasible"), _stream(stream)), "bp_lb_eval_batch")
+
+
+def bp_lb_eval_batch_noalloc(offsets, sizes, capacity, bins, out_bound, out_argmax=None,
+                             out_feasible=None, stream=None):
+    """bp_lb_eval_batch without a handle and without any device allocation (for
+    callers that cannot allocate where they check); at most NOALLOC_MAX_BATCH
+    instances; calls that overlap on the GPU race (they share fixed scratch)."""
+    import torch
+    _check(lib().bp_lb_eval_batch_noalloc(
+        offsets.numel() - 1, _ptr(offsets, torch.int64, "offsets"), _ptr(sizes, torch.int32, "sizes"),
+        _ptr(capacity, torch.int64, "capacity"), _ptr(bins, torch.int64, "bins"),
+        _ptr(out_bound, torch.int64, "out_bound"), _ptr(out_argmax, torch.int64, "out_argmax"),
+        _ptr(out_feasible, torch.uint8, "out_feasible"), _stream(stream)),
+        "bp_lb_eval_batch_noalloc")
 
 
 def bp_lb_eval_batch_i64(h, offsets, sizes, capacity, bins, out_bound, out_argmax=None,
