@@ -39,10 +39,18 @@ WORKLOAD = "search-node batch: {} partial packings of n=500 items, sizes U[1,c/2
 NODES, N_ITEMS, CAP = 4096, 500, 10_000
 
 # Integer operations per (item, parameter) pair in the kernel's formulation of
-# each DFF (compare/select/add for MT and RAD2; multiply-high division for the
-# others); see the evaluators in csrc/bp_lb_eval.cuh.
-OPS_PER_EVAL = {0: 2, 1: 4, 2: 7, 3: 3, 4: 4, 5: 6}
-OPS_PER_EVAL_VB2_FLOAT = 5
+# each DFF, counted from the source expressions of csrc/bp_lb_eval.cuh:
+#   MT   compare + conditional add                                   2
+#   RAD2 two compares + two counts                                   4
+#   FS1  mul, mul-high, shift, add, mul, compare, conditional add    7
+#   CCM1 one multiply-high-add (c <= 131071)                         1   (else 3)
+#   VB2  mul-add, mul-high, shift, add (c <= 65535)                  4   (fp32 path 5)
+#   BJ1  mul-high, two mul-adds, min, add (c <= 65535)               5   (else 6)
+def ops_per_eval(d, c):
+    return {0: 2, 1: 4, 2: 7,
+            3: 1 if c <= 131071 else 3,
+            4: 4 if c <= 65535 else 5,
+            5: 5 if c <= 65535 else 6}[d]
 SM_COUNT_NOMINAL = 152
 
 
@@ -68,11 +76,8 @@ def algorithmic_work(nd):
         c = int(nd.base.capacity[nd.node_base[j]])
         cnt = param_counts(c)
         for d in range(6):
-            per = OPS_PER_EVAL[d]
-            if d == 4 and c > 65535:
-                per = OPS_PER_EVAL_VB2_FLOAT
             evals += int(r[j]) * cnt[d]
-            ops += int(r[j]) * cnt[d] * per
+            ops += int(r[j]) * cnt[d] * ops_per_eval(d, c)
     return evals, ops
 
 

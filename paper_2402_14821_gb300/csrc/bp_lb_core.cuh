@@ -43,6 +43,8 @@ constexpr int64_t kNarrowCap = int64_t(1) << 28;   // 32-bit partial sums, all D
 constexpr int64_t kVb2MagicCap = 65535;            // 2(u*l + c - 1) < 2^32
 constexpr int64_t kVb2FloatCap = int64_t(1) << 22; // fp32 quotient estimate exact
 constexpr int64_t kFs1FastCap = 21262214;          // 101 * c < 2^31
+constexpr int64_t kCcm1NoShiftCap = 131071;        // u e < (c/2)^2 < 2^32
+constexpr int64_t kBj1NoShiftCap = 65535;          // w e < c^2 < 2^32
 
 // ---------------------------------------------------------------------------
 // Parameter ranges (Sec. 3.1, integer lambda):
@@ -103,6 +105,16 @@ BPLB_HD Div31 div31_make(uint32_t d) {
   const uint64_t num = uint64_t(1) << (31 + r.l);
   r.m = (uint32_t)((num + d - 1) / d);
   return r;
+}
+
+// Division without the final shift, for small numerators: with
+// m1 = ceil(2^32 / d) (d >= 2) and e = m1 d - 2^32 < d,
+//   n m1 / 2^32 = n / d + n e / (d 2^32),
+// so floor(n m1 / 2^32) = floor(n / d) whenever n e < 2^32, in particular
+// whenever n d < 2^32.  For d = 1 the magic 2^32 does not fit; m1 = 2^32 - 1
+// then gives n - 1 for n >= 1 (and 0 for n = 0), which callers correct.
+BPLB_HD uint32_t div_noshift_make(uint32_t d) {
+  return d <= 1 ? 0xFFFFFFFFu : (uint32_t)(((uint64_t(1) << 32) + d - 1) / d);
 }
 
 // floor(n / d) given n2 = 2n (n < 2^31).

@@ -46,11 +46,15 @@ BPLB_D void mt_list(const uint32_t *s, int beg, int end, int K, const uint32_t (
 #pragma unroll
       for (int j = 0; j < T; ++j) {
         if (!BIG) {
-          a[j] += (v.x >= thr[j] ? v.x : 0u) + (v.y >= thr[j] ? v.y : 0u);
-          a[j] += (v.z >= thr[j] ? v.z : 0u) + (v.w >= thr[j] ? v.w : 0u);
+          if (v.x >= thr[j]) a[j] += v.x;
+          if (v.y >= thr[j]) a[j] += v.y;
+          if (v.z >= thr[j]) a[j] += v.z;
+          if (v.w >= thr[j]) a[j] += v.w;
         } else {
-          a[j] += (v.x < thr[j] ? v.x : 0u) + (v.y < thr[j] ? v.y : 0u);
-          a[j] += (v.z < thr[j] ? v.z : 0u) + (v.w < thr[j] ? v.w : 0u);
+          if (v.x < thr[j]) a[j] += v.x;
+          if (v.y < thr[j]) a[j] += v.y;
+          if (v.z < thr[j]) a[j] += v.z;
+          if (v.w < thr[j]) a[j] += v.w;
         }
       }
     }
@@ -104,7 +108,7 @@ BPLB_D void fs1_list(const uint32_t *s, int beg, int end, int K, const uint32_t 
 }
 
 template <int T>
-BPLB_D void fs1_list_wide(const uint32_t *s, int beg, int end, const int64_t (&lam)[T], int64_t c,
+__device__ __noinline__ void fs1_list_wide(const uint32_t *s, int beg, int end, const int64_t (&lam)[T], int64_t c,
                           int64_t (&acc)[T]) {
   for (int i = beg; i < end; ++i) {
     const int64_t w = s[i];
@@ -131,6 +135,39 @@ BPLB_D void ccm1_list(const uint32_t *s, int beg, int end, int K, const Div31 (&
       for (int j = 0; j < T; ++j) {
         a[j] += div31(v.x, D[j]) + div31(v.y, D[j]);
         a[j] += div31(v.z, D[j]) + div31(v.w, D[j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < T; ++j) acc[j] += SIGN * (int64_t)a[j];
+  }
+}
+
+// mad.hi.u32: hi32(a * b) + c in one integer multiply-add (FMA pipe).
+BPLB_D uint32_t mad_hi(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+
+// c <= 131071, list holds u (not 2u): acc += SIGN * floor(u / l) with one
+// multiply-high-add per item (no shift; u * l < 2^32).  For l = 1 each nonzero
+// item yields u - 1: the caller adds the item count back.
+template <int T, int SIGN>
+BPLB_D void ccm1_list_noshift(const uint32_t *s, int beg, int end, int K, const uint32_t (&m1)[T],
+                              int64_t (&acc)[T]) {
+  for (int g0 = beg; g0 < end; g0 += K) {
+    const int g1 = min(end, g0 + K);
+    uint32_t a[T];
+#pragma unroll
+    for (int j = 0; j < T; ++j) a[j] = 0;
+    for (int i = g0; i < g1; i += 4) {
+      const uint4 v = lds4(s, i);
+#pragma unroll
+      for (int j = 0; j < T; ++j) {
+        a[j] = mad_hi(v.x, m1[j], a[j]);
+        a[j] = mad_hi(v.y, m1[j], a[j]);
+        a[j] = mad_hi(v.z, m1[j], a[j]);
+        a[j] = mad_hi(v.w, m1[j], a[j]);
       }
     }
 #pragma unroll
@@ -205,7 +242,7 @@ BPLB_D void vb2_list_float(const uint32_t *s, const float *sa, int beg, int end,
 }
 
 template <int T, int SIGN>
-BPLB_D void vb2_list_wide(const uint32_t *s, int beg, int end, const int64_t (&lam)[T], int64_t c,
+__device__ __noinline__ void vb2_list_wide(const uint32_t *s, int beg, int end, const int64_t (&lam)[T], int64_t c,
                           int64_t (&acc)[T]) {
   for (int i = beg; i < end; ++i) {
     const int64_t u = s[i] >> 1;
@@ -243,8 +280,39 @@ BPLB_D void bj1_list(const uint32_t *s, int beg, int end, int K, const Div31 (&D
   }
 }
 
+// c <= 65535, list holds raw w: with q = floor(w / l) (multiply-high, no
+// shift; w * l < 2^32) and cm = c mod l,
+//   cm q + min(w mod l, cm) = min(w - (l - cm) q, cm (q + 1)),
+// two multiply-adds and a min per item.  For l = 1, cm = 0 and the term is
+// min(., 0) = 0 whatever q is, as it must be.
 template <int T>
-BPLB_D void bj1_list_wide(const uint32_t *s, int beg, int end, const int64_t (&lam)[T], int64_t c,
+BPLB_D void bj1_list_noshift(const uint32_t *s, int beg, int end, int K, const uint32_t (&m1)[T],
+                             const uint32_t (&lmc)[T], const uint32_t (&cm)[T],
+                             int64_t (&acc)[T]) {
+  for (int g0 = beg; g0 < end; g0 += K) {
+    const int g1 = min(end, g0 + K);
+    uint32_t a[T];
+#pragma unroll
+    for (int j = 0; j < T; ++j) a[j] = 0;
+    for (int i = g0; i < g1; i += 4) {
+      const uint4 v = lds4(s, i);
+      const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+#pragma unroll
+        for (int j = 0; j < T; ++j) {
+          const uint32_t q = __umulhi(w4[e], m1[j]);
+          a[j] += min(w4[e] - lmc[j] * q, cm[j] * q + cm[j]);
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < T; ++j) acc[j] += (int64_t)a[j];
+  }
+}
+
+template <int T>
+__device__ __noinline__ void bj1_list_wide(const uint32_t *s, int beg, int end, const int64_t (&lam)[T], int64_t c,
                           int64_t (&acc)[T]) {
   for (int i = beg; i < end; ++i) {
     const int64_t w = s[i] >> 1;

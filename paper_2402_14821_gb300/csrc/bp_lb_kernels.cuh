@@ -240,13 +240,14 @@ struct LocalSums {
 };
 
 // Stages stream positions [p, p + len) into the shared lists:
-//   ULIST: small items as 2w from index 0 up, big items as 2(c - w) from
-//          kListTop - 1 down (plus fl(u / c) in s_a when stage_a);
-//   else:  every nonzero item as w (or 2w when WDOUBLE) from index 0 up.
-// Sizes outside [0, c] set S.err.  COUNT adds the instance sums.
-template <int NT, int MODE, bool ULIST, bool WDOUBLE>
+//   ULIST: small items as u = w from index 0 up, big items as u = c - w from
+//          kListTop - 1 down, each stored as u << shift (plus fl(u / c) in
+//          s_a when stage_a);
+//   else:  every nonzero item as w << shift from index 0 up.
+// Sizes outside [0, c] set S.err.  `count` adds the instance sums.
+template <int NT, int MODE, bool ULIST>
 __device__ __forceinline__ void stage_chunk(const EvalArgs &A, const InstView &I, const uint32_t *s_load,
-                                            int64_t p, int len, bool stage_a, bool count,
+                                            int64_t p, int len, bool stage_a, bool count, int shift,
                                             uint32_t *s_items, float *s_a, TileShared &S,
                                             LocalSums &ls) {
   const int64_t c = I.c;
@@ -275,17 +276,17 @@ __device__ __forceinline__ void stage_chunk(const EvalArgs &A, const InstView &I
       const int ps = warp_append(small, &S.ns);
       const int pb = warp_append(big, &S.nb);
       if (small) {
-        s_items[ps] = (uint32_t)(2 * w);
+        s_items[ps] = (uint32_t)w << shift;
         if (stage_a) s_a[ps] = __fdiv_rn((float)w, (float)c);
       }
       if (big) {
         const int slot = kListTop - 1 - pb;
-        s_items[slot] = (uint32_t)(2 * (c - w));
+        s_items[slot] = (uint32_t)(c - w) << shift;
         if (stage_a) s_a[slot] = __fdiv_rn((float)(c - w), (float)c);
       }
     } else {
       const int ps = warp_append(have, &S.ns);
-      if (have) s_items[ps] = WDOUBLE ? (uint32_t)(2 * w) : (uint32_t)w;
+      if (have) s_items[ps] = (uint32_t)w << shift;
     }
   }
 }
@@ -312,6 +313,11 @@ __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int
   const bool stage_a = (D == kVB2) && !vb2_magic && c <= kVb2FloatCap;
   const bool narrow = c <= kNarrowCap;  // BJ1: terms < 2c stay below 2^30
   const bool fs1_fast = c <= kFs1FastCap;
+  const bool ccm1_noshift = c <= kCcm1NoShiftCap;
+  const bool bj1_noshift = c <= kBj1NoShiftCap;
+  // stored value: u or w itself where the kernel divides it without a shift
+  // (or compares it to raw thresholds), else doubled
+  const int shift = (D == kFS1 || (D == kCCM1 && ccm1_noshift) || (D == kBJ1 && bj1_noshift)) ? 0 : 1;
   const Div31 Dc = div31_make((uint32_t)c);
   const uint32_t c2 = (uint32_t)(2 * c);
 
@@ -355,15 +361,22 @@ __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int
       } else if (D == kFS1) {
         k0[j] = 2u * l32 + 2u;
       } else if (D == kCCM1) {
-        Dl[j] = div31_make(l32);
+        if (ccm1_noshift) k0[j] = div_noshift_make(l32);
+        else Dl[j] = div31_make(l32);
       } else if (D == kVB2) {
         k0[j] = l32;
         kf[j] = (float)l32;
       } else {  // BJ1
         Dl[j] = div31_make(l32);
-        k0[j] = 2u * l32;
-        const uint32_t q = div31(c2, Dl[j]);       // floor(c / l)
-        k1[j] = 2u * ((uint32_t)c - q * l32);      // 2 (c mod l)
+        const uint32_t cm = (uint32_t)c - div31(c2, Dl[j]) * l32;  // c mod l
+        if (bj1_noshift) {
+          k0[j] = div_noshift_make(l32);
+          k1[j] = l32 - cm;
+          k2[j] = cm;
+        } else {
+          k0[j] = 2u * l32;
+          k1[j] = 2u * cm;
+        }
       }
     }
     int64_t acc[T];
@@ -386,8 +399,8 @@ __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int
         }
         __syncthreads();
         const int len = (int)min((int64_t)kChunk, L - p);
-        stage_chunk<NT, MODE, ULIST, D == kBJ1>(A, I, s_load, p, len, stage_a, g == 0, s_items,
-                                                s_a, S, ls);
+        stage_chunk<NT, MODE, ULIST>(A, I, s_load, p, len, stage_a, g == 0, shift, s_items, s_a,
+                                     S, ls);
         __syncthreads();
         const int ns = S.ns, nb = S.nb;
         const int ns_pad = (ns + 3) & ~3;
@@ -424,8 +437,13 @@ __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int
           else fs1_list_wide<T>(s_items, 0, ns_pad, lam, c, acc);
         } else if (D == kCCM1) {
           const int K = group_len(c / 2);  // terms floor(u / l) <= c / 2
-          ccm1_list<T, 1>(s_items, 0, ns_pad, K, Dl, acc);
-          ccm1_list<T, -1>(s_items, bstart, kListTop, K, Dl, acc);
+          if (ccm1_noshift) {
+            ccm1_list_noshift<T, 1>(s_items, 0, ns_pad, K, k0, acc);
+            ccm1_list_noshift<T, -1>(s_items, bstart, kListTop, K, k0, acc);
+          } else {
+            ccm1_list<T, 1>(s_items, 0, ns_pad, K, Dl, acc);
+            ccm1_list<T, -1>(s_items, bstart, kListTop, K, Dl, acc);
+          }
         } else if (D == kVB2) {
           const int K = group_len(c / 2 + 1);
           if (vb2_magic) {
@@ -441,7 +459,8 @@ __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int
             vb2_list_wide<T, -1>(s_items, bstart, kListTop, lam, c, acc);
           }
         } else {  // BJ1
-          if (narrow) bj1_list<T>(s_items, 0, ns_pad, group_len(2 * c), Dl, k0, k1, acc);
+          if (bj1_noshift) bj1_list_noshift<T>(s_items, 0, ns_pad, group_len(c), k0, k1, k2, acc);
+          else if (narrow) bj1_list<T>(s_items, 0, ns_pad, group_len(2 * c), Dl, k0, k1, acc);
           else bj1_list_wide<T>(s_items, 0, ns_pad, lam, c, acc);
         }
       }
@@ -479,7 +498,9 @@ __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int
       if (D == kMT) Ssum = mt_sum(sums, c, (uint64_t)acc[j]);
       else if (D == kRAD2) Ssum = rad2_sum(sums, c, n1[j], n2s[j], n2b[j]);
       else if (D == kFS1) Ssum = fs1_sum(acc[j]);
-      else if (D == kCCM1) Ssum = ccm1_sum(sums, c / l, acc[j]);
+      else if (D == kCCM1)
+        Ssum = ccm1_sum(sums, c / l,
+                        acc[j] + ((ccm1_noshift && l == 1) ? sums.n_small - sums.n_big : 0));
       else if (D == kVB2) Ssum = vb2_sum(sums, l, acc[j]);
       else Ssum = bj1_sum(sums, acc[j]);
       const int64_t lb = ceil_div_i64(Ssum, dff_at_c(D, l, c));

@@ -186,7 +186,7 @@ def test_batch_int64_sizes(cudalib, handle, orc):
 def test_batch_fast_path_boundaries(cudalib, handle, orc):
     """Capacities on both sides of every fast-path limit of the kernel."""
     rng = np.random.default_rng(3)
-    caps = [65534, 65535, 65536, 65537, 131071]
+    caps = [65534, 65535, 65536, 65537, 131071, 131072, 131073]
     inst = [rng.integers(0, c + 1, size=int(rng.integers(1, 9))) for c in caps]
     rg = I.ragged_from_list(inst, caps)
     assert_same(run_batch(cudalib, handle, rg), oracle_batch(orc, rg), "boundaries")
