@@ -321,6 +321,8 @@ def main():
     e2e_value = NODES * world / (t_e2e / 1e3)
 
     # ---- plain path: one check per launch ------------------------------------
+    w0, a0, c0, k0 = nd.node(0)
+    plain_shape, plain_us = B.bp_lb_autotune_plain_node(h, w0, a0, k0, reps=20)
     lat = []
     for j in range(min(args.plain_sample, NODES)):
         w, a, c, k = nd.node(j)
@@ -361,6 +363,7 @@ def main():
         "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
         "plain": {"value": plain_rate, "unit": UNIT, "p50_ms": float(np.percentile(lat, 50)),
                   "p99_ms": float(np.percentile(lat, 99)), "sample": len(lat),
+                  "launch_shape": plain_shape, "autotune_us": [round(x, 2) for x in plain_us],
                   "call": "bp_lb_eval_node (H2D, 1 launch, D2H, sync)"},
         "batched_over_plain": value / world / plain_rate,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,

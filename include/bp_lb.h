@@ -240,7 +240,9 @@ int bp_lb_eval_batch_noalloc(int32_t B, const int64_t *d_offsets,
 /* Input modes of the evaluation kernel, for the launch-shape calls below. */
 #define BP_MODE_RAGGED_I32 0   /* bp_lb_eval, bp_lb_eval_batch     */
 #define BP_MODE_RAGGED_I64 1   /* bp_lb_eval_batch_i64             */
-#define BP_MODE_NODES      2   /* bp_lb_eval_node, bp_lb_eval_nodes */
+#define BP_MODE_NODES      2   /* bp_lb_eval_nodes                 */
+#define BP_MODE_PLAIN_RAGGED 3 /* bp_lb_eval (plain path)          */
+#define BP_MODE_PLAIN_NODES  4 /* bp_lb_eval_node (plain path)     */
 
 /* The evaluation kernel is compiled for a small table of launch shapes:
  * nt threads per CTA, t parameters per thread and pass, g passes per tile
@@ -255,7 +257,9 @@ int bp_lb_num_launch_shapes(void);
 int bp_lb_launch_shape_info(int32_t id, int32_t *nt, int32_t *t, int32_t *g,
                             int32_t *min_blocks);
 
-/* Selects the shape the handle uses for one input mode (default 0).
+/* Selects the shape the handle uses for one mode (default 0 for the batched
+ * modes; a short-tile latency shape for the plain modes, which spread one
+ * check over all SMs).
  * Errors: BP_EINVAL (bad handle or mode), BP_ERANGE (bad id). */
 int bp_lb_set_launch_shape(bp_lb_t *h, int32_t mode, int32_t id);
 
@@ -289,6 +293,15 @@ int bp_lb_autotune_nodes(bp_lb_t *h, int32_t B, int32_t num_base,
                          bp_argmax_t *d_out_argmax, uint8_t *d_out_feasible,
                          int32_t reps, float *ms_per_shape,
                          int32_t *best_shape, void *stream);
+
+/* Plain-path autotuner: times `reps` bp_lb_eval_node calls (host wall
+ * clock; each call synchronises) with every launch shape on the given node
+ * and keeps the fastest for BP_MODE_PLAIN_NODES.  us_per_shape and
+ * best_shape may be NULL.  Errors: as bp_lb_eval_node, BP_EINVAL for
+ * reps < 1. */
+int bp_lb_autotune_plain_node(bp_lb_t *h, const int32_t *w, const int32_t *assign,
+                              int64_t n, int64_t bins, int32_t reps,
+                              float *us_per_shape, int32_t *best_shape);
 
 /* ---- inspection -------------------------------------------------------- */
 

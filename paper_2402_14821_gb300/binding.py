@@ -67,6 +67,8 @@ def _bind(lib):
         "bp_lb_selfcheck_division": (_c_i64, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                               _c_i64]),
         "bp_lb_eval_batch_noalloc": (ctypes.c_int, [_c_i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+        "bp_lb_autotune_plain_node": (ctypes.c_int, [_vp, _vp, _vp, _c_i64, _c_i64, _c_i32, _vp,
+                                                     P(_c_i32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -91,11 +93,11 @@ EXPORTED = ("bp_lb_strerror", "bp_lb_create", "bp_lb_destroy", "bp_lb_reserve", 
             "bp_lb_reduce_nodes", "bp_lb_debug_params", "bp_lb_param_count",
             "bp_lb_selfcheck_division", "bp_lb_num_launch_shapes", "bp_lb_launch_shape_info",
             "bp_lb_set_launch_shape", "bp_lb_get_launch_shape", "bp_lb_autotune_batch",
-            "bp_lb_autotune_nodes", "bp_lb_eval_batch_noalloc")
+            "bp_lb_autotune_nodes", "bp_lb_eval_batch_noalloc", "bp_lb_autotune_plain_node")
 
 NOALLOC_MAX_BATCH = 4096
 
-MODE_RAGGED_I32, MODE_RAGGED_I64, MODE_NODES = 0, 1, 2
+MODE_RAGGED_I32, MODE_RAGGED_I64, MODE_NODES, MODE_PLAIN_RAGGED, MODE_PLAIN_NODES = range(5)
 
 
 def strerror(status: int) -> str:
@@ -316,6 +318,20 @@ def bp_lb_autotune_nodes(h, base_offsets, base_sizes, base_capacity, node_base, 
         _ptr(out_feasible, torch.uint8, "out_feasible"), int(reps), ms, ctypes.byref(best),
         _stream(stream)), "bp_lb_autotune_nodes")
     return best.value, list(ms)
+
+
+def bp_lb_autotune_plain_node(h, w, assign, bins: int, reps: int = 20):
+    """Times the plain node path with every launch shape; keeps the fastest.
+    Returns (best shape, [microseconds per call per shape])."""
+    wa = np.ascontiguousarray(np.asarray(w, dtype=np.int32))
+    aa = np.ascontiguousarray(np.asarray(assign, dtype=np.int32))
+    n = bp_lb_num_launch_shapes()
+    us = (ctypes.c_float * n)()
+    best = ctypes.c_int32()
+    _check(lib().bp_lb_autotune_plain_node(h, wa.ctypes.data, aa.ctypes.data, len(wa), int(bins),
+                                           int(reps), us, ctypes.byref(best)),
+           "bp_lb_autotune_plain_node")
+    return best.value, list(us)
 
 
 def bp_lb_selfcheck_division(d_lo: int, d_hi: int, n_hi: int, samples: int) -> int:

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -23,6 +24,10 @@ using namespace bplb;
 namespace {
 
 constexpr size_t kListBytes = 2 * sizeof(uint32_t) * kListTop;  // items + fp32 quotients
+
+constexpr int kModePlainRagged = 3;  // BP_MODE_PLAIN_RAGGED
+constexpr int kModePlainNodes = 4;   // BP_MODE_PLAIN_NODES
+constexpr int kPlainDefaultShape = 6;
 
 struct PlainOut {  // device and pinned-host layout of one plain result
   int64_t bound;
@@ -55,8 +60,10 @@ struct bp_lb {
   unsigned long long *d_keys = nullptr;
   unsigned int *d_done = nullptr;
   unsigned long long *d_work = nullptr;
-  // launch shape per input mode (index into kShapes) and occupancy cache
-  int shape[3] = {0, 0, 0};
+  // launch shape (index into kShapes) per mode: batched ragged i32, ragged
+  // i64, nodes, then the plain ragged and plain node paths; occupancy cache of
+  // the batched modes
+  int shape[5] = {0, 0, 0, kPlainDefaultShape, kPlainDefaultShape};
   int occ_shape[3] = {-1, -1, -1};
   size_t occ_smem[3] = {0, 0, 0};
   int occ_blocks[3] = {0, 0, 0};
@@ -129,6 +136,7 @@ int grow_batch(bp_lb *h, int32_t B) {
 EvalArgs blank_args() {
   EvalArgs A;
   std::memset(&A, 0, sizeof(A));
+  A.one = 1u;
   return A;
 }
 
@@ -296,7 +304,7 @@ static EvalArgs plain_args(bp_lb *h, int64_t n, int64_t bins, int mode) {
   A.out_argmax = &h->d_out->arg;
   A.out_feasible = &h->d_out->feasible;
   A.tile_start = nullptr;
-  A.single_tiles = tiles_for(h->capacity, shape_lpt(h->shape[mode]));
+  A.single_tiles = tiles_for(h->capacity, shape_lpt(h->shape[mode]));  // mode: a plain mode
   A.single_c = h->capacity;
   A.single_k = bins;
   A.single_n = n;
@@ -318,9 +326,9 @@ int bp_lb_eval(bp_lb_t *h, const int32_t *sizes, int64_t n, int64_t bins, int64_
     BP_CHECK(cudaMemcpyAsync(h->d_items, h->h_items, sizeof(int32_t) * (size_t)n,
                              cudaMemcpyHostToDevice, h->stream));
   }
-  EvalArgs A = plain_args(h, n, bins, kSrcRaggedI32);
+  EvalArgs A = plain_args(h, n, bins, kModePlainRagged);
   A.sizes = h->d_items;
-  BP_CHECK_STATUS(launch_eval(h->shape[kSrcRaggedI32], kSrcRaggedI32, (unsigned)A.single_tiles,
+  BP_CHECK_STATUS(launch_eval(h->shape[kModePlainRagged], kSrcRaggedI32, (unsigned)A.single_tiles,
                               eval_smem<kSrcRaggedI32>(0), h->stream, A));
   return plain_finish(h, out_bound, out_argmax);
 }
@@ -337,11 +345,11 @@ int bp_lb_eval_node(bp_lb_t *h, const int32_t *w, const int32_t *assign, int64_t
     BP_CHECK(cudaMemcpyAsync(h->d_assign, h->h_assign, sizeof(int32_t) * (size_t)n,
                              cudaMemcpyHostToDevice, h->stream));
   }
-  EvalArgs A = plain_args(h, n, bins, kSrcNodes);
+  EvalArgs A = plain_args(h, n, bins, kModePlainNodes);
   A.base_sizes = h->d_items;
   A.assign = h->d_assign;
   A.max_bins = (int32_t)bins;
-  BP_CHECK_STATUS(launch_eval(h->shape[kSrcNodes], kSrcNodes, (unsigned)A.single_tiles,
+  BP_CHECK_STATUS(launch_eval(h->shape[kModePlainNodes], kSrcNodes, (unsigned)A.single_tiles,
                               eval_smem<kSrcNodes>(bins), h->stream, A));
   return plain_finish(h, out_bound, out_argmax);
 }
@@ -474,15 +482,45 @@ int bp_lb_launch_shape_info(int32_t id, int32_t *nt, int32_t *t, int32_t *g, int
 }
 
 int bp_lb_set_launch_shape(bp_lb_t *h, int32_t mode, int32_t id) {
-  if (!h || mode < 0 || mode > 2) return BP_EINVAL;
+  if (!h || mode < 0 || mode > 4) return BP_EINVAL;
   if (id < 0 || id >= kNumShapes) return BP_ERANGE;
   h->shape[mode] = id;
   return BP_OK;
 }
 
 int bp_lb_get_launch_shape(bp_lb_t *h, int32_t mode) {
-  if (!h || mode < 0 || mode > 2) return -1;
+  if (!h || mode < 0 || mode > 4) return -1;
   return h->shape[mode];
+}
+
+int bp_lb_autotune_plain_node(bp_lb_t *h, const int32_t *w, const int32_t *assign, int64_t n,
+                              int64_t bins, int32_t reps, float *us_per_shape,
+                              int32_t *best_shape) {
+  if (!h || reps < 1) return BP_EINVAL;
+  int best = h->shape[kModePlainNodes];
+  double best_us = -1.0;
+  for (int s = 0; s < kNumShapes; ++s) {
+    h->shape[kModePlainNodes] = s;
+    int64_t b;
+    int st = bp_lb_eval_node(h, w, assign, n, bins, &b, nullptr);  // warm-up
+    if (st != BP_OK && st != BP_ERANGE) {
+      h->shape[kModePlainNodes] = best;
+      return st;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    for (int r = 0; r < reps; ++r) bp_lb_eval_node(h, w, assign, n, bins, &b, nullptr);
+    const double us =
+        std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count() /
+        reps;
+    if (us_per_shape) us_per_shape[s] = (float)us;
+    if (best_us < 0 || us < best_us) {
+      best_us = us;
+      best = s;
+    }
+  }
+  h->shape[kModePlainNodes] = best;
+  if (best_shape) *best_shape = best;
+  return BP_OK;
 }
 
 int bp_lb_autotune_batch(bp_lb_t *h, int32_t B, const int64_t *d_offsets, const void *d_sizes,

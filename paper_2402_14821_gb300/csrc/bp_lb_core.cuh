@@ -113,8 +113,9 @@ BPLB_HD Div31 div31_make(uint32_t d) {
 // so floor(n m1 / 2^32) = floor(n / d) whenever n e < 2^32, in particular
 // whenever n d < 2^32.  For d = 1 the magic 2^32 does not fit; m1 = 2^32 - 1
 // then gives n - 1 for n >= 1 (and 0 for n = 0), which callers correct.
+// ceil(2^32 / d) = floor((2^32 - 1) / d) + 1 for d >= 2 (one 32-bit division).
 BPLB_HD uint32_t div_noshift_make(uint32_t d) {
-  return d <= 1 ? 0xFFFFFFFFu : (uint32_t)(((uint64_t(1) << 32) + d - 1) / d);
+  return d <= 1 ? 0xFFFFFFFFu : 0xFFFFFFFFu / d + 1u;
 }
 
 // floor(n / d) given n2 = 2n (n < 2^31).
@@ -139,6 +140,15 @@ struct InstSums {
 };
 
 BPLB_HD int64_t ceil_div_i64(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// ceil(a / b) for 0 <= a, 0 < b, with a 32-bit division whenever both fit.
+BPLB_HD int64_t ceil_div_fast(int64_t a, int64_t b) {
+  if (((uint64_t)a >> 32) == 0 && ((uint64_t)b >> 32) == 0) {
+    const uint32_t q = (uint32_t)a / (uint32_t)b;
+    return (int64_t)q + ((uint32_t)a != q * (uint32_t)b);
+  }
+  return (a + b - 1) / b;
+}
 
 // ---------------------------------------------------------------------------
 // S(d, lambda) = sum_i f_d(w_i, lambda) assembled from one lambda-dependent
@@ -203,6 +213,18 @@ BPLB_HD int64_t dff_at_c(int d, int64_t l, int64_t c) {
     case kCCM1: return 2 * (c / l);
     case kVB2:  return 2 * (l - 1);
     default:    return (c / l) * (l - c % l);
+  }
+}
+
+// The same with c / l given (both < 2^31, so the caller divides in 32 bits).
+BPLB_HD int64_t dff_at_c_q(int d, int64_t l, int64_t c, int64_t q) {
+  switch (d) {
+    case kMT:
+    case kRAD2: return c;
+    case kFS1:  return c * l;
+    case kCCM1: return 2 * q;
+    case kVB2:  return 2 * (l - 1);
+    default:    return q * (l - (c - q * l));
   }
 }
 

@@ -32,29 +32,57 @@ BPLB_HD int group_len(int64_t max_term) {
 BPLB_D uint4 lds4(const uint32_t *s, int i) { return *reinterpret_cast<const uint4 *>(s + i); }
 BPLB_D float4 lds4f(const float *s, int i) { return *reinterpret_cast<const float4 *>(s + i); }
 
+// Conditional accumulate on the FMA pipe: if (pred) a += x, issued as a
+// predicated integer multiply-add x * one + a.  `one` is 1 at run time (a
+// kernel argument), so the compiler keeps the multiply-add instead of turning
+// it into an ALU-pipe add; the compare itself stays on the ALU pipe.  Used to
+// balance the two integer pipes of an SM sub-partition.
+BPLB_D uint32_t add_if_ge(uint32_t a, uint32_t x, uint32_t t, uint32_t one) {
+  asm("{\n\t.reg .pred p;\n\tsetp.ge.u32 p, %1, %2;\n\t@p mad.lo.u32 %0, %1, %3, %0;\n\t}"
+      : "+r"(a) : "r"(x), "r"(t), "r"(one));
+  return a;
+}
+BPLB_D uint32_t add_if_lt(uint32_t a, uint32_t x, uint32_t t, uint32_t one) {
+  asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p mad.lo.u32 %0, %1, %3, %0;\n\t}"
+      : "+r"(a) : "r"(x), "r"(t), "r"(one));
+  return a;
+}
+// if (x >= t) n += 1 / if (x > t) n += 1, as predicated multiply-adds.
+BPLB_D uint32_t count_if_ge(uint32_t n, uint32_t x, uint32_t t, uint32_t one) {
+  asm("{\n\t.reg .pred p;\n\tsetp.ge.u32 p, %1, %2;\n\t@p mad.lo.u32 %0, %3, %3, %0;\n\t}"
+      : "+r"(n) : "r"(x), "r"(t), "r"(one));
+  return n;
+}
+BPLB_D uint32_t count_if_gt(uint32_t n, uint32_t x, uint32_t t, uint32_t one) {
+  asm("{\n\t.reg .pred p;\n\tsetp.gt.u32 p, %1, %2;\n\t@p mad.lo.u32 %0, %3, %3, %0;\n\t}"
+      : "+r"(n) : "r"(x), "r"(t), "r"(one));
+  return n;
+}
+
 // ---- MT: acc += sum_small u2*[u2 >= 2l]  (BIG: sum_big u2*[u2 < 2l]) ---------
 template <int T, bool BIG>
 BPLB_D void mt_list(const uint32_t *s, int beg, int end, int K, const uint32_t (&thr)[T],
-                    uint64_t (&acc)[T]) {
+                    uint32_t one, uint64_t (&acc)[T]) {
   for (int g0 = beg; g0 < end; g0 += K) {
     const int g1 = min(end, g0 + K);
     uint32_t a[T];
 #pragma unroll
     for (int j = 0; j < T; ++j) a[j] = 0;
+#pragma unroll 2
     for (int i = g0; i < g1; i += 4) {
       const uint4 v = lds4(s, i);
 #pragma unroll
       for (int j = 0; j < T; ++j) {
         if (!BIG) {
-          if (v.x >= thr[j]) a[j] += v.x;
-          if (v.y >= thr[j]) a[j] += v.y;
-          if (v.z >= thr[j]) a[j] += v.z;
-          if (v.w >= thr[j]) a[j] += v.w;
+          a[j] = add_if_ge(a[j], v.x, thr[j], one);
+          a[j] = add_if_ge(a[j], v.y, thr[j], one);
+          a[j] = add_if_ge(a[j], v.z, thr[j], one);
+          a[j] = add_if_ge(a[j], v.w, thr[j], one);
         } else {
-          if (v.x < thr[j]) a[j] += v.x;
-          if (v.y < thr[j]) a[j] += v.y;
-          if (v.z < thr[j]) a[j] += v.z;
-          if (v.w < thr[j]) a[j] += v.w;
+          a[j] = add_if_lt(a[j], v.x, thr[j], one);
+          a[j] = add_if_lt(a[j], v.y, thr[j], one);
+          a[j] = add_if_lt(a[j], v.z, thr[j], one);
+          a[j] = add_if_lt(a[j], v.w, thr[j], one);
         }
       }
     }
@@ -66,17 +94,28 @@ BPLB_D void mt_list(const uint32_t *s, int beg, int end, int K, const uint32_t (
 // ---- RAD2: n1 += #[u2 >= 2l] (SIGN), n2 += #[u2 > 2c - 4l] ---------------------
 template <int T, int SIGN>
 BPLB_D void rad2_list(const uint32_t *s, int beg, int end, const uint32_t (&t1)[T],
-                      const uint32_t (&t2)[T], int32_t (&n1)[T], uint32_t (&n2)[T]) {
+                      const uint32_t (&t2)[T], uint32_t one, int32_t (&n1)[T],
+                      uint32_t (&n2)[T]) {
+  uint32_t c1[T];
+#pragma unroll
+  for (int j = 0; j < T; ++j) c1[j] = 0;
+#pragma unroll 2
   for (int i = beg; i < end; i += 4) {
     const uint4 v = lds4(s, i);
 #pragma unroll
     for (int j = 0; j < T; ++j) {
-      const int32_t c1 = (int32_t)((v.x >= t1[j]) + (v.y >= t1[j]) + (v.z >= t1[j]) + (v.w >= t1[j]));
-      n1[j] += SIGN * c1;
-      n2[j] += (uint32_t)(v.x > t2[j]) + (uint32_t)(v.y > t2[j]) + (uint32_t)(v.z > t2[j]) +
-               (uint32_t)(v.w > t2[j]);
+      c1[j] = count_if_ge(c1[j], v.x, t1[j], one);
+      c1[j] = count_if_ge(c1[j], v.y, t1[j], one);
+      c1[j] = count_if_ge(c1[j], v.z, t1[j], one);
+      c1[j] = count_if_ge(c1[j], v.w, t1[j], one);
+      n2[j] = count_if_gt(n2[j], v.x, t2[j], one);
+      n2[j] = count_if_gt(n2[j], v.y, t2[j], one);
+      n2[j] = count_if_gt(n2[j], v.z, t2[j], one);
+      n2[j] = count_if_gt(n2[j], v.w, t2[j], one);
     }
   }
+#pragma unroll
+  for (int j = 0; j < T; ++j) n1[j] += SIGN * (int32_t)c1[j];
 }
 
 // ---- FS1 (raw w): acc += c * floor(w(l+1)/c) - w*[c | w(l+1)] ----------------
@@ -88,6 +127,7 @@ BPLB_D void fs1_list(const uint32_t *s, int beg, int end, int K, const uint32_t 
     uint32_t a0[T], a1[T];
 #pragma unroll
     for (int j = 0; j < T; ++j) a0[j] = a1[j] = 0;
+#pragma unroll 2
     for (int i = g0; i < g1; i += 4) {
       const uint4 v = lds4(s, i);
       const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
@@ -129,6 +169,7 @@ BPLB_D void ccm1_list(const uint32_t *s, int beg, int end, int K, const Div31 (&
     uint32_t a[T];
 #pragma unroll
     for (int j = 0; j < T; ++j) a[j] = 0;
+#pragma unroll 2
     for (int i = g0; i < g1; i += 4) {
       const uint4 v = lds4(s, i);
 #pragma unroll
@@ -160,6 +201,7 @@ BPLB_D void ccm1_list_noshift(const uint32_t *s, int beg, int end, int K, const 
     uint32_t a[T];
 #pragma unroll
     for (int j = 0; j < T; ++j) a[j] = 0;
+#pragma unroll 2
     for (int i = g0; i < g1; i += 4) {
       const uint4 v = lds4(s, i);
 #pragma unroll
@@ -177,7 +219,10 @@ BPLB_D void ccm1_list_noshift(const uint32_t *s, int beg, int end, int K, const 
 
 // ---- VB2 (u2 = 2u): acc += SIGN * ceil(u l / c) ---------------------------------
 // c <= 65535: ceil(u l / c) = floor((u l + c - 1) / c), numerator < 2^31, exact
-// multiply-high division by c.
+// multiply-high division by c.  A thread's parameters are consecutive
+// (lam[1] = lam[0] + 1 whenever lam[1] is valid), so the numerator of the
+// second one is the first one's plus u2: an ALU-pipe add replaces one
+// multiply-add, balancing the two integer pipes.
 template <int T, int SIGN>
 BPLB_D void vb2_list_magic(const uint32_t *s, int beg, int end, int K, const uint32_t (&lam)[T],
                            Div31 Dc, uint32_t add2, int64_t (&acc)[T]) {
@@ -186,13 +231,19 @@ BPLB_D void vb2_list_magic(const uint32_t *s, int beg, int end, int K, const uin
     uint32_t a[T];
 #pragma unroll
     for (int j = 0; j < T; ++j) a[j] = 0;
+#pragma unroll 2
     for (int i = g0; i < g1; i += 4) {
       const uint4 v = lds4(s, i);
+      const uint32_t u4[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-      for (int j = 0; j < T; ++j) {
-        // 2 (u l + c - 1) = u2 * l + (2c - 2)
-        a[j] += div31(v.x * lam[j] + add2, Dc) + div31(v.y * lam[j] + add2, Dc);
-        a[j] += div31(v.z * lam[j] + add2, Dc) + div31(v.w * lam[j] + add2, Dc);
+      for (int e = 0; e < 4; ++e) {
+        uint32_t x[T];
+#pragma unroll
+        for (int j = 0; j < T; ++j) {
+          // 2 (u l + c - 1) = u2 * l + (2c - 2)
+          x[j] = (T > 1 && j == 1) ? x[0] + u4[e] : u4[e] * lam[j] + add2;
+          a[j] += div31(x[j], Dc);
+        }
       }
     }
 #pragma unroll
@@ -220,6 +271,7 @@ BPLB_D void vb2_list_float(const uint32_t *s, const float *sa, int beg, int end,
     uint32_t a[T];
 #pragma unroll
     for (int j = 0; j < T; ++j) a[j] = 0;
+#pragma unroll 2
     for (int i = g0; i < g1; i += 4) {
       const uint4 v = lds4(s, i);
       const float4 f = lds4f(sa, i);
@@ -260,6 +312,7 @@ BPLB_D void bj1_list(const uint32_t *s, int beg, int end, int K, const Div31 (&D
     uint32_t a0[T], a1[T];
 #pragma unroll
     for (int j = 0; j < T; ++j) a0[j] = a1[j] = 0;
+#pragma unroll 2
     for (int i = g0; i < g1; i += 4) {
       const uint4 v = lds4(s, i);
       const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
@@ -280,20 +333,21 @@ BPLB_D void bj1_list(const uint32_t *s, int beg, int end, int K, const Div31 (&D
   }
 }
 
-// c <= 65535, list holds raw w: with q = floor(w / l) (multiply-high, no
-// shift; w * l < 2^32) and cm = c mod l,
-//   cm q + min(w mod l, cm) = min(w - (l - cm) q, cm (q + 1)),
-// two multiply-adds and a min per item.  For l = 1, cm = 0 and the term is
-// min(., 0) = 0 whatever q is, as it must be.
+// c <= 65535, list holds raw w: q = floor(w / l) by multiply-high without a
+// shift (w * l < 2^32), rho = w - q l; acc += cm * sum q + sum min(rho, cm)
+// with cm = c mod l: two multiply-adds (FMA pipe) and a min plus two adds (ALU
+// pipe) per item.  For l = 1, cm = 0 and q (= w - 1 for w >= 1) is multiplied
+// by 0, min(rho, 0) = 0: the term is 0, as it must be.
 template <int T>
 BPLB_D void bj1_list_noshift(const uint32_t *s, int beg, int end, int K, const uint32_t (&m1)[T],
-                             const uint32_t (&lmc)[T], const uint32_t (&cm)[T],
+                             const uint32_t (&lam)[T], const uint32_t (&cm)[T],
                              int64_t (&acc)[T]) {
   for (int g0 = beg; g0 < end; g0 += K) {
     const int g1 = min(end, g0 + K);
-    uint32_t a[T];
+    uint32_t a0[T], a1[T];
 #pragma unroll
-    for (int j = 0; j < T; ++j) a[j] = 0;
+    for (int j = 0; j < T; ++j) a0[j] = a1[j] = 0;
+#pragma unroll 2
     for (int i = g0; i < g1; i += 4) {
       const uint4 v = lds4(s, i);
       const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
@@ -302,12 +356,13 @@ BPLB_D void bj1_list_noshift(const uint32_t *s, int beg, int end, int K, const u
 #pragma unroll
         for (int j = 0; j < T; ++j) {
           const uint32_t q = __umulhi(w4[e], m1[j]);
-          a[j] += min(w4[e] - lmc[j] * q, cm[j] * q + cm[j]);
+          a0[j] += q;
+          a1[j] += min(w4[e] - q * lam[j], cm[j]);
         }
       }
     }
 #pragma unroll
-    for (int j = 0; j < T; ++j) acc[j] += (int64_t)a[j];
+    for (int j = 0; j < T; ++j) acc[j] += (int64_t)cm[j] * (int64_t)a0[j] + (int64_t)a1[j];
   }
 }
 

@@ -61,6 +61,7 @@ struct EvalArgs {
   unsigned long long *keys;   // [B] packed (bound, -index) maxima, zero between calls
   unsigned int *done;         // [B] finished-tile counters, zero between calls
   unsigned long long *work;   // [1] next tile (persistent mode), nullptr otherwise
+  uint32_t one;               // always 1 (see add_if_ge in bp_lb_eval.cuh)
 };
 
 // Instance view resolved per tile.
@@ -292,7 +293,8 @@ __device__ __forceinline__ void stage_chunk(const EvalArgs &A, const InstView &I
 }
 
 // Evaluates one tile of DFF D: lambdas [lam0, lam_end) in groups of NT * T,
-// thread t taking lam_g + j * NT + t (j < T) in group g.  Returns the
+// thread t taking the T consecutive lambdas lam_g + t * T + j (j < T) of group
+// g, so that the threads past the end of a short range form whole idle warps.  Returns the
 // thread's largest key make_key(lb, flat index); 0 if it had no parameter.
 // With DEBUG the thread's single parameter comes from a request list and its
 // bound is written to req_out instead.
@@ -339,7 +341,7 @@ __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int
       if (DEBUG) {
         l = (j == 0 && req_idx >= 0) ? req_lam[req_idx] : lo_d;
       } else {
-        l = lam0 + (int64_t)g * GW + (int64_t)j * NT + tid;
+        l = lam0 + (int64_t)g * GW + (int64_t)tid * T + j;
       }
       valid[j] = DEBUG ? (j == 0 && req_idx >= 0 && l >= lo_d && l <= hi_d) : (l < lam_end);
       lam[j] = valid[j] ? l : lo_d;
@@ -367,13 +369,13 @@ __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int
         k0[j] = l32;
         kf[j] = (float)l32;
       } else {  // BJ1
-        Dl[j] = div31_make(l32);
-        const uint32_t cm = (uint32_t)c - div31(c2, Dl[j]) * l32;  // c mod l
+        const uint32_t cm = (uint32_t)c - ((uint32_t)c / l32) * l32;  // c mod l
         if (bj1_noshift) {
           k0[j] = div_noshift_make(l32);
-          k1[j] = l32 - cm;
+          k1[j] = l32;
           k2[j] = cm;
         } else {
+          Dl[j] = div31_make(l32);
           k0[j] = 2u * l32;
           k1[j] = 2u * cm;
         }
@@ -417,7 +419,10 @@ __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int
         }
         __syncthreads();
       }
-      if (!S.err) {
+      bool any_valid = false;
+#pragma unroll
+      for (int j = 0; j < T; ++j) any_valid |= valid[j];
+      if (!S.err && any_valid) {
         const int ns_pad = (S.ns + 3) & ~3;
         const int bstart = (kListTop - S.nb) & ~3;
         if (D == kMT) {
@@ -425,13 +430,13 @@ __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int
           uint64_t a64[T];
 #pragma unroll
           for (int j = 0; j < T; ++j) a64[j] = 0;
-          mt_list<T, false>(s_items, 0, ns_pad, K, k0, a64);
-          mt_list<T, true>(s_items, bstart, kListTop, K, k0, a64);
+          mt_list<T, false>(s_items, 0, ns_pad, K, k0, A.one, a64);
+          mt_list<T, true>(s_items, bstart, kListTop, K, k0, A.one, a64);
 #pragma unroll
           for (int j = 0; j < T; ++j) acc[j] += (int64_t)a64[j];
         } else if (D == kRAD2) {
-          rad2_list<T, 1>(s_items, 0, ns_pad, k0, k1, n1, n2s);
-          rad2_list<T, -1>(s_items, bstart, kListTop, k0, k1, n1, n2b);
+          rad2_list<T, 1>(s_items, 0, ns_pad, k0, k1, A.one, n1, n2s);
+          rad2_list<T, -1>(s_items, bstart, kListTop, k0, k1, A.one, n1, n2b);
         } else if (D == kFS1) {
           if (fs1_fast) fs1_list<T>(s_items, 0, ns_pad, group_len(c), k0, Dc, c2, c, acc);
           else fs1_list_wide<T>(s_items, 0, ns_pad, lam, c, acc);
@@ -494,16 +499,17 @@ __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int
     for (int j = 0; j < T; ++j) {
       if (!valid[j]) continue;
       const int64_t l = lam[j];
+      const int64_t q = (D == kCCM1 || D == kBJ1) ? (int64_t)((uint32_t)c / (uint32_t)l) : 0;
       int64_t Ssum;
       if (D == kMT) Ssum = mt_sum(sums, c, (uint64_t)acc[j]);
       else if (D == kRAD2) Ssum = rad2_sum(sums, c, n1[j], n2s[j], n2b[j]);
       else if (D == kFS1) Ssum = fs1_sum(acc[j]);
       else if (D == kCCM1)
-        Ssum = ccm1_sum(sums, c / l,
+        Ssum = ccm1_sum(sums, q,
                         acc[j] + ((ccm1_noshift && l == 1) ? sums.n_small - sums.n_big : 0));
       else if (D == kVB2) Ssum = vb2_sum(sums, l, acc[j]);
       else Ssum = bj1_sum(sums, acc[j]);
-      const int64_t lb = ceil_div_i64(Ssum, dff_at_c(D, l, c));
+      const int64_t lb = ceil_div_fast(Ssum, dff_at_c_q(D, l, c, q));
       if (DEBUG) {
         req_out[req_idx] = lb;
       } else {

@@ -17,12 +17,16 @@ struct LaunchShape {
   int nt, t, g, minb;
 };
 
-constexpr int kNumShapes = 4;
+constexpr int kNumShapes = 8;
 constexpr LaunchShape kShapes[kNumShapes] = {
     {256, 4, 2, 3},  // 0: default
     {256, 2, 4, 4},  // 1: fewer registers, more resident warps
     {128, 4, 2, 6},  // 2: smaller CTAs
     {256, 4, 4, 3},  // 3: longer tiles (less staging per parameter)
+    {128, 4, 4, 6},  // 4: small CTAs, longer tiles
+    {128, 4, 8, 6},  // 5: small CTAs, longest tiles (search nodes)
+    {128, 2, 1, 6},  // 6: short tiles: one check spread over all SMs (latency)
+    {128, 1, 1, 8},  // 7: shortest tiles (latency)
 };
 
 constexpr int64_t shape_lpt(int s) { return (int64_t)kShapes[s].nt * kShapes[s].t * kShapes[s].g; }
@@ -55,8 +59,16 @@ inline EvalFn eval_fn(int shape, int mode) {
                                  kShapes[1].minb>;                                 \
       case 2: return eval_kernel<kShapes[2].nt, kShapes[2].t, kShapes[2].g, MODE,  \
                                  kShapes[2].minb>;                                 \
-      default: return eval_kernel<kShapes[3].nt, kShapes[3].t, kShapes[3].g, MODE, \
-                                  kShapes[3].minb>;                                \
+      case 3: return eval_kernel<kShapes[3].nt, kShapes[3].t, kShapes[3].g, MODE,  \
+                                 kShapes[3].minb>;                                 \
+      case 4: return eval_kernel<kShapes[4].nt, kShapes[4].t, kShapes[4].g, MODE,  \
+                                 kShapes[4].minb>;                                 \
+      case 5: return eval_kernel<kShapes[5].nt, kShapes[5].t, kShapes[5].g, MODE,  \
+                                 kShapes[5].minb>;                                 \
+      case 6: return eval_kernel<kShapes[6].nt, kShapes[6].t, kShapes[6].g, MODE,  \
+                                 kShapes[6].minb>;                                 \
+      default: return eval_kernel<kShapes[7].nt, kShapes[7].t, kShapes[7].g, MODE, \
+                                  kShapes[7].minb>;                                \
     }                                                                              \
   }                                                                                \
   }

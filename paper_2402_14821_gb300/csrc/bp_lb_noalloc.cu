@@ -85,6 +85,7 @@ extern "C" int bp_lb_eval_batch_noalloc(int32_t B, const int64_t *d_offsets,
 
   EvalArgs A;
   std::memset(&A, 0, sizeof(A));
+  A.one = 1u;
   A.B = B;
   A.offsets = d_offsets;
   A.sizes = d_sizes;

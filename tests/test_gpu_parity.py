@@ -328,13 +328,30 @@ def test_every_launch_shape_is_exact(cudalib, orc):
     h = cudalib.bp_lb_create(150, 4096)
     try:
         for shape in range(cudalib.bp_lb_num_launch_shapes()):
-            for mode in (cudalib.MODE_RAGGED_I32, cudalib.MODE_RAGGED_I64, cudalib.MODE_NODES):
+            for mode in (cudalib.MODE_RAGGED_I32, cudalib.MODE_RAGGED_I64, cudalib.MODE_NODES,
+                         cudalib.MODE_PLAIN_RAGGED, cudalib.MODE_PLAIN_NODES):
                 cudalib.bp_lb_set_launch_shape(h, mode, shape)
             assert_same(run_batch(cudalib, h, rg), want, f"shape {shape} i32")
             assert_same(run_batch(cudalib, h, rg, i64=True), want, f"shape {shape} i64")
             assert_same(run_nodes(cudalib, h, nd), want_nodes, f"shape {shape} nodes")
             w = rg.instance(3)
             assert cudalib.bp_lb_eval(h, w[w <= 150], 7)[0] == orc.lb(w[w <= 150], 150, 7)[0]
+            wn, an, cn, kn = nd.node(5)
+            if cn == 150:
+                assert cudalib.bp_lb_eval_node(h, wn, an, kn)[:3] == oracle_node(orc, nd, 5)[:3]
+    finally:
+        cudalib.bp_lb_destroy(h)
+
+
+def test_autotune_plain_node(cudalib, orc):
+    nd = I.search_nodes(nodes=4)
+    h = cudalib.bp_lb_create(10_000, 4096)
+    try:
+        w, a, c, k = nd.node(1)
+        best, us = cudalib.bp_lb_autotune_plain_node(h, w, a, k, reps=3)
+        assert cudalib.bp_lb_get_launch_shape(h, cudalib.MODE_PLAIN_NODES) == best
+        assert us[best] == min(us)
+        assert cudalib.bp_lb_eval_node(h, w, a, k) == oracle_node(orc, nd, 1)[:3]
     finally:
         cudalib.bp_lb_destroy(h)
 
