@@ -185,7 +185,13 @@ def main():
     ap.add_argument("--plain-sample", type=int, default=1024)
     ap.add_argument("--cpu-budget", type=float, default=15.0,
                     help="CPU-seconds of oracle work for the cpu_baseline sample")
+    ap.add_argument("--workload", choices=("search", "large", "ragged"), default="search",
+                    help="search: the benchmark line (4096 search nodes); large: n=10^4, "
+                         "c in {1e5, 1e6}, three size families, batches of 64; ragged: 10^4 "
+                         "ragged search nodes in one CUDA-graph launch")
     args = ap.parse_args()
+    if args.workload != "search":
+        return run_sweep(args)
 
     NODES = args.nodes
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -382,6 +388,138 @@ def main():
                                    f"{cpu_wall:.1f} s wall on {threads} threads"},
     }
     print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# secondary workloads (not the benchmark line): large instances, ragged batch
+# ---------------------------------------------------------------------------
+def _dev(x, dt):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).to(dt).cuda()
+
+
+def _time_steps(step, steps, flush, stream):
+    """Per-step CUDA-event times (ms) with an L2 flush before every step."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    torch.cuda.synchronize()
+    for e0, e1 in ev:
+        flush.zero_()
+        e0.record(stream)
+        step()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    return np.array([e0.elapsed_time(e1) for e0, e1 in ev])
+
+
+def _peak_ops():
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    return sms * 4 * 32 * float(measured_peaks().get("sm_max_mhz", 2070.0)) * 1e6
+
+
+def ragged_work(rg):
+    """(evals, ops) of a ragged batch of reduced instances."""
+    evals = ops = 0
+    for b in range(rg.count):
+        c = int(rg.capacity[b])
+        r = int(rg.offsets[b + 1] - rg.offsets[b])
+        cnt = param_counts(c)
+        evals += r * sum(cnt)
+        ops += r * sum(cnt[d] * ops_per_eval(d, c) for d in range(6))
+    return evals, ops
+
+
+def run_sweep(args):
+    import torch
+    from paper_2402_14821_gb300 import binding as B
+    from paper_2402_14821_gb300 import build
+    from paper_2402_14821_gb300 import instances as I
+
+    torch.cuda.set_device(0)
+    build.build()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    peak = _peak_ops()
+    h = B.bp_lb_create(150, 1 << 16)
+    out = {"workload": args.workload, "results": []}
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        if args.workload == "large":
+            steps = max(1, min(args.steps, 5))
+            for c in (10 ** 5, 10 ** 6):
+                for fam in I.FAMILIES:
+                    for dt in (np.int32, np.int64):
+                        rg = I.large_instances(fam, c, count=64, n=10_000, seed=2, dtype=dt)
+                        evals, ops = ragged_work(rg)
+                        tdt = torch.int32 if dt == np.int32 else torch.int64
+                        t = (_dev(rg.offsets, torch.int64), _dev(rg.sizes, tdt),
+                             _dev(rg.capacity, torch.int64), _dev(rg.bins, torch.int64))
+                        ob = torch.empty(rg.count, dtype=torch.int64, device="cuda")
+                        oa = B.argmax_tensor(rg.count)
+                        shape, _ = B.bp_lb_autotune_batch(h, *t, ob, oa, reps=1)
+                        step = lambda: B.bp_lb_eval_batch(h, *t, ob, oa, stream=stream)
+                        step()
+                        ms = _time_steps(step, steps, flush, stream)
+                        tm = float(ms.mean())
+                        out["results"].append({
+                            "c": c, "family": fam, "dtype": np.dtype(dt).name, "instances": 64,
+                            "n": 10_000, "ms_per_batch": tm, "checks_per_s": 64 / (tm / 1e3),
+                            "evals_per_s": evals / (tm / 1e3), "launch_shape": shape,
+                            "roofline_frac": ops / (tm / 1e3) / peak})
+                        print(json.dumps(out["results"][-1]), flush=True)
+        else:  # ragged
+            nd = I.ragged_nodes(seed=3)
+            rg_r = reduced_sizes(nd)
+            evals = ops = 0
+            for j in range(nd.count):
+                c = int(nd.base.capacity[j])
+                cnt = param_counts(c)
+                evals += int(rg_r[j]) * sum(cnt)
+                ops += int(rg_r[j]) * sum(cnt[d] * ops_per_eval(d, c) for d in range(6))
+            t_in = dict(base_offsets=_dev(nd.base.offsets, torch.int64),
+                        base_sizes=_dev(nd.base.sizes, torch.int32),
+                        base_capacity=_dev(nd.base.capacity, torch.int64),
+                        node_base=_dev(nd.node_base, torch.int32),
+                        assign_offsets=_dev(nd.assign_offsets, torch.int64),
+                        assign=_dev(nd.assign, torch.int32), bins=_dev(nd.bins, torch.int64))
+            mb = int(nd.bins.max())
+            ob = torch.empty(nd.count, dtype=torch.int64, device="cuda")
+            oa = B.argmax_tensor(nd.count)
+            of = torch.empty(nd.count, dtype=torch.uint8, device="cuda")
+            B.bp_lb_reserve(h, nd.count)
+            shape, shape_ms = B.bp_lb_autotune_nodes(h, max_bins=mb, out_bound=ob, out_argmax=oa,
+                                                     out_feasible=of, reps=1, **t_in)
+            direct = lambda: B.bp_lb_eval_nodes(h, max_bins=mb, out_bound=ob, out_argmax=oa,
+                                                out_feasible=of, stream=stream, **t_in)
+            # capture the whole batch (planning + persistent evaluation) in a CUDA graph
+            g = torch.cuda.CUDAGraph()
+            cs = torch.cuda.Stream()
+            cs.wait_stream(stream)
+            with torch.cuda.stream(cs):
+                direct()
+            stream.wait_stream(cs)
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g, stream=cs):
+                B.bp_lb_eval_nodes(h, max_bins=mb, out_bound=ob, out_argmax=oa, out_feasible=of,
+                                   stream=cs, **t_in)
+            g.replay()
+            torch.cuda.synchronize()
+            steps = max(3, min(args.steps, 20))
+            ms_graph = _time_steps(g.replay, steps, flush, stream)
+            ms_direct = _time_steps(direct, steps, flush, stream)
+            tm = float(ms_graph.mean())
+            out["results"].append({
+                "instances": nd.count, "ms_per_batch_graph": tm,
+                "ms_per_batch_direct": float(ms_direct.mean()),
+                "checks_per_s": nd.count / (tm / 1e3), "evals_per_s": evals / (tm / 1e3),
+                "evals_per_batch": evals, "launch_shape": shape,
+                "autotune_ms": [round(x, 3) for x in shape_ms],
+                "roofline_frac": ops / (tm / 1e3) / peak})
+            print(json.dumps(out["results"][-1]), flush=True)
+    out["clocks"] = clk.summary()
+    B.bp_lb_destroy(h)
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":
