@@ -185,10 +185,11 @@ def main():
     ap.add_argument("--plain-sample", type=int, default=1024)
     ap.add_argument("--cpu-budget", type=float, default=15.0,
                     help="CPU-seconds of oracle work for the cpu_baseline sample")
-    ap.add_argument("--workload", choices=("search", "large", "ragged"), default="search",
+    ap.add_argument("--workload", choices=("search", "large", "ragged", "serve"), default="search",
                     help="search: the benchmark line (4096 search nodes); large: n=10^4, "
                          "c in {1e5, 1e6}, three size families, batches of 64; ragged: 10^4 "
-                         "ragged search nodes in one CUDA-graph launch")
+                         "ragged search nodes in one CUDA-graph launch; serve: 256 simulated "
+                         "searches against the continuous-batching server, offered rates swept")
     args = ap.parse_args()
     if args.workload != "search":
         return run_sweep(args)
@@ -468,6 +469,29 @@ def run_sweep(args):
                             "evals_per_s": evals / (tm / 1e3), "launch_shape": shape,
                             "roofline_frac": ops / (tm / 1e3) / peak})
                         print(json.dumps(out["results"][-1]), flush=True)
+        elif args.workload == "serve":
+            from paper_2402_14821_gb300 import search_sim
+            searches = search_sim.make_searches(count=256, seed=4)
+            tot = lambda c: sum(param_counts(c))
+            srv = B.bp_serve_create(pool_items=1 << 23, max_instances=256,
+                                    max_queued_items=3 << 20, slots=3, max_batch=256,
+                                    max_bins=16384)
+            ids = [B.bp_serve_register(srv, s.w, s.c) for s in searches]
+            for rate in (10.0, 100.0, 1e3, 1e4, 1e5, 1e6):
+                res = search_sim.drive(B, srv, searches, ids, rate=rate, duration_s=4.0,
+                                       param_total=tot)
+                lat = res["latency_us"] / 1e3
+                el = res["elapsed_s"]
+                out["results"].append({
+                    "offered_checks_per_s": rate, "achieved_checks_per_s": res["done"] / el,
+                    "evals_per_s": res["evals"] / el, "done": res["done"],
+                    "submitted": res["submitted"], "refused": res["refused"],
+                    "infeasible": res["infeasible"],
+                    "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+                    "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None})
+                print(json.dumps(out["results"][-1]), flush=True)
+            out["server"] = B.bp_serve_stats(srv)
+            B.bp_serve_destroy(srv)
         else:  # ragged
             nd = I.ragged_nodes(seed=3)
             rg_r = reduced_sizes(nd)

@@ -303,6 +303,79 @@ int bp_lb_autotune_plain_node(bp_lb_t *h, const int32_t *w, const int32_t *assig
                               int64_t n, int64_t bins, int32_t reps,
                               float *us_per_shape, int32_t *best_shape);
 
+/* ---- serving: continuous batching of checks from concurrent searches ---- */
+
+/* A request loop for many concurrent searches (the paper's CP solver issues
+ * one check per propagation of the bin_packing constraint, Alg. 1).  Base
+ * instances are registered once and stay resident on the device; a check is
+ * a partial packing of one of them.  A scheduler thread forms batches from
+ * pending checks whenever one of `slots` in-flight slots frees up and runs
+ * them with bp_lb_eval_nodes on that slot's own stream and scratch, so a
+ * batch admitted while others run shares the SMs with them.  Admission is by
+ * device-memory footprint: the resident pool holds at most pool_items sizes
+ * and at most max_queued_items assignment entries may be pending or in
+ * flight; a request that does not fit is refused with BP_EBUSY and should be
+ * retried after polling.  Results are identical to bp_lb_eval_nodes on the
+ * same node (every check is independent of the others in its batch). */
+typedef struct bp_serve bp_serve_t;
+
+typedef struct {
+    int64_t request;      /* id returned by bp_serve_submit                     */
+    int64_t tag;          /* the caller's tag                                    */
+    int64_t bound;        /* LB, or -BP_ERANGE (bad node) / -BP_ECUDA             */
+    bp_argmax_t argmax;   /* first attaining (DFF, lambda)                       */
+    double latency_us;    /* from submit to the result being collected           */
+    int32_t status;       /* BP_OK, BP_ERANGE or BP_ECUDA                         */
+    uint8_t feasible;     /* 1 iff bound <= bins                                  */
+    uint8_t pad[3];
+} bp_serve_result_t;
+
+/* Creates a server on the current device and starts its scheduler thread.
+ *   pool_items        device slots for resident base-instance sizes (int32);
+ *   max_instances     most instances that can be registered;
+ *   max_queued_items  bound on the assignment entries of pending plus
+ *                     in-flight checks (each slot stages max_queued_items /
+ *                     slots of them, which also bounds one instance's size);
+ *   slots             batches in flight at once, 1..16;
+ *   max_batch         checks per batch;
+ *   max_bins          bound on any check's bin count (<= 16384).
+ * Errors: BP_EINVAL, BP_ERANGE, BP_ENOMEM, BP_ECUDA. */
+int bp_serve_create(int64_t pool_items, int32_t max_instances,
+                    int64_t max_queued_items, int32_t slots, int32_t max_batch,
+                    int64_t max_bins, bp_serve_t **out);
+
+/* Finishes every pending and in-flight check, stops the scheduler and frees
+ * the server.  Results not yet polled are discarded. */
+int bp_serve_destroy(bp_serve_t *s);
+
+/* Uploads a base instance (host sizes, each in [0, capacity]) to the
+ * resident pool; *out_id receives its id.  BP_EBUSY when the pool or the
+ * instance table is full; BP_ERANGE for bad sizes, capacity or an instance
+ * larger than a slot. */
+int bp_serve_register(bp_serve_t *s, const int32_t *sizes, int64_t n,
+                      int64_t capacity, int32_t *out_id);
+
+/* Queues one check of a registered instance: assign[0..n) host (n = the
+ * instance's size; -1 = unpacked, else a bin in [0, bins)); the array is
+ * copied before the call returns.  *out_request (may be NULL) receives the
+ * request id.  BP_EBUSY when the queued-entries bound would be exceeded;
+ * BP_EINVAL for an unknown instance; BP_ERANGE for bins outside
+ * [0, max_bins].  A bad assignment or overfull bin is reported in the
+ * result (status BP_ERANGE). */
+int bp_serve_submit(bp_serve_t *s, int32_t instance, const int32_t *assign,
+                    int64_t bins, int64_t tag, int64_t *out_request);
+
+/* Moves up to max_results finished checks to out[] and their number to
+ * *count, waiting up to wait_us microseconds for the first one (0 = do not
+ * wait).  Returns BP_ETIMEOUT when it waited and nothing finished. */
+int bp_serve_poll(bp_serve_t *s, bp_serve_result_t *out, int32_t max_results,
+                  int32_t *count, int32_t wait_us);
+
+/* Counters (any pointer may be NULL).  Returns the scheduler's status:
+ * BP_OK, or BP_ECUDA once a batch failed on the device. */
+int bp_serve_stats(bp_serve_t *s, int64_t *pending, int64_t *queued_items,
+                   int64_t *batches, int64_t *done, int64_t *refused);
+
 /* ---- inspection -------------------------------------------------------- */
 
 /* Per-parameter bounds for spot checks of very long sweeps: for j < m,

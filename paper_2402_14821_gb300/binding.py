@@ -28,6 +28,13 @@ class BpArgmax(ctypes.Structure):
     _fields_ = [("dff", ctypes.c_int32), ("pad", ctypes.c_int32), ("lam", ctypes.c_int64)]
 
 
+class BpServeResult(ctypes.Structure):
+    _fields_ = [("request", ctypes.c_int64), ("tag", ctypes.c_int64), ("bound", ctypes.c_int64),
+                ("dff", ctypes.c_int32), ("argpad", ctypes.c_int32), ("lam", ctypes.c_int64),
+                ("latency_us", ctypes.c_double), ("status", ctypes.c_int32),
+                ("feasible", ctypes.c_uint8), ("pad", ctypes.c_uint8 * 3)]
+
+
 class BpLbError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -69,6 +76,13 @@ def _bind(lib):
         "bp_lb_eval_batch_noalloc": (ctypes.c_int, [_c_i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
         "bp_lb_autotune_plain_node": (ctypes.c_int, [_vp, _vp, _vp, _c_i64, _c_i64, _c_i32, _vp,
                                                      P(_c_i32)]),
+        "bp_serve_create": (ctypes.c_int, [_c_i64, _c_i32, _c_i64, _c_i32, _c_i32, _c_i64, P(_vp)]),
+        "bp_serve_destroy": (ctypes.c_int, [_vp]),
+        "bp_serve_register": (ctypes.c_int, [_vp, _vp, _c_i64, _c_i64, P(_c_i32)]),
+        "bp_serve_submit": (ctypes.c_int, [_vp, _c_i32, _vp, _c_i64, _c_i64, P(_c_i64)]),
+        "bp_serve_poll": (ctypes.c_int, [_vp, P(BpServeResult), _c_i32, P(_c_i32), _c_i32]),
+        "bp_serve_stats": (ctypes.c_int, [_vp, P(_c_i64), P(_c_i64), P(_c_i64), P(_c_i64),
+                                          P(_c_i64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -93,7 +107,9 @@ EXPORTED = ("bp_lb_strerror", "bp_lb_create", "bp_lb_destroy", "bp_lb_reserve", 
             "bp_lb_reduce_nodes", "bp_lb_debug_params", "bp_lb_param_count",
             "bp_lb_selfcheck_division", "bp_lb_num_launch_shapes", "bp_lb_launch_shape_info",
             "bp_lb_set_launch_shape", "bp_lb_get_launch_shape", "bp_lb_autotune_batch",
-            "bp_lb_autotune_nodes", "bp_lb_eval_batch_noalloc", "bp_lb_autotune_plain_node")
+            "bp_lb_autotune_nodes", "bp_lb_eval_batch_noalloc", "bp_lb_autotune_plain_node",
+            "bp_serve_create", "bp_serve_destroy", "bp_serve_register", "bp_serve_submit",
+            "bp_serve_poll", "bp_serve_stats")
 
 NOALLOC_MAX_BATCH = 4096
 
@@ -336,3 +352,54 @@ def bp_lb_autotune_plain_node(h, w, assign, bins: int, reps: int = 20):
 
 def bp_lb_selfcheck_division(d_lo: int, d_hi: int, n_hi: int, samples: int) -> int:
     return lib().bp_lb_selfcheck_division(d_lo, d_hi, n_hi, samples)
+
+
+# -- serving -------------------------------------------------------------------------
+def bp_serve_create(pool_items: int, max_instances: int, max_queued_items: int, slots: int = 3,
+                    max_batch: int = 4096, max_bins: int = 16384):
+    s = _vp()
+    _check(lib().bp_serve_create(int(pool_items), int(max_instances), int(max_queued_items),
+                                 int(slots), int(max_batch), int(max_bins), ctypes.byref(s)),
+           "bp_serve_create")
+    return s
+
+
+def bp_serve_destroy(s):
+    _check(lib().bp_serve_destroy(s), "bp_serve_destroy")
+
+
+def bp_serve_register(s, sizes, capacity: int) -> int:
+    a = np.ascontiguousarray(np.asarray(sizes, dtype=np.int32))
+    i = ctypes.c_int32()
+    _check(lib().bp_serve_register(s, a.ctypes.data, len(a), int(capacity), ctypes.byref(i)),
+           "bp_serve_register")
+    return i.value
+
+
+def bp_serve_submit(s, instance: int, assign, bins: int, tag: int = 0):
+    """Returns the request id, or None when admission refused it (BP_EBUSY)."""
+    a = np.ascontiguousarray(np.asarray(assign, dtype=np.int32))
+    rid = ctypes.c_int64()
+    st = lib().bp_serve_submit(s, int(instance), a.ctypes.data, int(bins), int(tag),
+                               ctypes.byref(rid))
+    if st == BP_EBUSY:
+        return None
+    _check(st, "bp_serve_submit")
+    return rid.value
+
+
+def bp_serve_poll(s, max_results: int = 1024, wait_us: int = 0):
+    """List of finished results (BpServeResult records)."""
+    buf = (BpServeResult * max_results)()
+    cnt = ctypes.c_int32()
+    st = lib().bp_serve_poll(s, buf, int(max_results), ctypes.byref(cnt), int(wait_us))
+    if st not in (BP_OK, BP_ETIMEOUT):
+        _check(st, "bp_serve_poll")
+    return [buf[i] for i in range(cnt.value)]
+
+
+def bp_serve_stats(s):
+    v = [ctypes.c_int64() for _ in range(5)]
+    st = lib().bp_serve_stats(s, *[ctypes.byref(x) for x in v])
+    return dict(zip(("pending", "queued_items", "batches", "done", "refused"),
+                    (x.value for x in v)), status=st)

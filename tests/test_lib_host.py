@@ -21,7 +21,7 @@ def lib():
 def declared_symbols():
     txt = open(os.path.join(ROOT, "include", "bp_lb.h")).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(bp_lb_\w+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(bp_(?:lb|serve)_\w+)\s*\(", txt)))
 
 
 def test_exports_every_declared_symbol(lib):
@@ -68,3 +68,14 @@ def test_create_rejects_bad_arguments(lib):
         with pytest.raises(binding.BpLbError) as e:
             binding.bp_lb_create(cap, items)
         assert e.value.status == binding.BP_ERANGE
+
+
+def test_serve_rejects_bad_arguments_before_any_device_work(lib):
+    for args in ((0, 4, 100, 2, 8, 16), (100, 0, 100, 2, 8, 16), (100, 4, 0, 2, 8, 16),
+                 (100, 4, 100, 0, 8, 16), (100, 4, 100, 17, 8, 16), (100, 4, 100, 2, 0, 16),
+                 (100, 4, 100, 2, 8, 16385)):
+        with pytest.raises(binding.BpLbError) as e:
+            binding.bp_serve_create(*args)
+        assert e.value.status == binding.BP_ERANGE
+    assert binding.lib().bp_serve_destroy(None) == binding.BP_OK
+    assert binding.lib().bp_serve_stats(None, None, None, None, None, None) == binding.BP_EINVAL
