@@ -185,8 +185,10 @@ def main():
     ap.add_argument("--plain-sample", type=int, default=1024)
     ap.add_argument("--cpu-budget", type=float, default=15.0,
                     help="CPU-seconds of oracle work for the cpu_baseline sample")
-    ap.add_argument("--workload", choices=("search", "large", "ragged", "serve"), default="search",
-                    help="search: the benchmark line (4096 search nodes); large: n=10^4, "
+    ap.add_argument("--workload", choices=("search", "plain", "large", "ragged", "serve"),
+                    default="search",
+                    help="search: the benchmark line (4096 search nodes); plain: one check of "
+                         "n=50, c=150 per call (bp_lb_eval), 10^4 calls; large: n=10^4, "
                          "c in {1e5, 1e6}, three size families, batches of 64; ragged: 10^4 "
                          "ragged search nodes in one CUDA-graph launch; serve: 256 simulated "
                          "searches against the continuous-batching server, offered rates swept")
@@ -469,6 +471,35 @@ def run_sweep(args):
                             "evals_per_s": evals / (tm / 1e3), "launch_shape": shape,
                             "roofline_frac": ops / (tm / 1e3) / peak})
                         print(json.dumps(out["results"][-1]), flush=True)
+        elif args.workload == "plain":
+            import oracle
+            rg = I.plain_single(seed=0)
+            w, c, k = rg.instance(0), int(rg.capacity[0]), int(rg.bins[0])
+            hp = B.bp_lb_create(c, 1024)
+            for _ in range(100):
+                B.bp_lb_eval(hp, w, k)
+            lat = []
+            for _ in range(10_000):
+                t0 = time.perf_counter()
+                B.bp_lb_eval(hp, w, k)
+                lat.append(time.perf_counter() - t0)
+            lat = np.array(lat) * 1e3
+            got = B.bp_lb_eval(hp, w, k)
+            B.bp_lb_destroy(hp)
+            orc = oracle.load()
+            t0 = time.perf_counter()
+            reps = 200
+            for _ in range(reps):
+                want = orc.lb(w, c, k)
+            t_orc = (time.perf_counter() - t0) / reps
+            evals = len(w) * sum(param_counts(c))
+            out["results"].append({
+                "n": len(w), "c": c, "bins": k, "bound": got[0], "matches_oracle": got == want[:3],
+                "checks_per_s": 1e3 / float(lat.mean()), "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "evals_per_check": evals,
+                "oracle_1thread_checks_per_s": 1.0 / t_orc,
+                "oracle_1thread_evals_per_s": evals / t_orc})
+            print(json.dumps(out["results"][-1]), flush=True)
         elif args.workload == "serve":
             from paper_2402_14821_gb300 import search_sim
             searches = search_sim.make_searches(count=256, seed=4)
