@@ -52,6 +52,10 @@ def ops_per_eval(d, c):
             4: 4 if c <= 65535 else 5,
             5: 5 if c <= 65535 else 6}[d]
 SM_COUNT_NOMINAL = 152
+# DRAM bytes (read + write) per search node of one eval_kernel launch over the
+# 4096-node batch, from ncu (dram__bytes_read.sum + dram__bytes_write.sum:
+# 8.83e6 bytes per launch); see profiles/eval_kernel_search_nodes.md.
+TRAFFIC_BYTES_PER_NODE = 8.83e6 / 4096
 
 
 def param_counts(c):
@@ -183,6 +187,8 @@ def main():
     ap.add_argument("--nodes", type=int, default=NODES,
                     help="search nodes per batch (4096 is the benchmark workload)")
     ap.add_argument("--plain-sample", type=int, default=1024)
+    ap.add_argument("--shape", type=int, default=-1,
+                    help="fix the batched launch shape (default: autotune on the batch)")
     ap.add_argument("--cpu-budget", type=float, default=15.0,
                     help="CPU-seconds of oracle work for the cpu_baseline sample")
     ap.add_argument("--workload", choices=("search", "plain", "large", "ragged", "serve"),
@@ -262,9 +268,13 @@ def main():
     h = B.bp_lb_create(CAP, 1 << 16)
     B.bp_lb_reserve(h, NODES)
     # autotuner: pick the launch shape on this batch (not timed)
-    shape, shape_ms = B.bp_lb_autotune_nodes(h, max_bins=max_bins, out_bound=out_b,
-                                             out_argmax=out_a, out_feasible=out_f, reps=2,
-                                             stream=stream, **t_in)
+    if args.shape >= 0:
+        shape, shape_ms = args.shape, []
+        B.bp_lb_set_launch_shape(h, B.MODE_NODES, shape)
+    else:
+        shape, shape_ms = B.bp_lb_autotune_nodes(h, max_bins=max_bins, out_bound=out_b,
+                                                 out_argmax=out_a, out_feasible=out_f, reps=2,
+                                                 stream=stream, **t_in)
 
     def step():
         B.bp_lb_eval_nodes(h, max_bins=max_bins, out_bound=out_b, out_argmax=out_a,
@@ -378,7 +388,8 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9,
-                     "unit": "Gop/s", "frac": achieved / peak_ops, "traffic": None,
+                     "unit": "Gop/s", "frac": achieved / peak_ops,
+                     "traffic": TRAFFIC_BYTES_PER_NODE * NODES,
                      "peak_basis": f"{sms} SMs x 4 SMSP x 32 lanes x {sm_mhz_max:.0f} MHz "
                                    "(integer issue, one warp instruction per clock per SMSP)",
                      "kernel": "eval_kernel (plan_kernel included in the timed step)"},
