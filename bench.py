@@ -53,9 +53,10 @@ def ops_per_eval(d, c):
             5: 5 if c <= 65535 else 6}[d]
 SM_COUNT_NOMINAL = 152
 # DRAM bytes (read + write) per search node of one eval_kernel launch over the
-# 4096-node batch, from ncu (dram__bytes_read.sum + dram__bytes_write.sum:
-# 8.83e6 bytes per launch); see profiles/eval_kernel_search_nodes.md.
-TRAFFIC_BYTES_PER_NODE = 8.83e6 / 4096
+# 4096-node batch, from ncu (dram__bytes_read.sum + dram__bytes_write.sum), or
+# None while the kernel has changed since the last capture; see
+# profiles/eval_kernel_search_nodes.md.
+TRAFFIC_BYTES_PER_NODE = None
 
 
 def param_counts(c):
@@ -72,16 +73,23 @@ def reduced_sizes(nd):
     return r
 
 
-def algorithmic_work(nd):
-    """(item-parameter evals, integer ops) of one batch."""
+def algorithmic_work(nd, algo=1):
+    """(item-parameter evals of the whole check, integer ops of the direct
+    kernel) of one batch: the direct kernel evaluates every (item, parameter)
+    pair of the DFFs the router leaves to it; MT, CCM1 and BJ1 go to the
+    prefix-count kernel where their tables fit (bp_lb_dff_route)."""
+    from paper_2402_14821_gb300 import binding as B
     r = reduced_sizes(nd)
     evals = ops = 0
     for j in range(nd.count):
-        c = int(nd.base.capacity[nd.node_base[j]])
+        b = int(nd.node_base[j])
+        c = int(nd.base.capacity[b])
+        L = int(nd.base.offsets[b + 1] - nd.base.offsets[b]) + int(nd.bins[j])
         cnt = param_counts(c)
         for d in range(6):
             evals += int(r[j]) * cnt[d]
-            ops += int(r[j]) * cnt[d] * ops_per_eval(d, c)
+            if B.bp_lb_dff_route(d, c, L, algo) == B.ALGO_DIRECT:
+                ops += int(r[j]) * cnt[d] * ops_per_eval(d, c)
     return evals, ops
 
 
@@ -294,6 +302,8 @@ def main():
     barrier()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
+    B.bp_lb_set_kernel_timing(h, True)   # events around each kernel of a step, on its stream
+    B.bp_lb_kernel_times(h)
     with ClockSampler(torch.cuda.current_device()) as clk:
         barrier()
         for e0, e1 in ev:
@@ -303,6 +313,10 @@ def main():
             e1.record(stream)
         barrier()
     step_ms = np.array([e0.elapsed_time(e1) for e0, e1 in ev])
+    ms_prefix, ms_direct, n_calls = B.bp_lb_kernel_times(h)
+    B.bp_lb_set_kernel_timing(h, False)
+    t_direct = ms_direct / max(1, n_calls)
+    t_prefix = ms_prefix / max(1, n_calls)
     t_step = float(step_ms.mean())
     if world > 1:
         import torch.distributed as dist
@@ -341,7 +355,10 @@ def main():
 
     # ---- plain path: one check per launch ------------------------------------
     w0, a0, c0, k0 = nd.node(0)
-    plain_shape, plain_us = B.bp_lb_autotune_plain_node(h, w0, a0, k0, reps=20)
+    plain_best, plain_us = B.bp_lb_autotune_plain_node(h, w0, a0, k0, reps=20)
+    nshapes = B.bp_lb_num_launch_shapes()
+    plain_shape = {"algorithm": ("direct", "prefix")[plain_best // nshapes],
+                   "shape": plain_best % nshapes}
     lat = []
     for j in range(min(args.plain_sample, NODES)):
         w, a, c, k = nd.node(j)
@@ -369,7 +386,7 @@ def main():
     sm_mhz_max = float(peaks.get("sm_max_mhz", 2070.0))
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     peak_ops = sms * 4 * 32 * sm_mhz_max * 1e6        # one warp instruction / clk / SMSP
-    achieved = ops / (t_step / 1e3)
+    achieved = ops / (t_direct / 1e3)
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -389,13 +406,16 @@ def main():
                 "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9,
                      "unit": "Gop/s", "frac": achieved / peak_ops,
-                     "traffic": TRAFFIC_BYTES_PER_NODE * NODES,
+                     "traffic": (TRAFFIC_BYTES_PER_NODE * NODES
+                                 if TRAFFIC_BYTES_PER_NODE is not None else None),
                      "peak_basis": f"{sms} SMs x 4 SMSP x 32 lanes x {sm_mhz_max:.0f} MHz "
                                    "(integer issue, one warp instruction per clock per SMSP)",
-                     "kernel": "eval_kernel (plan_kernel included in the timed step)"},
+                     "kernel": "eval_kernel (direct evaluation: VB2, RAD2, FS1 here), its own "
+                               "CUDA-event time per launch",
+                     "direct_kernel_ms": t_direct, "prefix_kernel_ms": t_prefix},
         "launch_shape": {"chosen": shape, "nt_t_g_minb": list(B.bp_lb_launch_shape_info(shape)),
                          "autotune_ms": [round(x, 4) for x in shape_ms]},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": 3 * args.steps,
         "clocks": clocks,
         "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"{cpu_m} of the {NODES} nodes (reduction + full bound), "
@@ -433,15 +453,17 @@ def _peak_ops():
     return sms * 4 * 32 * float(measured_peaks().get("sm_max_mhz", 2070.0)) * 1e6
 
 
-def ragged_work(rg):
-    """(evals, ops) of a ragged batch of reduced instances."""
+def ragged_work(rg, algo=1):
+    """(evals, direct-kernel ops) of a ragged batch of reduced instances."""
+    from paper_2402_14821_gb300 import binding as B
     evals = ops = 0
     for b in range(rg.count):
         c = int(rg.capacity[b])
         r = int(rg.offsets[b + 1] - rg.offsets[b])
         cnt = param_counts(c)
         evals += r * sum(cnt)
-        ops += r * sum(cnt[d] * ops_per_eval(d, c) for d in range(6))
+        ops += r * sum(cnt[d] * ops_per_eval(d, c) for d in range(6)
+                       if B.bp_lb_dff_route(d, c, r, algo) == B.ALGO_DIRECT)
     return evals, ops
 
 
@@ -474,13 +496,19 @@ def run_sweep(args):
                         shape, _ = B.bp_lb_autotune_batch(h, *t, ob, oa, reps=1)
                         step = lambda: B.bp_lb_eval_batch(h, *t, ob, oa, stream=stream)
                         step()
+                        B.bp_lb_set_kernel_timing(h, True)
+                        B.bp_lb_kernel_times(h)
                         ms = _time_steps(step, steps, flush, stream)
+                        kp, kd, kn = B.bp_lb_kernel_times(h)
+                        B.bp_lb_set_kernel_timing(h, False)
                         tm = float(ms.mean())
+                        td = kd / max(1, kn)
                         out["results"].append({
                             "c": c, "family": fam, "dtype": np.dtype(dt).name, "instances": 64,
                             "n": 10_000, "ms_per_batch": tm, "checks_per_s": 64 / (tm / 1e3),
                             "evals_per_s": evals / (tm / 1e3), "launch_shape": shape,
-                            "roofline_frac": ops / (tm / 1e3) / peak})
+                            "direct_kernel_ms": td, "prefix_kernel_ms": kp / max(1, kn),
+                            "roofline_frac": ops / (td / 1e3) / peak})
                         print(json.dumps(out["results"][-1]), flush=True)
         elif args.workload == "plain":
             import oracle
@@ -536,13 +564,7 @@ def run_sweep(args):
             B.bp_serve_destroy(srv)
         else:  # ragged
             nd = I.ragged_nodes(seed=3)
-            rg_r = reduced_sizes(nd)
-            evals = ops = 0
-            for j in range(nd.count):
-                c = int(nd.base.capacity[j])
-                cnt = param_counts(c)
-                evals += int(rg_r[j]) * sum(cnt)
-                ops += int(rg_r[j]) * sum(cnt[d] * ops_per_eval(d, c) for d in range(6))
+            evals, ops = algorithmic_work(nd)
             t_in = dict(base_offsets=_dev(nd.base.offsets, torch.int64),
                         base_sizes=_dev(nd.base.sizes, torch.int32),
                         base_capacity=_dev(nd.base.capacity, torch.int64),
@@ -573,7 +595,12 @@ def run_sweep(args):
             torch.cuda.synchronize()
             steps = max(3, min(args.steps, 20))
             ms_graph = _time_steps(g.replay, steps, flush, stream)
+            B.bp_lb_set_kernel_timing(h, True)
+            B.bp_lb_kernel_times(h)
             ms_direct = _time_steps(direct, steps, flush, stream)
+            kp, kd, kn = B.bp_lb_kernel_times(h)
+            B.bp_lb_set_kernel_timing(h, False)
+            td = kd / max(1, kn)
             tm = float(ms_graph.mean())
             out["results"].append({
                 "instances": nd.count, "ms_per_batch_graph": tm,
@@ -581,7 +608,8 @@ def run_sweep(args):
                 "checks_per_s": nd.count / (tm / 1e3), "evals_per_s": evals / (tm / 1e3),
                 "evals_per_batch": evals, "launch_shape": shape,
                 "autotune_ms": [round(x, 3) for x in shape_ms],
-                "roofline_frac": ops / (tm / 1e3) / peak})
+                "direct_kernel_ms": td, "prefix_kernel_ms": kp / max(1, kn),
+                "roofline_frac": ops / (td / 1e3) / peak})
             print(json.dumps(out["results"][-1]), flush=True)
     out["clocks"] = clk.summary()
     B.bp_lb_destroy(h)

@@ -235,6 +235,34 @@ int bp_lb_eval_batch_noalloc(int32_t B, const int64_t *d_offsets,
                              bp_argmax_t *d_out_argmax,
                              uint8_t *d_out_feasible, void *stream);
 
+/* ---- evaluation algorithm ------------------------------------------------ */
+
+/* BP_ALGO_DIRECT evaluates every (DFF, lambda) pair item by item (Alg. 2's
+ * loops).  BP_ALGO_PREFIX (the default) computes the same bounds exactly but
+ * evaluates MT, CCM1 and BJ1 from value-indexed prefix counts and sums built
+ * in shared memory (O(1), O(c / lambda) and O(c / lambda) lookups per
+ * parameter instead of one evaluation per item) wherever those tables fit
+ * (c up to 12286 for BJ1, 49150 for MT and CCM1, and reduced sizes summing to
+ * less than 2^31); the other DFFs, and those three beyond the limits, stay on
+ * the direct path.  Results are identical either way. */
+#define BP_ALGO_DIRECT 0
+#define BP_ALGO_PREFIX 1
+
+/* Selects the algorithm of a handle.  Errors: BP_EINVAL, BP_ERANGE. */
+int bp_lb_set_algorithm(bp_lb_t *h, int32_t algo);
+
+/* The handle's algorithm (batched modes), or -1 for a NULL handle. */
+int bp_lb_get_algorithm(bp_lb_t *h);
+
+/* Measurement aid: with timing on, every batched call records CUDA events
+ * on its stream around its prefix-count launch and its direct launch (not
+ * for use under stream capture).  bp_lb_kernel_times waits for the events
+ * recorded since the previous query and returns the total milliseconds of
+ * each kernel and the number of calls (any pointer may be NULL). */
+int bp_lb_set_kernel_timing(bp_lb_t *h, int32_t on);
+int bp_lb_kernel_times(bp_lb_t *h, double *ms_prefix, double *ms_direct,
+                       int64_t *calls);
+
 /* ---- launch shapes and autotuning ---------------------------------------- */
 
 /* Input modes of the evaluation kernel, for the launch-shape calls below. */
@@ -295,10 +323,12 @@ int bp_lb_autotune_nodes(bp_lb_t *h, int32_t B, int32_t num_base,
                          int32_t *best_shape, void *stream);
 
 /* Plain-path autotuner: times `reps` bp_lb_eval_node calls (host wall
- * clock; each call synchronises) with every launch shape on the given node
- * and keeps the fastest for BP_MODE_PLAIN_NODES.  us_per_shape and
- * best_shape may be NULL.  Errors: as bp_lb_eval_node, BP_EINVAL for
- * reps < 1. */
+ * clock; each call synchronises) with every algorithm and launch shape on the
+ * given node and keeps the fastest for the plain node path.  us_per_shape
+ * (may be NULL) receives 2 * bp_lb_num_launch_shapes() values: first every
+ * shape with BP_ALGO_DIRECT, then every shape with BP_ALGO_PREFIX;
+ * *best_shape (may be NULL) the winning index into that list.
+ * Errors: as bp_lb_eval_node, BP_EINVAL for reps < 1. */
 int bp_lb_autotune_plain_node(bp_lb_t *h, const int32_t *w, const int32_t *assign,
                               int64_t n, int64_t bins, int32_t reps,
                               float *us_per_shape, int32_t *best_shape);
@@ -392,6 +422,12 @@ int bp_lb_debug_params(bp_lb_t *h, const int32_t *d_sizes, int64_t n,
  * range), and the range itself; host-only helper, no device work.
  * Returns -1 for a bad d or c. */
 int64_t bp_lb_param_count(int32_t d, int64_t c, int64_t *lo, int64_t *hi);
+
+/* Which path evaluates DFF d of an instance with capacity c whose item
+ * stream has stream_len entries (reduced items, or base items plus bins for a
+ * search node) under algorithm `algo`: BP_ALGO_PREFIX or BP_ALGO_DIRECT;
+ * -1 for bad arguments.  Host-only, for accounting. */
+int bp_lb_dff_route(int32_t d, int64_t c, int64_t stream_len, int32_t algo);
 
 /* Host-side exhaustive self-check of the exact division used by the kernels
  * (Granlund-Montgomery multiply-high division by invariant integers):

@@ -76,6 +76,12 @@ def _bind(lib):
         "bp_lb_eval_batch_noalloc": (ctypes.c_int, [_c_i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
         "bp_lb_autotune_plain_node": (ctypes.c_int, [_vp, _vp, _vp, _c_i64, _c_i64, _c_i32, _vp,
                                                      P(_c_i32)]),
+        "bp_lb_set_algorithm": (ctypes.c_int, [_vp, _c_i32]),
+        "bp_lb_get_algorithm": (ctypes.c_int, [_vp]),
+        "bp_lb_set_kernel_timing": (ctypes.c_int, [_vp, _c_i32]),
+        "bp_lb_dff_route": (ctypes.c_int, [_c_i32, _c_i64, _c_i64, _c_i32]),
+        "bp_lb_kernel_times": (ctypes.c_int, [_vp, P(ctypes.c_double), P(ctypes.c_double),
+                                              P(_c_i64)]),
         "bp_serve_create": (ctypes.c_int, [_c_i64, _c_i32, _c_i64, _c_i32, _c_i32, _c_i64, P(_vp)]),
         "bp_serve_destroy": (ctypes.c_int, [_vp]),
         "bp_serve_register": (ctypes.c_int, [_vp, _vp, _c_i64, _c_i64, P(_c_i32)]),
@@ -109,7 +115,10 @@ EXPORTED = ("bp_lb_strerror", "bp_lb_create", "bp_lb_destroy", "bp_lb_reserve", 
             "bp_lb_set_launch_shape", "bp_lb_get_launch_shape", "bp_lb_autotune_batch",
             "bp_lb_autotune_nodes", "bp_lb_eval_batch_noalloc", "bp_lb_autotune_plain_node",
             "bp_serve_create", "bp_serve_destroy", "bp_serve_register", "bp_serve_submit",
-            "bp_serve_poll", "bp_serve_stats")
+            "bp_serve_poll", "bp_serve_stats", "bp_lb_set_algorithm", "bp_lb_get_algorithm",
+            "bp_lb_set_kernel_timing", "bp_lb_kernel_times", "bp_lb_dff_route")
+
+ALGO_DIRECT, ALGO_PREFIX = 0, 1
 
 NOALLOC_MAX_BATCH = 4096
 
@@ -279,6 +288,31 @@ def bp_lb_param_count(d: int, c: int):
     return n, lo.value, hi.value
 
 
+def bp_lb_set_algorithm(h, algo: int):
+    _check(lib().bp_lb_set_algorithm(h, int(algo)), "bp_lb_set_algorithm")
+
+
+def bp_lb_get_algorithm(h) -> int:
+    return lib().bp_lb_get_algorithm(h)
+
+
+def bp_lb_set_kernel_timing(h, on: bool):
+    _check(lib().bp_lb_set_kernel_timing(h, int(bool(on))), "bp_lb_set_kernel_timing")
+
+
+def bp_lb_kernel_times(h):
+    """(ms in prefix kernels, ms in direct kernels, calls) since the last query."""
+    p, d, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    _check(lib().bp_lb_kernel_times(h, ctypes.byref(p), ctypes.byref(d), ctypes.byref(n)),
+           "bp_lb_kernel_times")
+    return p.value, d.value, n.value
+
+
+def bp_lb_dff_route(d: int, c: int, stream_len: int, algo: int = 1) -> int:
+    """ALGO_PREFIX or ALGO_DIRECT: the path that evaluates DFF d of such an instance."""
+    return lib().bp_lb_dff_route(int(d), int(c), int(stream_len), int(algo))
+
+
 def bp_lb_num_launch_shapes() -> int:
     return lib().bp_lb_num_launch_shapes()
 
@@ -337,11 +371,12 @@ def bp_lb_autotune_nodes(h, base_offsets, base_sizes, base_capacity, node_base, 
 
 
 def bp_lb_autotune_plain_node(h, w, assign, bins: int, reps: int = 20):
-    """Times the plain node path with every launch shape; keeps the fastest.
-    Returns (best shape, [microseconds per call per shape])."""
+    """Times the plain node path with every algorithm and launch shape; keeps the
+    fastest.  Returns (best index, [microseconds per call]): index a * shapes + s
+    for algorithm a (0 direct, 1 prefix) and shape s."""
     wa = np.ascontiguousarray(np.asarray(w, dtype=np.int32))
     aa = np.ascontiguousarray(np.asarray(assign, dtype=np.int32))
-    n = bp_lb_num_launch_shapes()
+    n = 2 * bp_lb_num_launch_shapes()
     us = (ctypes.c_float * n)()
     best = ctypes.c_int32()
     _check(lib().bp_lb_autotune_plain_node(h, wa.ctypes.data, aa.ctypes.data, len(wa), int(bins),

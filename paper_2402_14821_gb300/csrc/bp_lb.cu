@@ -12,6 +12,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <array>
+#include <vector>
 
 #include "../../include/bp_lb.h"
 #include "bp_lb_core.cuh"
@@ -57,6 +59,14 @@ struct bp_lb {
   // batch scratch
   int32_t cap_batch = 0;
   int64_t *d_tile_start = nullptr;
+  int64_t *d_ptile_start = nullptr;  // prefix-kernel tile table
+  int32_t prefix_on = 1;             // batched modes: BP_ALGO_PREFIX (default) or DIRECT
+  int32_t plain_prefix_on = 1;       // plain modes
+  // optional per-kernel timing of batched calls (events around each launch)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::array<cudaEvent_t, 3>> ev_pending;
+  size_t ev_next = 0;
   unsigned long long *d_keys = nullptr;
   unsigned int *d_done = nullptr;
   unsigned long long *d_work = nullptr;
@@ -118,13 +128,16 @@ int grow_batch(bp_lb *h, int32_t B) {
   if (B <= h->cap_batch) return BP_OK;
   int32_t cap = std::max<int32_t>(B, 1024);
   cudaFree(h->d_tile_start);
+  cudaFree(h->d_ptile_start);
   cudaFree(h->d_keys);
   cudaFree(h->d_done);
   h->d_tile_start = nullptr;
+  h->d_ptile_start = nullptr;
   h->d_keys = nullptr;
   h->d_done = nullptr;
   h->cap_batch = 0;
   BP_CHECK(cudaMalloc(&h->d_tile_start, sizeof(int64_t) * ((size_t)cap + 1)));
+  BP_CHECK(cudaMalloc(&h->d_ptile_start, sizeof(int64_t) * ((size_t)cap + 1)));
   BP_CHECK(cudaMalloc(&h->d_keys, sizeof(unsigned long long) * (size_t)cap));
   BP_CHECK(cudaMalloc(&h->d_done, sizeof(unsigned int) * (size_t)cap));
   BP_CHECK(cudaMemset(h->d_keys, 0, sizeof(unsigned long long) * (size_t)cap));
@@ -140,6 +153,28 @@ EvalArgs blank_args() {
   return A;
 }
 
+// Dynamic shared memory of the prefix-count kernel.
+size_t prefix_smem(int mode, int64_t max_bins) {
+  return (size_t)kPrefixSmemBytes + (mode == kSrcNodes ? sizeof(uint32_t) * (size_t)max_bins : 0);
+}
+
+int launch_prefix(int mode, unsigned grid, size_t smem, cudaStream_t st, EvalArgs &A) {
+  void *args[] = {&A};
+  return cuda_status(cudaLaunchKernel((const void *)prefix_fn(mode), dim3(grid),
+                                      dim3(kPrefixNT), args, smem, st));
+}
+
+// Next event of the timing pool (grown on demand; timing is for measurement
+// runs, not for stream capture).
+cudaEvent_t next_event(bp_lb *h) {
+  if (h->ev_next == h->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    h->ev_pool.push_back(e);
+  }
+  return h->ev_pool[h->ev_next++];
+}
+
 template <int MODE>
 int launch_batch(bp_lb *h, EvalArgs A, size_t smem, cudaStream_t st) {
   if (A.B == 0) return BP_OK;
@@ -149,12 +184,37 @@ int launch_batch(bp_lb *h, EvalArgs A, size_t smem, cudaStream_t st) {
   A.keys = h->d_keys;
   A.done = h->d_done;
   A.work = h->d_work;
+  A.prefix_on = h->prefix_on;
+  A.ptile_start = h->d_ptile_start;
+  A.pwork = h->d_work + 1;
+  A.plpt = kPrefixLPTBatch;
   const int shape = h->shape[MODE];
   const int occ = occupancy(h, MODE, smem);
   if (occ <= 0) return BP_ECUDA;
-  plan_kernel<MODE><<<1, 1024, 0, st>>>(A, shape_lpt(shape), h->d_tile_start);
+  plan_kernel<MODE><<<1, 1024, 0, st>>>(A, shape_lpt(shape), h->d_tile_start, h->d_ptile_start);
   BP_CHECK(cudaGetLastError());
-  return launch_eval(shape, MODE, (unsigned)(h->num_sms * occ), smem, st, A);
+  std::array<cudaEvent_t, 3> ev = {nullptr, nullptr, nullptr};
+  if (h->timing) {
+    for (auto &e : ev)
+      if (!(e = next_event(h))) return BP_ECUDA;
+    BP_CHECK(cudaEventRecord(ev[0], st));
+  }
+  if (h->prefix_on) {
+    // the prefix-count tiles first (short), then the persistent direct kernel
+    const size_t ps = prefix_smem(MODE, A.max_bins);
+    int pocc = 0;
+    BP_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pocc, (const void *)prefix_fn(MODE),
+                                                           kPrefixNT, ps));
+    if (pocc <= 0) return BP_ECUDA;
+    BP_CHECK_STATUS(launch_prefix(MODE, (unsigned)(h->num_sms * pocc), ps, st, A));
+  }
+  if (h->timing) BP_CHECK(cudaEventRecord(ev[1], st));
+  BP_CHECK_STATUS(launch_eval(shape, MODE, (unsigned)(h->num_sms * occ), smem, st, A));
+  if (h->timing) {
+    BP_CHECK(cudaEventRecord(ev[2], st));
+    h->ev_pending.push_back(ev);
+  }
+  return BP_OK;
 }
 
 // Times `reps` calls of `call` per launch shape with CUDA events on `st`,
@@ -238,10 +298,16 @@ int bp_lb_create(int64_t capacity, int64_t max_items, bp_lb_t **out) {
     if ((st = cuda_status(cudaMallocHost(&h->h_out, sizeof(PlainOut)))) != BP_OK) break;
     if ((st = cuda_status(cudaMalloc(&h->d_key1, sizeof(unsigned long long)))) != BP_OK) break;
     if ((st = cuda_status(cudaMalloc(&h->d_done1, sizeof(unsigned int)))) != BP_OK) break;
-    if ((st = cuda_status(cudaMalloc(&h->d_work, sizeof(unsigned long long)))) != BP_OK) break;
+    if ((st = cuda_status(cudaMalloc(&h->d_work, 2 * sizeof(unsigned long long)))) != BP_OK) break;
     if ((st = cuda_status(cudaMemset(h->d_key1, 0, sizeof(unsigned long long)))) != BP_OK) break;
     if ((st = cuda_status(cudaMemset(h->d_done1, 0, sizeof(unsigned int)))) != BP_OK) break;
-    if ((st = cuda_status(cudaMemset(h->d_work, 0, sizeof(unsigned long long)))) != BP_OK) break;
+    if ((st = cuda_status(cudaMemset(h->d_work, 0, 2 * sizeof(unsigned long long)))) != BP_OK)
+      break;
+    for (int mode = 0; mode < 3 && st == BP_OK; ++mode)
+      st = cuda_status(cudaFuncSetAttribute((const void *)prefix_fn(mode),
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)prefix_smem(mode, kMaxNodeBins)));
+    if (st != BP_OK) break;
     // the plain node path may use the full on-chip bin table
     const size_t smem_nodes = eval_smem<kSrcNodes>(kMaxNodeBins);
     for (int sh = 0; sh < kNumShapes && st == BP_OK; ++sh)
@@ -276,8 +342,10 @@ int bp_lb_destroy(bp_lb_t *h) {
   cudaFree(h->d_done1);
   cudaFree(h->d_work);
   cudaFree(h->d_tile_start);
+  cudaFree(h->d_ptile_start);
   cudaFree(h->d_keys);
   cudaFree(h->d_done);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
   return BP_OK;
@@ -304,7 +372,12 @@ static EvalArgs plain_args(bp_lb *h, int64_t n, int64_t bins, int mode) {
   A.out_argmax = &h->d_out->arg;
   A.out_feasible = &h->d_out->feasible;
   A.tile_start = nullptr;
-  A.single_tiles = tiles_for(h->capacity, shape_lpt(h->shape[mode]));  // mode: a plain mode
+  // mode is a plain mode; the sum bound is the stream length times c
+  const int64_t sb = (mode == kModePlainNodes ? n + bins : n) * h->capacity;
+  A.prefix_on = h->plain_prefix_on;
+  A.plpt = kPrefixLPTSingle;
+  A.single_tiles = direct_tiles(h->capacity, shape_lpt(h->shape[mode]), sb, A.prefix_on);
+  A.single_ptiles = prefix_tiles(h->capacity, A.plpt, sb, A.prefix_on);
   A.single_c = h->capacity;
   A.single_k = bins;
   A.single_n = n;
@@ -328,6 +401,9 @@ int bp_lb_eval(bp_lb_t *h, const int32_t *sizes, int64_t n, int64_t bins, int64_
   }
   EvalArgs A = plain_args(h, n, bins, kModePlainRagged);
   A.sizes = h->d_items;
+  if (A.single_ptiles > 0)
+    BP_CHECK_STATUS(launch_prefix(kSrcRaggedI32, (unsigned)A.single_ptiles,
+                                  prefix_smem(kSrcRaggedI32, 0), h->stream, A));
   BP_CHECK_STATUS(launch_eval(h->shape[kModePlainRagged], kSrcRaggedI32, (unsigned)A.single_tiles,
                               eval_smem<kSrcRaggedI32>(0), h->stream, A));
   return plain_finish(h, out_bound, out_argmax);
@@ -349,6 +425,9 @@ int bp_lb_eval_node(bp_lb_t *h, const int32_t *w, const int32_t *assign, int64_t
   A.base_sizes = h->d_items;
   A.assign = h->d_assign;
   A.max_bins = (int32_t)bins;
+  if (A.single_ptiles > 0)
+    BP_CHECK_STATUS(launch_prefix(kSrcNodes, (unsigned)A.single_ptiles, prefix_smem(kSrcNodes, bins),
+                                  h->stream, A));
   BP_CHECK_STATUS(launch_eval(h->shape[kModePlainNodes], kSrcNodes, (unsigned)A.single_tiles,
                               eval_smem<kSrcNodes>(bins), h->stream, A));
   return plain_finish(h, out_bound, out_argmax);
@@ -470,6 +549,43 @@ int bp_lb_debug_params(bp_lb_t *h, const int32_t *d_sizes, int64_t n, int64_t c,
   return BP_OK;
 }
 
+int bp_lb_set_algorithm(bp_lb_t *h, int32_t algo) {
+  if (!h) return BP_EINVAL;
+  if (algo != BP_ALGO_DIRECT && algo != BP_ALGO_PREFIX) return BP_ERANGE;
+  h->prefix_on = h->plain_prefix_on = algo == BP_ALGO_PREFIX;
+  return BP_OK;
+}
+
+int bp_lb_set_kernel_timing(bp_lb_t *h, int32_t on) {
+  if (!h) return BP_EINVAL;
+  h->timing = on != 0;
+  return BP_OK;
+}
+
+int bp_lb_kernel_times(bp_lb_t *h, double *ms_prefix, double *ms_direct, int64_t *calls) {
+  if (!h) return BP_EINVAL;
+  double p = 0.0, d = 0.0;
+  for (const auto &ev : h->ev_pending) {
+    BP_CHECK(cudaEventSynchronize(ev[2]));
+    float a = 0.f, b = 0.f;
+    BP_CHECK(cudaEventElapsedTime(&a, ev[0], ev[1]));
+    BP_CHECK(cudaEventElapsedTime(&b, ev[1], ev[2]));
+    p += a;
+    d += b;
+  }
+  if (ms_prefix) *ms_prefix = p;
+  if (ms_direct) *ms_direct = d;
+  if (calls) *calls = (int64_t)h->ev_pending.size();
+  h->ev_pending.clear();
+  h->ev_next = 0;
+  return BP_OK;
+}
+
+int bp_lb_get_algorithm(bp_lb_t *h) {
+  if (!h) return -1;
+  return h->prefix_on ? BP_ALGO_PREFIX : BP_ALGO_DIRECT;
+}
+
 int bp_lb_num_launch_shapes(void) { return kNumShapes; }
 
 int bp_lb_launch_shape_info(int32_t id, int32_t *nt, int32_t *t, int32_t *g, int32_t *min_blocks) {
@@ -497,29 +613,34 @@ int bp_lb_autotune_plain_node(bp_lb_t *h, const int32_t *w, const int32_t *assig
                               int64_t bins, int32_t reps, float *us_per_shape,
                               int32_t *best_shape) {
   if (!h || reps < 1) return BP_EINVAL;
-  int best = h->shape[kModePlainNodes];
+  int best = h->shape[kModePlainNodes], best_algo = h->plain_prefix_on;
   double best_us = -1.0;
-  for (int s = 0; s < kNumShapes; ++s) {
-    h->shape[kModePlainNodes] = s;
-    int64_t b;
-    int st = bp_lb_eval_node(h, w, assign, n, bins, &b, nullptr);  // warm-up
-    if (st != BP_OK && st != BP_ERANGE) {
-      h->shape[kModePlainNodes] = best;
-      return st;
-    }
-    const auto t0 = std::chrono::steady_clock::now();
-    for (int r = 0; r < reps; ++r) bp_lb_eval_node(h, w, assign, n, bins, &b, nullptr);
-    const double us =
-        std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count() /
-        reps;
-    if (us_per_shape) us_per_shape[s] = (float)us;
-    if (best_us < 0 || us < best_us) {
-      best_us = us;
-      best = s;
+  for (int algo = 0; algo < 2; ++algo) {
+    h->plain_prefix_on = algo;
+    for (int s = 0; s < kNumShapes; ++s) {
+      h->shape[kModePlainNodes] = s;
+      int64_t b;
+      int st = bp_lb_eval_node(h, w, assign, n, bins, &b, nullptr);  // warm-up
+      if (st != BP_OK && st != BP_ERANGE) {
+        h->shape[kModePlainNodes] = best;
+        h->plain_prefix_on = best_algo;
+        return st;
+      }
+      const auto t0 = std::chrono::steady_clock::now();
+      for (int r = 0; r < reps; ++r) bp_lb_eval_node(h, w, assign, n, bins, &b, nullptr);
+      const double us = std::chrono::duration<double, std::micro>(
+                            std::chrono::steady_clock::now() - t0).count() / reps;
+      if (us_per_shape) us_per_shape[algo * kNumShapes + s] = (float)us;
+      if (best_us < 0 || us < best_us) {
+        best_us = us;
+        best = s;
+        best_algo = algo;
+      }
     }
   }
   h->shape[kModePlainNodes] = best;
-  if (best_shape) *best_shape = best;
+  h->plain_prefix_on = best_algo;
+  if (best_shape) *best_shape = best_algo * kNumShapes + best;
   return BP_OK;
 }
 
@@ -550,6 +671,12 @@ int bp_lb_autotune_nodes(bp_lb_t *h, int32_t B, int32_t num_base, const int64_t 
                             d_node_base, d_assign_offsets, d_assign, d_bins, max_bins, d_out_bound,
                             d_out_argmax, d_out_feasible, stream);
   });
+}
+
+int bp_lb_dff_route(int32_t d, int64_t c, int64_t stream_len, int32_t algo) {
+  if (d < 0 || d >= kNumDff || c < 1 || c > kMaxCapacity || stream_len < 0) return -1;
+  return prefix_handles(d, c, stream_len * c, algo == BP_ALGO_PREFIX) ? BP_ALGO_PREFIX
+                                                                       : BP_ALGO_DIRECT;
 }
 
 int64_t bp_lb_param_count(int32_t d, int64_t c, int64_t *lo, int64_t *hi) {

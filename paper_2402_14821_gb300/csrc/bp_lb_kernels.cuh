@@ -62,7 +62,43 @@ struct EvalArgs {
   unsigned int *done;         // [B] finished-tile counters, zero between calls
   unsigned long long *work;   // [1] next tile (persistent mode), nullptr otherwise
   uint32_t one;               // always 1 (see add_if_ge in bp_lb_eval.cuh)
+  int32_t prefix_on;          // route MT/CCM1/BJ1 to the prefix-count kernel where it fits
+  const int64_t *ptile_start; // [B+1] prefix-kernel tile table, or nullptr (single instance)
+  int64_t single_ptiles;
+  unsigned long long *pwork;  // [1] next prefix tile (persistent mode)
+  int64_t plpt;               // parameters per prefix-kernel tile
 };
+
+// Shared-memory budget of the prefix-count tables (bytes), and the number of
+// parameters per prefix-kernel tile for batches (long tiles amortise building
+// the tables) and for a single check (short tiles spread it over more SMs).
+constexpr int64_t kPrefixSmemBytes = 98304;
+constexpr int64_t kPrefixLPTBatch = 16384;
+constexpr int64_t kPrefixLPTSingle = 1024;
+
+// Whether the prefix-count kernel evaluates DFF d of an instance with
+// capacity c whose reduced sizes sum to at most sum_bound (its tables must fit
+// in shared memory and its sums in 32 bits); otherwise the direct kernel does.
+BPLB_HD bool prefix_handles(int d, int64_t c, int64_t sum_bound, int32_t on) {
+  if (!on || sum_bound >= (int64_t(1) << 31)) return false;
+  if (d == kMT || d == kCCM1) return 4 * ((c - 1) / 2 + 2) <= kPrefixSmemBytes;
+  if (d == kBJ1) return 8 * (c + 2) <= kPrefixSmemBytes;
+  return false;
+}
+
+// Tiles of the direct kernel (lpt parameters each) and of the prefix kernel.
+BPLB_HD int64_t direct_tiles(int64_t c, int64_t lpt, int64_t sum_bound, int32_t on) {
+  int64_t t = 0;
+  for (int d = 0; d < kNumDff; ++d)
+    if (!prefix_handles(d, c, sum_bound, on)) t += (param_count(d, c) + lpt - 1) / lpt;
+  return t;
+}
+BPLB_HD int64_t prefix_tiles(int64_t c, int64_t lpt, int64_t sum_bound, int32_t on) {
+  int64_t t = 0;
+  for (int d = 0; d < kNumDff; ++d)
+    if (prefix_handles(d, c, sum_bound, on)) t += (param_count(d, c) + lpt - 1) / lpt;
+  return t;
+}
 
 // Instance view resolved per tile.
 struct InstView {
@@ -133,23 +169,60 @@ __device__ __forceinline__ void write_result(const EvalArgs &A, int64_t b, unsig
 // (exclusive scan of tiles per instance; 0 tiles and an error result for an
 // invalid one), clears keys/done and resets the work counter.
 // ---------------------------------------------------------------------------
+// Block-wide exclusive scan step of plan_kernel: returns the exclusive prefix
+// of v within this pass plus *carry, and advances *carry by the pass total.
+__device__ __forceinline__ int64_t plan_scan(int64_t v, int64_t *s_warp, int64_t *carry) {
+  int64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if ((int)lane_id() >= o) x += y;
+  }
+  if (lane_id() == 31) s_warp[threadIdx.x >> 5] = x;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int nw = blockDim.x >> 5;
+    int64_t wv = (int)threadIdx.x < nw ? s_warp[threadIdx.x] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xFFFFFFFFu, wv, o);
+      if ((int)threadIdx.x >= o) wv += y;
+    }
+    s_warp[threadIdx.x] = wv;  // inclusive warp prefix
+  }
+  __syncthreads();
+  const int64_t warp_excl = (threadIdx.x >> 5) ? s_warp[(threadIdx.x >> 5) - 1] : 0;
+  const int64_t excl = *carry + warp_excl + x - v;
+  const int64_t total = s_warp[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  if (threadIdx.x == 0) *carry += total;
+  __syncthreads();
+  return excl;
+}
+
+// plan_kernel: one block.  Validates every instance and writes the tile
+// tables of the direct kernel (tile_start[0..B]) and of the prefix kernel
+// (ptile_start[0..B]); an invalid instance gets no tiles and an error result.
+// Clears keys/done and resets both work counters.
 template <int MODE>
-__global__ void __launch_bounds__(1024) plan_kernel(EvalArgs A, int64_t lpt, int64_t *tile_start) {
+__global__ void __launch_bounds__(1024)
+    plan_kernel(EvalArgs A, int64_t lpt, int64_t *tile_start, int64_t *ptile_start) {
   __shared__ int64_t s_warp[32];
-  __shared__ int64_t s_carry;
+  __shared__ int64_t s_carry[2];
   if (threadIdx.x == 0) {
-    s_carry = 0;
+    s_carry[0] = s_carry[1] = 0;
     *A.work = 0ull;
+    if (A.pwork) *A.pwork = 0ull;
   }
   __syncthreads();
   for (int64_t b0 = 0; b0 < A.B; b0 += blockDim.x) {
     const int64_t b = b0 + threadIdx.x;
-    int64_t tiles = 0;
+    int64_t tiles = 0, ptiles = 0;
     if (b < A.B) {
       A.keys[b] = 0ull;
       A.done[b] = 0u;
       bool ok;
-      int64_t c;
+      int64_t c, L;
       if (MODE == kSrcNodes) {
         const int32_t base = A.node_base[b];
         ok = base >= 0 && base < A.num_base;
@@ -159,42 +232,30 @@ __global__ void __launch_bounds__(1024) plan_kernel(EvalArgs A, int64_t lpt, int
         const int64_t k = A.bins[b];
         ok = ok && c >= 1 && c <= kMaxCapacity && n >= 0 && n <= kMaxItems && na == n && k >= 0 &&
              k <= A.max_bins;
+        L = n + k;
       } else {
         c = A.capacity[b];
-        const int64_t r = A.offsets[b + 1] - A.offsets[b];
-        ok = c >= 1 && c <= kMaxCapacity && r >= 0 && r <= kMaxItems && A.bins[b] >= 0;
+        L = A.offsets[b + 1] - A.offsets[b];
+        ok = c >= 1 && c <= kMaxCapacity && L >= 0 && L <= kMaxItems && A.bins[b] >= 0;
       }
-      if (ok) tiles = tiles_for(c, lpt);
-      else write_error(A, b);
-    }
-    // block-wide inclusive scan of `tiles`
-    int64_t v = tiles;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int64_t x = __shfl_up_sync(0xFFFFFFFFu, v, o);
-      if ((int)lane_id() >= o) v += x;
-    }
-    if (lane_id() == 31) s_warp[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      const int nw = blockDim.x >> 5;
-      int64_t wv = (int)threadIdx.x < nw ? s_warp[threadIdx.x] : 0;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int64_t x = __shfl_up_sync(0xFFFFFFFFu, wv, o);
-        if ((int)threadIdx.x >= o) wv += x;
+      if (ok) {
+        tiles = direct_tiles(c, lpt, L * c, A.prefix_on);
+        ptiles = prefix_tiles(c, A.plpt, L * c, A.prefix_on);
+      } else {
+        write_error(A, b);
       }
-      s_warp[threadIdx.x] = wv;  // inclusive warp prefix
     }
-    __syncthreads();
-    const int64_t warp_excl = (threadIdx.x >> 5) ? s_warp[(threadIdx.x >> 5) - 1] : 0;
-    const int64_t incl = s_carry + warp_excl + v;
-    if (b < A.B) tile_start[b] = incl - tiles;
-    __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) s_carry = incl;
-    __syncthreads();
+    const int64_t e0 = plan_scan(tiles, s_warp, &s_carry[0]);
+    const int64_t e1 = plan_scan(ptiles, s_warp, &s_carry[1]);
+    if (b < A.B) {
+      tile_start[b] = e0;
+      if (ptile_start) ptile_start[b] = e1;
+    }
   }
-  if (threadIdx.x == 0) tile_start[A.B] = s_carry;
+  if (threadIdx.x == 0) {
+    tile_start[A.B] = s_carry[0];
+    if (ptile_start) ptile_start[A.B] = s_carry[1];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -233,6 +294,48 @@ __device__ __forceinline__ bool fetch_item(const EvalArgs &A, const InstView &I,
 template <int MODE>
 __device__ __forceinline__ int64_t stream_len(const InstView &I) {
   return MODE == kSrcNodes ? I.n + I.k : I.n;
+}
+
+// Upper bound on the sum of an instance's reduced sizes (its stream length
+// times c), the quantity prefix_handles tests; plan_kernel uses the same.
+template <int MODE>
+__device__ __forceinline__ int64_t sum_bound(const InstView &I) {
+  return stream_len<MODE>(I) * I.c;
+}
+
+// Tiles of instance b over both kernels (the finished-tile ticket target).
+__device__ __forceinline__ int64_t instance_tiles(const EvalArgs &A, int64_t b) {
+  if (!A.tile_start) return A.single_tiles + A.single_ptiles;
+  const int64_t nt = A.tile_start[b + 1] - A.tile_start[b];
+  return A.ptile_start ? nt + (A.ptile_start[b + 1] - A.ptile_start[b]) : nt;
+}
+
+// Block max of the threads' keys, one atomicMax into the instance's slot, and
+// the finished-tile ticket: the CTA finishing the instance's last tile writes
+// its outputs and clears the slot.
+template <int NT>
+__device__ void fold_and_finalize(const EvalArgs &A, int64_t b, unsigned long long best, bool err,
+                                  int64_t ntiles, const InstView &I,
+                                  unsigned long long *warp_key) {
+  const int tid = threadIdx.x;
+  best = warp_max_u64(best);
+  if (lane_id() == 0) warp_key[tid >> 5] = best;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long m = 0ull;
+    for (int w = 0; w < NT / 32; ++w) m = warp_key[w] > m ? warp_key[w] : m;
+    if (m && !err) atomicMax(&A.keys[b], m);
+    __threadfence();
+    const unsigned int ticket = atomicAdd(&A.done[b], 1u);
+    if ((int64_t)ticket == ntiles - 1) {
+      __threadfence();
+      const unsigned long long key = atomicExch(&A.keys[b], 0ull);
+      A.done[b] = 0u;
+      if (err) write_error(A, b);
+      else write_result(A, b, key, I.c, I.k);
+    }
+  }
+  __syncthreads();
 }
 
 // Local (per-thread) instance sums, reduced over the block once per tile.
@@ -533,7 +636,9 @@ __device__ void process_tile(const EvalArgs &A, int64_t b, int64_t lt, int64_t n
   const int64_t c = I.c;
   int d = 0;
   int64_t rem = lt;
+  const int64_t sb = sum_bound<MODE>(I);
   for (d = 0; d < kNumDff; ++d) {
+    if (prefix_handles(d, c, sb, A.prefix_on)) continue;
     const int64_t nt = (param_count(d, c) + LPT - 1) / LPT;
     if (rem < nt) break;
     rem -= nt;
@@ -569,25 +674,7 @@ __device__ void process_tile(const EvalArgs &A, int64_t b, int64_t lt, int64_t n
     case kVB2: best = tile_dff<NT, T, kVB2, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S); break;
     default: best = tile_dff<NT, T, kBJ1, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S); break;
   }
-  const bool err = S.err != 0;
-  best = warp_max_u64(best);
-  if (lane_id() == 0) S.warp_key[tid >> 5] = best;
-  __syncthreads();
-  if (tid == 0) {
-    unsigned long long m = 0ull;
-    for (int w = 0; w < NT / 32; ++w) m = S.warp_key[w] > m ? S.warp_key[w] : m;
-    if (m && !err) atomicMax(&A.keys[b], m);
-    __threadfence();
-    const unsigned int ticket = atomicAdd(&A.done[b], 1u);
-    if ((int64_t)ticket == ntiles - 1) {
-      __threadfence();
-      const unsigned long long key = atomicExch(&A.keys[b], 0ull);
-      A.done[b] = 0u;
-      if (err) write_error(A, b);
-      else write_result(A, b, key, c, I.k);
-    }
-  }
-  __syncthreads();
+  fold_and_finalize<NT>(A, b, best, S.err != 0, ntiles, I, S.warp_key);
 }
 
 template <int MODE>
@@ -657,7 +744,7 @@ __global__ void __launch_bounds__(NT, MINB) eval_kernel(EvalArgs A) {
     __syncthreads();
     const int64_t b = s_inst;
     const int64_t t0 = A.tile_start ? A.tile_start[b] : 0;
-    const int64_t nt = A.tile_start ? A.tile_start[b + 1] - t0 : A.single_tiles;
+    const int64_t nt = instance_tiles(A, b);
     const InstView I = resolve_instance<MODE>(A, b);
     process_tile<NT, T, G, MODE>(A, b, t - t0, nt, I, s_items, s_a, s_load, S);
     if (!A.work) break;

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include "bp_lb_kernels.cuh"
+#include "bp_lb_prefix.cuh"
 
 namespace bplb {
 
@@ -33,7 +34,8 @@ constexpr int64_t shape_lpt(int s) { return (int64_t)kShapes[s].nt * kShapes[s].
 
 using EvalFn = void (*)(EvalArgs);
 
-// Host stubs of the instantiated kernels, one table per input mode.
+// Host stubs of the instantiated kernels, one table per input mode; shape -1
+// is the prefix-count kernel of that mode.
 EvalFn eval_fn_ragged_i32(int shape);
 EvalFn eval_fn_ragged_i64(int shape);
 EvalFn eval_fn_nodes(int shape);
@@ -46,6 +48,8 @@ inline EvalFn eval_fn(int shape, int mode) {
   }
 }
 
+inline EvalFn prefix_fn(int mode) { return eval_fn(-1, mode); }
+
 }  // namespace bplb
 
 // Instantiates every shape of one mode (used once per translation unit).
@@ -53,6 +57,7 @@ inline EvalFn eval_fn(int shape, int mode) {
   namespace bplb {                                                                 \
   EvalFn NAME(int shape) {                                                         \
     switch (shape) {                                                               \
+      case -1: return prefix_kernel<MODE>;                                         \
       case 0: return eval_kernel<kShapes[0].nt, kShapes[0].t, kShapes[0].g, MODE,  \
                                  kShapes[0].minb>;                                 \
       case 1: return eval_kernel<kShapes[1].nt, kShapes[1].t, kShapes[1].g, MODE,  \

@@ -349,8 +349,9 @@ def test_autotune_plain_node(cudalib, orc):
     try:
         w, a, c, k = nd.node(1)
         best, us = cudalib.bp_lb_autotune_plain_node(h, w, a, k, reps=3)
-        assert cudalib.bp_lb_get_launch_shape(h, cudalib.MODE_PLAIN_NODES) == best
-        assert us[best] == min(us)
+        nshapes = cudalib.bp_lb_num_launch_shapes()
+        assert len(us) == 2 * nshapes and us[best] == min(us)
+        assert cudalib.bp_lb_get_launch_shape(h, cudalib.MODE_PLAIN_NODES) == best % nshapes
         assert cudalib.bp_lb_eval_node(h, w, a, k) == oracle_node(orc, nd, 1)[:3]
     finally:
         cudalib.bp_lb_destroy(h)
@@ -369,3 +370,30 @@ def test_autotune_nodes(cudalib, handle, orc):
     assert cudalib.bp_lb_get_launch_shape(handle, cudalib.MODE_NODES) == best
     for j in (0, 100, 255):
         assert (int(out_b[j]),) == (oracle_node(orc, nd, j)[0],)
+
+
+# ---------------------------------------------------------------------------
+# prefix-count variant (default) and direct evaluation give identical results
+# ---------------------------------------------------------------------------
+def test_prefix_and_direct_match_oracle(cudalib, orc):
+    rng = np.random.default_rng(13)
+    caps = [1, 2, 3, 7, 150, 999, 4096, 12286, 12287, 24000, 49150, 49151, 70000]
+    inst = [rng.integers(0, c + 1, size=int(rng.integers(0, 60 if c < 20000 else 20)))
+            for c in caps]
+    # zeros, full and half items
+    inst[5][:3] = [0, 999, 499] if len(inst[5]) >= 3 else inst[5][:3]
+    rg = I.ragged_from_list(inst, caps)
+    want = oracle_batch(orc, rg)
+    nd = I.ragged_nodes(seed=14, count=80, n_lo=1, n_hi=3000, caps=(150, 1000, 9999, 12286))
+    want_nodes = tuple(np.array(x) for x in zip(*[oracle_node(orc, nd, j) for j in range(nd.count)]))
+    h = cudalib.bp_lb_create(4096, 4096)
+    try:
+        for algo in (cudalib.ALGO_DIRECT, cudalib.ALGO_PREFIX):
+            cudalib.bp_lb_set_algorithm(h, algo)
+            assert cudalib.bp_lb_get_algorithm(h) == algo
+            assert_same(run_batch(cudalib, h, rg), want, f"algo {algo} ragged")
+            assert_same(run_nodes(cudalib, h, nd), want_nodes, f"algo {algo} nodes")
+            w = inst[6]
+            assert cudalib.bp_lb_eval(h, w, 3)[:3] == orc.lb(w, 4096, 3)[:3]
+    finally:
+        cudalib.bp_lb_destroy(h)
