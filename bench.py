@@ -410,7 +410,7 @@ def main():
                                  if TRAFFIC_BYTES_PER_NODE is not None else None),
                      "peak_basis": f"{sms} SMs x 4 SMSP x 32 lanes x {sm_mhz_max:.0f} MHz "
                                    "(integer issue, one warp instruction per clock per SMSP)",
-                     "kernel": "eval_kernel (direct evaluation: VB2, RAD2, FS1 here), its own "
+                     "kernel": "eval_kernel (direct evaluation: VB2, FS1 here), its own "
                                "CUDA-event time per launch",
                      "direct_kernel_ms": t_direct, "prefix_kernel_ms": t_prefix},
         "launch_shape": {"chosen": shape, "nt_t_g_minb": list(B.bp_lb_launch_shape_info(shape)),

@@ -239,12 +239,12 @@ int bp_lb_eval_batch_noalloc(int32_t B, const int64_t *d_offsets,
 
 /* BP_ALGO_DIRECT evaluates every (DFF, lambda) pair item by item (Alg. 2's
  * loops).  BP_ALGO_PREFIX (the default) computes the same bounds exactly but
- * evaluates MT, CCM1 and BJ1 from value-indexed prefix counts and sums built
- * in shared memory (O(1), O(c / lambda) and O(c / lambda) lookups per
- * parameter instead of one evaluation per item) wherever those tables fit
- * (c up to 12286 for BJ1, 49150 for MT and CCM1, and reduced sizes summing to
- * less than 2^31); the other DFFs, and those three beyond the limits, stay on
- * the direct path.  Results are identical either way. */
+ * evaluates MT, RAD2, CCM1 and BJ1 from value-indexed suffix counts and sums
+ * built in shared memory (O(1), O(1), O(c / lambda) and O(c / lambda) lookups
+ * per parameter instead of one evaluation per item) wherever those tables fit
+ * in 48 KB (c up to 12286 for RAD2 and BJ1, 24574 for MT and CCM1) and the
+ * reduced sizes sum to less than 2^31; VB2, FS1, and the others beyond those
+ * limits, stay on the direct path.  Results are identical either way. */
 #define BP_ALGO_DIRECT 0
 #define BP_ALGO_PREFIX 1
 

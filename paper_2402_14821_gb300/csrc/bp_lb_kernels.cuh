@@ -62,28 +62,42 @@ struct EvalArgs {
   unsigned int *done;         // [B] finished-tile counters, zero between calls
   unsigned long long *work;   // [1] next tile (persistent mode), nullptr otherwise
   uint32_t one;               // always 1 (see add_if_ge in bp_lb_eval.cuh)
-  int32_t prefix_on;          // route MT/CCM1/BJ1 to the prefix-count kernel where it fits
+  int32_t prefix_on;          // route MT/RAD2/CCM1/BJ1 to the prefix-count kernel where they fit
   const int64_t *ptile_start; // [B+1] prefix-kernel tile table, or nullptr (single instance)
   int64_t single_ptiles;
   unsigned long long *pwork;  // [1] next prefix tile (persistent mode)
   int64_t plpt;               // parameters per prefix-kernel tile
 };
 
-// Shared-memory budget of the prefix-count tables (bytes), and the number of
-// parameters per prefix-kernel tile for batches (long tiles amortise building
-// the tables) and for a single check (short tiles spread it over more SMs).
-constexpr int64_t kPrefixSmemBytes = 98304;
+// Shared-memory budget of the prefix-count tables (bytes; 48 KB lets four
+// CTAs share an SM), and the number of parameters per prefix-kernel tile for
+// batches (long tiles amortise building the tables) and for a single check
+// (short tiles spread it over more SMs).
+constexpr int64_t kPrefixSmemBytes = 49152;
 constexpr int64_t kPrefixLPTBatch = 16384;
 constexpr int64_t kPrefixLPTSingle = 1024;
+
+// Bytes of the prefix-count tables of DFF d at capacity c (0: not on that path):
+// u-domain tables of (c - 1) / 2 + 2 entries (MT one, RAD2 two, CCM1 one) and
+// the w-domain table of c + 2 entries (BJ1), all int32.
+BPLB_HD int64_t prefix_table_bytes(int d, int64_t c) {
+  const int64_t nu = (c - 1) / 2 + 2;
+  switch (d) {
+    case kMT:
+    case kCCM1: return 4 * nu;
+    case kRAD2: return 8 * nu;
+    case kBJ1:  return 4 * (c + 2);
+    default:    return 0;
+  }
+}
 
 // Whether the prefix-count kernel evaluates DFF d of an instance with
 // capacity c whose reduced sizes sum to at most sum_bound (its tables must fit
 // in shared memory and its sums in 32 bits); otherwise the direct kernel does.
 BPLB_HD bool prefix_handles(int d, int64_t c, int64_t sum_bound, int32_t on) {
   if (!on || sum_bound >= (int64_t(1) << 31)) return false;
-  if (d == kMT || d == kCCM1) return 4 * ((c - 1) / 2 + 2) <= kPrefixSmemBytes;
-  if (d == kBJ1) return 8 * (c + 2) <= kPrefixSmemBytes;
-  return false;
+  const int64_t bytes = prefix_table_bytes(d, c);
+  return bytes > 0 && bytes <= kPrefixSmemBytes;
 }
 
 // Tiles of the direct kernel (lpt parameters each) and of the prefix kernel.

@@ -1,25 +1,33 @@
-// bp_lb_prefix.cuh -- prefix-count evaluation of MT, CCM1 and BJ1.
+// bp_lb_prefix.cuh -- prefix-count evaluation of MT, RAD2, CCM1 and BJ1.
 //
 // Same bounds as the direct evaluators (bit-exact), asymptotically less work:
 // per tile the instance's items are histogrammed by value in shared memory and
-// scanned, after which each parameter needs O(1) (MT), O(U / l) (CCM1) or
-// O(c / l) (BJ1) table lookups instead of one evaluation per item:
+// suffix-scanned, after which each parameter needs O(1) (MT, RAD2), O(U / l)
+// (CCM1) or O(c / l) (BJ1) table lookups instead of one evaluation per item.
+// With u, the small/big classes and cm = c mod l as in bp_lb_core.cuh, and the
+// u-domain tables (x in [0, U + 1], U = floor((c - 1) / 2), entry U + 1 = 0)
+//   E(x)  = sum_small u [u >= x] - sum_big u [u >= x],
+//   N'(x) = #small[u >= x] - #big[u >= x],   Ns(x) = #small[u >= x],
+// and the w-domain table (x in [0, c + 1]) NN(x) = sum_w max(0, w - x + 1):
+//   MT:   sum_small u [u >= l] + sum_big u [u < l] = E(l) + TB, TB = sum_big u;
+//   RAD2: #small[u >= l] - #big[u >= l] = N'(l), and with y = c - 2l + 1
+//         #small[u > c - 2l] = Ns(y), #big[u > c - 2l] = Ns(y) - N'(y);
+//   CCM1: sum_small floor(u / l) - sum_big floor(u / l) = sum_{j >= 1} N'(j l),
+//         since floor(u / l) counts the multiples j l <= u;
+//   BJ1:  cm q + min(rho, cm) (w = q l + rho) counts the x <= w in the union
+//         of the blocks [j l + 1, j l + cm], j >= 0, so summed over the items
+//         it is sum_j (NN(j l + 1) - NN(j l + cm + 1)) over j = 0 .. floor(c / l).
+// NN is the suffix sum of the suffix count N(x) = #[w >= x]: a histogram
+// scanned twice.  Every table entry and every sum above is bounded by the
+// instance's size total, below 2^31 on this path (prefix_handles), so the
+// tables and accumulators are 32-bit.  VB2 and FS1 stay on the direct kernel.
 //
-//   MT:   sum_small u [u >= l] + sum_big u [u < l] = E(l) + TB, with
-//         E(x) = sum over values y >= x of (small sum at y - big sum at y)
-//         and TB the total of the big u;
-//   CCM1: sum_small floor(u / l) - sum_big floor(u / l) = sum_{j >= 1} N(j l),
-//         with N(x) = #small[u >= x] - #big[u >= x], since floor(u / l) counts
-//         the multiples j l <= u;
-//   BJ1:  sum_w (cm q + min(rho, cm)) over the blocks [j l, j l + l) of the
-//         value range (q = j inside block j):
-//           cm * sum_{j >= 1} #[w >= j l]
-//         + sum_j ( sum_{w in [jl, jl + cm)} (w - j l) + cm #[w in [jl + cm, jl + l)] ),
-//         read from the prefix count C(x) = #[w < x] and prefix sum
-//         Sm(x) = sum_{w < x} w.
-// (u, the small/big classes, cm = c mod l and the sums assembled from these
-// accumulators are those of bp_lb_core.cuh.)  VB2, RAD2 and FS1 stay on the
-// direct kernel.
+// Only bounds above L1 = ceil(sum w / c) can change the maximum: L1 is MT's
+// bound at l = 0, the smallest flattened index, which wins every tie at L1.
+// Each thread keeps its best bound B (starting at L1) and only divides for a
+// parameter whose sum S exceeds B f(c, l), i.e. whose bound exceeds B; since a
+// thread meets its parameters in increasing order, an equal bound later never
+// displaces the earlier one, exactly as in the full maximum.
 #pragma once
 
 #include "bp_lb_kernels.cuh"
@@ -27,64 +35,65 @@
 namespace bplb {
 
 constexpr int kPrefixNT = 256;
-// Parameters needing more lookups than this are "heavy": the whole CTA
-// shares their lookups; the others take one thread each.
-constexpr int kHeavyBlocks = 256;
-constexpr int kMaxHeavy = 256;
+constexpr int kPrefixWarps = kPrefixNT / 32;
+// Parameters with at least this many lookups are shared by the whole CTA
+// (kCtaBlocks) or by one warp (kWarpBlocks); the rest take one thread each.
+constexpr uint32_t kCtaBlocks = kPrefixNT;
+constexpr uint32_t kWarpBlocks = 32;
+constexpr int kMaxHeavy = kPrefixNT;
 
 struct PrefixShared {
   int err;
   int pad_;
-  unsigned long long warp_key[kPrefixNT / 32];
-  long long sums[8];  // n_small, n_big, n_half, n_full, sumw_big, sumw, total big u, total count
-  int64_t seg[kPrefixNT];
-  unsigned long long heavy_acc[kMaxHeavy];  // two's-complement partial sums of heavy parameters
+  unsigned long long warp_key[kPrefixWarps];
+  long long sums[8];  // n_small, n_big, n_half, n_full, sumw_big, sumw, total big u, unused
+  uint32_t wtot[2][kPrefixWarps];
+  uint32_t heavy_acc[kMaxHeavy];
 };
 
-// Shared-memory array lengths (entries) of the prefix tables.
-BPLB_HD int64_t prefix_u_len(int64_t c) { return (c - 1) / 2 + 2; }   // u in [0, (c-1)/2] + 0-sentinel
-BPLB_HD int64_t prefix_w_len(int64_t c) { return c + 2; }             // x in [0, c + 1]
-
-// In-place block-wide scan of a[0 .. n): inclusive suffix sums (SUFFIX) or
-// exclusive prefix sums.  Each thread scans one contiguous segment serially;
-// the segment totals are scanned with warp shuffles (every warp its 32
-// totals, then warp 0 the warp totals).
-template <bool SUFFIX>
-__device__ void block_scan_i32(int32_t *a, int n, int64_t *seg) {
-  const int tid = threadIdx.x;
-  const int per = (n + kPrefixNT - 1) / kPrefixNT;
-  const int s0 = min(n, tid * per), s1 = min(n, s0 + per);
-  int64_t tot = 0;
-  for (int i = s0; i < s1; ++i) tot += a[SUFFIX ? n - 1 - i : i];
-  // inclusive scan of the totals within the warp
-  int64_t x = tot;
+// Sum of v over the threads after this one (higher threadIdx.x).  wtot must
+// not be in use by another call until the caller's next barrier.
+__device__ __forceinline__ uint32_t block_sum_after(uint32_t v, uint32_t *wtot) {
+  const int lane = (int)lane_id(), warp = (int)(threadIdx.x >> 5);
+  uint32_t x = v;  // inclusive suffix within the warp
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const int64_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-    if ((int)lane_id() >= o) x += y;
+    const uint32_t y = __shfl_down_sync(0xFFFFFFFFu, x, o);
+    if (lane + o < 32) x += y;
   }
-  if (lane_id() == 31) seg[tid >> 5] = x;
+  if (lane == 0) wtot[warp] = x;
   __syncthreads();
-  if (tid < 32) {
-    int64_t wv = tid < kPrefixNT / 32 ? seg[tid] : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int64_t y = __shfl_up_sync(0xFFFFFFFFu, wv, o);
-      if (tid >= o) wv += y;
-    }
-    if (tid < kPrefixNT / 32) seg[32 + tid] = wv;  // inclusive warp prefix
-  }
-  __syncthreads();
-  int64_t run = x - tot + ((tid >> 5) ? seg[32 + (tid >> 5) - 1] : 0);  // exclusive
+  uint32_t later = 0;
+  for (int w = warp + 1; w < kPrefixWarps; ++w) later += wtot[w];
+  return x - v + later;
+}
+
+// In-place suffix scan of a[0 .. n): a[x] <- sum_{y >= x} a[y], applied once
+// or (TWICE) two times.  Thread t scans the contiguous segment
+// [t per, t per + per) with per odd (consecutive lanes then hit distinct
+// banks); the values entering each segment from above come from block sums
+// of the segment totals (TWICE: also of the once-scanned segments' sums).
+template <bool TWICE>
+__device__ void suffix_scan(int32_t *a, int n, PrefixShared &S) {
+  const int per = ((n + kPrefixNT - 1) / kPrefixNT) | 1;
+  const int s0 = min(n, (int)threadIdx.x * per), s1 = min(n, s0 + per);
+  uint32_t h = 0, m = 0;
   for (int i = s0; i < s1; ++i) {
-    const int idx = SUFFIX ? n - 1 - i : i;
-    const int64_t v = a[idx];
-    if (SUFFIX) {
-      run += v;
-      a[idx] = (int32_t)run;
+    const uint32_t v = (uint32_t)a[i];
+    h += v;
+    if (TWICE) m += v * (uint32_t)(i - s0 + 1);  // this segment's part of the twice-scanned a[s0]
+  }
+  const uint32_t n_after = block_sum_after(h, S.wtot[0]);
+  uint32_t nn_after = 0;
+  if (TWICE) nn_after = block_sum_after(m + (uint32_t)(s1 - s0) * n_after, S.wtot[1]);
+  uint32_t nr = n_after, nnr = nn_after;
+  for (int i = s1 - 1; i >= s0; --i) {
+    nr += (uint32_t)a[i];
+    if (TWICE) {
+      nnr += nr;
+      a[i] = (int32_t)nnr;
     } else {
-      a[idx] = (int32_t)run;
-      run += v;
+      a[i] = (int32_t)nr;
     }
   }
   __syncthreads();
@@ -110,53 +119,68 @@ __device__ __forceinline__ void node_loads(const InstView &I, uint32_t *s_load, 
   }
 }
 
-// One parameter's accumulator, lanes `lane` (stride `stride`) of its blocks.
+// Table geometry and constants of one tile.
+struct PrefixCtx {
+  InstSums s;
+  int64_t c;
+  int64_t TB;     // sum of u over big items
+  uint32_t U;     // floor((c - 1) / 2): largest small or big u
+  uint32_t U1;    // U + 1: the zero sentinel of the u-domain tables
+  int64_t lo_d;   // first parameter of the DFF
+  uint32_t gbase; // its flattened index
+};
+
+// Lookup blocks of one parameter (D = CCM1 or BJ1): b0, b0 + bs, ...
+//   CCM1: block b is x = (b + 1) l <= U, term N'(x);
+//   BJ1:  block b is x = b l + 1 <= c, term NN(x) - NN(x + cm)  (cm > 0).
 template <int D>
-__device__ __forceinline__ int64_t prefix_acc(const int32_t *T0, const int32_t *T1, int64_t c,
-                                              int64_t l, int lane, int stride, int64_t R,
-                                              int64_t TB) {
-  int64_t acc = 0;
-  if (D == kMT) {
-    if (lane == 0) {
-      const int64_t U1 = prefix_u_len(c) - 1;  // sentinel index
-      acc = (int64_t)T0[l < U1 ? l : U1] + TB;
-    }
-  } else if (D == kCCM1) {
-    // indices < 2^31 (c <= 2^30): 32-bit loop arithmetic
-    const uint32_t U = (uint32_t)(prefix_u_len(c) - 2), l32 = (uint32_t)l;
-    const uint32_t step = (uint32_t)stride * l32;
-    int32_t a32 = 0;  // partial sums of at most U / l terms of |N| <= r: 32 bits suffice
-    for (uint32_t x = (1u + (uint32_t)lane) * l32; x <= U; x += step) a32 += T0[x];
-    acc = a32;
-  } else {  // BJ1: T0 = C (prefix count), T1 = Sm (prefix sum)
-    const uint32_t c32 = (uint32_t)c, l32 = (uint32_t)l;
-    const uint32_t cm = c32 % l32;
-    const uint32_t top = c32 + 1u;
-    const uint32_t step = (uint32_t)stride * l32;
-    int64_t nq = 0;  // sum over blocks j >= 1 of #[w >= j l]
-    for (uint32_t a = (uint32_t)lane * l32; a <= c32; a += step) {
-      const uint32_t b1 = min(a + cm, top), b2 = min(a + l32, top);
-      const int32_t Ca = T0[a], Cb1 = T0[b1], Cb2 = T0[b2];
-      acc += (int64_t)(T1[b1] - T1[a]) - (int64_t)a * (Cb1 - Ca) + (int64_t)cm * (Cb2 - Cb1);
-      if (a > 0) nq += R - Ca;
-    }
-    acc += (int64_t)cm * nq;
+__device__ __forceinline__ uint32_t block_terms(const int32_t *T, uint32_t c32, uint32_t U,
+                                                uint32_t l, uint32_t cm, uint32_t b0, uint32_t bs) {
+  const uint32_t step = bs * l;
+  uint32_t acc = 0;
+  if (D == kCCM1) {
+    uint32_t x = (b0 + 1u) * l;
+#pragma unroll 4
+    for (; x <= U; x += step) acc += (uint32_t)T[x];
+  } else {
+    uint32_t x = b0 * l + 1u;
+#pragma unroll 4
+    for (; x <= c32; x += step) acc += (uint32_t)(T[x] - T[x + cm]);
   }
   return acc;
 }
 
+// Sum S(l) and denominator f(c, l) from the accumulator, and the candidate
+// test against the thread's best bound B (see the file comment).
 template <int D>
-__device__ __forceinline__ int64_t prefix_bound(const InstSums &s, int64_t c, int64_t l,
-                                                int64_t acc) {
-  int64_t S;
-  if (D == kMT) S = mt_sum(s, c, (uint64_t)(2 * acc));
-  else if (D == kCCM1) S = ccm1_sum(s, (int64_t)((uint32_t)c / (uint32_t)l), acc);
-  else S = bj1_sum(s, acc);
-  const int64_t q = (D == kMT) ? 0 : (int64_t)((uint32_t)c / (uint32_t)l);
-  return ceil_div_fast(S, dff_at_c_q(D, l, c, q));
+__device__ __forceinline__ void consider(const PrefixCtx &x, uint32_t l, int64_t acc, int64_t &B,
+                                         unsigned long long &best) {
+  const int64_t c = x.c;
+  int64_t S, f;
+  if (D == kMT) {
+    S = mt_sum(x.s, c, (uint64_t)(2 * acc));
+    f = c;
+  } else if (D == kRAD2) {
+    S = acc;  // assembled by the caller
+    f = c;
+  } else {
+    const uint32_t q = (uint32_t)c / l;
+    if (D == kCCM1) {
+      S = ccm1_sum(x.s, (int64_t)q, acc);
+      f = 2 * (int64_t)q;
+    } else {
+      S = bj1_sum(x.s, acc);
+      f = (int64_t)q * (int64_t)(l - ((uint32_t)c - q * l));
+    }
+  }
+  if (S > B * f || (D == kMT && l == 0u)) {
+    const int64_t lb = ceil_div_fast(S, f);
+    B = lb;
+    best = make_key(lb, x.gbase + (uint32_t)((int64_t)l - x.lo_d));
+  }
 }
 
-// Builds the tables of DFF D for instance I and evaluates lambdas
+// Builds the table(s) of DFF D for instance I and evaluates parameters
 // [lam0, lam_end); returns the thread's best key.
 template <int MODE, int D>
 __device__ unsigned long long prefix_tile_dff(const EvalArgs &A, const InstView &I, int64_t lam0,
@@ -164,16 +188,22 @@ __device__ unsigned long long prefix_tile_dff(const EvalArgs &A, const InstView 
                                               PrefixShared &S) {
   const int tid = threadIdx.x;
   const int64_t c = I.c;
-  const int nU = (int)prefix_u_len(c), nW = (int)prefix_w_len(c);
-  int32_t *T0 = tab;
-  int32_t *T1 = tab + nW;  // BJ1 only
-  const int nzero = (D == kBJ1) ? 2 * nW : nU;
-  for (int i = tid; i < nzero; i += kPrefixNT) tab[i] = 0;
+  const uint32_t c32 = (uint32_t)c;
+  const uint32_t U = (uint32_t)((c - 1) / 2);
+  const int nU = (int)U + 2, nW = (int)c + 2;
+  int32_t *T0 = tab;       // E, N', N' or NN
+  int32_t *T1 = tab + nU;  // RAD2: Ns
+  const int nzero = (D == kBJ1) ? nW : (D == kRAD2 ? 2 * nU : nU);
+  {
+    int4 *t4 = reinterpret_cast<int4 *>(tab);
+    const int4 z = make_int4(0, 0, 0, 0);
+    for (int i = tid; i < (nzero + 3) / 4; i += kPrefixNT) t4[i] = z;
+  }
   if (tid < 8) S.sums[tid] = 0;
   __syncthreads();
 
   // ---- histogram the instance's items ----------------------------------------
-  int64_t ls[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int64_t ls[7] = {0, 0, 0, 0, 0, 0, 0};
   const int64_t L = stream_len<MODE>(I);
   for (int64_t q = tid; q < L; q += kPrefixNT) {
     int64_t w = 0;
@@ -183,10 +213,8 @@ __device__ unsigned long long prefix_tile_dff(const EvalArgs &A, const InstView 
       continue;
     }
     ls[5] += w;
-    ls[7] += 1;
     if (D == kBJ1) {
       atomicAdd(&T0[w], 1);
-      atomicAdd(&T1[w], (int32_t)w);
       continue;
     }
     if (w == 0) continue;
@@ -195,6 +223,7 @@ __device__ unsigned long long prefix_tile_dff(const EvalArgs &A, const InstView 
     } else if (2 * w < c) {
       ls[0]++;
       atomicAdd(&T0[w], D == kMT ? (int32_t)w : 1);
+      if (D == kRAD2) atomicAdd(&T1[w], 1);
     } else if (2 * w > c) {
       const int64_t u = c - w;
       ls[1]++;
@@ -206,74 +235,118 @@ __device__ unsigned long long prefix_tile_dff(const EvalArgs &A, const InstView 
     }
   }
 #pragma unroll
-  for (int e = 0; e < 8; ++e) {
+  for (int e = 0; e < 7; ++e) {
     const long long x = warp_sum((long long)ls[e]);
     if (lane_id() == 0 && x != 0) atomicAdd((unsigned long long *)&S.sums[e], (unsigned long long)x);
   }
   __syncthreads();
   if (D == kBJ1) {
-    block_scan_i32<false>(T0, nW, S.seg);
-    block_scan_i32<false>(T1, nW, S.seg);
+    suffix_scan<true>(T0, nW, S);
   } else {
-    block_scan_i32<true>(T0, nU, S.seg);
+    suffix_scan<false>(T0, nU, S);
+    if (D == kRAD2) suffix_scan<false>(T1, nU, S);
   }
   if (S.err) return 0ull;
 
-  InstSums sums;
-  sums.n_small = S.sums[0];
-  sums.n_big = S.sums[1];
-  sums.n_half = S.sums[2];
-  sums.n_full = S.sums[3];
-  sums.sumw_big = S.sums[4];
-  sums.sumw = S.sums[5];
-  const int64_t TB = S.sums[6];
-  const int64_t R = S.sums[7];
-  int64_t lo_d, hi_d;
-  param_range(D, c, lo_d, hi_d);
-  const uint32_t gbase = flat_index(D, lo_d, c);
+  PrefixCtx x;
+  x.s.n_small = S.sums[0];
+  x.s.n_big = S.sums[1];
+  x.s.n_half = S.sums[2];
+  x.s.n_full = S.sums[3];
+  x.s.sumw_big = S.sums[4];
+  x.s.sumw = S.sums[5];
+  x.TB = S.sums[6];
+  x.c = c;
+  x.U = U;
+  x.U1 = U + 1u;
+  int64_t hi_d;
+  param_range(D, c, x.lo_d, hi_d);
+  x.gbase = flat_index(D, x.lo_d, c);
+  int64_t B = ceil_div_fast(x.s.sumw, c);  // L1
   unsigned long long best = 0ull;
 
-  // ---- heavy parameters (many lookups): the whole CTA shares their blocks ----
-  int64_t heavy_end = lam0;
-  if (D == kCCM1) heavy_end = max(lam0, min(lam_end, (prefix_u_len(c) - 2) / kHeavyBlocks + 1));
-  if (D == kBJ1) heavy_end = max(lam0, min(lam_end, c / kHeavyBlocks + 1));
-  heavy_end = min(heavy_end, lam0 + kMaxHeavy);
-  const int nheavy = (int)(heavy_end - lam0);
-  if (nheavy > 0) {
-    for (int i = tid; i < nheavy; i += kPrefixNT) S.heavy_acc[i] = 0ull;
+  if (D == kMT || D == kRAD2) {
+    for (int64_t l = lam0 + tid; l < lam_end; l += kPrefixNT) {
+      const uint32_t l32 = (uint32_t)l;
+      int64_t acc;
+      if (D == kMT) {
+        acc = (int64_t)T0[min(l32, x.U1)] + x.TB;
+      } else {
+        const uint32_t y = min(c32 - 2u * l32 + 1u, x.U1);
+        const int64_t n1 = T0[l32], n2s = T1[y], n2b = (int64_t)T1[y] - T0[y];
+        acc = rad2_sum(x.s, c, n1, n2s, n2b);
+      }
+      consider<D>(x, l32, acc, B, best);
+    }
+    return best;
+  }
+
+  // CCM1 / BJ1: lookups per parameter fall like X / l.
+  const uint32_t X = (D == kCCM1) ? U : c32;
+  const int64_t cta_end = max(lam0, min(lam_end, min((int64_t)(X / kCtaBlocks) + 1, lam0 + kMaxHeavy)));
+  const int64_t warp_end = max(cta_end, min(lam_end, (int64_t)(X / kWarpBlocks) + 1));
+  const int lane = (int)lane_id(), warp = tid >> 5;
+
+  // ---- parameters shared by the whole CTA ---------------------------------------
+  const int ncta = (int)(cta_end - lam0);
+  if (ncta > 0) {
+    for (int i = tid; i < ncta; i += kPrefixNT) S.heavy_acc[i] = 0u;
     __syncthreads();
-    for (int i = 0; i < nheavy; ++i) {
-      const int64_t l = lam0 + i;
-      if (D == kBJ1 && (uint32_t)c % (uint32_t)l == 0) continue;  // c mod l = 0: every BJ1 term is 0
-      long long part = prefix_acc<D>(T0, T1, c, l, tid, kPrefixNT, R, TB);
-      part = warp_sum(part);
-      if (lane_id() == 0 && part != 0)
-        atomicAdd(&S.heavy_acc[i], (unsigned long long)part);
+    for (int i = 0; i < ncta; ++i) {
+      const uint32_t l = (uint32_t)(lam0 + i);
+      const uint32_t cm = c32 % l;
+      if (D == kBJ1 && cm == 0u) continue;  // every BJ1 term is 0
+      const uint32_t part = warp_sum(block_terms<D>(T0, c32, U, l, cm, (uint32_t)tid, kPrefixNT));
+      if (lane == 0 && part != 0u) atomicAdd(&S.heavy_acc[i], part);
     }
     __syncthreads();
-    for (int i = tid; i < nheavy; i += kPrefixNT) {
-      const int64_t l = lam0 + i;
-      const int64_t acc = (int64_t)S.heavy_acc[i];
-      const unsigned long long key = make_key(prefix_bound<D>(sums, c, l, acc),
-                                              gbase + (uint32_t)(l - lo_d));
-      best = key > best ? key : best;
+    if (tid < ncta) {
+      const uint32_t l = (uint32_t)(lam0 + tid);
+      const int64_t acc = (D == kCCM1) ? (int64_t)(int32_t)S.heavy_acc[tid] : (int64_t)S.heavy_acc[tid];
+      consider<D>(x, l, acc, B, best);
     }
   }
-  // ---- light parameters: one thread each ----------------------------------------
-  for (int64_t l = heavy_end + tid; l < lam_end; l += kPrefixNT) {
-    const int64_t acc =
-        (D == kBJ1 && (uint32_t)c % (uint32_t)l == 0) ? 0 : prefix_acc<D>(T0, T1, c, l, 0, 1, R, TB);
-    const unsigned long long key = make_key(prefix_bound<D>(sums, c, l, acc),
-                                            gbase + (uint32_t)(l - lo_d));
-    best = key > best ? key : best;
+
+  // ---- parameters shared by one warp (lane t of a round of 32 keeps the t-th) ---
+  {
+    const int64_t nwarp = warp_end - cta_end;
+    // warp w takes the parameters cta_end + w + 8 i, i = 0, 1, ...
+    const int64_t mine_n = nwarp > warp ? (nwarp - warp + kPrefixWarps - 1) / kPrefixWarps : 0;
+    for (int64_t r0 = 0; r0 < mine_n; r0 += 32) {
+      uint32_t mine = 0;
+      const int cnt = (int)min((int64_t)32, mine_n - r0);
+      for (int t = 0; t < cnt; ++t) {
+        const uint32_t l = (uint32_t)(cta_end + warp + (r0 + t) * kPrefixWarps);
+        const uint32_t cm = c32 % l;
+        uint32_t part = 0;
+        if (D == kCCM1 || cm != 0u) part = warp_sum(block_terms<D>(T0, c32, U, l, cm, (uint32_t)lane, 32u));
+        if (lane == t) mine = part;
+      }
+      if (lane < cnt) {
+        const uint32_t l = (uint32_t)(cta_end + warp + (r0 + lane) * kPrefixWarps);
+        consider<D>(x, l, D == kCCM1 ? (int64_t)(int32_t)mine : (int64_t)mine, B, best);
+      }
+    }
+  }
+
+  // ---- one thread per parameter; alternate directions balance the rounds --------
+  for (int64_t r = warp_end; r < lam_end; r += kPrefixNT) {
+    const int64_t round = (r - warp_end) / kPrefixNT;
+    const int64_t l = r + ((round & 1) ? kPrefixNT - 1 - tid : tid);
+    if (l >= lam_end) continue;
+    const uint32_t l32 = (uint32_t)l;
+    const uint32_t cm = c32 % l32;
+    uint32_t acc = 0;
+    if (D == kCCM1 || cm != 0u) acc = block_terms<D>(T0, c32, U, l32, cm, 0u, 1u);
+    consider<D>(x, l32, D == kCCM1 ? (int64_t)(int32_t)acc : (int64_t)acc, B, best);
   }
   return best;
 }
 
-// Persistent kernel over the prefix tile table (instance, DFF in {MT, CCM1,
-// BJ1} routed here by prefix_handles, A.plpt consecutive lambdas).
+// Persistent kernel over the prefix tile table (instance, DFF in {MT, RAD2,
+// CCM1, BJ1} routed here by prefix_handles, A.plpt consecutive lambdas).
 template <int MODE>
-__global__ void __launch_bounds__(kPrefixNT, 2) prefix_kernel(EvalArgs A) {
+__global__ void __launch_bounds__(kPrefixNT, 4) prefix_kernel(EvalArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ PrefixShared S;
   __shared__ long long s_tile, s_inst;
@@ -327,6 +400,7 @@ __global__ void __launch_bounds__(kPrefixNT, 2) prefix_kernel(EvalArgs A) {
     __syncthreads();
     unsigned long long best;
     if (d == kMT) best = prefix_tile_dff<MODE, kMT>(A, I, lam0, lam_end, tab, s_load, S);
+    else if (d == kRAD2) best = prefix_tile_dff<MODE, kRAD2>(A, I, lam0, lam_end, tab, s_load, S);
     else if (d == kCCM1) best = prefix_tile_dff<MODE, kCCM1>(A, I, lam0, lam_end, tab, s_load, S);
     else best = prefix_tile_dff<MODE, kBJ1>(A, I, lam0, lam_end, tab, s_load, S);
     __syncthreads();

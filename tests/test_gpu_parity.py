@@ -377,11 +377,16 @@ def test_autotune_nodes(cudalib, handle, orc):
 # ---------------------------------------------------------------------------
 def test_prefix_and_direct_match_oracle(cudalib, orc):
     rng = np.random.default_rng(13)
-    caps = [1, 2, 3, 7, 150, 999, 4096, 12286, 12287, 24000, 49150, 49151, 70000]
+    caps = [1, 2, 3, 7, 150, 999, 4096, 12286, 12287, 24000, 24574, 24575, 70000]
     inst = [rng.integers(0, c + 1, size=int(rng.integers(0, 60 if c < 20000 else 20)))
             for c in caps]
     # zeros, full and half items
     inst[5][:3] = [0, 999, 499] if len(inst[5]) >= 3 else inst[5][:3]
+    # equal sizes: many parameters tie at the maximum (first index must win)
+    for c in (96, 1000, 5040, 12285):
+        for w in (1, c // 3 + 1, c // 2, c // 4, c - 1, c):
+            caps.append(c)
+            inst.append(np.full(int(rng.integers(1, 40)), w))
     rg = I.ragged_from_list(inst, caps)
     want = oracle_batch(orc, rg)
     nd = I.ragged_nodes(seed=14, count=80, n_lo=1, n_hi=3000, caps=(150, 1000, 9999, 12286))

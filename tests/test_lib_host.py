@@ -83,17 +83,20 @@ def test_serve_rejects_bad_arguments_before_any_device_work(lib):
 
 def test_dff_route(lib):
     P, D = binding.ALGO_PREFIX, binding.ALGO_DIRECT
-    # VB2, RAD2 and FS1 are always direct; MT/CCM1/BJ1 go to the prefix tables
-    # while they fit (BJ1: 8 (c + 2) bytes <= 96 KiB; MT, CCM1: 4 ((c-1)/2 + 2))
-    for d in (1, 2, 4):
+    # VB2 and FS1 are always direct; MT/RAD2/CCM1/BJ1 go to the prefix tables
+    # while they fit in 48 KiB (BJ1: 4 (c + 2) bytes; RAD2: 8 ((c-1)/2 + 2);
+    # MT, CCM1: 4 ((c-1)/2 + 2))
+    for d in (2, 4):
         assert binding.bp_lb_dff_route(d, 1000, 500, P) == D
-    for d in (0, 3, 5):
+    for d in (0, 1, 3, 5):
         assert binding.bp_lb_dff_route(d, 10_000, 630, P) == P
         assert binding.bp_lb_dff_route(d, 10_000, 630, D) == D
-    assert binding.bp_lb_dff_route(5, 12286, 10, P) == P
-    assert binding.bp_lb_dff_route(5, 12287, 10, P) == D
-    assert binding.bp_lb_dff_route(3, 49150, 10, P) == P
-    assert binding.bp_lb_dff_route(3, 49151, 10, P) == D
+    for d in (1, 5):
+        assert binding.bp_lb_dff_route(d, 12286, 10, P) == P
+        assert binding.bp_lb_dff_route(d, 12287, 10, P) == D
+    for d in (0, 3):
+        assert binding.bp_lb_dff_route(d, 24574, 10, P) == P
+        assert binding.bp_lb_dff_route(d, 24575, 10, P) == D
     # reduced sizes that could sum past 2^31 stay direct
     assert binding.bp_lb_dff_route(3, 10_000, 300_000, P) == D
     assert binding.bp_lb_dff_route(6, 10, 1, P) == -1
