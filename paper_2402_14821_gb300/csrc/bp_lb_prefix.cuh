@@ -38,7 +38,7 @@ constexpr int kPrefixNT = 256;
 constexpr int kPrefixWarps = kPrefixNT / 32;
 // Parameters with at least this many lookups are shared by the whole CTA
 // (kCtaBlocks) or by one warp (kWarpBlocks); the rest take one thread each.
-constexpr uint32_t kCtaBlocks = kPrefixNT;
+constexpr uint32_t kCtaBlocks = 1024;
 constexpr uint32_t kWarpBlocks = 32;
 constexpr int kMaxHeavy = kPrefixNT;
 
@@ -49,6 +49,7 @@ struct PrefixShared {
   long long sums[8];  // n_small, n_big, n_half, n_full, sumw_big, sumw, total big u, unused
   uint32_t wtot[2][kPrefixWarps];
   uint32_t heavy_acc[kMaxHeavy];
+  uint32_t heavy_cm[kMaxHeavy];
 };
 
 // Sum of v over the threads after this one (higher threadIdx.x).  wtot must
@@ -119,20 +120,10 @@ __device__ __forceinline__ void node_loads(const InstView &I, uint32_t *s_load, 
   }
 }
 
-// Table geometry and constants of one tile.
-struct PrefixCtx {
-  InstSums s;
-  int64_t c;
-  int64_t TB;     // sum of u over big items
-  uint32_t U;     // floor((c - 1) / 2): largest small or big u
-  uint32_t U1;    // U + 1: the zero sentinel of the u-domain tables
-  int64_t lo_d;   // first parameter of the DFF
-  uint32_t gbase; // its flattened index
-};
-
-// Lookup blocks of one parameter (D = CCM1 or BJ1): b0, b0 + bs, ...
+// Strided lookup blocks b0, b0 + bs, ... of one parameter (D = CCM1 or BJ1):
 //   CCM1: block b is x = (b + 1) l <= U, term N'(x);
 //   BJ1:  block b is x = b l + 1 <= c, term NN(x) - NN(x + cm)  (cm > 0).
+// Unrolled by two with explicit bounds (no trip-count division).
 template <int D>
 __device__ __forceinline__ uint32_t block_terms(const int32_t *T, uint32_t c32, uint32_t U,
                                                 uint32_t l, uint32_t cm, uint32_t b0, uint32_t bs) {
@@ -140,43 +131,35 @@ __device__ __forceinline__ uint32_t block_terms(const int32_t *T, uint32_t c32, 
   uint32_t acc = 0;
   if (D == kCCM1) {
     uint32_t x = (b0 + 1u) * l;
-#pragma unroll 4
-    for (; x <= U; x += step) acc += (uint32_t)T[x];
+    for (; x + step <= U; x += 2u * step) acc += (uint32_t)T[x] + (uint32_t)T[x + step];
+    if (x <= U) acc += (uint32_t)T[x];
   } else {
     uint32_t x = b0 * l + 1u;
-#pragma unroll 4
-    for (; x <= c32; x += step) acc += (uint32_t)(T[x] - T[x + cm]);
+    const int32_t *T2 = T + cm;
+    for (; x + step <= c32; x += 2u * step)
+      acc += (uint32_t)(T[x] - T2[x]) + (uint32_t)(T[x + step] - T2[x + step]);
+    if (x <= c32) acc += (uint32_t)(T[x] - T2[x]);
   }
   return acc;
 }
 
-// Sum S(l) and denominator f(c, l) from the accumulator, and the candidate
-// test against the thread's best bound B (see the file comment).
-template <int D>
-__device__ __forceinline__ void consider(const PrefixCtx &x, uint32_t l, int64_t acc, int64_t &B,
-                                         unsigned long long &best) {
-  const int64_t c = x.c;
-  int64_t S, f;
-  if (D == kMT) {
-    S = mt_sum(x.s, c, (uint64_t)(2 * acc));
-    f = c;
-  } else if (D == kRAD2) {
-    S = acc;  // assembled by the caller
-    f = c;
-  } else {
-    const uint32_t q = (uint32_t)c / l;
-    if (D == kCCM1) {
-      S = ccm1_sum(x.s, (int64_t)q, acc);
-      f = 2 * (int64_t)q;
-    } else {
-      S = bj1_sum(x.s, acc);
-      f = (int64_t)q * (int64_t)(l - ((uint32_t)c - q * l));
-    }
-  }
-  if (S > B * f || (D == kMT && l == 0u)) {
+// BJ1 blocks j = 0 .. q of one parameter (q + 1 of them, cm > 0).
+__device__ __forceinline__ uint32_t bj1_blocks(const int32_t *T, uint32_t l, uint32_t cm, uint32_t q) {
+  const int32_t *p = T + 1, *p2 = T + 1 + cm;
+  uint32_t acc = 0, n = q + 1u;
+  for (; n >= 2u; n -= 2u, p += 2u * l, p2 += 2u * l)
+    acc += (uint32_t)(p[0] - p2[0]) + (uint32_t)(p[l] - p2[l]);
+  if (n) acc += (uint32_t)(p[0] - p2[0]);
+  return acc;
+}
+
+// The candidate test (file comment): divide only when S > B f.
+__device__ __forceinline__ void try_key(int64_t S, int64_t f, uint32_t g, int64_t &B,
+                                        unsigned long long &best) {
+  if (S > B * f) {
     const int64_t lb = ceil_div_fast(S, f);
     B = lb;
-    best = make_key(lb, x.gbase + (uint32_t)((int64_t)l - x.lo_d));
+    best = make_key(lb, g);
   }
 }
 
@@ -203,7 +186,7 @@ __device__ unsigned long long prefix_tile_dff(const EvalArgs &A, const InstView 
   __syncthreads();
 
   // ---- histogram the instance's items ----------------------------------------
-  int64_t ls[7] = {0, 0, 0, 0, 0, 0, 0};
+  uint32_t ls[7] = {0, 0, 0, 0, 0, 0, 0};
   const int64_t L = stream_len<MODE>(I);
   for (int64_t q = tid; q < L; q += kPrefixNT) {
     int64_t w = 0;
@@ -212,7 +195,7 @@ __device__ unsigned long long prefix_tile_dff(const EvalArgs &A, const InstView 
       S.err = 1;
       continue;
     }
-    ls[5] += w;
+    ls[5] += (uint32_t)w;
     if (D == kBJ1) {
       atomicAdd(&T0[w], 1);
       continue;
@@ -227,17 +210,18 @@ __device__ unsigned long long prefix_tile_dff(const EvalArgs &A, const InstView 
     } else if (2 * w > c) {
       const int64_t u = c - w;
       ls[1]++;
-      ls[4] += w;
-      ls[6] += u;
+      ls[4] += (uint32_t)w;
+      ls[6] += (uint32_t)u;
       atomicAdd(&T0[u], D == kMT ? -(int32_t)u : -1);
     } else {
       ls[2]++;
     }
   }
+  // every count and sum is below 2^31 on this path: 32-bit warp reductions
 #pragma unroll
   for (int e = 0; e < 7; ++e) {
-    const long long x = warp_sum((long long)ls[e]);
-    if (lane_id() == 0 && x != 0) atomicAdd((unsigned long long *)&S.sums[e], (unsigned long long)x);
+    const uint32_t x = __reduce_add_sync(0xFFFFFFFFu, ls[e]);
+    if (lane_id() == 0 && x != 0u) atomicAdd((unsigned long long *)&S.sums[e], (unsigned long long)x);
   }
   __syncthreads();
   if (D == kBJ1) {
@@ -248,97 +232,137 @@ __device__ unsigned long long prefix_tile_dff(const EvalArgs &A, const InstView 
   }
   if (S.err) return 0ull;
 
-  PrefixCtx x;
-  x.s.n_small = S.sums[0];
-  x.s.n_big = S.sums[1];
-  x.s.n_half = S.sums[2];
-  x.s.n_full = S.sums[3];
-  x.s.sumw_big = S.sums[4];
-  x.s.sumw = S.sums[5];
-  x.TB = S.sums[6];
-  x.c = c;
-  x.U = U;
-  x.U1 = U + 1u;
-  int64_t hi_d;
-  param_range(D, c, x.lo_d, hi_d);
-  x.gbase = flat_index(D, x.lo_d, c);
-  int64_t B = ceil_div_fast(x.s.sumw, c);  // L1
+  const int64_t n_big = S.sums[1], n_half = S.sums[2], n_full = S.sums[3];
+  const int64_t sumw_big = S.sums[4], sumw = S.sums[5], TB = S.sums[6];
+  int64_t lo_d, hi_d;
+  param_range(D, c, lo_d, hi_d);
+  // flattened index of parameter l is gofs + l
+  const uint32_t gofs = flat_index(D, lo_d, c) - (uint32_t)lo_d;
+  int64_t B = ceil_div_fast(sumw, c);  // L1
   unsigned long long best = 0ull;
+  // S(l) = sum_w f(w, l) from the accumulators (bp_lb_core.cuh), l-independent parts:
+  //   MT:   E(l) + kS;   RAD2: A n1 + (B2 - A) n2s - (c - A - B2) n2b + kS;
+  //   CCM1: 2 acc + q kS;   BJ1: sumw - acc
+  int64_t kS;
+  if (D == kMT) kS = TB + sumw_big + n_half * (c / 2) + n_full * c;
+  else if (D == kRAD2) kS = n_big * c + n_half * (c / 2) + n_full * c;
+  else if (D == kCCM1) kS = 2 * n_big + n_half + 2 * n_full;
+  else kS = sumw;
 
   if (D == kMT || D == kRAD2) {
+    if (D == kMT && lam0 == 0 && tid == 0) best = make_key(B, gofs);  // l = 0: the bound L1
+    const int64_t A3 = c / 3, B2 = c / 2;
     for (int64_t l = lam0 + tid; l < lam_end; l += kPrefixNT) {
       const uint32_t l32 = (uint32_t)l;
-      int64_t acc;
+      int64_t Sv;
       if (D == kMT) {
-        acc = (int64_t)T0[min(l32, x.U1)] + x.TB;
+        Sv = (int64_t)T0[min(l32, U + 1u)] + kS;
       } else {
-        const uint32_t y = min(c32 - 2u * l32 + 1u, x.U1);
+        const uint32_t y = min(c32 - 2u * l32 + 1u, U + 1u);
         const int64_t n1 = T0[l32], n2s = T1[y], n2b = (int64_t)T1[y] - T0[y];
-        acc = rad2_sum(x.s, c, n1, n2s, n2b);
+        Sv = A3 * n1 + (B2 - A3) * n2s - (c - A3 - B2) * n2b + kS;
       }
-      consider<D>(x, l32, acc, B, best);
+      try_key(Sv, c, gofs + l32, B, best);
     }
     return best;
   }
 
-  // CCM1 / BJ1: lookups per parameter fall like X / l.
+  // CCM1 / BJ1: the lookups of parameter l fall like X / l.
   const uint32_t X = (D == kCCM1) ? U : c32;
   const int64_t cta_end = max(lam0, min(lam_end, min((int64_t)(X / kCtaBlocks) + 1, lam0 + kMaxHeavy)));
   const int64_t warp_end = max(cta_end, min(lam_end, (int64_t)(X / kWarpBlocks) + 1));
   const int lane = (int)lane_id(), warp = tid >> 5;
+  // S and f of parameter l with q = floor(c / l) and the accumulator
+  auto finish = [&](uint32_t l, uint32_t q, uint32_t acc) {
+    int64_t Sv, f;
+    if (D == kCCM1) {
+      Sv = 2 * (int64_t)(int32_t)acc + (int64_t)q * kS;
+      f = 2 * (int64_t)q;
+    } else {
+      Sv = kS - (int64_t)acc;
+      f = (int64_t)(q * (l - (c32 - q * l)));  // q (l - cm) <= c
+    }
+    try_key(Sv, f, gofs + l, B, best);
+  };
 
   // ---- parameters shared by the whole CTA ---------------------------------------
   const int ncta = (int)(cta_end - lam0);
   if (ncta > 0) {
-    for (int i = tid; i < ncta; i += kPrefixNT) S.heavy_acc[i] = 0u;
+    if (tid < ncta) {
+      const uint32_t l = (uint32_t)(lam0 + tid);
+      S.heavy_cm[tid] = c32 % l;
+      S.heavy_acc[tid] = 0u;
+    }
     __syncthreads();
     for (int i = 0; i < ncta; ++i) {
       const uint32_t l = (uint32_t)(lam0 + i);
-      const uint32_t cm = c32 % l;
+      const uint32_t cm = S.heavy_cm[i];
       if (D == kBJ1 && cm == 0u) continue;  // every BJ1 term is 0
-      const uint32_t part = warp_sum(block_terms<D>(T0, c32, U, l, cm, (uint32_t)tid, kPrefixNT));
+      const uint32_t part =
+          __reduce_add_sync(0xFFFFFFFFu, block_terms<D>(T0, c32, U, l, cm, (uint32_t)tid, kPrefixNT));
       if (lane == 0 && part != 0u) atomicAdd(&S.heavy_acc[i], part);
     }
     __syncthreads();
     if (tid < ncta) {
       const uint32_t l = (uint32_t)(lam0 + tid);
-      const int64_t acc = (D == kCCM1) ? (int64_t)(int32_t)S.heavy_acc[tid] : (int64_t)S.heavy_acc[tid];
-      consider<D>(x, l, acc, B, best);
+      finish(l, c32 / l, S.heavy_acc[tid]);
     }
   }
 
-  // ---- parameters shared by one warp (lane t of a round of 32 keeps the t-th) ---
+  // ---- parameters shared by one warp --------------------------------------------
+  // Round i gives warp w the parameter cta_end + 8 i + w (i even) or + 7 - w
+  // (i odd); lane t of a batch of 32 rounds owns the t-th one: it computes
+  // its quotient, broadcasts cm, and keeps the warp's sum.
   {
     const int64_t nwarp = warp_end - cta_end;
-    // warp w takes the parameters cta_end + w + 8 i, i = 0, 1, ...
-    const int64_t mine_n = nwarp > warp ? (nwarp - warp + kPrefixWarps - 1) / kPrefixWarps : 0;
-    for (int64_t r0 = 0; r0 < mine_n; r0 += 32) {
+    const int64_t rounds = (nwarp + kPrefixWarps - 1) / kPrefixWarps;
+    for (int64_t r0 = 0; r0 < rounds; r0 += 32) {
+      const int64_t ri = r0 + lane;
+      const int64_t my_l = cta_end + ri * kPrefixWarps + ((ri & 1) ? kPrefixWarps - 1 - warp : warp);
+      const bool mine_ok = ri < rounds && my_l < warp_end;
+      const uint32_t ml = mine_ok ? (uint32_t)my_l : 1u;
+      const uint32_t mq = c32 / ml;
+      const uint32_t mcm = c32 - mq * ml;
       uint32_t mine = 0;
-      const int cnt = (int)min((int64_t)32, mine_n - r0);
+      const int cnt = (int)min((int64_t)32, rounds - r0);
       for (int t = 0; t < cnt; ++t) {
-        const uint32_t l = (uint32_t)(cta_end + warp + (r0 + t) * kPrefixWarps);
-        const uint32_t cm = c32 % l;
-        uint32_t part = 0;
-        if (D == kCCM1 || cm != 0u) part = warp_sum(block_terms<D>(T0, c32, U, l, cm, (uint32_t)lane, 32u));
+        const uint32_t l = __shfl_sync(0xFFFFFFFFu, ml, t);
+        const uint32_t cm = __shfl_sync(0xFFFFFFFFu, mcm, t);
+        const bool ok = __shfl_sync(0xFFFFFFFFu, (int)mine_ok, t) != 0;
+        if (!ok || (D == kBJ1 && cm == 0u)) continue;
+        const uint32_t part =
+            __reduce_add_sync(0xFFFFFFFFu, block_terms<D>(T0, c32, U, l, cm, (uint32_t)lane, 32u));
         if (lane == t) mine = part;
       }
-      if (lane < cnt) {
-        const uint32_t l = (uint32_t)(cta_end + warp + (r0 + lane) * kPrefixWarps);
-        consider<D>(x, l, D == kCCM1 ? (int64_t)(int32_t)mine : (int64_t)mine, B, best);
-      }
+      if (mine_ok) finish(ml, mq, mine);
     }
   }
 
   // ---- one thread per parameter; alternate directions balance the rounds --------
-  for (int64_t r = warp_end; r < lam_end; r += kPrefixNT) {
-    const int64_t round = (r - warp_end) / kPrefixNT;
-    const int64_t l = r + ((round & 1) ? kPrefixNT - 1 - tid : tid);
-    if (l >= lam_end) continue;
-    const uint32_t l32 = (uint32_t)l;
-    const uint32_t cm = c32 % l32;
-    uint32_t acc = 0;
-    if (D == kCCM1 || cm != 0u) acc = block_terms<D>(T0, c32, U, l32, cm, 0u, 1u);
-    consider<D>(x, l32, D == kCCM1 ? (int64_t)(int32_t)acc : (int64_t)acc, B, best);
+  // A thread's parameters increase, so its quotient q = floor(c / l) only
+  // needs decrementing after the first division.
+  {
+    uint32_t q = 0;
+    bool first = true, odd = false;
+    for (int64_t r = warp_end; r < lam_end; r += kPrefixNT, odd = !odd) {
+      const int64_t l = r + (odd ? kPrefixNT - 1 - tid : tid);
+      if (l >= lam_end) continue;
+      const uint32_t l32 = (uint32_t)l;
+      if (first) {
+        q = c32 / l32;
+        first = false;
+      } else {
+        while (q * l32 > c32) --q;
+      }
+      uint32_t acc = 0;
+      if (D == kCCM1) {
+        acc = block_terms<D>(T0, c32, U, l32, 0u, 0u, 1u);
+      } else {
+        const uint32_t cm = c32 - q * l32;
+        if (cm != 0u) acc = bj1_blocks(T0, l32, cm, q);
+      }
+      finish(l32, q, acc);
+    }
   }
   return best;
 }
