@@ -44,12 +44,12 @@ NODES, N_ITEMS, CAP = 4096, 500, 10_000
 #   RAD2 two compares + two counts                                   4
 #   FS1  mul, mul-high, shift, add, mul, compare, conditional add    7
 #   CCM1 one multiply-high-add (c <= 131071)                         1   (else 3)
-#   VB2  mul-add, mul-high, shift, add (c <= 65535)                  4   (fp32 path 5)
+#   VB2  mul-add, half of a two-word add of an item pair (c <= 65535) 2   (fp32 path 5)
 #   BJ1  mul-high, two mul-adds, min, add (c <= 65535)               5   (else 6)
 def ops_per_eval(d, c):
     return {0: 2, 1: 4, 2: 7,
             3: 1 if c <= 131071 else 3,
-            4: 4 if c <= 65535 else 5,
+            4: 2 if c <= 65535 else 5,
             5: 5 if c <= 65535 else 6}[d]
 SM_COUNT_NOMINAL = 152
 # DRAM bytes (read + write) per search node of one eval_kernel launch over the
@@ -76,7 +76,7 @@ def reduced_sizes(nd):
 def algorithmic_work(nd, algo=1):
     """(item-parameter evals of the whole check, integer ops of the direct
     kernel) of one batch: the direct kernel evaluates every (item, parameter)
-    pair of the DFFs the router leaves to it; MT, CCM1 and BJ1 go to the
+    pair of the DFFs the router leaves to it; MT, RAD2, CCM1 and BJ1 go to the
     prefix-count kernel where their tables fit (bp_lb_dff_route)."""
     from paper_2402_14821_gb300 import binding as B
     r = reduced_sizes(nd)

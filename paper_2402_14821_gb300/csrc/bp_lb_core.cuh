@@ -40,7 +40,7 @@ constexpr int64_t kMaxCapacity = int64_t(1) << 30;
 constexpr int64_t kMaxItems = int64_t(1) << 20;
 // Fast-path limits (the generic 64-bit path takes over above them).
 constexpr int64_t kNarrowCap = int64_t(1) << 28;   // 32-bit partial sums, all DFFs
-constexpr int64_t kVb2MagicCap = 65535;            // 2(u*l + c - 1) < 2^32
+constexpr int64_t kVb2FixedCap = 65535;            // (l + 1) c < 2^32 for l <= c
 constexpr int64_t kVb2FloatCap = int64_t(1) << 22; // fp32 quotient estimate exact
 constexpr int64_t kFs1FastCap = 21262214;          // 101 * c < 2^31
 constexpr int64_t kCcm1NoShiftCap = 131071;        // u e < (c/2)^2 < 2^32

@@ -217,39 +217,39 @@ BPLB_D void ccm1_list_noshift(const uint32_t *s, int beg, int end, int K, const 
   }
 }
 
-// ---- VB2 (u2 = 2u): acc += SIGN * ceil(u l / c) ---------------------------------
-// c <= 65535: ceil(u l / c) = floor((u l + c - 1) / c), numerator < 2^31, exact
-// multiply-high division by c.  A thread's parameters are consecutive
-// (lam[1] = lam[0] + 1 whenever lam[1] is valid), so the numerator of the
-// second one is the first one's plus u2: an ALU-pipe add replaces one
-// multiply-add, balancing the two integer pipes.
+// ---- VB2, c <= 65535: acc += SIGN * sum ceil(u l / c) by fixed-point fractions ----
+// The list holds F = ceil(u 2^32 / c) (< 2^31 as u < c / 2).  With
+// Y0 = ceil((c - 1) 2^32 / c), the 64-bit Y = l F + Y0 equals
+// 2^32 (u l + c - 1) / c + e with 0 <= e < l + 1; the fraction of
+// (u l + c - 1) / c is at most (c - 1) / c, and (l + 1) c < 2^32 keeps
+// e / 2^32 below 1 / c, so floor(Y / 2^32) = floor((u l + c - 1) / c)
+// = ceil(u l / c) exactly.  Over the list,
+//   sum floor(Y / 2^32) = (sum Y - sum (Y mod 2^32)) / 2^32,
+// with sum Y = l sum F + n Y0 and Y mod 2^32 one 32-bit multiply-add per
+// item: no multiply-high in the loop (padding slots hold F = 0 and cancel).
 template <int T, int SIGN>
-BPLB_D void vb2_list_magic(const uint32_t *s, int beg, int end, int K, const uint32_t (&lam)[T],
-                           Div31 Dc, uint32_t add2, int64_t (&acc)[T]) {
-  for (int g0 = beg; g0 < end; g0 += K) {
-    const int g1 = min(end, g0 + K);
-    uint32_t a[T];
+BPLB_D void vb2_list_fixed(const uint32_t *s, int beg, int end, const uint32_t (&lam)[T],
+                           uint32_t Y0, uint64_t sumF, int64_t (&acc)[T]) {
+  uint64_t z[T];
 #pragma unroll
-    for (int j = 0; j < T; ++j) a[j] = 0;
+  for (int j = 0; j < T; ++j) z[j] = 0;
 #pragma unroll 2
-    for (int i = g0; i < g1; i += 4) {
-      const uint4 v = lds4(s, i);
-      const uint32_t u4[4] = {v.x, v.y, v.z, v.w};
+  for (int i = beg; i < end; i += 4) {
+    const uint4 v = lds4(s, i);
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        uint32_t x[T];
-#pragma unroll
-        for (int j = 0; j < T; ++j) {
-          // 2 (u l + c - 1) = u2 * l + (2c - 2)
-          x[j] = (T > 1 && j == 1) ? x[0] + u4[e] : u4[e] * lam[j] + add2;
-          a[j] += div31(x[j], Dc);
-        }
-      }
+    for (int j = 0; j < T; ++j) {
+      z[j] += (uint64_t)(v.x * lam[j] + Y0) + (uint64_t)(v.y * lam[j] + Y0);
+      z[j] += (uint64_t)(v.z * lam[j] + Y0) + (uint64_t)(v.w * lam[j] + Y0);
     }
-#pragma unroll
-    for (int j = 0; j < T; ++j) acc[j] += SIGN * (int64_t)a[j];
   }
+  const uint64_t nY0 = (uint64_t)(end - beg) * Y0;
+#pragma unroll
+  for (int j = 0; j < T; ++j)
+    acc[j] += SIGN * (int64_t)(((uint64_t)lam[j] * sumF + nY0 - z[j]) >> 32);
 }
+
+// The fixed-point list value F = ceil(u 2^32 / c) and offset Y0 of vb2_list_fixed.
+BPLB_HD uint32_t vb2_fixed_frac(uint64_t u, uint64_t c) { return (uint32_t)(((u << 32) + c - 1) / c); }
 
 // 65535 < c <= 2^22: an fp32 estimate of the quotient, corrected exactly.
 //   a = fl(u / c) (correctly rounded, staged with the list), relative error

@@ -280,6 +280,7 @@ struct TileShared {
   int pad_;
   unsigned long long warp_key[32];
   long long sums[6];
+  unsigned long long sumF[2];  // VB2 fixed point: sum of F over the small and big lists
 };
 
 // Fetches stream position q: returns true and the size when q is an item of
@@ -365,10 +366,11 @@ struct LocalSums {
 // Sizes outside [0, c] set S.err.  `count` adds the instance sums.
 template <int NT, int MODE, bool ULIST>
 __device__ __forceinline__ void stage_chunk(const EvalArgs &A, const InstView &I, const uint32_t *s_load,
-                                            int64_t p, int len, bool stage_a, bool count, int shift,
-                                            uint32_t *s_items, float *s_a, TileShared &S,
+                                            int64_t p, int len, bool stage_a, bool fixed, bool count,
+                                            int shift, uint32_t *s_items, float *s_a, TileShared &S,
                                             LocalSums &ls) {
   const int64_t c = I.c;
+  uint64_t fs = 0, fb = 0;  // sums of the fixed-point values (fixed only)
   for (int o = 0; o < len; o += NT) {
     const int64_t q = p + o + threadIdx.x;
     int64_t w = 0;
@@ -394,17 +396,37 @@ __device__ __forceinline__ void stage_chunk(const EvalArgs &A, const InstView &I
       const int ps = warp_append(small, &S.ns);
       const int pb = warp_append(big, &S.nb);
       if (small) {
-        s_items[ps] = (uint32_t)w << shift;
+        if (fixed) {
+          const uint32_t F = vb2_fixed_frac((uint64_t)w, (uint64_t)c);
+          s_items[ps] = F;
+          fs += F;
+        } else {
+          s_items[ps] = (uint32_t)w << shift;
+        }
         if (stage_a) s_a[ps] = __fdiv_rn((float)w, (float)c);
       }
       if (big) {
         const int slot = kListTop - 1 - pb;
-        s_items[slot] = (uint32_t)(c - w) << shift;
+        if (fixed) {
+          const uint32_t F = vb2_fixed_frac((uint64_t)(c - w), (uint64_t)c);
+          s_items[slot] = F;
+          fb += F;
+        } else {
+          s_items[slot] = (uint32_t)(c - w) << shift;
+        }
         if (stage_a) s_a[slot] = __fdiv_rn((float)(c - w), (float)c);
       }
     } else {
       const int ps = warp_append(have, &S.ns);
       if (have) s_items[ps] = (uint32_t)w << shift;
+    }
+  }
+  if (fixed) {
+    fs = warp_sum(fs);
+    fb = warp_sum(fb);
+    if (lane_id() == 0) {
+      if (fs) atomicAdd(&S.sumF[0], (unsigned long long)fs);
+      if (fb) atomicAdd(&S.sumF[1], (unsigned long long)fb);
     }
   }
 }
@@ -428,8 +450,9 @@ __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int
   int64_t lo_d, hi_d;
   param_range(D, c, lo_d, hi_d);
   const uint32_t gbase = flat_index(D, lo_d, c);
-  const bool vb2_magic = c <= kVb2MagicCap;
-  const bool stage_a = (D == kVB2) && !vb2_magic && c <= kVb2FloatCap;
+  const bool vb2_fixed = (D == kVB2) && c <= kVb2FixedCap;
+  const bool stage_a = (D == kVB2) && !vb2_fixed && c <= kVb2FloatCap;
+  const uint32_t Y0 = vb2_fixed ? vb2_fixed_frac((uint64_t)c - 1, (uint64_t)c) : 0u;
   const bool narrow = c <= kNarrowCap;  // BJ1: terms < 2c stay below 2^30
   const bool fs1_fast = c <= kFs1FastCap;
   const bool ccm1_noshift = c <= kCcm1NoShiftCap;
@@ -515,11 +538,12 @@ __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int
         if (tid == 0) {
           S.ns = 0;
           S.nb = 0;
+          S.sumF[0] = S.sumF[1] = 0ull;
         }
         __syncthreads();
         const int len = (int)min((int64_t)kChunk, L - p);
-        stage_chunk<NT, MODE, ULIST>(A, I, s_load, p, len, stage_a, g == 0, shift, s_items, s_a,
-                                     S, ls);
+        stage_chunk<NT, MODE, ULIST>(A, I, s_load, p, len, stage_a, vb2_fixed, g == 0, shift,
+                                     s_items, s_a, S, ls);
         __syncthreads();
         const int ns = S.ns, nb = S.nb;
         const int ns_pad = (ns + 3) & ~3;
@@ -568,10 +592,9 @@ __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int
           }
         } else if (D == kVB2) {
           const int K = group_len(c / 2 + 1);
-          if (vb2_magic) {
-            const uint32_t add2 = (uint32_t)(2 * c - 2);
-            vb2_list_magic<T, 1>(s_items, 0, ns_pad, K, k0, Dc, add2, acc);
-            vb2_list_magic<T, -1>(s_items, bstart, kListTop, K, k0, Dc, add2, acc);
+          if (vb2_fixed) {
+            vb2_list_fixed<T, 1>(s_items, 0, ns_pad, k0, Y0, S.sumF[0], acc);
+            vb2_list_fixed<T, -1>(s_items, bstart, kListTop, k0, Y0, S.sumF[1], acc);
           } else if (stage_a) {
             const uint32_t K2 = 0u - c2 * kF32RoundBits;
             vb2_list_float<T, 1>(s_items, s_a, 0, ns_pad, K, k0, kf, c2, K2, acc);
