@@ -73,14 +73,27 @@ def reduced_sizes(nd):
     return r
 
 
-def algorithmic_work(nd, algo=1):
-    """(item-parameter evals of the whole check, integer ops of the direct
-    kernel) of one batch: the direct kernel evaluates every (item, parameter)
-    pair of the DFFs the router leaves to it; MT, RAD2, CCM1 and BJ1 go to the
-    prefix-count kernel where their tables fit (bp_lb_dff_route)."""
+VB2_FIXED_CAP = 65535
+
+
+def kernel_of(d, c, stream_len, algo=1):
+    """Which batched kernel evaluates DFF d: "prefix" (the prefix-count kernel,
+    where bp_lb_dff_route says so), "vb2" (VB2 at c <= 65535, its own kernel)
+    or "direct" (the generic direct kernel)."""
     from paper_2402_14821_gb300 import binding as B
+    if B.bp_lb_dff_route(d, c, stream_len, algo) == B.ALGO_PREFIX:
+        return "prefix"
+    return "vb2" if d == 4 and c <= VB2_FIXED_CAP else "direct"
+
+
+def algorithmic_work(nd, algo=1):
+    """(item-parameter evals of the whole check, {kernel: integer ops}) of one
+    batch: the VB2 kernel and the generic direct kernel evaluate every (item,
+    parameter) pair of the DFFs routed to them; MT, RAD2, CCM1 and BJ1 go to
+    the prefix-count kernel where their tables fit."""
     r = reduced_sizes(nd)
-    evals = ops = 0
+    evals = 0
+    ops = {"vb2": 0, "direct": 0, "prefix": 0}
     for j in range(nd.count):
         b = int(nd.node_base[j])
         c = int(nd.base.capacity[b])
@@ -88,8 +101,9 @@ def algorithmic_work(nd, algo=1):
         cnt = param_counts(c)
         for d in range(6):
             evals += int(r[j]) * cnt[d]
-            if B.bp_lb_dff_route(d, c, L, algo) == B.ALGO_DIRECT:
-                ops += int(r[j]) * cnt[d] * ops_per_eval(d, c)
+            k = kernel_of(d, c, L, algo)
+            if k != "prefix":
+                ops[k] += int(r[j]) * cnt[d] * ops_per_eval(d, c)
     return evals, ops
 
 
@@ -313,9 +327,10 @@ def main():
             e1.record(stream)
         barrier()
     step_ms = np.array([e0.elapsed_time(e1) for e0, e1 in ev])
-    ms_prefix, ms_direct, n_calls = B.bp_lb_kernel_times(h)
+    ms_prefix, ms_vb2, ms_direct, n_calls = B.bp_lb_kernel_times(h)
     B.bp_lb_set_kernel_timing(h, False)
     t_direct = ms_direct / max(1, n_calls)
+    t_vb2 = ms_vb2 / max(1, n_calls)
     t_prefix = ms_prefix / max(1, n_calls)
     t_step = float(step_ms.mean())
     if world > 1:
@@ -386,7 +401,11 @@ def main():
     sm_mhz_max = float(peaks.get("sm_max_mhz", 2070.0))
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     peak_ops = sms * 4 * 32 * sm_mhz_max * 1e6        # one warp instruction / clk / SMSP
-    achieved = ops / (t_direct / 1e3)
+    # the dominant item-by-item kernel: the VB2 kernel unless the generic one
+    # took longer
+    dom = "vb2" if t_vb2 >= t_direct else "direct"
+    t_dom = t_vb2 if dom == "vb2" else t_direct
+    achieved = ops[dom] / (t_dom / 1e3)
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -410,12 +429,17 @@ def main():
                                  if TRAFFIC_BYTES_PER_NODE is not None else None),
                      "peak_basis": f"{sms} SMs x 4 SMSP x 32 lanes x {sm_mhz_max:.0f} MHz "
                                    "(integer issue, one warp instruction per clock per SMSP)",
-                     "kernel": "eval_kernel (direct evaluation: VB2, FS1 here), its own "
-                               "CUDA-event time per launch",
-                     "direct_kernel_ms": t_direct, "prefix_kernel_ms": t_prefix},
+                     "kernel": ("vb2_kernel (VB2 item by item, fixed-point quotients)"
+                                if dom == "vb2" else
+                                "eval_kernel (generic direct evaluation: FS1, VB2 here)")
+                               + ", its own CUDA-event time per launch",
+                     "vb2_kernel_ms": t_vb2, "direct_kernel_ms": t_direct,
+                     "prefix_kernel_ms": t_prefix,
+                     "direct_kernel_frac": (ops["direct"] / (t_direct / 1e3) / peak_ops
+                                            if t_direct > 0 else None)},
         "launch_shape": {"chosen": shape, "nt_t_g_minb": list(B.bp_lb_launch_shape_info(shape)),
                          "autotune_ms": [round(x, 4) for x in shape_ms]},
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": 4 * args.steps,
         "clocks": clocks,
         "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"{cpu_m} of the {NODES} nodes (reduction + full bound), "
@@ -454,8 +478,8 @@ def _peak_ops():
 
 
 def ragged_work(rg, algo=1):
-    """(evals, direct-kernel ops) of a ragged batch of reduced instances."""
-    from paper_2402_14821_gb300 import binding as B
+    """(evals, item-by-item integer ops of the VB2 and direct kernels) of a
+    ragged batch of reduced instances."""
     evals = ops = 0
     for b in range(rg.count):
         c = int(rg.capacity[b])
@@ -463,7 +487,7 @@ def ragged_work(rg, algo=1):
         cnt = param_counts(c)
         evals += r * sum(cnt)
         ops += r * sum(cnt[d] * ops_per_eval(d, c) for d in range(6)
-                       if B.bp_lb_dff_route(d, c, r, algo) == B.ALGO_DIRECT)
+                       if kernel_of(d, c, r, algo) != "prefix")
     return evals, ops
 
 
@@ -499,15 +523,16 @@ def run_sweep(args):
                         B.bp_lb_set_kernel_timing(h, True)
                         B.bp_lb_kernel_times(h)
                         ms = _time_steps(step, steps, flush, stream)
-                        kp, kd, kn = B.bp_lb_kernel_times(h)
+                        kp, kv, kd, kn = B.bp_lb_kernel_times(h)
                         B.bp_lb_set_kernel_timing(h, False)
                         tm = float(ms.mean())
-                        td = kd / max(1, kn)
+                        td = (kv + kd) / max(1, kn)
                         out["results"].append({
                             "c": c, "family": fam, "dtype": np.dtype(dt).name, "instances": 64,
                             "n": 10_000, "ms_per_batch": tm, "checks_per_s": 64 / (tm / 1e3),
                             "evals_per_s": evals / (tm / 1e3), "launch_shape": shape,
-                            "direct_kernel_ms": td, "prefix_kernel_ms": kp / max(1, kn),
+                            "item_kernels_ms": td, "vb2_kernel_ms": kv / max(1, kn),
+                            "prefix_kernel_ms": kp / max(1, kn),
                             "roofline_frac": ops / (td / 1e3) / peak})
                         print(json.dumps(out["results"][-1]), flush=True)
         elif args.workload == "plain":
@@ -564,7 +589,8 @@ def run_sweep(args):
             B.bp_serve_destroy(srv)
         else:  # ragged
             nd = I.ragged_nodes(seed=3)
-            evals, ops = algorithmic_work(nd)
+            evals, kops = algorithmic_work(nd)
+            ops = kops["vb2"] + kops["direct"]
             t_in = dict(base_offsets=_dev(nd.base.offsets, torch.int64),
                         base_sizes=_dev(nd.base.sizes, torch.int32),
                         base_capacity=_dev(nd.base.capacity, torch.int64),
@@ -598,9 +624,9 @@ def run_sweep(args):
             B.bp_lb_set_kernel_timing(h, True)
             B.bp_lb_kernel_times(h)
             ms_direct = _time_steps(direct, steps, flush, stream)
-            kp, kd, kn = B.bp_lb_kernel_times(h)
+            kp, kv, kd, kn = B.bp_lb_kernel_times(h)
             B.bp_lb_set_kernel_timing(h, False)
-            td = kd / max(1, kn)
+            td = (kv + kd) / max(1, kn)
             tm = float(ms_graph.mean())
             out["results"].append({
                 "instances": nd.count, "ms_per_batch_graph": tm,
@@ -608,7 +634,8 @@ def run_sweep(args):
                 "checks_per_s": nd.count / (tm / 1e3), "evals_per_s": evals / (tm / 1e3),
                 "evals_per_batch": evals, "launch_shape": shape,
                 "autotune_ms": [round(x, 3) for x in shape_ms],
-                "direct_kernel_ms": td, "prefix_kernel_ms": kp / max(1, kn),
+                "item_kernels_ms": td, "vb2_kernel_ms": kv / max(1, kn),
+                "prefix_kernel_ms": kp / max(1, kn),
                 "roofline_frac": ops / (td / 1e3) / peak})
             print(json.dumps(out["results"][-1]), flush=True)
     out["clocks"] = clk.summary()

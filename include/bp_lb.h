@@ -255,12 +255,15 @@ int bp_lb_set_algorithm(bp_lb_t *h, int32_t algo);
 int bp_lb_get_algorithm(bp_lb_t *h);
 
 /* Measurement aid: with timing on, every batched call records CUDA events
- * on its stream around its prefix-count launch and its direct launch (not
- * for use under stream capture).  bp_lb_kernel_times waits for the events
- * recorded since the previous query and returns the total milliseconds of
- * each kernel and the number of calls (any pointer may be NULL). */
+ * on its stream around its three evaluation launches -- the prefix-count
+ * kernel, the VB2 kernel (VB2 at c <= 65535, evaluated item by item with its
+ * fixed-point quotients) and the generic direct kernel (every other (DFF,
+ * lambda) evaluated item by item) -- (not for use under stream capture).
+ * bp_lb_kernel_times waits for the events recorded since the previous query
+ * and returns the total milliseconds of each kernel and the number of calls
+ * (any pointer may be NULL). */
 int bp_lb_set_kernel_timing(bp_lb_t *h, int32_t on);
-int bp_lb_kernel_times(bp_lb_t *h, double *ms_prefix, double *ms_direct,
+int bp_lb_kernel_times(bp_lb_t *h, double *ms_prefix, double *ms_vb2, double *ms_direct,
                        int64_t *calls);
 
 /* ---- launch shapes and autotuning ---------------------------------------- */

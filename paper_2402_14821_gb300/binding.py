@@ -81,7 +81,7 @@ def _bind(lib):
         "bp_lb_set_kernel_timing": (ctypes.c_int, [_vp, _c_i32]),
         "bp_lb_dff_route": (ctypes.c_int, [_c_i32, _c_i64, _c_i64, _c_i32]),
         "bp_lb_kernel_times": (ctypes.c_int, [_vp, P(ctypes.c_double), P(ctypes.c_double),
-                                              P(_c_i64)]),
+                                              P(ctypes.c_double), P(_c_i64)]),
         "bp_serve_create": (ctypes.c_int, [_c_i64, _c_i32, _c_i64, _c_i32, _c_i32, _c_i64, P(_vp)]),
         "bp_serve_destroy": (ctypes.c_int, [_vp]),
         "bp_serve_register": (ctypes.c_int, [_vp, _vp, _c_i64, _c_i64, P(_c_i32)]),
@@ -301,11 +301,13 @@ def bp_lb_set_kernel_timing(h, on: bool):
 
 
 def bp_lb_kernel_times(h):
-    """(ms in prefix kernels, ms in direct kernels, calls) since the last query."""
-    p, d, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
-    _check(lib().bp_lb_kernel_times(h, ctypes.byref(p), ctypes.byref(d), ctypes.byref(n)),
+    """(ms in the prefix-count kernel, ms in the VB2 kernel, ms in the generic
+    direct kernel, calls) since the last query."""
+    p, v, d, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    _check(lib().bp_lb_kernel_times(h, ctypes.byref(p), ctypes.byref(v), ctypes.byref(d),
+                                    ctypes.byref(n)),
            "bp_lb_kernel_times")
-    return p.value, d.value, n.value
+    return p.value, v.value, d.value, n.value
 
 
 def bp_lb_dff_route(d: int, c: int, stream_len: int, algo: int = 1) -> int:

@@ -60,12 +60,16 @@ struct bp_lb {
   int32_t cap_batch = 0;
   int64_t *d_tile_start = nullptr;
   int64_t *d_ptile_start = nullptr;  // prefix-kernel tile table
+  int64_t *d_vtile_start = nullptr;  // VB2-kernel tile table
   int32_t prefix_on = 1;             // batched modes: BP_ALGO_PREFIX (default) or DIRECT
   int32_t plain_prefix_on = 1;       // plain modes
+  // batched modes send VB2 (c <= 65535) to the VB2 kernel; the plain path
+  // keeps it in the direct kernel (one launch fewer per check)
+  int32_t vb2_on = 1;
   // optional per-kernel timing of batched calls (events around each launch)
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
-  std::vector<std::array<cudaEvent_t, 3>> ev_pending;
+  std::vector<std::array<cudaEvent_t, 4>> ev_pending;
   size_t ev_next = 0;
   unsigned long long *d_keys = nullptr;
   unsigned int *d_done = nullptr;
@@ -129,15 +133,18 @@ int grow_batch(bp_lb *h, int32_t B) {
   int32_t cap = std::max<int32_t>(B, 1024);
   cudaFree(h->d_tile_start);
   cudaFree(h->d_ptile_start);
+  cudaFree(h->d_vtile_start);
   cudaFree(h->d_keys);
   cudaFree(h->d_done);
   h->d_tile_start = nullptr;
   h->d_ptile_start = nullptr;
+  h->d_vtile_start = nullptr;
   h->d_keys = nullptr;
   h->d_done = nullptr;
   h->cap_batch = 0;
   BP_CHECK(cudaMalloc(&h->d_tile_start, sizeof(int64_t) * ((size_t)cap + 1)));
   BP_CHECK(cudaMalloc(&h->d_ptile_start, sizeof(int64_t) * ((size_t)cap + 1)));
+  BP_CHECK(cudaMalloc(&h->d_vtile_start, sizeof(int64_t) * ((size_t)cap + 1)));
   BP_CHECK(cudaMalloc(&h->d_keys, sizeof(unsigned long long) * (size_t)cap));
   BP_CHECK(cudaMalloc(&h->d_done, sizeof(unsigned int) * (size_t)cap));
   BP_CHECK(cudaMemset(h->d_keys, 0, sizeof(unsigned long long) * (size_t)cap));
@@ -164,6 +171,11 @@ int launch_prefix(int mode, unsigned grid, size_t smem, cudaStream_t st, EvalArg
                                       dim3(kPrefixNT), args, smem, st));
 }
 
+// Dynamic shared memory of the VB2 kernel.
+size_t vb2_smem(int mode, int64_t max_bins) {
+  return kVb2ListBytes + (mode == kSrcNodes ? sizeof(uint32_t) * (size_t)max_bins : 0);
+}
+
 // Next event of the timing pool (grown on demand; timing is for measurement
 // runs, not for stream capture).
 cudaEvent_t next_event(bp_lb *h) {
@@ -188,12 +200,16 @@ int launch_batch(bp_lb *h, EvalArgs A, size_t smem, cudaStream_t st) {
   A.ptile_start = h->d_ptile_start;
   A.pwork = h->d_work + 1;
   A.plpt = kPrefixLPTBatch;
+  A.vb2_on = h->vb2_on;
+  A.vtile_start = h->d_vtile_start;
+  A.vwork = h->d_work + 2;
   const int shape = h->shape[MODE];
   const int occ = occupancy(h, MODE, smem);
   if (occ <= 0) return BP_ECUDA;
-  plan_kernel<MODE><<<1, 1024, 0, st>>>(A, shape_lpt(shape), h->d_tile_start, h->d_ptile_start);
+  plan_kernel<MODE><<<1, 1024, 0, st>>>(A, shape_lpt(shape), h->d_tile_start, h->d_ptile_start,
+                                        h->d_vtile_start);
   BP_CHECK(cudaGetLastError());
-  std::array<cudaEvent_t, 3> ev = {nullptr, nullptr, nullptr};
+  std::array<cudaEvent_t, 4> ev = {nullptr, nullptr, nullptr, nullptr};
   if (h->timing) {
     for (auto &e : ev)
       if (!(e = next_event(h))) return BP_ECUDA;
@@ -209,9 +225,21 @@ int launch_batch(bp_lb *h, EvalArgs A, size_t smem, cudaStream_t st) {
     BP_CHECK_STATUS(launch_prefix(MODE, (unsigned)(h->num_sms * pocc), ps, st, A));
   }
   if (h->timing) BP_CHECK(cudaEventRecord(ev[1], st));
+  if (h->vb2_on) {
+    // VB2's tiles on their own kernel (empty when no instance has any)
+    const size_t vs = vb2_smem(MODE, A.max_bins);
+    int vocc = 0;
+    BP_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &vocc, (const void *)vb2_fn(shape, MODE), kVb2NT, vs));
+    if (vocc <= 0) return BP_ECUDA;
+    void *args[] = {&A};
+    BP_CHECK(cudaLaunchKernel((const void *)vb2_fn(shape, MODE), dim3((unsigned)(h->num_sms * vocc)),
+                              dim3(kVb2NT), args, vs, st));
+  }
+  if (h->timing) BP_CHECK(cudaEventRecord(ev[2], st));
   BP_CHECK_STATUS(launch_eval(shape, MODE, (unsigned)(h->num_sms * occ), smem, st, A));
   if (h->timing) {
-    BP_CHECK(cudaEventRecord(ev[2], st));
+    BP_CHECK(cudaEventRecord(ev[3], st));
     h->ev_pending.push_back(ev);
   }
   return BP_OK;
@@ -298,10 +326,10 @@ int bp_lb_create(int64_t capacity, int64_t max_items, bp_lb_t **out) {
     if ((st = cuda_status(cudaMallocHost(&h->h_out, sizeof(PlainOut)))) != BP_OK) break;
     if ((st = cuda_status(cudaMalloc(&h->d_key1, sizeof(unsigned long long)))) != BP_OK) break;
     if ((st = cuda_status(cudaMalloc(&h->d_done1, sizeof(unsigned int)))) != BP_OK) break;
-    if ((st = cuda_status(cudaMalloc(&h->d_work, 2 * sizeof(unsigned long long)))) != BP_OK) break;
+    if ((st = cuda_status(cudaMalloc(&h->d_work, 3 * sizeof(unsigned long long)))) != BP_OK) break;
     if ((st = cuda_status(cudaMemset(h->d_key1, 0, sizeof(unsigned long long)))) != BP_OK) break;
     if ((st = cuda_status(cudaMemset(h->d_done1, 0, sizeof(unsigned int)))) != BP_OK) break;
-    if ((st = cuda_status(cudaMemset(h->d_work, 0, 2 * sizeof(unsigned long long)))) != BP_OK)
+    if ((st = cuda_status(cudaMemset(h->d_work, 0, 3 * sizeof(unsigned long long)))) != BP_OK)
       break;
     for (int mode = 0; mode < 3 && st == BP_OK; ++mode)
       st = cuda_status(cudaFuncSetAttribute((const void *)prefix_fn(mode),
@@ -310,10 +338,15 @@ int bp_lb_create(int64_t capacity, int64_t max_items, bp_lb_t **out) {
     if (st != BP_OK) break;
     // the plain node path may use the full on-chip bin table
     const size_t smem_nodes = eval_smem<kSrcNodes>(kMaxNodeBins);
-    for (int sh = 0; sh < kNumShapes && st == BP_OK; ++sh)
+    for (int sh = 0; sh < kNumShapes && st == BP_OK; ++sh) {
       st = cuda_status(cudaFuncSetAttribute((const void *)eval_fn(sh, kSrcNodes),
                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)smem_nodes));
+      if (st == BP_OK)
+        st = cuda_status(cudaFuncSetAttribute((const void *)vb2_fn(sh, kSrcNodes),
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)vb2_smem(kSrcNodes, kMaxNodeBins)));
+    }
     if (st != BP_OK) break;
     if ((st = cuda_status(cudaFuncSetAttribute(reduce_kernel<256>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -343,6 +376,7 @@ int bp_lb_destroy(bp_lb_t *h) {
   cudaFree(h->d_work);
   cudaFree(h->d_tile_start);
   cudaFree(h->d_ptile_start);
+  cudaFree(h->d_vtile_start);
   cudaFree(h->d_keys);
   cudaFree(h->d_done);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -375,9 +409,12 @@ static EvalArgs plain_args(bp_lb *h, int64_t n, int64_t bins, int mode) {
   // mode is a plain mode; the sum bound is the stream length times c
   const int64_t sb = (mode == kModePlainNodes ? n + bins : n) * h->capacity;
   A.prefix_on = h->plain_prefix_on;
+  A.vb2_on = 0;
   A.plpt = kPrefixLPTSingle;
-  A.single_tiles = direct_tiles(h->capacity, shape_lpt(h->shape[mode]), sb, A.prefix_on);
-  A.single_ptiles = prefix_tiles(h->capacity, A.plpt, sb, A.prefix_on);
+  A.single_tiles =
+      route_tiles(kRouteDirect, h->capacity, shape_lpt(h->shape[mode]), sb, A.prefix_on, 0);
+  A.single_ptiles = route_tiles(kRoutePrefix, h->capacity, A.plpt, sb, A.prefix_on, 0);
+  A.single_vtiles = 0;
   A.single_c = h->capacity;
   A.single_k = bins;
   A.single_n = n;
@@ -562,18 +599,22 @@ int bp_lb_set_kernel_timing(bp_lb_t *h, int32_t on) {
   return BP_OK;
 }
 
-int bp_lb_kernel_times(bp_lb_t *h, double *ms_prefix, double *ms_direct, int64_t *calls) {
+int bp_lb_kernel_times(bp_lb_t *h, double *ms_prefix, double *ms_vb2, double *ms_direct,
+                       int64_t *calls) {
   if (!h) return BP_EINVAL;
-  double p = 0.0, d = 0.0;
+  double p = 0.0, v = 0.0, d = 0.0;
   for (const auto &ev : h->ev_pending) {
-    BP_CHECK(cudaEventSynchronize(ev[2]));
-    float a = 0.f, b = 0.f;
+    BP_CHECK(cudaEventSynchronize(ev[3]));
+    float a = 0.f, b = 0.f, e = 0.f;
     BP_CHECK(cudaEventElapsedTime(&a, ev[0], ev[1]));
     BP_CHECK(cudaEventElapsedTime(&b, ev[1], ev[2]));
+    BP_CHECK(cudaEventElapsedTime(&e, ev[2], ev[3]));
     p += a;
-    d += b;
+    v += b;
+    d += e;
   }
   if (ms_prefix) *ms_prefix = p;
+  if (ms_vb2) *ms_vb2 = v;
   if (ms_direct) *ms_direct = d;
   if (calls) *calls = (int64_t)h->ev_pending.size();
   h->ev_pending.clear();

@@ -67,6 +67,11 @@ struct EvalArgs {
   int64_t single_ptiles;
   unsigned long long *pwork;  // [1] next prefix tile (persistent mode)
   int64_t plpt;               // parameters per prefix-kernel tile
+  int32_t vb2_on;             // route VB2 (c <= kVb2FixedCap) to the VB2 kernel
+  int32_t pad_vb2;
+  const int64_t *vtile_start; // [B+1] VB2-kernel tile table, or nullptr (single instance)
+  int64_t single_vtiles;
+  unsigned long long *vwork;  // [1] next VB2 tile (persistent mode)
 };
 
 // Shared-memory budget of the prefix-count tables (bytes; 48 KB lets four
@@ -100,17 +105,27 @@ BPLB_HD bool prefix_handles(int d, int64_t c, int64_t sum_bound, int32_t on) {
   return bytes > 0 && bytes <= kPrefixSmemBytes;
 }
 
-// Tiles of the direct kernel (lpt parameters each) and of the prefix kernel.
-BPLB_HD int64_t direct_tiles(int64_t c, int64_t lpt, int64_t sum_bound, int32_t on) {
-  int64_t t = 0;
-  for (int d = 0; d < kNumDff; ++d)
-    if (!prefix_handles(d, c, sum_bound, on)) t += (param_count(d, c) + lpt - 1) / lpt;
-  return t;
+// Parameters per tile of the VB2 kernel.
+constexpr int64_t kVb2LPT = 4096;
+
+// Which kernel evaluates DFF d of an instance: the prefix-count kernel
+// (prefix_handles), the VB2 kernel (VB2 on its fixed-point path), or the
+// generic direct kernel.
+enum : int { kRouteDirect = 0, kRoutePrefix = 1, kRouteVb2 = 2 };
+
+BPLB_HD int dff_kernel(int d, int64_t c, int64_t sum_bound, int32_t prefix_on, int32_t vb2_on) {
+  if (prefix_handles(d, c, sum_bound, prefix_on)) return kRoutePrefix;
+  if (vb2_on && d == kVB2 && c <= kVb2FixedCap) return kRouteVb2;
+  return kRouteDirect;
 }
-BPLB_HD int64_t prefix_tiles(int64_t c, int64_t lpt, int64_t sum_bound, int32_t on) {
+
+// Tiles of one kernel for an instance: lpt parameters each, DFFs in paper order.
+BPLB_HD int64_t route_tiles(int route, int64_t c, int64_t lpt, int64_t sum_bound, int32_t prefix_on,
+                            int32_t vb2_on) {
   int64_t t = 0;
   for (int d = 0; d < kNumDff; ++d)
-    if (prefix_handles(d, c, sum_bound, on)) t += (param_count(d, c) + lpt - 1) / lpt;
+    if (dff_kernel(d, c, sum_bound, prefix_on, vb2_on) == route)
+      t += (param_count(d, c) + lpt - 1) / lpt;
   return t;
 }
 
@@ -215,23 +230,26 @@ __device__ __forceinline__ int64_t plan_scan(int64_t v, int64_t *s_warp, int64_t
 }
 
 // plan_kernel: one block.  Validates every instance and writes the tile
-// tables of the direct kernel (tile_start[0..B]) and of the prefix kernel
-// (ptile_start[0..B]); an invalid instance gets no tiles and an error result.
-// Clears keys/done and resets both work counters.
+// tables of the direct kernel (tile_start[0..B]), of the prefix kernel
+// (ptile_start[0..B]) and of the VB2 kernel (vtile_start[0..B]); an invalid
+// instance gets no tiles and an error result.  Clears keys/done and resets
+// the work counters.
 template <int MODE>
 __global__ void __launch_bounds__(1024)
-    plan_kernel(EvalArgs A, int64_t lpt, int64_t *tile_start, int64_t *ptile_start) {
+    plan_kernel(EvalArgs A, int64_t lpt, int64_t *tile_start, int64_t *ptile_start,
+                int64_t *vtile_start) {
   __shared__ int64_t s_warp[32];
-  __shared__ int64_t s_carry[2];
+  __shared__ int64_t s_carry[3];
   if (threadIdx.x == 0) {
-    s_carry[0] = s_carry[1] = 0;
+    s_carry[0] = s_carry[1] = s_carry[2] = 0;
     *A.work = 0ull;
     if (A.pwork) *A.pwork = 0ull;
+    if (A.vwork) *A.vwork = 0ull;
   }
   __syncthreads();
   for (int64_t b0 = 0; b0 < A.B; b0 += blockDim.x) {
     const int64_t b = b0 + threadIdx.x;
-    int64_t tiles = 0, ptiles = 0;
+    int64_t tiles = 0, ptiles = 0, vtiles = 0;
     if (b < A.B) {
       A.keys[b] = 0ull;
       A.done[b] = 0u;
@@ -253,22 +271,26 @@ __global__ void __launch_bounds__(1024)
         ok = c >= 1 && c <= kMaxCapacity && L >= 0 && L <= kMaxItems && A.bins[b] >= 0;
       }
       if (ok) {
-        tiles = direct_tiles(c, lpt, L * c, A.prefix_on);
-        ptiles = prefix_tiles(c, A.plpt, L * c, A.prefix_on);
+        tiles = route_tiles(kRouteDirect, c, lpt, L * c, A.prefix_on, A.vb2_on);
+        ptiles = route_tiles(kRoutePrefix, c, A.plpt, L * c, A.prefix_on, A.vb2_on);
+        vtiles = route_tiles(kRouteVb2, c, kVb2LPT, L * c, A.prefix_on, A.vb2_on);
       } else {
         write_error(A, b);
       }
     }
     const int64_t e0 = plan_scan(tiles, s_warp, &s_carry[0]);
     const int64_t e1 = plan_scan(ptiles, s_warp, &s_carry[1]);
+    const int64_t e2 = plan_scan(vtiles, s_warp, &s_carry[2]);
     if (b < A.B) {
       tile_start[b] = e0;
       if (ptile_start) ptile_start[b] = e1;
+      if (vtile_start) vtile_start[b] = e2;
     }
   }
   if (threadIdx.x == 0) {
     tile_start[A.B] = s_carry[0];
     if (ptile_start) ptile_start[A.B] = s_carry[1];
+    if (vtile_start) vtile_start[A.B] = s_carry[2];
   }
 }
 
@@ -318,11 +340,13 @@ __device__ __forceinline__ int64_t sum_bound(const InstView &I) {
   return stream_len<MODE>(I) * I.c;
 }
 
-// Tiles of instance b over both kernels (the finished-tile ticket target).
+// Tiles of instance b over all kernels (the finished-tile ticket target).
 __device__ __forceinline__ int64_t instance_tiles(const EvalArgs &A, int64_t b) {
-  if (!A.tile_start) return A.single_tiles + A.single_ptiles;
-  const int64_t nt = A.tile_start[b + 1] - A.tile_start[b];
-  return A.ptile_start ? nt + (A.ptile_start[b + 1] - A.ptile_start[b]) : nt;
+  if (!A.tile_start) return A.single_tiles + A.single_ptiles + A.single_vtiles;
+  int64_t nt = A.tile_start[b + 1] - A.tile_start[b];
+  if (A.ptile_start) nt += A.ptile_start[b + 1] - A.ptile_start[b];
+  if (A.vtile_start) nt += A.vtile_start[b + 1] - A.vtile_start[b];
+  return nt;
 }
 
 // Block max of the threads' keys, one atomicMax into the instance's slot, and
@@ -353,12 +377,33 @@ __device__ void fold_and_finalize(const EvalArgs &A, int64_t b, unsigned long lo
   __syncthreads();
 }
 
+// Bin loads of a search node into s_load (read back by
+// fetch_item); sets *err for a bad assignment or an overfull bin.
+template <int NT, int MODE>
+__device__ __forceinline__ void node_loads(const InstView &I, uint32_t *s_load, int *err) {
+  if (MODE == kSrcNodes) {
+    for (int64_t j = threadIdx.x; j < I.k; j += NT) s_load[j] = 0u;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < I.n; i += NT) {
+      const int32_t a = I.a[i];
+      const int32_t w = I.w[i];
+      if (w < 0 || (int64_t)w > I.c || a < -1 || (int64_t)a >= I.k) {
+        *err = 1;
+      } else if (a >= 0) {
+        const uint32_t old = atomicAdd(&s_load[a], (uint32_t)w);
+        if ((int64_t)old + w > I.c) *err = 1;
+      }
+    }
+  }
+}
+
 // Local (per-thread) instance sums, reduced over the block once per tile.
 struct LocalSums {
   int64_t v[6];  // n_small, n_big, n_half, n_full, sumw_big, sumw
 };
 
-// Stages stream positions [p, p + len) into the shared lists:
+// Stages stream positions [p, p + len) into the shared lists (and, with
+// `count`, adds the instance sums into S.sums):
 //   ULIST: small items as u = w from index 0 up, big items as u = c - w from
 //          kListTop - 1 down, each stored as u << shift (plus fl(u / c) in
 //          s_a when stage_a);
@@ -367,9 +412,11 @@ struct LocalSums {
 template <int NT, int MODE, bool ULIST>
 __device__ __forceinline__ void stage_chunk(const EvalArgs &A, const InstView &I, const uint32_t *s_load,
                                             int64_t p, int len, bool stage_a, bool fixed, bool count,
-                                            int shift, uint32_t *s_items, float *s_a, TileShared &S,
-                                            LocalSums &ls) {
+                                            int shift, uint32_t *s_items, float *s_a, TileShared &S) {
   const int64_t c = I.c;
+  LocalSums ls;
+#pragma unroll
+  for (int e = 0; e < 6; ++e) ls.v[e] = 0;
   uint64_t fs = 0, fb = 0;  // sums of the fixed-point values (fixed only)
   for (int o = 0; o < len; o += NT) {
     const int64_t q = p + o + threadIdx.x;
@@ -429,6 +476,15 @@ __device__ __forceinline__ void stage_chunk(const EvalArgs &A, const InstView &I
       if (fb) atomicAdd(&S.sumF[1], (unsigned long long)fb);
     }
   }
+  // the instance sums go to shared memory now, so that no register holds
+  // them through the evaluation
+  if (count) {
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+      const long long x = warp_sum((long long)ls.v[e]);
+      if (lane_id() == 0 && x != 0) atomicAdd((unsigned long long *)&S.sums[e], (unsigned long long)x);
+    }
+  }
 }
 
 // Evaluates one tile of DFF D: lambdas [lam0, lam_end) in groups of NT * T,
@@ -437,7 +493,7 @@ __device__ __forceinline__ void stage_chunk(const EvalArgs &A, const InstView &I
 // thread's largest key make_key(lb, flat index); 0 if it had no parameter.
 // With DEBUG the thread's single parameter comes from a request list and its
 // bound is written to req_out instead.
-template <int NT, int T, int D, int MODE, bool DEBUG>
+template <int NT, int T, int D, int MODE, bool DEBUG, bool VB2_FIXED_ONLY = false>
 __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int64_t lam0,
                                        int64_t lam_end, uint32_t *s_items, float *s_a,
                                        const uint32_t *s_load, TileShared &S,
@@ -450,8 +506,10 @@ __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int
   int64_t lo_d, hi_d;
   param_range(D, c, lo_d, hi_d);
   const uint32_t gbase = flat_index(D, lo_d, c);
-  const bool vb2_fixed = (D == kVB2) && c <= kVb2FixedCap;
-  const bool stage_a = (D == kVB2) && !vb2_fixed && c <= kVb2FloatCap;
+  // VB2_FIXED_ONLY: the caller guarantees c <= kVb2FixedCap (the other VB2
+  // paths are compiled out of that instantiation)
+  const bool vb2_fixed = (D == kVB2) && (VB2_FIXED_ONLY || c <= kVb2FixedCap);
+  const bool stage_a = (D == kVB2) && !VB2_FIXED_ONLY && !vb2_fixed && c <= kVb2FloatCap;
   const uint32_t Y0 = vb2_fixed ? vb2_fixed_frac((uint64_t)c - 1, (uint64_t)c) : 0u;
   const bool narrow = c <= kNarrowCap;  // BJ1: terms < 2c stay below 2^30
   const bool fs1_fast = c <= kFs1FastCap;
@@ -466,9 +524,6 @@ __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int
   const int64_t L = stream_len<MODE>(I);
   const bool one_chunk = L <= kChunk;
   const int ngroups = DEBUG ? 1 : (int)((lam_end - lam0 + GW - 1) / GW);
-  LocalSums ls;
-#pragma unroll
-  for (int e = 0; e < 6; ++e) ls.v[e] = 0;
   unsigned long long best = 0ull;
 
   for (int g = 0; g < ngroups; ++g) {
@@ -540,10 +595,11 @@ __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int
           S.nb = 0;
           S.sumF[0] = S.sumF[1] = 0ull;
         }
+        if (g == 0 && p == 0 && tid < 6) S.sums[tid] = 0;
         __syncthreads();
         const int len = (int)min((int64_t)kChunk, L - p);
         stage_chunk<NT, MODE, ULIST>(A, I, s_load, p, len, stage_a, vb2_fixed, g == 0, shift,
-                                     s_items, s_a, S, ls);
+                                     s_items, s_a, S);
         __syncthreads();
         const int ns = S.ns, nb = S.nb;
         const int ns_pad = (ns + 3) & ~3;
@@ -595,6 +651,8 @@ __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int
           if (vb2_fixed) {
             vb2_list_fixed<T, 1>(s_items, 0, ns_pad, k0, Y0, S.sumF[0], acc);
             vb2_list_fixed<T, -1>(s_items, bstart, kListTop, k0, Y0, S.sumF[1], acc);
+          } else if (VB2_FIXED_ONLY) {
+            // unreachable: c <= kVb2FixedCap
           } else if (stage_a) {
             const uint32_t K2 = 0u - c2 * kF32RoundBits;
             vb2_list_float<T, 1>(s_items, s_a, 0, ns_pad, K, k0, kf, c2, K2, acc);
@@ -613,18 +671,8 @@ __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int
       if (L == 0) break;
     }
 
-    // ---- instance sums (once, after the first pass over the stream) ------------
-    if (g == 0) {
-      if (tid < 6) S.sums[tid] = 0;
-      __syncthreads();
-#pragma unroll
-      for (int e = 0; e < 6; ++e) {
-        const long long x = warp_sum((long long)ls.v[e]);
-        if (lane_id() == 0 && x != 0)
-          atomicAdd((unsigned long long *)&S.sums[e], (unsigned long long)x);
-      }
-      __syncthreads();
-    }
+    // the instance sums are complete after the first pass over the stream
+    if (g == 0 && !one_chunk) __syncthreads();
     if (S.err) break;
     InstSums sums;
     sums.n_small = S.sums[0];
@@ -675,7 +723,7 @@ __device__ void process_tile(const EvalArgs &A, int64_t b, int64_t lt, int64_t n
   int64_t rem = lt;
   const int64_t sb = sum_bound<MODE>(I);
   for (d = 0; d < kNumDff; ++d) {
-    if (prefix_handles(d, c, sb, A.prefix_on)) continue;
+    if (dff_kernel(d, c, sb, A.prefix_on, A.vb2_on) != kRouteDirect) continue;
     const int64_t nt = (param_count(d, c) + LPT - 1) / LPT;
     if (rem < nt) break;
     rem -= nt;
@@ -686,27 +734,18 @@ __device__ void process_tile(const EvalArgs &A, int64_t b, int64_t lt, int64_t n
   const int64_t lam_end = min(hi_d + 1, lam0 + LPT);
 
   if (tid == 0) S.err = 0;
-  if (MODE == kSrcNodes) {
-    for (int64_t j = tid; j < I.k; j += NT) s_load[j] = 0u;
-    __syncthreads();
-    for (int64_t i = tid; i < I.n; i += NT) {
-      const int32_t a = I.a[i];
-      const int32_t w = I.w[i];
-      if (w < 0 || (int64_t)w > c || a < -1 || (int64_t)a >= I.k) {
-        S.err = 1;
-      } else if (a >= 0) {
-        const uint32_t old = atomicAdd(&s_load[a], (uint32_t)w);
-        if ((int64_t)old + w > c) S.err = 1;
-      }
-    }
-  }
+  __syncthreads();
+  node_loads<NT, MODE>(I, s_load, &S.err);
   __syncthreads();
 
+  // FS1 (100 parameters) takes one parameter per thread, so that its tile
+  // keeps every warp busy; the tile's parameter range (NT T G) is unchanged.
+  constexpr int T_FS1 = 1;
   unsigned long long best;
   switch (d) {
     case kMT: best = tile_dff<NT, T, kMT, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S); break;
     case kRAD2: best = tile_dff<NT, T, kRAD2, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S); break;
-    case kFS1: best = tile_dff<NT, T, kFS1, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S); break;
+    case kFS1: best = tile_dff<NT, T_FS1, kFS1, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S); break;
     case kCCM1: best = tile_dff<NT, T, kCCM1, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S); break;
     case kVB2: best = tile_dff<NT, T, kVB2, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S); break;
     default: best = tile_dff<NT, T, kBJ1, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S); break;

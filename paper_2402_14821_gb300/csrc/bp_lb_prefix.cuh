@@ -100,26 +100,6 @@ __device__ void suffix_scan(int32_t *a, int n, PrefixShared &S) {
   __syncthreads();
 }
 
-// Bin loads of a search node into s_load (shared with the direct kernel's
-// staging); sets *err for a bad assignment or an overfull bin.
-template <int NT, int MODE>
-__device__ __forceinline__ void node_loads(const InstView &I, uint32_t *s_load, int *err) {
-  if (MODE == kSrcNodes) {
-    for (int64_t j = threadIdx.x; j < I.k; j += NT) s_load[j] = 0u;
-    __syncthreads();
-    for (int64_t i = threadIdx.x; i < I.n; i += NT) {
-      const int32_t a = I.a[i];
-      const int32_t w = I.w[i];
-      if (w < 0 || (int64_t)w > I.c || a < -1 || (int64_t)a >= I.k) {
-        *err = 1;
-      } else if (a >= 0) {
-        const uint32_t old = atomicAdd(&s_load[a], (uint32_t)w);
-        if ((int64_t)old + w > I.c) *err = 1;
-      }
-    }
-  }
-}
-
 // Strided lookup blocks b0, b0 + bs, ... of one parameter (D = CCM1 or BJ1):
 //   CCM1: block b is x = (b + 1) l <= U, term N'(x);
 //   BJ1:  block b is x = b l + 1 <= c, term NN(x) - NN(x + cm)  (cm > 0).

@@ -1,0 +1,83 @@
+// bp_lb_vb2.cuh -- the VB2 kernel: VB2 on its fixed-point path (c <= 65535).
+//
+// VB2 has about c parameters, more than any other DFF except BJ1, and no
+// prefix-count form (its breakpoints c j / l move with every l), so in a
+// batch it is most of the item-by-item work.  Its fixed-point evaluator
+// (vb2_list_fixed: one 32-bit multiply-add and half of a two-word add per
+// item and parameter) needs few registers; in the generic direct kernel it
+// would run at the occupancy that kernel's widest DFF path allows.  This
+// kernel evaluates the VB2 tiles alone, with the same tile evaluation
+// (tile_dff) compiled for VB2's fixed-point path only, so that its register
+// footprint -- and hence its resident warps -- are VB2's own.  Tiles carry
+// kVb2LPT consecutive parameters of one instance; finalisation is shared with
+// the other kernels through the instance's key slot and finished-tile ticket.
+#pragma once
+
+#include "bp_lb_kernels.cuh"
+
+namespace bplb {
+
+constexpr int kVb2NT = 128;
+
+// Resident CTAs per SM asked of the compiler for VT parameters per thread
+// (registers capped at 65536 / (128 MINB)).
+constexpr int vb2_minb(int vt) { return vt <= 4 ? 10 : 8; }
+
+// Dynamic shared memory: the two item lists, then the bin loads of a node.
+constexpr size_t kVb2ListBytes = sizeof(uint32_t) * kListTop;
+
+template <int MODE, int VT>
+__global__ void __launch_bounds__(kVb2NT, vb2_minb(VT)) vb2_kernel(EvalArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ TileShared S;
+  __shared__ long long s_tile, s_inst;
+  uint32_t *s_items = reinterpret_cast<uint32_t *>(smem_raw);
+  uint32_t *s_load = reinterpret_cast<uint32_t *>(smem_raw + kVb2ListBytes);
+
+  const int64_t total = A.vtile_start ? A.vtile_start[A.B] : A.single_vtiles;
+  int64_t t = blockIdx.x;
+  if (A.vwork) {
+    if (threadIdx.x == 0) s_tile = (long long)atomicAdd(A.vwork, 1ull);
+    __syncthreads();
+    t = s_tile;
+  }
+  while (t < total) {
+    if (threadIdx.x == 0) {
+      int64_t b = 0;
+      if (A.vtile_start) {
+        int64_t lo = 0, hi = A.B - 1;  // largest b with vtile_start[b] <= t
+        while (lo < hi) {
+          const int64_t mid = (lo + hi + 1) >> 1;
+          if (A.vtile_start[mid] <= t) lo = mid;
+          else hi = mid - 1;
+        }
+        b = lo;
+      }
+      s_inst = b;
+    }
+    __syncthreads();
+    const int64_t b = s_inst;
+    const InstView I = resolve_instance<MODE>(A, b);
+    const int64_t t0 = A.vtile_start ? A.vtile_start[b] : 0;
+    const int64_t ntiles = instance_tiles(A, b);
+    int64_t lo_d, hi_d;
+    param_range(kVB2, I.c, lo_d, hi_d);
+    const int64_t lam0 = lo_d + (t - t0) * kVb2LPT;
+    const int64_t lam_end = min(hi_d + 1, lam0 + kVb2LPT);
+
+    if (threadIdx.x == 0) S.err = 0;
+    __syncthreads();
+    node_loads<kVb2NT, MODE>(I, s_load, &S.err);
+    __syncthreads();
+    const unsigned long long best = tile_dff<kVb2NT, VT, kVB2, MODE, false, true>(
+        A, I, lam0, lam_end, s_items, nullptr, s_load, S);
+    __syncthreads();
+    fold_and_finalize<kVb2NT>(A, b, best, S.err != 0, ntiles, I, S.warp_key);
+    if (!A.vwork) break;
+    if (threadIdx.x == 0) s_tile = (long long)atomicAdd(A.vwork, 1ull);
+    __syncthreads();
+    t = s_tile;
+  }
+}
+
+}  // namespace bplb
