@@ -753,6 +753,62 @@ __device__ void process_tile(const EvalArgs &A, int64_t b, int64_t lt, int64_t n
   fold_and_finalize<NT>(A, b, best, S.err != 0, ntiles, I, S.warp_key);
 }
 
+// ---------------------------------------------------------------------------
+// Persistent tile loop shared by the evaluation kernels.  A kernel's tile
+// table start[0..B] (nullptr: one instance with its tiles in single mode) maps
+// tile t to the largest b with start[b] <= t.  Warp 0 finds it with 32-way
+// probes (three dependent loads for 4096 instances instead of twelve), and
+// the next tile index is fetched when the current tile starts, so that the
+// atomic's latency overlaps the tile's work.
+// ---------------------------------------------------------------------------
+struct TileCursor {
+  long long tile, inst;
+};
+
+__device__ __forceinline__ int64_t warp_find_instance(const int64_t *start, int64_t B, int64_t t) {
+  int64_t lo = 0, hi = B - 1;  // invariant: start[lo] <= t
+  const int lane = (int)lane_id();
+  while (lo < hi) {
+    const int64_t step = (hi - lo + 32) / 32;  // probes lo + j step, j < 32, cover [lo, hi]
+    const int64_t idx = lo + (int64_t)lane * step;
+    const bool ok = idx <= hi && start[idx] <= t;
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, ok);  // bit 0 set: start[lo] <= t
+    const int k = 31 - __clz((int)m);
+    lo += (int64_t)k * step;
+    hi = min(hi, lo + step - 1);
+  }
+  return lo;
+}
+
+// Publishes tile t (and its instance) to the CTA; called by every thread,
+// with t taken from thread 0.
+__device__ __forceinline__ void tile_publish(const int64_t *start, int64_t B, int64_t total,
+                                             unsigned long long t0_value, TileCursor &cur) {
+  if (threadIdx.x < 32) {
+    const int64_t t = (int64_t)__shfl_sync(0xFFFFFFFFu, t0_value, 0);
+    int64_t b = 0;
+    if (start && t < total) b = warp_find_instance(start, B, t);
+    if (threadIdx.x == 0) {
+      cur.tile = t;
+      cur.inst = b;
+    }
+  }
+  __syncthreads();
+}
+
+// The first tile of this CTA: the next from the work counter, or blockIdx.x.
+__device__ __forceinline__ void tile_first(const int64_t *start, int64_t B, int64_t total,
+                                           unsigned long long *work, TileCursor &cur) {
+  unsigned long long t = blockIdx.x;
+  if (work && threadIdx.x == 0) t = atomicAdd(work, 1ull);
+  tile_publish(start, B, total, t, cur);
+}
+
+// Thread 0's claim on the CTA's next tile (persistent mode), issued early.
+__device__ __forceinline__ unsigned long long tile_claim(unsigned long long *work) {
+  return (work && threadIdx.x == 0) ? atomicAdd(work, 1ull) : ~0ull;
+}
+
 template <int MODE>
 __device__ __forceinline__ InstView resolve_instance(const EvalArgs &A, int64_t b) {
   InstView I;
@@ -790,43 +846,22 @@ template <int NT, int T, int G, int MODE, int MINB>
 __global__ void __launch_bounds__(NT, MINB) eval_kernel(EvalArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ TileShared S;
-  __shared__ long long s_tile;
-  __shared__ long long s_inst;
+  __shared__ TileCursor cur;
   uint32_t *s_items = reinterpret_cast<uint32_t *>(smem_raw);
   float *s_a = reinterpret_cast<float *>(smem_raw + sizeof(uint32_t) * kListTop);
   uint32_t *s_load = reinterpret_cast<uint32_t *>(smem_raw + 2 * sizeof(uint32_t) * kListTop);
 
   const int64_t total = A.tile_start ? A.tile_start[A.B] : A.single_tiles;
-  int64_t t = blockIdx.x;
-  if (A.work) {
-    if (threadIdx.x == 0) s_tile = (long long)atomicAdd(A.work, 1ull);
-    __syncthreads();
-    t = s_tile;
-  }
-  while (t < total) {
-    if (threadIdx.x == 0) {
-      int64_t b = 0;
-      if (A.tile_start) {
-        int64_t lo = 0, hi = A.B - 1;  // largest b with tile_start[b] <= t
-        while (lo < hi) {
-          const int64_t mid = (lo + hi + 1) >> 1;
-          if (A.tile_start[mid] <= t) lo = mid;
-          else hi = mid - 1;
-        }
-        b = lo;
-      }
-      s_inst = b;
-    }
-    __syncthreads();
-    const int64_t b = s_inst;
+  tile_first(A.tile_start, A.B, total, A.work, cur);
+  while (cur.tile < total) {
+    const int64_t t = cur.tile, b = cur.inst;
+    const unsigned long long next = tile_claim(A.work);
     const int64_t t0 = A.tile_start ? A.tile_start[b] : 0;
     const int64_t nt = instance_tiles(A, b);
     const InstView I = resolve_instance<MODE>(A, b);
     process_tile<NT, T, G, MODE>(A, b, t - t0, nt, I, s_items, s_a, s_load, S);
     if (!A.work) break;
-    if (threadIdx.x == 0) s_tile = (long long)atomicAdd(A.work, 1ull);
-    __syncthreads();
-    t = s_tile;
+    tile_publish(A.tile_start, A.B, total, next, cur);
   }
 }
 

@@ -123,23 +123,30 @@ __device__ __forceinline__ uint32_t block_terms(const int32_t *T, uint32_t c32, 
   return acc;
 }
 
-// BJ1 blocks j = 0 .. q of one parameter (q + 1 of them, cm > 0).
-__device__ __forceinline__ uint32_t bj1_blocks(const int32_t *T, uint32_t l, uint32_t cm, uint32_t q) {
-  const int32_t *p = T + 1, *p2 = T + 1 + cm;
-  uint32_t acc = 0, n = q + 1u;
-  for (; n >= 2u; n -= 2u, p += 2u * l, p2 += 2u * l)
-    acc += (uint32_t)(p[0] - p2[0]) + (uint32_t)(p[l] - p2[l]);
-  if (n) acc += (uint32_t)(p[0] - p2[0]);
+// BJ1 accumulator of one parameter from its blocks j = 0 .. q (cm > 0).  The
+// outer two lookups are known: NN(1) = sum w, and block q ends at
+// q l + cm + 1 = c + 1 where NN is 0, so
+//   acc = sum w - NN(cm + 1) + NN(q l + 1) + sum_{j=1}^{q-1} (NN(j l + 1) - NN(j l + cm + 1)).
+__device__ __forceinline__ uint32_t bj1_blocks(const int32_t *T, uint32_t sumw, uint32_t l,
+                                               uint32_t cm, uint32_t q) {
+  uint32_t acc = sumw - (uint32_t)T[cm + 1u] + (uint32_t)T[q * l + 1u];
+  uint32_t x = l + 1u;
+  const uint32_t xe = q * l + 1u;  // first x past the inner blocks
+  for (; x + l < xe; x += 2u * l)
+    acc += (uint32_t)(T[x] - T[x + cm]) + (uint32_t)(T[x + l] - T[x + l + cm]);
+  if (x < xe) acc += (uint32_t)(T[x] - T[x + cm]);
   return acc;
 }
 
-// The candidate test (file comment): divide only when S > B f.
-__device__ __forceinline__ void try_key(int64_t S, int64_t f, uint32_t g, int64_t &B,
+// The candidate test (file comment): divide only when S > B f.  Every sum
+// and denominator here is below 2^32 (prefix_handles), so all is 32-bit
+// except the product.
+__device__ __forceinline__ void try_key(uint32_t S, uint32_t f, uint32_t g, uint32_t &B,
                                         unsigned long long &best) {
-  if (S > B * f) {
-    const int64_t lb = ceil_div_fast(S, f);
-    B = lb;
-    best = make_key(lb, g);
+  if ((uint64_t)B * f < (uint64_t)S) {
+    const uint32_t q = S / f;
+    B = q + (S != q * f);
+    best = make_key((int64_t)B, g);
   }
 }
 
@@ -212,37 +219,41 @@ __device__ unsigned long long prefix_tile_dff(const EvalArgs &A, const InstView 
   }
   if (S.err) return 0ull;
 
-  const int64_t n_big = S.sums[1], n_half = S.sums[2], n_full = S.sums[3];
-  const int64_t sumw_big = S.sums[4], sumw = S.sums[5], TB = S.sums[6];
+  // all below 2^31 on this path (prefix_handles); the sums S(l) below 2^32
+  const uint32_t n_big = (uint32_t)S.sums[1], n_half = (uint32_t)S.sums[2];
+  const uint32_t n_full = (uint32_t)S.sums[3], sumw_big = (uint32_t)S.sums[4];
+  const uint32_t sumw = (uint32_t)S.sums[5], TB = (uint32_t)S.sums[6];
   int64_t lo_d, hi_d;
   param_range(D, c, lo_d, hi_d);
   // flattened index of parameter l is gofs + l
   const uint32_t gofs = flat_index(D, lo_d, c) - (uint32_t)lo_d;
-  int64_t B = ceil_div_fast(sumw, c);  // L1
+  uint32_t B = sumw / c32 + (sumw % c32 != 0u);  // L1
   unsigned long long best = 0ull;
-  // S(l) = sum_w f(w, l) from the accumulators (bp_lb_core.cuh), l-independent parts:
+  // S(l) = sum_w f(w, l) from the accumulators (bp_lb_core.cuh), l-independent
+  // parts in kS, evaluated in wrapping 32-bit arithmetic (exact: S < 2^32):
   //   MT:   E(l) + kS;   RAD2: A n1 + (B2 - A) n2s - (c - A - B2) n2b + kS;
   //   CCM1: 2 acc + q kS;   BJ1: sumw - acc
-  int64_t kS;
-  if (D == kMT) kS = TB + sumw_big + n_half * (c / 2) + n_full * c;
-  else if (D == kRAD2) kS = n_big * c + n_half * (c / 2) + n_full * c;
-  else if (D == kCCM1) kS = 2 * n_big + n_half + 2 * n_full;
+  uint32_t kS;
+  if (D == kMT) kS = TB + sumw_big + n_half * (c32 / 2u) + n_full * c32;
+  else if (D == kRAD2) kS = n_big * c32 + n_half * (c32 / 2u) + n_full * c32;
+  else if (D == kCCM1) kS = 2u * n_big + n_half + 2u * n_full;
   else kS = sumw;
+  const uint32_t l0 = (uint32_t)lam0, le = (uint32_t)lam_end;  // parameters < 2^31 here
 
   if (D == kMT || D == kRAD2) {
-    if (D == kMT && lam0 == 0 && tid == 0) best = make_key(B, gofs);  // l = 0: the bound L1
-    const int64_t A3 = c / 3, B2 = c / 2;
-    for (int64_t l = lam0 + tid; l < lam_end; l += kPrefixNT) {
-      const uint32_t l32 = (uint32_t)l;
-      int64_t Sv;
+    if (D == kMT && l0 == 0u && tid == 0) best = make_key((int64_t)B, gofs);  // l = 0: L1
+    const uint32_t A3 = c32 / 3u, B2 = c32 / 2u;
+    for (uint32_t l = l0 + (uint32_t)tid; l < le; l += kPrefixNT) {
+      uint32_t Sv;
       if (D == kMT) {
-        Sv = (int64_t)T0[min(l32, U + 1u)] + kS;
+        Sv = (uint32_t)T0[min(l, U + 1u)] + kS;
       } else {
-        const uint32_t y = min(c32 - 2u * l32 + 1u, U + 1u);
-        const int64_t n1 = T0[l32], n2s = T1[y], n2b = (int64_t)T1[y] - T0[y];
-        Sv = A3 * n1 + (B2 - A3) * n2s - (c - A3 - B2) * n2b + kS;
+        const uint32_t y = min(c32 - 2u * l + 1u, U + 1u);
+        const uint32_t n1 = (uint32_t)T0[l], n2s = (uint32_t)T1[y];
+        const uint32_t n2b = n2s - (uint32_t)T0[y];
+        Sv = A3 * n1 + (B2 - A3) * n2s - (c32 - A3 - B2) * n2b + kS;
       }
-      try_key(Sv, c, gofs + l32, B, best);
+      try_key(Sv, c32, gofs + l, B, best);
     }
     return best;
   }
@@ -254,13 +265,13 @@ __device__ unsigned long long prefix_tile_dff(const EvalArgs &A, const InstView 
   const int lane = (int)lane_id(), warp = tid >> 5;
   // S and f of parameter l with q = floor(c / l) and the accumulator
   auto finish = [&](uint32_t l, uint32_t q, uint32_t acc) {
-    int64_t Sv, f;
+    uint32_t Sv, f;
     if (D == kCCM1) {
-      Sv = 2 * (int64_t)(int32_t)acc + (int64_t)q * kS;
-      f = 2 * (int64_t)q;
+      Sv = 2u * acc + q * kS;
+      f = 2u * q;
     } else {
-      Sv = kS - (int64_t)acc;
-      f = (int64_t)(q * (l - (c32 - q * l)));  // q (l - cm) <= c
+      Sv = kS - acc;
+      f = q * (l - (c32 - q * l));  // q (l - cm) <= c
     }
     try_key(Sv, f, gofs + l, B, best);
   };
@@ -324,24 +335,23 @@ __device__ unsigned long long prefix_tile_dff(const EvalArgs &A, const InstView 
   {
     uint32_t q = 0;
     bool first = true, odd = false;
-    for (int64_t r = warp_end; r < lam_end; r += kPrefixNT, odd = !odd) {
-      const int64_t l = r + (odd ? kPrefixNT - 1 - tid : tid);
-      if (l >= lam_end) continue;
-      const uint32_t l32 = (uint32_t)l;
+    for (uint32_t r = (uint32_t)warp_end; r < le; r += kPrefixNT, odd = !odd) {
+      const uint32_t l = r + (odd ? kPrefixNT - 1 - tid : tid);
+      if (l >= le) continue;
       if (first) {
-        q = c32 / l32;
+        q = c32 / l;
         first = false;
       } else {
-        while (q * l32 > c32) --q;
+        while (q * l > c32) --q;
       }
       uint32_t acc = 0;
       if (D == kCCM1) {
-        acc = block_terms<D>(T0, c32, U, l32, 0u, 0u, 1u);
+        acc = block_terms<D>(T0, c32, U, l, 0u, 0u, 1u);
       } else {
-        const uint32_t cm = c32 - q * l32;
-        if (cm != 0u) acc = bj1_blocks(T0, l32, cm, q);
+        const uint32_t cm = c32 - q * l;
+        if (cm != 0u) acc = bj1_blocks(T0, sumw, l, cm, q);
       }
-      finish(l32, q, acc);
+      finish(l, q, acc);
     }
   }
   return best;
@@ -353,33 +363,15 @@ template <int MODE>
 __global__ void __launch_bounds__(kPrefixNT, 4) prefix_kernel(EvalArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ PrefixShared S;
-  __shared__ long long s_tile, s_inst;
+  __shared__ TileCursor cur;
   int32_t *tab = reinterpret_cast<int32_t *>(smem_raw);
   uint32_t *s_load = reinterpret_cast<uint32_t *>(smem_raw + kPrefixSmemBytes);
 
   const int64_t total = A.ptile_start ? A.ptile_start[A.B] : A.single_ptiles;
-  int64_t t = blockIdx.x;
-  if (A.pwork) {
-    if (threadIdx.x == 0) s_tile = (long long)atomicAdd(A.pwork, 1ull);
-    __syncthreads();
-    t = s_tile;
-  }
-  while (t < total) {
-    if (threadIdx.x == 0) {
-      int64_t b = 0;
-      if (A.ptile_start) {
-        int64_t lo = 0, hi = A.B - 1;
-        while (lo < hi) {
-          const int64_t mid = (lo + hi + 1) >> 1;
-          if (A.ptile_start[mid] <= t) lo = mid;
-          else hi = mid - 1;
-        }
-        b = lo;
-      }
-      s_inst = b;
-    }
-    __syncthreads();
-    const int64_t b = s_inst;
+  tile_first(A.ptile_start, A.B, total, A.pwork, cur);
+  while (cur.tile < total) {
+    const int64_t t = cur.tile, b = cur.inst;
+    const unsigned long long next = tile_claim(A.pwork);
     const InstView I = resolve_instance<MODE>(A, b);
     const int64_t t0 = A.ptile_start ? A.ptile_start[b] : 0;
     const int64_t ntiles = instance_tiles(A, b);
@@ -410,9 +402,7 @@ __global__ void __launch_bounds__(kPrefixNT, 4) prefix_kernel(EvalArgs A) {
     __syncthreads();
     fold_and_finalize<kPrefixNT>(A, b, best, S.err != 0, ntiles, I, S.warp_key);
     if (!A.pwork) break;
-    if (threadIdx.x == 0) s_tile = (long long)atomicAdd(A.pwork, 1ull);
-    __syncthreads();
-    t = s_tile;
+    tile_publish(A.ptile_start, A.B, total, next, cur);
   }
 }
 

@@ -21,7 +21,7 @@ constexpr int kVb2NT = 128;
 
 // Resident CTAs per SM asked of the compiler for VT parameters per thread
 // (registers capped at 65536 / (128 MINB)).
-constexpr int vb2_minb(int vt) { return vt <= 4 ? 10 : 8; }
+constexpr int vb2_minb(int vt) { return vt <= 2 ? 10 : (vt <= 4 ? 8 : 6); }
 
 // Dynamic shared memory: the two item lists, then the bin loads of a node.
 constexpr size_t kVb2ListBytes = sizeof(uint32_t) * kListTop;
@@ -30,33 +30,15 @@ template <int MODE, int VT>
 __global__ void __launch_bounds__(kVb2NT, vb2_minb(VT)) vb2_kernel(EvalArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ TileShared S;
-  __shared__ long long s_tile, s_inst;
+  __shared__ TileCursor cur;
   uint32_t *s_items = reinterpret_cast<uint32_t *>(smem_raw);
   uint32_t *s_load = reinterpret_cast<uint32_t *>(smem_raw + kVb2ListBytes);
 
   const int64_t total = A.vtile_start ? A.vtile_start[A.B] : A.single_vtiles;
-  int64_t t = blockIdx.x;
-  if (A.vwork) {
-    if (threadIdx.x == 0) s_tile = (long long)atomicAdd(A.vwork, 1ull);
-    __syncthreads();
-    t = s_tile;
-  }
-  while (t < total) {
-    if (threadIdx.x == 0) {
-      int64_t b = 0;
-      if (A.vtile_start) {
-        int64_t lo = 0, hi = A.B - 1;  // largest b with vtile_start[b] <= t
-        while (lo < hi) {
-          const int64_t mid = (lo + hi + 1) >> 1;
-          if (A.vtile_start[mid] <= t) lo = mid;
-          else hi = mid - 1;
-        }
-        b = lo;
-      }
-      s_inst = b;
-    }
-    __syncthreads();
-    const int64_t b = s_inst;
+  tile_first(A.vtile_start, A.B, total, A.vwork, cur);
+  while (cur.tile < total) {
+    const int64_t t = cur.tile, b = cur.inst;
+    const unsigned long long next = tile_claim(A.vwork);
     const InstView I = resolve_instance<MODE>(A, b);
     const int64_t t0 = A.vtile_start ? A.vtile_start[b] : 0;
     const int64_t ntiles = instance_tiles(A, b);
@@ -74,9 +56,7 @@ __global__ void __launch_bounds__(kVb2NT, vb2_minb(VT)) vb2_kernel(EvalArgs A) {
     __syncthreads();
     fold_and_finalize<kVb2NT>(A, b, best, S.err != 0, ntiles, I, S.warp_key);
     if (!A.vwork) break;
-    if (threadIdx.x == 0) s_tile = (long long)atomicAdd(A.vwork, 1ull);
-    __syncthreads();
-    t = s_tile;
+    tile_publish(A.vtile_start, A.B, total, next, cur);
   }
 }
 
