@@ -388,6 +388,30 @@ def main():
     for j in (0, NODES // 2, NODES - 1):
         w, a, c, k = nd.node(j)
         assert B.bp_lb_eval_node(h, w, a, k)[0] == int(out_b[j].item())
+    full_feasible = out_f.clone()
+
+    # ---- verdict-only mode (early exit): same batch, same launch shape --------
+    B.bp_lb_set_result_mode(h, B.RESULT_VERDICT)
+    for _ in range(3):
+        step()
+    barrier()
+    vev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    for e0, e1 in vev:
+        flush.zero_()
+        e0.record(stream)
+        step()
+        e1.record(stream)
+    barrier()
+    v_ms = np.array([e0.elapsed_time(e1) for e0, e1 in vev])
+    assert torch.equal(out_f, full_feasible)   # the same verdicts as the full maximum
+    B.bp_lb_set_result_mode(h, B.RESULT_FULL)
+    t_verdict = float(v_ms.mean())
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_verdict], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_verdict = float(t.item())
 
     B.bp_lb_destroy(h)
     if rank != 0:
@@ -421,6 +445,11 @@ def main():
                   "launch_shape": plain_shape, "autotune_us": [round(x, 2) for x in plain_us],
                   "call": "bp_lb_eval_node (H2D, 1 launch, D2H, sync)"},
         "batched_over_plain": value / world / plain_rate,
+        "verdict": {"value": NODES * world / (t_verdict / 1e3), "unit": UNIT,
+                    "ms_per_step": t_verdict, "p50_ms": float(np.percentile(v_ms, 50)),
+                    "p99_ms": float(np.percentile(v_ms, 99)),
+                    "mode": "verdict only (Alg. 2 early exit; VB2 parameters whose upper "
+                            "bound is <= k skipped); same verdicts as the full maximum"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9,
@@ -439,7 +468,7 @@ def main():
                                             if t_direct > 0 else None)},
         "launch_shape": {"chosen": shape, "nt_t_g_minb": list(B.bp_lb_launch_shape_info(shape)),
                          "autotune_ms": [round(x, 4) for x in shape_ms]},
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": 4 * args.steps,  # plan, prefix, VB2 and generic kernels per step
         "clocks": clocks,
         "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"{cpu_m} of the {NODES} nodes (reduction + full bound), "

@@ -254,6 +254,31 @@ int bp_lb_set_algorithm(bp_lb_t *h, int32_t algo);
 /* The handle's algorithm (batched modes), or -1 for a NULL handle. */
 int bp_lb_get_algorithm(bp_lb_t *h);
 
+/* ---- result mode: full maximum or verdict only ---------------------------- */
+
+/* BP_RESULT_FULL (the default) returns, per instance, the exact maximum over
+ * every (DFF, lambda) bound and its first argmax (reading R3 of the design:
+ * Alg. 2 without its early exit), and the verdict bound <= k.
+ * BP_RESULT_VERDICT returns the verdict only, exactly, with Alg. 2's early
+ * exit (Sec. 3.1, Alg. 2): once any bound of an instance exceeds k, its
+ * remaining tiles stop (a flag -- the instance's result slot -- read by every
+ * kernel when it starts a tile and between parameter groups), and on the VB2
+ * path a warp skips its parameters when an upper bound on each of their
+ * bounds, from the instance's sums alone, is <= k (such a parameter cannot
+ * change the verdict).  The cheap DFFs run first (the prefix-count kernel,
+ * then VB2, then the rest), so a decided instance skips the expensive ones.
+ * In this mode out_feasible is exact; out_bound / out_argmax hold a genuine
+ * bound of the instance and the (DFF, lambda) that gives it: one above k
+ * when infeasible (which one may vary between runs), one <= k when feasible
+ * (the largest evaluated, not necessarily the maximum).
+ * Errors: BP_EINVAL (NULL handle), BP_ERANGE (unknown mode). */
+#define BP_RESULT_FULL 0
+#define BP_RESULT_VERDICT 1
+int bp_lb_set_result_mode(bp_lb_t *h, int32_t mode);
+
+/* The handle's result mode, or -1 for a NULL handle. */
+int bp_lb_get_result_mode(bp_lb_t *h);
+
 /* Measurement aid: with timing on, every batched call records CUDA events
  * on its stream around its three evaluation launches -- the prefix-count
  * kernel, the VB2 kernel (VB2 at c <= 65535, evaluated item by item with its

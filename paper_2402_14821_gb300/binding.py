@@ -77,6 +77,8 @@ def _bind(lib):
         "bp_lb_autotune_plain_node": (ctypes.c_int, [_vp, _vp, _vp, _c_i64, _c_i64, _c_i32, _vp,
                                                      P(_c_i32)]),
         "bp_lb_set_algorithm": (ctypes.c_int, [_vp, _c_i32]),
+        "bp_lb_set_result_mode": (ctypes.c_int, [_vp, _c_i32]),
+        "bp_lb_get_result_mode": (ctypes.c_int, [_vp]),
         "bp_lb_get_algorithm": (ctypes.c_int, [_vp]),
         "bp_lb_set_kernel_timing": (ctypes.c_int, [_vp, _c_i32]),
         "bp_lb_dff_route": (ctypes.c_int, [_c_i32, _c_i64, _c_i64, _c_i32]),
@@ -116,9 +118,11 @@ EXPORTED = ("bp_lb_strerror", "bp_lb_create", "bp_lb_destroy", "bp_lb_reserve", 
             "bp_lb_autotune_nodes", "bp_lb_eval_batch_noalloc", "bp_lb_autotune_plain_node",
             "bp_serve_create", "bp_serve_destroy", "bp_serve_register", "bp_serve_submit",
             "bp_serve_poll", "bp_serve_stats", "bp_lb_set_algorithm", "bp_lb_get_algorithm",
-            "bp_lb_set_kernel_timing", "bp_lb_kernel_times", "bp_lb_dff_route")
+            "bp_lb_set_kernel_timing", "bp_lb_kernel_times", "bp_lb_dff_route",
+            "bp_lb_set_result_mode", "bp_lb_get_result_mode")
 
 ALGO_DIRECT, ALGO_PREFIX = 0, 1
+RESULT_FULL, RESULT_VERDICT = 0, 1
 
 NOALLOC_MAX_BATCH = 4096
 
@@ -294,6 +298,16 @@ def bp_lb_set_algorithm(h, algo: int):
 
 def bp_lb_get_algorithm(h) -> int:
     return lib().bp_lb_get_algorithm(h)
+
+
+def bp_lb_set_result_mode(h, mode: int):
+    """RESULT_FULL (exact maximum and argmax) or RESULT_VERDICT (exact verdict,
+    early exit; the bound is a genuine witness, not the maximum)."""
+    _check(lib().bp_lb_set_result_mode(h, int(mode)), "bp_lb_set_result_mode")
+
+
+def bp_lb_get_result_mode(h) -> int:
+    return lib().bp_lb_get_result_mode(h)
 
 
 def bp_lb_set_kernel_timing(h, on: bool):

@@ -66,6 +66,7 @@ struct bp_lb {
   // batched modes send VB2 (c <= 65535) to the VB2 kernel; the plain path
   // keeps it in the direct kernel (one launch fewer per check)
   int32_t vb2_on = 1;
+  int32_t verdict = 0;  // BP_RESULT_FULL (0) or BP_RESULT_VERDICT (1)
   // optional per-kernel timing of batched calls (events around each launch)
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -201,6 +202,7 @@ int launch_batch(bp_lb *h, EvalArgs A, size_t smem, cudaStream_t st) {
   A.pwork = h->d_work + 1;
   A.plpt = kPrefixLPTBatch;
   A.vb2_on = h->vb2_on;
+  A.verdict = h->verdict;
   A.vtile_start = h->d_vtile_start;
   A.vwork = h->d_work + 2;
   const int shape = h->shape[MODE];
@@ -410,6 +412,7 @@ static EvalArgs plain_args(bp_lb *h, int64_t n, int64_t bins, int mode) {
   const int64_t sb = (mode == kModePlainNodes ? n + bins : n) * h->capacity;
   A.prefix_on = h->plain_prefix_on;
   A.vb2_on = 0;
+  A.verdict = h->verdict;
   A.plpt = kPrefixLPTSingle;
   A.single_tiles =
       route_tiles(kRouteDirect, h->capacity, shape_lpt(h->shape[mode]), sb, A.prefix_on, 0);
@@ -591,6 +594,18 @@ int bp_lb_set_algorithm(bp_lb_t *h, int32_t algo) {
   if (algo != BP_ALGO_DIRECT && algo != BP_ALGO_PREFIX) return BP_ERANGE;
   h->prefix_on = h->plain_prefix_on = algo == BP_ALGO_PREFIX;
   return BP_OK;
+}
+
+int bp_lb_set_result_mode(bp_lb_t *h, int32_t mode) {
+  if (!h) return BP_EINVAL;
+  if (mode != BP_RESULT_FULL && mode != BP_RESULT_VERDICT) return BP_ERANGE;
+  h->verdict = mode == BP_RESULT_VERDICT;
+  return BP_OK;
+}
+
+int bp_lb_get_result_mode(bp_lb_t *h) {
+  if (!h) return -1;
+  return h->verdict ? BP_RESULT_VERDICT : BP_RESULT_FULL;
 }
 
 int bp_lb_set_kernel_timing(bp_lb_t *h, int32_t on) {

@@ -72,6 +72,8 @@ struct EvalArgs {
   const int64_t *vtile_start; // [B+1] VB2-kernel tile table, or nullptr (single instance)
   int64_t single_vtiles;
   unsigned long long *vwork;  // [1] next VB2 tile (persistent mode)
+  int32_t verdict;            // verdict-only mode (early exit, exact feasibility)
+  int32_t pad_verdict;
 };
 
 // Shared-memory budget of the prefix-count tables (bytes; 48 KB lets four
@@ -139,6 +141,14 @@ struct InstView {
 };
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+// Verdict mode (Alg. 2's early exit): an instance is decided once its result
+// slot holds a bound above k -- it is infeasible whatever the remaining
+// parameters give.  Read by one thread; the caller broadcasts the answer.
+__device__ __forceinline__ bool slot_decided(const unsigned long long *slot, int64_t k) {
+  const unsigned long long key = *reinterpret_cast<const volatile unsigned long long *>(slot);
+  return (int64_t)(key >> 32) > k;
+}
 
 // Warp-aggregated append to a shared-memory list counter; returns the slot.
 __device__ __forceinline__ int warp_append(bool pred, int *counter) {
@@ -299,7 +309,8 @@ __global__ void __launch_bounds__(1024)
 // ---------------------------------------------------------------------------
 struct TileShared {
   int ns, nb, err;
-  int pad_;
+  int skip;     // verdict mode: the instance was decided before this tile
+  int stop[2];  // verdict mode: decided before group g (double-buffered by g & 1)
   unsigned long long warp_key[32];
   long long sums[6];
   unsigned long long sumF[2];  // VB2 fixed point: sum of F over the small and big lists
@@ -498,7 +509,8 @@ __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int
                                        int64_t lam_end, uint32_t *s_items, float *s_a,
                                        const uint32_t *s_load, TileShared &S,
                                        const int64_t *req_lam = nullptr, int64_t *req_out = nullptr,
-                                       int64_t req_idx = -1) {
+                                       int64_t req_idx = -1,
+                                       unsigned long long *vslot = nullptr) {
   constexpr bool ULIST = (D == kMT || D == kRAD2 || D == kCCM1 || D == kVB2);
   constexpr int GW = NT * T;
   const int tid = threadIdx.x;
@@ -527,6 +539,12 @@ __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int
   unsigned long long best = 0ull;
 
   for (int g = 0; g < ngroups; ++g) {
+    // verdict mode: stop once another tile (or an earlier group) decided the instance
+    if (vslot != nullptr && g > 0) {
+      if (tid == 0) S.stop[g & 1] = slot_decided(vslot, I.k) ? 1 : 0;
+      __syncthreads();
+      if (S.stop[g & 1]) break;
+    }
     // ---- this group's parameters and their constants -------------------------
     int64_t lam[T];
     bool valid[T];
@@ -615,6 +633,32 @@ __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int
           }
         }
         __syncthreads();
+      }
+      // Verdict mode, VB2: a warp skips the items when none of its parameters
+      // can have a bound above k.  With ceil(x) < x + 1 for the small list
+      // and ceil(x) >= x for the big one, acc <= floor(X / c),
+      // X = l D + n_small (c - 1), D = sum_small u - sum_big u, and
+      // lb <= k whenever S(acc) <= 2 k (l - 1), i.e. floor(X / c) <= M with
+      // M = floor(((l - 1)(2k - K) + 2 n_small - 2 n_big) / 2),
+      // K = 2 n_big + n_half + 2 n_full (vb2_sum in bp_lb_core.cuh).
+      if (D == kVB2 && vslot != nullptr && one_chunk && !S.err) {
+        const int64_t ns_ = S.sums[0], nb_ = S.sums[1], nh_ = S.sums[2], nf_ = S.sums[3];
+        const int64_t swb = S.sums[4], sw = S.sums[5];
+        const int64_t Dd = (sw - swb - nh_ * (c / 2) - nf_ * c) - (nb_ * c - swb);
+        const int64_t K = 2 * nb_ + nh_ + 2 * nf_;
+        const int64_t kk = min(I.k, (int64_t)1 << 40);  // bounds never reach 2^40
+        bool need = false;
+#pragma unroll
+        for (int j = 0; j < T; ++j) {
+          if (!valid[j]) continue;
+          const int64_t l = lam[j];
+          const int64_t M = ((l - 1) * (2 * kk - K) + 2 * ns_ - 2 * nb_) >> 1;
+          need |= l * Dd + ns_ * (c - 1) > (M + 1) * c - 1;
+        }
+        if (!__any_sync(0xFFFFFFFFu, need)) {
+#pragma unroll
+          for (int j = 0; j < T; ++j) valid[j] = false;
+        }
       }
       bool any_valid = false;
 #pragma unroll
@@ -705,6 +749,8 @@ __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int
         best = key > best ? key : best;
       }
     }
+    // verdict mode: publish a bound above k at once, so that other tiles stop
+    if (vslot != nullptr && (int64_t)(best >> 32) > I.k) atomicMax(vslot, best);
   }
   return best;
 }
@@ -733,22 +779,26 @@ __device__ void process_tile(const EvalArgs &A, int64_t b, int64_t lt, int64_t n
   const int64_t lam0 = lo_d + rem * LPT;
   const int64_t lam_end = min(hi_d + 1, lam0 + LPT);
 
-  if (tid == 0) S.err = 0;
+  unsigned long long *vslot = A.verdict ? &A.keys[b] : nullptr;
+  if (tid == 0) {
+    S.err = 0;
+    S.skip = (vslot != nullptr && slot_decided(vslot, I.k)) ? 1 : 0;
+  }
   __syncthreads();
-  node_loads<NT, MODE>(I, s_load, &S.err);
+  if (!S.skip) node_loads<NT, MODE>(I, s_load, &S.err);
   __syncthreads();
 
   // FS1 (100 parameters) takes one parameter per thread, so that its tile
   // keeps every warp busy; the tile's parameter range (NT T G) is unchanged.
   constexpr int T_FS1 = 1;
-  unsigned long long best;
-  switch (d) {
-    case kMT: best = tile_dff<NT, T, kMT, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S); break;
-    case kRAD2: best = tile_dff<NT, T, kRAD2, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S); break;
-    case kFS1: best = tile_dff<NT, T_FS1, kFS1, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S); break;
-    case kCCM1: best = tile_dff<NT, T, kCCM1, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S); break;
-    case kVB2: best = tile_dff<NT, T, kVB2, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S); break;
-    default: best = tile_dff<NT, T, kBJ1, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S); break;
+  unsigned long long best = 0ull;
+  if (!S.skip) switch (d) {
+    case kMT: best = tile_dff<NT, T, kMT, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S, nullptr, nullptr, -1, vslot); break;
+    case kRAD2: best = tile_dff<NT, T, kRAD2, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S, nullptr, nullptr, -1, vslot); break;
+    case kFS1: best = tile_dff<NT, T_FS1, kFS1, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S, nullptr, nullptr, -1, vslot); break;
+    case kCCM1: best = tile_dff<NT, T, kCCM1, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S, nullptr, nullptr, -1, vslot); break;
+    case kVB2: best = tile_dff<NT, T, kVB2, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S, nullptr, nullptr, -1, vslot); break;
+    default: best = tile_dff<NT, T, kBJ1, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S, nullptr, nullptr, -1, vslot); break;
   }
   fold_and_finalize<NT>(A, b, best, S.err != 0, ntiles, I, S.warp_key);
 }

@@ -44,7 +44,7 @@ constexpr int kMaxHeavy = kPrefixNT;
 
 struct PrefixShared {
   int err;
-  int pad_;
+  int skip;  // verdict mode: the instance was decided before this tile
   unsigned long long warp_key[kPrefixWarps];
   long long sums[8];  // n_small, n_big, n_half, n_full, sumw_big, sumw, total big u, unused
   uint32_t wtot[2][kPrefixWarps];
@@ -390,15 +390,20 @@ __global__ void __launch_bounds__(kPrefixNT, 4) prefix_kernel(EvalArgs A) {
     const int64_t lam0 = lo_d + rem * A.plpt;
     const int64_t lam_end = min(hi_d + 1, lam0 + A.plpt);
 
-    if (threadIdx.x == 0) S.err = 0;
+    if (threadIdx.x == 0) {
+      S.err = 0;
+      S.skip = (A.verdict && slot_decided(&A.keys[b], I.k)) ? 1 : 0;
+    }
     __syncthreads();
-    node_loads<kPrefixNT, MODE>(I, s_load, &S.err);
-    __syncthreads();
-    unsigned long long best;
-    if (d == kMT) best = prefix_tile_dff<MODE, kMT>(A, I, lam0, lam_end, tab, s_load, S);
-    else if (d == kRAD2) best = prefix_tile_dff<MODE, kRAD2>(A, I, lam0, lam_end, tab, s_load, S);
-    else if (d == kCCM1) best = prefix_tile_dff<MODE, kCCM1>(A, I, lam0, lam_end, tab, s_load, S);
-    else best = prefix_tile_dff<MODE, kBJ1>(A, I, lam0, lam_end, tab, s_load, S);
+    unsigned long long best = 0ull;
+    if (!S.skip) {
+      node_loads<kPrefixNT, MODE>(I, s_load, &S.err);
+      __syncthreads();
+      if (d == kMT) best = prefix_tile_dff<MODE, kMT>(A, I, lam0, lam_end, tab, s_load, S);
+      else if (d == kRAD2) best = prefix_tile_dff<MODE, kRAD2>(A, I, lam0, lam_end, tab, s_load, S);
+      else if (d == kCCM1) best = prefix_tile_dff<MODE, kCCM1>(A, I, lam0, lam_end, tab, s_load, S);
+      else best = prefix_tile_dff<MODE, kBJ1>(A, I, lam0, lam_end, tab, s_load, S);
+    }
     __syncthreads();
     fold_and_finalize<kPrefixNT>(A, b, best, S.err != 0, ntiles, I, S.warp_key);
     if (!A.pwork) break;

@@ -47,12 +47,19 @@ __global__ void __launch_bounds__(kVb2NT, vb2_minb(VT)) vb2_kernel(EvalArgs A) {
     const int64_t lam0 = lo_d + (t - t0) * kVb2LPT;
     const int64_t lam_end = min(hi_d + 1, lam0 + kVb2LPT);
 
-    if (threadIdx.x == 0) S.err = 0;
+    unsigned long long *vslot = A.verdict ? &A.keys[b] : nullptr;
+    if (threadIdx.x == 0) {
+      S.err = 0;
+      S.skip = (vslot != nullptr && slot_decided(vslot, I.k)) ? 1 : 0;
+    }
     __syncthreads();
-    node_loads<kVb2NT, MODE>(I, s_load, &S.err);
-    __syncthreads();
-    const unsigned long long best = tile_dff<kVb2NT, VT, kVB2, MODE, false, true>(
-        A, I, lam0, lam_end, s_items, nullptr, s_load, S);
+    unsigned long long best = 0ull;
+    if (!S.skip) {
+      node_loads<kVb2NT, MODE>(I, s_load, &S.err);
+      __syncthreads();
+      best = tile_dff<kVb2NT, VT, kVB2, MODE, false, true>(A, I, lam0, lam_end, s_items, nullptr,
+                                                            s_load, S, nullptr, nullptr, -1, vslot);
+    }
     __syncthreads();
     fold_and_finalize<kVb2NT>(A, b, best, S.err != 0, ntiles, I, S.warp_key);
     if (!A.vwork) break;
