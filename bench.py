@@ -52,11 +52,12 @@ def ops_per_eval(d, c):
             4: 2 if c <= 65535 else 5,
             5: 5 if c <= 65535 else 6}[d]
 SM_COUNT_NOMINAL = 152
-# DRAM bytes (read + write) per search node of one eval_kernel launch over the
-# 4096-node batch, from ncu (dram__bytes_read.sum + dram__bytes_write.sum), or
-# None while the kernel has changed since the last capture; see
-# profiles/eval_kernel_search_nodes.md.
-TRAFFIC_BYTES_PER_NODE = None
+# DRAM bytes (read + write) per search node of one vb2_kernel launch, from one
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of a 512-node
+# launch, divided by 512: traffic grows with the nodes, each node's assignment
+# being read from DRAM once), or None while the kernel has changed since the
+# last capture.
+TRAFFIC_BYTES_PER_NODE = 2185
 
 
 def param_counts(c):
@@ -455,7 +456,8 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9,
                      "unit": "Gop/s", "frac": achieved / peak_ops,
                      "traffic": (TRAFFIC_BYTES_PER_NODE * NODES
-                                 if TRAFFIC_BYTES_PER_NODE is not None else None),
+                                 if TRAFFIC_BYTES_PER_NODE is not None and dom == "vb2"
+                                 else None),
                      "peak_basis": f"{sms} SMs x 4 SMSP x 32 lanes x {sm_mhz_max:.0f} MHz "
                                    "(integer issue, one warp instruction per clock per SMSP)",
                      "kernel": ("vb2_kernel (VB2 item by item, fixed-point quotients)"
