@@ -214,7 +214,7 @@ def main():
                     help="fix the batched launch shape (default: autotune on the batch)")
     ap.add_argument("--cpu-budget", type=float, default=15.0,
                     help="CPU-seconds of oracle work for the cpu_baseline sample")
-    ap.add_argument("--workload", choices=("search", "plain", "large", "ragged", "serve"),
+    ap.add_argument("--workload", choices=("search", "plain", "large", "ragged", "serve", "table1"),
                     default="search",
                     help="search: the benchmark line (4096 search nodes); plain: one check of "
                          "n=50, c=150 per call (bp_lb_eval), 10^4 calls; large: n=10^4, "
@@ -522,6 +522,93 @@ def ragged_work(rg, algo=1):
     return evals, ops
 
 
+def bound_strength(B, I, h, stream, flush):
+    """Table 1's statistics on the synthetic families (root of the search, no
+    packing): per DFF the instances where it is the only one / one of those
+    reaching the optimum (known for the triplet family) and the best bound
+    among the six, and the sum of its bounds; every bound against L2; and the
+    time of the collection and of L2 on the device."""
+    import torch
+    names = ["MT", "RAD2", "FS1", "CCM1", "VB2", "BJ1"]
+    res = []
+    tot = {nm: dict(only_opt=0, total_opt=0, only_best=0, total_best=0, sum=0, above_l2=0,
+                    equal_l2=0, below_l2=0) for nm in names}
+    coll_tot = dict(instances=0, above_l2=0, equal_l2=0, below_l2=0, opt=0, l2_opt=0, with_opt=0)
+    for fam, rg, opt in I.strength_families():
+        t = (_dev(rg.offsets, torch.int64), _dev(rg.sizes, torch.int32),
+             _dev(rg.capacity, torch.int64), _dev(rg.bins, torch.int64))
+        ob = torch.empty(rg.count, dtype=torch.int64, device="cuda")
+        oa = B.argmax_tensor(rg.count)
+        per = np.zeros((6, rg.count), dtype=np.int64)
+        for d in range(6):
+            B.bp_lb_set_dff_mask(h, 1 << d)
+            B.bp_lb_eval_batch(h, *t, ob, oa, stream=stream)
+            torch.cuda.synchronize()
+            per[d] = ob.cpu().numpy()
+        B.bp_lb_set_dff_mask(h, 63)
+        B.bp_lb_eval_batch(h, *t, ob, oa, stream=stream)
+        ms_coll = float(_time_steps(lambda: B.bp_lb_eval_batch(h, *t, ob, oa, stream=stream), 5,
+                                    flush, stream).mean())
+        lb = ob.cpu().numpy()
+        l2t = torch.empty(rg.count, dtype=torch.int64, device="cuda")
+        B.bp_lb_l2_batch(h, t[0], t[1], t[2], l2t, stream=stream)
+        ms_l2 = float(_time_steps(lambda: B.bp_lb_l2_batch(h, t[0], t[1], t[2], l2t, stream=stream),
+                                  5, flush, stream).mean())
+        l2 = l2t.cpu().numpy()
+        l1 = np.array([-(-int(rg.instance(j).sum()) // int(rg.capacity[j])) for j in range(rg.count)])
+        assert np.array_equal(lb, per.max(axis=0))        # the collection is the max of its DFFs
+        best = per.max(axis=0)
+        nbest = (per == best[None, :]).sum(axis=0)
+        row = {"family": fam, "instances": rg.count, "ms_collection": ms_coll, "ms_l2": ms_l2,
+               "sum_l1": int(l1.sum()), "sum_l2": int(l2.sum()), "sum_collection": int(lb.sum()),
+               "collection_vs_l2": {"above": int((lb > l2).sum()), "equal": int((lb == l2).sum()),
+                                    "below": int((lb < l2).sum())}, "dff": {}}
+        if opt is not None:
+            opt = np.asarray(opt)
+            nopt = (per == opt[None, :]).sum(axis=0)
+            row["optimum_reached"] = {"collection": int((lb == opt).sum()), "L2": int((l2 == opt).sum())}
+            coll_tot["opt"] += int((lb == opt).sum())
+            coll_tot["l2_opt"] += int((l2 == opt).sum())
+            coll_tot["with_opt"] += rg.count
+        for d, nm in enumerate(names):
+            x = per[d]
+            e = {"total_best": int((x == best).sum()), "only_best": int(((x == best) & (nbest == 1)).sum()),
+                 "sum": int(x.sum()), "above_l2": int((x > l2).sum()), "equal_l2": int((x == l2).sum()),
+                 "below_l2": int((x < l2).sum())}
+            if opt is not None:
+                e["total_opt"] = int((x == opt).sum())
+                e["only_opt"] = int(((x == opt) & (nopt == 1)).sum())
+            row["dff"][nm] = e
+            for k2, v in e.items():
+                tot[nm][k2] += v
+        for k2 in ("above", "equal", "below"):
+            coll_tot[k2 + "_l2"] += row["collection_vs_l2"][k2]
+        coll_tot["instances"] += rg.count
+        print(json.dumps(row), flush=True)
+        res.append(row)
+    res.append({"family": "all", "dff": tot, "collection": coll_tot})
+    print(json.dumps(res[-1]), flush=True)
+    # throughput of L2 against the collection on one larger batch
+    rng = np.random.default_rng(61)
+    rg = I.ragged_from_list([I.uniform_sizes(rng, 1000, 20, 100) for _ in range(4096)], [150] * 4096)
+    t = (_dev(rg.offsets, torch.int64), _dev(rg.sizes, torch.int32),
+         _dev(rg.capacity, torch.int64), _dev(rg.bins, torch.int64))
+    ob = torch.empty(rg.count, dtype=torch.int64, device="cuda")
+    l2t = torch.empty(rg.count, dtype=torch.int64, device="cuda")
+    B.bp_lb_l2_batch(h, t[0], t[1], t[2], l2t, stream=stream)
+    B.bp_lb_eval_batch(h, *t, ob, stream=stream)
+    ms_l2 = float(_time_steps(lambda: B.bp_lb_l2_batch(h, t[0], t[1], t[2], l2t, stream=stream),
+                              10, flush, stream).mean())
+    ms_c = float(_time_steps(lambda: B.bp_lb_eval_batch(h, *t, ob, stream=stream), 10, flush,
+                             stream).mean())
+    res.append({"throughput": "4096 instances, n = 1000, sizes U[20, 100], c = 150",
+                "l2_instances_per_s": 4096 / (ms_l2 / 1e3), "l2_ms": ms_l2,
+                "collection_instances_per_s": 4096 / (ms_c / 1e3), "collection_ms": ms_c,
+                "l2_below_collection": int((l2t < ob).sum().item())})
+    print(json.dumps(res[-1]), flush=True)
+    return res
+
+
 def run_sweep(args):
     import torch
     from paper_2402_14821_gb300 import binding as B
@@ -618,6 +705,8 @@ def run_sweep(args):
                 print(json.dumps(out["results"][-1]), flush=True)
             out["server"] = B.bp_serve_stats(srv)
             B.bp_serve_destroy(srv)
+        elif args.workload == "table1":
+            out["results"] = bound_strength(B, I, h, stream, flush)
         else:  # ragged
             nd = I.ragged_nodes(seed=3)
             evals, kops = algorithmic_work(nd)

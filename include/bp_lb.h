@@ -279,6 +279,41 @@ int bp_lb_set_result_mode(bp_lb_t *h, int32_t mode);
 /* The handle's result mode, or -1 for a NULL handle. */
 int bp_lb_get_result_mode(bp_lb_t *h);
 
+/* ---- L2, the comparator ---------------------------------------------------- */
+
+/* Martello and Toth's L2 (Sec. 3.1, the bound the DFF collection replaces)
+ * of B ragged instances, on the device: L2 = max over integer lambda in
+ * [0, floor(c/2)] of |W1| + |W2| + max(0, ceil((sum W3 - (c |W2| - sum W2)) / c)).
+ * One CTA per instance sorts its items in shared memory and evaluates every
+ * lambda where the sets change (O(r log r)); results are exact.
+ *   d_offsets   device int64[B+1], instance b is d_sizes[d_offsets[b] .. d_offsets[b+1]);
+ *   d_sizes     device int32, each in [0, c];
+ *   d_capacity  device int64[B], 1 <= c <= 2^30;
+ *   d_out_l2    device int64[B] (caller-owned): L2, or -BP_ERANGE for an
+ *               instance with a size outside [0, c], a bad capacity or more
+ *               than 8192 items;
+ *   stream      a cudaStream_t (NULL: the legacy default stream).
+ * Stream-ordered; returns BP_EINVAL for NULL pointers or B < 0. */
+int bp_lb_l2_batch(bp_lb_t *h, int32_t B, const int64_t *d_offsets, const int32_t *d_sizes,
+                   const int64_t *d_capacity, int64_t *d_out_l2, void *stream);
+
+/* ---- which DFFs make up the bound ----------------------------------------- */
+
+/* Bit d of `mask` keeps DFF d (BP_DFF_MT = 0 ... BP_DFF_BJ1 = 5) in the
+ * bound; the default is all six (63).  With a single DFF f the result is its
+ * own bound L_f = max over lambda of ceil(sum f(w, lambda) / f(c, lambda))
+ * and its first argmax (Sec. 3.1, Table 1 reports these per DFF).  When
+ * every DFF left in has an empty parameter range at an instance's capacity
+ * (RAD2 at c in {1, 2, 4, 5, 8}, VB2 and CCM1 at c = 1), that instance's
+ * bound is 0 with argmax {-1, 0, -1} (the plain path then returns without a
+ * launch and without checking a node's assignment).  Applies to every call
+ * of the handle.  Errors: BP_EINVAL (NULL handle), BP_ERANGE (mask outside
+ * 1..63). */
+int bp_lb_set_dff_mask(bp_lb_t *h, int32_t mask);
+
+/* The handle's DFF mask, or -1 for a NULL handle. */
+int bp_lb_get_dff_mask(bp_lb_t *h);
+
 /* Measurement aid: with timing on, every batched call records CUDA events
  * on its stream around its three evaluation launches -- the prefix-count
  * kernel, the VB2 kernel (VB2 at c <= 65535, evaluated item by item with its

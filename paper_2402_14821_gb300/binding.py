@@ -78,6 +78,9 @@ def _bind(lib):
                                                      P(_c_i32)]),
         "bp_lb_set_algorithm": (ctypes.c_int, [_vp, _c_i32]),
         "bp_lb_set_result_mode": (ctypes.c_int, [_vp, _c_i32]),
+        "bp_lb_set_dff_mask": (ctypes.c_int, [_vp, _c_i32]),
+        "bp_lb_l2_batch": (ctypes.c_int, [_vp, _c_i32, _vp, _vp, _vp, _vp, _vp]),
+        "bp_lb_get_dff_mask": (ctypes.c_int, [_vp]),
         "bp_lb_get_result_mode": (ctypes.c_int, [_vp]),
         "bp_lb_get_algorithm": (ctypes.c_int, [_vp]),
         "bp_lb_set_kernel_timing": (ctypes.c_int, [_vp, _c_i32]),
@@ -119,7 +122,8 @@ EXPORTED = ("bp_lb_strerror", "bp_lb_create", "bp_lb_destroy", "bp_lb_reserve", 
             "bp_serve_create", "bp_serve_destroy", "bp_serve_register", "bp_serve_submit",
             "bp_serve_poll", "bp_serve_stats", "bp_lb_set_algorithm", "bp_lb_get_algorithm",
             "bp_lb_set_kernel_timing", "bp_lb_kernel_times", "bp_lb_dff_route",
-            "bp_lb_set_result_mode", "bp_lb_get_result_mode")
+            "bp_lb_set_result_mode", "bp_lb_get_result_mode", "bp_lb_set_dff_mask",
+            "bp_lb_get_dff_mask", "bp_lb_l2_batch")
 
 ALGO_DIRECT, ALGO_PREFIX = 0, 1
 RESULT_FULL, RESULT_VERDICT = 0, 1
@@ -227,6 +231,16 @@ def bp_lb_eval_batch(h, offsets, sizes, capacity, bins, out_bound, out_argmax=No
               _ptr(out_feasible, torch.uint8, "out_feasible"), _stream(stream)), "bp_lb_eval_batch")
 
 
+def bp_lb_l2_batch(h, offsets, sizes, capacity, out_l2, stream=None):
+    """Martello-Toth L2 of each ragged instance (int32 sizes) into out_l2 (int64)."""
+    import torch
+    _check(lib().bp_lb_l2_batch(h, offsets.numel() - 1, _ptr(offsets, torch.int64, "offsets"),
+                                _ptr(sizes, torch.int32, "sizes"),
+                                _ptr(capacity, torch.int64, "capacity"),
+                                _ptr(out_l2, torch.int64, "out_l2"), _stream(stream)),
+           "bp_lb_l2_batch")
+
+
 def bp_lb_eval_batch_noalloc(offsets, sizes, capacity, bins, out_bound, out_argmax=None,
                              out_feasible=None, stream=None):
     """bp_lb_eval_batch without a handle and without any device allocation (for
@@ -308,6 +322,15 @@ def bp_lb_set_result_mode(h, mode: int):
 
 def bp_lb_get_result_mode(h) -> int:
     return lib().bp_lb_get_result_mode(h)
+
+
+def bp_lb_set_dff_mask(h, mask: int):
+    """Bit d keeps DFF d (MT, RAD2, FS1, CCM1, VB2, BJ1) in the bound; 63 = all."""
+    _check(lib().bp_lb_set_dff_mask(h, int(mask)), "bp_lb_set_dff_mask")
+
+
+def bp_lb_get_dff_mask(h) -> int:
+    return lib().bp_lb_get_dff_mask(h)
 
 
 def bp_lb_set_kernel_timing(h, on: bool):

@@ -20,6 +20,7 @@
 #include "bp_lb_eval.cuh"
 #include "bp_lb_kernels.cuh"
 #include "bp_lb_launch.cuh"
+#include "bp_lb_l2.cuh"
 
 using namespace bplb;
 
@@ -67,6 +68,7 @@ struct bp_lb {
   // keeps it in the direct kernel (one launch fewer per check)
   int32_t vb2_on = 1;
   int32_t verdict = 0;  // BP_RESULT_FULL (0) or BP_RESULT_VERDICT (1)
+  uint32_t dff_off = 0;  // DFFs left out of the bound (bit d), default none
   // optional per-kernel timing of batched calls (events around each launch)
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -203,6 +205,7 @@ int launch_batch(bp_lb *h, EvalArgs A, size_t smem, cudaStream_t st) {
   A.plpt = kPrefixLPTBatch;
   A.vb2_on = h->vb2_on;
   A.verdict = h->verdict;
+  A.dff_off = h->dff_off;
   A.vtile_start = h->d_vtile_start;
   A.vwork = h->d_work + 2;
   const int shape = h->shape[MODE];
@@ -350,6 +353,10 @@ int bp_lb_create(int64_t capacity, int64_t max_items, bp_lb_t **out) {
                                               (int)vb2_smem(kSrcNodes, kMaxNodeBins)));
     }
     if (st != BP_OK) break;
+    if ((st = cuda_status(cudaFuncSetAttribute(l2_kernel<kL2NT>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)kL2SmemBytes))) != BP_OK)
+      break;
     if ((st = cuda_status(cudaFuncSetAttribute(reduce_kernel<256>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)(sizeof(uint32_t) * kMaxNodeBins)))) != BP_OK)
@@ -401,6 +408,18 @@ static int plain_finish(bp_lb *h, int64_t *out_bound, bp_argmax_t *out_argmax) {
   return BP_OK;
 }
 
+// The plain result when no parameter is left to evaluate (every DFF left in
+// has an empty range at this capacity): bound 0, no argmax.
+static int plain_empty(int64_t *out_bound, bp_argmax_t *out_argmax) {
+  *out_bound = 0;
+  if (out_argmax) {
+    out_argmax->dff = -1;
+    out_argmax->pad = 0;
+    out_argmax->lambda = -1;
+  }
+  return BP_OK;
+}
+
 static EvalArgs plain_args(bp_lb *h, int64_t n, int64_t bins, int mode) {
   EvalArgs A = blank_args();
   A.B = 1;
@@ -413,10 +432,11 @@ static EvalArgs plain_args(bp_lb *h, int64_t n, int64_t bins, int mode) {
   A.prefix_on = h->plain_prefix_on;
   A.vb2_on = 0;
   A.verdict = h->verdict;
+  A.dff_off = h->dff_off;
   A.plpt = kPrefixLPTSingle;
-  A.single_tiles =
-      route_tiles(kRouteDirect, h->capacity, shape_lpt(h->shape[mode]), sb, A.prefix_on, 0);
-  A.single_ptiles = route_tiles(kRoutePrefix, h->capacity, A.plpt, sb, A.prefix_on, 0);
+  A.single_tiles = route_tiles(kRouteDirect, h->capacity, shape_lpt(h->shape[mode]), sb,
+                               A.prefix_on, 0, A.dff_off);
+  A.single_ptiles = route_tiles(kRoutePrefix, h->capacity, A.plpt, sb, A.prefix_on, 0, A.dff_off);
   A.single_vtiles = 0;
   A.single_c = h->capacity;
   A.single_k = bins;
@@ -441,11 +461,13 @@ int bp_lb_eval(bp_lb_t *h, const int32_t *sizes, int64_t n, int64_t bins, int64_
   }
   EvalArgs A = plain_args(h, n, bins, kModePlainRagged);
   A.sizes = h->d_items;
+  if (A.single_ptiles + A.single_tiles == 0) return plain_empty(out_bound, out_argmax);
   if (A.single_ptiles > 0)
     BP_CHECK_STATUS(launch_prefix(kSrcRaggedI32, (unsigned)A.single_ptiles,
                                   prefix_smem(kSrcRaggedI32, 0), h->stream, A));
-  BP_CHECK_STATUS(launch_eval(h->shape[kModePlainRagged], kSrcRaggedI32, (unsigned)A.single_tiles,
-                              eval_smem<kSrcRaggedI32>(0), h->stream, A));
+  if (A.single_tiles > 0)
+    BP_CHECK_STATUS(launch_eval(h->shape[kModePlainRagged], kSrcRaggedI32,
+                                (unsigned)A.single_tiles, eval_smem<kSrcRaggedI32>(0), h->stream, A));
   return plain_finish(h, out_bound, out_argmax);
 }
 
@@ -465,11 +487,13 @@ int bp_lb_eval_node(bp_lb_t *h, const int32_t *w, const int32_t *assign, int64_t
   A.base_sizes = h->d_items;
   A.assign = h->d_assign;
   A.max_bins = (int32_t)bins;
+  if (A.single_ptiles + A.single_tiles == 0) return plain_empty(out_bound, out_argmax);
   if (A.single_ptiles > 0)
     BP_CHECK_STATUS(launch_prefix(kSrcNodes, (unsigned)A.single_ptiles, prefix_smem(kSrcNodes, bins),
                                   h->stream, A));
-  BP_CHECK_STATUS(launch_eval(h->shape[kModePlainNodes], kSrcNodes, (unsigned)A.single_tiles,
-                              eval_smem<kSrcNodes>(bins), h->stream, A));
+  if (A.single_tiles > 0)
+    BP_CHECK_STATUS(launch_eval(h->shape[kModePlainNodes], kSrcNodes, (unsigned)A.single_tiles,
+                                eval_smem<kSrcNodes>(bins), h->stream, A));
   return plain_finish(h, out_bound, out_argmax);
 }
 
@@ -568,6 +592,18 @@ int bp_lb_reduce_nodes(bp_lb_t *h, int32_t B, int32_t num_base, const int64_t *d
   return BP_OK;
 }
 
+int bp_lb_l2_batch(bp_lb_t *h, int32_t B, const int64_t *d_offsets, const int32_t *d_sizes,
+                   const int64_t *d_capacity, int64_t *d_out_l2, void *stream) {
+  if (!h || B < 0) return BP_EINVAL;
+  if (B == 0) return BP_OK;
+  if (!d_offsets || !d_sizes || !d_capacity || !d_out_l2) return BP_EINVAL;
+  const int grid = (int)std::min<int64_t>(B, (int64_t)h->num_sms * 2);
+  l2_kernel<kL2NT><<<grid, kL2NT, kL2SmemBytes, (cudaStream_t)stream>>>(B, d_offsets, d_sizes,
+                                                                       d_capacity, d_out_l2);
+  BP_CHECK(cudaGetLastError());
+  return BP_OK;
+}
+
 int bp_lb_debug_params(bp_lb_t *h, const int32_t *d_sizes, int64_t n, int64_t c,
                        const int32_t *d_dff, const int64_t *d_lambda, int64_t m, int64_t *d_out_lb,
                        void *stream) {
@@ -606,6 +642,18 @@ int bp_lb_set_result_mode(bp_lb_t *h, int32_t mode) {
 int bp_lb_get_result_mode(bp_lb_t *h) {
   if (!h) return -1;
   return h->verdict ? BP_RESULT_VERDICT : BP_RESULT_FULL;
+}
+
+int bp_lb_set_dff_mask(bp_lb_t *h, int32_t mask) {
+  if (!h) return BP_EINVAL;
+  if (mask < 1 || mask > 63) return BP_ERANGE;
+  h->dff_off = (~(uint32_t)mask) & 63u;
+  return BP_OK;
+}
+
+int bp_lb_get_dff_mask(bp_lb_t *h) {
+  if (!h) return -1;
+  return (int)((~h->dff_off) & 63u);
 }
 
 int bp_lb_set_kernel_timing(bp_lb_t *h, int32_t on) {

@@ -73,7 +73,7 @@ struct EvalArgs {
   int64_t single_vtiles;
   unsigned long long *vwork;  // [1] next VB2 tile (persistent mode)
   int32_t verdict;            // verdict-only mode (early exit, exact feasibility)
-  int32_t pad_verdict;
+  uint32_t dff_off;           // bit d set: DFF d is left out of the bound (default 0: all six)
 };
 
 // Shared-memory budget of the prefix-count tables (bytes; 48 KB lets four
@@ -112,10 +112,12 @@ constexpr int64_t kVb2LPT = 4096;
 
 // Which kernel evaluates DFF d of an instance: the prefix-count kernel
 // (prefix_handles), the VB2 kernel (VB2 on its fixed-point path), or the
-// generic direct kernel.
-enum : int { kRouteDirect = 0, kRoutePrefix = 1, kRouteVb2 = 2 };
+// generic direct kernel; none when the DFF is left out (dff_off).
+enum : int { kRouteNone = -1, kRouteDirect = 0, kRoutePrefix = 1, kRouteVb2 = 2 };
 
-BPLB_HD int dff_kernel(int d, int64_t c, int64_t sum_bound, int32_t prefix_on, int32_t vb2_on) {
+BPLB_HD int dff_kernel(int d, int64_t c, int64_t sum_bound, int32_t prefix_on, int32_t vb2_on,
+                       uint32_t dff_off) {
+  if ((dff_off >> d) & 1u) return kRouteNone;
   if (prefix_handles(d, c, sum_bound, prefix_on)) return kRoutePrefix;
   if (vb2_on && d == kVB2 && c <= kVb2FixedCap) return kRouteVb2;
   return kRouteDirect;
@@ -123,10 +125,10 @@ BPLB_HD int dff_kernel(int d, int64_t c, int64_t sum_bound, int32_t prefix_on, i
 
 // Tiles of one kernel for an instance: lpt parameters each, DFFs in paper order.
 BPLB_HD int64_t route_tiles(int route, int64_t c, int64_t lpt, int64_t sum_bound, int32_t prefix_on,
-                            int32_t vb2_on) {
+                            int32_t vb2_on, uint32_t dff_off) {
   int64_t t = 0;
   for (int d = 0; d < kNumDff; ++d)
-    if (dff_kernel(d, c, sum_bound, prefix_on, vb2_on) == route)
+    if (dff_kernel(d, c, sum_bound, prefix_on, vb2_on, dff_off) == route)
       t += (param_count(d, c) + lpt - 1) / lpt;
   return t;
 }
@@ -196,7 +198,9 @@ __device__ __forceinline__ void write_result(const EvalArgs &A, int64_t b, unsig
   A.out_bound[b] = lb;
   if (A.out_argmax) {
     bp_argmax_t r;
-    unflatten(g, c, r.dff, r.lambda);
+    r.dff = -1;  // key 0: no parameter was evaluated
+    r.lambda = -1;
+    if (key != 0ull) unflatten(g, c, r.dff, r.lambda);
     r.pad = 0;
     A.out_argmax[b] = r;
   }
@@ -281,9 +285,11 @@ __global__ void __launch_bounds__(1024)
         ok = c >= 1 && c <= kMaxCapacity && L >= 0 && L <= kMaxItems && A.bins[b] >= 0;
       }
       if (ok) {
-        tiles = route_tiles(kRouteDirect, c, lpt, L * c, A.prefix_on, A.vb2_on);
-        ptiles = route_tiles(kRoutePrefix, c, A.plpt, L * c, A.prefix_on, A.vb2_on);
-        vtiles = route_tiles(kRouteVb2, c, kVb2LPT, L * c, A.prefix_on, A.vb2_on);
+        tiles = route_tiles(kRouteDirect, c, lpt, L * c, A.prefix_on, A.vb2_on, A.dff_off);
+        ptiles = route_tiles(kRoutePrefix, c, A.plpt, L * c, A.prefix_on, A.vb2_on, A.dff_off);
+        vtiles = route_tiles(kRouteVb2, c, kVb2LPT, L * c, A.prefix_on, A.vb2_on, A.dff_off);
+        // no parameter at all (only DFFs with an empty range left in): bound 0
+        if (tiles + ptiles + vtiles == 0) write_result(A, b, 0ull, c, A.bins[b]);
       } else {
         write_error(A, b);
       }
@@ -769,7 +775,7 @@ __device__ void process_tile(const EvalArgs &A, int64_t b, int64_t lt, int64_t n
   int64_t rem = lt;
   const int64_t sb = sum_bound<MODE>(I);
   for (d = 0; d < kNumDff; ++d) {
-    if (dff_kernel(d, c, sb, A.prefix_on, A.vb2_on) != kRouteDirect) continue;
+    if (dff_kernel(d, c, sb, A.prefix_on, A.vb2_on, A.dff_off) != kRouteDirect) continue;
     const int64_t nt = (param_count(d, c) + LPT - 1) / LPT;
     if (rem < nt) break;
     rem -= nt;

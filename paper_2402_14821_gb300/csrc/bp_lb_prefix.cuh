@@ -138,15 +138,18 @@ __device__ __forceinline__ uint32_t bj1_blocks(const int32_t *T, uint32_t sumw, 
   return acc;
 }
 
-// The candidate test (file comment): divide only when S > B f.  Every sum
-// and denominator here is below 2^32 (prefix_handles), so all is 32-bit
+// The candidate test (file comment): divide only when S > B f, or for the
+// thread's first parameter (so that a bound is kept even when no parameter
+// beats B, e.g. with MT left out of the bound and B starting at 0).  Every
+// sum and denominator here is below 2^32 (prefix_handles), so all is 32-bit
 // except the product.
 __device__ __forceinline__ void try_key(uint32_t S, uint32_t f, uint32_t g, uint32_t &B,
                                         unsigned long long &best) {
-  if ((uint64_t)B * f < (uint64_t)S) {
+  if ((uint64_t)B * f < (uint64_t)S || best == 0ull) {
     const uint32_t q = S / f;
-    B = q + (S != q * f);
-    best = make_key((int64_t)B, g);
+    const uint32_t lb = q + (S != q * f);
+    B = max(B, lb);
+    best = make_key((int64_t)lb, g);
   }
 }
 
@@ -227,7 +230,8 @@ __device__ unsigned long long prefix_tile_dff(const EvalArgs &A, const InstView 
   param_range(D, c, lo_d, hi_d);
   // flattened index of parameter l is gofs + l
   const uint32_t gofs = flat_index(D, lo_d, c) - (uint32_t)lo_d;
-  uint32_t B = sumw / c32 + (sumw % c32 != 0u);  // L1
+  // L1 (MT's bound at l = 0) when MT is part of the bound, else no floor
+  uint32_t B = (A.dff_off & 1u) ? 0u : sumw / c32 + (sumw % c32 != 0u);
   unsigned long long best = 0ull;
   // S(l) = sum_w f(w, l) from the accumulators (bp_lb_core.cuh), l-independent
   // parts in kS, evaluated in wrapping 32-bit arithmetic (exact: S < 2^32):
@@ -380,7 +384,7 @@ __global__ void __launch_bounds__(kPrefixNT, 4) prefix_kernel(EvalArgs A) {
     int d = 0;
     const int64_t sb = sum_bound<MODE>(I);
     for (d = 0; d < kNumDff; ++d) {
-      if (!prefix_handles(d, I.c, sb, A.prefix_on)) continue;
+      if (dff_kernel(d, I.c, sb, A.prefix_on, A.vb2_on, A.dff_off) != kRoutePrefix) continue;
       const int64_t nt = (param_count(d, I.c) + A.plpt - 1) / A.plpt;
       if (rem < nt) break;
       rem -= nt;

@@ -242,3 +242,70 @@ def random_small(rng: np.random.Generator, n_max: int, c_max: int):
     c = int(rng.integers(1, c_max + 1))
     n = int(rng.integers(0, n_max + 1))
     return rng.integers(0, c + 1, size=n, dtype=np.int64), c
+
+
+def strength_families(seed: int = 6):
+    """Seeded stand-ins shaped like the paper's benchmark classes (Sec. 5; no
+    instance of those sets is reproduced), for comparing bound strength
+    (Table 1's statistics) at the root of the search:
+      U   c = 150, sizes U[20, 100], n in {120, 250, 500, 1000}
+      T   c = 1000, triplets filling bins exactly, n in {60, 120, 249, 501}
+          (optimum n / 3 by construction)
+      S1  n in {50, 100, 200, 500}, c in {100, 120, 150}, sizes U[1, 100],
+          U[20, 100] or U[30, 100] (at most about three items per bin)
+      S2  c = 1000, n as S1, sizes U[a (1 - d), a (1 + d)] with mean
+          a in {c/3, c/5, c/7, c/9}, d in {0.2, 0.5, 0.9} (three to nine per bin)
+      S3  c = 100000, n = 200, sizes U[20000, 35000]
+      W   n in {100, 200}, sizes 1 + floor(1000 X), X ~ Weibull(k),
+          k in {0.5, 1.0, ..., 5.0}, c = round(s max w), s in {1.0, 1.4, 2.0}
+    Returns a list of (family, Ragged, optimum or None per instance)."""
+    rng = _rng(seed)
+    fams = []
+
+    def add(name, inst, caps, opt=None):
+        fams.append((name, ragged_from_list(inst, caps), opt))
+
+    inst, caps = [], []
+    for n in (120, 250, 500, 1000):
+        for _ in range(20):
+            inst.append(uniform_sizes(rng, n, 20, 100))
+            caps.append(150)
+    add("U", inst, caps)
+    inst, caps, opt = [], [], []
+    for n in (60, 120, 249, 501):
+        for _ in range(20):
+            inst.append(triplet_sizes(rng, n, 1000))
+            caps.append(1000)
+            opt.append(n // 3)
+    add("T", inst, caps, opt)
+    inst, caps = [], []
+    for n in (50, 100, 200, 500):
+        for c in (100, 120, 150):
+            for lo in (1, 20, 30):
+                for _ in range(5):
+                    inst.append(uniform_sizes(rng, n, lo, 100))
+                    caps.append(c)
+    add("S1", inst, caps)
+    inst, caps = [], []
+    for n in (50, 100, 200, 500):
+        for a in (1000 // 3, 1000 // 5, 1000 // 7, 1000 // 9):
+            for d in (0.2, 0.5, 0.9):
+                for _ in range(2):
+                    inst.append(uniform_sizes(rng, n, max(1, int(a * (1 - d))), int(a * (1 + d))))
+                    caps.append(1000)
+    add("S2", inst, caps)
+    inst, caps = [], []
+    for _ in range(10):
+        inst.append(uniform_sizes(rng, 200, 20000, 35000))
+        caps.append(100000)
+    add("S3", inst, caps)
+    inst, caps = [], []
+    for n in (100, 200):
+        for k in np.arange(0.5, 5.01, 0.5):
+            w = 1 + np.floor(1000.0 * rng.weibull(float(k), size=n)).astype(np.int64)
+            for s in (1.0, 1.4, 2.0):
+                inst.append(w.copy())
+                caps.append(int(round(s * int(w.max()))))
+    add("W", inst, caps)
+    return fams
+
