@@ -44,12 +44,12 @@ NODES, N_ITEMS, CAP = 4096, 500, 10_000
 #   RAD2 two compares + two counts                                   4
 #   FS1  mul, mul-high, shift, add, mul, compare, conditional add    7
 #   CCM1 one multiply-high-add (c <= 131071)                         1   (else 3)
-#   VB2  mul-add, half of a two-word add of an item pair (c <= 65535) 2   (fp32 path 5)
+#   VB2  mul-add, shift, half of a 3-input add (c <= 65535)         2.5 (fp32 path 5)
 #   BJ1  mul-high, two mul-adds, min, add (c <= 65535)               5   (else 6)
 def ops_per_eval(d, c):
     return {0: 2, 1: 4, 2: 7,
             3: 1 if c <= 131071 else 3,
-            4: 2 if c <= 65535 else 5,
+            4: 2.5 if c <= 65535 else 5,
             5: 5 if c <= 65535 else 6}[d]
 SM_COUNT_NOMINAL = 152
 # DRAM bytes (read + write) per search node of one vb2_kernel launch, from one
@@ -104,7 +104,7 @@ def algorithmic_work(nd, algo=1):
             evals += int(r[j]) * cnt[d]
             k = kernel_of(d, c, L, algo)
             if k != "prefix":
-                ops[k] += int(r[j]) * cnt[d] * ops_per_eval(d, c)
+                ops[k] += r[j] * cnt[d] * ops_per_eval(d, c)
     return evals, ops
 
 

@@ -223,29 +223,33 @@ BPLB_D void ccm1_list_noshift(const uint32_t *s, int beg, int end, int K, const 
 // 2^32 (u l + c - 1) / c + e with 0 <= e < l + 1; the fraction of
 // (u l + c - 1) / c is at most (c - 1) / c, and (l + 1) c < 2^32 keeps
 // e / 2^32 below 1 / c, so floor(Y / 2^32) = floor((u l + c - 1) / c)
-// = ceil(u l / c) exactly.  Over the list,
-//   sum floor(Y / 2^32) = (sum Y - sum (Y mod 2^32)) / 2^32,
-// with sum Y = l sum F + n Y0 and Y mod 2^32 one 32-bit multiply-add per
-// item: no multiply-high in the loop (padding slots hold F = 0 and cancel).
+// = ceil(u l / c) exactly.  Over a list of n entries,
+//   sum floor(Y / 2^32) = (sum Y - Z) / 2^32,  Z = sum (Y mod 2^32),
+// with sum Y = l sum F + n Y0 known and Y mod 2^32 one 32-bit multiply-add
+// per item: no multiply-high in the loop.  Z itself is not summed: with
+// H = sum ((Y mod 2^32) >> 16) (a 32-bit sum while n < 2^16),
+// Z lies in [H 2^16, H 2^16 + n 2^16) and Z = sum Y mod 2^32, so
+//   sum floor(Y / 2^32) = (sum Y - H 2^16) >> 32.
+// Padding slots hold F = 0 and cancel.
 template <int T, int SIGN>
 BPLB_D void vb2_list_fixed(const uint32_t *s, int beg, int end, const uint32_t (&lam)[T],
                            uint32_t Y0, uint64_t sumF, int64_t (&acc)[T]) {
-  uint64_t z[T];
+  uint32_t h[T];
 #pragma unroll
-  for (int j = 0; j < T; ++j) z[j] = 0;
+  for (int j = 0; j < T; ++j) h[j] = 0;
 #pragma unroll 2
   for (int i = beg; i < end; i += 4) {
     const uint4 v = lds4(s, i);
 #pragma unroll
     for (int j = 0; j < T; ++j) {
-      z[j] += (uint64_t)(v.x * lam[j] + Y0) + (uint64_t)(v.y * lam[j] + Y0);
-      z[j] += (uint64_t)(v.z * lam[j] + Y0) + (uint64_t)(v.w * lam[j] + Y0);
+      h[j] += ((v.x * lam[j] + Y0) >> 16) + ((v.y * lam[j] + Y0) >> 16);
+      h[j] += ((v.z * lam[j] + Y0) >> 16) + ((v.w * lam[j] + Y0) >> 16);
     }
   }
   const uint64_t nY0 = (uint64_t)(end - beg) * Y0;
 #pragma unroll
   for (int j = 0; j < T; ++j)
-    acc[j] += SIGN * (int64_t)(((uint64_t)lam[j] * sumF + nY0 - z[j]) >> 32);
+    acc[j] += SIGN * (int64_t)(((uint64_t)lam[j] * sumF + nY0 - ((uint64_t)h[j] << 16)) >> 32);
 }
 
 // The fixed-point list value F = ceil(u 2^32 / c) and offset Y0 of vb2_list_fixed.
