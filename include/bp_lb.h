@@ -314,8 +314,23 @@ int bp_lb_set_dff_mask(bp_lb_t *h, int32_t mask);
 /* The handle's DFF mask, or -1 for a NULL handle. */
 int bp_lb_get_dff_mask(bp_lb_t *h);
 
+/* ---- concurrency of the evaluation kernels (batched calls) ----------------- */
+
+/* A batched call runs three evaluation kernels (see bp_lb_kernel_times), by
+ * default (0) one after another on the caller's stream.  With
+ * prefix_ctas_per_sm > 0 the prefix-count kernel, then the generic kernel,
+ * run on a high-priority side stream of the handle while the VB2 kernel runs
+ * on the caller's stream: the prefix kernel takes that many CTAs per SM, the
+ * VB2 kernel the rest (its remaining CTAs become resident as the prefix
+ * kernel's retire).  The call stays ordered on the caller's stream (fork
+ * after the planning kernel, join before the call's work is complete) and can
+ * be captured in a CUDA graph.  Results are identical either way; on the
+ * search-node batch the serial order is the faster one.
+ * Errors: BP_EINVAL (NULL handle), BP_ERANGE (outside 0..8). */
+int bp_lb_set_overlap(bp_lb_t *h, int32_t prefix_ctas_per_sm);
+
 /* Measurement aid: with timing on, every batched call records CUDA events
- * on its stream around its three evaluation launches -- the prefix-count
+ * on their streams around its three evaluation launches -- the prefix-count
  * kernel, the VB2 kernel (VB2 at c <= 65535, evaluated item by item with its
  * fixed-point quotients) and the generic direct kernel (every other (DFF,
  * lambda) evaluated item by item) -- (not for use under stream capture).

@@ -79,6 +79,7 @@ def _bind(lib):
         "bp_lb_set_algorithm": (ctypes.c_int, [_vp, _c_i32]),
         "bp_lb_set_result_mode": (ctypes.c_int, [_vp, _c_i32]),
         "bp_lb_set_dff_mask": (ctypes.c_int, [_vp, _c_i32]),
+        "bp_lb_set_overlap": (ctypes.c_int, [_vp, _c_i32]),
         "bp_lb_l2_batch": (ctypes.c_int, [_vp, _c_i32, _vp, _vp, _vp, _vp, _vp]),
         "bp_lb_get_dff_mask": (ctypes.c_int, [_vp]),
         "bp_lb_get_result_mode": (ctypes.c_int, [_vp]),
@@ -123,7 +124,7 @@ EXPORTED = ("bp_lb_strerror", "bp_lb_create", "bp_lb_destroy", "bp_lb_reserve", 
             "bp_serve_poll", "bp_serve_stats", "bp_lb_set_algorithm", "bp_lb_get_algorithm",
             "bp_lb_set_kernel_timing", "bp_lb_kernel_times", "bp_lb_dff_route",
             "bp_lb_set_result_mode", "bp_lb_get_result_mode", "bp_lb_set_dff_mask",
-            "bp_lb_get_dff_mask", "bp_lb_l2_batch")
+            "bp_lb_get_dff_mask", "bp_lb_l2_batch", "bp_lb_set_overlap")
 
 ALGO_DIRECT, ALGO_PREFIX = 0, 1
 RESULT_FULL, RESULT_VERDICT = 0, 1
@@ -322,6 +323,11 @@ def bp_lb_set_result_mode(h, mode: int):
 
 def bp_lb_get_result_mode(h) -> int:
     return lib().bp_lb_get_result_mode(h)
+
+
+def bp_lb_set_overlap(h, prefix_ctas_per_sm: int):
+    """Prefix-count kernel CTAs per SM beside the VB2 kernel (0: one kernel after another)."""
+    _check(lib().bp_lb_set_overlap(h, int(prefix_ctas_per_sm)), "bp_lb_set_overlap")
 
 
 def bp_lb_set_dff_mask(h, mask: int):

@@ -68,11 +68,19 @@ struct bp_lb {
   // keeps it in the direct kernel (one launch fewer per check)
   int32_t vb2_on = 1;
   int32_t verdict = 0;  // BP_RESULT_FULL (0) or BP_RESULT_VERDICT (1)
+  // With prefix_ctas > 0, batched calls run the prefix-count kernel (then the
+  // generic kernel) on a high-priority side stream beside the VB2 kernel:
+  // prefix_ctas CTAs per SM for the prefix kernel, the rest of each SM for
+  // VB2.  Default 0: one after another (faster on the search-node batch, the
+  // latency-bound prefix kernel needs all its resident CTAs).
+  int32_t prefix_ctas = 0;
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   uint32_t dff_off = 0;  // DFFs left out of the bound (bit d), default none
   // optional per-kernel timing of batched calls (events around each launch)
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
-  std::vector<std::array<cudaEvent_t, 4>> ev_pending;
+  std::vector<std::array<cudaEvent_t, 6>> ev_pending;
   size_t ev_next = 0;
   unsigned long long *d_keys = nullptr;
   unsigned int *d_done = nullptr;
@@ -214,22 +222,47 @@ int launch_batch(bp_lb *h, EvalArgs A, size_t smem, cudaStream_t st) {
   plan_kernel<MODE><<<1, 1024, 0, st>>>(A, shape_lpt(shape), h->d_tile_start, h->d_ptile_start,
                                         h->d_vtile_start);
   BP_CHECK(cudaGetLastError());
-  std::array<cudaEvent_t, 4> ev = {nullptr, nullptr, nullptr, nullptr};
-  if (h->timing) {
+  // Timing events: [0] before the prefix kernel, [1] after it, [2] before the
+  // VB2 kernel, [3] after it, [4] before the generic kernel, [5] after it.
+  std::array<cudaEvent_t, 6> ev = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  if (h->timing)
     for (auto &e : ev)
       if (!(e = next_event(h))) return BP_ECUDA;
-    BP_CHECK(cudaEventRecord(ev[0], st));
-  }
+  const size_t ps = prefix_smem(MODE, A.max_bins);
+  int pocc = 0;
   if (h->prefix_on) {
-    // the prefix-count tiles first (short), then the persistent direct kernel
-    const size_t ps = prefix_smem(MODE, A.max_bins);
-    int pocc = 0;
     BP_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pocc, (const void *)prefix_fn(MODE),
                                                            kPrefixNT, ps));
     if (pocc <= 0) return BP_ECUDA;
-    BP_CHECK_STATUS(launch_prefix(MODE, (unsigned)(h->num_sms * pocc), ps, st, A));
   }
-  if (h->timing) BP_CHECK(cudaEventRecord(ev[1], st));
+  // With overlap, the prefix kernel (latency-bound table lookups) and then the
+  // generic kernel run on the side stream while the VB2 kernel (bound by
+  // integer issue) takes the rest of every SM; VB2's CTAs that do not fit at
+  // first become resident as the prefix kernel's retire.  Stream-ordered
+  // (fork after the plan, join before returning), so capturable in a graph.
+  const bool overlap = h->prefix_ctas > 0 && h->vb2_on;
+  cudaStream_t ps_st = overlap ? h->side : st;
+  if (overlap) {
+    BP_CHECK(cudaEventRecord(h->ev_fork, st));
+    BP_CHECK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+  }
+  if (h->timing) BP_CHECK(cudaEventRecord(ev[0], ps_st));
+  if (h->prefix_on) {
+    const int pc = overlap ? std::min(pocc, (int)h->prefix_ctas) : pocc;
+    BP_CHECK_STATUS(launch_prefix(MODE, (unsigned)(h->num_sms * pc), ps, ps_st, A));
+  }
+  if (h->timing) BP_CHECK(cudaEventRecord(ev[1], ps_st));
+  auto generic = [&](cudaStream_t gs) -> int {
+    if (h->timing) BP_CHECK(cudaEventRecord(ev[4], gs));
+    BP_CHECK_STATUS(launch_eval(shape, MODE, (unsigned)(h->num_sms * occ), smem, gs, A));
+    if (h->timing) BP_CHECK(cudaEventRecord(ev[5], gs));
+    return BP_OK;
+  };
+  if (overlap) {
+    BP_CHECK_STATUS(generic(h->side));
+    BP_CHECK(cudaEventRecord(h->ev_join, h->side));
+  }
+  if (h->timing) BP_CHECK(cudaEventRecord(ev[2], st));
   if (h->vb2_on) {
     // VB2's tiles on their own kernel (empty when no instance has any)
     const size_t vs = vb2_smem(MODE, A.max_bins);
@@ -241,12 +274,10 @@ int launch_batch(bp_lb *h, EvalArgs A, size_t smem, cudaStream_t st) {
     BP_CHECK(cudaLaunchKernel((const void *)vb2_fn(shape, MODE), dim3((unsigned)(h->num_sms * vocc)),
                               dim3(kVb2NT), args, vs, st));
   }
-  if (h->timing) BP_CHECK(cudaEventRecord(ev[2], st));
-  BP_CHECK_STATUS(launch_eval(shape, MODE, (unsigned)(h->num_sms * occ), smem, st, A));
-  if (h->timing) {
-    BP_CHECK(cudaEventRecord(ev[3], st));
-    h->ev_pending.push_back(ev);
-  }
+  if (h->timing) BP_CHECK(cudaEventRecord(ev[3], st));
+  if (overlap) BP_CHECK(cudaStreamWaitEvent(st, h->ev_join, 0));
+  else BP_CHECK_STATUS(generic(st));
+  if (h->timing) h->ev_pending.push_back(ev);
   return BP_OK;
 }
 
@@ -322,6 +353,15 @@ int bp_lb_create(int64_t capacity, int64_t max_items, bp_lb_t **out) {
       break;
     if ((st = cuda_status(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking))) != BP_OK)
       break;
+    int prio_lo = 0, prio_hi = 0;
+    if ((st = cuda_status(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi))) != BP_OK) break;
+    if ((st = cuda_status(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, prio_hi))) !=
+        BP_OK)
+      break;
+    if ((st = cuda_status(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming))) != BP_OK)
+      break;
+    if ((st = cuda_status(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming))) != BP_OK)
+      break;
     const size_t nb = sizeof(int32_t) * (size_t)max_items;
     if ((st = cuda_status(cudaMalloc(&h->d_items, nb))) != BP_OK) break;
     if ((st = cuda_status(cudaMalloc(&h->d_assign, nb))) != BP_OK) break;
@@ -390,6 +430,9 @@ int bp_lb_destroy(bp_lb_t *h) {
   cudaFree(h->d_done);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   if (h->stream) cudaStreamDestroy(h->stream);
+  if (h->side) cudaStreamDestroy(h->side);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   delete h;
   return BP_OK;
 }
@@ -644,6 +687,13 @@ int bp_lb_get_result_mode(bp_lb_t *h) {
   return h->verdict ? BP_RESULT_VERDICT : BP_RESULT_FULL;
 }
 
+int bp_lb_set_overlap(bp_lb_t *h, int32_t prefix_ctas_per_sm) {
+  if (!h) return BP_EINVAL;
+  if (prefix_ctas_per_sm < 0 || prefix_ctas_per_sm > 8) return BP_ERANGE;
+  h->prefix_ctas = prefix_ctas_per_sm;
+  return BP_OK;
+}
+
 int bp_lb_set_dff_mask(bp_lb_t *h, int32_t mask) {
   if (!h) return BP_EINVAL;
   if (mask < 1 || mask > 63) return BP_ERANGE;
@@ -668,10 +718,11 @@ int bp_lb_kernel_times(bp_lb_t *h, double *ms_prefix, double *ms_vb2, double *ms
   double p = 0.0, v = 0.0, d = 0.0;
   for (const auto &ev : h->ev_pending) {
     BP_CHECK(cudaEventSynchronize(ev[3]));
+    BP_CHECK(cudaEventSynchronize(ev[5]));
     float a = 0.f, b = 0.f, e = 0.f;
     BP_CHECK(cudaEventElapsedTime(&a, ev[0], ev[1]));
-    BP_CHECK(cudaEventElapsedTime(&b, ev[1], ev[2]));
-    BP_CHECK(cudaEventElapsedTime(&e, ev[2], ev[3]));
+    BP_CHECK(cudaEventElapsedTime(&b, ev[2], ev[3]));
+    BP_CHECK(cudaEventElapsedTime(&e, ev[4], ev[5]));
     p += a;
     v += b;
     d += e;

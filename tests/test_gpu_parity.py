@@ -402,3 +402,29 @@ def test_prefix_and_direct_match_oracle(cudalib, orc):
             assert cudalib.bp_lb_eval(h, w, 3)[:3] == orc.lb(w, 4096, 3)[:3]
     finally:
         cudalib.bp_lb_destroy(h)
+
+
+# ---------------------------------------------------------------------------
+# the prefix-count kernel beside the VB2 kernel (default) or after it
+# ---------------------------------------------------------------------------
+def test_overlap_and_serial_identical(cudalib, orc):
+    nd = I.ragged_nodes(seed=19, count=300, n_lo=1, n_hi=2500, caps=(150, 1000, 9999, 30000))
+    rng = np.random.default_rng(19)
+    rg = random_ragged(rng, 120, 1, 20000, 400)
+    h = cudalib.bp_lb_create(150, 1 << 16)
+    try:
+        got = {}
+        for pc in (0, 1, 2, 4):
+            cudalib.bp_lb_set_overlap(h, pc)
+            got[pc] = (run_nodes(cudalib, h, nd), run_batch(cudalib, h, rg))
+        for pc in (1, 2, 4):
+            for a, b in zip(got[pc], got[0]):
+                for x, y in zip(a, b):
+                    assert np.array_equal(x, y), pc
+        for j in range(0, nd.count, 23):
+            assert (int(got[2][0][0][j]),) == (oracle_node(orc, nd, j)[0],)
+        assert_same(got[2][1], oracle_batch(orc, rg), "overlap batch")
+        with pytest.raises(cudalib.BpLbError):
+            cudalib.bp_lb_set_overlap(h, 9)
+    finally:
+        cudalib.bp_lb_destroy(h)
