@@ -123,13 +123,39 @@ BPLB_HD int dff_kernel(int d, int64_t c, int64_t sum_bound, int32_t prefix_on, i
   return kRouteDirect;
 }
 
-// Tiles of one kernel for an instance: lpt parameters each, DFFs in paper order.
+// MT, RAD2 and CCM1 share one prefix-kernel tile per instance (the u group:
+// one pass over the items builds E and a table of packed small/big counts)
+// when at least two of them go to the prefix kernel, each of those fits one
+// tile of lpt parameters, the two u-domain tables fit the budget, and the
+// counts fit 16 bits (stream length below 2^15; sum_bound = stream length c).
+BPLB_HD bool prefix_u_merged(int64_t c, int64_t sum_bound, int32_t prefix_on, int32_t vb2_on,
+                             uint32_t dff_off, int64_t lpt) {
+  if (!prefix_on || sum_bound / c >= (int64_t(1) << 15)) return false;
+  if (8 * ((c - 1) / 2 + 2) > kPrefixSmemBytes) return false;
+  const int ds[3] = {kMT, kRAD2, kCCM1};
+  int members = 0;
+  for (int i = 0; i < 3; ++i) {
+    const int64_t pc = param_count(ds[i], c);
+    if (pc == 0 || dff_kernel(ds[i], c, sum_bound, prefix_on, vb2_on, dff_off) != kRoutePrefix)
+      continue;
+    if (pc > lpt) return false;
+    ++members;
+  }
+  return members >= 2;
+}
+
+// Tiles of one kernel for an instance: lpt parameters each, DFFs in paper
+// order; on the prefix kernel the u group, when merged, is one tile.
 BPLB_HD int64_t route_tiles(int route, int64_t c, int64_t lpt, int64_t sum_bound, int32_t prefix_on,
                             int32_t vb2_on, uint32_t dff_off) {
-  int64_t t = 0;
-  for (int d = 0; d < kNumDff; ++d)
+  const bool merged =
+      route == kRoutePrefix && prefix_u_merged(c, sum_bound, prefix_on, vb2_on, dff_off, lpt);
+  int64_t t = merged ? 1 : 0;
+  for (int d = 0; d < kNumDff; ++d) {
+    if (merged && d != kBJ1) continue;
     if (dff_kernel(d, c, sum_bound, prefix_on, vb2_on, dff_off) == route)
       t += (param_count(d, c) + lpt - 1) / lpt;
+  }
   return t;
 }
 

@@ -100,19 +100,46 @@ __device__ void suffix_scan(int32_t *a, int n, PrefixShared &S) {
   __syncthreads();
 }
 
+// In-place suffix scan of packed count words (low 16 bits: small items at
+// u, high 16 bits: big items at u), each word then rewritten as
+// (N'(x) mod 2^16) | (Ns(x) << 16) with N' = Ns - Nb.  Every lane's total is
+// at most the stream length (< 2^15 on this path), so the packed sums never
+// carry from one lane into the other.
+__device__ __forceinline__ void packed_count_scan(uint32_t *a, int n, PrefixShared &S) {
+  const int per = ((n + kPrefixNT - 1) / kPrefixNT) | 1;
+  const int s0 = min(n, (int)threadIdx.x * per), s1 = min(n, s0 + per);
+  uint32_t h = 0;
+  for (int i = s0; i < s1; ++i) h += a[i];
+  uint32_t run = block_sum_after(h, S.wtot[0]);
+  for (int i = s1 - 1; i >= s0; --i) {
+    run += a[i];
+    const uint32_t ns = run & 0xFFFFu, nb = run >> 16;
+    a[i] = ((ns - nb) & 0xFFFFu) | (ns << 16);
+  }
+  __syncthreads();
+}
+
+// N' at x: an int32 table (CCM1's own tile) or the low 16 bits of a packed
+// count word (the u-group tile, packed_count_scan).
+template <bool PACKED>
+__device__ __forceinline__ int32_t np_at(const int32_t *T, uint32_t x) {
+  return PACKED ? (int32_t)reinterpret_cast<const int16_t *>(T)[2u * x] : T[x];
+}
+
 // Strided lookup blocks b0, b0 + bs, ... of one parameter (D = CCM1 or BJ1):
 //   CCM1: block b is x = (b + 1) l <= U, term N'(x);
 //   BJ1:  block b is x = b l + 1 <= c, term NN(x) - NN(x + cm)  (cm > 0).
 // Unrolled by two with explicit bounds (no trip-count division).
-template <int D>
+template <int D, bool PACKED>
 __device__ __forceinline__ uint32_t block_terms(const int32_t *T, uint32_t c32, uint32_t U,
                                                 uint32_t l, uint32_t cm, uint32_t b0, uint32_t bs) {
   const uint32_t step = bs * l;
   uint32_t acc = 0;
   if (D == kCCM1) {
     uint32_t x = (b0 + 1u) * l;
-    for (; x + step <= U; x += 2u * step) acc += (uint32_t)T[x] + (uint32_t)T[x + step];
-    if (x <= U) acc += (uint32_t)T[x];
+    for (; x + step <= U; x += 2u * step)
+      acc += (uint32_t)np_at<PACKED>(T, x) + (uint32_t)np_at<PACKED>(T, x + step);
+    if (x <= U) acc += (uint32_t)np_at<PACKED>(T, x);
   } else {
     uint32_t x = b0 * l + 1u;
     const int32_t *T2 = T + cm;
@@ -153,121 +180,75 @@ __device__ __forceinline__ void try_key(uint32_t S, uint32_t f, uint32_t g, uint
   }
 }
 
-// Builds the table(s) of DFF D for instance I and evaluates parameters
-// [lam0, lam_end); returns the thread's best key.
-template <int MODE, int D>
-__device__ unsigned long long prefix_tile_dff(const EvalArgs &A, const InstView &I, int64_t lam0,
-                                              int64_t lam_end, int32_t *tab, uint32_t *s_load,
-                                              PrefixShared &S) {
-  const int tid = threadIdx.x;
-  const int64_t c = I.c;
-  const uint32_t c32 = (uint32_t)c;
-  const uint32_t U = (uint32_t)((c - 1) / 2);
-  const int nU = (int)U + 2, nW = (int)c + 2;
-  int32_t *T0 = tab;       // E, N', N' or NN
-  int32_t *T1 = tab + nU;  // RAD2: Ns
-  const int nzero = (D == kBJ1) ? nW : (D == kRAD2 ? 2 * nU : nU);
-  {
-    int4 *t4 = reinterpret_cast<int4 *>(tab);
-    const int4 z = make_int4(0, 0, 0, 0);
-    for (int i = tid; i < (nzero + 3) / 4; i += kPrefixNT) t4[i] = z;
-  }
-  if (tid < 8) S.sums[tid] = 0;
-  __syncthreads();
+// Pseudo-DFF of the merged u-group tile: MT, RAD2 and CCM1 of one instance
+// from one histogram pass (E and packed small/big counts, prefix_u_merged).
+constexpr int kPrefixU = kNumDff;
 
-  // ---- histogram the instance's items ----------------------------------------
-  uint32_t ls[7] = {0, 0, 0, 0, 0, 0, 0};
-  const int64_t L = stream_len<MODE>(I);
-  for (int64_t q = tid; q < L; q += kPrefixNT) {
-    int64_t w = 0;
-    if (!fetch_item<MODE>(A, I, s_load, q, w)) continue;
-    if (w < 0 || w > c) {
-      S.err = 1;
-      continue;
-    }
-    ls[5] += (uint32_t)w;
-    if (D == kBJ1) {
-      atomicAdd(&T0[w], 1);
-      continue;
-    }
-    if (w == 0) continue;
-    if (w == c) {
-      ls[3]++;
-    } else if (2 * w < c) {
-      ls[0]++;
-      atomicAdd(&T0[w], D == kMT ? (int32_t)w : 1);
-      if (D == kRAD2) atomicAdd(&T1[w], 1);
-    } else if (2 * w > c) {
-      const int64_t u = c - w;
-      ls[1]++;
-      ls[4] += (uint32_t)w;
-      ls[6] += (uint32_t)u;
-      atomicAdd(&T0[u], D == kMT ? -(int32_t)u : -1);
+// Per-tile constants of the parameter loops.
+struct PrefixEval {
+  uint32_t c32, U;
+  uint32_t sumw, n_big, n_half, n_full, sumw_big, TB;
+  uint32_t B;                // the thread's best bound so far (L1 or 0 at first)
+  unsigned long long best;   // the thread's best key
+};
+
+// MT: S(l) = E(l) + TB + sumw_big + n_half (c/2) + n_full c, f = c; one lookup.
+__device__ __forceinline__ void eval_mt(const int32_t *E, int64_t lam0, int64_t lam_end,
+                                        int64_t c, PrefixEval &x) {
+  int64_t lo_d, hi_d;
+  param_range(kMT, c, lo_d, hi_d);
+  const uint32_t gofs = flat_index(kMT, lo_d, c) - (uint32_t)lo_d;
+  const uint32_t kS = x.TB + x.sumw_big + x.n_half * (x.c32 / 2u) + x.n_full * x.c32;
+  const uint32_t l0 = (uint32_t)lam0, le = (uint32_t)lam_end;
+  if (l0 == 0u && threadIdx.x == 0 && !x.best) x.best = make_key((int64_t)x.B, gofs);  // l = 0: L1
+  for (uint32_t l = l0 + threadIdx.x; l < le; l += kPrefixNT)
+    try_key((uint32_t)E[min(l, x.U + 1u)] + kS, x.c32, gofs + l, x.B, x.best);
+}
+
+// RAD2: n1 = N'(l), n2s = Ns(y), n2b = Ns(y) - N'(y), y = c - 2l + 1; f = c.
+template <bool PACKED>
+__device__ __forceinline__ void eval_rad2(const int32_t *T0, const int32_t *T1, int64_t lam0,
+                                          int64_t lam_end, int64_t c, PrefixEval &x) {
+  int64_t lo_d, hi_d;
+  param_range(kRAD2, c, lo_d, hi_d);
+  const uint32_t gofs = flat_index(kRAD2, lo_d, c) - (uint32_t)lo_d;
+  const uint32_t A3 = x.c32 / 3u, B2 = x.c32 / 2u;
+  const uint32_t kS = x.n_big * x.c32 + x.n_half * B2 + x.n_full * x.c32;
+  for (uint32_t l = (uint32_t)lam0 + threadIdx.x; l < (uint32_t)lam_end; l += kPrefixNT) {
+    const uint32_t y = min(x.c32 - 2u * l + 1u, x.U + 1u);
+    uint32_t n1, n2s, npy;
+    if (PACKED) {
+      const uint32_t *P = reinterpret_cast<const uint32_t *>(T1);
+      n1 = (uint32_t)np_at<true>(T1, l);
+      n2s = P[y] >> 16;
+      npy = (uint32_t)np_at<true>(T1, y);
     } else {
-      ls[2]++;
+      n1 = (uint32_t)T0[l];
+      n2s = (uint32_t)T1[y];
+      npy = (uint32_t)T0[y];
     }
+    const uint32_t n2b = n2s - npy;
+    try_key(A3 * n1 + (B2 - A3) * n2s - (x.c32 - A3 - B2) * n2b + kS, x.c32, gofs + l, x.B, x.best);
   }
-  // every count and sum is below 2^31 on this path: 32-bit warp reductions
-#pragma unroll
-  for (int e = 0; e < 7; ++e) {
-    const uint32_t x = __reduce_add_sync(0xFFFFFFFFu, ls[e]);
-    if (lane_id() == 0 && x != 0u) atomicAdd((unsigned long long *)&S.sums[e], (unsigned long long)x);
-  }
-  __syncthreads();
-  if (D == kBJ1) {
-    suffix_scan<true>(T0, nW, S);
-  } else {
-    suffix_scan<false>(T0, nU, S);
-    if (D == kRAD2) suffix_scan<false>(T1, nU, S);
-  }
-  if (S.err) return 0ull;
+}
 
-  // all below 2^31 on this path (prefix_handles); the sums S(l) below 2^32
-  const uint32_t n_big = (uint32_t)S.sums[1], n_half = (uint32_t)S.sums[2];
-  const uint32_t n_full = (uint32_t)S.sums[3], sumw_big = (uint32_t)S.sums[4];
-  const uint32_t sumw = (uint32_t)S.sums[5], TB = (uint32_t)S.sums[6];
+// CCM1 / BJ1: the lookups of parameter l fall like X / l, so heavy parameters
+// are shared by the CTA, medium ones by a warp, the rest take a thread each.
+template <int D, bool PACKED>
+__device__ void eval_harmonic(const int32_t *T0, int64_t lam0, int64_t lam_end, int64_t c,
+                              PrefixEval &x, PrefixShared &S) {
+  const int tid = threadIdx.x;
+  const uint32_t c32 = x.c32, U = x.U;
   int64_t lo_d, hi_d;
   param_range(D, c, lo_d, hi_d);
-  // flattened index of parameter l is gofs + l
   const uint32_t gofs = flat_index(D, lo_d, c) - (uint32_t)lo_d;
-  // L1 (MT's bound at l = 0) when MT is part of the bound, else no floor
-  uint32_t B = (A.dff_off & 1u) ? 0u : sumw / c32 + (sumw % c32 != 0u);
-  unsigned long long best = 0ull;
-  // S(l) = sum_w f(w, l) from the accumulators (bp_lb_core.cuh), l-independent
-  // parts in kS, evaluated in wrapping 32-bit arithmetic (exact: S < 2^32):
-  //   MT:   E(l) + kS;   RAD2: A n1 + (B2 - A) n2s - (c - A - B2) n2b + kS;
-  //   CCM1: 2 acc + q kS;   BJ1: sumw - acc
-  uint32_t kS;
-  if (D == kMT) kS = TB + sumw_big + n_half * (c32 / 2u) + n_full * c32;
-  else if (D == kRAD2) kS = n_big * c32 + n_half * (c32 / 2u) + n_full * c32;
-  else if (D == kCCM1) kS = 2u * n_big + n_half + 2u * n_full;
-  else kS = sumw;
-  const uint32_t l0 = (uint32_t)lam0, le = (uint32_t)lam_end;  // parameters < 2^31 here
-
-  if (D == kMT || D == kRAD2) {
-    if (D == kMT && l0 == 0u && tid == 0) best = make_key((int64_t)B, gofs);  // l = 0: L1
-    const uint32_t A3 = c32 / 3u, B2 = c32 / 2u;
-    for (uint32_t l = l0 + (uint32_t)tid; l < le; l += kPrefixNT) {
-      uint32_t Sv;
-      if (D == kMT) {
-        Sv = (uint32_t)T0[min(l, U + 1u)] + kS;
-      } else {
-        const uint32_t y = min(c32 - 2u * l + 1u, U + 1u);
-        const uint32_t n1 = (uint32_t)T0[l], n2s = (uint32_t)T1[y];
-        const uint32_t n2b = n2s - (uint32_t)T0[y];
-        Sv = A3 * n1 + (B2 - A3) * n2s - (c32 - A3 - B2) * n2b + kS;
-      }
-      try_key(Sv, c32, gofs + l, B, best);
-    }
-    return best;
-  }
-
-  // CCM1 / BJ1: the lookups of parameter l fall like X / l.
+  //   CCM1: S = 2 acc + q kS, f = 2q;   BJ1: S = sumw - acc, f = q (l - cm)
+  const uint32_t kS = (D == kCCM1) ? 2u * x.n_big + x.n_half + 2u * x.n_full : x.sumw;
+  const uint32_t le = (uint32_t)lam_end;
   const uint32_t X = (D == kCCM1) ? U : c32;
   const int64_t cta_end = max(lam0, min(lam_end, min((int64_t)(X / kCtaBlocks) + 1, lam0 + kMaxHeavy)));
   const int64_t warp_end = max(cta_end, min(lam_end, (int64_t)(X / kWarpBlocks) + 1));
   const int lane = (int)lane_id(), warp = tid >> 5;
-  // S and f of parameter l with q = floor(c / l) and the accumulator
   auto finish = [&](uint32_t l, uint32_t q, uint32_t acc) {
     uint32_t Sv, f;
     if (D == kCCM1) {
@@ -277,7 +258,7 @@ __device__ unsigned long long prefix_tile_dff(const EvalArgs &A, const InstView 
       Sv = kS - acc;
       f = q * (l - (c32 - q * l));  // q (l - cm) <= c
     }
-    try_key(Sv, f, gofs + l, B, best);
+    try_key(Sv, f, gofs + l, x.B, x.best);
   };
 
   // ---- parameters shared by the whole CTA ---------------------------------------
@@ -293,8 +274,8 @@ __device__ unsigned long long prefix_tile_dff(const EvalArgs &A, const InstView 
       const uint32_t l = (uint32_t)(lam0 + i);
       const uint32_t cm = S.heavy_cm[i];
       if (D == kBJ1 && cm == 0u) continue;  // every BJ1 term is 0
-      const uint32_t part =
-          __reduce_add_sync(0xFFFFFFFFu, block_terms<D>(T0, c32, U, l, cm, (uint32_t)tid, kPrefixNT));
+      const uint32_t part = __reduce_add_sync(
+          0xFFFFFFFFu, block_terms<D, PACKED>(T0, c32, U, l, cm, (uint32_t)tid, kPrefixNT));
       if (lane == 0 && part != 0u) atomicAdd(&S.heavy_acc[i], part);
     }
     __syncthreads();
@@ -325,8 +306,8 @@ __device__ unsigned long long prefix_tile_dff(const EvalArgs &A, const InstView 
         const uint32_t cm = __shfl_sync(0xFFFFFFFFu, mcm, t);
         const bool ok = __shfl_sync(0xFFFFFFFFu, (int)mine_ok, t) != 0;
         if (!ok || (D == kBJ1 && cm == 0u)) continue;
-        const uint32_t part =
-            __reduce_add_sync(0xFFFFFFFFu, block_terms<D>(T0, c32, U, l, cm, (uint32_t)lane, 32u));
+        const uint32_t part = __reduce_add_sync(
+            0xFFFFFFFFu, block_terms<D, PACKED>(T0, c32, U, l, cm, (uint32_t)lane, 32u));
         if (lane == t) mine = part;
       }
       if (mine_ok) finish(ml, mq, mine);
@@ -350,15 +331,154 @@ __device__ unsigned long long prefix_tile_dff(const EvalArgs &A, const InstView 
       }
       uint32_t acc = 0;
       if (D == kCCM1) {
-        acc = block_terms<D>(T0, c32, U, l, 0u, 0u, 1u);
+        acc = block_terms<D, PACKED>(T0, c32, U, l, 0u, 0u, 1u);
       } else {
         const uint32_t cm = c32 - q * l;
-        if (cm != 0u) acc = bj1_blocks(T0, sumw, l, cm, q);
+        if (cm != 0u) acc = bj1_blocks(T0, x.sumw, l, cm, q);
       }
       finish(l, q, acc);
     }
   }
-  return best;
+}
+
+// Builds the table(s) of D (a DFF, or kPrefixU for the merged u group) for
+// instance I -- one pass over the node's base items both accumulates its bin
+// loads and histograms its unpacked items, a second pass histograms the bin
+// loads -- and evaluates parameters [lam0, lam_end) (the u group: all of its
+// members); returns the thread's best key.
+template <int MODE, int D>
+__device__ unsigned long long prefix_tile(const EvalArgs &A, const InstView &I, int64_t lam0,
+                                          int64_t lam_end, int32_t *tab, uint32_t *s_load,
+                                          PrefixShared &S) {
+  const int tid = threadIdx.x;
+  const int64_t c = I.c;
+  const uint32_t c32 = (uint32_t)c;
+  const uint32_t U = (uint32_t)((c - 1) / 2);
+  const int nU = (int)U + 2, nW = (int)c + 2;
+  int32_t *T0 = tab;       // E (MT, u group), N' (CCM1, RAD2), NN (BJ1)
+  int32_t *T1 = tab + nU;  // Ns (RAD2), packed small/big counts (u group)
+  const int nzero = (D == kBJ1) ? nW : ((D == kRAD2 || D == kPrefixU) ? 2 * nU : nU);
+  {
+    int4 *t4 = reinterpret_cast<int4 *>(tab);
+    const int4 z = make_int4(0, 0, 0, 0);
+    for (int i = tid; i < (nzero + 3) / 4; i += kPrefixNT) t4[i] = z;
+  }
+  if (MODE == kSrcNodes)
+    for (int64_t j = tid; j < I.k; j += kPrefixNT) s_load[j] = 0u;
+  if (tid < 8) S.sums[tid] = 0;
+  __syncthreads();
+
+  // ---- histogram the instance's reduced items ------------------------------------
+  uint32_t ls[7] = {0, 0, 0, 0, 0, 0, 0};
+  auto visit = [&](int64_t w) {
+    if (w < 0 || w > c) {
+      S.err = 1;
+      return;
+    }
+    ls[5] += (uint32_t)w;
+    if (D == kBJ1) {
+      atomicAdd(&T0[w], 1);
+      return;
+    }
+    if (w == 0) return;
+    if (w == c) {
+      ls[3]++;
+    } else if (2 * w < c) {
+      ls[0]++;
+      atomicAdd(&T0[w], (D == kMT || D == kPrefixU) ? (int32_t)w : 1);
+      if (D == kRAD2) atomicAdd(&T1[w], 1);
+      if (D == kPrefixU) atomicAdd(reinterpret_cast<uint32_t *>(&T1[w]), 1u);
+    } else if (2 * w > c) {
+      const int64_t u = c - w;
+      ls[1]++;
+      ls[4] += (uint32_t)w;
+      ls[6] += (uint32_t)u;
+      atomicAdd(&T0[u], (D == kMT || D == kPrefixU) ? -(int32_t)u : -1);
+      if (D == kPrefixU) atomicAdd(reinterpret_cast<uint32_t *>(&T1[u]), 1u << 16);
+    } else {
+      ls[2]++;
+    }
+  };
+  if (MODE == kSrcNodes) {
+    for (int64_t i = tid; i < I.n; i += kPrefixNT) {
+      const int32_t a = I.a[i];
+      const int32_t w = I.w[i];
+      if (w < 0 || (int64_t)w > c || a < -1 || (int64_t)a >= I.k) {
+        S.err = 1;
+      } else if (a >= 0) {
+        const uint32_t old = atomicAdd(&s_load[a], (uint32_t)w);
+        if ((int64_t)old + w > c) S.err = 1;
+      } else {
+        visit(w);
+      }
+    }
+    __syncthreads();
+    for (int64_t j = tid; j < I.k; j += kPrefixNT) visit((int64_t)s_load[j]);
+  } else {
+    const int64_t L = stream_len<MODE>(I);
+    for (int64_t q = tid; q < L; q += kPrefixNT) {
+      int64_t w = 0;
+      fetch_item<MODE>(A, I, s_load, q, w);
+      visit(w);
+    }
+  }
+  // every count and sum is below 2^31 on this path: 32-bit warp reductions
+#pragma unroll
+  for (int e = 0; e < 7; ++e) {
+    const uint32_t xs = __reduce_add_sync(0xFFFFFFFFu, ls[e]);
+    if (lane_id() == 0 && xs != 0u) atomicAdd((unsigned long long *)&S.sums[e], (unsigned long long)xs);
+  }
+  __syncthreads();
+  if (D == kBJ1) {
+    suffix_scan<true>(T0, nW, S);
+  } else {
+    suffix_scan<false>(T0, nU, S);
+    if (D == kRAD2) suffix_scan<false>(T1, nU, S);
+    if (D == kPrefixU) packed_count_scan(reinterpret_cast<uint32_t *>(T1), nU, S);
+  }
+  if (S.err) return 0ull;
+
+  // all below 2^31 on this path (prefix_handles); the sums S(l) below 2^32,
+  // evaluated in wrapping 32-bit arithmetic
+  PrefixEval x;
+  x.c32 = c32;
+  x.U = U;
+  x.n_big = (uint32_t)S.sums[1];
+  x.n_half = (uint32_t)S.sums[2];
+  x.n_full = (uint32_t)S.sums[3];
+  x.sumw_big = (uint32_t)S.sums[4];
+  x.sumw = (uint32_t)S.sums[5];
+  x.TB = (uint32_t)S.sums[6];
+  // L1 (MT's bound at l = 0) when MT is part of the bound, else no floor
+  x.B = (A.dff_off & 1u) ? 0u : x.sumw / c32 + (x.sumw % c32 != 0u);
+  x.best = 0ull;
+
+  if (D == kMT) eval_mt(T0, lam0, lam_end, c, x);
+  if (D == kRAD2) eval_rad2<false>(T0, T1, lam0, lam_end, c, x);
+  if (D == kCCM1 || D == kBJ1) eval_harmonic<D, false>(T0, lam0, lam_end, c, x, S);
+  if (D == kPrefixU) {
+    // the members in paper order, so that each thread meets its parameters in
+    // increasing flattened index
+    const int64_t sb = sum_bound<MODE>(I);
+    auto member = [&](int d) {
+      return param_count(d, c) > 0 &&
+             dff_kernel(d, c, sb, A.prefix_on, A.vb2_on, A.dff_off) == kRoutePrefix;
+    };
+    int64_t lo, hi;
+    if (member(kMT)) {
+      param_range(kMT, c, lo, hi);
+      eval_mt(T0, lo, hi + 1, c, x);
+    }
+    if (member(kRAD2)) {
+      param_range(kRAD2, c, lo, hi);
+      eval_rad2<true>(T0, T1, lo, hi + 1, c, x);
+    }
+    if (member(kCCM1)) {
+      param_range(kCCM1, c, lo, hi);
+      eval_harmonic<kCCM1, true>(T1, lo, hi + 1, c, x, S);
+    }
+  }
+  return x.best;
 }
 
 // Persistent kernel over the prefix tile table (instance, DFF in {MT, RAD2,
@@ -379,18 +499,27 @@ __global__ void __launch_bounds__(kPrefixNT, 4) prefix_kernel(EvalArgs A) {
     const InstView I = resolve_instance<MODE>(A, b);
     const int64_t t0 = A.ptile_start ? A.ptile_start[b] : 0;
     const int64_t ntiles = instance_tiles(A, b);
-    // which DFF and lambdas
+    // which DFF (or the merged u group) and lambdas
     int64_t rem = t - t0;
     int d = 0;
     const int64_t sb = sum_bound<MODE>(I);
-    for (d = 0; d < kNumDff; ++d) {
-      if (dff_kernel(d, I.c, sb, A.prefix_on, A.vb2_on, A.dff_off) != kRoutePrefix) continue;
-      const int64_t nt = (param_count(d, I.c) + A.plpt - 1) / A.plpt;
-      if (rem < nt) break;
-      rem -= nt;
+    const bool merged = prefix_u_merged(I.c, sb, A.prefix_on, A.vb2_on, A.dff_off, A.plpt);
+    if (merged) {
+      if (rem == 0) d = kPrefixU;
+      else {
+        d = kBJ1;  // tiles after the u group's one are BJ1's
+        rem -= 1;
+      }
+    } else {
+      for (d = 0; d < kNumDff; ++d) {
+        if (dff_kernel(d, I.c, sb, A.prefix_on, A.vb2_on, A.dff_off) != kRoutePrefix) continue;
+        const int64_t nt = (param_count(d, I.c) + A.plpt - 1) / A.plpt;
+        if (rem < nt) break;
+        rem -= nt;
+      }
     }
-    int64_t lo_d, hi_d;
-    param_range(d, I.c, lo_d, hi_d);
+    int64_t lo_d = 0, hi_d = -1;
+    if (d != kPrefixU) param_range(d, I.c, lo_d, hi_d);
     const int64_t lam0 = lo_d + rem * A.plpt;
     const int64_t lam_end = min(hi_d + 1, lam0 + A.plpt);
 
@@ -401,12 +530,11 @@ __global__ void __launch_bounds__(kPrefixNT, 4) prefix_kernel(EvalArgs A) {
     __syncthreads();
     unsigned long long best = 0ull;
     if (!S.skip) {
-      node_loads<kPrefixNT, MODE>(I, s_load, &S.err);
-      __syncthreads();
-      if (d == kMT) best = prefix_tile_dff<MODE, kMT>(A, I, lam0, lam_end, tab, s_load, S);
-      else if (d == kRAD2) best = prefix_tile_dff<MODE, kRAD2>(A, I, lam0, lam_end, tab, s_load, S);
-      else if (d == kCCM1) best = prefix_tile_dff<MODE, kCCM1>(A, I, lam0, lam_end, tab, s_load, S);
-      else best = prefix_tile_dff<MODE, kBJ1>(A, I, lam0, lam_end, tab, s_load, S);
+      if (d == kPrefixU) best = prefix_tile<MODE, kPrefixU>(A, I, lam0, lam_end, tab, s_load, S);
+      else if (d == kMT) best = prefix_tile<MODE, kMT>(A, I, lam0, lam_end, tab, s_load, S);
+      else if (d == kRAD2) best = prefix_tile<MODE, kRAD2>(A, I, lam0, lam_end, tab, s_load, S);
+      else if (d == kCCM1) best = prefix_tile<MODE, kCCM1>(A, I, lam0, lam_end, tab, s_load, S);
+      else best = prefix_tile<MODE, kBJ1>(A, I, lam0, lam_end, tab, s_load, S);
     }
     __syncthreads();
     fold_and_finalize<kPrefixNT>(A, b, best, S.err != 0, ntiles, I, S.warp_key);

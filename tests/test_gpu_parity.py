@@ -428,3 +428,13 @@ def test_overlap_and_serial_identical(cudalib, orc):
             cudalib.bp_lb_set_overlap(h, 9)
     finally:
         cudalib.bp_lb_destroy(h)
+
+
+def test_prefix_long_stream_unmerged(cudalib, handle, orc):
+    """A stream of 2^15 items or more: the prefix kernel's per-DFF tiles (the
+    merged u-group tile needs 16-bit counts)."""
+    rng = np.random.default_rng(29)
+    inst = [rng.integers(1, 1001, size=40000), rng.integers(1, 501, size=33000),
+            rng.integers(1, 1001, size=300)]
+    rg = I.ragged_from_list(inst, [1000, 1000, 1000])
+    assert_same(run_batch(cudalib, handle, rg), oracle_batch(orc, rg), "long streams")
