@@ -57,7 +57,7 @@ SM_COUNT_NOMINAL = 152
 # launch, divided by 512: traffic grows with the nodes, each node's assignment
 # being read from DRAM once), or None while the kernel has changed since the
 # last capture.
-TRAFFIC_BYTES_PER_NODE = None  # vb2_kernel changed since the last capture
+TRAFFIC_BYTES_PER_NODE = 2182
 
 
 def param_counts(c):
