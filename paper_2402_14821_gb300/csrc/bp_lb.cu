@@ -64,6 +64,11 @@ struct bp_lb {
   int64_t *d_vtile_start = nullptr;  // VB2-kernel tile table
   int32_t prefix_on = 1;             // batched modes: BP_ALGO_PREFIX (default) or DIRECT
   int32_t plain_prefix_on = 1;       // plain modes
+  // global-memory slices for prefix tables too large for shared memory:
+  // kGlobalTableInts int32 per prefix-kernel CTA, allocated on first use
+  int32_t *d_gscratch = nullptr;
+  int64_t gscratch_ctas = 0;
+  bool gscratch_failed = false;
   // batched modes send VB2 (c <= 65535) to the VB2 kernel; the plain path
   // keeps it in the direct kernel (one launch fewer per check)
   int32_t vb2_on = 1;
@@ -182,6 +187,25 @@ int launch_prefix(int mode, unsigned grid, size_t smem, cudaStream_t st, EvalArg
                                       dim3(kPrefixNT), args, smem, st));
 }
 
+// The prefix_on bits for a call whose prefix kernel runs `ctas` CTAs: the
+// global-table bit only when the scratch covers them (allocated on first use;
+// if that fails, tables stay in shared memory).
+int32_t prefix_bits(bp_lb *h, bool on, int64_t ctas) {
+  if (!on) return 0;
+  if (!h->d_gscratch && !h->gscratch_failed) {
+    const int64_t n = (int64_t)h->num_sms * 4;  // the prefix kernel's most resident CTAs
+    if (cudaMalloc(&h->d_gscratch, sizeof(int32_t) * (size_t)kGlobalTableInts * (size_t)n) ==
+        cudaSuccess) {
+      h->gscratch_ctas = n;
+    } else {
+      cudaGetLastError();  // clear the allocation error
+      h->d_gscratch = nullptr;
+      h->gscratch_failed = true;
+    }
+  }
+  return kPrefixShared | ((h->d_gscratch && ctas <= h->gscratch_ctas) ? kPrefixGlobal : 0);
+}
+
 // Dynamic shared memory of the VB2 kernel.
 size_t vb2_smem(int mode, int64_t max_bins) {
   return kVb2ListBytes + (mode == kSrcNodes ? sizeof(uint32_t) * (size_t)max_bins : 0);
@@ -207,7 +231,8 @@ int launch_batch(bp_lb *h, EvalArgs A, size_t smem, cudaStream_t st) {
   A.keys = h->d_keys;
   A.done = h->d_done;
   A.work = h->d_work;
-  A.prefix_on = h->prefix_on;
+  A.prefix_on = prefix_bits(h, h->prefix_on != 0, (int64_t)h->num_sms * 4);
+  A.gscratch = h->d_gscratch;
   A.ptile_start = h->d_ptile_start;
   A.pwork = h->d_work + 1;
   A.plpt = kPrefixLPTBatch;
@@ -234,6 +259,7 @@ int launch_batch(bp_lb *h, EvalArgs A, size_t smem, cudaStream_t st) {
     BP_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pocc, (const void *)prefix_fn(MODE),
                                                            kPrefixNT, ps));
     if (pocc <= 0) return BP_ECUDA;
+    pocc = std::min(pocc, 4);  // the global scratch covers num_sms x 4 CTAs
   }
   // With overlap, the prefix kernel (latency-bound table lookups) and then the
   // generic kernel run on the side stream while the VB2 kernel (bound by
@@ -428,6 +454,7 @@ int bp_lb_destroy(bp_lb_t *h) {
   cudaFree(h->d_vtile_start);
   cudaFree(h->d_keys);
   cudaFree(h->d_done);
+  cudaFree(h->d_gscratch);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   if (h->stream) cudaStreamDestroy(h->stream);
   if (h->side) cudaStreamDestroy(h->side);
@@ -472,11 +499,17 @@ static EvalArgs plain_args(bp_lb *h, int64_t n, int64_t bins, int mode) {
   A.tile_start = nullptr;
   // mode is a plain mode; the sum bound is the stream length times c
   const int64_t sb = (mode == kModePlainNodes ? n + bins : n) * h->capacity;
-  A.prefix_on = h->plain_prefix_on;
   A.vb2_on = 0;
   A.verdict = h->verdict;
   A.dff_off = h->dff_off;
   A.plpt = kPrefixLPTSingle;
+  // global prefix tables when the scratch covers the prefix tiles (one CTA each)
+  A.prefix_on = prefix_bits(h, h->plain_prefix_on != 0, 0);
+  if (A.prefix_on & kPrefixGlobal) {
+    const int64_t pt = route_tiles(kRoutePrefix, h->capacity, A.plpt, sb, A.prefix_on, 0, A.dff_off);
+    if (pt > h->gscratch_ctas) A.prefix_on = kPrefixShared;
+  }
+  A.gscratch = h->d_gscratch;
   A.single_tiles = route_tiles(kRouteDirect, h->capacity, shape_lpt(h->shape[mode]), sb,
                                A.prefix_on, 0, A.dff_off);
   A.single_ptiles = route_tiles(kRoutePrefix, h->capacity, A.plpt, sb, A.prefix_on, 0, A.dff_off);
@@ -830,8 +863,8 @@ int bp_lb_autotune_nodes(bp_lb_t *h, int32_t B, int32_t num_base, const int64_t 
 
 int bp_lb_dff_route(int32_t d, int64_t c, int64_t stream_len, int32_t algo) {
   if (d < 0 || d >= kNumDff || c < 1 || c > kMaxCapacity || stream_len < 0) return -1;
-  return prefix_handles(d, c, stream_len * c, algo == BP_ALGO_PREFIX) ? BP_ALGO_PREFIX
-                                                                       : BP_ALGO_DIRECT;
+  const int32_t on = algo == BP_ALGO_PREFIX ? (kPrefixShared | kPrefixGlobal) : 0;
+  return prefix_handles(d, c, stream_len * c, on) ? BP_ALGO_PREFIX : BP_ALGO_DIRECT;
 }
 
 int64_t bp_lb_param_count(int32_t d, int64_t c, int64_t *lo, int64_t *hi) {

@@ -62,7 +62,7 @@ struct EvalArgs {
   unsigned int *done;         // [B] finished-tile counters, zero between calls
   unsigned long long *work;   // [1] next tile (persistent mode), nullptr otherwise
   uint32_t one;               // always 1 (see add_if_ge in bp_lb_eval.cuh)
-  int32_t prefix_on;          // route MT/RAD2/CCM1/BJ1 to the prefix-count kernel where they fit
+  int32_t prefix_on;          // kPrefixShared | kPrefixGlobal bits (0: no prefix-count kernel)
   const int64_t *ptile_start; // [B+1] prefix-kernel tile table, or nullptr (single instance)
   int64_t single_ptiles;
   unsigned long long *pwork;  // [1] next prefix tile (persistent mode)
@@ -74,6 +74,7 @@ struct EvalArgs {
   unsigned long long *vwork;  // [1] next VB2 tile (persistent mode)
   int32_t verdict;            // verdict-only mode (early exit, exact feasibility)
   uint32_t dff_off;           // bit d set: DFF d is left out of the bound (default 0: all six)
+  int32_t *gscratch;          // prefix tables in global memory: kGlobalTableInts per CTA
 };
 
 // Shared-memory budget of the prefix-count tables (bytes; 48 KB lets four
@@ -98,13 +99,29 @@ BPLB_HD int64_t prefix_table_bytes(int d, int64_t c) {
   }
 }
 
-// Whether the prefix-count kernel evaluates DFF d of an instance with
-// capacity c whose reduced sizes sum to at most sum_bound (its tables must fit
-// in shared memory and its sums in 32 bits); otherwise the direct kernel does.
-BPLB_HD bool prefix_handles(int d, int64_t c, int64_t sum_bound, int32_t on) {
-  if (!on || sum_bound >= (int64_t(1) << 31)) return false;
+// prefix_on bits: the prefix-count kernel is on (its tables in shared
+// memory where they fit), and its tables may also live in a global-memory
+// scratch of kGlobalTableInts int32 per CTA (L2-resident; for capacities up
+// to about 2^20).
+constexpr int32_t kPrefixShared = 1;
+constexpr int32_t kPrefixGlobal = 2;
+constexpr int64_t kGlobalTableInts = int64_t(1) << 20;
+
+// Where the prefix-count kernel keeps the tables of DFF d of an instance with
+// capacity c whose reduced sizes sum to at most sum_bound: 0 nowhere (the
+// direct kernels evaluate it), 1 shared memory, 2 the global scratch.  The
+// sums must fit 32 bits.
+BPLB_HD int prefix_home(int d, int64_t c, int64_t sum_bound, int32_t on) {
+  if (!(on & kPrefixShared) || sum_bound >= (int64_t(1) << 31)) return 0;
   const int64_t bytes = prefix_table_bytes(d, c);
-  return bytes > 0 && bytes <= kPrefixSmemBytes;
+  if (bytes == 0) return 0;
+  if (bytes <= kPrefixSmemBytes) return 1;
+  if ((on & kPrefixGlobal) && bytes <= 4 * kGlobalTableInts) return 2;
+  return 0;
+}
+
+BPLB_HD bool prefix_handles(int d, int64_t c, int64_t sum_bound, int32_t on) {
+  return prefix_home(d, c, sum_bound, on) != 0;
 }
 
 // Parameters per tile of the VB2 kernel.
@@ -123,25 +140,45 @@ BPLB_HD int dff_kernel(int d, int64_t c, int64_t sum_bound, int32_t prefix_on, i
   return kRouteDirect;
 }
 
+// Where the u group's tables (E plus packed counts, 8 bytes per u) live: 1
+// shared memory, 2 the global scratch, 0 neither.
+BPLB_HD int prefix_u_home(int64_t c, int32_t on) {
+  const int64_t bytes = 8 * ((c - 1) / 2 + 2);
+  if (bytes <= kPrefixSmemBytes) return 1;
+  if ((on & kPrefixGlobal) && bytes <= 4 * kGlobalTableInts) return 2;
+  return 0;
+}
+
 // MT, RAD2 and CCM1 share one prefix-kernel tile per instance (the u group:
 // one pass over the items builds E and a table of packed small/big counts)
-// when at least two of them go to the prefix kernel, each of those fits one
-// tile of lpt parameters, the two u-domain tables fit the budget, and the
-// counts fit 16 bits (stream length below 2^15; sum_bound = stream length c).
+// when at least two of them go to the prefix kernel, the two u-domain tables
+// fit (shared memory, each member then within one tile of lpt parameters; or
+// the global scratch), and the counts fit 16 bits (stream length below 2^15;
+// sum_bound = stream length c).
 BPLB_HD bool prefix_u_merged(int64_t c, int64_t sum_bound, int32_t prefix_on, int32_t vb2_on,
                              uint32_t dff_off, int64_t lpt) {
-  if (!prefix_on || sum_bound / c >= (int64_t(1) << 15)) return false;
-  if (8 * ((c - 1) / 2 + 2) > kPrefixSmemBytes) return false;
+  if (!(prefix_on & kPrefixShared) || sum_bound / c >= (int64_t(1) << 15)) return false;
+  const int home = prefix_u_home(c, prefix_on);
+  if (home == 0) return false;
   const int ds[3] = {kMT, kRAD2, kCCM1};
   int members = 0;
   for (int i = 0; i < 3; ++i) {
     const int64_t pc = param_count(ds[i], c);
     if (pc == 0 || dff_kernel(ds[i], c, sum_bound, prefix_on, vb2_on, dff_off) != kRoutePrefix)
       continue;
-    if (pc > lpt) return false;
+    if (home == 1 && pc > lpt) return false;
     ++members;
   }
   return members >= 2;
+}
+
+// Prefix-kernel tiles of DFF d (routed there): one when its tables are in the
+// global scratch (built once per tile, so the tile takes the whole range),
+// else ceil(count / lpt).
+BPLB_HD int64_t prefix_dff_tiles(int d, int64_t c, int64_t sum_bound, int32_t on, int64_t lpt) {
+  const int64_t pc = param_count(d, c);
+  if (pc == 0) return 0;
+  return prefix_home(d, c, sum_bound, on) == 2 ? 1 : (pc + lpt - 1) / lpt;
 }
 
 // Tiles of one kernel for an instance: lpt parameters each, DFFs in paper
@@ -153,8 +190,9 @@ BPLB_HD int64_t route_tiles(int route, int64_t c, int64_t lpt, int64_t sum_bound
   int64_t t = merged ? 1 : 0;
   for (int d = 0; d < kNumDff; ++d) {
     if (merged && d != kBJ1) continue;
-    if (dff_kernel(d, c, sum_bound, prefix_on, vb2_on, dff_off) == route)
-      t += (param_count(d, c) + lpt - 1) / lpt;
+    if (dff_kernel(d, c, sum_bound, prefix_on, vb2_on, dff_off) != route) continue;
+    t += route == kRoutePrefix ? prefix_dff_tiles(d, c, sum_bound, prefix_on, lpt)
+                               : (param_count(d, c) + lpt - 1) / lpt;
   }
   return t;
 }

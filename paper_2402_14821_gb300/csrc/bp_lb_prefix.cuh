@@ -347,7 +347,8 @@ __device__ void eval_harmonic(const int32_t *T0, int64_t lam0, int64_t lam_end, 
 // loads -- and evaluates parameters [lam0, lam_end) (the u group: all of its
 // members); returns the thread's best key.
 template <int MODE, int D>
-__device__ unsigned long long prefix_tile(const EvalArgs &A, const InstView &I, int64_t lam0,
+__device__ __forceinline__ unsigned long long prefix_tile(const EvalArgs &A, const InstView &I,
+                                                          int64_t lam0,
                                           int64_t lam_end, int32_t *tab, uint32_t *s_load,
                                           PrefixShared &S) {
   const int tid = threadIdx.x;
@@ -482,13 +483,15 @@ __device__ unsigned long long prefix_tile(const EvalArgs &A, const InstView &I, 
 }
 
 // Persistent kernel over the prefix tile table (instance, DFF in {MT, RAD2,
-// CCM1, BJ1} routed here by prefix_handles, A.plpt consecutive lambdas).
+// CCM1, BJ1} routed here by prefix_handles or the merged u group, A.plpt
+// consecutive lambdas -- all of them when the tables are in the global
+// scratch).
 template <int MODE>
 __global__ void __launch_bounds__(kPrefixNT, 4) prefix_kernel(EvalArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ PrefixShared S;
   __shared__ TileCursor cur;
-  int32_t *tab = reinterpret_cast<int32_t *>(smem_raw);
+  int32_t *stab = reinterpret_cast<int32_t *>(smem_raw);
   uint32_t *s_load = reinterpret_cast<uint32_t *>(smem_raw + kPrefixSmemBytes);
 
   const int64_t total = A.ptile_start ? A.ptile_start[A.B] : A.single_ptiles;
@@ -499,7 +502,8 @@ __global__ void __launch_bounds__(kPrefixNT, 4) prefix_kernel(EvalArgs A) {
     const InstView I = resolve_instance<MODE>(A, b);
     const int64_t t0 = A.ptile_start ? A.ptile_start[b] : 0;
     const int64_t ntiles = instance_tiles(A, b);
-    // which DFF (or the merged u group) and lambdas
+    // which DFF (or the merged u group) and lambdas; tables in shared memory
+    // or in this CTA's slice of the global scratch
     int64_t rem = t - t0;
     int d = 0;
     const int64_t sb = sum_bound<MODE>(I);
@@ -513,15 +517,19 @@ __global__ void __launch_bounds__(kPrefixNT, 4) prefix_kernel(EvalArgs A) {
     } else {
       for (d = 0; d < kNumDff; ++d) {
         if (dff_kernel(d, I.c, sb, A.prefix_on, A.vb2_on, A.dff_off) != kRoutePrefix) continue;
-        const int64_t nt = (param_count(d, I.c) + A.plpt - 1) / A.plpt;
+        const int64_t nt = prefix_dff_tiles(d, I.c, sb, A.prefix_on, A.plpt);
         if (rem < nt) break;
         rem -= nt;
       }
     }
+    const int home = (d == kPrefixU) ? prefix_u_home(I.c, A.prefix_on)
+                                     : prefix_home(d, I.c, sb, A.prefix_on);
+    int32_t *gtab = A.gscratch + (size_t)blockIdx.x * (size_t)kGlobalTableInts;
     int64_t lo_d = 0, hi_d = -1;
     if (d != kPrefixU) param_range(d, I.c, lo_d, hi_d);
-    const int64_t lam0 = lo_d + rem * A.plpt;
-    const int64_t lam_end = min(hi_d + 1, lam0 + A.plpt);
+    const int64_t lpt = (home == 2) ? hi_d - lo_d + 1 : A.plpt;  // global tables: one tile
+    const int64_t lam0 = lo_d + rem * lpt;
+    const int64_t lam_end = min(hi_d + 1, lam0 + lpt);
 
     if (threadIdx.x == 0) {
       S.err = 0;
@@ -529,12 +537,20 @@ __global__ void __launch_bounds__(kPrefixNT, 4) prefix_kernel(EvalArgs A) {
     }
     __syncthreads();
     unsigned long long best = 0ull;
-    if (!S.skip) {
-      if (d == kPrefixU) best = prefix_tile<MODE, kPrefixU>(A, I, lam0, lam_end, tab, s_load, S);
-      else if (d == kMT) best = prefix_tile<MODE, kMT>(A, I, lam0, lam_end, tab, s_load, S);
-      else if (d == kRAD2) best = prefix_tile<MODE, kRAD2>(A, I, lam0, lam_end, tab, s_load, S);
-      else if (d == kCCM1) best = prefix_tile<MODE, kCCM1>(A, I, lam0, lam_end, tab, s_load, S);
-      else best = prefix_tile<MODE, kBJ1>(A, I, lam0, lam_end, tab, s_load, S);
+    // one instantiation per table space, so that shared-memory tables are
+    // accessed with shared-memory instructions
+    if (!S.skip && home != 2) {
+      if (d == kPrefixU) best = prefix_tile<MODE, kPrefixU>(A, I, lam0, lam_end, stab, s_load, S);
+      else if (d == kMT) best = prefix_tile<MODE, kMT>(A, I, lam0, lam_end, stab, s_load, S);
+      else if (d == kRAD2) best = prefix_tile<MODE, kRAD2>(A, I, lam0, lam_end, stab, s_load, S);
+      else if (d == kCCM1) best = prefix_tile<MODE, kCCM1>(A, I, lam0, lam_end, stab, s_load, S);
+      else best = prefix_tile<MODE, kBJ1>(A, I, lam0, lam_end, stab, s_load, S);
+    } else if (!S.skip) {
+      if (d == kPrefixU) best = prefix_tile<MODE, kPrefixU>(A, I, lam0, lam_end, gtab, s_load, S);
+      else if (d == kMT) best = prefix_tile<MODE, kMT>(A, I, lam0, lam_end, gtab, s_load, S);
+      else if (d == kRAD2) best = prefix_tile<MODE, kRAD2>(A, I, lam0, lam_end, gtab, s_load, S);
+      else if (d == kCCM1) best = prefix_tile<MODE, kCCM1>(A, I, lam0, lam_end, gtab, s_load, S);
+      else best = prefix_tile<MODE, kBJ1>(A, I, lam0, lam_end, gtab, s_load, S);
     }
     __syncthreads();
     fold_and_finalize<kPrefixNT>(A, b, best, S.err != 0, ntiles, I, S.warp_key);
