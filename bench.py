@@ -52,12 +52,18 @@ def ops_per_eval(d, c):
             4: 2.5 if c <= 65535 else 5,
             5: 5 if c <= 65535 else 6}[d]
 SM_COUNT_NOMINAL = 152
-# DRAM bytes (read + write) per search node of one vb2_kernel launch, from one
-# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of a 512-node
-# launch, divided by 512: traffic grows with the nodes, each node's assignment
+# DRAM bytes (read + write) per search node of one launch of each kernel, from
+# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of a 512-node
+# launch, divided by 512: traffic grows with the nodes, each node's inputs
 # being read from DRAM once), or None while the kernel has changed since the
 # last capture.
-TRAFFIC_BYTES_PER_NODE = 2182
+TRAFFIC_BYTES_PER_NODE = {"prefix": None, "vb2": None, "direct": None}
+
+# Prefix-count kernel: its algorithmic work is shared-memory table traffic, in
+# 32-bit words -- zeroing, histogram updates, three accesses per entry and
+# scan, and the lookups of every parameter it does not prune (csrc/
+# bp_lb_prefix.cuh) -- against one 32-lane word access per SM per clock.
+PREFIX_CTA_BLOCKS, PREFIX_WARP_BLOCKS, PREFIX_MAX_HEAVY = 1024, 32, 256
 
 
 def param_counts(c):
@@ -74,6 +80,57 @@ def reduced_sizes(nd):
     return r
 
 
+def prefix_smem_words(nd, prune=True):
+    """Shared-memory words of one prefix-kernel launch on a search-node batch
+    with every node at capacity c <= 12286 (tables in shared memory, u group
+    merged, FS1 on BJ1's tile, one tile each), pruning as in the kernel
+    (against L1: prune_bj1, prune_ccm1)."""
+    total = 0
+    cache = {}
+    for j in range(nd.count):
+        w, a, c, k = nd.node(j)
+        w = np.asarray(w, dtype=np.int64)
+        a = np.asarray(a)
+        loads = np.bincount(a[a >= 0], weights=w[a >= 0], minlength=k).astype(np.int64)
+        red = np.concatenate([w[a < 0], loads])
+        n_as = int(np.sum(a >= 0))
+        U = (c - 1) // 2
+        nU, nW = U + 2, c + 2
+        small = red[(red > 0) & (2 * red < c)]
+        big = red[(2 * red > c) & (red < c)]
+        nh, nf, nb = int(np.sum(2 * red == c)), int(np.sum(red == c)), len(big)
+        sumw = int(red.sum())
+        L1 = -(-sumw // c)
+        sws, sub = int(small.sum()), int((c - big).sum())
+        kS = 2 * nb + nh + 2 * nf
+        key = (c, sumw)
+        if key not in cache:
+            lam = np.arange(1, c + 1, dtype=np.int64)
+            q, cm = c // lam, c % lam
+            keep = (cm > 0) & ~(prune & (L1 * (c - cm) >= sumw))
+            heavy = lam < max(min(c // PREFIX_CTA_BLOCKS + 1, 1 + PREFIX_MAX_HEAVY),
+                              c // PREFIX_WARP_BLOCKS + 1)
+            bj1 = np.where(heavy, 2 * ((c - 1) // lam + 1), 2 * q)
+            lp = np.arange(2, 102)
+            fs1 = 2 * int(lp.sum()) + 2 * int(sum(np.gcd(c, lp)))
+            cache[key] = int(bj1[keep].sum()) + fs1
+        # node loads, once per tile: zero k, one atomic per packed item, read k
+        loads_words = 2 * (k + n_as + k)
+        # u group: E and packed counts (zero, 2 updates per small or big item,
+        # 2 scans), MT 1 lookup per parameter, RAD2 3, CCM1 floor(U / l)
+        lam = np.arange(1, c // 2 + 1, dtype=np.int64)
+        q = c // lam
+        ccm1_keep = ~(prune & (2 * sws - 2 * sub + 2 * nb * (lam - 1) + q * lam * kS
+                               <= 2 * q * lam * L1))
+        ccm1 = int((U // lam)[ccm1_keep].sum())
+        pc = param_counts(c)
+        u_words = 2 * nU + 2 * (len(small) + nb) + 6 * nU + pc[0] + 3 * pc[1] + ccm1
+        # w group: NN (zero, one update per reduced item, scanned twice), FS1, BJ1
+        w_words = nW + len(red) + 3 * nW + cache[key]
+        total += loads_words + u_words + w_words
+    return total
+
+
 VB2_FIXED_CAP = 65535
 
 
@@ -88,10 +145,11 @@ def kernel_of(d, c, stream_len, algo=1):
 
 
 def algorithmic_work(nd, algo=1):
-    """(item-parameter evals of the whole check, {kernel: integer ops}) of one
-    batch: the VB2 kernel and the generic direct kernel evaluate every (item,
-    parameter) pair of the DFFs routed to them; MT, RAD2, CCM1 and BJ1 go to
-    the prefix-count kernel where their tables fit."""
+    """(item-parameter pairs of the whole check, {kernel: integer ops}) of one
+    batch: the generic direct kernel evaluates every (item, parameter) pair of
+    the DFFs other than VB2 routed to it; MT, RAD2, FS1, CCM1 and BJ1 go to the
+    prefix-count kernel where their tables fit.  VB2's pairs are pruned on the
+    device, which counts the ones it evaluates (bp_lb_kernel_work)."""
     r = reduced_sizes(nd)
     evals = 0
     ops = {"vb2": 0, "direct": 0, "prefix": 0}
@@ -103,7 +161,7 @@ def algorithmic_work(nd, algo=1):
         for d in range(6):
             evals += int(r[j]) * cnt[d]
             k = kernel_of(d, c, L, algo)
-            if k != "prefix":
+            if k != "prefix" and d != 4:
                 ops[k] += r[j] * cnt[d] * ops_per_eval(d, c)
     return evals, ops
 
@@ -329,6 +387,7 @@ def main():
         barrier()
     step_ms = np.array([e0.elapsed_time(e1) for e0, e1 in ev])
     ms_prefix, ms_vb2, ms_direct, n_calls = B.bp_lb_kernel_times(h)
+    kwork = B.bp_lb_kernel_work(h)        # VB2 pairs and parameters actually evaluated
     B.bp_lb_set_kernel_timing(h, False)
     t_direct = ms_direct / max(1, n_calls)
     t_vb2 = ms_vb2 / max(1, n_calls)
@@ -426,11 +485,31 @@ def main():
     sm_mhz_max = float(peaks.get("sm_max_mhz", 2070.0))
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     peak_ops = sms * 4 * 32 * sm_mhz_max * 1e6        # one warp instruction / clk / SMSP
-    # the dominant item-by-item kernel: the VB2 kernel unless the generic one
-    # took longer
-    dom = "vb2" if t_vb2 >= t_direct else "direct"
-    t_dom = t_vb2 if dom == "vb2" else t_direct
-    achieved = ops[dom] / (t_dom / 1e3)
+    peak_words = sms * 32 * sm_mhz_max * 1e6          # one 32-lane shared access / clk / SM
+    calls = max(1, n_calls)
+    # work per step actually done by each kernel: the VB2 pairs the kernels
+    # counted (pruning skips the rest), the generic kernel's other DFFs, the
+    # prefix kernel's shared-memory words (host model of the same pruning)
+    vb2_pairs = kwork[0] / calls
+    work = {"vb2": vb2_pairs * ops_per_eval(4, CAP),
+            "direct": ops["direct"] + kwork[1] / calls * ops_per_eval(4, CAP),
+            "prefix": float(prefix_smem_words(nd))}
+    tms = {"vb2": t_vb2, "direct": t_direct, "prefix": t_prefix}
+    peak = {"vb2": peak_ops, "direct": peak_ops, "prefix": peak_words}
+    frac = {kk: (work[kk] / (tms[kk] / 1e3) / peak[kk] if tms[kk] > 0 and work[kk] > 0 else None)
+            for kk in tms}
+    dom = max(tms, key=lambda kk: tms[kk])           # the kernel that takes longest
+    achieved = work[dom] / (tms[dom] / 1e3)
+    kernel_name = {"vb2": "vb2_kernel (VB2 item by item, fixed-point quotients, pruned)",
+                   "direct": "eval_kernel (generic direct evaluation)",
+                   "prefix": "prefix_kernel (MT, RAD2, FS1, CCM1, BJ1 from shared-memory "
+                             "prefix tables, pruned against L1)"}[dom]
+    basis = ({"prefix": f"{sms} SMs x 32 lanes x {sm_mhz_max:.0f} MHz (one 32-bit shared-memory "
+                        "word per lane per clock: 128 B/clk/SM); work = shared-memory words of "
+                        "table building and lookups"}
+             .get(dom, f"{sms} SMs x 4 SMSP x 32 lanes x {sm_mhz_max:.0f} MHz (integer issue, "
+                       "one warp instruction per clock per SMSP); work = integer ops of the "
+                       "(item, parameter) pairs evaluated"))
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -451,23 +530,21 @@ def main():
                     "p99_ms": float(np.percentile(v_ms, 99)),
                     "mode": "verdict only (Alg. 2 early exit; VB2 parameters whose upper "
                             "bound is <= k skipped); same verdicts as the full maximum"},
+        "pruning": {"vb2_params_evaluated": kwork[2] / calls, "vb2_params_pruned": kwork[3] / calls,
+                    "vb2_pairs_evaluated": vb2_pairs,
+                    "note": "exact: results identical with pruning off (bp_lb_set_pruning)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9,
-                     "unit": "Gop/s", "frac": achieved / peak_ops,
-                     "traffic": (TRAFFIC_BYTES_PER_NODE * NODES
-                                 if TRAFFIC_BYTES_PER_NODE is not None and dom == "vb2"
-                                 else None),
-                     "peak_basis": f"{sms} SMs x 4 SMSP x 32 lanes x {sm_mhz_max:.0f} MHz "
-                                   "(integer issue, one warp instruction per clock per SMSP)",
-                     "kernel": ("vb2_kernel (VB2 item by item, fixed-point quotients)"
-                                if dom == "vb2" else
-                                "eval_kernel (generic direct evaluation: FS1, VB2 here)")
-                               + ", its own CUDA-event time per launch",
-                     "vb2_kernel_ms": t_vb2, "direct_kernel_ms": t_direct,
-                     "prefix_kernel_ms": t_prefix,
-                     "direct_kernel_frac": (ops["direct"] / (t_direct / 1e3) / peak_ops
-                                            if t_direct > 0 else None)},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak[dom] / 1e9,
+                     "unit": "Gword/s" if dom == "prefix" else "Gop/s", "frac": frac[dom],
+                     "traffic": (TRAFFIC_BYTES_PER_NODE[dom] * NODES
+                                 if TRAFFIC_BYTES_PER_NODE[dom] is not None else None),
+                     "peak_basis": basis,
+                     "kernel": kernel_name + ", its own CUDA-event time per launch",
+                     "prefix_kernel_ms": t_prefix, "vb2_kernel_ms": t_vb2,
+                     "direct_kernel_ms": t_direct,
+                     "prefix_kernel_frac": frac["prefix"], "vb2_kernel_frac": frac["vb2"],
+                     "direct_kernel_frac": frac["direct"]},
         "launch_shape": {"chosen": shape, "nt_t_g_minb": list(B.bp_lb_launch_shape_info(shape)),
                          "autotune_ms": [round(x, 4) for x in shape_ms]},
         "gpu_launches": 4 * args.steps,  # plan, prefix, VB2 and generic kernels per step
@@ -509,8 +586,8 @@ def _peak_ops():
 
 
 def ragged_work(rg, algo=1):
-    """(evals, item-by-item integer ops of the VB2 and direct kernels) of a
-    ragged batch of reduced instances."""
+    """(evals, item-by-item integer ops of the direct kernel but VB2's, which
+    the device counts) of a ragged batch of reduced instances."""
     evals = ops = 0
     for b in range(rg.count):
         c = int(rg.capacity[b])
@@ -518,7 +595,7 @@ def ragged_work(rg, algo=1):
         cnt = param_counts(c)
         evals += r * sum(cnt)
         ops += r * sum(cnt[d] * ops_per_eval(d, c) for d in range(6)
-                       if kernel_of(d, c, r, algo) != "prefix")
+                       if d != 4 and kernel_of(d, c, r, algo) != "prefix")
     return evals, ops
 
 
@@ -642,9 +719,11 @@ def run_sweep(args):
                         B.bp_lb_kernel_times(h)
                         ms = _time_steps(step, steps, flush, stream)
                         kp, kv, kd, kn = B.bp_lb_kernel_times(h)
+                        kw = B.bp_lb_kernel_work(h)
                         B.bp_lb_set_kernel_timing(h, False)
                         tm = float(ms.mean())
                         td = (kv + kd) / max(1, kn)
+                        ops += (kw[0] + kw[1]) / max(1, kn) * ops_per_eval(4, c)
                         out["results"].append({
                             "c": c, "family": fam, "dtype": np.dtype(dt).name, "instances": 64,
                             "n": 10_000, "ms_per_batch": tm, "checks_per_s": 64 / (tm / 1e3),
@@ -710,7 +789,7 @@ def run_sweep(args):
         else:  # ragged
             nd = I.ragged_nodes(seed=3)
             evals, kops = algorithmic_work(nd)
-            ops = kops["vb2"] + kops["direct"]
+            ops = kops["direct"]
             t_in = dict(base_offsets=_dev(nd.base.offsets, torch.int64),
                         base_sizes=_dev(nd.base.sizes, torch.int32),
                         base_capacity=_dev(nd.base.capacity, torch.int64),
@@ -745,7 +824,10 @@ def run_sweep(args):
             B.bp_lb_kernel_times(h)
             ms_direct = _time_steps(direct, steps, flush, stream)
             kp, kv, kd, kn = B.bp_lb_kernel_times(h)
+            kw = B.bp_lb_kernel_work(h)
             B.bp_lb_set_kernel_timing(h, False)
+            # VB2 on its kernel up to c = 65535, on the generic one above
+            ops += (kw[0] * ops_per_eval(4, 9999) + kw[1] * ops_per_eval(4, 100_000)) / max(1, kn)
             td = (kv + kd) / max(1, kn)
             tm = float(ms_graph.mean())
             out["results"].append({

@@ -263,9 +263,9 @@ int bp_lb_get_algorithm(bp_lb_t *h);
  * exit (Sec. 3.1, Alg. 2): once any bound of an instance exceeds k, its
  * remaining tiles stop (a flag -- the instance's result slot -- read by every
  * kernel when it starts a tile and between parameter groups), and on the VB2
- * path a warp skips its parameters when an upper bound on each of their
- * bounds, from the instance's sums alone, is <= k (such a parameter cannot
- * change the verdict).  The cheap DFFs run first (the prefix-count kernel,
+ * path a parameter is skipped when an upper bound on its bound, from the
+ * instance's sums alone, is <= k (it cannot change the verdict; this holds
+ * with VB2 pruning off too).  The cheap DFFs run first (the prefix-count kernel,
  * then VB2, then the rest), so a decided instance skips the expensive ones.
  * In this mode out_feasible is exact; out_bound / out_argmax hold a genuine
  * bound of the instance and the (DFF, lambda) that gives it: one above k
@@ -278,6 +278,23 @@ int bp_lb_set_result_mode(bp_lb_t *h, int32_t mode);
 
 /* The handle's result mode, or -1 for a NULL handle. */
 int bp_lb_get_result_mode(bp_lb_t *h);
+
+/* ---- VB2 pruning ------------------------------------------------------------ */
+
+/* On (1, the default): in both result modes a VB2 parameter is skipped when
+ * an upper bound on its bound, from the instance's sums alone (sum of
+ * ceil(x) < sum of (x + 1) over the small items, >= x over the big ones),
+ * shows it cannot change the result: in full mode when that upper bound is
+ * below the instance's best bound so far -- or equal to it, with the best one
+ * earlier in (DFF, lambda) order -- read from the instance's result slot
+ * (it only grows, and the prefix-count kernel has filled it before VB2
+ * runs); in verdict mode when it is <= k.  Results are identical with
+ * pruning off (0); only the work differs.  Errors: BP_EINVAL (NULL handle),
+ * BP_ERANGE (not 0 or 1). */
+int bp_lb_set_pruning(bp_lb_t *h, int32_t on);
+
+/* The handle's pruning switch, or -1 for a NULL handle. */
+int bp_lb_get_pruning(bp_lb_t *h);
 
 /* ---- L2, the comparator ---------------------------------------------------- */
 
@@ -340,6 +357,14 @@ int bp_lb_set_overlap(bp_lb_t *h, int32_t prefix_ctas_per_sm);
 int bp_lb_set_kernel_timing(bp_lb_t *h, int32_t on);
 int bp_lb_kernel_times(bp_lb_t *h, double *ms_prefix, double *ms_vb2, double *ms_direct,
                        int64_t *calls);
+
+/* Measurement aid: work counted by the batched calls made with timing on,
+ * since the previous query (which resets the counters; it synchronizes the
+ * device): out4[0] VB2 (item, parameter) pairs evaluated by the VB2 kernel,
+ * out4[1] VB2 pairs evaluated by the generic kernel, out4[2] VB2 parameters
+ * evaluated, out4[3] VB2 parameters pruned (bp_lb_set_pruning).
+ * Errors: BP_EINVAL (NULL pointer), BP_ECUDA. */
+int bp_lb_kernel_work(bp_lb_t *h, int64_t *out4);
 
 /* ---- launch shapes and autotuning ---------------------------------------- */
 

@@ -78,6 +78,9 @@ def _bind(lib):
                                                      P(_c_i32)]),
         "bp_lb_set_algorithm": (ctypes.c_int, [_vp, _c_i32]),
         "bp_lb_set_result_mode": (ctypes.c_int, [_vp, _c_i32]),
+        "bp_lb_set_pruning": (ctypes.c_int, [_vp, _c_i32]),
+        "bp_lb_kernel_work": (ctypes.c_int, [_vp, _vp]),
+        "bp_lb_get_pruning": (ctypes.c_int, [_vp]),
         "bp_lb_set_dff_mask": (ctypes.c_int, [_vp, _c_i32]),
         "bp_lb_set_overlap": (ctypes.c_int, [_vp, _c_i32]),
         "bp_lb_l2_batch": (ctypes.c_int, [_vp, _c_i32, _vp, _vp, _vp, _vp, _vp]),
@@ -124,7 +127,8 @@ EXPORTED = ("bp_lb_strerror", "bp_lb_create", "bp_lb_destroy", "bp_lb_reserve", 
             "bp_serve_poll", "bp_serve_stats", "bp_lb_set_algorithm", "bp_lb_get_algorithm",
             "bp_lb_set_kernel_timing", "bp_lb_kernel_times", "bp_lb_dff_route",
             "bp_lb_set_result_mode", "bp_lb_get_result_mode", "bp_lb_set_dff_mask",
-            "bp_lb_get_dff_mask", "bp_lb_l2_batch", "bp_lb_set_overlap")
+            "bp_lb_get_dff_mask", "bp_lb_l2_batch", "bp_lb_set_overlap", "bp_lb_set_pruning",
+            "bp_lb_get_pruning", "bp_lb_kernel_work")
 
 ALGO_DIRECT, ALGO_PREFIX = 0, 1
 RESULT_FULL, RESULT_VERDICT = 0, 1
@@ -323,6 +327,24 @@ def bp_lb_set_result_mode(h, mode: int):
 
 def bp_lb_get_result_mode(h) -> int:
     return lib().bp_lb_get_result_mode(h)
+
+
+def bp_lb_kernel_work(h):
+    """(VB2 pairs by the VB2 kernel, VB2 pairs by the generic kernel, VB2
+    parameters evaluated, VB2 parameters pruned) since the last query; counted
+    while kernel timing is on."""
+    out = np.zeros(4, dtype=np.int64)
+    _check(lib().bp_lb_kernel_work(h, out.ctypes.data), "bp_lb_kernel_work")
+    return tuple(int(x) for x in out)
+
+
+def bp_lb_set_pruning(h, on: bool):
+    """VB2 pruning on (default) or off; results are identical either way."""
+    _check(lib().bp_lb_set_pruning(h, int(bool(on))), "bp_lb_set_pruning")
+
+
+def bp_lb_get_pruning(h) -> int:
+    return lib().bp_lb_get_pruning(h)
 
 
 def bp_lb_set_overlap(h, prefix_ctas_per_sm: int):

@@ -73,6 +73,7 @@ struct bp_lb {
   // keeps it in the direct kernel (one launch fewer per check)
   int32_t vb2_on = 1;
   int32_t verdict = 0;  // BP_RESULT_FULL (0) or BP_RESULT_VERDICT (1)
+  int32_t prune = 1;    // skip VB2 parameters that provably cannot win (exact)
   // With prefix_ctas > 0, batched calls run the prefix-count kernel (then the
   // generic kernel) on a high-priority side stream beside the VB2 kernel:
   // prefix_ctas CTAs per SM for the prefix kernel, the rest of each SM for
@@ -84,11 +85,13 @@ struct bp_lb {
   uint32_t dff_off = 0;  // DFFs left out of the bound (bit d), default none
   // optional per-kernel timing of batched calls (events around each launch)
   bool timing = false;
+  unsigned long long *d_work_count = nullptr;  // 4 counters (EvalArgs::work_count)
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::array<cudaEvent_t, 6>> ev_pending;
   size_t ev_next = 0;
   unsigned long long *d_keys = nullptr;
   unsigned int *d_done = nullptr;
+  long long *d_isums = nullptr;  // [cap_batch][8] instance sums (EvalArgs::isums)
   unsigned long long *d_work = nullptr;
   // launch shape (index into kShapes) per mode: batched ragged i32, ragged
   // i64, nodes, then the plain ragged and plain node paths; occupancy cache of
@@ -152,6 +155,8 @@ int grow_batch(bp_lb *h, int32_t B) {
   cudaFree(h->d_vtile_start);
   cudaFree(h->d_keys);
   cudaFree(h->d_done);
+  cudaFree(h->d_isums);
+  h->d_isums = nullptr;
   h->d_tile_start = nullptr;
   h->d_ptile_start = nullptr;
   h->d_vtile_start = nullptr;
@@ -163,6 +168,8 @@ int grow_batch(bp_lb *h, int32_t B) {
   BP_CHECK(cudaMalloc(&h->d_vtile_start, sizeof(int64_t) * ((size_t)cap + 1)));
   BP_CHECK(cudaMalloc(&h->d_keys, sizeof(unsigned long long) * (size_t)cap));
   BP_CHECK(cudaMalloc(&h->d_done, sizeof(unsigned int) * (size_t)cap));
+  BP_CHECK(cudaMalloc(&h->d_isums, sizeof(long long) * 8 * (size_t)cap));
+  BP_CHECK(cudaMemset(h->d_isums, 0, sizeof(long long) * 8 * (size_t)cap));
   BP_CHECK(cudaMemset(h->d_keys, 0, sizeof(unsigned long long) * (size_t)cap));
   BP_CHECK(cudaMemset(h->d_done, 0, sizeof(unsigned int) * (size_t)cap));
   h->cap_batch = cap;
@@ -238,7 +245,10 @@ int launch_batch(bp_lb *h, EvalArgs A, size_t smem, cudaStream_t st) {
   A.plpt = kPrefixLPTBatch;
   A.vb2_on = h->vb2_on;
   A.verdict = h->verdict;
+  A.prune = h->prune;
   A.dff_off = h->dff_off;
+  A.work_count = h->timing ? h->d_work_count : nullptr;
+  A.isums = h->d_isums;
   A.vtile_start = h->d_vtile_start;
   A.vwork = h->d_work + 2;
   const int shape = h->shape[MODE];
@@ -455,6 +465,8 @@ int bp_lb_destroy(bp_lb_t *h) {
   cudaFree(h->d_keys);
   cudaFree(h->d_done);
   cudaFree(h->d_gscratch);
+  cudaFree(h->d_work_count);
+  cudaFree(h->d_isums);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   if (h->stream) cudaStreamDestroy(h->stream);
   if (h->side) cudaStreamDestroy(h->side);
@@ -501,6 +513,7 @@ static EvalArgs plain_args(bp_lb *h, int64_t n, int64_t bins, int mode) {
   const int64_t sb = (mode == kModePlainNodes ? n + bins : n) * h->capacity;
   A.vb2_on = 0;
   A.verdict = h->verdict;
+  A.prune = h->prune;
   A.dff_off = h->dff_off;
   A.plpt = kPrefixLPTSingle;
   // global prefix tables when the scratch covers the prefix tiles (one CTA each)
@@ -720,6 +733,18 @@ int bp_lb_get_result_mode(bp_lb_t *h) {
   return h->verdict ? BP_RESULT_VERDICT : BP_RESULT_FULL;
 }
 
+int bp_lb_set_pruning(bp_lb_t *h, int32_t on) {
+  if (!h) return BP_EINVAL;
+  if (on != 0 && on != 1) return BP_ERANGE;
+  h->prune = on;
+  return BP_OK;
+}
+
+int bp_lb_get_pruning(bp_lb_t *h) {
+  if (!h) return -1;
+  return h->prune;
+}
+
 int bp_lb_set_overlap(bp_lb_t *h, int32_t prefix_ctas_per_sm) {
   if (!h) return BP_EINVAL;
   if (prefix_ctas_per_sm < 0 || prefix_ctas_per_sm > 8) return BP_ERANGE;
@@ -741,7 +766,24 @@ int bp_lb_get_dff_mask(bp_lb_t *h) {
 
 int bp_lb_set_kernel_timing(bp_lb_t *h, int32_t on) {
   if (!h) return BP_EINVAL;
+  if (on && !h->d_work_count) {
+    BP_CHECK(cudaMalloc(&h->d_work_count, 4 * sizeof(unsigned long long)));
+    BP_CHECK(cudaMemsetAsync(h->d_work_count, 0, 4 * sizeof(unsigned long long), h->stream));
+    BP_CHECK(cudaStreamSynchronize(h->stream));
+  }
   h->timing = on != 0;
+  return BP_OK;
+}
+
+int bp_lb_kernel_work(bp_lb_t *h, int64_t *out4) {
+  if (!h || !out4) return BP_EINVAL;
+  unsigned long long v[4] = {0ull, 0ull, 0ull, 0ull};
+  if (h->d_work_count) {
+    BP_CHECK(cudaDeviceSynchronize());
+    BP_CHECK(cudaMemcpy(v, h->d_work_count, sizeof(v), cudaMemcpyDeviceToHost));
+    BP_CHECK(cudaMemset(h->d_work_count, 0, sizeof(v)));
+  }
+  for (int i = 0; i < 4; ++i) out4[i] = (int64_t)v[i];
   return BP_OK;
 }
 

@@ -75,6 +75,16 @@ struct EvalArgs {
   int32_t verdict;            // verdict-only mode (early exit, exact feasibility)
   uint32_t dff_off;           // bit d set: DFF d is left out of the bound (default 0: all six)
   int32_t *gscratch;          // prefix tables in global memory: kGlobalTableInts per CTA
+  int32_t prune;              // skip parameters that provably cannot win (exact)
+  int32_t pad_prune;
+  // measurement (nullptr unless kernel timing is on): [0] VB2 (item,
+  // parameter) pairs evaluated by the VB2 kernel, [1] by the generic kernel,
+  // [2] VB2 parameters evaluated, [3] VB2 parameters pruned
+  unsigned long long *work_count;
+  // [B][8] per instance: n_small, n_big, n_half, n_full, sum_big w, sum w of
+  // the reduced instance, written by the prefix kernel; [7] = 1 once written
+  // (cleared by the plan kernel).  nullptr: not kept.
+  long long *isums;
 };
 
 // Shared-memory budget of the prefix-count tables (bytes; 48 KB lets four
@@ -87,13 +97,14 @@ constexpr int64_t kPrefixLPTSingle = 1024;
 
 // Bytes of the prefix-count tables of DFF d at capacity c (0: not on that path):
 // u-domain tables of (c - 1) / 2 + 2 entries (MT one, RAD2 two, CCM1 one) and
-// the w-domain table of c + 2 entries (BJ1), all int32.
+// the w-domain table of c + 2 entries (FS1, BJ1), all int32.
 BPLB_HD int64_t prefix_table_bytes(int d, int64_t c) {
   const int64_t nu = (c - 1) / 2 + 2;
   switch (d) {
     case kMT:
     case kCCM1: return 4 * nu;
     case kRAD2: return 8 * nu;
+    case kFS1:
     case kBJ1:  return 4 * (c + 2);
     default:    return 0;
   }
@@ -110,9 +121,10 @@ constexpr int64_t kGlobalTableInts = int64_t(1) << 20;
 // Where the prefix-count kernel keeps the tables of DFF d of an instance with
 // capacity c whose reduced sizes sum to at most sum_bound: 0 nowhere (the
 // direct kernels evaluate it), 1 shared memory, 2 the global scratch.  The
-// sums must fit 32 bits.
+// sums must fit 32 bits; FS1's count sum, at most 101 sum_bound / c, too.
 BPLB_HD int prefix_home(int d, int64_t c, int64_t sum_bound, int32_t on) {
   if (!(on & kPrefixShared) || sum_bound >= (int64_t(1) << 31)) return 0;
+  if (d == kFS1 && sum_bound / c >= (int64_t(1) << 25)) return 0;
   const int64_t bytes = prefix_table_bytes(d, c);
   if (bytes == 0) return 0;
   if (bytes <= kPrefixSmemBytes) return 1;
@@ -172,6 +184,14 @@ BPLB_HD bool prefix_u_merged(int64_t c, int64_t sum_bound, int32_t prefix_on, in
   return members >= 2;
 }
 
+// FS1 shares the first of BJ1's prefix-kernel tiles (both read the w-domain
+// table) when both go to the prefix kernel; otherwise it has a tile of its own.
+BPLB_HD bool prefix_w_merged(int64_t c, int64_t sum_bound, int32_t prefix_on, int32_t vb2_on,
+                             uint32_t dff_off) {
+  return dff_kernel(kFS1, c, sum_bound, prefix_on, vb2_on, dff_off) == kRoutePrefix &&
+         dff_kernel(kBJ1, c, sum_bound, prefix_on, vb2_on, dff_off) == kRoutePrefix;
+}
+
 // Prefix-kernel tiles of DFF d (routed there): one when its tables are in the
 // global scratch (built once per tile, so the tile takes the whole range),
 // else ceil(count / lpt).
@@ -182,14 +202,17 @@ BPLB_HD int64_t prefix_dff_tiles(int d, int64_t c, int64_t sum_bound, int32_t on
 }
 
 // Tiles of one kernel for an instance: lpt parameters each, DFFs in paper
-// order; on the prefix kernel the u group, when merged, is one tile.
+// order; on the prefix kernel the u group, when merged, is one tile, and FS1
+// rides on BJ1's first tile when prefix_w_merged.
 BPLB_HD int64_t route_tiles(int route, int64_t c, int64_t lpt, int64_t sum_bound, int32_t prefix_on,
                             int32_t vb2_on, uint32_t dff_off) {
-  const bool merged =
-      route == kRoutePrefix && prefix_u_merged(c, sum_bound, prefix_on, vb2_on, dff_off, lpt);
+  const bool pre = route == kRoutePrefix;
+  const bool merged = pre && prefix_u_merged(c, sum_bound, prefix_on, vb2_on, dff_off, lpt);
+  const bool wmerged = pre && prefix_w_merged(c, sum_bound, prefix_on, vb2_on, dff_off);
   int64_t t = merged ? 1 : 0;
   for (int d = 0; d < kNumDff; ++d) {
-    if (merged && d != kBJ1) continue;
+    if (merged && (d == kMT || d == kRAD2 || d == kCCM1)) continue;
+    if (wmerged && d == kFS1) continue;
     if (dff_kernel(d, c, sum_bound, prefix_on, vb2_on, dff_off) != route) continue;
     t += route == kRoutePrefix ? prefix_dff_tiles(d, c, sum_bound, prefix_on, lpt)
                                : (param_count(d, c) + lpt - 1) / lpt;
@@ -331,6 +354,7 @@ __global__ void __launch_bounds__(1024)
     if (b < A.B) {
       A.keys[b] = 0ull;
       A.done[b] = 0u;
+      if (A.isums) A.isums[8 * b + 7] = 0;
       bool ok;
       int64_t c, L;
       if (MODE == kSrcNodes) {
@@ -381,6 +405,8 @@ struct TileShared {
   int ns, nb, err;
   int skip;     // verdict mode: the instance was decided before this tile
   int stop[2];  // verdict mode: decided before group g (double-buffered by g & 1)
+  long long kcut[2];  // VB2 pruning: the cut of group g (double-buffered by g & 1)
+  unsigned long long wc[4];  // work counts of this CTA (EvalArgs::work_count)
   unsigned long long warp_key[32];
   long long sums[6];
   unsigned long long sumF[2];  // VB2 fixed point: sum of F over the small and big lists
@@ -568,6 +594,67 @@ __device__ __forceinline__ void stage_chunk(const EvalArgs &A, const InstView &I
   }
 }
 
+// VB2 pruning (exact).  A VB2 parameter whose bound is at most kcut is
+// skipped: in verdict mode kcut = k (it cannot make the instance infeasible);
+// in full mode kcut comes from the instance's best key so far, B (read from
+// its slot; it only grows): B when that key's flattened index precedes VB2's
+// (a tie then loses to it), else B - 1 -- a skipped parameter is then below
+// the final maximum or ties it behind an earlier parameter.  -1: no cut.
+__device__ __forceinline__ long long vb2_cut(const unsigned long long *slot, uint32_t gbase) {
+  const unsigned long long key = *reinterpret_cast<const volatile unsigned long long *>(slot);
+  if (key == 0ull) return -1;
+  const long long B = (long long)(key >> 32);
+  const uint32_t g = 0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull);
+  return g < gbase ? B : B - 1;
+}
+
+// Whether VB2 parameter l may have a bound above kk (false proves lb <= kk).
+// With ceil(x) < x + 1 for the small list and ceil(x) >= x for the big one,
+// acc <= floor(X / c), X = l D + n_small (c - 1), D = sum_small u - sum_big u,
+// and lb <= kk whenever S(acc) <= 2 kk (l - 1), i.e. floor(X / c) <= M with
+// M = floor(((l - 1)(2 kk - K) + 2 n_small - 2 n_big) / 2),
+// K = 2 n_big + n_half + 2 n_full (vb2_sum in bp_lb_core.cuh).  kk is at most
+// the stream length L (every VB2 bound is at most L), so up to c = 65535 all
+// of it fits 64 bits; larger capacities use 128.
+__device__ __forceinline__ bool vb2_may_exceed(int64_t l, int64_t kk, int64_t c, int64_t Dd,
+                                               int64_t ns, int64_t nb, int64_t K) {
+  if (c <= kVb2FixedCap) {
+    const int64_t M = ((l - 1) * (2 * kk - K) + 2 * ns - 2 * nb) >> 1;
+    return l * Dd + ns * (c - 1) > (M + 1) * c - 1;
+  }
+  const __int128 M = ((__int128)(l - 1) * (2 * kk - K) + 2 * ns - 2 * nb) >> 1;
+  return (__int128)l * Dd + (__int128)ns * (c - 1) > (M + 1) * (__int128)c - 1;
+}
+
+// Whether some VB2 parameter in [l0, l1] may have a bound above kk (c <=
+// 65535, kk <= L).  vb2_may_exceed(l) implies G(l) > 0 with
+// G(l) = 2 X(l) - c (Y(l) + 1) + 2, Y(l) = (l - 1)(2 kk - K) + 2 n_small - 2 n_big
+// (M = floor(Y / 2) >= (Y - 1) / 2), and G is linear in l: G <= 0 at both ends
+// rules out the whole range.
+__device__ __forceinline__ bool vb2_range_may_exceed(int64_t l0, int64_t l1, int64_t kk, int64_t c,
+                                                     int64_t Dd, int64_t ns, int64_t nb,
+                                                     int64_t K) {
+  auto G = [&](int64_t l) {
+    const int64_t X = l * Dd + ns * (c - 1);
+    const int64_t Y = (l - 1) * (2 * kk - K) + 2 * ns - 2 * nb;
+    return 2 * X - c * (Y + 1) + 2;
+  };
+  return G(l0) > 0 || G(l1) > 0;
+}
+
+// Work counters of a CTA (measurement only): cleared at the kernel's start,
+// added to EvalArgs::work_count once at its end.
+__device__ __forceinline__ void work_count_begin(const EvalArgs &A, TileShared &S) {
+  if (A.work_count != nullptr && threadIdx.x < 4) S.wc[threadIdx.x] = 0ull;
+}
+
+__device__ __forceinline__ void work_count_flush(const EvalArgs &A, TileShared &S) {
+  if (A.work_count == nullptr) return;
+  __syncthreads();
+  if (threadIdx.x < 4 && S.wc[threadIdx.x] != 0ull)
+    atomicAdd(&A.work_count[threadIdx.x], S.wc[threadIdx.x]);
+}
+
 // Evaluates one tile of DFF D: lambdas [lam0, lam_end) in groups of NT * T,
 // thread t taking the T consecutive lambdas lam_g + t * T + j (j < T) of group
 // g, so that the threads past the end of a short range form whole idle warps.  Returns the
@@ -580,7 +667,8 @@ __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int
                                        const uint32_t *s_load, TileShared &S,
                                        const int64_t *req_lam = nullptr, int64_t *req_out = nullptr,
                                        int64_t req_idx = -1,
-                                       unsigned long long *vslot = nullptr) {
+                                       unsigned long long *vslot = nullptr,
+                                       unsigned long long *kslot = nullptr) {
   constexpr bool ULIST = (D == kMT || D == kRAD2 || D == kCCM1 || D == kVB2);
   constexpr int GW = NT * T;
   const int tid = threadIdx.x;
@@ -608,12 +696,18 @@ __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int
   const int ngroups = DEBUG ? 1 : (int)((lam_end - lam0 + GW - 1) / GW);
   unsigned long long best = 0ull;
 
+  // VB2 pruning against the instance's best key so far (full mode)
+  const bool kprune = D == kVB2 && !DEBUG && kslot != nullptr;
   for (int g = 0; g < ngroups; ++g) {
-    // verdict mode: stop once another tile (or an earlier group) decided the instance
-    if (vslot != nullptr && g > 0) {
-      if (tid == 0) S.stop[g & 1] = slot_decided(vslot, I.k) ? 1 : 0;
+    // verdict mode: stop once another tile (or an earlier group) decided the
+    // instance; full mode: this group's VB2 cut
+    if ((vslot != nullptr || kprune) && g > 0) {
+      if (tid == 0) {
+        if (vslot != nullptr) S.stop[g & 1] = slot_decided(vslot, I.k) ? 1 : 0;
+        if (kprune) S.kcut[g & 1] = vb2_cut(kslot, gbase);
+      }
       __syncthreads();
-      if (S.stop[g & 1]) break;
+      if (vslot != nullptr && S.stop[g & 1]) break;
     }
     // ---- this group's parameters and their constants -------------------------
     int64_t lam[T];
@@ -682,6 +776,7 @@ __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int
           S.ns = 0;
           S.nb = 0;
           S.sumF[0] = S.sumF[1] = 0ull;
+          if (kprune && g == 0) S.kcut[0] = vb2_cut(kslot, gbase);
         }
         if (g == 0 && p == 0 && tid < 6) S.sums[tid] = 0;
         __syncthreads();
@@ -704,30 +799,46 @@ __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int
         }
         __syncthreads();
       }
-      // Verdict mode, VB2: a warp skips the items when none of its parameters
-      // can have a bound above k.  With ceil(x) < x + 1 for the small list
-      // and ceil(x) >= x for the big one, acc <= floor(X / c),
-      // X = l D + n_small (c - 1), D = sum_small u - sum_big u, and
-      // lb <= k whenever S(acc) <= 2 k (l - 1), i.e. floor(X / c) <= M with
-      // M = floor(((l - 1)(2k - K) + 2 n_small - 2 n_big) / 2),
-      // K = 2 n_big + n_half + 2 n_full (vb2_sum in bp_lb_core.cuh).
-      if (D == kVB2 && vslot != nullptr && one_chunk && !S.err) {
-        const int64_t ns_ = S.sums[0], nb_ = S.sums[1], nh_ = S.sums[2], nf_ = S.sums[3];
-        const int64_t swb = S.sums[4], sw = S.sums[5];
-        const int64_t Dd = (sw - swb - nh_ * (c / 2) - nf_ * c) - (nb_ * c - swb);
-        const int64_t K = 2 * nb_ + nh_ + 2 * nf_;
-        const int64_t kk = min(I.k, (int64_t)1 << 40);  // bounds never reach 2^40
-        bool need = false;
+      int nv_before = 0;
 #pragma unroll
-        for (int j = 0; j < T; ++j) {
-          if (!valid[j]) continue;
-          const int64_t l = lam[j];
-          const int64_t M = ((l - 1) * (2 * kk - K) + 2 * ns_ - 2 * nb_) >> 1;
-          need |= l * Dd + ns_ * (c - 1) > (M + 1) * c - 1;
+      for (int j = 0; j < T; ++j) nv_before += valid[j] ? 1 : 0;
+      // VB2 pruning (vb2_cut, vb2_may_exceed): parameters that cannot exceed
+      // the cut are dropped, and a warp left with none skips the items.  The
+      // instance sums are complete once the first pass over the stream is.
+      if (D == kVB2 && (vslot != nullptr || kprune) && (one_chunk || g > 0) && !S.err) {
+        const int64_t cut = vslot != nullptr ? I.k : (int64_t)S.kcut[g & 1];
+        if (cut >= 0) {
+          const int64_t ns_ = S.sums[0], nb_ = S.sums[1], nh_ = S.sums[2], nf_ = S.sums[3];
+          const int64_t swb = S.sums[4], sw = S.sums[5];
+          const int64_t Dd = (sw - swb - nh_ * (c / 2) - nf_ * c) - (nb_ * c - swb);
+          const int64_t K = 2 * nb_ + nh_ + 2 * nf_;
+          const int64_t kk = min(cut, L);
+#pragma unroll
+          for (int j = 0; j < T; ++j)
+            valid[j] = valid[j] && vb2_may_exceed(lam[j], kk, c, Dd, ns_, nb_, K);
+          bool mine = false;
+#pragma unroll
+          for (int j = 0; j < T; ++j) mine |= valid[j];
+          if (!__any_sync(0xFFFFFFFFu, mine)) {
+#pragma unroll
+            for (int j = 0; j < T; ++j) valid[j] = false;
+          }
         }
-        if (!__any_sync(0xFFFFFFFFu, need)) {
+      }
+      if (D == kVB2 && !DEBUG && A.work_count != nullptr && !S.err) {
+        int nv = 0;
 #pragma unroll
-          for (int j = 0; j < T; ++j) valid[j] = false;
+        for (int j = 0; j < T; ++j) nv += valid[j] ? 1 : 0;
+        const uint32_t tot = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)nv);
+        const uint32_t totb = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)nv_before);
+        if (lane_id() == 0) {
+          if (tot != 0u)
+            atomicAdd(&S.wc[VB2_FIXED_ONLY ? 0 : 1],
+                      (unsigned long long)tot * (unsigned long long)(S.ns + S.nb));
+          if (p == 0) {
+            atomicAdd(&S.wc[2], (unsigned long long)tot);
+            atomicAdd(&S.wc[3], (unsigned long long)(totb - tot));
+          }
         }
       }
       bool any_valid = false;
@@ -867,7 +978,8 @@ __device__ void process_tile(const EvalArgs &A, int64_t b, int64_t lt, int64_t n
     case kRAD2: best = tile_dff<NT, T, kRAD2, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S, nullptr, nullptr, -1, vslot); break;
     case kFS1: best = tile_dff<NT, T_FS1, kFS1, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S, nullptr, nullptr, -1, vslot); break;
     case kCCM1: best = tile_dff<NT, T, kCCM1, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S, nullptr, nullptr, -1, vslot); break;
-    case kVB2: best = tile_dff<NT, T, kVB2, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S, nullptr, nullptr, -1, vslot); break;
+    case kVB2: best = tile_dff<NT, T, kVB2, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S, nullptr, nullptr, -1, vslot,
+                                                         A.prune && !A.verdict ? &A.keys[b] : nullptr); break;
     default: best = tile_dff<NT, T, kBJ1, MODE, false>(A, I, lam0, lam_end, s_items, s_a, s_load, S, nullptr, nullptr, -1, vslot); break;
   }
   fold_and_finalize<NT>(A, b, best, S.err != 0, ntiles, I, S.warp_key);
@@ -972,6 +1084,7 @@ __global__ void __launch_bounds__(NT, MINB) eval_kernel(EvalArgs A) {
   uint32_t *s_load = reinterpret_cast<uint32_t *>(smem_raw + 2 * sizeof(uint32_t) * kListTop);
 
   const int64_t total = A.tile_start ? A.tile_start[A.B] : A.single_tiles;
+  work_count_begin(A, S);
   tile_first(A.tile_start, A.B, total, A.work, cur);
   while (cur.tile < total) {
     const int64_t t = cur.tile, b = cur.inst;
@@ -983,6 +1096,7 @@ __global__ void __launch_bounds__(NT, MINB) eval_kernel(EvalArgs A) {
     if (!A.work) break;
     tile_publish(A.tile_start, A.B, total, next, cur);
   }
+  work_count_flush(A, S);
 }
 
 // Per-(DFF, lambda) bounds of one instance: grid (ceil(m / NT), 6); block

@@ -86,6 +86,7 @@ extern "C" int bp_lb_eval_batch_noalloc(int32_t B, const int64_t *d_offsets,
   EvalArgs A;
   std::memset(&A, 0, sizeof(A));
   A.one = 1u;
+  A.prune = 1;
   A.B = B;
   A.offsets = d_offsets;
   A.sizes = d_sizes;

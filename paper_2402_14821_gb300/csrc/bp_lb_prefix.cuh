@@ -1,9 +1,10 @@
-// bp_lb_prefix.cuh -- prefix-count evaluation of MT, RAD2, CCM1 and BJ1.
+// bp_lb_prefix.cuh -- prefix-count evaluation of MT, RAD2, FS1, CCM1 and BJ1.
 //
 // Same bounds as the direct evaluators (bit-exact), asymptotically less work:
 // per tile the instance's items are histogrammed by value in shared memory and
-// suffix-scanned, after which each parameter needs O(1) (MT, RAD2), O(U / l)
-// (CCM1) or O(c / l) (BJ1) table lookups instead of one evaluation per item.
+// suffix-scanned, after which each parameter needs O(1) (MT, RAD2), O(l)
+// (FS1), O(U / l) (CCM1) or O(c / l) (BJ1) table lookups instead of one
+// evaluation per item.
 // With u, the small/big classes and cm = c mod l as in bp_lb_core.cuh, and the
 // u-domain tables (x in [0, U + 1], U = floor((c - 1) / 2), entry U + 1 = 0)
 //   E(x)  = sum_small u [u >= x] - sum_big u [u >= x],
@@ -16,11 +17,18 @@
 //         since floor(u / l) counts the multiples j l <= u;
 //   BJ1:  cm q + min(rho, cm) (w = q l + rho) counts the x <= w in the union
 //         of the blocks [j l + 1, j l + cm], j >= 0, so summed over the items
-//         it is sum_j (NN(j l + 1) - NN(j l + cm + 1)) over j = 0 .. floor(c / l).
+//         it is sum_j (NN(j l + 1) - NN(j l + cm + 1)) over j = 0 .. floor(c / l);
+//   FS1:  with l' = l + 1, w maps to w l when c divides w l', else to
+//         floor(w l' / c) c, so S = c sum_w floor(w l' / c) - sum_{c | w l'} w;
+//         floor(w l' / c) counts the j in [1, l'] with w >= ceil(j c / l'), and
+//         c divides w l' exactly for the multiples w = m c / gcd(c, l'):
+//         S = c sum_{j=1}^{l'} N(ceil(j c / l')) - sum_m m g #[w = m g].
 // NN is the suffix sum of the suffix count N(x) = #[w >= x]: a histogram
-// scanned twice.  Every table entry and every sum above is bounded by the
-// instance's size total, below 2^31 on this path (prefix_handles), so the
-// tables and accumulators are 32-bit.  VB2 and FS1 stay on the direct kernel.
+// scanned twice; N(x) = NN(x) - NN(x + 1), #[w = x] = N(x) - N(x + 1).  Every
+// table entry and every sum above is bounded by the instance's size total,
+// below 2^31 on this path (prefix_handles), so the tables and accumulators are
+// 32-bit (FS1's S, up to l' times the total, is formed in 64 bits).  VB2 stays
+// on the direct kernels.
 //
 // Only bounds above L1 = ceil(sum w / c) can change the maximum: L1 is MT's
 // bound at l = 0, the smallest flattened index, which wins every tie at L1.
@@ -41,6 +49,8 @@ constexpr int kPrefixWarps = kPrefixNT / 32;
 constexpr uint32_t kCtaBlocks = 1024;
 constexpr uint32_t kWarpBlocks = 32;
 constexpr int kMaxHeavy = kPrefixNT;
+// FS1's parameters l in [1, 100] (param_range)
+constexpr int kFs1Params = 100;
 
 struct PrefixShared {
   int err;
@@ -50,6 +60,8 @@ struct PrefixShared {
   uint32_t wtot[2][kPrefixWarps];
   uint32_t heavy_acc[kMaxHeavy];
   uint32_t heavy_cm[kMaxHeavy];
+  uint32_t fs1_cnt[kFs1Params];  // FS1: per parameter, sum_j N(ceil(j c / l'))
+  uint32_t fs1_dv[kFs1Params];   //      and the multiples' sum
 };
 
 // Sum of v over the threads after this one (higher threadIdx.x).  wtot must
@@ -190,7 +202,32 @@ struct PrefixEval {
   uint32_t sumw, n_big, n_half, n_full, sumw_big, TB;
   uint32_t B;                // the thread's best bound so far (L1 or 0 at first)
   unsigned long long best;   // the thread's best key
+  uint32_t L1;               // pruning cut (prune_ccm1, prune_bj1): L1
+  bool prune;                // pruning on and MT part of the bound
 };
+
+// Pruning (exact) against L1 = MT's bound at l = 0, which has the smallest
+// flattened index, so that a parameter whose bound is at most L1 cannot
+// change the maximum or its first argmax.  Upper bounds from the instance's
+// sums alone:
+//   BJ1: f(w) = p (l - cm) + max(0, rho - cm) <= w (l - cm) / l (w = p l + rho,
+//        rho < l), so lb <= ceil(sum w / (q l)) = ceil(sum w / (c - cm));
+//   CCM1: floor(u / l) <= u / l for the small items and >= (u - l + 1) / l for
+//        the big ones, so with sws = sum_small u, sub = sum_big u,
+//        l S <= 2 sws - 2 sub + 2 n_big (l - 1) + q l kS.
+__device__ __forceinline__ bool prune_bj1(const PrefixEval &x, uint32_t cm) {
+  return x.prune && (uint64_t)x.L1 * (uint64_t)(x.c32 - cm) >= (uint64_t)x.sumw;
+}
+
+__device__ __forceinline__ bool prune_ccm1(const PrefixEval &x, uint32_t l, uint32_t q,
+                                           uint32_t kS) {
+  if (!x.prune) return false;
+  const int64_t sws = (int64_t)x.sumw - x.sumw_big - (int64_t)x.n_half * (x.c32 / 2u) -
+                      (int64_t)x.n_full * x.c32;
+  const int64_t lS = 2 * sws - 2 * (int64_t)x.TB + 2 * (int64_t)x.n_big * (l - 1) +
+                     (int64_t)q * l * kS;
+  return lS <= 2 * (int64_t)q * l * x.L1;
+}
 
 // MT: S(l) = E(l) + TB + sumw_big + n_half (c/2) + n_full c, f = c; one lookup.
 __device__ __forceinline__ void eval_mt(const int32_t *E, int64_t lam0, int64_t lam_end,
@@ -232,6 +269,82 @@ __device__ __forceinline__ void eval_rad2(const int32_t *T0, const int32_t *T1, 
   }
 }
 
+// FS1 from the w-domain table (file comment).  Its terms (l', j), j in
+// [1, l'] -- 5150 of them for l in [1, 100] -- are cut into equal runs, one per
+// thread.  A run walks j (and on to the next l' where one ends) with an
+// incremental quotient j c = q l' + r, so that ceil(j c / l') = q + [r > 0]
+// and the multiples of the divisibility sum are exactly the terms with r = 0
+// (w = j c / l'); it adds its count and multiples' sums per parameter into
+// shared memory, after which thread l - lo forms S(l) in 64 bits and keeps
+// the key (the first parameters its thread meets).  With c < 2^20 on this path
+// every j c fits 32 bits; the count sum, at most 101 (sum w) / c, is below 2^32
+// by prefix_home, and the multiples' sum is at most sum w.
+__device__ __forceinline__ uint32_t tri(uint32_t m) { return m * (m + 1u) / 2u; }
+
+__device__ __forceinline__ void eval_fs1(const int32_t *T, int64_t c, PrefixEval &x,
+                                         PrefixShared &S) {
+  int64_t lo_d, hi_d;
+  param_range(kFS1, c, lo_d, hi_d);
+  const uint32_t lo = (uint32_t)lo_d, hi = (uint32_t)hi_d;
+  const uint32_t gofs = flat_index(kFS1, lo_d, c) - lo;
+  const uint32_t c32 = x.c32;
+  const uint32_t base = tri(lo);  // term index of (l' = lo + 1, j = 1), plus base
+  const uint32_t total = tri(hi + 1u) - base;
+  const uint32_t per = (total + kPrefixNT - 1) / kPrefixNT;
+  uint32_t p = threadIdx.x * per;
+  const uint32_t pe = min(total, p + per);
+  if (p < pe) {
+    // the run's first term: l = the largest m with tri(m) <= p + base
+    const uint32_t P = p + base;
+    uint32_t l = (uint32_t)((sqrtf(8.0f * (float)P + 1.0f) - 1.0f) * 0.5f);
+    while (tri(l + 1u) <= P) ++l;
+    while (tri(l) > P) --l;
+    uint32_t j = P - tri(l) + 1u;
+    while (p < pe) {
+      const uint32_t lp = l + 1u;
+      const uint32_t cq = c32 / lp, cr = c32 - cq * lp;
+      uint32_t q = (j * c32) / lp;
+      uint32_t r = j * c32 - q * lp;
+      const uint32_t j0 = j, jend = min(lp, j + (pe - p) - 1u);
+      uint32_t cnt = 0, dv = 0;
+      for (;;) {
+        const uint32_t xj = q + (r != 0u);  // in [1, c]
+        const int32_t nx = T[xj] - T[xj + 1u];
+        cnt += (uint32_t)nx;
+        if (r == 0u) {  // c divides xj l': xj's items map to xj l
+          const int32_t nx1 = (xj < c32) ? T[xj + 1u] - T[xj + 2u] : 0;  // N(c + 1) = 0
+          dv += xj * (uint32_t)(nx - nx1);
+        }
+        if (j == jend) break;
+        ++j;
+        q += cq;
+        r += cr;
+        if (r >= lp) {
+          r -= lp;
+          ++q;
+        }
+      }
+      atomicAdd(&S.fs1_cnt[l - lo], cnt);
+      if (dv != 0u) atomicAdd(&S.fs1_dv[l - lo], dv);
+      p += jend - j0 + 1u;
+      ++l;
+      j = 1u;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x <= hi - lo) {
+    const uint32_t l = lo + threadIdx.x;
+    const uint64_t Sv = (uint64_t)c32 * S.fs1_cnt[threadIdx.x] - S.fs1_dv[threadIdx.x];
+    const uint64_t f = (uint64_t)c32 * l;
+    if ((uint64_t)x.B * f < Sv || x.best == 0ull) {
+      const uint64_t qv = Sv / f;
+      const uint32_t lb = (uint32_t)(qv + (Sv != qv * f));
+      x.B = max(x.B, lb);
+      x.best = make_key((int64_t)lb, gofs + l);
+    }
+  }
+}
+
 // CCM1 / BJ1: the lookups of parameter l fall like X / l, so heavy parameters
 // are shared by the CTA, medium ones by a warp, the rest take a thread each.
 template <int D, bool PACKED>
@@ -262,24 +375,30 @@ __device__ void eval_harmonic(const int32_t *T0, int64_t lam0, int64_t lam_end, 
   };
 
   // ---- parameters shared by the whole CTA ---------------------------------------
+  // pruned parameters (prune_bj1, prune_ccm1) are skipped altogether
+  auto pruned = [&](uint32_t l, uint32_t q, uint32_t cm) {
+    return D == kBJ1 ? prune_bj1(x, cm) : prune_ccm1(x, l, q, kS);
+  };
+  constexpr uint32_t kPruned = 0xFFFFFFFFu;  // heavy_cm marker (cm < l otherwise)
   const int ncta = (int)(cta_end - lam0);
   if (ncta > 0) {
     if (tid < ncta) {
       const uint32_t l = (uint32_t)(lam0 + tid);
-      S.heavy_cm[tid] = c32 % l;
+      const uint32_t q = c32 / l, cm = c32 - q * l;
+      S.heavy_cm[tid] = pruned(l, q, cm) ? kPruned : cm;
       S.heavy_acc[tid] = 0u;
     }
     __syncthreads();
     for (int i = 0; i < ncta; ++i) {
       const uint32_t l = (uint32_t)(lam0 + i);
       const uint32_t cm = S.heavy_cm[i];
-      if (D == kBJ1 && cm == 0u) continue;  // every BJ1 term is 0
+      if (cm == kPruned || (D == kBJ1 && cm == 0u)) continue;  // cm = 0: every BJ1 term is 0
       const uint32_t part = __reduce_add_sync(
           0xFFFFFFFFu, block_terms<D, PACKED>(T0, c32, U, l, cm, (uint32_t)tid, kPrefixNT));
       if (lane == 0 && part != 0u) atomicAdd(&S.heavy_acc[i], part);
     }
     __syncthreads();
-    if (tid < ncta) {
+    if (tid < ncta && S.heavy_cm[tid] != kPruned) {
       const uint32_t l = (uint32_t)(lam0 + tid);
       finish(l, c32 / l, S.heavy_acc[tid]);
     }
@@ -295,10 +414,11 @@ __device__ void eval_harmonic(const int32_t *T0, int64_t lam0, int64_t lam_end, 
     for (int64_t r0 = 0; r0 < rounds; r0 += 32) {
       const int64_t ri = r0 + lane;
       const int64_t my_l = cta_end + ri * kPrefixWarps + ((ri & 1) ? kPrefixWarps - 1 - warp : warp);
-      const bool mine_ok = ri < rounds && my_l < warp_end;
-      const uint32_t ml = mine_ok ? (uint32_t)my_l : 1u;
+      const bool in_range = ri < rounds && my_l < warp_end;
+      const uint32_t ml = in_range ? (uint32_t)my_l : 1u;
       const uint32_t mq = c32 / ml;
       const uint32_t mcm = c32 - mq * ml;
+      const bool mine_ok = in_range && !pruned(ml, mq, mcm);
       uint32_t mine = 0;
       const int cnt = (int)min((int64_t)32, rounds - r0);
       for (int t = 0; t < cnt; ++t) {
@@ -329,6 +449,7 @@ __device__ void eval_harmonic(const int32_t *T0, int64_t lam0, int64_t lam_end, 
       } else {
         while (q * l > c32) --q;
       }
+      if (pruned(l, q, c32 - q * l)) continue;
       uint32_t acc = 0;
       if (D == kCCM1) {
         acc = block_terms<D, PACKED>(T0, c32, U, l, 0u, 0u, 1u);
@@ -345,12 +466,14 @@ __device__ void eval_harmonic(const int32_t *T0, int64_t lam0, int64_t lam_end, 
 // instance I -- one pass over the node's base items both accumulates its bin
 // loads and histograms its unpacked items, a second pass histograms the bin
 // loads -- and evaluates parameters [lam0, lam_end) (the u group: all of its
-// members); returns the thread's best key.
+// members), after FS1's when with_fs1 (D = BJ1: the w-domain table; FS1's own
+// tile is BJ1's with an empty range); returns the thread's best key.
 template <int MODE, int D>
 __device__ __forceinline__ unsigned long long prefix_tile(const EvalArgs &A, const InstView &I,
-                                                          int64_t lam0,
-                                          int64_t lam_end, int32_t *tab, uint32_t *s_load,
-                                          PrefixShared &S) {
+                                                          int64_t lam0, int64_t lam_end,
+                                                          bool with_fs1, int32_t *tab,
+                                                          uint32_t *s_load, PrefixShared &S,
+                                                          long long *isum_out) {
   const int tid = threadIdx.x;
   const int64_t c = I.c;
   const uint32_t c32 = (uint32_t)c;
@@ -367,6 +490,10 @@ __device__ __forceinline__ unsigned long long prefix_tile(const EvalArgs &A, con
   if (MODE == kSrcNodes)
     for (int64_t j = tid; j < I.k; j += kPrefixNT) s_load[j] = 0u;
   if (tid < 8) S.sums[tid] = 0;
+  if (D == kBJ1 && with_fs1 && tid < kFs1Params) {
+    S.fs1_cnt[tid] = 0u;
+    S.fs1_dv[tid] = 0u;
+  }
   __syncthreads();
 
   // ---- histogram the instance's reduced items ------------------------------------
@@ -430,6 +557,14 @@ __device__ __forceinline__ unsigned long long prefix_tile(const EvalArgs &A, con
     if (lane_id() == 0 && xs != 0u) atomicAdd((unsigned long long *)&S.sums[e], (unsigned long long)xs);
   }
   __syncthreads();
+  // the class counts and sums of the instance, for the VB2 kernel's tile
+  // pruning (every tile but BJ1's classifies the items)
+  if (D != kBJ1 && isum_out != nullptr && threadIdx.x == 0 && !S.err) {
+#pragma unroll
+    for (int e = 0; e < 6; ++e) isum_out[e] = S.sums[e];
+    __threadfence();
+    isum_out[7] = 1;
+  }
   if (D == kBJ1) {
     suffix_scan<true>(T0, nW, S);
   } else {
@@ -451,9 +586,12 @@ __device__ __forceinline__ unsigned long long prefix_tile(const EvalArgs &A, con
   x.sumw = (uint32_t)S.sums[5];
   x.TB = (uint32_t)S.sums[6];
   // L1 (MT's bound at l = 0) when MT is part of the bound, else no floor
-  x.B = (A.dff_off & 1u) ? 0u : x.sumw / c32 + (x.sumw % c32 != 0u);
+  x.L1 = x.sumw / c32 + (x.sumw % c32 != 0u);
+  x.B = (A.dff_off & 1u) ? 0u : x.L1;
+  x.prune = A.prune && !(A.dff_off & 1u);
   x.best = 0ull;
 
+  if (D == kBJ1 && with_fs1) eval_fs1(T0, c, x, S);  // FS1 precedes BJ1 in paper order
   if (D == kMT) eval_mt(T0, lam0, lam_end, c, x);
   if (D == kRAD2) eval_rad2<false>(T0, T1, lam0, lam_end, c, x);
   if (D == kCCM1 || D == kBJ1) eval_harmonic<D, false>(T0, lam0, lam_end, c, x, S);
@@ -483,9 +621,9 @@ __device__ __forceinline__ unsigned long long prefix_tile(const EvalArgs &A, con
 }
 
 // Persistent kernel over the prefix tile table (instance, DFF in {MT, RAD2,
-// CCM1, BJ1} routed here by prefix_handles or the merged u group, A.plpt
+// FS1, CCM1, BJ1} routed here by prefix_handles or the merged u group, A.plpt
 // consecutive lambdas -- all of them when the tables are in the global
-// scratch).
+// scratch; FS1 with BJ1's first tile when prefix_w_merged).
 template <int MODE>
 __global__ void __launch_bounds__(kPrefixNT, 4) prefix_kernel(EvalArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -508,14 +646,14 @@ __global__ void __launch_bounds__(kPrefixNT, 4) prefix_kernel(EvalArgs A) {
     int d = 0;
     const int64_t sb = sum_bound<MODE>(I);
     const bool merged = prefix_u_merged(I.c, sb, A.prefix_on, A.vb2_on, A.dff_off, A.plpt);
-    if (merged) {
-      if (rem == 0) d = kPrefixU;
-      else {
-        d = kBJ1;  // tiles after the u group's one are BJ1's
-        rem -= 1;
-      }
+    const bool wmerged = prefix_w_merged(I.c, sb, A.prefix_on, A.vb2_on, A.dff_off);
+    if (merged && rem == 0) {
+      d = kPrefixU;
     } else {
+      if (merged) rem -= 1;  // the u group's tile comes first
       for (d = 0; d < kNumDff; ++d) {
+        if (merged && (d == kMT || d == kRAD2 || d == kCCM1)) continue;
+        if (wmerged && d == kFS1) continue;
         if (dff_kernel(d, I.c, sb, A.prefix_on, A.vb2_on, A.dff_off) != kRoutePrefix) continue;
         const int64_t nt = prefix_dff_tiles(d, I.c, sb, A.prefix_on, A.plpt);
         if (rem < nt) break;
@@ -526,10 +664,13 @@ __global__ void __launch_bounds__(kPrefixNT, 4) prefix_kernel(EvalArgs A) {
                                      : prefix_home(d, I.c, sb, A.prefix_on);
     int32_t *gtab = A.gscratch + (size_t)blockIdx.x * (size_t)kGlobalTableInts;
     int64_t lo_d = 0, hi_d = -1;
-    if (d != kPrefixU) param_range(d, I.c, lo_d, hi_d);
+    if (d != kPrefixU && d != kFS1) param_range(d, I.c, lo_d, hi_d);
     const int64_t lpt = (home == 2) ? hi_d - lo_d + 1 : A.plpt;  // global tables: one tile
     const int64_t lam0 = lo_d + rem * lpt;
     const int64_t lam_end = min(hi_d + 1, lam0 + lpt);
+    // FS1 on BJ1's table: on its own tile (empty BJ1 range) or BJ1's first
+    const bool with_fs1 = d == kFS1 || (wmerged && d == kBJ1 && rem == 0);
+    long long *isum = A.isums != nullptr ? A.isums + 8 * b : nullptr;
 
     if (threadIdx.x == 0) {
       S.err = 0;
@@ -540,17 +681,17 @@ __global__ void __launch_bounds__(kPrefixNT, 4) prefix_kernel(EvalArgs A) {
     // one instantiation per table space, so that shared-memory tables are
     // accessed with shared-memory instructions
     if (!S.skip && home != 2) {
-      if (d == kPrefixU) best = prefix_tile<MODE, kPrefixU>(A, I, lam0, lam_end, stab, s_load, S);
-      else if (d == kMT) best = prefix_tile<MODE, kMT>(A, I, lam0, lam_end, stab, s_load, S);
-      else if (d == kRAD2) best = prefix_tile<MODE, kRAD2>(A, I, lam0, lam_end, stab, s_load, S);
-      else if (d == kCCM1) best = prefix_tile<MODE, kCCM1>(A, I, lam0, lam_end, stab, s_load, S);
-      else best = prefix_tile<MODE, kBJ1>(A, I, lam0, lam_end, stab, s_load, S);
+      if (d == kPrefixU) best = prefix_tile<MODE, kPrefixU>(A, I, lam0, lam_end, false, stab, s_load, S, isum);
+      else if (d == kMT) best = prefix_tile<MODE, kMT>(A, I, lam0, lam_end, false, stab, s_load, S, isum);
+      else if (d == kRAD2) best = prefix_tile<MODE, kRAD2>(A, I, lam0, lam_end, false, stab, s_load, S, isum);
+      else if (d == kCCM1) best = prefix_tile<MODE, kCCM1>(A, I, lam0, lam_end, false, stab, s_load, S, isum);
+      else best = prefix_tile<MODE, kBJ1>(A, I, lam0, lam_end, with_fs1, stab, s_load, S, nullptr);
     } else if (!S.skip) {
-      if (d == kPrefixU) best = prefix_tile<MODE, kPrefixU>(A, I, lam0, lam_end, gtab, s_load, S);
-      else if (d == kMT) best = prefix_tile<MODE, kMT>(A, I, lam0, lam_end, gtab, s_load, S);
-      else if (d == kRAD2) best = prefix_tile<MODE, kRAD2>(A, I, lam0, lam_end, gtab, s_load, S);
-      else if (d == kCCM1) best = prefix_tile<MODE, kCCM1>(A, I, lam0, lam_end, gtab, s_load, S);
-      else best = prefix_tile<MODE, kBJ1>(A, I, lam0, lam_end, gtab, s_load, S);
+      if (d == kPrefixU) best = prefix_tile<MODE, kPrefixU>(A, I, lam0, lam_end, false, gtab, s_load, S, isum);
+      else if (d == kMT) best = prefix_tile<MODE, kMT>(A, I, lam0, lam_end, false, gtab, s_load, S, isum);
+      else if (d == kRAD2) best = prefix_tile<MODE, kRAD2>(A, I, lam0, lam_end, false, gtab, s_load, S, isum);
+      else if (d == kCCM1) best = prefix_tile<MODE, kCCM1>(A, I, lam0, lam_end, false, gtab, s_load, S, isum);
+      else best = prefix_tile<MODE, kBJ1>(A, I, lam0, lam_end, with_fs1, gtab, s_load, S, nullptr);
     }
     __syncthreads();
     fold_and_finalize<kPrefixNT>(A, b, best, S.err != 0, ntiles, I, S.warp_key);

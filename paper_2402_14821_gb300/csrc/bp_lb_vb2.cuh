@@ -35,6 +35,7 @@ __global__ void __launch_bounds__(kVb2NT, vb2_minb(VT)) vb2_kernel(EvalArgs A) {
   uint32_t *s_load = reinterpret_cast<uint32_t *>(smem_raw + kVb2ListBytes);
 
   const int64_t total = A.vtile_start ? A.vtile_start[A.B] : A.single_vtiles;
+  work_count_begin(A, S);
   tile_first(A.vtile_start, A.B, total, A.vwork, cur);
   while (cur.tile < total) {
     const int64_t t = cur.tile, b = cur.inst;
@@ -51,20 +52,39 @@ __global__ void __launch_bounds__(kVb2NT, vb2_minb(VT)) vb2_kernel(EvalArgs A) {
     if (threadIdx.x == 0) {
       S.err = 0;
       S.skip = (vslot != nullptr && slot_decided(vslot, I.k)) ? 1 : 0;
+      // the whole tile pruned (vb2_range_may_exceed) from the instance sums the
+      // prefix kernel published, before anything is staged
+      if (!S.skip && A.isums != nullptr && (A.verdict || A.prune)) {
+        const volatile long long *is = A.isums + 8 * b;
+        if (is[7] == 1) {
+          __threadfence();
+          const int64_t cut = A.verdict ? I.k : (int64_t)vb2_cut(&A.keys[b], flat_index(kVB2, lo_d, I.c));
+          if (cut >= 0) {
+            const int64_t c = I.c;
+            const int64_t ns = is[0], nb = is[1], nh = is[2], nf = is[3], swb = is[4], sw = is[5];
+            const int64_t Dd = (sw - swb - nh * (c / 2) - nf * c) - (nb * c - swb);
+            const int64_t K = 2 * nb + nh + 2 * nf;
+            const int64_t kk = min(cut, stream_len<MODE>(I));
+            if (!vb2_range_may_exceed(lam0, lam_end - 1, kk, c, Dd, ns, nb, K)) S.skip = 1;
+          }
+        }
+      }
     }
     __syncthreads();
     unsigned long long best = 0ull;
     if (!S.skip) {
       node_loads<kVb2NT, MODE>(I, s_load, &S.err);
       __syncthreads();
-      best = tile_dff<kVb2NT, VT, kVB2, MODE, false, true>(A, I, lam0, lam_end, s_items, nullptr,
-                                                            s_load, S, nullptr, nullptr, -1, vslot);
+      best = tile_dff<kVb2NT, VT, kVB2, MODE, false, true>(
+          A, I, lam0, lam_end, s_items, nullptr, s_load, S, nullptr, nullptr, -1, vslot,
+          A.prune && !A.verdict ? &A.keys[b] : nullptr);
     }
     __syncthreads();
     fold_and_finalize<kVb2NT>(A, b, best, S.err != 0, ntiles, I, S.warp_key);
     if (!A.vwork) break;
     tile_publish(A.vtile_start, A.B, total, next, cur);
   }
+  work_count_flush(A, S);
 }
 
 }  // namespace bplb

@@ -83,17 +83,17 @@ def test_serve_rejects_bad_arguments_before_any_device_work(lib):
 
 def test_dff_route(lib):
     P, D = binding.ALGO_PREFIX, binding.ALGO_DIRECT
-    # VB2 and FS1 are always direct; MT/RAD2/CCM1/BJ1 go to the prefix tables
+    # VB2 is always direct; MT/RAD2/FS1/CCM1/BJ1 go to the prefix tables
     # (shared memory up to 48 KiB, else a 4 MiB global slice per CTA:
-    # BJ1 4 (c + 2) bytes; RAD2 8 ((c-1)/2 + 2); MT, CCM1 4 ((c-1)/2 + 2))
-    for d in (2, 4):
-        assert binding.bp_lb_dff_route(d, 1000, 500, P) == D
-    for d in (0, 1, 3, 5):
+    # FS1, BJ1 4 (c + 2) bytes; RAD2 8 ((c-1)/2 + 2); MT, CCM1 4 ((c-1)/2 + 2))
+    assert binding.bp_lb_dff_route(4, 1000, 500, P) == D
+    for d in (0, 1, 2, 3, 5):
         assert binding.bp_lb_dff_route(d, 10_000, 630, P) == P
         assert binding.bp_lb_dff_route(d, 10_000, 630, D) == D
         assert binding.bp_lb_dff_route(d, 100_000, 500, P) == P      # global tables
-    assert binding.bp_lb_dff_route(5, 1_048_574, 10, P) == P
-    assert binding.bp_lb_dff_route(5, 1_048_575, 10, P) == D
+    for d in (2, 5):
+        assert binding.bp_lb_dff_route(d, 1_048_574, 10, P) == P
+        assert binding.bp_lb_dff_route(d, 1_048_575, 10, P) == D
     assert binding.bp_lb_dff_route(1, 1_048_574, 10, P) == P
     assert binding.bp_lb_dff_route(1, 1_048_575, 10, P) == D
     for d in (0, 3):
@@ -101,4 +101,7 @@ def test_dff_route(lib):
         assert binding.bp_lb_dff_route(d, 2_097_151, 10, P) == D
     # reduced sizes that could sum past 2^31 stay direct
     assert binding.bp_lb_dff_route(3, 10_000, 300_000, P) == D
+    # FS1's count sum (at most 101 sum w / c) must fit 32 bits: streams below 2^25
+    assert binding.bp_lb_dff_route(2, 10, (1 << 25) - 1, P) == P
+    assert binding.bp_lb_dff_route(2, 10, 1 << 25, P) == D
     assert binding.bp_lb_dff_route(6, 10, 1, P) == -1
