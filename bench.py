@@ -467,6 +467,23 @@ def main():
     assert torch.equal(out_f, full_feasible)   # the same verdicts as the full maximum
     B.bp_lb_set_result_mode(h, B.RESULT_FULL)
     t_verdict = float(v_ms.mean())
+
+    # ---- the same batch with pruning off (identical results, all the work) ----
+    B.bp_lb_set_pruning(h, False)
+    for _ in range(3):
+        step()
+    barrier()
+    pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(min(args.steps, 30))]
+    for e0, e1 in pev:
+        flush.zero_()
+        e0.record(stream)
+        step()
+        e1.record(stream)
+    barrier()
+    t_noprune = float(np.mean([e0.elapsed_time(e1) for e0, e1 in pev]))
+    assert torch.equal(out_f, full_feasible)
+    B.bp_lb_set_pruning(h, True)
     if world > 1:
         import torch.distributed as dist
         t = torch.tensor([t_verdict], device=dev)
@@ -532,6 +549,8 @@ def main():
                             "bound is <= k skipped); same verdicts as the full maximum"},
         "pruning": {"vb2_params_evaluated": kwork[2] / calls, "vb2_params_pruned": kwork[3] / calls,
                     "vb2_pairs_evaluated": vb2_pairs,
+                    "off": {"value": NODES * world / (t_noprune / 1e3), "unit": UNIT,
+                            "ms_per_step": t_noprune},
                     "note": "exact: results identical with pruning off (bp_lb_set_pruning)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},

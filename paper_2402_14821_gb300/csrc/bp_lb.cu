@@ -251,6 +251,8 @@ int launch_batch(bp_lb *h, EvalArgs A, size_t smem, cudaStream_t st) {
   A.isums = h->d_isums;
   A.vtile_start = h->d_vtile_start;
   A.vwork = h->d_work + 2;
+  A.vlpt = reinterpret_cast<long long *>(h->d_work + 3);
+  A.vb2_target_tiles = (int64_t)h->num_sms * kVb2TilesPerSm;
   const int shape = h->shape[MODE];
   const int occ = occupancy(h, MODE, smem);
   if (occ <= 0) return BP_ECUDA;
@@ -407,10 +409,10 @@ int bp_lb_create(int64_t capacity, int64_t max_items, bp_lb_t **out) {
     if ((st = cuda_status(cudaMallocHost(&h->h_out, sizeof(PlainOut)))) != BP_OK) break;
     if ((st = cuda_status(cudaMalloc(&h->d_key1, sizeof(unsigned long long)))) != BP_OK) break;
     if ((st = cuda_status(cudaMalloc(&h->d_done1, sizeof(unsigned int)))) != BP_OK) break;
-    if ((st = cuda_status(cudaMalloc(&h->d_work, 3 * sizeof(unsigned long long)))) != BP_OK) break;
+    if ((st = cuda_status(cudaMalloc(&h->d_work, 4 * sizeof(unsigned long long)))) != BP_OK) break;
     if ((st = cuda_status(cudaMemset(h->d_key1, 0, sizeof(unsigned long long)))) != BP_OK) break;
     if ((st = cuda_status(cudaMemset(h->d_done1, 0, sizeof(unsigned int)))) != BP_OK) break;
-    if ((st = cuda_status(cudaMemset(h->d_work, 0, 3 * sizeof(unsigned long long)))) != BP_OK)
+    if ((st = cuda_status(cudaMemset(h->d_work, 0, 4 * sizeof(unsigned long long)))) != BP_OK)
       break;
     for (int mode = 0; mode < 3 && st == BP_OK; ++mode)
       st = cuda_status(cudaFuncSetAttribute((const void *)prefix_fn(mode),

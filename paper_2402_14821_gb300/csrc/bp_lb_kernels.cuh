@@ -85,6 +85,10 @@ struct EvalArgs {
   // the reduced instance, written by the prefix kernel; [7] = 1 once written
   // (cleared by the plan kernel).  nullptr: not kept.
   long long *isums;
+  // VB2 kernel tile length, chosen by the plan kernel (nullptr: kVb2LPT), and
+  // the number of VB2 tiles it aims at
+  long long *vlpt;
+  int64_t vb2_target_tiles;
 };
 
 // Shared-memory budget of the prefix-count tables (bytes; 48 KB lets four
@@ -136,8 +140,13 @@ BPLB_HD bool prefix_handles(int d, int64_t c, int64_t sum_bound, int32_t on) {
   return prefix_home(d, c, sum_bound, on) != 0;
 }
 
-// Parameters per tile of the VB2 kernel.
+// Parameters per tile of the VB2 kernel: at least kVb2LPT; longer (up to
+// kVb2MaxLPT, in multiples of 1024) when the batch has more than
+// vb2_target_tiles tiles' worth, so that tiles pruned whole (they only pass
+// through the scheduler) are few.
 constexpr int64_t kVb2LPT = 4096;
+constexpr int64_t kVb2MaxLPT = 65536;
+constexpr int64_t kVb2TilesPerSm = 24;
 
 // Which kernel evaluates DFF d of an instance: the prefix-count kernel
 // (prefix_handles), the VB2 kernel (VB2 on its fixed-point path), or the
@@ -348,6 +357,42 @@ __global__ void __launch_bounds__(1024)
     if (A.vwork) *A.vwork = 0ull;
   }
   __syncthreads();
+  // the VB2 tile length (vlpt): VB2's parameters of the whole batch over the
+  // target tile count
+  int64_t vlpt = kVb2LPT;
+  if (A.vlpt != nullptr && A.vb2_on) {
+    for (int64_t b0 = 0; b0 < A.B; b0 += blockDim.x) {
+      const int64_t b = b0 + threadIdx.x;
+      int64_t pv = 0;
+      if (b < A.B) {
+        int64_t c = 0, L = 0;
+        if (MODE == kSrcNodes) {
+          const int32_t base = A.node_base[b];
+          if (base >= 0 && base < A.num_base) {
+            c = A.base_capacity[base];
+            L = A.base_offsets[base + 1] - A.base_offsets[base] + A.bins[b];
+          }
+        } else {
+          c = A.capacity[b];
+          L = A.offsets[b + 1] - A.offsets[b];
+        }
+        if (c >= 1 && c <= kVb2FixedCap && L >= 0 &&
+            dff_kernel(kVB2, c, L * c, A.prefix_on, A.vb2_on, A.dff_off) == kRouteVb2)
+          pv = param_count(kVB2, c);
+      }
+      plan_scan(pv, s_warp, &s_carry[2]);
+    }
+    __syncthreads();
+    const int64_t tot = s_carry[2];
+    const int64_t want = (tot + max(A.vb2_target_tiles, (int64_t)1) - 1) / max(A.vb2_target_tiles, (int64_t)1);
+    vlpt = min(kVb2MaxLPT, max(kVb2LPT, (want + 1023) / 1024 * 1024));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      *A.vlpt = vlpt;
+      s_carry[2] = 0;
+    }
+    __syncthreads();
+  }
   for (int64_t b0 = 0; b0 < A.B; b0 += blockDim.x) {
     const int64_t b = b0 + threadIdx.x;
     int64_t tiles = 0, ptiles = 0, vtiles = 0;
@@ -375,7 +420,7 @@ __global__ void __launch_bounds__(1024)
       if (ok) {
         tiles = route_tiles(kRouteDirect, c, lpt, L * c, A.prefix_on, A.vb2_on, A.dff_off);
         ptiles = route_tiles(kRoutePrefix, c, A.plpt, L * c, A.prefix_on, A.vb2_on, A.dff_off);
-        vtiles = route_tiles(kRouteVb2, c, kVb2LPT, L * c, A.prefix_on, A.vb2_on, A.dff_off);
+        vtiles = route_tiles(kRouteVb2, c, vlpt, L * c, A.prefix_on, A.vb2_on, A.dff_off);
         // no parameter at all (only DFFs with an empty range left in): bound 0
         if (tiles + ptiles + vtiles == 0) write_result(A, b, 0ull, c, A.bins[b]);
       } else {
@@ -406,6 +451,7 @@ struct TileShared {
   int skip;     // verdict mode: the instance was decided before this tile
   int stop[2];  // verdict mode: decided before group g (double-buffered by g & 1)
   long long kcut[2];  // VB2 pruning: the cut of group g (double-buffered by g & 1)
+  int gskip[2];       // VB2 pruning: group g pruned whole
   unsigned long long wc[4];  // work counts of this CTA (EvalArgs::work_count)
   unsigned long long warp_key[32];
   long long sums[6];
@@ -705,9 +751,28 @@ __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int
       if (tid == 0) {
         if (vslot != nullptr) S.stop[g & 1] = slot_decided(vslot, I.k) ? 1 : 0;
         if (kprune) S.kcut[g & 1] = vb2_cut(kslot, gbase);
+        // the whole group pruned (vb2_range_may_exceed; the instance sums are
+        // complete after the first group)
+        S.gskip[g & 1] = 0;
+        if (D == kVB2 && c <= kVb2FixedCap && !S.err) {
+          const int64_t cut = vslot != nullptr ? I.k : (int64_t)S.kcut[g & 1];
+          if (cut >= 0) {
+            const int64_t ns_ = S.sums[0], nb_ = S.sums[1], nh_ = S.sums[2], nf_ = S.sums[3];
+            const int64_t swb = S.sums[4], sw = S.sums[5];
+            const int64_t Dd = (sw - swb - nh_ * (c / 2) - nf_ * c) - (nb_ * c - swb);
+            const int64_t K = 2 * nb_ + nh_ + 2 * nf_;
+            const int64_t gl0 = lam0 + (int64_t)g * GW;
+            const int64_t gl1 = min(lam_end, gl0 + GW) - 1;
+            if (!vb2_range_may_exceed(gl0, gl1, min(cut, L), c, Dd, ns_, nb_, K)) {
+              S.gskip[g & 1] = 1;
+              if (A.work_count != nullptr) atomicAdd(&S.wc[3], (unsigned long long)(gl1 - gl0 + 1));
+            }
+          }
+        }
       }
       __syncthreads();
       if (vslot != nullptr && S.stop[g & 1]) break;
+      if (S.gskip[g & 1]) continue;
     }
     // ---- this group's parameters and their constants -------------------------
     int64_t lam[T];

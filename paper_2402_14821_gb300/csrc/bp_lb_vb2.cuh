@@ -9,7 +9,8 @@
 // kernel evaluates the VB2 tiles alone, with the same tile evaluation
 // (tile_dff) compiled for VB2's fixed-point path only, so that its register
 // footprint -- and hence its resident warps -- are VB2's own.  Tiles carry
-// kVb2LPT consecutive parameters of one instance; finalisation is shared with
+// vlpt consecutive parameters of one instance (the plan kernel's choice,
+// kVb2LPT at least); finalisation is shared with
 // the other kernels through the instance's key slot and finished-tile ticket.
 #pragma once
 
@@ -35,6 +36,7 @@ __global__ void __launch_bounds__(kVb2NT, vb2_minb(VT)) vb2_kernel(EvalArgs A) {
   uint32_t *s_load = reinterpret_cast<uint32_t *>(smem_raw + kVb2ListBytes);
 
   const int64_t total = A.vtile_start ? A.vtile_start[A.B] : A.single_vtiles;
+  const int64_t vlpt = A.vlpt != nullptr ? (int64_t)*A.vlpt : kVb2LPT;
   work_count_begin(A, S);
   tile_first(A.vtile_start, A.B, total, A.vwork, cur);
   while (cur.tile < total) {
@@ -45,8 +47,8 @@ __global__ void __launch_bounds__(kVb2NT, vb2_minb(VT)) vb2_kernel(EvalArgs A) {
     const int64_t ntiles = instance_tiles(A, b);
     int64_t lo_d, hi_d;
     param_range(kVB2, I.c, lo_d, hi_d);
-    const int64_t lam0 = lo_d + (t - t0) * kVb2LPT;
-    const int64_t lam_end = min(hi_d + 1, lam0 + kVb2LPT);
+    const int64_t lam0 = lo_d + (t - t0) * vlpt;
+    const int64_t lam_end = min(hi_d + 1, lam0 + vlpt);
 
     unsigned long long *vslot = A.verdict ? &A.keys[b] : nullptr;
     if (threadIdx.x == 0) {
@@ -65,7 +67,10 @@ __global__ void __launch_bounds__(kVb2NT, vb2_minb(VT)) vb2_kernel(EvalArgs A) {
             const int64_t Dd = (sw - swb - nh * (c / 2) - nf * c) - (nb * c - swb);
             const int64_t K = 2 * nb + nh + 2 * nf;
             const int64_t kk = min(cut, stream_len<MODE>(I));
-            if (!vb2_range_may_exceed(lam0, lam_end - 1, kk, c, Dd, ns, nb, K)) S.skip = 1;
+            if (!vb2_range_may_exceed(lam0, lam_end - 1, kk, c, Dd, ns, nb, K)) {
+              S.skip = 1;
+              if (A.work_count != nullptr) atomicAdd(&S.wc[3], (unsigned long long)(lam_end - lam0));
+            }
           }
         }
       }
