@@ -63,7 +63,7 @@ TRAFFIC_BYTES_PER_NODE = {"prefix": None, "vb2": None, "direct": None}
 # 32-bit words -- zeroing, histogram updates, three accesses per entry and
 # scan, and the lookups of every parameter it does not prune (csrc/
 # bp_lb_prefix.cuh) -- against one 32-lane word access per SM per clock.
-PREFIX_CTA_BLOCKS, PREFIX_WARP_BLOCKS, PREFIX_MAX_HEAVY = 1024, 32, 256
+PREFIX_CTA_BLOCKS, PREFIX_WARP_BLOCKS, PREFIX_MAX_HEAVY, PREFIX_PRUNE_MIN = 1024, 32, 256, 4
 
 
 def param_counts(c):
@@ -78,6 +78,11 @@ def reduced_sizes(nd):
         a = nd.assign[nd.assign_offsets[j]:nd.assign_offsets[j + 1]]
         r[j] = int(np.sum(a == -1)) + len(np.unique(a[a >= 0]))
     return r
+
+
+def _warp_end(X):
+    """First parameter of the prefix kernel's thread phase (CCM1: X = U, BJ1: X = c)."""
+    return max(min(X // PREFIX_CTA_BLOCKS + 1, 1 + PREFIX_MAX_HEAVY), X // PREFIX_WARP_BLOCKS + 1)
 
 
 def prefix_smem_words(nd, prune=True):
@@ -105,15 +110,17 @@ def prefix_smem_words(nd, prune=True):
         kS = 2 * nb + nh + 2 * nf
         key = (c, sumw)
         if key not in cache:
+            # BJ1: one lookup per multiple of l (the D table), none when c mod l
+            # = 0; pruned in the CTA and warp phases, and in the thread phase
+            # when it has at least PREFIX_PRUNE_MIN terms
             lam = np.arange(1, c + 1, dtype=np.int64)
             q, cm = c // lam, c % lam
-            keep = (cm > 0) & ~(prune & (L1 * (c - cm) >= sumw))
-            heavy = lam < max(min(c // PREFIX_CTA_BLOCKS + 1, 1 + PREFIX_MAX_HEAVY),
-                              c // PREFIX_WARP_BLOCKS + 1)
-            bj1 = np.where(heavy, 2 * ((c - 1) // lam + 1), 2 * q)
+            heavy = lam < _warp_end(c)
+            cut = prune & (L1 * (c - cm) >= sumw) & (heavy | (q >= PREFIX_PRUNE_MIN))
+            keep = (cm > 0) & ~cut
             lp = np.arange(2, 102)
             fs1 = 2 * int(lp.sum()) + 2 * int(sum(np.gcd(c, lp)))
-            cache[key] = int(bj1[keep].sum()) + fs1
+            cache[key] = int(q[keep].sum()) + fs1 + 4 * (c // 2 + 1)   # + NN -> D
         # node loads, once per tile: zero k, one atomic per packed item, read k
         loads_words = 2 * (k + n_as + k)
         # u group: E and packed counts (zero, 2 updates per small or big item,
@@ -121,7 +128,8 @@ def prefix_smem_words(nd, prune=True):
         lam = np.arange(1, c // 2 + 1, dtype=np.int64)
         q = c // lam
         ccm1_keep = ~(prune & (2 * sws - 2 * sub + 2 * nb * (lam - 1) + q * lam * kS
-                               <= 2 * q * lam * L1))
+                               <= 2 * q * lam * L1)
+                      & ((lam < _warp_end(U)) | (q >= PREFIX_PRUNE_MIN)))
         ccm1 = int((U // lam)[ccm1_keep].sum())
         pc = param_counts(c)
         u_words = 2 * nU + 2 * (len(small) + nb) + 6 * nU + pc[0] + 3 * pc[1] + ccm1

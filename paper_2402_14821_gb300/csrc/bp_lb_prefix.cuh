@@ -17,7 +17,12 @@
 //         since floor(u / l) counts the multiples j l <= u;
 //   BJ1:  cm q + min(rho, cm) (w = q l + rho) counts the x <= w in the union
 //         of the blocks [j l + 1, j l + cm], j >= 0, so summed over the items
-//         it is sum_j (NN(j l + 1) - NN(j l + cm + 1)) over j = 0 .. floor(c / l);
+//         it is sum_j (NN(j l + 1) - NN(j l + cm + 1)) over j = 0 .. floor(c / l),
+//         and S = sum w minus that.  With q = floor(c / l), j l + cm + 1 =
+//         c + 1 - (q - j) l, NN(1) = sum w and NN(c + 1) = 0, the terms pair up
+//         into S = sum_{i=1}^{q} D(i l), D(x) = NN(c + 1 - x) - NN(1 + x): one
+//         lookup per multiple of l, like CCM1.  D overwrites NN in place (the
+//         pair x, c - x reads and writes the same two entries) once FS1 is done;
 //   FS1:  with l' = l + 1, w maps to w l when c divides w l', else to
 //         floor(w l' / c) c, so S = c sum_w floor(w l' / c) - sum_{c | w l'} w;
 //         floor(w l' / c) counts the j in [1, l'] with w >= ceil(j c / l'), and
@@ -49,6 +54,10 @@ constexpr int kPrefixWarps = kPrefixNT / 32;
 constexpr uint32_t kCtaBlocks = 1024;
 constexpr uint32_t kWarpBlocks = 32;
 constexpr int kMaxHeavy = kPrefixNT;
+// Parameters with fewer terms than this are evaluated without the pruning test.
+constexpr uint32_t kPruneMinTerms = 4;
+// Consecutive parameters per thread in the last phase of CCM1 and BJ1.
+constexpr uint32_t kRun = 8;
 // FS1's parameters l in [1, 100] (param_range)
 constexpr int kFs1Params = 100;
 
@@ -62,6 +71,11 @@ struct PrefixShared {
   uint32_t heavy_cm[kMaxHeavy];
   uint32_t fs1_cnt[kFs1Params];  // FS1: per parameter, sum_j N(ceil(j c / l'))
   uint32_t fs1_dv[kFs1Params];   //      and the multiples' sum
+  uint32_t fs1_cq[kFs1Params], fs1_cr[kFs1Params], fs1_mg[kFs1Params];  // c = cq l' + cr; 2^20 / l' up
+  // the tile, decoded by thread 0: DFF (or the u group), table home, FS1 on
+  // this tile, the u group's members (bit d), lambda range
+  int dec_d, dec_home, dec_fs1, dec_umask;
+  long long dec_lam0, dec_lam_end;
 };
 
 // Sum of v over the threads after this one (higher threadIdx.x).  wtot must
@@ -139,52 +153,62 @@ __device__ __forceinline__ int32_t np_at(const int32_t *T, uint32_t x) {
 }
 
 // Strided lookup blocks b0, b0 + bs, ... of one parameter (D = CCM1 or BJ1):
-//   CCM1: block b is x = (b + 1) l <= U, term N'(x);
-//   BJ1:  block b is x = b l + 1 <= c, term NN(x) - NN(x + cm)  (cm > 0).
-// Unrolled by two with explicit bounds (no trip-count division).
+// block b is the multiple x = (b + 1) l <= X, its term N'(x) (CCM1, X = U) or
+// D(x) at entry 1 + x (BJ1, X = c).  Unrolled by two with explicit bounds (no
+// trip-count division).
 template <int D, bool PACKED>
-__device__ __forceinline__ uint32_t block_terms(const int32_t *T, uint32_t c32, uint32_t U,
-                                                uint32_t l, uint32_t cm, uint32_t b0, uint32_t bs) {
+__device__ __forceinline__ uint32_t block_terms(const int32_t *T, uint32_t X, uint32_t l,
+                                                uint32_t b0, uint32_t bs) {
+  constexpr uint32_t OFF = (D == kBJ1) ? 1u : 0u;
   const uint32_t step = bs * l;
   uint32_t acc = 0;
-  if (D == kCCM1) {
-    uint32_t x = (b0 + 1u) * l;
-    for (; x + step <= U; x += 2u * step)
-      acc += (uint32_t)np_at<PACKED>(T, x) + (uint32_t)np_at<PACKED>(T, x + step);
-    if (x <= U) acc += (uint32_t)np_at<PACKED>(T, x);
-  } else {
-    uint32_t x = b0 * l + 1u;
-    const int32_t *T2 = T + cm;
-    for (; x + step <= c32; x += 2u * step)
-      acc += (uint32_t)(T[x] - T2[x]) + (uint32_t)(T[x + step] - T2[x + step]);
-    if (x <= c32) acc += (uint32_t)(T[x] - T2[x]);
-  }
+  uint32_t x = (b0 + 1u) * l;
+  for (; x + step <= X; x += 2u * step)
+    acc += (uint32_t)np_at<PACKED>(T, x + OFF) + (uint32_t)np_at<PACKED>(T, x + step + OFF);
+  if (x <= X) acc += (uint32_t)np_at<PACKED>(T, x + OFF);
   return acc;
 }
 
-// BJ1 accumulator of one parameter from its blocks j = 0 .. q (cm > 0).  The
-// outer two lookups are known: NN(1) = sum w, and block q ends at
-// q l + cm + 1 = c + 1 where NN is 0, so
-//   acc = sum w - NN(cm + 1) + NN(q l + 1) + sum_{j=1}^{q-1} (NN(j l + 1) - NN(j l + cm + 1)).
-__device__ __forceinline__ uint32_t bj1_blocks(const int32_t *T, uint32_t sumw, uint32_t l,
-                                               uint32_t cm, uint32_t q) {
-  uint32_t acc = sumw - (uint32_t)T[cm + 1u] + (uint32_t)T[q * l + 1u];
-  uint32_t x = l + 1u;
-  const uint32_t xe = q * l + 1u;  // first x past the inner blocks
-  for (; x + l < xe; x += 2u * l)
-    acc += (uint32_t)(T[x] - T[x + cm]) + (uint32_t)(T[x + l] - T[x + l + cm]);
-  if (x < xe) acc += (uint32_t)(T[x] - T[x + cm]);
+// Sum of the terms at the first m multiples of l: N'(i l) (CCM1) or D(i l)
+// at entry 1 + i l (BJ1), i = 1 .. m; unrolled by four.
+template <int D, bool PACKED>
+__device__ __forceinline__ uint32_t harmonic_sum(const int32_t *T, uint32_t l, uint32_t m) {
+  constexpr uint32_t OFF = (D == kBJ1) ? 1u : 0u;
+  const uint32_t l2 = 2u * l;
+  if (m <= 3u) {
+    uint32_t acc = m >= 1u ? (uint32_t)np_at<PACKED>(T, l + OFF) : 0u;
+    if (m >= 2u) acc += (uint32_t)np_at<PACKED>(T, l2 + OFF);
+    if (m == 3u) acc += (uint32_t)np_at<PACKED>(T, l2 + l + OFF);
+    return acc;
+  }
+  uint32_t acc = 0, x = l + OFF, i = 0;
+  for (; i + 4u <= m; i += 4u, x += 2u * l2)
+    acc += (uint32_t)np_at<PACKED>(T, x) + (uint32_t)np_at<PACKED>(T, x + l) +
+           (uint32_t)np_at<PACKED>(T, x + l2) + (uint32_t)np_at<PACKED>(T, x + l2 + l);
+  for (; i < m; ++i, x += l) acc += (uint32_t)np_at<PACKED>(T, x);
   return acc;
+}
+
+// NN -> D in place (file comment): D(x) = NN(c + 1 - x) - NN(1 + x) at entry
+// 1 + x, x in [0, c]; the pair (x, c - x) owns entries 1 + x and c + 1 - x.
+__device__ __forceinline__ void nn_to_d(int32_t *T, uint32_t c32) {
+  for (uint32_t x = threadIdx.x; 2u * x <= c32; x += kPrefixNT) {
+    const int32_t a = T[1u + x], b = T[c32 + 1u - x];
+    T[1u + x] = b - a;
+    T[c32 + 1u - x] = a - b;
+  }
+  __syncthreads();
 }
 
 // The candidate test (file comment): divide only when S > B f, or for the
-// thread's first parameter (so that a bound is kept even when no parameter
-// beats B, e.g. with MT left out of the bound and B starting at 0).  Every
-// sum and denominator here is below 2^32 (prefix_handles), so all is 32-bit
-// except the product.
+// thread's first parameter when there is no floor (B = 0: MT left out of the
+// bound, or L1 = 0), so that a bound is kept even when no parameter beats B.
+// With the floor L1 a thread may keep nothing: every bound it saw is <= L1,
+// which MT's l = 0 holds with the smallest index.  Every sum and denominator
+// here is below 2^32 (prefix_handles), so all is 32-bit except the product.
 __device__ __forceinline__ void try_key(uint32_t S, uint32_t f, uint32_t g, uint32_t &B,
                                         unsigned long long &best) {
-  if ((uint64_t)B * f < (uint64_t)S || best == 0ull) {
+  if ((uint64_t)B * f < (uint64_t)S || (best == 0ull && B == 0u)) {
     const uint32_t q = S / f;
     const uint32_t lb = q + (S != q * f);
     B = max(B, lb);
@@ -302,9 +326,17 @@ __device__ __forceinline__ void eval_fs1(const int32_t *T, int64_t c, PrefixEval
     uint32_t j = P - tri(l) + 1u;
     while (p < pe) {
       const uint32_t lp = l + 1u;
-      const uint32_t cq = c32 / lp, cr = c32 - cq * lp;
-      uint32_t q = (j * c32) / lp;
-      uint32_t r = j * c32 - q * lp;
+      // j c = q l' + r from the per-parameter constants: j cr < l'^2 <= 10201,
+      // so its quotient by l' from the rounded-up 2^20 / l' is within one
+      const uint32_t cq = S.fs1_cq[l - lo], cr = S.fs1_cr[l - lo];
+      const uint32_t n = j * cr;
+      uint32_t t = (n * S.fs1_mg[l - lo]) >> 20;
+      uint32_t r = n - t * lp;
+      if ((int32_t)r < 0) {
+        --t;
+        r += lp;
+      }
+      uint32_t q = j * cq + t;
       const uint32_t j0 = j, jend = min(lp, j + (pe - p) - 1u);
       uint32_t cnt = 0, dv = 0;
       for (;;) {
@@ -336,7 +368,7 @@ __device__ __forceinline__ void eval_fs1(const int32_t *T, int64_t c, PrefixEval
     const uint32_t l = lo + threadIdx.x;
     const uint64_t Sv = (uint64_t)c32 * S.fs1_cnt[threadIdx.x] - S.fs1_dv[threadIdx.x];
     const uint64_t f = (uint64_t)c32 * l;
-    if ((uint64_t)x.B * f < Sv || x.best == 0ull) {
+    if ((uint64_t)x.B * f < Sv || (x.best == 0ull && x.B == 0u)) {
       const uint64_t qv = Sv / f;
       const uint32_t lb = (uint32_t)(qv + (Sv != qv * f));
       x.B = max(x.B, lb);
@@ -355,7 +387,7 @@ __device__ void eval_harmonic(const int32_t *T0, int64_t lam0, int64_t lam_end, 
   int64_t lo_d, hi_d;
   param_range(D, c, lo_d, hi_d);
   const uint32_t gofs = flat_index(D, lo_d, c) - (uint32_t)lo_d;
-  //   CCM1: S = 2 acc + q kS, f = 2q;   BJ1: S = sumw - acc, f = q (l - cm)
+  //   CCM1: S = 2 acc + q kS, f = 2q;   BJ1: S = acc (sum w when cm = 0), f = q (l - cm)
   const uint32_t kS = (D == kCCM1) ? 2u * x.n_big + x.n_half + 2u * x.n_full : x.sumw;
   const uint32_t le = (uint32_t)lam_end;
   const uint32_t X = (D == kCCM1) ? U : c32;
@@ -368,8 +400,9 @@ __device__ void eval_harmonic(const int32_t *T0, int64_t lam0, int64_t lam_end, 
       Sv = 2u * acc + q * kS;
       f = 2u * q;
     } else {
-      Sv = kS - acc;
-      f = q * (l - (c32 - q * l));  // q (l - cm) <= c
+      const uint32_t cm = c32 - q * l;
+      Sv = cm == 0u ? kS : acc;
+      f = q * (l - cm);  // <= c
     }
     try_key(Sv, f, gofs + l, x.B, x.best);
   };
@@ -392,9 +425,9 @@ __device__ void eval_harmonic(const int32_t *T0, int64_t lam0, int64_t lam_end, 
     for (int i = 0; i < ncta; ++i) {
       const uint32_t l = (uint32_t)(lam0 + i);
       const uint32_t cm = S.heavy_cm[i];
-      if (cm == kPruned || (D == kBJ1 && cm == 0u)) continue;  // cm = 0: every BJ1 term is 0
+      if (cm == kPruned || (D == kBJ1 && cm == 0u)) continue;  // BJ1, cm = 0: S = sum w
       const uint32_t part = __reduce_add_sync(
-          0xFFFFFFFFu, block_terms<D, PACKED>(T0, c32, U, l, cm, (uint32_t)tid, kPrefixNT));
+          0xFFFFFFFFu, block_terms<D, PACKED>(T0, X, l, (uint32_t)tid, kPrefixNT));
       if (lane == 0 && part != 0u) atomicAdd(&S.heavy_acc[i], part);
     }
     __syncthreads();
@@ -427,37 +460,50 @@ __device__ void eval_harmonic(const int32_t *T0, int64_t lam0, int64_t lam_end, 
         const bool ok = __shfl_sync(0xFFFFFFFFu, (int)mine_ok, t) != 0;
         if (!ok || (D == kBJ1 && cm == 0u)) continue;
         const uint32_t part = __reduce_add_sync(
-            0xFFFFFFFFu, block_terms<D, PACKED>(T0, c32, U, l, cm, (uint32_t)lane, 32u));
+            0xFFFFFFFFu, block_terms<D, PACKED>(T0, X, l, (uint32_t)lane, 32u));
         if (lane == t) mine = part;
       }
       if (mine_ok) finish(ml, mq, mine);
     }
   }
 
-  // ---- one thread per parameter; alternate directions balance the rounds --------
-  // A thread's parameters increase, so its quotient q = floor(c / l) only
-  // needs decrementing after the first division.
+  // ---- one thread per run of kRun parameters -----------------------------------------
+  // Warp blocks of 32 kRun consecutive lambdas from warp_end on; round i gives
+  // warp w the block i kPrefixWarps + w (i even) or + kPrefixWarps - 1 - w (i
+  // odd), so that the warps' loads balance, and lane t of it the lambdas
+  // base + t + 32 k, k < kRun: a thread's parameters increase, and at each
+  // step the warp reads consecutive lambdas' terms.  One division per run for
+  // q = floor(c / l) and m = floor(X / l) (the number of terms), decrements
+  // after it.  The pruning tests (prune_bj1, prune_ccm1) in their linear forms
+  // with per-thread constants, and only for parameters with many terms.
   {
-    uint32_t q = 0;
-    bool first = true, odd = false;
-    for (uint32_t r = (uint32_t)warp_end; r < le; r += kPrefixNT, odd = !odd) {
-      const uint32_t l = r + (odd ? kPrefixNT - 1 - tid : tid);
-      if (l >= le) continue;
-      if (first) {
-        q = c32 / l;
-        first = false;
-      } else {
-        while (q * l > c32) --q;
+    const int64_t A0 = 2 * ((int64_t)x.sumw - x.sumw_big - (int64_t)x.n_half * (c32 / 2u) -
+                            (int64_t)x.n_full * c32 - (int64_t)x.TB - (int64_t)x.n_big);
+    const int64_t A1 = 2 * (int64_t)x.n_big;
+    const int64_t A2 = 2 * (int64_t)x.L1 - (int64_t)kS;
+    constexpr uint32_t kBlock = 32u * kRun;
+    bool odd = false;
+    for (uint32_t r0 = (uint32_t)warp_end; r0 < le; r0 += kBlock * kPrefixWarps, odd = !odd) {
+      const uint32_t wb = odd ? (uint32_t)(kPrefixWarps - 1 - warp) : (uint32_t)warp;
+      const uint32_t l0 = r0 + wb * kBlock + (uint32_t)lane;
+      if (l0 >= le) continue;
+      uint32_t q = c32 / l0, m = (D == kCCM1) ? U / l0 : 0u;
+      for (uint32_t l = l0; l < le && l < l0 + kBlock; l += 32u) {
+        while (q * l > c32) --q;  // q l <= c (l0 + kBlock) / l0 < 2^32 here
+        if (D == kCCM1) {
+          while (m * l > U) --m;
+        } else {
+          m = q;
+        }
+        if (x.prune && m >= kPruneMinTerms) {
+          const bool cut = (D == kBJ1) ? (uint64_t)x.L1 * (uint64_t)(q * l) >= (uint64_t)x.sumw
+                                       : A0 + A1 * (int64_t)l <= (int64_t)(q * l) * A2;
+          if (cut) continue;
+        }
+        uint32_t acc = 0;
+        if (D == kCCM1 || q * l != c32) acc = harmonic_sum<D, PACKED>(T0, l, m);
+        finish(l, q, acc);
       }
-      if (pruned(l, q, c32 - q * l)) continue;
-      uint32_t acc = 0;
-      if (D == kCCM1) {
-        acc = block_terms<D, PACKED>(T0, c32, U, l, 0u, 0u, 1u);
-      } else {
-        const uint32_t cm = c32 - q * l;
-        if (cm != 0u) acc = bj1_blocks(T0, x.sumw, l, cm, q);
-      }
-      finish(l, q, acc);
     }
   }
 }
@@ -471,7 +517,8 @@ __device__ void eval_harmonic(const int32_t *T0, int64_t lam0, int64_t lam_end, 
 template <int MODE, int D>
 __device__ __forceinline__ unsigned long long prefix_tile(const EvalArgs &A, const InstView &I,
                                                           int64_t lam0, int64_t lam_end,
-                                                          bool with_fs1, int32_t *tab,
+                                                          bool with_fs1, uint32_t umask,
+                                                          int32_t *tab,
                                                           uint32_t *s_load, PrefixShared &S,
                                                           long long *isum_out) {
   const int tid = threadIdx.x;
@@ -491,8 +538,13 @@ __device__ __forceinline__ unsigned long long prefix_tile(const EvalArgs &A, con
     for (int64_t j = tid; j < I.k; j += kPrefixNT) s_load[j] = 0u;
   if (tid < 8) S.sums[tid] = 0;
   if (D == kBJ1 && with_fs1 && tid < kFs1Params) {
+    // FS1's parameters l = tid + 1 (l' = tid + 2)
+    const uint32_t lp = (uint32_t)tid + 2u, cq = c32 / lp;
     S.fs1_cnt[tid] = 0u;
     S.fs1_dv[tid] = 0u;
+    S.fs1_cq[tid] = cq;
+    S.fs1_cr[tid] = c32 - cq * lp;
+    S.fs1_mg[tid] = ((1u << 20) + lp - 1u) / lp;
   }
   __syncthreads();
 
@@ -592,17 +644,14 @@ __device__ __forceinline__ unsigned long long prefix_tile(const EvalArgs &A, con
   x.best = 0ull;
 
   if (D == kBJ1 && with_fs1) eval_fs1(T0, c, x, S);  // FS1 precedes BJ1 in paper order
+  if (D == kBJ1 && lam0 < lam_end) nn_to_d(T0, c32);   // FS1's lookups are done
   if (D == kMT) eval_mt(T0, lam0, lam_end, c, x);
   if (D == kRAD2) eval_rad2<false>(T0, T1, lam0, lam_end, c, x);
   if (D == kCCM1 || D == kBJ1) eval_harmonic<D, false>(T0, lam0, lam_end, c, x, S);
   if (D == kPrefixU) {
     // the members in paper order, so that each thread meets its parameters in
     // increasing flattened index
-    const int64_t sb = sum_bound<MODE>(I);
-    auto member = [&](int d) {
-      return param_count(d, c) > 0 &&
-             dff_kernel(d, c, sb, A.prefix_on, A.vb2_on, A.dff_off) == kRoutePrefix;
-    };
+    auto member = [&](int d) { return ((umask >> d) & 1u) != 0u; };
     int64_t lo, hi;
     if (member(kMT)) {
       param_range(kMT, c, lo, hi);
@@ -640,58 +689,71 @@ __global__ void __launch_bounds__(kPrefixNT, 4) prefix_kernel(EvalArgs A) {
     const InstView I = resolve_instance<MODE>(A, b);
     const int64_t t0 = A.ptile_start ? A.ptile_start[b] : 0;
     const int64_t ntiles = instance_tiles(A, b);
-    // which DFF (or the merged u group) and lambdas; tables in shared memory
-    // or in this CTA's slice of the global scratch
-    int64_t rem = t - t0;
-    int d = 0;
-    const int64_t sb = sum_bound<MODE>(I);
-    const bool merged = prefix_u_merged(I.c, sb, A.prefix_on, A.vb2_on, A.dff_off, A.plpt);
-    const bool wmerged = prefix_w_merged(I.c, sb, A.prefix_on, A.vb2_on, A.dff_off);
-    if (merged && rem == 0) {
-      d = kPrefixU;
-    } else {
-      if (merged) rem -= 1;  // the u group's tile comes first
-      for (d = 0; d < kNumDff; ++d) {
-        if (merged && (d == kMT || d == kRAD2 || d == kCCM1)) continue;
-        if (wmerged && d == kFS1) continue;
-        if (dff_kernel(d, I.c, sb, A.prefix_on, A.vb2_on, A.dff_off) != kRoutePrefix) continue;
-        const int64_t nt = prefix_dff_tiles(d, I.c, sb, A.prefix_on, A.plpt);
-        if (rem < nt) break;
-        rem -= nt;
-      }
-    }
-    const int home = (d == kPrefixU) ? prefix_u_home(I.c, A.prefix_on)
-                                     : prefix_home(d, I.c, sb, A.prefix_on);
-    int32_t *gtab = A.gscratch + (size_t)blockIdx.x * (size_t)kGlobalTableInts;
-    int64_t lo_d = 0, hi_d = -1;
-    if (d != kPrefixU && d != kFS1) param_range(d, I.c, lo_d, hi_d);
-    const int64_t lpt = (home == 2) ? hi_d - lo_d + 1 : A.plpt;  // global tables: one tile
-    const int64_t lam0 = lo_d + rem * lpt;
-    const int64_t lam_end = min(hi_d + 1, lam0 + lpt);
-    // FS1 on BJ1's table: on its own tile (empty BJ1 range) or BJ1's first
-    const bool with_fs1 = d == kFS1 || (wmerged && d == kBJ1 && rem == 0);
-    long long *isum = A.isums != nullptr ? A.isums + 8 * b : nullptr;
-
+    // which DFF (or the merged u group) and lambdas, tables in shared memory
+    // or in this CTA's slice of the global scratch: decoded by thread 0
     if (threadIdx.x == 0) {
+      int64_t rem = t - t0;
+      int d = 0;
+      const int64_t sb = sum_bound<MODE>(I);
+      const bool merged = prefix_u_merged(I.c, sb, A.prefix_on, A.vb2_on, A.dff_off, A.plpt);
+      const bool wmerged = prefix_w_merged(I.c, sb, A.prefix_on, A.vb2_on, A.dff_off);
+      if (merged && rem == 0) {
+        d = kPrefixU;
+      } else {
+        if (merged) rem -= 1;  // the u group's tile comes first
+        for (d = 0; d < kNumDff; ++d) {
+          if (merged && (d == kMT || d == kRAD2 || d == kCCM1)) continue;
+          if (wmerged && d == kFS1) continue;
+          if (dff_kernel(d, I.c, sb, A.prefix_on, A.vb2_on, A.dff_off) != kRoutePrefix) continue;
+          const int64_t nt = prefix_dff_tiles(d, I.c, sb, A.prefix_on, A.plpt);
+          if (rem < nt) break;
+          rem -= nt;
+        }
+      }
+      const int home = (d == kPrefixU) ? prefix_u_home(I.c, A.prefix_on)
+                                       : prefix_home(d, I.c, sb, A.prefix_on);
+      int64_t lo_d = 0, hi_d = -1;
+      if (d != kPrefixU && d != kFS1) param_range(d, I.c, lo_d, hi_d);
+      const int64_t lpt = (home == 2) ? hi_d - lo_d + 1 : A.plpt;  // global tables: one tile
+      const int64_t lam0 = lo_d + rem * lpt;
+      int umask = 0;
+      if (d == kPrefixU)
+        for (int u = 0; u < 4; ++u)
+          if (u != kFS1 && param_count(u, I.c) > 0 &&
+              dff_kernel(u, I.c, sb, A.prefix_on, A.vb2_on, A.dff_off) == kRoutePrefix)
+            umask |= 1 << u;
+      S.dec_d = d;
+      S.dec_home = home;
+      // FS1 on BJ1's table: on its own tile (empty BJ1 range) or BJ1's first
+      S.dec_fs1 = (d == kFS1 || (wmerged && d == kBJ1 && rem == 0)) ? 1 : 0;
+      S.dec_umask = umask;
+      S.dec_lam0 = lam0;
+      S.dec_lam_end = min(hi_d + 1, lam0 + lpt);
       S.err = 0;
       S.skip = (A.verdict && slot_decided(&A.keys[b], I.k)) ? 1 : 0;
     }
     __syncthreads();
+    const int d = S.dec_d, home = S.dec_home;
+    const bool with_fs1 = S.dec_fs1 != 0;
+    const int64_t lam0 = S.dec_lam0, lam_end = S.dec_lam_end;
+    const uint32_t umask = (uint32_t)S.dec_umask;
+    int32_t *gtab = A.gscratch + (size_t)blockIdx.x * (size_t)kGlobalTableInts;
+    long long *isum = A.isums != nullptr ? A.isums + 8 * b : nullptr;
     unsigned long long best = 0ull;
     // one instantiation per table space, so that shared-memory tables are
     // accessed with shared-memory instructions
     if (!S.skip && home != 2) {
-      if (d == kPrefixU) best = prefix_tile<MODE, kPrefixU>(A, I, lam0, lam_end, false, stab, s_load, S, isum);
-      else if (d == kMT) best = prefix_tile<MODE, kMT>(A, I, lam0, lam_end, false, stab, s_load, S, isum);
-      else if (d == kRAD2) best = prefix_tile<MODE, kRAD2>(A, I, lam0, lam_end, false, stab, s_load, S, isum);
-      else if (d == kCCM1) best = prefix_tile<MODE, kCCM1>(A, I, lam0, lam_end, false, stab, s_load, S, isum);
-      else best = prefix_tile<MODE, kBJ1>(A, I, lam0, lam_end, with_fs1, stab, s_load, S, nullptr);
+      if (d == kPrefixU) best = prefix_tile<MODE, kPrefixU>(A, I, lam0, lam_end, false, umask, stab, s_load, S, isum);
+      else if (d == kMT) best = prefix_tile<MODE, kMT>(A, I, lam0, lam_end, false, umask, stab, s_load, S, isum);
+      else if (d == kRAD2) best = prefix_tile<MODE, kRAD2>(A, I, lam0, lam_end, false, umask, stab, s_load, S, isum);
+      else if (d == kCCM1) best = prefix_tile<MODE, kCCM1>(A, I, lam0, lam_end, false, umask, stab, s_load, S, isum);
+      else best = prefix_tile<MODE, kBJ1>(A, I, lam0, lam_end, with_fs1, 0u, stab, s_load, S, nullptr);
     } else if (!S.skip) {
-      if (d == kPrefixU) best = prefix_tile<MODE, kPrefixU>(A, I, lam0, lam_end, false, gtab, s_load, S, isum);
-      else if (d == kMT) best = prefix_tile<MODE, kMT>(A, I, lam0, lam_end, false, gtab, s_load, S, isum);
-      else if (d == kRAD2) best = prefix_tile<MODE, kRAD2>(A, I, lam0, lam_end, false, gtab, s_load, S, isum);
-      else if (d == kCCM1) best = prefix_tile<MODE, kCCM1>(A, I, lam0, lam_end, false, gtab, s_load, S, isum);
-      else best = prefix_tile<MODE, kBJ1>(A, I, lam0, lam_end, with_fs1, gtab, s_load, S, nullptr);
+      if (d == kPrefixU) best = prefix_tile<MODE, kPrefixU>(A, I, lam0, lam_end, false, umask, gtab, s_load, S, isum);
+      else if (d == kMT) best = prefix_tile<MODE, kMT>(A, I, lam0, lam_end, false, umask, gtab, s_load, S, isum);
+      else if (d == kRAD2) best = prefix_tile<MODE, kRAD2>(A, I, lam0, lam_end, false, umask, gtab, s_load, S, isum);
+      else if (d == kCCM1) best = prefix_tile<MODE, kCCM1>(A, I, lam0, lam_end, false, umask, gtab, s_load, S, isum);
+      else best = prefix_tile<MODE, kBJ1>(A, I, lam0, lam_end, with_fs1, 0u, gtab, s_load, S, nullptr);
     }
     __syncthreads();
     fold_and_finalize<kPrefixNT>(A, b, best, S.err != 0, ntiles, I, S.warp_key);
