@@ -133,6 +133,19 @@ def prefix_smem_words(nd, prune=True):
         ccm1 = int((U // lam)[ccm1_keep].sum())
         pc = param_counts(c)
         u_words = 2 * nU + 2 * (len(small) + nb) + 6 * nU + pc[0] + 3 * pc[1] + ccm1
+        # VB2 on the u-group tile (vb2_table_plan): floor((U l - 1) / c) + 1
+        # lookups for each l in [2, lmax] when pruning leaves only those
+        if prune and c <= VB2_FIXED_CAP:
+            L = len(w) + k
+            kk = min(L1, L)
+            D = sws - sub
+            alpha = 2 * D - c * (2 * kk - kS)
+            beta = 2 * len(small) * (c - 1) + c * (2 * kk - kS) - c * (2 * len(small) - 2 * nb + 1) + 2
+            if alpha < 0 and 2 * alpha + beta > 0:
+                lmax = min(c, (beta - 1) // (-alpha))
+                if U * lmax * lmax // (2 * c) + lmax <= 1 << 16:
+                    lv = np.arange(2, lmax + 1, dtype=np.int64)
+                    u_words += int(((U * lv - 1) // c + 1).sum())
         # w group: NN (zero, one update per reduced item, scanned twice), FS1, BJ1
         w_words = nW + len(red) + 3 * nW + cache[key]
         total += loads_words + u_words + w_words
@@ -483,6 +496,8 @@ def main():
     barrier()
     pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(min(args.steps, 30))]
+    B.bp_lb_set_kernel_timing(h, True)
+    B.bp_lb_kernel_times(h)
     for e0, e1 in pev:
         flush.zero_()
         e0.record(stream)
@@ -490,6 +505,9 @@ def main():
         e1.record(stream)
     barrier()
     t_noprune = float(np.mean([e0.elapsed_time(e1) for e0, e1 in pev]))
+    np_k = B.bp_lb_kernel_times(h)
+    B.bp_lb_kernel_work(h)
+    B.bp_lb_set_kernel_timing(h, False)
     assert torch.equal(out_f, full_feasible)
     B.bp_lb_set_pruning(h, True)
     if world > 1:
@@ -528,7 +546,8 @@ def main():
     kernel_name = {"vb2": "vb2_kernel (VB2 item by item, fixed-point quotients, pruned)",
                    "direct": "eval_kernel (generic direct evaluation)",
                    "prefix": "prefix_kernel (MT, RAD2, FS1, CCM1, BJ1 from shared-memory "
-                             "prefix tables, pruned against L1)"}[dom]
+                             "prefix tables, pruned against L1; VB2 from the count table when "
+                             "pruning leaves only small lambda)"}[dom]
     basis = ({"prefix": f"{sms} SMs x 32 lanes x {sm_mhz_max:.0f} MHz (one 32-bit shared-memory "
                         "word per lane per clock: 128 B/clk/SM); work = shared-memory words of "
                         "table building and lookups"}
@@ -558,7 +577,10 @@ def main():
         "pruning": {"vb2_params_evaluated": kwork[2] / calls, "vb2_params_pruned": kwork[3] / calls,
                     "vb2_pairs_evaluated": vb2_pairs,
                     "off": {"value": NODES * world / (t_noprune / 1e3), "unit": UNIT,
-                            "ms_per_step": t_noprune},
+                            "ms_per_step": t_noprune,
+                            "kernel_ms": {"prefix": np_k[0] / max(1, np_k[3]),
+                                          "vb2": np_k[1] / max(1, np_k[3]),
+                                          "direct": np_k[2] / max(1, np_k[3])}},
                     "note": "exact: results identical with pruning off (bp_lb_set_pruning)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},

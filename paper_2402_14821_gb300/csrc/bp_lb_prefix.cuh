@@ -76,6 +76,8 @@ struct PrefixShared {
   // this tile, the u group's members (bit d), lambda range
   int dec_d, dec_home, dec_fs1, dec_umask;
   long long dec_lam0, dec_lam_end;
+  int vb2_mode;  // vb2_table_plan of this u-group tile, with its cut and last l
+  long long vb2_kk, vb2_lmax;
 };
 
 // Sum of v over the threads after this one (higher threadIdx.x).  wtot must
@@ -508,6 +510,84 @@ __device__ void eval_harmonic(const int32_t *T0, int64_t lam0, int64_t lam_end, 
   }
 }
 
+// VB2 on the u group's tile.  For u >= 1, ceil(l u / c) counts the j in
+// [0, l) with u >= floor(j c / l) + 1, so summed with sign over the small and
+// big items VB2's accumulator is sum_j N'(floor(j c / l) + 1), the terms
+// vanishing past U: about l / 2 lookups of the packed table per parameter.
+// That is only cheap for small l, so the tile takes VB2 when pruning leaves
+// only such parameters: every parameter that may matter satisfies
+// G(l) = alpha l + beta > 0 (vb2_range_may_exceed), and with alpha < 0 those
+// are l <= lmax.  Returns 0 (VB2 stays with its kernel), 1 (evaluate l in
+// [2, lmax] here) or 2 (no VB2 parameter can matter); the cut kk is k in
+// verdict mode, else L1 (MT in the bound), clamped to the stream length.
+constexpr int64_t kVb2TableTerms = 1 << 16;  // lookups per tile at most
+
+template <int MODE>
+__device__ __forceinline__ int vb2_table_plan(const EvalArgs &A, const InstView &I,
+                                              const PrefixShared &S, uint32_t L1, int64_t &kk,
+                                              int64_t &lmax) {
+  const int64_t c = I.c;
+  if (!(A.prune || A.verdict) || ((A.dff_off >> kVB2) & 1u) || !A.vb2_on || c > kVb2FixedCap ||
+      c < 2)
+    return 0;
+  const int64_t cut = A.verdict ? I.k : ((A.dff_off & 1u) ? -1 : (int64_t)L1);
+  if (cut < 0) return 0;
+  kk = min(cut, stream_len<MODE>(I));
+  const int64_t ns = S.sums[0], nb = S.sums[1], nh = S.sums[2], nf = S.sums[3];
+  const int64_t swb = S.sums[4], sw = S.sums[5];
+  const int64_t Dd = (sw - swb - nh * (c / 2) - nf * c) - (nb * c - swb);
+  const int64_t K = 2 * nb + nh + 2 * nf;
+  const int64_t alpha = 2 * Dd - c * (2 * kk - K);
+  const int64_t beta = 2 * ns * (c - 1) + c * (2 * kk - K) - c * (2 * ns - 2 * nb + 1) + 2;
+  if (alpha >= 0) return (alpha * c + beta <= 0) ? 2 : 0;
+  if (2 * alpha + beta <= 0) return 2;
+  lmax = min(c, (beta - 1) / (-alpha));
+  const int64_t U = (c - 1) / 2;
+  return (U * lmax * lmax / (2 * c) + lmax <= kVb2TableTerms) ? 1 : 0;
+}
+
+// VB2's parameters l in [2, lmax] from the packed count table T (entry x:
+// N'(x) in its low 16 bits), one thread each: round i gives thread t the
+// parameter 2 + i kPrefixNT + t (i even) or + kPrefixNT - 1 - t (i odd), so
+// that the threads' term counts (about l / 2) balance and each thread's
+// parameters increase.  The terms walk j with an incremental quotient
+// j c = q l + r (no division but c / l per parameter).  Every l in the range
+// is evaluated exactly (the range is a relaxation of the parameters that can
+// matter; the others only cost their lookups).
+__device__ __forceinline__ void eval_vb2_table(const int32_t *T, int64_t c, PrefixEval &x,
+                                               const PrefixShared &S, int64_t lmax) {
+  const uint32_t c32 = x.c32, U = x.U;
+  const uint32_t gofs = flat_index(kVB2, 2, c) - 2u;
+  const int64_t ns = S.sums[0], nb = S.sums[1];
+  const int64_t K = 2 * nb + S.sums[2] + 2 * S.sums[3];
+  const uint32_t n = (uint32_t)lmax - 1u;  // parameters 2 .. lmax
+  bool odd = false;
+  for (uint32_t r0 = 0; r0 < n; r0 += kPrefixNT, odd = !odd) {
+    const uint32_t p = r0 + (odd ? (uint32_t)(kPrefixNT - 1) - threadIdx.x : threadIdx.x);
+    if (p >= n) continue;
+    const uint32_t l = 2u + p;
+    const uint32_t cq = c32 / l, cr = c32 - cq * l;
+    uint32_t q = 0, r = 0;
+    int32_t acc = 0;
+    while (q < U) {  // the term's entry q + 1 <= U
+      acc += np_at<true>(T, q + 1u);
+      q += cq;
+      r += cr;
+      if (r >= l) {
+        r -= l;
+        ++q;
+      }
+    }
+    const int64_t Sv = 2 * ((int64_t)acc - ns + nb) + (int64_t)(l - 1u) * K;  // >= 0
+    const uint64_t f = 2u * (l - 1u);
+    if ((uint64_t)x.B * f < (uint64_t)Sv || (x.best == 0ull && x.B == 0u)) {
+      const uint32_t lb = (uint32_t)(((uint64_t)Sv + f - 1u) / f);
+      x.B = max(x.B, lb);
+      x.best = make_key((int64_t)lb, gofs + l);
+    }
+  }
+}
+
 // Builds the table(s) of D (a DFF, or kPrefixU for the merged u group) for
 // instance I -- one pass over the node's base items both accumulates its bin
 // loads and histograms its unpacked items, a second pass histograms the bin
@@ -609,13 +689,26 @@ __device__ __forceinline__ unsigned long long prefix_tile(const EvalArgs &A, con
     if (lane_id() == 0 && xs != 0u) atomicAdd((unsigned long long *)&S.sums[e], (unsigned long long)xs);
   }
   __syncthreads();
-  // the class counts and sums of the instance, for the VB2 kernel's tile
-  // pruning (every tile but BJ1's classifies the items)
-  if (D != kBJ1 && isum_out != nullptr && threadIdx.x == 0 && !S.err) {
+  // VB2 on this tile (u group only; vb2_table_plan), then the class counts
+  // and sums of the instance for the VB2 kernel's tile pruning (every tile
+  // but BJ1's classifies the items), flagged 2 when VB2 is done here
+  // (thread 0; the scans' barriers publish S.vb2_* before they are read)
+  if (threadIdx.x == 0) {
+    int mode = 0;
+    int64_t kk = 0, lmax = 0;
+    if (D == kPrefixU && !S.err) {
+      const uint32_t sw32 = (uint32_t)S.sums[5];
+      mode = vb2_table_plan<MODE>(A, I, S, sw32 / c32 + (sw32 % c32 != 0u), kk, lmax);
+    }
+    S.vb2_mode = mode;
+    S.vb2_kk = kk;
+    S.vb2_lmax = lmax;
+    if (D != kBJ1 && isum_out != nullptr && !S.err) {
 #pragma unroll
-    for (int e = 0; e < 6; ++e) isum_out[e] = S.sums[e];
-    __threadfence();
-    isum_out[7] = 1;
+      for (int e = 0; e < 6; ++e) isum_out[e] = S.sums[e];
+      __threadfence();
+      isum_out[7] = mode != 0 ? 2 : 1;
+    }
   }
   if (D == kBJ1) {
     suffix_scan<true>(T0, nW, S);
@@ -665,6 +758,7 @@ __device__ __forceinline__ unsigned long long prefix_tile(const EvalArgs &A, con
       param_range(kCCM1, c, lo, hi);
       eval_harmonic<kCCM1, true>(T1, lo, hi + 1, c, x, S);
     }
+    if (S.vb2_mode == 1) eval_vb2_table(T1, c, x, S, S.vb2_lmax);
   }
   return x.best;
 }

@@ -58,7 +58,9 @@ __global__ void __launch_bounds__(kVb2NT, vb2_minb(VT)) vb2_kernel(EvalArgs A) {
       // prefix kernel published, before anything is staged
       if (!S.skip && A.isums != nullptr && (A.verdict || A.prune)) {
         const volatile long long *is = A.isums + 8 * b;
-        if (is[7] == 1) {
+        const long long flag = is[7];
+        if (flag == 2) S.skip = 1;  // VB2 done on the prefix kernel's u-group tile
+        if (flag == 1) {
           __threadfence();
           const int64_t cut = A.verdict ? I.k : (int64_t)vb2_cut(&A.keys[b], flat_index(kVB2, lo_d, I.c));
           if (cut >= 0) {
