@@ -140,3 +140,65 @@ def test_verdict_huge_k_large_capacity(cudalib, orc):
             assert orc.lb_param(int(dd[j]), int(ll[j]), rg.instance(j), caps[j]) == b[j]
     finally:
         cudalib.bp_lb_destroy(h)
+
+
+def _vb2_table_mode(w, c, k):
+    """The u-group tile's VB2 plan (vb2_table_plan in bp_lb_prefix.cuh),
+    restated: 1 when VB2's parameters that can matter all lie in [2, lmax]
+    with few enough count-table lookups."""
+    w = np.asarray(w, dtype=np.int64)
+    w = w[w > 0]
+    small = w[2 * w < c]
+    big = w[(2 * w > c) & (w < c)]
+    nh, nf = int(np.sum(2 * w == c)), int(np.sum(w == c))
+    ns, nb = len(small), len(big)
+    L1 = -(-int(w.sum()) // c)
+    kk = min(L1, len(w) + 0)
+    K = 2 * nb + nh + 2 * nf
+    D = int(small.sum()) - int((c - big).sum())
+    alpha = 2 * D - c * (2 * kk - K)
+    beta = 2 * ns * (c - 1) + c * (2 * kk - K) - c * (2 * ns - 2 * nb + 1) + 2
+    if alpha >= 0 or 2 * alpha + beta <= 0:
+        return 0
+    lmax = min(c, (beta - 1) // (-alpha))
+    U = (c - 1) // 2
+    return 1 if U * lmax * lmax // (2 * c) + lmax <= (1 << 16) else 0
+
+
+def vb2_strong_instances(orc, seed=67, tries=6000):
+    """Random small instances (items above c / 2 mixed with small ones, and
+    uniform ones), kept when VB2 is the argmax of the full bound, plus every
+    tenth of the others."""
+    rng = np.random.default_rng(seed)
+    inst, caps = [], []
+    for t in range(tries):
+        c = int(rng.choice([60, 100, 150]))
+        n = int(rng.integers(3, 60))
+        if t % 2:
+            w = rng.integers(1, c + 1, n)
+        else:
+            w = np.concatenate([rng.integers(c // 2 + 1, c, n // 2 + 1), rng.integers(1, c // 2, n // 2 + 1)])
+        d = orc.lb([int(x) for x in w], c, 0)[1]
+        if d == 4 or t % 10 == 0:
+            inst.append(w)
+            caps.append(c)
+    return I.ragged_from_list(inst, caps)
+
+
+def test_vb2_on_count_table(cudalib, orc):
+    """VB2 evaluated from the u-group tile's count table (vb2_table_plan picks
+    it for instances whose VB2 parameters that can matter are small): bound
+    and argmax equal the oracle's, VB2 the argmax of several, with pruning
+    on and off."""
+    rg = vb2_strong_instances(orc)
+    want = oracle_batch(orc, rg)
+    modes = np.array([_vb2_table_mode(rg.instance(j), int(rg.capacity[j]), 0)
+                      for j in range(rg.count)])
+    assert int(np.sum((np.asarray(want[1]) == 4) & (modes == 1))) >= 2
+    h = cudalib.bp_lb_create(150, 1 << 16)
+    try:
+        for got in both(cudalib, h, rg):
+            for x, y in zip(got, want):
+                assert np.array_equal(np.asarray(x), np.asarray(y))
+    finally:
+        cudalib.bp_lb_destroy(h)
