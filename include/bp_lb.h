@@ -279,6 +279,40 @@ int bp_lb_set_result_mode(bp_lb_t *h, int32_t mode);
 /* The handle's result mode, or -1 for a NULL handle. */
 int bp_lb_get_result_mode(bp_lb_t *h);
 
+/* ---- reduction variants (search-node mode) --------------------------------- */
+
+/* The paper's reduction (Sec. 3 "Feasibility check", Fig. 3) turns each
+ * non-empty bin of a search node into one item of its packed load
+ * (BP_REDUCE_LOADS, the default).  Two variants, not defined in the paper
+ * (they keep every bound valid: any completion of the partial packing still
+ * fits the reduced instance in the k bins):
+ *   BP_REDUCE_CLOSE  a bin whose free space is smaller than every unpacked
+ *                    item of nonzero size (every bin, when there is none)
+ *                    can take nothing more: its item is c;
+ *   bin maximum loads (bp_lb_set_bin_max): a bin that may hold at most
+ *                    cap_j <= c becomes an item of load + c - cap_j (the
+ *                    capacity it cannot use is filled), then CLOSE applies
+ *                    to that item when set.
+ * The mode applies to every search-node call of the handle
+ * (bp_lb_eval_nodes, bp_lb_eval_node, bp_lb_reduce_nodes); the maximum loads
+ * to the batched ones (bp_lb_eval_nodes, bp_lb_reduce_nodes).
+ * Errors: BP_EINVAL (NULL handle), BP_ERANGE (unknown mode). */
+#define BP_REDUCE_LOADS 0
+#define BP_REDUCE_CLOSE 1
+int bp_lb_set_reduction(bp_lb_t *h, int32_t mode);
+
+/* The handle's reduction mode, or -1 for a NULL handle. */
+int bp_lb_get_reduction(bp_lb_t *h);
+
+/* Per-bin maximum loads for the handle's batched search-node calls: node b's
+ * bin j may hold at most d_bin_max[d_offsets[b] + j], which must lie in
+ * [0, c] and be at least the bin's packed load (else that node's result is
+ * -BP_ERANGE); d_offsets[b + 1] - d_offsets[b] must equal the node's bins.
+ * Device pointers owned by the caller, read by every later batched
+ * search-node call until cleared (both NULL).  Errors: BP_EINVAL (NULL
+ * handle, or exactly one pointer NULL). */
+int bp_lb_set_bin_max(bp_lb_t *h, const int64_t *d_offsets, const int32_t *d_bin_max);
+
 /* ---- VB2 pruning ------------------------------------------------------------ */
 
 /* On (1, the default): in both result modes a VB2 parameter is skipped when

@@ -48,6 +48,9 @@ def _bind(lib):
     lib.orc_lb.restype = ctypes.c_int
     lib.orc_reduce.argtypes = [_i64p, _i32p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _i64p]
     lib.orc_reduce.restype = ctypes.c_int64
+    lib.orc_reduce_ex.argtypes = [_i64p, _i32p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                  ctypes.c_int, _i64p, _i64p]
+    lib.orc_reduce_ex.restype = ctypes.c_int64
     lib.orc_l1.argtypes = [_i64p, ctypes.c_int64, ctypes.c_int64]
     lib.orc_l1.restype = ctypes.c_int64
     lib.orc_l2.argtypes = [_i64p, ctypes.c_int64, ctypes.c_int64]
@@ -110,6 +113,24 @@ class Oracle:
         asg = np.ascontiguousarray(np.asarray(assign, dtype=np.int32))
         out = np.zeros(len(a) + max(k, 0), dtype=np.int64)
         r = self.lib.orc_reduce(p, asg.ctypes.data_as(_i32p), len(a), k, c, out.ctypes.data_as(_i64p))
+        if r < 0:
+            raise ValueError("oracle: invalid partial packing")
+        return out[:r].copy()
+
+    def reduce_ex(self, w, assign, k: int, c: int, mode: int = 0, bin_max=None) -> np.ndarray:
+        """A reduction variant (orc_reduce_ex): mode 1 closes bins that no
+        unpacked item fits; bin_max caps each bin's load."""
+        a, p = self._arr64(w)
+        asg = np.ascontiguousarray(np.asarray(assign, dtype=np.int32))
+        out = np.zeros(len(a) + max(k, 0), dtype=np.int64)
+        bm = None
+        if bin_max is not None:
+            bm = np.ascontiguousarray(np.asarray(bin_max, dtype=np.int64))
+            if len(bm) != k:
+                raise ValueError("bin_max needs one entry per bin")
+        r = self.lib.orc_reduce_ex(p, asg.ctypes.data_as(_i32p), len(a), k, c, int(mode),
+                                   bm.ctypes.data_as(_i64p) if bm is not None else None,
+                                   out.ctypes.data_as(_i64p))
         if r < 0:
             raise ValueError("oracle: invalid partial packing")
         return out[:r].copy()

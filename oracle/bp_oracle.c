@@ -36,6 +36,11 @@
  *       the bin's packed load, bins in index order; empty bins (load 0) are
  *       dropped because f(0) = 0 for every DFF.
  *   R7  L2 (Sec. 3.1) is evaluated over integer lambda in [0, c/2].
+ *   R8  orc_reduce_ex's variants of the reduction (bins that no unpacked item
+ *       fits count as full; per-bin maximum loads) are not defined in the
+ *       paper: parity unpinned against it.  Their validity (a completable
+ *       partial packing gives a reduced instance that fits the k bins) and
+ *       their agreement with R6 when neither is used are pinned by the tests.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -202,6 +207,42 @@ int64_t orc_reduce(const int64_t *w, const int32_t *assign, int64_t n,
     for (int64_t j = 0; j < k; j++) {
         if (load[j] > c) { free(load); return -1; }
         if (load[j] > 0) out[r++] = load[j];
+    }
+    free(load);
+    return r;
+}
+
+/* Reduction variants -- not defined in the paper (parity unpinned against
+ * it; the tests pin their validity by brute force instead):
+ *   bin_max != NULL: bin j holds at most bin_max[j] (0 <= bin_max[j] <= c);
+ *       its virtual item is its load plus the capacity it cannot use,
+ *       load + c - bin_max[j];
+ *   mode 1 ("close"): a bin whose free space is smaller than every unpacked
+ *       item of nonzero size can take nothing more, so its virtual item is c.
+ * Unpacked items as in orc_reduce; bins whose virtual item is 0 dropped.
+ * Returns the reduced length, or -1 for an invalid partial packing. */
+int64_t orc_reduce_ex(const int64_t *w, const int32_t *assign, int64_t n, int64_t k,
+                      int64_t c, int mode, const int64_t *bin_max, int64_t *out)
+{
+    int64_t *load = (int64_t *)calloc((size_t)(k > 0 ? k : 1), sizeof(int64_t));
+    if (!load) return -1;
+    int64_t r = 0;
+    int64_t minw = -1;  /* smallest unpacked size > 0; -1: none */
+    for (int64_t i = 0; i < n; i++) {
+        if (assign[i] < -1 || assign[i] >= k) { free(load); return -1; }
+        if (assign[i] == -1) {
+            out[r++] = w[i];
+            if (w[i] > 0 && (minw < 0 || w[i] < minw)) minw = w[i];
+        } else {
+            load[assign[i]] += w[i];
+        }
+    }
+    for (int64_t j = 0; j < k; j++) {
+        int64_t cap = bin_max ? bin_max[j] : c;
+        if (cap < 0 || cap > c || load[j] > cap) { free(load); return -1; }
+        int64_t v = load[j] + (c - cap);
+        if (mode == 1 && v > 0 && (minw < 0 || c - v < minw)) v = c;
+        if (v > 0) out[r++] = v;
     }
     free(load);
     return r;

@@ -80,6 +80,9 @@ def _bind(lib):
         "bp_lb_set_result_mode": (ctypes.c_int, [_vp, _c_i32]),
         "bp_lb_set_pruning": (ctypes.c_int, [_vp, _c_i32]),
         "bp_lb_kernel_work": (ctypes.c_int, [_vp, _vp]),
+        "bp_lb_set_reduction": (ctypes.c_int, [_vp, _c_i32]),
+        "bp_lb_get_reduction": (ctypes.c_int, [_vp]),
+        "bp_lb_set_bin_max": (ctypes.c_int, [_vp, _vp, _vp]),
         "bp_lb_get_pruning": (ctypes.c_int, [_vp]),
         "bp_lb_set_dff_mask": (ctypes.c_int, [_vp, _c_i32]),
         "bp_lb_set_overlap": (ctypes.c_int, [_vp, _c_i32]),
@@ -128,10 +131,12 @@ EXPORTED = ("bp_lb_strerror", "bp_lb_create", "bp_lb_destroy", "bp_lb_reserve", 
             "bp_lb_set_kernel_timing", "bp_lb_kernel_times", "bp_lb_dff_route",
             "bp_lb_set_result_mode", "bp_lb_get_result_mode", "bp_lb_set_dff_mask",
             "bp_lb_get_dff_mask", "bp_lb_l2_batch", "bp_lb_set_overlap", "bp_lb_set_pruning",
-            "bp_lb_get_pruning", "bp_lb_kernel_work")
+            "bp_lb_get_pruning", "bp_lb_kernel_work", "bp_lb_set_reduction",
+            "bp_lb_get_reduction", "bp_lb_set_bin_max")
 
 ALGO_DIRECT, ALGO_PREFIX = 0, 1
 RESULT_FULL, RESULT_VERDICT = 0, 1
+REDUCE_LOADS, REDUCE_CLOSE = 0, 1
 
 NOALLOC_MAX_BATCH = 4096
 
@@ -336,6 +341,26 @@ def bp_lb_kernel_work(h):
     out = np.zeros(4, dtype=np.int64)
     _check(lib().bp_lb_kernel_work(h, out.ctypes.data), "bp_lb_kernel_work")
     return tuple(int(x) for x in out)
+
+
+def bp_lb_set_reduction(h, mode: int):
+    """REDUCE_LOADS (the paper's reduction) or REDUCE_CLOSE (bins that no
+    unpacked item fits count as full)."""
+    _check(lib().bp_lb_set_reduction(h, int(mode)), "bp_lb_set_reduction")
+
+
+def bp_lb_get_reduction(h) -> int:
+    return lib().bp_lb_get_reduction(h)
+
+
+def bp_lb_set_bin_max(h, offsets=None, bin_max=None):
+    """Per-bin maximum loads (device int64 offsets [B+1], int32 caps) for the
+    batched search-node calls; no arguments clears them.  The tensors must
+    stay alive while they are set."""
+    import torch
+    _check(lib().bp_lb_set_bin_max(h, _ptr(offsets, torch.int64, "offsets"),
+                                   _ptr(bin_max, torch.int32, "bin_max")),
+           "bp_lb_set_bin_max")
 
 
 def bp_lb_set_pruning(h, on: bool):

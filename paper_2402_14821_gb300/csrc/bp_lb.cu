@@ -74,6 +74,9 @@ struct bp_lb {
   int32_t vb2_on = 1;
   int32_t verdict = 0;  // BP_RESULT_FULL (0) or BP_RESULT_VERDICT (1)
   int32_t prune = 1;    // skip VB2 parameters that provably cannot win (exact)
+  int32_t reduce_mode = BP_REDUCE_LOADS;     // search-node reduction variant
+  const int64_t *d_bin_max_offsets = nullptr;  // optional per-bin maximum loads (caller's)
+  const int32_t *d_bin_max = nullptr;
   // With prefix_ctas > 0, batched calls run the prefix-count kernel (then the
   // generic kernel) on a high-priority side stream beside the VB2 kernel:
   // prefix_ctas CTAs per SM for the prefix kernel, the rest of each SM for
@@ -246,6 +249,7 @@ int launch_batch(bp_lb *h, EvalArgs A, size_t smem, cudaStream_t st) {
   A.vb2_on = h->vb2_on;
   A.verdict = h->verdict;
   A.prune = h->prune;
+  A.reduce_mode = h->reduce_mode;
   A.dff_off = h->dff_off;
   A.work_count = h->timing ? h->d_work_count : nullptr;
   A.isums = h->d_isums;
@@ -516,6 +520,7 @@ static EvalArgs plain_args(bp_lb *h, int64_t n, int64_t bins, int mode) {
   A.vb2_on = 0;
   A.verdict = h->verdict;
   A.prune = h->prune;
+  A.reduce_mode = h->reduce_mode;
   A.dff_off = h->dff_off;
   A.plpt = kPrefixLPTSingle;
   // global prefix tables when the scratch covers the prefix tiles (one CTA each)
@@ -650,6 +655,8 @@ int bp_lb_eval_nodes(bp_lb_t *h, int32_t B, int32_t num_base, const int64_t *d_b
   A.out_bound = d_out_bound;
   A.out_argmax = d_out_argmax;
   A.out_feasible = d_out_feasible;
+  A.bin_max_offsets = h->d_bin_max_offsets;
+  A.bin_max = h->d_bin_max;
   return launch_batch<kSrcNodes>(h, A, eval_smem<kSrcNodes>(max_bins), (cudaStream_t)stream);
 }
 
@@ -676,6 +683,9 @@ int bp_lb_reduce_nodes(bp_lb_t *h, int32_t B, int32_t num_base, const int64_t *d
   A.assign = d_assign;
   A.bins = d_bins;
   A.max_bins = (int32_t)max_bins;
+  A.reduce_mode = h->reduce_mode;
+  A.bin_max_offsets = h->d_bin_max_offsets;
+  A.bin_max = h->d_bin_max;
   const int grid = (int)std::min<int64_t>(B, (int64_t)h->num_sms * 8);
   reduce_kernel<256><<<grid, 256, sizeof(uint32_t) * (size_t)max_bins, (cudaStream_t)stream>>>(
       A, d_out_offsets, d_out_sizes, d_out_count);
@@ -733,6 +743,26 @@ int bp_lb_set_result_mode(bp_lb_t *h, int32_t mode) {
 int bp_lb_get_result_mode(bp_lb_t *h) {
   if (!h) return -1;
   return h->verdict ? BP_RESULT_VERDICT : BP_RESULT_FULL;
+}
+
+int bp_lb_set_reduction(bp_lb_t *h, int32_t mode) {
+  if (!h) return BP_EINVAL;
+  if (mode != BP_REDUCE_LOADS && mode != BP_REDUCE_CLOSE) return BP_ERANGE;
+  h->reduce_mode = mode;
+  return BP_OK;
+}
+
+int bp_lb_get_reduction(bp_lb_t *h) {
+  if (!h) return -1;
+  return h->reduce_mode;
+}
+
+int bp_lb_set_bin_max(bp_lb_t *h, const int64_t *d_offsets, const int32_t *d_bin_max) {
+  if (!h) return BP_EINVAL;
+  if ((d_offsets == nullptr) != (d_bin_max == nullptr)) return BP_EINVAL;
+  h->d_bin_max_offsets = d_offsets;
+  h->d_bin_max = d_bin_max;
+  return BP_OK;
 }
 
 int bp_lb_set_pruning(bp_lb_t *h, int32_t on) {

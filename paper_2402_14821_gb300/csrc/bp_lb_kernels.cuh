@@ -89,6 +89,13 @@ struct EvalArgs {
   // the number of VB2 tiles it aims at
   long long *vlpt;
   int64_t vb2_target_tiles;
+  // reduction variants of the search-node mode (transform_bins):
+  // BP_REDUCE_LOADS or BP_REDUCE_CLOSE, and optional per-bin maximum loads
+  // (node b's bin j: bin_max[bin_max_offsets[b] + j], 0 <= it <= c)
+  int32_t reduce_mode;
+  int32_t pad_reduce;
+  const int64_t *bin_max_offsets;
+  const int32_t *bin_max;
 };
 
 // Shared-memory budget of the prefix-count tables (bytes; 48 KB lets four
@@ -410,7 +417,8 @@ __global__ void __launch_bounds__(1024)
         const int64_t na = A.assign_offsets[b + 1] - A.assign_offsets[b];
         const int64_t k = A.bins[b];
         ok = ok && c >= 1 && c <= kMaxCapacity && n >= 0 && n <= kMaxItems && na == n && k >= 0 &&
-             k <= A.max_bins;
+             k <= A.max_bins &&
+             (A.bin_max == nullptr || A.bin_max_offsets[b + 1] - A.bin_max_offsets[b] == k);
         L = n + k;
       } else {
         c = A.capacity[b];
@@ -456,6 +464,7 @@ struct TileShared {
   unsigned long long warp_key[32];
   long long sums[6];
   unsigned long long sumF[2];  // VB2 fixed point: sum of F over the small and big lists
+  uint32_t minw;               // smallest unpacked size > 0 of a node (transform_bins)
 };
 
 // Fetches stream position q: returns true and the size when q is an item of
@@ -532,10 +541,48 @@ __device__ void fold_and_finalize(const EvalArgs &A, int64_t b, unsigned long lo
 
 // Bin loads of a search node into s_load (read back by
 // fetch_item); sets *err for a bad assignment or an overfull bin.
+// Reduction variants (search-node mode; not in the paper, which reduces a
+// bin to one item of its packed load, Fig. 3): a bin with maximum load
+// cap_j < c becomes an item of load + c - cap_j (the capacity it cannot use
+// is filled), and under BP_REDUCE_CLOSE a bin whose free space is below the
+// smallest unpacked item of nonzero size (minw; all bins when there is none)
+// becomes an item of size c.  Any completion of the partial packing still
+// fits the reduced instance in the k bins, so every bound stays valid.
+// Rewrites the bin loads s_load[0 .. k) in place; a cap outside [0, c] or
+// below the bin's load sets *err.
+template <int NT>
+__device__ __forceinline__ void transform_bins(const EvalArgs &A, int64_t b, const InstView &I,
+                                               uint32_t *s_load, uint32_t minw, int *err) {
+  const int32_t *cap = A.bin_max != nullptr ? A.bin_max + A.bin_max_offsets[b] : nullptr;
+  for (int64_t j = threadIdx.x; j < I.k; j += NT) {
+    int64_t v = s_load[j];
+    if (cap != nullptr) {
+      const int32_t m = cap[j];
+      if (m < 0 || (int64_t)m > I.c || v > (int64_t)m) {
+        *err = 1;
+        continue;
+      }
+      v += I.c - m;
+    }
+    if (A.reduce_mode == BP_REDUCE_CLOSE && v > 0 && I.c - v < (int64_t)minw) v = I.c;
+    s_load[j] = (uint32_t)v;
+  }
+}
+
+__device__ __forceinline__ bool bins_transformed(const EvalArgs &A) {
+  return A.reduce_mode != BP_REDUCE_LOADS || A.bin_max != nullptr;
+}
+
+// Bin loads of search node b in shared memory (the reduction of Fig. 3, with
+// the variants of transform_bins); *minw is scratch for the smallest unpacked
+// size.  The caller synchronises before reading s_load.
 template <int NT, int MODE>
-__device__ __forceinline__ void node_loads(const InstView &I, uint32_t *s_load, int *err) {
+__device__ __forceinline__ void node_loads(const EvalArgs &A, int64_t b, const InstView &I,
+                                           uint32_t *s_load, uint32_t *minw, int *err) {
   if (MODE == kSrcNodes) {
+    const bool tr = bins_transformed(A);
     for (int64_t j = threadIdx.x; j < I.k; j += NT) s_load[j] = 0u;
+    if (tr && threadIdx.x == 0) *minw = 0xFFFFFFFFu;
     __syncthreads();
     for (int64_t i = threadIdx.x; i < I.n; i += NT) {
       const int32_t a = I.a[i];
@@ -545,7 +592,13 @@ __device__ __forceinline__ void node_loads(const InstView &I, uint32_t *s_load, 
       } else if (a >= 0) {
         const uint32_t old = atomicAdd(&s_load[a], (uint32_t)w);
         if ((int64_t)old + w > I.c) *err = 1;
+      } else if (tr && w > 0) {
+        atomicMin(minw, (uint32_t)w);
       }
+    }
+    if (tr) {
+      __syncthreads();
+      transform_bins<NT>(A, b, I, s_load, *minw, err);
     }
   }
 }
@@ -1031,7 +1084,7 @@ __device__ void process_tile(const EvalArgs &A, int64_t b, int64_t lt, int64_t n
     S.skip = (vslot != nullptr && slot_decided(vslot, I.k)) ? 1 : 0;
   }
   __syncthreads();
-  if (!S.skip) node_loads<NT, MODE>(I, s_load, &S.err);
+  if (!S.skip) node_loads<NT, MODE>(A, b, I, s_load, &S.minw, &S.err);
   __syncthreads();
 
   // FS1 (100 parameters) takes one parameter per thread, so that its tile
@@ -1213,6 +1266,7 @@ __global__ void __launch_bounds__(NT)
   __shared__ int s_err;
   __shared__ int s_warp[NT / 32];
   __shared__ long long s_base;
+  __shared__ uint32_t s_minw;
   for (int64_t b = blockIdx.x; b < A.B; b += gridDim.x) {
     const int tid = threadIdx.x;
     const int32_t base = A.node_base[b];
@@ -1232,6 +1286,7 @@ __global__ void __launch_bounds__(NT)
     if (tid == 0) {
       s_err = 0;
       s_base = 0;
+      s_minw = 0xFFFFFFFFu;
     }
     for (int64_t j = tid; j < k; j += NT) s_load[j] = 0u;
     __syncthreads();
@@ -1241,9 +1296,22 @@ __global__ void __launch_bounds__(NT)
       else if (ai >= 0) {
         const uint32_t old = atomicAdd(&s_load[ai], (uint32_t)wi);
         if ((int64_t)old + wi > c) s_err = 1;
+      } else if (wi > 0) {
+        atomicMin(&s_minw, (uint32_t)wi);
       }
     }
     __syncthreads();
+    if (bins_transformed(A) && !s_err &&
+        (A.bin_max == nullptr || A.bin_max_offsets[b + 1] - A.bin_max_offsets[b] == k)) {
+      InstView I;
+      I.c = c;
+      I.k = k;
+      transform_bins<NT>(A, b, I, s_load, s_minw, &s_err);
+      __syncthreads();
+    } else if (A.bin_max != nullptr && A.bin_max_offsets[b + 1] - A.bin_max_offsets[b] != k) {
+      s_err = 1;
+      __syncthreads();
+    }
     if (s_err) {
       if (tid == 0) out_count[b] = -BP_ERANGE;
       __syncthreads();

@@ -78,6 +78,7 @@ struct PrefixShared {
   long long dec_lam0, dec_lam_end;
   int vb2_mode;  // vb2_table_plan of this u-group tile, with its cut and last l
   long long vb2_kk, vb2_lmax;
+  uint32_t minw;  // smallest unpacked size > 0 of the node (transform_bins)
 };
 
 // Sum of v over the threads after this one (higher threadIdx.x).  wtot must
@@ -600,7 +601,7 @@ __device__ __forceinline__ unsigned long long prefix_tile(const EvalArgs &A, con
                                                           bool with_fs1, uint32_t umask,
                                                           int32_t *tab,
                                                           uint32_t *s_load, PrefixShared &S,
-                                                          long long *isum_out) {
+                                                          long long *isum_out, int64_t b) {
   const int tid = threadIdx.x;
   const int64_t c = I.c;
   const uint32_t c32 = (uint32_t)c;
@@ -614,8 +615,10 @@ __device__ __forceinline__ unsigned long long prefix_tile(const EvalArgs &A, con
     const int4 z = make_int4(0, 0, 0, 0);
     for (int i = tid; i < (nzero + 3) / 4; i += kPrefixNT) t4[i] = z;
   }
+  const bool tr = MODE == kSrcNodes && bins_transformed(A);
   if (MODE == kSrcNodes)
     for (int64_t j = tid; j < I.k; j += kPrefixNT) s_load[j] = 0u;
+  if (tr && tid == 0) S.minw = 0xFFFFFFFFu;
   if (tid < 8) S.sums[tid] = 0;
   if (D == kBJ1 && with_fs1 && tid < kFs1Params) {
     // FS1's parameters l = tid + 1 (l' = tid + 2)
@@ -670,9 +673,14 @@ __device__ __forceinline__ unsigned long long prefix_tile(const EvalArgs &A, con
         if ((int64_t)old + w > c) S.err = 1;
       } else {
         visit(w);
+        if (tr && w > 0) atomicMin(&S.minw, (uint32_t)w);
       }
     }
     __syncthreads();
+    if (tr) {
+      transform_bins<kPrefixNT>(A, b, I, s_load, S.minw, &S.err);
+      __syncthreads();
+    }
     for (int64_t j = tid; j < I.k; j += kPrefixNT) visit((int64_t)s_load[j]);
   } else {
     const int64_t L = stream_len<MODE>(I);
@@ -837,17 +845,17 @@ __global__ void __launch_bounds__(kPrefixNT, 4) prefix_kernel(EvalArgs A) {
     // one instantiation per table space, so that shared-memory tables are
     // accessed with shared-memory instructions
     if (!S.skip && home != 2) {
-      if (d == kPrefixU) best = prefix_tile<MODE, kPrefixU>(A, I, lam0, lam_end, false, umask, stab, s_load, S, isum);
-      else if (d == kMT) best = prefix_tile<MODE, kMT>(A, I, lam0, lam_end, false, umask, stab, s_load, S, isum);
-      else if (d == kRAD2) best = prefix_tile<MODE, kRAD2>(A, I, lam0, lam_end, false, umask, stab, s_load, S, isum);
-      else if (d == kCCM1) best = prefix_tile<MODE, kCCM1>(A, I, lam0, lam_end, false, umask, stab, s_load, S, isum);
-      else best = prefix_tile<MODE, kBJ1>(A, I, lam0, lam_end, with_fs1, 0u, stab, s_load, S, nullptr);
+      if (d == kPrefixU) best = prefix_tile<MODE, kPrefixU>(A, I, lam0, lam_end, false, umask, stab, s_load, S, isum, b);
+      else if (d == kMT) best = prefix_tile<MODE, kMT>(A, I, lam0, lam_end, false, umask, stab, s_load, S, isum, b);
+      else if (d == kRAD2) best = prefix_tile<MODE, kRAD2>(A, I, lam0, lam_end, false, umask, stab, s_load, S, isum, b);
+      else if (d == kCCM1) best = prefix_tile<MODE, kCCM1>(A, I, lam0, lam_end, false, umask, stab, s_load, S, isum, b);
+      else best = prefix_tile<MODE, kBJ1>(A, I, lam0, lam_end, with_fs1, 0u, stab, s_load, S, nullptr, b);
     } else if (!S.skip) {
-      if (d == kPrefixU) best = prefix_tile<MODE, kPrefixU>(A, I, lam0, lam_end, false, umask, gtab, s_load, S, isum);
-      else if (d == kMT) best = prefix_tile<MODE, kMT>(A, I, lam0, lam_end, false, umask, gtab, s_load, S, isum);
-      else if (d == kRAD2) best = prefix_tile<MODE, kRAD2>(A, I, lam0, lam_end, false, umask, gtab, s_load, S, isum);
-      else if (d == kCCM1) best = prefix_tile<MODE, kCCM1>(A, I, lam0, lam_end, false, umask, gtab, s_load, S, isum);
-      else best = prefix_tile<MODE, kBJ1>(A, I, lam0, lam_end, with_fs1, 0u, gtab, s_load, S, nullptr);
+      if (d == kPrefixU) best = prefix_tile<MODE, kPrefixU>(A, I, lam0, lam_end, false, umask, gtab, s_load, S, isum, b);
+      else if (d == kMT) best = prefix_tile<MODE, kMT>(A, I, lam0, lam_end, false, umask, gtab, s_load, S, isum, b);
+      else if (d == kRAD2) best = prefix_tile<MODE, kRAD2>(A, I, lam0, lam_end, false, umask, gtab, s_load, S, isum, b);
+      else if (d == kCCM1) best = prefix_tile<MODE, kCCM1>(A, I, lam0, lam_end, false, umask, gtab, s_load, S, isum, b);
+      else best = prefix_tile<MODE, kBJ1>(A, I, lam0, lam_end, with_fs1, 0u, gtab, s_load, S, nullptr, b);
     }
     __syncthreads();
     fold_and_finalize<kPrefixNT>(A, b, best, S.err != 0, ntiles, I, S.warp_key);

@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kVb2NT, vb2_minb(VT)) vb2_kernel(EvalArgs A) {
     __syncthreads();
     unsigned long long best = 0ull;
     if (!S.skip) {
-      node_loads<kVb2NT, MODE>(I, s_load, &S.err);
+      node_loads<kVb2NT, MODE>(A, b, I, s_load, &S.minw, &S.err);
       __syncthreads();
       best = tile_dff<kVb2NT, VT, kVB2, MODE, false, true>(
           A, I, lam0, lam_end, s_items, nullptr, s_load, S, nullptr, nullptr, -1, vslot,
