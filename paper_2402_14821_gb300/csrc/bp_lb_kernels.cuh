@@ -135,7 +135,7 @@ constexpr int64_t kGlobalTableInts = int64_t(1) << 20;
 // sums must fit 32 bits; FS1's count sum, at most 101 sum_bound / c, too.
 BPLB_HD int prefix_home(int d, int64_t c, int64_t sum_bound, int32_t on) {
   if (!(on & kPrefixShared) || sum_bound >= (int64_t(1) << 31)) return 0;
-  if (d == kFS1 && sum_bound / c >= (int64_t(1) << 25)) return 0;
+  if (d == kFS1 && sum_bound >= (int64_t(1) << 25) * c) return 0;  // sum_bound / c >= 2^25
   const int64_t bytes = prefix_table_bytes(d, c);
   if (bytes == 0) return 0;
   if (bytes <= kPrefixSmemBytes) return 1;
@@ -185,7 +185,7 @@ BPLB_HD int prefix_u_home(int64_t c, int32_t on) {
 // sum_bound = stream length c).
 BPLB_HD bool prefix_u_merged(int64_t c, int64_t sum_bound, int32_t prefix_on, int32_t vb2_on,
                              uint32_t dff_off, int64_t lpt) {
-  if (!(prefix_on & kPrefixShared) || sum_bound / c >= (int64_t(1) << 15)) return false;
+  if (!(prefix_on & kPrefixShared) || sum_bound >= (int64_t(1) << 15) * c) return false;
   const int home = prefix_u_home(c, prefix_on);
   if (home == 0) return false;
   const int ds[3] = {kMT, kRAD2, kCCM1};
@@ -198,6 +198,12 @@ BPLB_HD bool prefix_u_merged(int64_t c, int64_t sum_bound, int32_t prefix_on, in
     ++members;
   }
   return members >= 2;
+}
+
+// ceil(count / lpt) in 32 bits: counts are at most 2^30 + 1 and tile
+// lengths at most 2^16 wherever tiles are counted.
+BPLB_HD int64_t tile_count(int64_t count, int64_t lpt) {
+  return (int64_t)(((uint32_t)count + (uint32_t)lpt - 1u) / (uint32_t)lpt);
 }
 
 // FS1 shares the first of BJ1's prefix-kernel tiles (both read the w-domain
@@ -214,7 +220,7 @@ BPLB_HD bool prefix_w_merged(int64_t c, int64_t sum_bound, int32_t prefix_on, in
 BPLB_HD int64_t prefix_dff_tiles(int d, int64_t c, int64_t sum_bound, int32_t on, int64_t lpt) {
   const int64_t pc = param_count(d, c);
   if (pc == 0) return 0;
-  return prefix_home(d, c, sum_bound, on) == 2 ? 1 : (pc + lpt - 1) / lpt;
+  return prefix_home(d, c, sum_bound, on) == 2 ? 1 : tile_count(pc, lpt);
 }
 
 // Tiles of one kernel for an instance: lpt parameters each, DFFs in paper
@@ -231,7 +237,7 @@ BPLB_HD int64_t route_tiles(int route, int64_t c, int64_t lpt, int64_t sum_bound
     if (wmerged && d == kFS1) continue;
     if (dff_kernel(d, c, sum_bound, prefix_on, vb2_on, dff_off) != route) continue;
     t += route == kRoutePrefix ? prefix_dff_tiles(d, c, sum_bound, prefix_on, lpt)
-                               : (param_count(d, c) + lpt - 1) / lpt;
+                               : tile_count(param_count(d, c), lpt);
   }
   return t;
 }
@@ -364,45 +370,12 @@ __global__ void __launch_bounds__(1024)
     if (A.vwork) *A.vwork = 0ull;
   }
   __syncthreads();
-  // the VB2 tile length (vlpt): VB2's parameters of the whole batch over the
-  // target tile count
-  int64_t vlpt = kVb2LPT;
-  if (A.vlpt != nullptr && A.vb2_on) {
-    for (int64_t b0 = 0; b0 < A.B; b0 += blockDim.x) {
-      const int64_t b = b0 + threadIdx.x;
-      int64_t pv = 0;
-      if (b < A.B) {
-        int64_t c = 0, L = 0;
-        if (MODE == kSrcNodes) {
-          const int32_t base = A.node_base[b];
-          if (base >= 0 && base < A.num_base) {
-            c = A.base_capacity[base];
-            L = A.base_offsets[base + 1] - A.base_offsets[base] + A.bins[b];
-          }
-        } else {
-          c = A.capacity[b];
-          L = A.offsets[b + 1] - A.offsets[b];
-        }
-        if (c >= 1 && c <= kVb2FixedCap && L >= 0 &&
-            dff_kernel(kVB2, c, L * c, A.prefix_on, A.vb2_on, A.dff_off) == kRouteVb2)
-          pv = param_count(kVB2, c);
-      }
-      plan_scan(pv, s_warp, &s_carry[2]);
-    }
-    __syncthreads();
-    const int64_t tot = s_carry[2];
-    const int64_t want = (tot + max(A.vb2_target_tiles, (int64_t)1) - 1) / max(A.vb2_target_tiles, (int64_t)1);
-    vlpt = min(kVb2MaxLPT, max(kVb2LPT, (want + 1023) / 1024 * 1024));
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      *A.vlpt = vlpt;
-      s_carry[2] = 0;
-    }
-    __syncthreads();
-  }
+  // one pass over the instances: validate, count the direct and prefix tiles
+  // and VB2's parameters (kept in vtile_start[b] until the VB2 tile length is
+  // known: VB2's parameters of the whole batch over the target tile count)
   for (int64_t b0 = 0; b0 < A.B; b0 += blockDim.x) {
     const int64_t b = b0 + threadIdx.x;
-    int64_t tiles = 0, ptiles = 0, vtiles = 0;
+    int64_t tiles = 0, ptiles = 0, pv = 0;
     if (b < A.B) {
       A.keys[b] = 0ull;
       A.done[b] = 0u;
@@ -428,20 +401,45 @@ __global__ void __launch_bounds__(1024)
       if (ok) {
         tiles = route_tiles(kRouteDirect, c, lpt, L * c, A.prefix_on, A.vb2_on, A.dff_off);
         ptiles = route_tiles(kRoutePrefix, c, A.plpt, L * c, A.prefix_on, A.vb2_on, A.dff_off);
-        vtiles = route_tiles(kRouteVb2, c, vlpt, L * c, A.prefix_on, A.vb2_on, A.dff_off);
+        if (vtile_start != nullptr &&
+            dff_kernel(kVB2, c, L * c, A.prefix_on, A.vb2_on, A.dff_off) == kRouteVb2)
+          pv = param_count(kVB2, c);
         // no parameter at all (only DFFs with an empty range left in): bound 0
-        if (tiles + ptiles + vtiles == 0) write_result(A, b, 0ull, c, A.bins[b]);
+        if (tiles + ptiles + pv == 0) write_result(A, b, 0ull, c, A.bins[b]);
       } else {
         write_error(A, b);
       }
     }
     const int64_t e0 = plan_scan(tiles, s_warp, &s_carry[0]);
     const int64_t e1 = plan_scan(ptiles, s_warp, &s_carry[1]);
-    const int64_t e2 = plan_scan(vtiles, s_warp, &s_carry[2]);
+    plan_scan(pv, s_warp, &s_carry[2]);
     if (b < A.B) {
       tile_start[b] = e0;
       if (ptile_start) ptile_start[b] = e1;
-      if (vtile_start) vtile_start[b] = e2;
+      if (vtile_start) vtile_start[b] = pv;
+    }
+  }
+  __syncthreads();
+  int64_t vlpt = kVb2LPT;
+  if (A.vlpt != nullptr && A.vb2_on) {
+    const int64_t tgt = max(A.vb2_target_tiles, (int64_t)1);
+    const int64_t want = (s_carry[2] + tgt - 1) / tgt;
+    vlpt = min(kVb2MaxLPT, max(kVb2LPT, (want + 1023) / 1024 * 1024));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (A.vlpt != nullptr) *A.vlpt = vlpt;
+    s_carry[2] = 0;
+  }
+  __syncthreads();
+  // the VB2 tile table from the kept parameter counts (each thread rereads
+  // its own entries)
+  if (vtile_start != nullptr) {
+    for (int64_t b0 = 0; b0 < A.B; b0 += blockDim.x) {
+      const int64_t b = b0 + threadIdx.x;
+      const int64_t pv = b < A.B ? vtile_start[b] : 0;
+      const int64_t e2 = plan_scan(tile_count(pv, vlpt), s_warp, &s_carry[2]);
+      if (b < A.B) vtile_start[b] = e2;
     }
   }
   if (threadIdx.x == 0) {
