@@ -485,13 +485,15 @@ __device__ void eval_harmonic(const int32_t *T0, int64_t lam0, int64_t lam_end, 
     const int64_t A1 = 2 * (int64_t)x.n_big;
     const int64_t A2 = 2 * (int64_t)x.L1 - (int64_t)kS;
     constexpr uint32_t kBlock = 32u * kRun;
+    // BJ1's l > c / 2 (q = 1) are taken below, four at a time
+    const uint32_t lq1 = (D == kBJ1) ? max((uint32_t)warp_end, min(le, c32 / 2u + 1u)) : le;
     bool odd = false;
-    for (uint32_t r0 = (uint32_t)warp_end; r0 < le; r0 += kBlock * kPrefixWarps, odd = !odd) {
+    for (uint32_t r0 = (uint32_t)warp_end; r0 < lq1; r0 += kBlock * kPrefixWarps, odd = !odd) {
       const uint32_t wb = odd ? (uint32_t)(kPrefixWarps - 1 - warp) : (uint32_t)warp;
       const uint32_t l0 = r0 + wb * kBlock + (uint32_t)lane;
-      if (l0 >= le) continue;
+      if (l0 >= lq1) continue;
       uint32_t q = c32 / l0, m = (D == kCCM1) ? U / l0 : 0u;
-      for (uint32_t l = l0; l < le && l < l0 + kBlock; l += 32u) {
+      for (uint32_t l = l0; l < lq1 && l < l0 + kBlock; l += 32u) {
         while (q * l > c32) --q;  // q l <= c (l0 + kBlock) / l0 < 2^32 here
         if (D == kCCM1) {
           while (m * l > U) --m;
@@ -506,6 +508,27 @@ __device__ void eval_harmonic(const int32_t *T0, int64_t lam0, int64_t lam_end, 
         uint32_t acc = 0;
         if (D == kCCM1 || q * l != c32) acc = harmonic_sum<D, PACKED>(T0, l, m);
         finish(l, q, acc);
+      }
+    }
+    // BJ1, q = 1: S = D(l) at entry 1 + l (D(c) = sum w covers c mod l = 0),
+    // f = 2l - c.  Parameters from la (entry 1 + la 16-byte aligned) go four
+    // to a thread per step, one 16-byte load each; the few before la one each.
+    if (D == kBJ1 && lq1 < le) {
+      const uint32_t la = min(le, lq1 + ((3u - lq1 % 4u) % 4u));  // la = 3 mod 4
+      if (lq1 + (uint32_t)tid < la) {
+        const uint32_t l = lq1 + (uint32_t)tid;
+        try_key((uint32_t)T0[1u + l], 2u * l - c32, gofs + l, x.B, x.best);
+      }
+      for (uint32_t l = la + 4u * (uint32_t)tid; l < le; l += 4u * kPrefixNT) {
+        if (l + 3u < le) {
+          const int4 v = *reinterpret_cast<const int4 *>(T0 + 1u + l);
+          try_key((uint32_t)v.x, 2u * l - c32, gofs + l, x.B, x.best);
+          try_key((uint32_t)v.y, 2u * l + 2u - c32, gofs + l + 1u, x.B, x.best);
+          try_key((uint32_t)v.z, 2u * l + 4u - c32, gofs + l + 2u, x.B, x.best);
+          try_key((uint32_t)v.w, 2u * l + 6u - c32, gofs + l + 3u, x.B, x.best);
+        } else {
+          for (uint32_t e = l; e < le; ++e) try_key((uint32_t)T0[1u + e], 2u * e - c32, gofs + e, x.B, x.best);
+        }
       }
     }
   }
