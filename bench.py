@@ -57,7 +57,7 @@ SM_COUNT_NOMINAL = 152
 # launch, divided by 512: traffic grows with the nodes, each node's inputs
 # being read from DRAM once), or None while the kernel has changed since the
 # last capture.
-TRAFFIC_BYTES_PER_NODE = {"prefix": 2333, "vb2": None, "direct": None}
+TRAFFIC_BYTES_PER_NODE = {"prefix": 2336, "vb2": None, "direct": None}
 
 # Prefix-count kernel: its algorithmic work is shared-memory table traffic, in
 # 32-bit words -- zeroing, histogram updates, three accesses per entry and
