@@ -256,6 +256,17 @@ __device__ __forceinline__ bool prune_ccm1(const PrefixEval &x, uint32_t l, uint
   return lS <= 2 * (int64_t)q * l * x.L1;
 }
 
+// Word offset of p within its 16-byte line (0..3): entry e of a table at p
+// starts a 16-byte load iff (word_phase(p) + e) % 4 == 0.
+__device__ __forceinline__ uint32_t word_phase(const int32_t *p) {
+  return (uint32_t)((reinterpret_cast<uintptr_t>(p) >> 2) & 3u);
+}
+
+// First l >= l0 with (phase + l) % 4 == 0.
+__device__ __forceinline__ uint32_t aligned_from(uint32_t l0, uint32_t phase) {
+  return l0 + ((4u - ((phase + l0) & 3u)) & 3u);
+}
+
 // MT: S(l) = E(l) + TB + sumw_big + n_half (c/2) + n_full c, f = c; one lookup.
 __device__ __forceinline__ void eval_mt(const int32_t *E, int64_t lam0, int64_t lam_end,
                                         int64_t c, PrefixEval &x) {
@@ -514,7 +525,7 @@ __device__ void eval_harmonic(const int32_t *T0, int64_t lam0, int64_t lam_end, 
     // f = 2l - c.  Parameters from la (entry 1 + la 16-byte aligned) go four
     // to a thread per step, one 16-byte load each; the few before la one each.
     if (D == kBJ1 && lq1 < le) {
-      const uint32_t la = min(le, lq1 + ((3u - lq1 % 4u) % 4u));  // la = 3 mod 4
+      const uint32_t la = min(le, aligned_from(lq1, word_phase(T0 + 1)));  // T0 + 1 + la aligned
       if (lq1 + (uint32_t)tid < la) {
         const uint32_t l = lq1 + (uint32_t)tid;
         try_key((uint32_t)T0[1u + l], 2u * l - c32, gofs + l, x.B, x.best);
