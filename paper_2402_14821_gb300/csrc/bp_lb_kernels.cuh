@@ -1144,11 +1144,13 @@ __device__ __forceinline__ void tile_publish(const int64_t *start, int64_t B, in
   __syncthreads();
 }
 
-// The first tile of this CTA: the next from the work counter, or blockIdx.x.
+// The first tile of this CTA: the next from the work counter, or blockIdx.x
+// (also when the kernel has no tile at all: its CTAs leave without touching
+// the shared counter).
 __device__ __forceinline__ void tile_first(const int64_t *start, int64_t B, int64_t total,
                                            unsigned long long *work, TileCursor &cur) {
   unsigned long long t = blockIdx.x;
-  if (work && threadIdx.x == 0) t = atomicAdd(work, 1ull);
+  if (work && threadIdx.x == 0 && total > 0) t = atomicAdd(work, 1ull);
   tile_publish(start, B, total, t, cur);
 }
 
