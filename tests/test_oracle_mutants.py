@@ -14,6 +14,8 @@ import oracle as O
 from test_oracle_pins import (check_bruteforce_opt, check_dual_feasible_dp, check_fig3,
                               check_full_maximum, check_l1_special_cases, check_l2,
                               check_param_counts, check_reduction, check_vb2_cap)
+from test_oracle_reduction import (check_closing_grows, check_examples, check_plain_variant,
+                                   check_variants_valid)
 
 SRC = os.path.join(os.path.dirname(O.__file__), "bp_oracle.c")
 
@@ -56,6 +58,12 @@ MUTANTS = [
      "if (assign[i] >= -1) out[r++] = w[i];"),
     ("l2_medium_bound", "else if (2 * w[i] > c && w[i] <= c - l) { n2++; s2 += w[i]; }",
      "else if (2 * w[i] >= c && w[i] <= c - l) { n2++; s2 += w[i]; }"),
+    ("reduce_ex_filler_sign", "int64_t v = load[j] + (c - cap);", "int64_t v = load[j] - (c - cap);"),
+    ("reduce_ex_close_when_equal", "if (mode == 1 && v > 0 && (minw < 0 || c - v < minw)) v = c;",
+     "if (mode == 1 && v > 0 && (minw < 0 || c - v <= minw)) v = c;"),
+    ("reduce_ex_close_empty_bins", "if (mode == 1 && v > 0 && (minw < 0 || c - v < minw)) v = c;",
+     "if (mode == 1 && v >= 0 && (minw < 0 || c - v < minw)) v = c;"),
+    ("reduce_ex_cap_ignored", "int64_t cap = bin_max ? bin_max[j] : c;", "int64_t cap = c;"),
 ]
 
 BATTERY = (
@@ -68,6 +76,11 @@ BATTERY = (
     lambda o: check_vb2_cap(o, trials=60),
     lambda o: check_reduction(o, trials=80),
     lambda o: check_full_maximum(o),
+    lambda o: check_plain_variant(o, trials=100),
+    lambda o: check_variants_valid(o, 1, True, trials=160),
+    lambda o: check_variants_valid(o, 1, False, trials=160),
+    lambda o: check_closing_grows(o),
+    lambda o: check_examples(o),
 )
 
 

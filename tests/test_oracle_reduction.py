@@ -48,23 +48,21 @@ def random_case(rng, with_cap):
     return w, assign, k, c, cap
 
 
-def test_plain_variant_is_the_papers_reduction(orc):
+def check_plain_variant(orc, trials=300):
     rng = np.random.default_rng(3)
-    for _ in range(300):
+    for _ in range(trials):
         w, assign, k, c, _ = random_case(rng, False)
         want = orc.reduce(w, assign, k, c)
         assert np.array_equal(orc.reduce_ex(w, assign, k, c, 0, None), want)
         assert np.array_equal(orc.reduce_ex(w, assign, k, c, 0, [c] * k), want)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-@pytest.mark.parametrize("with_cap", [False, True])
-def test_reduction_variants_are_valid(orc, mode, with_cap):
+def check_variants_valid(orc, mode, with_cap, trials=400):
     """Completable partial packing => the reduced instance fits in k bins of
     size c (so every DFF bound of it is <= k)."""
     rng = np.random.default_rng(10 + 2 * mode + with_cap)
     seen = 0
-    for _ in range(400):
+    for _ in range(trials):
         w, assign, k, c, cap = random_case(rng, with_cap)
         if not completions_exist(w, assign, k, c, cap):
             continue
@@ -72,10 +70,10 @@ def test_reduction_variants_are_valid(orc, mode, with_cap):
         red = orc.reduce_ex(w, assign, k, c, mode, cap if with_cap else None)
         assert orc.opt_bins(red, c) <= k, (w, assign, k, c, cap, list(red))
         assert orc.lb(red, c, k)[0] <= k
-    assert seen > 100
+    assert seen > trials // 4
 
 
-def test_closing_only_grows_items(orc):
+def check_closing_grows(orc):
     rng = np.random.default_rng(21)
     grew = 0
     for _ in range(500):
@@ -92,7 +90,7 @@ def test_closing_only_grows_items(orc):
     assert grew > 20
 
 
-def test_full_cap_bin_and_errors(orc):
+def check_examples(orc):
     # a bin whose cap equals its load has no free space: its item is c
     assert list(orc.reduce_ex([3, 4, 2], [0, 1, -1], 2, 10, 0, [3, 10])) == [2, 10, 4]
     # closing: free space 3 of bin 0 is below the smallest unpacked item (4)
@@ -103,3 +101,21 @@ def test_full_cap_bin_and_errors(orc):
         orc.reduce_ex([5], [0], 1, 10, 0, [4])      # load above the cap
     with pytest.raises(ValueError):
         orc.reduce_ex([5], [0], 1, 10, 0, [11])     # cap above c
+
+
+def test_plain_variant_is_the_papers_reduction(orc):
+    check_plain_variant(orc)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("with_cap", [False, True])
+def test_reduction_variants_are_valid(orc, mode, with_cap):
+    check_variants_valid(orc, mode, with_cap)
+
+
+def test_closing_only_grows_items(orc):
+    check_closing_grows(orc)
+
+
+def test_full_cap_bin_and_errors(orc):
+    check_examples(orc)
