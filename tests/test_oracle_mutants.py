@@ -13,7 +13,8 @@ import pytest
 import oracle as O
 from test_oracle_pins import (check_bruteforce_opt, check_dual_feasible_dp, check_fig3,
                               check_full_maximum, check_l1_special_cases, check_l2,
-                              check_param_counts, check_reduction, check_vb2_cap)
+                              check_param_counts, check_reduction, check_vb2_cap,
+                              check_vb2_cap_golden)
 from test_oracle_reduction import (check_closing_grows, check_examples, check_plain_variant,
                                    check_variants_valid)
 
@@ -64,6 +65,15 @@ MUTANTS = [
     ("reduce_ex_close_empty_bins", "if (mode == 1 && v > 0 && (minw < 0 || c - v < minw)) v = c;",
      "if (mode == 1 && v >= 0 && (minw < 0 || c - v < minw)) v = c;"),
     ("reduce_ex_cap_ignored", "int64_t cap = bin_max ? bin_max[j] : c;", "int64_t cap = c;"),
+    # the VB2 cap of Sec. 4: floor(UINT_MAX / (r max w')), at most c
+    ("vb2_cap_no_r", "int64_t cap = (int64_t)4294967295LL / (r * wmax);",
+     "int64_t cap = (int64_t)4294967295LL / wmax;"),
+    ("vb2_cap_sum_not_max", "if (wr[i] > wmax) wmax = wr[i];", "wmax += wr[i];"),
+    ("vb2_cap_signed_limit", "int64_t cap = (int64_t)4294967295LL / (r * wmax);",
+     "int64_t cap = (int64_t)2147483647LL / (r * wmax);"),
+    ("vb2_cap_ceil", "int64_t cap = (int64_t)4294967295LL / (r * wmax);",
+     "int64_t cap = ((int64_t)4294967295LL + r * wmax - 1) / (r * wmax);"),
+    ("vb2_cap_not_min_c", "return cap < c ? cap : c;", "return cap;"),
 ]
 
 BATTERY = (
@@ -74,6 +84,7 @@ BATTERY = (
     lambda o: check_l2(o, trials=150),
     lambda o: check_l1_special_cases(o, trials=60),
     lambda o: check_vb2_cap(o, trials=60),
+    lambda o: check_vb2_cap_golden(o),
     lambda o: check_reduction(o, trials=80),
     lambda o: check_full_maximum(o),
     lambda o: check_plain_variant(o, trials=100),

@@ -12,7 +12,10 @@ Nothing here compares the oracle with itself or with the CUDA path.  The pins:
        lambda = c and at every divisor of c;
   (p5) the worked example of Fig. 3 (tests/golden/fig3_partial_packing.txt)
        and the hand-derived parameter counts (tests/golden/param_counts.txt);
-  (p6) the VB2 overflow cap of Sec. 4 only removes parameters;
+  (p6) the VB2 overflow cap of Sec. 4 only removes parameters, and on the
+       hand-derived cases of tests/golden/vb2_cap.txt (the cap cuts VB2's
+       range below c, stops at c, or empties it) it gives the hand-derived
+       L_VB2 and excludes a better parameter;
   plus reduction invariants (Sec. 3 "Feasibility check").
 Each check is a plain function so that the mutation test can run the whole
 battery against deliberately broken copies of the oracle.
@@ -51,6 +54,24 @@ def load_fig3():
                 out[tok[0]] = int(tok[1])
     out["items"], out["assign"], out["params"] = items, assign, params
     return out
+
+
+def load_vb2_cap():
+    cases = []
+    with open(os.path.join(GOLDEN, "vb2_cap.txt")) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if not line:
+                continue
+            name, c, items, cap, bnd, lam, wl, wlb = line.split()
+            sizes = []
+            for part in items.split(","):
+                cnt, size = part.split("x")
+                sizes += [int(size)] * int(cnt)
+            cases.append(dict(name=name, c=int(c), items=sizes, cap=int(cap),
+                              capped=(int(bnd), int(lam)),
+                              witness=None if wl == "-" else (int(wl), int(wlb))))
+    return cases
 
 
 def load_param_counts():
@@ -196,6 +217,27 @@ def check_vb2_cap(orc, trials=100, seed=14):
             assert cap == full
 
 
+def check_vb2_cap_golden(orc):
+    """The cap of Sec. 4 on hand-derived cases: L_VB2 over the capped range
+    is the hand-derived (bound, first lambda); a witness parameter just past
+    the cap (or past c, where the cap stops) has the hand-derived, larger
+    bound, so the capped range really ends where the golden file says."""
+    for g in load_vb2_cap():
+        c, items = g["c"], g["items"]
+        assert orc.lb_dff(O.VB2, items, c, vb2_cap=True) == g["capped"], g["name"]
+        if g["witness"] is not None:
+            wl, wlb = g["witness"]
+            assert wl > g["cap"] and wlb > g["capped"][0]
+            assert orc.lb_param(O.VB2, wl, items, c) == wlb, g["name"]
+        if g["cap"] >= 2:
+            # the last parameter of the capped range is evaluated: its bound
+            # is at most the capped maximum
+            assert orc.lb_param(O.VB2, g["cap"], items, c) <= g["capped"][0], g["name"]
+        if c <= 4096:  # cap >= c: the capped bound is the uncapped one
+            assert g["cap"] == c
+            assert orc.lb_dff(O.VB2, items, c) == g["capped"], g["name"]
+
+
 def check_reduction(orc, trials=200, seed=15):
     rng = np.random.default_rng(seed)
     for _ in range(trials):
@@ -289,6 +331,10 @@ def test_l1_special_cases(orc):
 
 def test_vb2_cap(orc):
     check_vb2_cap(orc)
+
+
+def test_vb2_cap_golden(orc):
+    check_vb2_cap_golden(orc)
 
 
 def test_full_maximum(orc):
