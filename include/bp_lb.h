@@ -220,13 +220,24 @@ int bp_lb_reduce_nodes(bp_lb_t *h, int32_t B, int32_t num_base,
  *   Its scratch (tile table, result slots, counters: about 82 KB) is one
  *   fixed __device__ array in the library, held by every GPU that loads the
  *   library until the process exits.
- *   The first call on a device looks up that array's device address
- *   (cudaGetSymbolAddress) with the device current; make that first call
- *   before any stream capture on the device.
+ *   The first call on a device (B = 0 is allowed, as a warm-up with NULL
+ *   pointers) does a one-time set-up with the device current: it looks up
+ *   that array's device address (cudaGetSymbolAddress) and queries the two
+ *   kernels it launches.  Under CUDA's lazy module loading (the default,
+ *   CUDA_MODULE_LOADING=LAZY) that is when the driver loads this library's
+ *   kernels and the array onto the device, which may take device memory, so
+ *   make that first call at start-up, before another allocator takes the
+ *   device and before any stream capture on it.  The address is kept per
+ *   device for the life of the process: cudaDeviceReset after the first
+ *   call is not supported.
  *   All calls share the one array: calls whose work overlaps on the GPU (on
  *   different streams, or from different host threads) race and give wrong
  *   results; order them on one stream.  Each call clears the parts it uses.
- *   It always uses launch shape 0 (no autotuning: that needs a handle).
+ *   It evaluates every DFF item by item in the generic kernel (the
+ *   BP_ALGO_DIRECT algorithm, VB2 included) with launch shape 0 and no
+ *   autotuning: the prefix-count tables and the separate VB2 kernel need
+ *   scratch that only a handle owns.  At large capacities that costs several
+ *   times a handle's default path, more as c grows.
  * Errors: BP_EINVAL (NULL required pointer, B < 0), BP_ERANGE
  * (B > BP_NOALLOC_MAX_BATCH, checked before any launch), BP_ECUDA. */
 int bp_lb_eval_batch_noalloc(int32_t B, const int64_t *d_offsets,
@@ -329,6 +340,30 @@ int bp_lb_set_pruning(bp_lb_t *h, int32_t on);
 
 /* The handle's pruning switch, or -1 for a NULL handle. */
 int bp_lb_get_pruning(bp_lb_t *h);
+
+/* ---- VB2's parameter cap (the paper's overflow guard) ----------------------- */
+
+/* Sec. 4 ("Implementation details") limits VB2's parameter to
+ * floor(UINT_MAX / (r max w')), UINT_MAX = 2^32 - 1, r the number of items of
+ * the reduced instance and max w' the largest of them, because the paper's
+ * kernels hold VB2's intermediates in unsigned 32-bit integers.  This library
+ * computes every bound exactly and by default evaluates VB2 over its whole
+ * printed range [2, c] (Sec. 3.1).  With the cap on (1), VB2 is evaluated over
+ * [2, min(c, floor(UINT_MAX / (r max w')))] instead (the whole range when
+ * r max w' = 0; no VB2 parameter at all when the floor is below 2), so that
+ * the bound the paper's implementation computes can be reproduced; the other
+ * DFFs and the arithmetic are unchanged.  r counts every entry of a reduced
+ * instance given as a list (zero sizes included) and, for a search node, its
+ * unpacked items plus one item per non-empty bin (after a reduction variant,
+ * per bp_lb_set_reduction).  Applies to every evaluation call of the handle
+ * (batched and plain; not bp_lb_debug_params, which takes any lambda in
+ * [2, c]); costs one extra launch per call.  An invalid instance is reported
+ * as without the cap.  Default off (0).
+ * Errors: BP_EINVAL (NULL handle), BP_ERANGE (not 0 or 1). */
+int bp_lb_set_vb2_cap(bp_lb_t *h, int32_t on);
+
+/* The handle's VB2 cap switch, or -1 for a NULL handle. */
+int bp_lb_get_vb2_cap(bp_lb_t *h);
 
 /* ---- L2, the comparator ---------------------------------------------------- */
 

@@ -84,6 +84,8 @@ def _bind(lib):
         "bp_lb_get_reduction": (ctypes.c_int, [_vp]),
         "bp_lb_set_bin_max": (ctypes.c_int, [_vp, _vp, _vp]),
         "bp_lb_get_pruning": (ctypes.c_int, [_vp]),
+        "bp_lb_set_vb2_cap": (ctypes.c_int, [_vp, _c_i32]),
+        "bp_lb_get_vb2_cap": (ctypes.c_int, [_vp]),
         "bp_lb_set_dff_mask": (ctypes.c_int, [_vp, _c_i32]),
         "bp_lb_set_overlap": (ctypes.c_int, [_vp, _c_i32]),
         "bp_lb_l2_batch": (ctypes.c_int, [_vp, _c_i32, _vp, _vp, _vp, _vp, _vp]),
@@ -132,7 +134,8 @@ EXPORTED = ("bp_lb_strerror", "bp_lb_create", "bp_lb_destroy", "bp_lb_reserve", 
             "bp_lb_set_result_mode", "bp_lb_get_result_mode", "bp_lb_set_dff_mask",
             "bp_lb_get_dff_mask", "bp_lb_l2_batch", "bp_lb_set_overlap", "bp_lb_set_pruning",
             "bp_lb_get_pruning", "bp_lb_kernel_work", "bp_lb_set_reduction",
-            "bp_lb_get_reduction", "bp_lb_set_bin_max")
+            "bp_lb_get_reduction", "bp_lb_set_bin_max", "bp_lb_set_vb2_cap",
+            "bp_lb_get_vb2_cap")
 
 ALGO_DIRECT, ALGO_PREFIX = 0, 1
 RESULT_FULL, RESULT_VERDICT = 0, 1
@@ -370,6 +373,15 @@ def bp_lb_set_pruning(h, on: bool):
 
 def bp_lb_get_pruning(h) -> int:
     return lib().bp_lb_get_pruning(h)
+
+
+def bp_lb_set_vb2_cap(h, on: bool):
+    """The paper's VB2 parameter cap (Sec. 4) on or off (default off)."""
+    _check(lib().bp_lb_set_vb2_cap(h, int(bool(on))), "bp_lb_set_vb2_cap")
+
+
+def bp_lb_get_vb2_cap(h) -> int:
+    return lib().bp_lb_get_vb2_cap(h)
 
 
 def bp_lb_set_overlap(h, prefix_ctas_per_sm: int):

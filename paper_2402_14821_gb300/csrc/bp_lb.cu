@@ -86,6 +86,11 @@ struct bp_lb {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   uint32_t dff_off = 0;  // DFFs left out of the bound (bit d), default none
+  // VB2's parameter cap of Sec. 4 (bp_lb_set_vb2_cap): off by default; when
+  // on, vb2cap_kernel writes each instance's last VB2 parameter here
+  int32_t vb2_cap = 0;
+  int64_t *d_vb2hi = nullptr;   // [cap_batch], batched calls
+  int64_t *d_vb2hi1 = nullptr;  // [1], the plain path
   // optional per-kernel timing of batched calls (events around each launch)
   bool timing = false;
   unsigned long long *d_work_count = nullptr;  // 4 counters (EvalArgs::work_count)
@@ -159,7 +164,9 @@ int grow_batch(bp_lb *h, int32_t B) {
   cudaFree(h->d_keys);
   cudaFree(h->d_done);
   cudaFree(h->d_isums);
+  cudaFree(h->d_vb2hi);
   h->d_isums = nullptr;
+  h->d_vb2hi = nullptr;
   h->d_tile_start = nullptr;
   h->d_ptile_start = nullptr;
   h->d_vtile_start = nullptr;
@@ -172,6 +179,7 @@ int grow_batch(bp_lb *h, int32_t B) {
   BP_CHECK(cudaMalloc(&h->d_keys, sizeof(unsigned long long) * (size_t)cap));
   BP_CHECK(cudaMalloc(&h->d_done, sizeof(unsigned int) * (size_t)cap));
   BP_CHECK(cudaMalloc(&h->d_isums, sizeof(long long) * 8 * (size_t)cap));
+  BP_CHECK(cudaMalloc(&h->d_vb2hi, sizeof(int64_t) * (size_t)cap));
   BP_CHECK(cudaMemset(h->d_isums, 0, sizeof(long long) * 8 * (size_t)cap));
   BP_CHECK(cudaMemset(h->d_keys, 0, sizeof(unsigned long long) * (size_t)cap));
   BP_CHECK(cudaMemset(h->d_done, 0, sizeof(unsigned int) * (size_t)cap));
@@ -214,6 +222,19 @@ int32_t prefix_bits(bp_lb *h, bool on, int64_t ctas) {
     }
   }
   return kPrefixShared | ((h->d_gscratch && ctas <= h->gscratch_ctas) ? kPrefixGlobal : 0);
+}
+
+// VB2's cap (vb2cap_kernel) of the A.B instances into hi[0 .. A.B).
+int launch_vb2cap(bp_lb *h, int mode, const EvalArgs &A, int64_t *hi, cudaStream_t st) {
+  const unsigned grid = (unsigned)std::min<int64_t>(A.B, (int64_t)h->num_sms * 8);
+  const size_t smem = mode == kSrcNodes ? sizeof(uint32_t) * (size_t)A.max_bins : 0;
+  if (mode == kSrcRaggedI32)
+    vb2cap_kernel<256, kSrcRaggedI32><<<grid, 256, smem, st>>>(A, hi);
+  else if (mode == kSrcRaggedI64)
+    vb2cap_kernel<256, kSrcRaggedI64><<<grid, 256, smem, st>>>(A, hi);
+  else
+    vb2cap_kernel<256, kSrcNodes><<<grid, 256, smem, st>>>(A, hi);
+  return cuda_status(cudaGetLastError());
 }
 
 // Dynamic shared memory of the VB2 kernel.
@@ -263,6 +284,11 @@ int launch_batch(bp_lb *h, EvalArgs A, size_t smem, cudaStream_t st) {
   plan_kernel<MODE><<<1, 1024, 0, st>>>(A, shape_lpt(shape), h->d_tile_start, h->d_ptile_start,
                                         h->d_vtile_start);
   BP_CHECK(cudaGetLastError());
+  if (h->vb2_cap) {
+    // each instance's last VB2 parameter under the cap, before any VB2 tile
+    A.vb2_hi = h->d_vb2hi;
+    BP_CHECK_STATUS(launch_vb2cap(h, MODE, A, h->d_vb2hi, st));
+  }
   // Timing events: [0] before the prefix kernel, [1] after it, [2] before the
   // VB2 kernel, [3] after it, [4] before the generic kernel, [5] after it.
   std::array<cudaEvent_t, 6> ev = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -414,6 +440,7 @@ int bp_lb_create(int64_t capacity, int64_t max_items, bp_lb_t **out) {
     if ((st = cuda_status(cudaMalloc(&h->d_key1, sizeof(unsigned long long)))) != BP_OK) break;
     if ((st = cuda_status(cudaMalloc(&h->d_done1, sizeof(unsigned int)))) != BP_OK) break;
     if ((st = cuda_status(cudaMalloc(&h->d_work, 4 * sizeof(unsigned long long)))) != BP_OK) break;
+    if ((st = cuda_status(cudaMalloc(&h->d_vb2hi1, sizeof(int64_t)))) != BP_OK) break;
     if ((st = cuda_status(cudaMemset(h->d_key1, 0, sizeof(unsigned long long)))) != BP_OK) break;
     if ((st = cuda_status(cudaMemset(h->d_done1, 0, sizeof(unsigned int)))) != BP_OK) break;
     if ((st = cuda_status(cudaMemset(h->d_work, 0, 4 * sizeof(unsigned long long)))) != BP_OK)
@@ -438,6 +465,10 @@ int bp_lb_create(int64_t capacity, int64_t max_items, bp_lb_t **out) {
     if ((st = cuda_status(cudaFuncSetAttribute(l2_kernel<kL2NT>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)kL2SmemBytes))) != BP_OK)
+      break;
+    if ((st = cuda_status(cudaFuncSetAttribute(vb2cap_kernel<256, kSrcNodes>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)(sizeof(uint32_t) * kMaxNodeBins)))) != BP_OK)
       break;
     if ((st = cuda_status(cudaFuncSetAttribute(reduce_kernel<256>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -473,6 +504,8 @@ int bp_lb_destroy(bp_lb_t *h) {
   cudaFree(h->d_gscratch);
   cudaFree(h->d_work_count);
   cudaFree(h->d_isums);
+  cudaFree(h->d_vb2hi);
+  cudaFree(h->d_vb2hi1);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   if (h->stream) cudaStreamDestroy(h->stream);
   if (h->side) cudaStreamDestroy(h->side);
@@ -558,6 +591,10 @@ int bp_lb_eval(bp_lb_t *h, const int32_t *sizes, int64_t n, int64_t bins, int64_
   EvalArgs A = plain_args(h, n, bins, kModePlainRagged);
   A.sizes = h->d_items;
   if (A.single_ptiles + A.single_tiles == 0) return plain_empty(out_bound, out_argmax);
+  if (h->vb2_cap) {
+    A.vb2_hi = h->d_vb2hi1;
+    BP_CHECK_STATUS(launch_vb2cap(h, kSrcRaggedI32, A, h->d_vb2hi1, h->stream));
+  }
   if (A.single_ptiles > 0)
     BP_CHECK_STATUS(launch_prefix(kSrcRaggedI32, (unsigned)A.single_ptiles,
                                   prefix_smem(kSrcRaggedI32, 0), h->stream, A));
@@ -584,6 +621,10 @@ int bp_lb_eval_node(bp_lb_t *h, const int32_t *w, const int32_t *assign, int64_t
   A.assign = h->d_assign;
   A.max_bins = (int32_t)bins;
   if (A.single_ptiles + A.single_tiles == 0) return plain_empty(out_bound, out_argmax);
+  if (h->vb2_cap) {
+    A.vb2_hi = h->d_vb2hi1;
+    BP_CHECK_STATUS(launch_vb2cap(h, kSrcNodes, A, h->d_vb2hi1, h->stream));
+  }
   if (A.single_ptiles > 0)
     BP_CHECK_STATUS(launch_prefix(kSrcNodes, (unsigned)A.single_ptiles, prefix_smem(kSrcNodes, bins),
                                   h->stream, A));
@@ -731,6 +772,18 @@ int bp_lb_set_algorithm(bp_lb_t *h, int32_t algo) {
   if (algo != BP_ALGO_DIRECT && algo != BP_ALGO_PREFIX) return BP_ERANGE;
   h->prefix_on = h->plain_prefix_on = algo == BP_ALGO_PREFIX;
   return BP_OK;
+}
+
+int bp_lb_set_vb2_cap(bp_lb_t *h, int32_t on) {
+  if (!h) return BP_EINVAL;
+  if (on != 0 && on != 1) return BP_ERANGE;
+  h->vb2_cap = on;
+  return BP_OK;
+}
+
+int bp_lb_get_vb2_cap(bp_lb_t *h) {
+  if (!h) return -1;
+  return h->vb2_cap;
 }
 
 int bp_lb_set_result_mode(bp_lb_t *h, int32_t mode) {

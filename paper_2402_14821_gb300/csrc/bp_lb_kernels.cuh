@@ -96,6 +96,11 @@ struct EvalArgs {
   int32_t pad_reduce;
   const int64_t *bin_max_offsets;
   const int32_t *bin_max;
+  // VB2's parameter cap of Sec. 4 (bp_lb_set_vb2_cap): per instance the
+  // largest VB2 parameter evaluated, min(c, floor(UINT_MAX / (r max w'))),
+  // written by vb2cap_kernel before the evaluation kernels; nullptr: VB2's
+  // whole range [2, c].
+  const int64_t *vb2_hi;
 };
 
 // Shared-memory budget of the prefix-count tables (bytes; 48 KB lets four
@@ -314,6 +319,12 @@ __device__ __forceinline__ void write_result(const EvalArgs &A, int64_t b, unsig
     A.out_argmax[b] = r;
   }
   if (A.out_feasible) A.out_feasible[b] = (uint8_t)(lb <= k);
+}
+
+// Last VB2 parameter of instance b: its range's upper end, or the cap of
+// Sec. 4 when the handle has it on (vb2cap_kernel).
+__device__ __forceinline__ int64_t vb2_last(const EvalArgs &A, int64_t b, int64_t hi_d) {
+  return A.vb2_hi != nullptr ? min(hi_d, A.vb2_hi[b]) : hi_d;
 }
 
 // ---------------------------------------------------------------------------
@@ -1073,8 +1084,9 @@ __device__ void process_tile(const EvalArgs &A, int64_t b, int64_t lt, int64_t n
   }
   int64_t lo_d, hi_d;
   param_range(d, c, lo_d, hi_d);
+  if (d == kVB2) hi_d = vb2_last(A, b, hi_d);
   const int64_t lam0 = lo_d + rem * LPT;
-  const int64_t lam_end = min(hi_d + 1, lam0 + LPT);
+  const int64_t lam_end = max(lam0, min(hi_d + 1, lam0 + LPT));
 
   unsigned long long *vslot = A.verdict ? &A.keys[b] : nullptr;
   if (tid == 0) {
@@ -1253,6 +1265,111 @@ __global__ void __launch_bounds__(NT)
     default: tile_dff<NT, 1, kBJ1, kSrcRaggedI32, true>(A, I, 0, 0, s_items, s_a, nullptr, S, req_lam, req_out, idx); break;
   }
   if (S.err && idx >= 0) req_out[idx] = -BP_ERANGE;  // a size outside [0, c]
+}
+
+// ---------------------------------------------------------------------------
+// vb2cap_kernel: VB2's parameter cap of Sec. 4 ("Implementation details"),
+// the paper's guard against 32-bit overflow: the largest VB2 parameter is
+// floor(UINT_MAX / (r max w')), r the number of items of the reduced instance
+// and max w' the largest of them, and never above c (VB2's range is [2, c]);
+// an instance with r = 0 or max w' = 0 keeps [2, c].  One CTA per instance
+// (grid-stride); for a search node the reduced instance is its unpacked items
+// (zero sizes included) and one item per non-empty bin, as in the reduction
+// of Fig. 3 and its variants (transform_bins).  Writes hi[b]; an invalid
+// instance (bad size or assignment, overfull bin) gets c, so that every one of
+// its VB2 tiles still stages it and reports the error.  The bounds themselves
+// stay exact: only the range changes.
+// ---------------------------------------------------------------------------
+template <int NT, int MODE>
+__global__ void __launch_bounds__(NT) vb2cap_kernel(EvalArgs A, int64_t *hi) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint32_t *s_load = reinterpret_cast<uint32_t *>(smem_raw);
+  __shared__ int s_err;
+  __shared__ uint32_t s_minw;
+  __shared__ unsigned long long s_r, s_wmax;
+  for (int64_t b = blockIdx.x; b < A.B; b += gridDim.x) {
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+      s_err = 0;
+      s_minw = 0xFFFFFFFFu;
+      s_r = 0ull;
+      s_wmax = 0ull;
+    }
+    InstView I;
+    bool ok;
+    if (MODE == kSrcNodes && A.tile_start != nullptr) {
+      const int32_t base = A.node_base[b];
+      ok = base >= 0 && base < A.num_base;
+      if (ok) ok = A.base_offsets[base + 1] - A.base_offsets[base] ==
+                   A.assign_offsets[b + 1] - A.assign_offsets[b];
+      if (ok) I = resolve_instance<MODE>(A, b);
+      else I.c = 0;
+      ok = ok && I.c >= 1 && I.c <= kMaxCapacity && I.n >= 0 && I.n <= kMaxItems && I.k >= 0 &&
+           I.k <= A.max_bins &&
+           (A.bin_max == nullptr || A.bin_max_offsets[b + 1] - A.bin_max_offsets[b] == I.k);
+    } else {
+      I = resolve_instance<MODE>(A, b);
+      ok = I.c >= 1 && I.c <= kMaxCapacity && I.n >= 0 && I.n <= kMaxItems;
+    }
+    if (!ok) {
+      if (tid == 0) hi[b] = max(I.c, (int64_t)0);
+      __syncthreads();
+      continue;
+    }
+    __syncthreads();
+    uint64_t r = 0, wmax = 0;
+    if (MODE == kSrcNodes) {
+      for (int64_t j = tid; j < I.k; j += NT) s_load[j] = 0u;
+      __syncthreads();
+      for (int64_t i = tid; i < I.n; i += NT) {
+        const int32_t a = I.a[i], w = I.w[i];
+        if (w < 0 || (int64_t)w > I.c || a < -1 || (int64_t)a >= I.k) {
+          s_err = 1;
+        } else if (a >= 0) {
+          const uint32_t old = atomicAdd(&s_load[a], (uint32_t)w);
+          if ((int64_t)old + w > I.c) s_err = 1;
+        } else {
+          ++r;  // an unpacked item, zero sizes included
+          wmax = max(wmax, (uint64_t)w);
+          if (w > 0) atomicMin(&s_minw, (uint32_t)w);
+        }
+      }
+      __syncthreads();
+      if (!s_err && bins_transformed(A)) {
+        transform_bins<NT>(A, b, I, s_load, s_minw, &s_err);
+        __syncthreads();
+      }
+      for (int64_t j = tid; j < I.k; j += NT) {
+        const uint32_t v = s_load[j];
+        r += v > 0u;  // empty bins are dropped
+        wmax = max(wmax, (uint64_t)v);
+      }
+    } else {
+      if (tid == 0) r = (uint64_t)I.n;  // every entry of the list is an item
+      for (int64_t q = tid; q < I.n; q += NT) {
+        int64_t w = 0;
+        fetch_item<MODE>(A, I, nullptr, q, w);
+        if (w < 0 || w > I.c) s_err = 1;
+        else wmax = max(wmax, (uint64_t)w);
+      }
+    }
+    r = warp_sum(r);
+    wmax = warp_max_u64(wmax);
+    if (lane_id() == 0) {
+      atomicAdd(&s_r, (unsigned long long)r);
+      atomicMax(&s_wmax, (unsigned long long)wmax);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const uint64_t rw = s_r * s_wmax;  // < 2^52: r <= 2^20 + 2^14, w' <= 2^30
+      int64_t v = I.c;
+      // an invalid instance keeps its whole range, so that each of its VB2
+      // tiles meets (and reports) the error
+      if (rw != 0ull && !s_err) v = min(v, (int64_t)(4294967295ull / rw));
+      hi[b] = v;
+    }
+    __syncthreads();
+  }
 }
 
 // ---------------------------------------------------------------------------

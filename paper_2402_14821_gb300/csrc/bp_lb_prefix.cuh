@@ -559,8 +559,8 @@ constexpr int64_t kVb2TableTerms = 1 << 16;  // lookups per tile at most
 
 template <int MODE>
 __device__ __forceinline__ int vb2_table_plan(const EvalArgs &A, const InstView &I,
-                                              const PrefixShared &S, uint32_t L1, int64_t &kk,
-                                              int64_t &lmax) {
+                                              const PrefixShared &S, uint32_t L1,
+                                              int64_t vb2_cap_hi, int64_t &kk, int64_t &lmax) {
   const int64_t c = I.c;
   if (!(A.prune || A.verdict) || ((A.dff_off >> kVB2) & 1u) || !A.vb2_on || c > kVb2FixedCap ||
       c < 2)
@@ -577,6 +577,10 @@ __device__ __forceinline__ int vb2_table_plan(const EvalArgs &A, const InstView 
   if (alpha >= 0) return (alpha * c + beta <= 0) ? 2 : 0;
   if (2 * alpha + beta <= 0) return 2;
   lmax = min(c, (beta - 1) / (-alpha));
+  if (A.vb2_hi != nullptr) {  // the cap of Sec. 4: no parameter above it
+    lmax = min(lmax, vb2_cap_hi);
+    if (lmax < 2) return 2;
+  }
   const int64_t U = (c - 1) / 2;
   return (U * lmax * lmax / (2 * c) + lmax <= kVb2TableTerms) ? 1 : 0;
 }
@@ -740,7 +744,8 @@ __device__ __forceinline__ unsigned long long prefix_tile(const EvalArgs &A, con
     int64_t kk = 0, lmax = 0;
     if (D == kPrefixU && !S.err) {
       const uint32_t sw32 = (uint32_t)S.sums[5];
-      mode = vb2_table_plan<MODE>(A, I, S, sw32 / c32 + (sw32 % c32 != 0u), kk, lmax);
+      const int64_t vhi = A.vb2_hi != nullptr ? A.vb2_hi[b] : c;
+      mode = vb2_table_plan<MODE>(A, I, S, sw32 / c32 + (sw32 % c32 != 0u), vhi, kk, lmax);
     }
     S.vb2_mode = mode;
     S.vb2_kk = kk;

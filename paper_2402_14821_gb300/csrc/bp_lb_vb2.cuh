@@ -47,13 +47,14 @@ __global__ void __launch_bounds__(kVb2NT, vb2_minb(VT)) vb2_kernel(EvalArgs A) {
     const int64_t ntiles = instance_tiles(A, b);
     int64_t lo_d, hi_d;
     param_range(kVB2, I.c, lo_d, hi_d);
+    hi_d = vb2_last(A, b, hi_d);  // the cap of Sec. 4, when on
     const int64_t lam0 = lo_d + (t - t0) * vlpt;
-    const int64_t lam_end = min(hi_d + 1, lam0 + vlpt);
+    const int64_t lam_end = max(lam0, min(hi_d + 1, lam0 + vlpt));
 
     unsigned long long *vslot = A.verdict ? &A.keys[b] : nullptr;
     if (threadIdx.x == 0) {
       S.err = 0;
-      S.skip = (vslot != nullptr && slot_decided(vslot, I.k)) ? 1 : 0;
+      S.skip = ((vslot != nullptr && slot_decided(vslot, I.k)) || lam_end <= lam0) ? 1 : 0;
       // the whole tile pruned (vb2_range_may_exceed) from the instance sums the
       // prefix kernel published, before anything is staged
       if (!S.skip && A.isums != nullptr && (A.verdict || A.prune)) {
