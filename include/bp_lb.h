@@ -435,6 +435,22 @@ int bp_lb_kernel_times(bp_lb_t *h, double *ms_prefix, double *ms_vb2, double *ms
  * Errors: BP_EINVAL (NULL pointer), BP_ECUDA. */
 int bp_lb_kernel_work(bp_lb_t *h, int64_t *out4);
 
+/* Measurement aid with no counterpart in the paper: the integer instruction
+ * issue rate of the current device, the peak against which the item-by-item
+ * kernels' roofline is reported.  Launches (stream-ordered, asynchronous)
+ * blocks_per_sm x SM-count CTAs of 256 threads that run only integer
+ * multiply-adds and xors in eight independent chains per thread (the two
+ * half-rate integer pipes together allow one warp instruction per clock per
+ * sub-partition), `trips` loop trips of 64 such operations each, and writes
+ * one word per thread to d_sink (device, caller-owned, at least
+ * blocks_per_sm x SM-count x 256 uint32).  *out_lane_ops receives the
+ * number of integer lane operations the launch performs; divided by the
+ * launch's CUDA-event time it is the sustained integer issue rate.
+ * Errors: BP_EINVAL (blocks_per_sm outside 1..8, trips < 1, NULL pointer),
+ * BP_ECUDA. */
+int bp_lb_probe_int_issue(int32_t blocks_per_sm, int32_t trips, uint32_t *d_sink,
+                          void *stream, int64_t *out_lane_ops);
+
 /* ---- launch shapes and autotuning ---------------------------------------- */
 
 /* Input modes of the evaluation kernel, for the launch-shape calls below. */
@@ -577,6 +593,36 @@ int bp_serve_poll(bp_serve_t *s, bp_serve_result_t *out, int32_t max_results,
  * BP_OK, or BP_ECUDA once a batch failed on the device. */
 int bp_serve_stats(bp_serve_t *s, int64_t *pending, int64_t *queued_items,
                    int64_t *batches, int64_t *done, int64_t *refused);
+
+/* ---- one instance over a range of parameters (sharding one check) -------- */
+
+/* The bound of Alg. 2 restricted to a contiguous range of parameters: the
+ * flattened index g numbers every (DFF, lambda) pair in the paper's order
+ * (MT, RAD2, FS1, CCM1, VB2, BJ1; lambda ascending within a DFF; Sec. 3.1
+ * ranges), 0 <= g < P(c) = sum of bp_lb_param_count over the six DFFs.  Over
+ * the pairs with g0 <= g < g1 this computes the largest bound and the
+ * smallest g attaining it, packed into one key
+ *   key = (bound << 32) | (2^32 - 1 - g),
+ * so that the maximum key over a partition of [0, P(c)) into ranges is the
+ * full bound and its first argmax (the collection's maximum, Alg. 2, with the
+ * first-attaining tie-break): one instance too large for one GPU is split
+ * over ranks by range, and the ranks' keys meet in one 8-byte MAX all-reduce.
+ *   d_sizes   device int32 sizes of the reduced instance, n of them, each in
+ *             [0, c];
+ *   c         its capacity, 1 <= c <= 2^30;
+ *   g0, g1    0 <= g0 <= g1 <= P(c);
+ *   d_out_key device int64[1] (caller-owned): the key; 0 when the range holds
+ *             no parameter (of the handle's DFF mask); -BP_ERANGE for a size
+ *             outside [0, c] (found by the range's evaluation).
+ * Every pair is evaluated item by item in the generic kernel (the handle's
+ * launch shape for BP_MODE_RAGGED_I32); the handle's DFF mask, VB2 pruning
+ * (exact, against the range's own best key) and VB2 cap apply.  Stream-
+ * ordered on `stream`; calls on one handle must be ordered on one stream.
+ * Errors: BP_EINVAL (NULL handle or pointer, n < 0), BP_ERANGE (c, n, or the
+ * range outside the limits above), BP_ECUDA. */
+int bp_lb_eval_range(bp_lb_t *h, const int32_t *d_sizes, int64_t n,
+                     int64_t c, int64_t g0, int64_t g1, int64_t *d_out_key,
+                     void *stream);
 
 /* ---- inspection -------------------------------------------------------- */
 

@@ -85,6 +85,8 @@ def _bind(lib):
         "bp_lb_set_bin_max": (ctypes.c_int, [_vp, _vp, _vp]),
         "bp_lb_get_pruning": (ctypes.c_int, [_vp]),
         "bp_lb_set_vb2_cap": (ctypes.c_int, [_vp, _c_i32]),
+        "bp_lb_probe_int_issue": (ctypes.c_int, [_c_i32, _c_i32, _vp, _vp, _i64p]),
+        "bp_lb_eval_range": (ctypes.c_int, [_vp, _vp, _c_i64, _c_i64, _c_i64, _c_i64, _vp, _vp]),
         "bp_lb_get_vb2_cap": (ctypes.c_int, [_vp]),
         "bp_lb_set_dff_mask": (ctypes.c_int, [_vp, _c_i32]),
         "bp_lb_set_overlap": (ctypes.c_int, [_vp, _c_i32]),
@@ -135,7 +137,7 @@ EXPORTED = ("bp_lb_strerror", "bp_lb_create", "bp_lb_destroy", "bp_lb_reserve", 
             "bp_lb_get_dff_mask", "bp_lb_l2_batch", "bp_lb_set_overlap", "bp_lb_set_pruning",
             "bp_lb_get_pruning", "bp_lb_kernel_work", "bp_lb_set_reduction",
             "bp_lb_get_reduction", "bp_lb_set_bin_max", "bp_lb_set_vb2_cap",
-            "bp_lb_get_vb2_cap")
+            "bp_lb_get_vb2_cap", "bp_lb_eval_range", "bp_lb_probe_int_issue")
 
 ALGO_DIRECT, ALGO_PREFIX = 0, 1
 RESULT_FULL, RESULT_VERDICT = 0, 1
@@ -373,6 +375,28 @@ def bp_lb_set_pruning(h, on: bool):
 
 def bp_lb_get_pruning(h) -> int:
     return lib().bp_lb_get_pruning(h)
+
+
+def bp_lb_eval_range(h, sizes, c: int, g0: int, g1: int, out_key, stream=None):
+    """Packed key (bound << 32 | 2^32 - 1 - g) of one reduced instance (int32
+    CUDA tensor) over the flattened parameter indices [g0, g1), written to the
+    int64 CUDA tensor out_key[0]."""
+    import torch
+    n = int(sizes.numel())
+    _check(lib().bp_lb_eval_range(h, _ptr(sizes, torch.int32, "sizes") if n else None, n, int(c),
+                                  int(g0), int(g1), _ptr(out_key, torch.int64, "out_key"),
+                                  _stream(stream)), "bp_lb_eval_range")
+
+
+def bp_lb_probe_int_issue(blocks_per_sm: int, trips: int, sink, stream=None) -> int:
+    """Launches the integer-issue probe; returns the lane operations it performs
+    (time the launch with CUDA events on `stream`)."""
+    import torch
+    ops = ctypes.c_int64()
+    _check(lib().bp_lb_probe_int_issue(int(blocks_per_sm), int(trips),
+                                       _ptr(sink, torch.int32, "sink"), _stream(stream),
+                                       ctypes.byref(ops)), "bp_lb_probe_int_issue")
+    return ops.value
 
 
 def bp_lb_set_vb2_cap(h, on: bool):

@@ -91,6 +91,12 @@ struct bp_lb {
   int32_t vb2_cap = 0;
   int64_t *d_vb2hi = nullptr;   // [cap_batch], batched calls
   int64_t *d_vb2hi1 = nullptr;  // [1], the plain path
+  // bp_lb_eval_range: its own result slot, ticket and (unused) outputs, so
+  // that it never shares scratch with the plain path's stream
+  unsigned long long *d_rkey = nullptr;
+  unsigned int *d_rdone = nullptr;
+  PlainOut *d_rout = nullptr;
+  int64_t *d_rvb2hi = nullptr;
   // optional per-kernel timing of batched calls (events around each launch)
   bool timing = false;
   unsigned long long *d_work_count = nullptr;  // 4 counters (EvalArgs::work_count)
@@ -441,6 +447,12 @@ int bp_lb_create(int64_t capacity, int64_t max_items, bp_lb_t **out) {
     if ((st = cuda_status(cudaMalloc(&h->d_done1, sizeof(unsigned int)))) != BP_OK) break;
     if ((st = cuda_status(cudaMalloc(&h->d_work, 4 * sizeof(unsigned long long)))) != BP_OK) break;
     if ((st = cuda_status(cudaMalloc(&h->d_vb2hi1, sizeof(int64_t)))) != BP_OK) break;
+    if ((st = cuda_status(cudaMalloc(&h->d_rkey, sizeof(unsigned long long)))) != BP_OK) break;
+    if ((st = cuda_status(cudaMalloc(&h->d_rdone, sizeof(unsigned int)))) != BP_OK) break;
+    if ((st = cuda_status(cudaMalloc(&h->d_rout, sizeof(PlainOut)))) != BP_OK) break;
+    if ((st = cuda_status(cudaMalloc(&h->d_rvb2hi, sizeof(int64_t)))) != BP_OK) break;
+    if ((st = cuda_status(cudaMemset(h->d_rkey, 0, sizeof(unsigned long long)))) != BP_OK) break;
+    if ((st = cuda_status(cudaMemset(h->d_rdone, 0, sizeof(unsigned int)))) != BP_OK) break;
     if ((st = cuda_status(cudaMemset(h->d_key1, 0, sizeof(unsigned long long)))) != BP_OK) break;
     if ((st = cuda_status(cudaMemset(h->d_done1, 0, sizeof(unsigned int)))) != BP_OK) break;
     if ((st = cuda_status(cudaMemset(h->d_work, 0, 4 * sizeof(unsigned long long)))) != BP_OK)
@@ -506,6 +518,10 @@ int bp_lb_destroy(bp_lb_t *h) {
   cudaFree(h->d_isums);
   cudaFree(h->d_vb2hi);
   cudaFree(h->d_vb2hi1);
+  cudaFree(h->d_rkey);
+  cudaFree(h->d_rdone);
+  cudaFree(h->d_rout);
+  cudaFree(h->d_rvb2hi);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   if (h->stream) cudaStreamDestroy(h->stream);
   if (h->side) cudaStreamDestroy(h->side);
@@ -765,6 +781,51 @@ int bp_lb_debug_params(bp_lb_t *h, const int32_t *d_sizes, int64_t n, int64_t c,
                                                                      d_out_lb);
   BP_CHECK(cudaGetLastError());
   return BP_OK;
+}
+
+int bp_lb_eval_range(bp_lb_t *h, const int32_t *d_sizes, int64_t n, int64_t c, int64_t g0,
+                     int64_t g1, int64_t *d_out_key, void *stream) {
+  if (!h || n < 0 || (n > 0 && !d_sizes) || !d_out_key) return BP_EINVAL;
+  if (c < 1 || c > kMaxCapacity || n > kMaxItems) return BP_ERANGE;
+  if (g0 < 0 || g0 > g1 || g1 > param_total(c)) return BP_ERANGE;
+  cudaStream_t st = (cudaStream_t)stream;
+  EvalArgs A = blank_args();
+  A.B = 1;
+  A.sizes = d_sizes;
+  A.single_c = c;
+  A.single_k = 0;
+  A.single_n = n;
+  A.out_bound = &h->d_rout->bound;
+  A.out_argmax = &h->d_rout->arg;
+  A.out_feasible = &h->d_rout->feasible;
+  A.out_key = d_out_key;
+  A.windowed = 1;
+  A.g_lo = (uint32_t)g0;
+  A.g_hi = (uint32_t)g1;
+  A.prefix_on = 0;  // every parameter item by item in the generic kernel
+  A.vb2_on = 0;
+  A.prune = h->prune;  // VB2 against this window's own best key so far (exact)
+  A.dff_off = h->dff_off;
+  A.keys = h->d_rkey;
+  A.done = h->d_rdone;
+  const int shape = h->shape[BP_MODE_RAGGED_I32];
+  const int64_t lpt = shape_lpt(shape);
+  int64_t tiles = 0;
+  for (int d = 0; d < kNumDff; ++d) {
+    if ((h->dff_off >> d) & 1u) continue;
+    int64_t lo, hi;
+    tiles += (window_range(d, c, 1, (uint32_t)g0, (uint32_t)g1, lo, hi) + lpt - 1) / lpt;
+  }
+  A.single_tiles = tiles;
+  if (tiles == 0) {  // no parameter in the window: key 0
+    BP_CHECK(cudaMemsetAsync(d_out_key, 0, sizeof(int64_t), st));
+    return BP_OK;
+  }
+  if (h->vb2_cap) {
+    A.vb2_hi = h->d_rvb2hi;
+    BP_CHECK_STATUS(launch_vb2cap(h, kSrcRaggedI32, A, h->d_rvb2hi, st));
+  }
+  return launch_eval(shape, kSrcRaggedI32, (unsigned)tiles, eval_smem<kSrcRaggedI32>(0), st, A);
 }
 
 int bp_lb_set_algorithm(bp_lb_t *h, int32_t algo) {

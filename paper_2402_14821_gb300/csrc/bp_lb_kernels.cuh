@@ -101,6 +101,13 @@ struct EvalArgs {
   // written by vb2cap_kernel before the evaluation kernels; nullptr: VB2's
   // whole range [2, c].
   const int64_t *vb2_hi;
+  // A window [g_lo, g_hi) of the flattened parameter index (bp_lb_eval_range):
+  // with `windowed` set, the direct kernel's tiles cover only the parameters
+  // inside it, and the finishing CTA also writes the packed key to out_key
+  // (nullptr: not written).
+  int32_t windowed;
+  uint32_t g_lo, g_hi;
+  int64_t *out_key;
 };
 
 // Shared-memory budget of the prefix-count tables (bytes; 48 KB lets four
@@ -294,6 +301,7 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
 }
 
 __device__ __forceinline__ void write_error(const EvalArgs &A, int64_t b) {
+  if (A.out_key != nullptr) A.out_key[b] = -BP_ERANGE;
   A.out_bound[b] = -BP_ERANGE;
   if (A.out_argmax) {
     bp_argmax_t e;
@@ -309,6 +317,7 @@ __device__ __forceinline__ void write_result(const EvalArgs &A, int64_t b, unsig
                                              int64_t c, int64_t k) {
   const int64_t lb = (int64_t)(key >> 32);
   const uint32_t g = 0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull);
+  if (A.out_key != nullptr) A.out_key[b] = (int64_t)key;
   A.out_bound[b] = lb;
   if (A.out_argmax) {
     bp_argmax_t r;
@@ -319,6 +328,25 @@ __device__ __forceinline__ void write_result(const EvalArgs &A, int64_t b, unsig
     A.out_argmax[b] = r;
   }
   if (A.out_feasible) A.out_feasible[b] = (uint8_t)(lb <= k);
+}
+
+// The parameters of DFF d that a call evaluates: its range [lo, hi], or with
+// a window [g_lo, g_hi) of the flattened index only those whose index lies
+// inside it (hi < lo when none).  Returns their number.
+BPLB_HD int64_t window_range(int d, int64_t c, int32_t windowed, uint32_t g_lo, uint32_t g_hi,
+                             int64_t &lo, int64_t &hi) {
+  param_range(d, c, lo, hi);
+  const int64_t n = hi >= lo ? hi - lo + 1 : 0;
+  if (!windowed) return n;
+  const int64_t off = flat_index(d, lo, c);  // index of the DFF's first parameter
+  const int64_t a = max((int64_t)g_lo - off, (int64_t)0), e = min((int64_t)g_hi - off, n);
+  if (e <= a) {
+    hi = lo - 1;
+    return 0;
+  }
+  hi = lo + e - 1;
+  lo += a;
+  return e - a;
 }
 
 // Last VB2 parameter of instance b: its range's upper end, or the cap of
@@ -1076,14 +1104,15 @@ __device__ void process_tile(const EvalArgs &A, int64_t b, int64_t lt, int64_t n
   int d = 0;
   int64_t rem = lt;
   const int64_t sb = sum_bound<MODE>(I);
+  int64_t lo_d, hi_d;
   for (d = 0; d < kNumDff; ++d) {
     if (dff_kernel(d, c, sb, A.prefix_on, A.vb2_on, A.dff_off) != kRouteDirect) continue;
-    const int64_t nt = (param_count(d, c) + LPT - 1) / LPT;
+    const int64_t nt =
+        (window_range(d, c, A.windowed, A.g_lo, A.g_hi, lo_d, hi_d) + LPT - 1) / LPT;
     if (rem < nt) break;
     rem -= nt;
   }
-  int64_t lo_d, hi_d;
-  param_range(d, c, lo_d, hi_d);
+  window_range(d, c, A.windowed, A.g_lo, A.g_hi, lo_d, hi_d);
   if (d == kVB2) hi_d = vb2_last(A, b, hi_d);
   const int64_t lam0 = lo_d + rem * LPT;
   const int64_t lam_end = max(lam0, min(hi_d + 1, lam0 + LPT));

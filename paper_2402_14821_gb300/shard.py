@@ -13,7 +13,9 @@ contiguous range of g, forms the packed key (bound << 32 | (2^32 - 1 - g)) of
 its best parameter, and the bound and its first argmax are the maximum key
 over ranks -- one 8-byte MAX all-reduce, the only collective of the path.
 
-Host logic only; the evaluation itself is the C ABI's (bp_lb_*).
+Host logic only; the evaluation itself is the C ABI's (bp_lb_eval_batch and
+the other batched calls for whole checks, bp_lb_eval_range for a range of one
+check's parameters).
 """
 from __future__ import annotations
 
@@ -64,6 +66,20 @@ def make_key(bound: int, g: int) -> int:
 def split_key(key: int):
     """(bound, g) of a packed key."""
     return int(key) >> 32, 0xFFFFFFFF - (int(key) & 0xFFFFFFFF)
+
+
+def rank_key(h, sizes, c: int, rank: int, world: int, stream=None) -> int:
+    """This rank's packed key for one instance: its contiguous range of the
+    flattened parameter index, evaluated on this rank's GPU through the C ABI
+    (bp_lb_eval_range).  `sizes` is the reduced instance as an int32 CUDA
+    tensor.  The MAX over ranks (allreduce_max_key) is the full bound and its
+    first argmax."""
+    import torch
+    from . import binding
+    g0, g1 = param_ranges(sum(param_counts(c)), world)[rank]
+    out = torch.empty(1, dtype=torch.int64, device=sizes.device)
+    binding.bp_lb_eval_range(h, sizes, c, g0, g1, out, stream)
+    return int(out.item())
 
 
 def allreduce_max_key(key: int, group=None) -> int:
