@@ -17,6 +17,10 @@
 // device address (on the host it names a host-side shadow), so the device
 // address is looked up once per device with cudaGetSymbolAddress, with that
 // device current, and passed to the kernels.
+//
+// It evaluates every DFF item by item in the generic kernel (the direct
+// algorithm, with VB2 there too, launch shape 0): the prefix-count tables and
+// the VB2 kernel need per-call scratch that only a handle owns.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -50,21 +54,47 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 namespace {
 
 std::mutex g_noalloc_mu;
-void *g_noalloc_addr[kMaxDevices] = {};
 
-// Device address of g_noalloc_scratch on the current device (looked up on the
-// first call for that device).
-int noalloc_scratch(unsigned char **out) {
+// Per-device set-up, done once with that device current: the array's device
+// address, the evaluation kernel's resident CTAs per SM and the SM count.
+struct NoAllocDevice {
+  void *addr = nullptr;
+  int sms = 0;
+  int occ = 0;
+};
+NoAllocDevice g_noalloc_dev[kMaxDevices];
+
+constexpr int kNoAllocShape = 0;
+constexpr size_t kNoAllocSmem = 2 * sizeof(uint32_t) * kListTop;
+
+// The current device's set-up, done on its first call: looks up the device
+// address of g_noalloc_scratch (cudaGetSymbolAddress) and queries the two
+// kernels this entry point launches (which loads them, and the array, under
+// CUDA's lazy module loading), so that later calls only launch.
+int noalloc_setup(NoAllocDevice *out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return BP_ECUDA;
   if (dev < 0 || dev >= kMaxDevices) return BP_ERANGE;
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
+  NoAllocDevice &d = g_noalloc_dev[dev];
+  if (!d.addr) {
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return BP_ECUDA;
-    g_noalloc_addr[dev] = p;
+    cudaFuncAttributes fa;
+    const void *fn = (const void *)eval_fn(kNoAllocShape, kSrcRaggedI32);
+    int sms = 0, occ = 0;
+    if (cudaFuncGetAttributes(&fa, (const void *)plan_kernel<kSrcRaggedI32>) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, fn) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kShapes[kNoAllocShape].nt,
+                                                      kNoAllocSmem) != cudaSuccess ||
+        occ <= 0)
+      return BP_ECUDA;
+    d.sms = sms;
+    d.occ = occ;
+    d.addr = p;
   }
-  *out = static_cast<unsigned char *>(g_noalloc_addr[dev]);
+  *out = d;
   return BP_OK;
 }
 
@@ -77,11 +107,13 @@ extern "C" int bp_lb_eval_batch_noalloc(int32_t B, const int64_t *d_offsets,
                                         void *stream) {
   if (B < 0) return BP_EINVAL;
   if (B > kNoAllocMax) return BP_ERANGE;
+  // the per-device set-up runs on the first call, B = 0 included
+  NoAllocDevice nd;
+  const int st = noalloc_setup(&nd);
+  if (st != BP_OK) return st;
   if (B == 0) return BP_OK;
   if (!d_offsets || !d_sizes || !d_capacity || !d_bins || !d_out_bound) return BP_EINVAL;
-  unsigned char *scratch = nullptr;
-  int st = noalloc_scratch(&scratch);
-  if (st != BP_OK) return st;
+  unsigned char *scratch = static_cast<unsigned char *>(nd.addr);
 
   EvalArgs A;
   std::memset(&A, 0, sizeof(A));
@@ -100,17 +132,8 @@ extern "C" int bp_lb_eval_batch_noalloc(int32_t B, const int64_t *d_offsets,
   A.keys = reinterpret_cast<unsigned long long *>(scratch + kOffKeys);
   A.done = reinterpret_cast<unsigned int *>(scratch + kOffDone);
 
-  int dev = 0, sms = 0, occ = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-    return BP_ECUDA;
-  const int shape = 0;
-  const size_t smem = 2 * sizeof(uint32_t) * kListTop;
+  const int shape = kNoAllocShape;
   const void *fn = (const void *)eval_fn(shape, kSrcRaggedI32);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kShapes[shape].nt, smem) !=
-          cudaSuccess ||
-      occ <= 0)
-    return BP_ECUDA;
   cudaStream_t s = (cudaStream_t)stream;
   // The planning kernel clears the result slots, finished-tile counters and
   // work counter of the B instances before the evaluation kernel runs.
@@ -119,8 +142,8 @@ extern "C" int bp_lb_eval_batch_noalloc(int32_t B, const int64_t *d_offsets,
                                                 nullptr, nullptr);
   if (cudaGetLastError() != cudaSuccess) return BP_ECUDA;
   void *args[] = {&A};
-  if (cudaLaunchKernel(fn, dim3((unsigned)(sms * occ)), dim3(kShapes[shape].nt), args, smem, s) !=
-      cudaSuccess)
+  if (cudaLaunchKernel(fn, dim3((unsigned)(nd.sms * nd.occ)), dim3(kShapes[shape].nt), args,
+                       kNoAllocSmem, s) != cudaSuccess)
     return BP_ECUDA;
   return BP_OK;
 }
