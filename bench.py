@@ -256,25 +256,42 @@ def measured_peaks():
 # ---------------------------------------------------------------------------
 # CPU oracle leg
 # ---------------------------------------------------------------------------
-def oracle_rate(nd, budget_s: float, threads: int):
-    """Checks/s of the oracle (reduction + full bound) over a bounded sample of
-    the nodes, run on `threads` host threads (ctypes releases the GIL)."""
+def _oracle_node_fn(nd):
     import oracle
     orc = oracle.load()
 
     def one(j):
-        w, a, c, k = nd.node(j)
+        w, a, c, k = nd.node(j % nd.count)
         orc.lb(orc.reduce(w, a, k, c), c, k)
+    return one
 
+
+def oracle_sample_size(nd, budget_s: float, threads: int) -> int:
+    """Nodes the oracle checks in about budget_s seconds of wall time on
+    `threads` host threads (from the time of one node)."""
+    one = _oracle_node_fn(nd)
     t0 = time.perf_counter()
     one(0)
     t_one = max(time.perf_counter() - t0, 1e-4)
-    m = int(max(threads, min(nd.count, budget_s / t_one)))
-    m = min(m, nd.count)
+    return int(min(nd.count, max(threads, budget_s * threads / t_one)))
+
+
+def oracle_run(nd, first: int, m: int, threads: int) -> float:
+    """Wall seconds of the oracle (reduction + full bound) over nodes first ..
+    first + m - 1 (mod the batch), on `threads` host threads (ctypes releases
+    the GIL)."""
+    one = _oracle_node_fn(nd)
     t0 = time.perf_counter()
     with cf.ThreadPoolExecutor(max_workers=threads) as ex:
-        list(ex.map(one, range(m)))
-    wall = time.perf_counter() - t0
+        list(ex.map(one, range(first, first + m)))
+    return time.perf_counter() - t0
+
+
+def oracle_rate(nd, budget_s: float, threads: int):
+    """Checks/s of the oracle over a bounded sample of the nodes (about
+    budget_s seconds of wall time): (rate, nodes, wall seconds)."""
+    m = oracle_sample_size(nd, budget_s, threads)
+    wall = oracle_run(nd, 0, m, threads)
     return m / wall, m, wall
 
 
@@ -316,23 +333,28 @@ def main():
             return
         nd = I.search_nodes(seed=1, n=N_ITEMS, c=CAP, nodes=NODES)
         threads = os.cpu_count() or 1
-        budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
-        for _ in range(args.warmup):
-            oracle_rate(nd, budget * 0.25, threads)
-        rates, walls, sample = [], [], 0
-        for _ in range(args.steps):
-            rate, m, wall = oracle_rate(nd, budget * threads, threads)
-            rates.append(rate)
-            walls.append(wall / m)
-            sample = m
-        value = float(np.mean(rates))
+        # one step = the oracle over a fixed bounded sample of m nodes (about
+        # `budget` seconds), consecutive steps taking consecutive nodes;
+        # ms_per_step is the wall time of the step that ran
+        budget = max(1.0, 45.0 / max(1, args.steps + args.warmup))
+        m = oracle_sample_size(nd, budget, threads)
+        walls = []
+        for i in range(args.warmup + args.steps):
+            wall = oracle_run(nd, i * m, m, threads)
+            if i >= args.warmup:
+                walls.append(wall)
+        t_step = float(np.mean(walls))
+        value = m / t_step
         line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": float(np.mean(walls)) * 1e3 * NODES, "higher_is_better": True,
+                "ms_per_step": t_step * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-                "config": {"workload": WORKLOAD.format(NODES), "nodes": NODES, "n": N_ITEMS, "c": CAP},
+                "config": {"workload": WORKLOAD.format(NODES), "nodes": NODES, "n": N_ITEMS, "c": CAP,
+                           "nodes_per_step": m,
+                           "step": f"the oracle over {m} of the {NODES} nodes (a bounded sample; "
+                                   "consecutive steps take consecutive nodes)"},
                 "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                                 "sample": f"{sample} of the {NODES} nodes per step, reduction + "
+                                 "sample": f"{m} of the {NODES} nodes per step, reduction + "
                                            f"full bound, {threads} host threads"},
                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
@@ -352,6 +374,10 @@ def main():
     build.build()
     dev = torch.device("cuda")
     stream = torch.cuda.current_stream()
+
+    # the integer issue peak this device sustains (the ALU-bound kernels'
+    # roofline denominator), measured before anything else runs
+    ipeak = issue_peak(B, stream)
 
     nd = I.search_nodes(seed=1 + rank, n=N_ITEMS, c=CAP, nodes=NODES)
     evals, ops = algorithmic_work(nd)
@@ -520,15 +546,18 @@ def main():
     if rank != 0:
         return
 
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak_ops = ipeak["lane_ops_per_s"]                # measured integer issue rate
+    sm_mhz = ipeak["sm_mhz"]                          # SM clock sampled during the probe
+    peak_words = sms * 32 * sm_mhz * 1e6              # one 32-lane shared access / clk / SM
+
+    # ---- secondary records on this GPU: hard nodes, the large sweep ------------
+    hard = hard_nodes_record(B, stream, flush, min(args.steps, 30), peak_ops)
+    large = large_record(B, stream, flush, peak_ops)
+
     # ---- CPU oracle baseline ---------------------------------------------------
     threads = os.cpu_count() or 1
     cpu_rate, cpu_m, cpu_wall = oracle_rate(nd, args.cpu_budget, threads)
-
-    peaks = measured_peaks()
-    sm_mhz_max = float(peaks.get("sm_max_mhz", 2070.0))
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
-    peak_ops = sms * 4 * 32 * sm_mhz_max * 1e6        # one warp instruction / clk / SMSP
-    peak_words = sms * 32 * sm_mhz_max * 1e6          # one 32-lane shared access / clk / SM
     calls = max(1, n_calls)
     # work per step actually done by each kernel: the VB2 pairs the kernels
     # counted (pruning skips the rest), the generic kernel's other DFFs, the
@@ -548,11 +577,11 @@ def main():
                    "prefix": "prefix_kernel (MT, RAD2, FS1, CCM1, BJ1 from shared-memory "
                              "prefix tables, pruned against L1; VB2 from the count table when "
                              "pruning leaves only small lambda)"}[dom]
-    basis = ({"prefix": f"{sms} SMs x 32 lanes x {sm_mhz_max:.0f} MHz (one 32-bit shared-memory "
-                        "word per lane per clock: 128 B/clk/SM); work = shared-memory words of "
-                        "table building and lookups"}
-             .get(dom, f"{sms} SMs x 4 SMSP x 32 lanes x {sm_mhz_max:.0f} MHz (integer issue, "
-                       "one warp instruction per clock per SMSP); work = integer ops of the "
+    basis = ({"prefix": f"{sms} SMs x 32 lanes x {sm_mhz:.0f} MHz, the SM clock measured under "
+                        "the issue probe (one 32-bit shared-memory word per lane per clock: "
+                        "128 B/clk/SM); work = shared-memory words of table building and lookups"}
+             .get(dom, f"measured integer issue rate {peak_ops / 1e12:.2f} T lane-ops/s "
+                       "(bp_lb_probe_int_issue, see issue_peak); work = integer ops of the "
                        "(item, parameter) pairs evaluated"))
     clocks = clk.summary()
     line = {
@@ -598,6 +627,9 @@ def main():
                          "autotune_ms": [round(x, 4) for x in shape_ms]},
         "gpu_launches": 4 * args.steps,  # plan, prefix, VB2 and generic kernels per step
         "clocks": clocks,
+        "issue_peak": ipeak,
+        "hard_nodes": hard,
+        "large": large,
         "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"{cpu_m} of the {NODES} nodes (reduction + full bound), "
                                    f"{cpu_wall:.1f} s wall on {threads} threads"},
@@ -628,10 +660,153 @@ def _time_steps(step, steps, flush, stream):
     return np.array([e0.elapsed_time(e1) for e0, e1 in ev])
 
 
-def _peak_ops():
+def issue_peak(B, stream, launches=25, target_ms=30.0):
+    """The integer issue rate the device sustains, measured by the library's
+    probe (bp_lb_probe_int_issue: integer multiply-adds and xors only, both
+    half-rate pipes busy): lane operations per second of its launches timed
+    with CUDA events, and the SM clock sampled meanwhile."""
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    return sms * 4 * 32 * float(measured_peaks().get("sm_max_mhz", 2070.0)) * 1e6
+    bps = 4
+    sink = torch.empty(sms * bps * 256, dtype=torch.int32, device="cuda")
+    ops1 = B.bp_lb_probe_int_issue(bps, 1, sink, stream)
+    trips = max(1, int(target_ms * 1e-3 * sms * 4 * 32 * 2.07e9 / ops1))
+    for _ in range(3):
+        B.bp_lb_probe_int_issue(bps, trips, sink, stream)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(launches)]
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for e0, e1 in ev:
+            e0.record(stream)
+            ops = B.bp_lb_probe_int_issue(bps, trips, sink, stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+    ms = np.array([e0.elapsed_time(e1) for e0, e1 in ev])
+    clocks = clk.summary()
+    rate = ops / (float(np.median(ms)) / 1e3)
+    mhz = clocks.get("sm_mhz") or float(measured_peaks().get("sm_max_mhz", 2070.0))
+    nominal = sms * 4 * 32 * mhz * 1e6
+    return {"lane_ops_per_s": rate, "ms_per_launch": float(np.median(ms)), "launches": launches,
+            "lane_ops_per_launch": ops, "sm_mhz": mhz, "clocks": clocks,
+            "nominal_at_that_clock": nominal, "frac_of_nominal": rate / nominal,
+            "probe": "bp_lb_probe_int_issue: 4 CTAs x 256 threads per SM, 8 independent "
+                     "chains per thread of one integer multiply-add (FMA pipe) and one xor "
+                     "(ALU pipe) per step"}
+
+
+def node_tensors(nd):
+    import torch
+    return dict(base_offsets=_dev(nd.base.offsets, torch.int64),
+                base_sizes=_dev(nd.base.sizes, torch.int32),
+                base_capacity=_dev(nd.base.capacity, torch.int64),
+                node_base=_dev(nd.node_base, torch.int32),
+                assign_offsets=_dev(nd.assign_offsets, torch.int64),
+                assign=_dev(nd.assign, torch.int32), bins=_dev(nd.bins, torch.int64))
+
+
+def hard_nodes_record(B, stream, flush, steps, peak_ops):
+    """The search-node step on nodes whose bounds mostly exceed L1 (triplet
+    instance, k = n/3; instances.hard_nodes), pruning on and off, per kernel."""
+    import torch
+    from paper_2402_14821_gb300 import instances as I
+    nd = I.hard_nodes()
+    t_in = node_tensors(nd)
+    mb = int(nd.bins.max())
+    ob = torch.empty(nd.count, dtype=torch.int64, device="cuda")
+    oa = B.argmax_tensor(nd.count)
+    of = torch.empty(nd.count, dtype=torch.uint8, device="cuda")
+    h = B.bp_lb_create(150, 1024)
+    out = {"workload": f"{nd.count} partial packings (uniform 0..60% committed) of one triplet "
+                       "instance, n=501 sizes in (c/4, c/2) filling 167 bins exactly, c=10000, "
+                       "k=167 bins (the optimum)"}
+    try:
+        B.bp_lb_reserve(h, nd.count)
+        shape, _ = B.bp_lb_autotune_nodes(h, max_bins=mb, out_bound=ob, out_argmax=oa,
+                                          out_feasible=of, reps=2, stream=stream, **t_in)
+        step = lambda: B.bp_lb_eval_nodes(h, max_bins=mb, out_bound=ob, out_argmax=oa,
+                                          out_feasible=of, stream=stream, **t_in)
+        res = {}
+        for prune in (True, False):
+            B.bp_lb_set_pruning(h, prune)
+            for _ in range(3):
+                step()
+            B.bp_lb_set_kernel_timing(h, True)
+            B.bp_lb_kernel_times(h)
+            ms = _time_steps(step, steps if prune else max(3, steps // 3), flush, stream)
+            kp, kv, kd, kn = B.bp_lb_kernel_times(h)
+            kw = B.bp_lb_kernel_work(h)
+            B.bp_lb_set_kernel_timing(h, False)
+            n = max(1, kn)
+            res[prune] = (ob.cpu().numpy().copy(), of.cpu().numpy().copy())
+            t = float(ms.mean())
+            vb2_frac = (kw[0] / n * ops_per_eval(4, CAP) / (kv / n / 1e3) / peak_ops
+                        if kv > 0 and kw[0] > 0 else None)
+            out["pruning_on" if prune else "pruning_off"] = {
+                "value": nd.count / (t / 1e3), "unit": UNIT, "ms_per_step": t,
+                "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+                "kernel_ms": {"prefix": kp / n, "vb2": kv / n, "direct": kd / n},
+                "vb2_pairs_evaluated": kw[0] / n, "vb2_params_pruned": kw[3] / n,
+                "vb2_kernel_frac_of_issue_peak": vb2_frac}
+        B.bp_lb_set_pruning(h, True)
+        assert np.array_equal(res[True][0], res[False][0])   # pruning is exact
+        b = res[True][0]
+        w0, _, c, _ = nd.node(0)
+        L1 = -(-int(np.asarray(w0, np.int64).sum()) // c)  # the reduction keeps the total
+        out.update({"launch_shape": shape, "frac_nodes_bound_above_L1": float(np.mean(b > L1)),
+                    "frac_nodes_infeasible": float(np.mean(res[True][1] == 0)),
+                    "pruning_speedup": out["pruning_off"]["ms_per_step"] /
+                                       out["pruning_on"]["ms_per_step"]})
+    finally:
+        B.bp_lb_destroy(h)
+    return out
+
+
+LARGE_CASES = ((10 ** 5, "uniform_wide"), (10 ** 5, "triplets"), (10 ** 5, "uniform_full"),
+               (10 ** 6, "triplets"))
+
+
+def large_record(B, stream, flush, peak_ops, cases=LARGE_CASES, steps=3):
+    """The large-instance sweep (n = 10^4, 64 instances per batch, int32 sizes):
+    per case the batch time, checks/s and the item-by-item kernels' fraction of
+    the integer issue peak (integer ops of the (item, parameter) pairs they
+    evaluate, VB2's counted by the kernels, over their own CUDA-event time)."""
+    import torch
+    from paper_2402_14821_gb300 import instances as I
+    h = B.bp_lb_create(150, 1024)
+    res = []
+    try:
+        for c, fam in cases:
+            rg = I.large_instances(fam, c, count=64, n=10_000, seed=2, dtype=np.int32)
+            evals, ops = ragged_work(rg)
+            t = (_dev(rg.offsets, torch.int64), _dev(rg.sizes, torch.int32),
+                 _dev(rg.capacity, torch.int64), _dev(rg.bins, torch.int64))
+            ob = torch.empty(rg.count, dtype=torch.int64, device="cuda")
+            oa = B.argmax_tensor(rg.count)
+            shape, _ = B.bp_lb_autotune_batch(h, *t, ob, oa, reps=1, stream=stream)
+            step = lambda: B.bp_lb_eval_batch(h, *t, ob, oa, stream=stream)
+            step()
+            B.bp_lb_set_kernel_timing(h, True)
+            B.bp_lb_kernel_times(h)
+            ms = _time_steps(step, steps, flush, stream)
+            kp, kv, kd, kn = B.bp_lb_kernel_times(h)
+            kw = B.bp_lb_kernel_work(h)
+            B.bp_lb_set_kernel_timing(h, False)
+            n = max(1, kn)
+            td = (kv + kd) / n
+            ops += (kw[0] + kw[1]) / n * ops_per_eval(4, c)
+            tm = float(ms.mean())
+            res.append({"c": c, "family": fam, "instances": 64, "n": 10_000, "dtype": "int32",
+                        "ms_per_batch": tm, "checks_per_s": 64 / (tm / 1e3),
+                        "evals_per_s_equivalent": evals / (tm / 1e3), "launch_shape": shape,
+                        "prefix_kernel_ms": kp / n, "item_kernels_ms": td,
+                        "item_kernel_ops": ops,
+                        "item_kernels_frac_of_issue_peak": ops / (td / 1e3) / peak_ops
+                        if td > 0 else None})
+            del t, ob, oa
+    finally:
+        B.bp_lb_destroy(h)
+    return res
 
 
 def ragged_work(rg, algo=1):
@@ -745,9 +920,10 @@ def run_sweep(args):
     build.build()
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    peak = _peak_ops()
+    ipeak = issue_peak(B, stream)
+    peak = ipeak["lane_ops_per_s"]
     h = B.bp_lb_create(150, 1 << 16)
-    out = {"workload": args.workload, "results": []}
+    out = {"workload": args.workload, "results": [], "issue_peak": ipeak}
     with ClockSampler(torch.cuda.current_device()) as clk:
         if args.workload == "large":
             steps = max(1, min(args.steps, 5))

@@ -198,6 +198,22 @@ def search_nodes(seed: int = 1, n: int = 500, c: int = 10_000, nodes: int = 4096
     return _nodes_from(base, np.zeros(nodes, np.int32), assigns, [k] * nodes)
 
 
+def hard_nodes(seed: int = 5, n: int = 501, c: int = 10_000, nodes: int = 4096,
+               frac_hi: float = 0.6) -> Nodes:
+    """Search nodes whose bounds mostly exceed L1: one triplet instance (n items
+    in (c/4, c/2) filling n/3 bins exactly, Falkenauer-T-like), k = n/3 bins --
+    the optimum, the bin count a search that has found it tries to beat -- and
+    `nodes` partial packings committing a uniform 0..60% of the items to random
+    bins without overflow.  A random partial packing rarely completes to the
+    perfect packing, so most nodes are infeasible with a bound above L1."""
+    rng = _rng(seed)
+    w = triplet_sizes(rng, n, c)
+    k = len(w) // 3
+    base = ragged_from_list([w], [c], bins=[k])
+    assigns = prepack(rng, [w] * nodes, [c] * nodes, [k] * nodes, frac_hi)
+    return _nodes_from(base, np.zeros(nodes, np.int32), assigns, [k] * nodes)
+
+
 FAMILIES = ("uniform_wide", "triplets", "uniform_full")
 
 

@@ -168,3 +168,52 @@ def test_ragged_nodes_graph_full_size(cudalib, orc):
             _check_sampled(B, h, orc, wr, c, b[j], d[j], l[j], rng, m=60)
     finally:
         B.bp_lb_destroy(h)
+
+
+def test_hard_nodes_full_size(cudalib, orc):
+    """The hard search-node batch (4096 partial packings of a triplet instance
+    with k = n/3 bins, most nodes with a bound above L1, so that pruning
+    against L1 skips little): sampled nodes against the oracle, with pruning
+    on and off (identical results), and most bounds above L1."""
+    import torch
+    B = cudalib
+    nd = I.hard_nodes()
+    t_in = dict(base_offsets=_dev(nd.base.offsets, torch.int64),
+                base_sizes=_dev(nd.base.sizes, torch.int32),
+                base_capacity=_dev(nd.base.capacity, torch.int64),
+                node_base=_dev(nd.node_base, torch.int32),
+                assign_offsets=_dev(nd.assign_offsets, torch.int64),
+                assign=_dev(nd.assign, torch.int32), bins=_dev(nd.bins, torch.int64))
+    mb = int(nd.bins.max())
+    h = B.bp_lb_create(150, 1024)
+    try:
+        res = []
+        for prune in (True, False):
+            B.bp_lb_set_pruning(h, prune)
+            ob = torch.empty(nd.count, dtype=torch.int64, device="cuda")
+            oa = B.argmax_tensor(nd.count)
+            of = torch.empty(nd.count, dtype=torch.uint8, device="cuda")
+            B.bp_lb_eval_nodes(h, max_bins=mb, out_bound=ob, out_argmax=oa, out_feasible=of,
+                               **t_in)
+            torch.cuda.synchronize()
+            d, l = B.decode_argmax(oa)
+            res.append((ob.cpu().numpy(), d, l, of.cpu().numpy().astype(bool)))
+        for x, y in zip(*res):
+            assert np.array_equal(x, y)
+        b, d, l, f = res[0]
+        w0, _, c, _ = nd.node(0)
+        L1 = -(-int(np.asarray(w0, np.int64).sum()) // c)   # the reduction keeps the total
+        assert np.mean(b > L1) > 0.5
+        rng = np.random.default_rng(8)
+        sample = rng.choice(nd.count, 40, replace=False)
+
+        def whole(j):
+            w, a, c, k = nd.node(j)
+            return orc.lb(orc.reduce(w, a, k, c), c, k)
+
+        with cf.ThreadPoolExecutor(8) as ex:
+            want = list(ex.map(whole, sample))
+        for j, wv in zip(sample, want):
+            assert (b[j], d[j], l[j], f[j]) == wv, j
+    finally:
+        B.bp_lb_destroy(h)
