@@ -310,13 +310,20 @@ def main():
                     help="fix the batched launch shape (default: autotune on the batch)")
     ap.add_argument("--cpu-budget", type=float, default=15.0,
                     help="CPU-seconds of oracle work for the cpu_baseline sample")
-    ap.add_argument("--workload", choices=("search", "plain", "large", "ragged", "serve", "table1"),
+    ap.add_argument("--workload", choices=("search", "plain", "large", "ragged", "serve", "table1",
+                                           "issue"),
                     default="search",
                     help="search: the benchmark line (4096 search nodes); plain: one check of "
                          "n=50, c=150 per call (bp_lb_eval), 10^4 calls; large: n=10^4, "
                          "c in {1e5, 1e6}, three size families, batches of 64; ragged: 10^4 "
                          "ragged search nodes in one CUDA-graph launch; serve: 256 simulated "
-                         "searches against the continuous-batching server, offered rates swept")
+                         "searches against the continuous-batching server, offered rates swept; "
+                         "issue: the integer-issue probe alone")
+    ap.add_argument("--large-cases", default="",
+                    help="large: comma-separated c:family cases (default: both c, all families)")
+    ap.add_argument("--large-count", type=int, default=64, help="large: instances per batch")
+    ap.add_argument("--dff-mask", type=int, default=63, help="large: DFFs in the bound (bits)")
+    ap.add_argument("--no-prune", action="store_true", help="large: pruning off (all the work)")
     args = ap.parse_args()
     if args.workload != "search":
         return run_sweep(args)
@@ -925,38 +932,45 @@ def run_sweep(args):
     h = B.bp_lb_create(150, 1 << 16)
     out = {"workload": args.workload, "results": [], "issue_peak": ipeak}
     with ClockSampler(torch.cuda.current_device()) as clk:
-        if args.workload == "large":
+        if args.workload == "issue":
+            out["results"].append({k: v for k, v in ipeak.items() if k != "clocks"})
+        elif args.workload == "large":
             steps = max(1, min(args.steps, 5))
-            for c in (10 ** 5, 10 ** 6):
-                for fam in I.FAMILIES:
-                    for dt in (np.int32, np.int64):
-                        rg = I.large_instances(fam, c, count=64, n=10_000, seed=2, dtype=dt)
-                        evals, ops = ragged_work(rg)
-                        tdt = torch.int32 if dt == np.int32 else torch.int64
-                        t = (_dev(rg.offsets, torch.int64), _dev(rg.sizes, tdt),
-                             _dev(rg.capacity, torch.int64), _dev(rg.bins, torch.int64))
-                        ob = torch.empty(rg.count, dtype=torch.int64, device="cuda")
-                        oa = B.argmax_tensor(rg.count)
-                        shape, _ = B.bp_lb_autotune_batch(h, *t, ob, oa, reps=1)
-                        step = lambda: B.bp_lb_eval_batch(h, *t, ob, oa, stream=stream)
-                        step()
-                        B.bp_lb_set_kernel_timing(h, True)
-                        B.bp_lb_kernel_times(h)
-                        ms = _time_steps(step, steps, flush, stream)
-                        kp, kv, kd, kn = B.bp_lb_kernel_times(h)
-                        kw = B.bp_lb_kernel_work(h)
-                        B.bp_lb_set_kernel_timing(h, False)
-                        tm = float(ms.mean())
-                        td = (kv + kd) / max(1, kn)
-                        ops += (kw[0] + kw[1]) / max(1, kn) * ops_per_eval(4, c)
-                        out["results"].append({
-                            "c": c, "family": fam, "dtype": np.dtype(dt).name, "instances": 64,
-                            "n": 10_000, "ms_per_batch": tm, "checks_per_s": 64 / (tm / 1e3),
-                            "evals_per_s": evals / (tm / 1e3), "launch_shape": shape,
-                            "item_kernels_ms": td, "vb2_kernel_ms": kv / max(1, kn),
-                            "prefix_kernel_ms": kp / max(1, kn),
-                            "roofline_frac": ops / (td / 1e3) / peak})
-                        print(json.dumps(out["results"][-1]), flush=True)
+            cases = ([(int(float(x.split(":")[0])), x.split(":")[1]) for x in args.large_cases.split(",")]
+                     if args.large_cases else [(c, f) for c in (10 ** 5, 10 ** 6) for f in I.FAMILIES])
+            B.bp_lb_set_dff_mask(h, args.dff_mask)
+            B.bp_lb_set_pruning(h, not args.no_prune)
+            count = args.large_count
+            for c, fam in cases:
+                for dt in (np.int32, np.int64):
+                    rg = I.large_instances(fam, c, count=count, n=10_000, seed=2, dtype=dt)
+                    evals, ops = ragged_work(rg)
+                    tdt = torch.int32 if dt == np.int32 else torch.int64
+                    t = (_dev(rg.offsets, torch.int64), _dev(rg.sizes, tdt),
+                         _dev(rg.capacity, torch.int64), _dev(rg.bins, torch.int64))
+                    ob = torch.empty(rg.count, dtype=torch.int64, device="cuda")
+                    oa = B.argmax_tensor(rg.count)
+                    shape, _ = B.bp_lb_autotune_batch(h, *t, ob, oa, reps=1)
+                    step = lambda: B.bp_lb_eval_batch(h, *t, ob, oa, stream=stream)
+                    step()
+                    B.bp_lb_set_kernel_timing(h, True)
+                    B.bp_lb_kernel_times(h)
+                    ms = _time_steps(step, steps, flush, stream)
+                    kp, kv, kd, kn = B.bp_lb_kernel_times(h)
+                    kw = B.bp_lb_kernel_work(h)
+                    B.bp_lb_set_kernel_timing(h, False)
+                    tm = float(ms.mean())
+                    td = (kv + kd) / max(1, kn)
+                    ops += (kw[0] + kw[1]) / max(1, kn) * ops_per_eval(4, c)
+                    out["results"].append({
+                        "c": c, "family": fam, "dtype": np.dtype(dt).name, "instances": count,
+                        "dff_mask": args.dff_mask, "pruning": not args.no_prune, "evals": evals,
+                        "n": 10_000, "ms_per_batch": tm, "checks_per_s": count / (tm / 1e3),
+                        "evals_per_s": evals / (tm / 1e3), "launch_shape": shape,
+                        "item_kernels_ms": td, "vb2_kernel_ms": kv / max(1, kn),
+                        "prefix_kernel_ms": kp / max(1, kn),
+                        "roofline_frac": ops / (td / 1e3) / peak})
+                    print(json.dumps(out["results"][-1]), flush=True)
         elif args.workload == "plain":
             import oracle
             rg = I.plain_single(seed=0)

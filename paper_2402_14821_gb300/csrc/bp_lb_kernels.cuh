@@ -762,20 +762,47 @@ __device__ __forceinline__ bool vb2_may_exceed(int64_t l, int64_t kk, int64_t c,
   return (__int128)l * Dd + (__int128)ns * (c - 1) > (M + 1) * (__int128)c - 1;
 }
 
-// Whether some VB2 parameter in [l0, l1] may have a bound above kk (c <=
-// 65535, kk <= L).  vb2_may_exceed(l) implies G(l) > 0 with
+// Whether some VB2 parameter in [l0, l1] may have a bound above kk (kk <= L).
+// vb2_may_exceed(l) implies G(l) > 0 with
 // G(l) = 2 X(l) - c (Y(l) + 1) + 2, Y(l) = (l - 1)(2 kk - K) + 2 n_small - 2 n_big
 // (M = floor(Y / 2) >= (Y - 1) / 2), and G is linear in l: G <= 0 at both ends
-// rules out the whole range.
+// rules out the whole range.  64-bit up to c = 65535, 128-bit above.
 __device__ __forceinline__ bool vb2_range_may_exceed(int64_t l0, int64_t l1, int64_t kk, int64_t c,
                                                      int64_t Dd, int64_t ns, int64_t nb,
                                                      int64_t K) {
+  if (c <= kVb2FixedCap) {
+    auto G = [&](int64_t l) {
+      const int64_t X = l * Dd + ns * (c - 1);
+      const int64_t Y = (l - 1) * (2 * kk - K) + 2 * ns - 2 * nb;
+      return 2 * X - c * (Y + 1) + 2;
+    };
+    return G(l0) > 0 || G(l1) > 0;
+  }
   auto G = [&](int64_t l) {
-    const int64_t X = l * Dd + ns * (c - 1);
-    const int64_t Y = (l - 1) * (2 * kk - K) + 2 * ns - 2 * nb;
-    return 2 * X - c * (Y + 1) + 2;
+    const __int128 X = (__int128)l * Dd + (__int128)ns * (c - 1);
+    const __int128 Y = (__int128)(l - 1) * (2 * kk - K) + 2 * ns - 2 * nb;
+    return 2 * X - (__int128)c * (Y + 1) + 2;
   };
   return G(l0) > 0 || G(l1) > 0;
+}
+
+// Whether a VB2 tile [l0, l1] of instance b can be skipped before anything is
+// staged, from the instance's class counts and sums that the prefix kernel
+// published (EvalArgs::isums, flag 1) and the instance's cut: k in verdict
+// mode, else from its best key so far (vb2_cut).  Thread 0 only.
+__device__ __forceinline__ bool vb2_tile_pruned(const EvalArgs &A, int64_t b, int64_t c, int64_t k,
+                                                int64_t L, int64_t l0, int64_t l1,
+                                                uint32_t gbase) {
+  if (A.isums == nullptr || !(A.verdict || A.prune) || l1 < l0) return false;
+  const volatile long long *is = A.isums + 8 * b;
+  if (is[7] != 1) return false;
+  __threadfence();
+  const int64_t cut = A.verdict ? k : (int64_t)vb2_cut(&A.keys[b], gbase);
+  if (cut < 0) return false;
+  const int64_t ns = is[0], nb = is[1], nh = is[2], nf = is[3], swb = is[4], sw = is[5];
+  const int64_t Dd = (sw - swb - nh * (c / 2) - nf * c) - (nb * c - swb);
+  const int64_t K = 2 * nb + nh + 2 * nf;
+  return !vb2_range_may_exceed(l0, l1, min(cut, L), c, Dd, ns, nb, K);
 }
 
 // Work counters of a CTA (measurement only): cleared at the kernel's start,
@@ -844,7 +871,7 @@ __device__ unsigned long long tile_dff(const EvalArgs &A, const InstView &I, int
         // the whole group pruned (vb2_range_may_exceed; the instance sums are
         // complete after the first group)
         S.gskip[g & 1] = 0;
-        if (D == kVB2 && c <= kVb2FixedCap && !S.err) {
+        if (D == kVB2 && !S.err) {
           const int64_t cut = vslot != nullptr ? I.k : (int64_t)S.kcut[g & 1];
           if (cut >= 0) {
             const int64_t ns_ = S.sums[0], nb_ = S.sums[1], nh_ = S.sums[2], nf_ = S.sums[3];
@@ -1121,6 +1148,14 @@ __device__ void process_tile(const EvalArgs &A, int64_t b, int64_t lt, int64_t n
   if (tid == 0) {
     S.err = 0;
     S.skip = (vslot != nullptr && slot_decided(vslot, I.k)) ? 1 : 0;
+    // a VB2 tile none of whose parameters can change the result, from the
+    // sums the prefix kernel published: skipped before anything is staged
+    if (!S.skip && d == kVB2 && lam_end > lam0 &&
+        vb2_tile_pruned(A, b, c, I.k, stream_len<MODE>(I), lam0, lam_end - 1,
+                        flat_index(kVB2, 2, c))) {
+      S.skip = 1;
+      if (A.work_count != nullptr) atomicAdd(&S.wc[3], (unsigned long long)(lam_end - lam0));
+    }
   }
   __syncthreads();
   if (!S.skip) node_loads<NT, MODE>(A, b, I, s_load, &S.minw, &S.err);
