@@ -38,19 +38,22 @@ UNIT = "checks/s"
 WORKLOAD = "search-node batch: {} partial packings of n=500 items, sizes U[1,c/2], c=10000"
 NODES, N_ITEMS, CAP = 4096, 500, 10_000
 
-# Integer operations per (item, parameter) pair in the kernel's formulation of
-# each DFF, counted from the source expressions of csrc/bp_lb_eval.cuh:
-#   MT   compare + conditional add                                   2
-#   RAD2 two compares + two counts                                   4
-#   FS1  mul, mul-high, shift, add, mul, compare, conditional add    7
-#   CCM1 one multiply-high-add (c <= 131071)                         1   (else 3)
-#   VB2  mul-add, shift, half of a 3-input add (c <= 65535)         2.5 (fp32 path 5)
-#   BJ1  mul-high, two mul-adds, min, add (c <= 65535)               5   (else 6)
+# Thread instructions per (item, parameter) pair of each DFF's item-by-item
+# evaluation: measured with ncu where the workloads use the path
+# (smsp__inst_executed.sum x 32 / pairs of one launch, pruning off, one
+# instance of n = 10^4; profiles/item_kernels_instructions_per_eval.md):
+#   generic kernel at c = 10^6: MT 2.39, RAD2 4.59, CCM1 2.87 (its wide path,
+#   c > 131071), VB2 5.71 (fp32-corrected path, 65535 < c <= 2^22), BJ1 5.45
+#   (wide path, c > 65535); VB2 kernel (fixed point, c <= 65535): 2.68.
+# The paths no workload puts on the item-by-item kernels keep the integer
+# operations counted from the source expressions of csrc/bp_lb_eval.cuh:
+# FS1 7 (mul, mul-high, shift, add, mul, compare, conditional add), CCM1 1 at
+# c <= 131071 (one multiply-high-add), BJ1 5 at c <= 65535, VB2 5 above 2^22.
 def ops_per_eval(d, c):
-    return {0: 2, 1: 4, 2: 7,
-            3: 1 if c <= 131071 else 3,
-            4: 2.5 if c <= 65535 else 5,
-            5: 5 if c <= 65535 else 6}[d]
+    return {0: 2.39, 1: 4.59, 2: 7,
+            3: 1 if c <= 131071 else 2.87,
+            4: 2.68 if c <= 65535 else (5.71 if c <= 1 << 22 else 5),
+            5: 5 if c <= 65535 else 5.45}[d]
 SM_COUNT_NOMINAL = 152
 # DRAM bytes (read + write) per search node of one launch of each kernel, from
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of a 512-node
@@ -324,6 +327,7 @@ def main():
     ap.add_argument("--large-count", type=int, default=64, help="large: instances per batch")
     ap.add_argument("--dff-mask", type=int, default=63, help="large: DFFs in the bound (bits)")
     ap.add_argument("--no-prune", action="store_true", help="large: pruning off (all the work)")
+    ap.add_argument("--large-dtypes", default="int32,int64", help="large: size types")
     args = ap.parse_args()
     if args.workload != "search":
         return run_sweep(args)
@@ -803,13 +807,32 @@ def large_record(B, stream, flush, peak_ops, cases=LARGE_CASES, steps=3):
             td = (kv + kd) / n
             ops += (kw[0] + kw[1]) / n * ops_per_eval(4, c)
             tm = float(ms.mean())
+            off = None
+            if c <= 10 ** 5:
+                # the same batch with pruning off: all the item-by-item work
+                B.bp_lb_set_pruning(h, False)
+                step()
+                B.bp_lb_set_kernel_timing(h, True)
+                B.bp_lb_kernel_times(h)
+                ms_off = _time_steps(step, steps, flush, stream)
+                kp2, kv2, kd2, kn2 = B.bp_lb_kernel_times(h)
+                kw2 = B.bp_lb_kernel_work(h)
+                B.bp_lb_set_kernel_timing(h, False)
+                B.bp_lb_set_pruning(h, True)
+                n2 = max(1, kn2)
+                td2 = (kv2 + kd2) / n2
+                ops2 = ragged_work(rg)[1] + (kw2[0] + kw2[1]) / n2 * ops_per_eval(4, c)
+                off = {"ms_per_batch": float(ms_off.mean()), "item_kernels_ms": td2,
+                       "prefix_kernel_ms": kp2 / n2, "item_kernel_ops": ops2,
+                       "item_kernels_frac_of_issue_peak": ops2 / (td2 / 1e3) / peak_ops
+                       if td2 > 0 else None}
             res.append({"c": c, "family": fam, "instances": 64, "n": 10_000, "dtype": "int32",
                         "ms_per_batch": tm, "checks_per_s": 64 / (tm / 1e3),
                         "evals_per_s_equivalent": evals / (tm / 1e3), "launch_shape": shape,
                         "prefix_kernel_ms": kp / n, "item_kernels_ms": td,
                         "item_kernel_ops": ops,
                         "item_kernels_frac_of_issue_peak": ops / (td / 1e3) / peak_ops
-                        if td > 0 else None})
+                        if td > 0 else None, "pruning_off": off})
             del t, ob, oa
     finally:
         B.bp_lb_destroy(h)
@@ -942,7 +965,7 @@ def run_sweep(args):
             B.bp_lb_set_pruning(h, not args.no_prune)
             count = args.large_count
             for c, fam in cases:
-                for dt in (np.int32, np.int64):
+                for dt in [np.dtype(x).type for x in args.large_dtypes.split(",")]:
                     rg = I.large_instances(fam, c, count=count, n=10_000, seed=2, dtype=dt)
                     evals, ops = ragged_work(rg)
                     tdt = torch.int32 if dt == np.int32 else torch.int64
@@ -950,7 +973,12 @@ def run_sweep(args):
                          _dev(rg.capacity, torch.int64), _dev(rg.bins, torch.int64))
                     ob = torch.empty(rg.count, dtype=torch.int64, device="cuda")
                     oa = B.argmax_tensor(rg.count)
-                    shape, _ = B.bp_lb_autotune_batch(h, *t, ob, oa, reps=1)
+                    if args.shape >= 0:
+                        shape = args.shape
+                        B.bp_lb_set_launch_shape(h, B.MODE_RAGGED_I32 if dt == np.int32
+                                                 else B.MODE_RAGGED_I64, shape)
+                    else:
+                        shape, _ = B.bp_lb_autotune_batch(h, *t, ob, oa, reps=1)
                     step = lambda: B.bp_lb_eval_batch(h, *t, ob, oa, stream=stream)
                     step()
                     B.bp_lb_set_kernel_timing(h, True)

@@ -441,7 +441,7 @@ int bp_lb_kernel_work(bp_lb_t *h, int64_t *out4);
  * blocks_per_sm x SM-count CTAs of 256 threads that run only integer
  * multiply-adds and xors in eight independent chains per thread (the two
  * half-rate integer pipes together allow one warp instruction per clock per
- * sub-partition), `trips` loop trips of 64 such operations each, and writes
+ * sub-partition), `trips` loop trips of 256 such operations each, and writes
  * one word per thread to d_sink (device, caller-owned, at least
  * blocks_per_sm x SM-count x 256 uint32).  *out_lane_ops receives the
  * number of integer lane operations the launch performs; divided by the

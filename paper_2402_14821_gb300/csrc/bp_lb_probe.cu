@@ -7,7 +7,7 @@
 // half that rate, so only a mix of the two can reach it.  The probe kernel
 // runs exactly such a mix with no memory traffic: per thread eight
 // independent chains, each step one multiply-add a = a * K + b and one xor
-// b ^= a, unrolled four steps deep; timing one launch with CUDA events gives
+// b ^= a, unrolled sixteen steps deep; timing one launch with CUDA events gives
 // the lane operations per second the device sustains at its current clock.
 #include <cuda_runtime.h>
 
@@ -19,7 +19,7 @@ namespace {
 
 constexpr int kProbeNT = 256;
 constexpr int kProbeChains = 8;
-constexpr int kProbeUnroll = 4;
+constexpr int kProbeUnroll = 16;
 // integer operations per thread and loop trip: chains x unroll x (mul-add + xor)
 constexpr int64_t kProbeOpsPerTrip = kProbeChains * kProbeUnroll * 2;
 
