@@ -76,6 +76,13 @@ struct PrefixShared {
   // this tile, the u group's members (bit d), lambda range
   int dec_d, dec_home, dec_fs1, dec_umask;
   long long dec_lam0, dec_lam_end;
+  // thread 0's routing of the last decoded instance, reused while the next
+  // tiles' instances have the same capacity and stream bound (every node of a
+  // search-node batch does): the u group merged, FS1 with BJ1, the u group's
+  // members and table home, and per DFF its prefix tiles and table home
+  long long rc_c, rc_sb;
+  int rc_merged, rc_wmerged, rc_umask, rc_uhome;
+  int rc_nt[kNumDff], rc_home[kNumDff];
   int vb2_mode;  // vb2_table_plan of this u-group tile, with its cut and last l
   long long vb2_kk, vb2_lmax;
   uint32_t minw;  // smallest unpacked size > 0 of the node (transform_bins)
@@ -823,6 +830,7 @@ __global__ void __launch_bounds__(kPrefixNT, 4) prefix_kernel(EvalArgs A) {
   uint32_t *s_load = reinterpret_cast<uint32_t *>(smem_raw + kPrefixSmemBytes);
 
   const int64_t total = A.ptile_start ? A.ptile_start[A.B] : A.single_ptiles;
+  if (threadIdx.x == 0) S.rc_c = -1;  // no routing cached yet
   tile_first(A.ptile_start, A.B, total, A.pwork, cur);
   while (cur.tile < total) {
     const int64_t t = cur.tile, b = cur.inst;
@@ -836,33 +844,43 @@ __global__ void __launch_bounds__(kPrefixNT, 4) prefix_kernel(EvalArgs A) {
       int64_t rem = t - t0;
       int d = 0;
       const int64_t sb = sum_bound<MODE>(I);
-      const bool merged = prefix_u_merged(I.c, sb, A.prefix_on, A.vb2_on, A.dff_off, A.plpt);
-      const bool wmerged = prefix_w_merged(I.c, sb, A.prefix_on, A.vb2_on, A.dff_off);
+      if (I.c != S.rc_c || sb != S.rc_sb) {  // route this instance (tile counts as route_tiles)
+        const bool merged = prefix_u_merged(I.c, sb, A.prefix_on, A.vb2_on, A.dff_off, A.plpt);
+        const bool wmerged = prefix_w_merged(I.c, sb, A.prefix_on, A.vb2_on, A.dff_off);
+        int umask = 0;
+        for (int e = 0; e < kNumDff; ++e) {
+          const bool pre = dff_kernel(e, I.c, sb, A.prefix_on, A.vb2_on, A.dff_off) == kRoutePrefix;
+          const bool member = merged && (e == kMT || e == kRAD2 || e == kCCM1);
+          if (member && param_count(e, I.c) > 0 && pre) umask |= 1 << e;
+          S.rc_nt[e] = (pre && !member && !(wmerged && e == kFS1))
+                           ? (int)prefix_dff_tiles(e, I.c, sb, A.prefix_on, A.plpt)
+                           : 0;
+          S.rc_home[e] = prefix_home(e, I.c, sb, A.prefix_on);
+        }
+        S.rc_merged = merged;
+        S.rc_wmerged = wmerged;
+        S.rc_umask = umask;
+        S.rc_uhome = prefix_u_home(I.c, A.prefix_on);
+        S.rc_c = I.c;
+        S.rc_sb = sb;
+      }
+      const bool merged = S.rc_merged != 0, wmerged = S.rc_wmerged != 0;
       if (merged && rem == 0) {
         d = kPrefixU;
       } else {
         if (merged) rem -= 1;  // the u group's tile comes first
         for (d = 0; d < kNumDff; ++d) {
-          if (merged && (d == kMT || d == kRAD2 || d == kCCM1)) continue;
-          if (wmerged && d == kFS1) continue;
-          if (dff_kernel(d, I.c, sb, A.prefix_on, A.vb2_on, A.dff_off) != kRoutePrefix) continue;
-          const int64_t nt = prefix_dff_tiles(d, I.c, sb, A.prefix_on, A.plpt);
+          const int64_t nt = S.rc_nt[d];
           if (rem < nt) break;
           rem -= nt;
         }
       }
-      const int home = (d == kPrefixU) ? prefix_u_home(I.c, A.prefix_on)
-                                       : prefix_home(d, I.c, sb, A.prefix_on);
+      const int home = (d == kPrefixU) ? S.rc_uhome : (d < kNumDff ? S.rc_home[d] : 0);
       int64_t lo_d = 0, hi_d = -1;
       if (d != kPrefixU && d != kFS1) param_range(d, I.c, lo_d, hi_d);
       const int64_t lpt = (home == 2) ? hi_d - lo_d + 1 : A.plpt;  // global tables: one tile
       const int64_t lam0 = lo_d + rem * lpt;
-      int umask = 0;
-      if (d == kPrefixU)
-        for (int u = 0; u < 4; ++u)
-          if (u != kFS1 && param_count(u, I.c) > 0 &&
-              dff_kernel(u, I.c, sb, A.prefix_on, A.vb2_on, A.dff_off) == kRoutePrefix)
-            umask |= 1 << u;
+      const int umask = d == kPrefixU ? S.rc_umask : 0;
       S.dec_d = d;
       S.dec_home = home;
       // FS1 on BJ1's table: on its own tile (empty BJ1 range) or BJ1's first
