@@ -550,16 +550,20 @@ __device__ __forceinline__ int64_t instance_tiles(const EvalArgs &A, int64_t b) 
 
 // Block max of the threads' keys, one atomicMax into the instance's slot, and
 // the finished-tile ticket: the CTA finishing the instance's last tile writes
-// its outputs and clears the slot.
+// its outputs and clears the slot.  Thread 32 (warp 1) does the global part,
+// with no barrier after it, so that its atomics' round trips overlap warp 0's
+// search for the CTA's next tile (tile_publish); nothing it reads in shared
+// memory is written again before the next tile's fold.
 template <int NT>
 __device__ void fold_and_finalize(const EvalArgs &A, int64_t b, unsigned long long best, bool err,
                                   int64_t ntiles, const InstView &I,
                                   unsigned long long *warp_key) {
+  static_assert(NT >= 64, "the fold's global part runs on warp 1");
   const int tid = threadIdx.x;
   best = warp_max_u64(best);
   if (lane_id() == 0) warp_key[tid >> 5] = best;
   __syncthreads();
-  if (tid == 0) {
+  if (tid == 32) {
     unsigned long long m = 0ull;
     for (int w = 0; w < NT / 32; ++w) m = warp_key[w] > m ? warp_key[w] : m;
     if (m && !err) atomicMax(&A.keys[b], m);
@@ -573,7 +577,6 @@ __device__ void fold_and_finalize(const EvalArgs &A, int64_t b, unsigned long lo
       else write_result(A, b, key, I.c, I.k);
     }
   }
-  __syncthreads();
 }
 
 // Bin loads of a search node into s_load (read back by
