@@ -328,6 +328,9 @@ def main():
     ap.add_argument("--dff-mask", type=int, default=63, help="large: DFFs in the bound (bits)")
     ap.add_argument("--no-prune", action="store_true", help="large: pruning off (all the work)")
     ap.add_argument("--large-dtypes", default="int32,int64", help="large: size types")
+    ap.add_argument("--records", default="hard,large",
+                    help="secondary records of the benchmark line (comma-separated: hard, large; "
+                         "'none' for the search-node step alone, e.g. under a profiler)")
     args = ap.parse_args()
     if args.workload != "search":
         return run_sweep(args)
@@ -563,8 +566,9 @@ def main():
     peak_words = sms * 32 * sm_mhz * 1e6              # one 32-lane shared access / clk / SM
 
     # ---- secondary records on this GPU: hard nodes, the large sweep ------------
-    hard = hard_nodes_record(B, stream, flush, min(args.steps, 30), peak_ops)
-    large = large_record(B, stream, flush, peak_ops)
+    recs = set(args.records.split(","))
+    hard = hard_nodes_record(B, stream, flush, min(args.steps, 30), peak_ops) if "hard" in recs else None
+    large = large_record(B, stream, flush, peak_ops) if "large" in recs else None
 
     # ---- CPU oracle baseline ---------------------------------------------------
     threads = os.cpu_count() or 1

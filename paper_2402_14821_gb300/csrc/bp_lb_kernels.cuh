@@ -273,6 +273,49 @@ __device__ __forceinline__ bool slot_decided(const unsigned long long *slot, int
   return (int64_t)(key >> 32) > k;
 }
 
+// Calls f(i, x[i], y[i]) (ONE: f(i, x[i], 0)) for i in [0, n), over the
+// CTA's NT threads, reading four consecutive entries with one 16-byte load
+// wherever the arrays allow.  Thread t takes the groups of four entries that
+// start on x's 16-byte boundaries (the first and last groups may be partial:
+// their entries inside [0, n) are read one at a time); y, when given, is read
+// alongside when it has the same 16-byte phase as x, else every entry is read
+// on its own.  f has one call site, so a large f is compiled once.
+template <int NT, bool ONE, class F>
+__device__ __forceinline__ void for_items_vec(const int32_t *x, const int32_t *y, int64_t n, F f) {
+  const int64_t px = (int64_t)((reinterpret_cast<uintptr_t>(x) >> 2) & 3u);
+  const int64_t py = ONE ? px : (int64_t)((reinterpret_cast<uintptr_t>(y) >> 2) & 3u);
+  const bool vec = px == py;
+  const int64_t ph = vec ? px : 0;  // x's offset (entries) within its 16-byte line
+  const int64_t ngroups = (n + ph + 3) >> 2;
+  for (int64_t g = threadIdx.x; g < ngroups; g += NT) {
+    const int64_t base = 4 * g - ph;  // entry index of the group's first value
+    int4 vx = make_int4(0, 0, 0, 0), vy = vx;
+    if (vec && base >= 0 && base + 3 < n) {
+      vx = *reinterpret_cast<const int4 *>(x + base);
+      if (!ONE) vy = *reinterpret_cast<const int4 *>(y + base);
+    } else {
+      if (base >= 0 && base < n) vx.x = x[base];
+      if (base + 1 >= 0 && base + 1 < n) vx.y = x[base + 1];
+      if (base + 2 >= 0 && base + 2 < n) vx.z = x[base + 2];
+      if (base + 3 < n) vx.w = x[base + 3];
+      if (!ONE) {
+        if (base >= 0 && base < n) vy.x = y[base];
+        if (base + 1 >= 0 && base + 1 < n) vy.y = y[base + 1];
+        if (base + 2 >= 0 && base + 2 < n) vy.z = y[base + 2];
+        if (base + 3 < n) vy.w = y[base + 3];
+      }
+    }
+#pragma unroll 1
+    for (int e = 0; e < 4; ++e) {
+      const int64_t i = base + e;
+      if (i < 0 || i >= n) continue;
+      const int32_t xv = e == 0 ? vx.x : (e == 1 ? vx.y : (e == 2 ? vx.z : vx.w));
+      const int32_t yv = e == 0 ? vy.x : (e == 1 ? vy.y : (e == 2 ? vy.z : vy.w));
+      f(i, xv, ONE ? 0 : yv);
+    }
+  }
+}
+
 // Warp-aggregated append to a shared-memory list counter; returns the slot.
 __device__ __forceinline__ int warp_append(bool pred, int *counter) {
   const unsigned mask = __ballot_sync(0xFFFFFFFFu, pred);
@@ -624,9 +667,7 @@ __device__ __forceinline__ void node_loads(const EvalArgs &A, int64_t b, const I
     for (int64_t j = threadIdx.x; j < I.k; j += NT) s_load[j] = 0u;
     if (tr && threadIdx.x == 0) *minw = 0xFFFFFFFFu;
     __syncthreads();
-    for (int64_t i = threadIdx.x; i < I.n; i += NT) {
-      const int32_t a = I.a[i];
-      const int32_t w = I.w[i];
+    for_items_vec<NT, false>(I.a, I.w, I.n, [&](int64_t, int32_t a, int32_t w) {
       if (w < 0 || (int64_t)w > I.c || a < -1 || (int64_t)a >= I.k) {
         *err = 1;
       } else if (a >= 0) {
@@ -635,7 +676,7 @@ __device__ __forceinline__ void node_loads(const EvalArgs &A, int64_t b, const I
       } else if (tr && w > 0) {
         atomicMin(minw, (uint32_t)w);
       }
-    }
+    });
     if (tr) {
       __syncthreads();
       transform_bins<NT>(A, b, I, s_load, *minw, err);

@@ -708,9 +708,8 @@ __device__ __forceinline__ unsigned long long prefix_tile(const EvalArgs &A, con
     }
   };
   if (MODE == kSrcNodes) {
-    for (int64_t i = tid; i < I.n; i += kPrefixNT) {
-      const int32_t a = I.a[i];
-      const int32_t w = I.w[i];
+    // the node's assignment and base sizes, 16 bytes per load where aligned
+    for_items_vec<kPrefixNT, false>(I.a, I.w, I.n, [&](int64_t, int32_t a, int32_t w) {
       if (w < 0 || (int64_t)w > c || a < -1 || (int64_t)a >= I.k) {
         S.err = 1;
       } else if (a >= 0) {
@@ -720,13 +719,17 @@ __device__ __forceinline__ unsigned long long prefix_tile(const EvalArgs &A, con
         visit(w);
         if (tr && w > 0) atomicMin(&S.minw, (uint32_t)w);
       }
-    }
+    });
     __syncthreads();
     if (tr) {
       transform_bins<kPrefixNT>(A, b, I, s_load, S.minw, &S.err);
       __syncthreads();
     }
     for (int64_t j = tid; j < I.k; j += kPrefixNT) visit((int64_t)s_load[j]);
+  } else if (MODE == kSrcRaggedI32) {
+    // the instance's sizes, 16 bytes per load where aligned
+    for_items_vec<kPrefixNT, true>(reinterpret_cast<const int32_t *>(A.sizes) + I.begin, nullptr, I.n,
+                                   [&](int64_t, int32_t w, int32_t) { visit(w); });
   } else {
     const int64_t L = stream_len<MODE>(I);
     for (int64_t q = tid; q < L; q += kPrefixNT) {
