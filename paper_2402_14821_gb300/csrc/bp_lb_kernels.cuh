@@ -438,11 +438,18 @@ __device__ __forceinline__ int64_t plan_scan(int64_t v, int64_t *s_warp, int64_t
 // tables of the direct kernel (tile_start[0..B]), of the prefix kernel
 // (ptile_start[0..B]) and of the VB2 kernel (vtile_start[0..B]); an invalid
 // instance gets no tiles and an error result.  Clears keys/done and resets
-// the work counters.
+// the work counters.  Each thread takes kPlanPerThread consecutive instances
+// (their tile counts summed locally, so that one block scan per quantity
+// covers 1024 kPlanPerThread instances: the scans' barriers are most of the
+// kernel's time) and keeps its last instance's routing, reused while the
+// capacity and stream length repeat (every node of a search-node batch).
+constexpr int kPlanPerThread = 4;
+
 template <int MODE>
 __global__ void __launch_bounds__(1024)
     plan_kernel(EvalArgs A, int64_t lpt, int64_t *tile_start, int64_t *ptile_start,
                 int64_t *vtile_start) {
+  constexpr int K = kPlanPerThread;
   __shared__ int64_t s_warp[32];
   __shared__ int64_t s_carry[3];
   if (threadIdx.x == 0) {
@@ -455,50 +462,74 @@ __global__ void __launch_bounds__(1024)
   // one pass over the instances: validate, count the direct and prefix tiles
   // and VB2's parameters (kept in vtile_start[b] until the VB2 tile length is
   // known: VB2's parameters of the whole batch over the target tile count)
-  for (int64_t b0 = 0; b0 < A.B; b0 += blockDim.x) {
-    const int64_t b = b0 + threadIdx.x;
-    int64_t tiles = 0, ptiles = 0, pv = 0;
-    if (b < A.B) {
-      A.keys[b] = 0ull;
-      A.done[b] = 0u;
-      if (A.isums) A.isums[8 * b + 7] = 0;
-      bool ok;
-      int64_t c, L;
-      if (MODE == kSrcNodes) {
-        const int32_t base = A.node_base[b];
-        ok = base >= 0 && base < A.num_base;
-        c = ok ? A.base_capacity[base] : 0;
-        const int64_t n = ok ? A.base_offsets[base + 1] - A.base_offsets[base] : 0;
-        const int64_t na = A.assign_offsets[b + 1] - A.assign_offsets[b];
-        const int64_t k = A.bins[b];
-        ok = ok && c >= 1 && c <= kMaxCapacity && n >= 0 && n <= kMaxItems && na == n && k >= 0 &&
-             k <= A.max_bins &&
-             (A.bin_max == nullptr || A.bin_max_offsets[b + 1] - A.bin_max_offsets[b] == k);
-        L = n + k;
-      } else {
-        c = A.capacity[b];
-        L = A.offsets[b + 1] - A.offsets[b];
-        ok = c >= 1 && c <= kMaxCapacity && L >= 0 && L <= kMaxItems && A.bins[b] >= 0;
+  int64_t rc_c = -1, rc_L = -1, rc_t = 0, rc_p = 0, rc_v = 0;  // routing of (rc_c, rc_L)
+  for (int64_t b0 = 0; b0 < A.B; b0 += (int64_t)blockDim.x * K) {
+    const int64_t bt = b0 + (int64_t)threadIdx.x * K;  // this thread's first instance
+    int64_t tiles[K], ptiles[K], pvs[K];
+    int64_t st = 0, sp = 0, sv = 0;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const int64_t b = bt + j;
+      tiles[j] = ptiles[j] = pvs[j] = 0;
+      if (b < A.B) {
+        A.keys[b] = 0ull;
+        A.done[b] = 0u;
+        if (A.isums) A.isums[8 * b + 7] = 0;
+        bool ok;
+        int64_t c, L;
+        if (MODE == kSrcNodes) {
+          const int32_t base = A.node_base[b];
+          ok = base >= 0 && base < A.num_base;
+          c = ok ? A.base_capacity[base] : 0;
+          const int64_t n = ok ? A.base_offsets[base + 1] - A.base_offsets[base] : 0;
+          const int64_t na = A.assign_offsets[b + 1] - A.assign_offsets[b];
+          const int64_t k = A.bins[b];
+          ok = ok && c >= 1 && c <= kMaxCapacity && n >= 0 && n <= kMaxItems && na == n &&
+               k >= 0 && k <= A.max_bins &&
+               (A.bin_max == nullptr || A.bin_max_offsets[b + 1] - A.bin_max_offsets[b] == k);
+          L = n + k;
+        } else {
+          c = A.capacity[b];
+          L = A.offsets[b + 1] - A.offsets[b];
+          ok = c >= 1 && c <= kMaxCapacity && L >= 0 && L <= kMaxItems && A.bins[b] >= 0;
+        }
+        if (ok) {
+          if (c != rc_c || L != rc_L) {
+            rc_t = route_tiles(kRouteDirect, c, lpt, L * c, A.prefix_on, A.vb2_on, A.dff_off);
+            rc_p = route_tiles(kRoutePrefix, c, A.plpt, L * c, A.prefix_on, A.vb2_on, A.dff_off);
+            rc_v = (vtile_start != nullptr &&
+                    dff_kernel(kVB2, c, L * c, A.prefix_on, A.vb2_on, A.dff_off) == kRouteVb2)
+                       ? param_count(kVB2, c)
+                       : 0;
+            rc_c = c;
+            rc_L = L;
+          }
+          tiles[j] = rc_t;
+          ptiles[j] = rc_p;
+          pvs[j] = rc_v;
+          // no parameter at all (only DFFs with an empty range left in): bound 0
+          if (rc_t + rc_p + rc_v == 0) write_result(A, b, 0ull, c, A.bins[b]);
+        } else {
+          write_error(A, b);
+        }
       }
-      if (ok) {
-        tiles = route_tiles(kRouteDirect, c, lpt, L * c, A.prefix_on, A.vb2_on, A.dff_off);
-        ptiles = route_tiles(kRoutePrefix, c, A.plpt, L * c, A.prefix_on, A.vb2_on, A.dff_off);
-        if (vtile_start != nullptr &&
-            dff_kernel(kVB2, c, L * c, A.prefix_on, A.vb2_on, A.dff_off) == kRouteVb2)
-          pv = param_count(kVB2, c);
-        // no parameter at all (only DFFs with an empty range left in): bound 0
-        if (tiles + ptiles + pv == 0) write_result(A, b, 0ull, c, A.bins[b]);
-      } else {
-        write_error(A, b);
-      }
+      st += tiles[j];
+      sp += ptiles[j];
+      sv += pvs[j];
     }
-    const int64_t e0 = plan_scan(tiles, s_warp, &s_carry[0]);
-    const int64_t e1 = plan_scan(ptiles, s_warp, &s_carry[1]);
-    plan_scan(pv, s_warp, &s_carry[2]);
-    if (b < A.B) {
-      tile_start[b] = e0;
-      if (ptile_start) ptile_start[b] = e1;
-      if (vtile_start) vtile_start[b] = pv;
+    int64_t e0 = plan_scan(st, s_warp, &s_carry[0]);
+    int64_t e1 = plan_scan(sp, s_warp, &s_carry[1]);
+    plan_scan(sv, s_warp, &s_carry[2]);
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const int64_t b = bt + j;
+      if (b < A.B) {
+        tile_start[b] = e0;
+        if (ptile_start) ptile_start[b] = e1;
+        if (vtile_start) vtile_start[b] = pvs[j];
+      }
+      e0 += tiles[j];
+      e1 += ptiles[j];
     }
   }
   __syncthreads();
@@ -517,11 +548,21 @@ __global__ void __launch_bounds__(1024)
   // the VB2 tile table from the kept parameter counts (each thread rereads
   // its own entries)
   if (vtile_start != nullptr) {
-    for (int64_t b0 = 0; b0 < A.B; b0 += blockDim.x) {
-      const int64_t b = b0 + threadIdx.x;
-      const int64_t pv = b < A.B ? vtile_start[b] : 0;
-      const int64_t e2 = plan_scan(tile_count(pv, vlpt), s_warp, &s_carry[2]);
-      if (b < A.B) vtile_start[b] = e2;
+    for (int64_t b0 = 0; b0 < A.B; b0 += (int64_t)blockDim.x * K) {
+      const int64_t bt = b0 + (int64_t)threadIdx.x * K;
+      int64_t vt[K];
+      int64_t sv = 0;
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        vt[j] = bt + j < A.B ? tile_count(vtile_start[bt + j], vlpt) : 0;
+        sv += vt[j];
+      }
+      int64_t e2 = plan_scan(sv, s_warp, &s_carry[2]);
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        if (bt + j < A.B) vtile_start[bt + j] = e2;
+        e2 += vt[j];
+      }
     }
   }
   if (threadIdx.x == 0) {
