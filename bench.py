@@ -58,9 +58,9 @@ SM_COUNT_NOMINAL = 152
 # DRAM bytes (read + write) per search node of one launch of each kernel, from
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of a 512-node
 # launch, divided by 512: traffic grows with the nodes, each node's inputs
-# being read from DRAM once), or None while the kernel has changed since the
-# last capture.
-TRAFFIC_BYTES_PER_NODE = {"prefix": 2336, "vb2": None, "direct": None}
+# being read from DRAM once; profiles/prefix_kernel_search_nodes.md), or None
+# while the kernel has changed since the last capture.
+TRAFFIC_BYTES_PER_NODE = {"prefix": 2352, "vb2": None, "direct": None}
 
 # Prefix-count kernel: its algorithmic work is shared-memory table traffic, in
 # 32-bit words -- zeroing, histogram updates, three accesses per entry and
@@ -314,14 +314,15 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0,
                     help="CPU-seconds of oracle work for the cpu_baseline sample")
     ap.add_argument("--workload", choices=("search", "plain", "large", "ragged", "serve", "table1",
-                                           "issue"),
+                                           "issue", "hard"),
                     default="search",
                     help="search: the benchmark line (4096 search nodes); plain: one check of "
                          "n=50, c=150 per call (bp_lb_eval), 10^4 calls; large: n=10^4, "
                          "c in {1e5, 1e6}, three size families, batches of 64; ragged: 10^4 "
                          "ragged search nodes in one CUDA-graph launch; serve: 256 simulated "
                          "searches against the continuous-batching server, offered rates swept; "
-                         "issue: the integer-issue probe alone")
+                         "issue: the integer-issue probe alone; hard: the hard search-node "
+                         "batch alone (the benchmark line's hard_nodes record)")
     ap.add_argument("--large-cases", default="",
                     help="large: comma-separated c:family cases (default: both c, all families)")
     ap.add_argument("--large-count", type=int, default=64, help="large: instances per batch")
@@ -720,7 +721,7 @@ def node_tensors(nd):
                 assign=_dev(nd.assign, torch.int32), bins=_dev(nd.bins, torch.int64))
 
 
-def hard_nodes_record(B, stream, flush, steps, peak_ops):
+def hard_nodes_record(B, stream, flush, steps, peak_ops, shape=-1):
     """The search-node step on nodes whose bounds mostly exceed L1 (triplet
     instance, k = n/3; instances.hard_nodes), pruning on and off, per kernel."""
     import torch
@@ -737,8 +738,11 @@ def hard_nodes_record(B, stream, flush, steps, peak_ops):
                        "k=167 bins (the optimum)"}
     try:
         B.bp_lb_reserve(h, nd.count)
-        shape, _ = B.bp_lb_autotune_nodes(h, max_bins=mb, out_bound=ob, out_argmax=oa,
-                                          out_feasible=of, reps=2, stream=stream, **t_in)
+        if shape >= 0:
+            B.bp_lb_set_launch_shape(h, B.MODE_NODES, shape)
+        else:
+            shape, _ = B.bp_lb_autotune_nodes(h, max_bins=mb, out_bound=ob, out_argmax=oa,
+                                              out_feasible=of, reps=2, stream=stream, **t_in)
         step = lambda: B.bp_lb_eval_nodes(h, max_bins=mb, out_bound=ob, out_argmax=oa,
                                           out_feasible=of, stream=stream, **t_in)
         res = {}
@@ -961,6 +965,9 @@ def run_sweep(args):
     with ClockSampler(torch.cuda.current_device()) as clk:
         if args.workload == "issue":
             out["results"].append({k: v for k, v in ipeak.items() if k != "clocks"})
+        elif args.workload == "hard":
+            out["results"].append(hard_nodes_record(B, stream, flush, max(3, min(args.steps, 30)),
+                                                    peak, args.shape))
         elif args.workload == "large":
             steps = max(1, min(args.steps, 5))
             cases = ([(int(float(x.split(":")[0])), x.split(":")[1]) for x in args.large_cases.split(",")]
