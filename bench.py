@@ -329,10 +329,15 @@ def main():
     ap.add_argument("--dff-mask", type=int, default=63, help="large: DFFs in the bound (bits)")
     ap.add_argument("--no-prune", action="store_true", help="large: pruning off (all the work)")
     ap.add_argument("--large-dtypes", default="int32,int64", help="large: size types")
+    ap.add_argument("--no-cluster", action="store_true",
+                    help="every handle with cluster tables off (bp_lb_set_cluster_tables): "
+                         "prefix tables of 48-512 KB in the global scratch instead")
     ap.add_argument("--records", default="hard,large",
                     help="secondary records of the benchmark line (comma-separated: hard, large; "
                          "'none' for the search-node step alone, e.g. under a profiler)")
     args = ap.parse_args()
+    global CLUSTER_TABLES
+    CLUSTER_TABLES = not args.no_cluster
     if args.workload != "search":
         return run_sweep(args)
 
@@ -408,7 +413,7 @@ def main():
     out_b = torch.empty(NODES, dtype=torch.int64, device=dev)
     out_a = B.argmax_tensor(NODES)
     out_f = torch.empty(NODES, dtype=torch.uint8, device=dev)
-    h = B.bp_lb_create(CAP, 1 << 16)
+    h = new_handle(B, CAP, 1 << 16)
     B.bp_lb_reserve(h, NODES)
     # autotuner: pick the launch shape on this batch (not timed)
     if args.shape >= 0:
@@ -448,12 +453,14 @@ def main():
             e1.record(stream)
         barrier()
     step_ms = np.array([e0.elapsed_time(e1) for e0, e1 in ev])
-    ms_prefix, ms_vb2, ms_direct, n_calls = B.bp_lb_kernel_times(h)
+    ms_cluster, ms_prefix, ms_vb2, ms_direct, n_calls = B.bp_lb_kernel_times4(h)
+    cluster_used = B.bp_lb_get_cluster_tables(h) == 1
     kwork = B.bp_lb_kernel_work(h)        # VB2 pairs and parameters actually evaluated
     B.bp_lb_set_kernel_timing(h, False)
     t_direct = ms_direct / max(1, n_calls)
     t_vb2 = ms_vb2 / max(1, n_calls)
     t_prefix = ms_prefix / max(1, n_calls)
+    t_cluster = ms_cluster / max(1, n_calls)
     t_step = float(step_ms.mean())
     if world > 1:
         import torch.distributed as dist
@@ -636,12 +643,14 @@ def main():
                      "peak_basis": basis,
                      "kernel": kernel_name + ", its own CUDA-event time per launch",
                      "prefix_kernel_ms": t_prefix, "vb2_kernel_ms": t_vb2,
-                     "direct_kernel_ms": t_direct,
+                     "direct_kernel_ms": t_direct, "cluster_kernel_ms": t_cluster,
                      "prefix_kernel_frac": frac["prefix"], "vb2_kernel_frac": frac["vb2"],
                      "direct_kernel_frac": frac["direct"]},
         "launch_shape": {"chosen": shape, "nt_t_g_minb": list(B.bp_lb_launch_shape_info(shape)),
                          "autotune_ms": [round(x, 4) for x in shape_ms]},
-        "gpu_launches": 4 * args.steps,  # plan, prefix, VB2 and generic kernels per step
+        # plan, prefix, VB2 and generic kernels per step, and the cluster
+        # kernel when the autotuner left cluster tables on
+        "gpu_launches": (4 + (1 if cluster_used else 0)) * args.steps,
         "clocks": clocks,
         "issue_peak": ipeak,
         "hard_nodes": hard,
@@ -656,6 +665,16 @@ def main():
 # ---------------------------------------------------------------------------
 # secondary workloads (not the benchmark line): large instances, ragged batch
 # ---------------------------------------------------------------------------
+CLUSTER_TABLES = True
+
+
+def new_handle(B, c, max_items):
+    """A handle with the run's cluster-table setting."""
+    h = B.bp_lb_create(c, max_items)
+    B.bp_lb_set_cluster_tables(h, CLUSTER_TABLES)
+    return h
+
+
 def _dev(x, dt):
     import torch
     return torch.from_numpy(np.ascontiguousarray(x)).to(dt).cuda()
@@ -732,7 +751,7 @@ def hard_nodes_record(B, stream, flush, steps, peak_ops, shape=-1):
     ob = torch.empty(nd.count, dtype=torch.int64, device="cuda")
     oa = B.argmax_tensor(nd.count)
     of = torch.empty(nd.count, dtype=torch.uint8, device="cuda")
-    h = B.bp_lb_create(150, 1024)
+    h = new_handle(B, 150, 1024)
     out = {"workload": f"{nd.count} partial packings (uniform 0..60% committed) of one triplet "
                        "instance, n=501 sizes in (c/4, c/2) filling 167 bins exactly, c=10000, "
                        "k=167 bins (the optimum)"}
@@ -753,7 +772,7 @@ def hard_nodes_record(B, stream, flush, steps, peak_ops, shape=-1):
             B.bp_lb_set_kernel_timing(h, True)
             B.bp_lb_kernel_times(h)
             ms = _time_steps(step, steps if prune else max(3, steps // 3), flush, stream)
-            kp, kv, kd, kn = B.bp_lb_kernel_times(h)
+            kc, kp, kv, kd, kn = B.bp_lb_kernel_times4(h)
             kw = B.bp_lb_kernel_work(h)
             B.bp_lb_set_kernel_timing(h, False)
             n = max(1, kn)
@@ -764,7 +783,8 @@ def hard_nodes_record(B, stream, flush, steps, peak_ops, shape=-1):
             out["pruning_on" if prune else "pruning_off"] = {
                 "value": nd.count / (t / 1e3), "unit": UNIT, "ms_per_step": t,
                 "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
-                "kernel_ms": {"prefix": kp / n, "vb2": kv / n, "direct": kd / n},
+                "kernel_ms": {"cluster": kc / n, "prefix": kp / n, "vb2": kv / n,
+                              "direct": kd / n},
                 "vb2_pairs_evaluated": kw[0] / n, "vb2_params_pruned": kw[3] / n,
                 "vb2_kernel_frac_of_issue_peak": vb2_frac}
         B.bp_lb_set_pruning(h, True)
@@ -792,7 +812,7 @@ def large_record(B, stream, flush, peak_ops, cases=LARGE_CASES, steps=3):
     evaluate, VB2's counted by the kernels, over their own CUDA-event time)."""
     import torch
     from paper_2402_14821_gb300 import instances as I
-    h = B.bp_lb_create(150, 1024)
+    h = new_handle(B, 150, 1024)
     res = []
     try:
         for c, fam in cases:
@@ -808,7 +828,7 @@ def large_record(B, stream, flush, peak_ops, cases=LARGE_CASES, steps=3):
             B.bp_lb_set_kernel_timing(h, True)
             B.bp_lb_kernel_times(h)
             ms = _time_steps(step, steps, flush, stream)
-            kp, kv, kd, kn = B.bp_lb_kernel_times(h)
+            kc, kp, kv, kd, kn = B.bp_lb_kernel_times4(h)
             kw = B.bp_lb_kernel_work(h)
             B.bp_lb_set_kernel_timing(h, False)
             n = max(1, kn)
@@ -823,7 +843,7 @@ def large_record(B, stream, flush, peak_ops, cases=LARGE_CASES, steps=3):
                 B.bp_lb_set_kernel_timing(h, True)
                 B.bp_lb_kernel_times(h)
                 ms_off = _time_steps(step, steps, flush, stream)
-                kp2, kv2, kd2, kn2 = B.bp_lb_kernel_times(h)
+                kc2, kp2, kv2, kd2, kn2 = B.bp_lb_kernel_times4(h)
                 kw2 = B.bp_lb_kernel_work(h)
                 B.bp_lb_set_kernel_timing(h, False)
                 B.bp_lb_set_pruning(h, True)
@@ -831,14 +851,15 @@ def large_record(B, stream, flush, peak_ops, cases=LARGE_CASES, steps=3):
                 td2 = (kv2 + kd2) / n2
                 ops2 = ragged_work(rg)[1] + (kw2[0] + kw2[1]) / n2 * ops_per_eval(4, c)
                 off = {"ms_per_batch": float(ms_off.mean()), "item_kernels_ms": td2,
-                       "prefix_kernel_ms": kp2 / n2, "item_kernel_ops": ops2,
+                       "prefix_kernel_ms": kp2 / n2, "cluster_kernel_ms": kc2 / n2,
+                       "item_kernel_ops": ops2,
                        "item_kernels_frac_of_issue_peak": ops2 / (td2 / 1e3) / peak_ops
                        if td2 > 0 else None}
             res.append({"c": c, "family": fam, "instances": 64, "n": 10_000, "dtype": "int32",
                         "ms_per_batch": tm, "checks_per_s": 64 / (tm / 1e3),
                         "evals_per_s_equivalent": evals / (tm / 1e3), "launch_shape": shape,
-                        "prefix_kernel_ms": kp / n, "item_kernels_ms": td,
-                        "item_kernel_ops": ops,
+                        "prefix_kernel_ms": kp / n, "cluster_kernel_ms": kc / n,
+                        "item_kernels_ms": td, "item_kernel_ops": ops,
                         "item_kernels_frac_of_issue_peak": ops / (td / 1e3) / peak_ops
                         if td > 0 else None, "pruning_off": off})
             del t, ob, oa
@@ -960,7 +981,7 @@ def run_sweep(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     ipeak = issue_peak(B, stream)
     peak = ipeak["lane_ops_per_s"]
-    h = B.bp_lb_create(150, 1 << 16)
+    h = new_handle(B, 150, 1 << 16)
     out = {"workload": args.workload, "results": [], "issue_peak": ipeak}
     with ClockSampler(torch.cuda.current_device()) as clk:
         if args.workload == "issue":
@@ -995,7 +1016,7 @@ def run_sweep(args):
                     B.bp_lb_set_kernel_timing(h, True)
                     B.bp_lb_kernel_times(h)
                     ms = _time_steps(step, steps, flush, stream)
-                    kp, kv, kd, kn = B.bp_lb_kernel_times(h)
+                    kc, kp, kv, kd, kn = B.bp_lb_kernel_times4(h)
                     kw = B.bp_lb_kernel_work(h)
                     B.bp_lb_set_kernel_timing(h, False)
                     tm = float(ms.mean())
@@ -1008,13 +1029,14 @@ def run_sweep(args):
                         "evals_per_s": evals / (tm / 1e3), "launch_shape": shape,
                         "item_kernels_ms": td, "vb2_kernel_ms": kv / max(1, kn),
                         "prefix_kernel_ms": kp / max(1, kn),
+                        "cluster_kernel_ms": kc / max(1, kn),
                         "roofline_frac": ops / (td / 1e3) / peak})
                     print(json.dumps(out["results"][-1]), flush=True)
         elif args.workload == "plain":
             import oracle
             rg = I.plain_single(seed=0)
             w, c, k = rg.instance(0), int(rg.capacity[0]), int(rg.bins[0])
-            hp = B.bp_lb_create(c, 1024)
+            hp = new_handle(B, c, 1024)
             for _ in range(100):
                 B.bp_lb_eval(hp, w, k)
             lat = []
@@ -1101,7 +1123,7 @@ def run_sweep(args):
             B.bp_lb_set_kernel_timing(h, True)
             B.bp_lb_kernel_times(h)
             ms_direct = _time_steps(direct, steps, flush, stream)
-            kp, kv, kd, kn = B.bp_lb_kernel_times(h)
+            kc, kp, kv, kd, kn = B.bp_lb_kernel_times4(h)
             kw = B.bp_lb_kernel_work(h)
             B.bp_lb_set_kernel_timing(h, False)
             # VB2 on its kernel up to c = 65535, on the generic one above
@@ -1115,7 +1137,7 @@ def run_sweep(args):
                 "evals_per_batch": evals, "launch_shape": shape,
                 "autotune_ms": [round(x, 3) for x in shape_ms],
                 "item_kernels_ms": td, "vb2_kernel_ms": kv / max(1, kn),
-                "prefix_kernel_ms": kp / max(1, kn),
+                "prefix_kernel_ms": kp / max(1, kn), "cluster_kernel_ms": kc / max(1, kn),
                 "roofline_frac": ops / (td / 1e3) / peak})
             print(json.dumps(out["results"][-1]), flush=True)
     out["clocks"] = clk.summary()

@@ -250,17 +250,41 @@ int bp_lb_eval_batch_noalloc(int32_t B, const int64_t *d_offsets,
 
 /* BP_ALGO_DIRECT evaluates every (DFF, lambda) pair item by item (Alg. 2's
  * loops).  BP_ALGO_PREFIX (the default) computes the same bounds exactly but
- * evaluates MT, RAD2, CCM1 and BJ1 from value-indexed suffix counts and sums
- * built in shared memory (O(1), O(1), O(c / lambda) and O(c / lambda) lookups
- * per parameter instead of one evaluation per item) wherever those tables fit
- * in 48 KB (c up to 12286 for RAD2 and BJ1, 24574 for MT and CCM1) and the
- * reduced sizes sum to less than 2^31; VB2, FS1, and the others beyond those
- * limits, stay on the direct path.  Results are identical either way. */
+ * evaluates MT, RAD2, FS1, CCM1 and BJ1 from value-indexed suffix counts and
+ * sums of the reduced instance (O(1), O(1), O(lambda), O(c / lambda) and
+ * O(c / lambda) lookups per parameter instead of one evaluation per item)
+ * when the reduced sizes sum to less than 2^31.  The tables live in one
+ * CTA's shared memory where they fit in 48 KB (c up to 12286 for RAD2, FS1,
+ * BJ1 and the merged MT/RAD2/CCM1 tile, 24574 for MT and CCM1 alone); else,
+ * with cluster tables on (bp_lb_set_cluster_tables), spread over
+ * the shared memory of a cluster of 8 CTAs, 64 KB each (c up to 131070, MT
+ * and CCM1 alone 262142); else in a global-memory scratch of 4 MB per CTA
+ * (c up to 1048574, MT and CCM1 alone 2097150); beyond that on the direct
+ * path.  VB2 stays on the direct kernels, except that in batched calls with
+ * pruning on (or in verdict mode) the merged MT/RAD2/CCM1 tile also takes
+ * VB2 when pruning leaves only parameters up to some lmax and their
+ * count-table lookups (about l / 2 each) stay within 65536 per CTA of the
+ * tile.  Results are identical either way. */
 #define BP_ALGO_DIRECT 0
 #define BP_ALGO_PREFIX 1
 
 /* Selects the algorithm of a handle.  Errors: BP_EINVAL, BP_ERANGE. */
 int bp_lb_set_algorithm(bp_lb_t *h, int32_t algo);
+
+/* Cluster tables on (1) or off (0, the default): with them on, prefix-count
+ * tables too large for one CTA's 48 KB but within 512 KB are built and read
+ * by a cluster of 8 CTAs in their shared memory (one launch more per batched
+ * call, the cluster kernel, which finds nothing to do when no instance has
+ * such tables); off, they go to the global scratch as beyond 512 KB.  A
+ * cluster takes one such instance's tables several times faster than one CTA
+ * with its tables in the global scratch, but occupies eight CTAs, so it pays
+ * for batches with fewer such instances than the GPU has CTA slots; the
+ * batched autotuners (bp_lb_autotune_batch, bp_lb_autotune_nodes) try both
+ * settings.  The paper has no counterpart (its kernel evaluates every pair
+ * item by item); results are identical either way.  Errors: BP_EINVAL (NULL handle), BP_ERANGE (not 0
+ * or 1).  bp_lb_get_cluster_tables: the setting, or -1 for a NULL handle. */
+int bp_lb_set_cluster_tables(bp_lb_t *h, int32_t on);
+int bp_lb_get_cluster_tables(bp_lb_t *h);
 
 /* The handle's algorithm (batched modes), or -1 for a NULL handle. */
 int bp_lb_get_algorithm(bp_lb_t *h);
@@ -402,10 +426,11 @@ int bp_lb_get_dff_mask(bp_lb_t *h);
 
 /* ---- concurrency of the evaluation kernels (batched calls) ----------------- */
 
-/* A batched call runs three evaluation kernels (see bp_lb_kernel_times), by
+/* A batched call runs four evaluation kernels (see bp_lb_kernel_times4), by
  * default (0) one after another on the caller's stream.  With
- * prefix_ctas_per_sm > 0 the prefix-count kernel, then the generic kernel,
- * run on a high-priority side stream of the handle while the VB2 kernel runs
+ * prefix_ctas_per_sm > 0 the cluster and prefix-count kernels, then the
+ * generic kernel, run on a high-priority side stream of the handle while the
+ * VB2 kernel runs
  * on the caller's stream: the prefix kernel takes that many CTAs per SM, the
  * VB2 kernel the rest (its remaining CTAs become resident as the prefix
  * kernel's retire).  The call stays ordered on the caller's stream (fork
@@ -422,10 +447,13 @@ int bp_lb_set_overlap(bp_lb_t *h, int32_t prefix_ctas_per_sm);
  * lambda) evaluated item by item) -- (not for use under stream capture).
  * bp_lb_kernel_times waits for the events recorded since the previous query
  * and returns the total milliseconds of each kernel and the number of calls
- * (any pointer may be NULL). */
+ * (any pointer may be NULL).  bp_lb_kernel_times4 does the same with the
+ * cluster kernel's time too: out_ms4 = {cluster, prefix, VB2, direct} (NULL:
+ * not written); either query consumes the events. */
 int bp_lb_set_kernel_timing(bp_lb_t *h, int32_t on);
 int bp_lb_kernel_times(bp_lb_t *h, double *ms_prefix, double *ms_vb2, double *ms_direct,
                        int64_t *calls);
+int bp_lb_kernel_times4(bp_lb_t *h, double *out_ms4, int64_t *calls);
 
 /* Measurement aid: work counted by the batched calls made with timing on,
  * since the previous query (which resets the counters; it synchronizes the
@@ -486,7 +514,8 @@ int bp_lb_get_launch_shape(bp_lb_t *h, int32_t mode);
  * `reps` times, timed with CUDA events on `stream`; keeps the fastest shape
  * for the mode and writes it to *best_shape (may be NULL), and the mean
  * milliseconds per call of every shape to ms_per_shape[0 .. num shapes) (may
- * be NULL).  The output buffers receive the batch's results.  Synchronises
+ * be NULL); then times the batch with that shape and cluster tables switched
+ * (bp_lb_set_cluster_tables) and keeps the faster setting.  The output buffers receive the batch's results.  Synchronises
  * the stream (not capturable).  Arguments as for bp_lb_eval_batch(_i64)
  * (sizes_are_i64 selects the size type) and bp_lb_eval_nodes.
  * Errors: as those calls, and BP_EINVAL for B < 1 or reps < 1. */

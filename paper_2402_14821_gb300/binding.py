@@ -90,6 +90,9 @@ def _bind(lib):
         "bp_lb_get_vb2_cap": (ctypes.c_int, [_vp]),
         "bp_lb_set_dff_mask": (ctypes.c_int, [_vp, _c_i32]),
         "bp_lb_set_overlap": (ctypes.c_int, [_vp, _c_i32]),
+        "bp_lb_set_cluster_tables": (ctypes.c_int, [_vp, _c_i32]),
+        "bp_lb_get_cluster_tables": (ctypes.c_int, [_vp]),
+        "bp_lb_kernel_times4": (ctypes.c_int, [_vp, P(ctypes.c_double), P(_c_i64)]),
         "bp_lb_l2_batch": (ctypes.c_int, [_vp, _c_i32, _vp, _vp, _vp, _vp, _vp]),
         "bp_lb_get_dff_mask": (ctypes.c_int, [_vp]),
         "bp_lb_get_result_mode": (ctypes.c_int, [_vp]),
@@ -137,7 +140,8 @@ EXPORTED = ("bp_lb_strerror", "bp_lb_create", "bp_lb_destroy", "bp_lb_reserve", 
             "bp_lb_get_dff_mask", "bp_lb_l2_batch", "bp_lb_set_overlap", "bp_lb_set_pruning",
             "bp_lb_get_pruning", "bp_lb_kernel_work", "bp_lb_set_reduction",
             "bp_lb_get_reduction", "bp_lb_set_bin_max", "bp_lb_set_vb2_cap",
-            "bp_lb_get_vb2_cap", "bp_lb_eval_range", "bp_lb_probe_int_issue")
+            "bp_lb_get_vb2_cap", "bp_lb_eval_range", "bp_lb_probe_int_issue",
+            "bp_lb_set_cluster_tables", "bp_lb_get_cluster_tables", "bp_lb_kernel_times4")
 
 ALGO_DIRECT, ALGO_PREFIX = 0, 1
 RESULT_FULL, RESULT_VERDICT = 0, 1
@@ -413,6 +417,15 @@ def bp_lb_set_overlap(h, prefix_ctas_per_sm: int):
     _check(lib().bp_lb_set_overlap(h, int(prefix_ctas_per_sm)), "bp_lb_set_overlap")
 
 
+def bp_lb_set_cluster_tables(h, on: bool):
+    """Prefix-count tables of 48-512 KB in a cluster's shared memory (default) or not."""
+    _check(lib().bp_lb_set_cluster_tables(h, int(bool(on))), "bp_lb_set_cluster_tables")
+
+
+def bp_lb_get_cluster_tables(h) -> int:
+    return lib().bp_lb_get_cluster_tables(h)
+
+
 def bp_lb_set_dff_mask(h, mask: int):
     """Bit d keeps DFF d (MT, RAD2, FS1, CCM1, VB2, BJ1) in the bound; 63 = all."""
     _check(lib().bp_lb_set_dff_mask(h, int(mask)), "bp_lb_set_dff_mask")
@@ -434,6 +447,15 @@ def bp_lb_kernel_times(h):
                                     ctypes.byref(n)),
            "bp_lb_kernel_times")
     return p.value, v.value, d.value, n.value
+
+
+def bp_lb_kernel_times4(h):
+    """(ms in the cluster kernel, the prefix-count kernel, the VB2 kernel, the
+    generic direct kernel, calls) since the last query."""
+    ms = (ctypes.c_double * 4)()
+    n = ctypes.c_int64()
+    _check(lib().bp_lb_kernel_times4(h, ms, ctypes.byref(n)), "bp_lb_kernel_times4")
+    return ms[0], ms[1], ms[2], ms[3], n.value
 
 
 def bp_lb_dff_route(d: int, c: int, stream_len: int, algo: int = 1) -> int:

@@ -10,7 +10,7 @@ LIB = os.path.join(HERE, "libbp_lb.so")
 SOURCES = ("bp_lb.cu", "bp_lb_inst_ragged_i32.cu", "bp_lb_inst_ragged_i64.cu",
            "bp_lb_inst_nodes.cu", "bp_lb_noalloc.cu", "bp_serve.cu", "bp_lb_probe.cu")
 DEPS = SOURCES + ("bp_lb_core.cuh", "bp_lb_eval.cuh", "bp_lb_kernels.cuh", "bp_lb_launch.cuh",
-                  "bp_lb_prefix.cuh", "bp_lb_vb2.cuh", "bp_lb_l2.cuh")
+                  "bp_lb_prefix.cuh", "bp_lb_vb2.cuh", "bp_lb_l2.cuh", "bp_lb_cluster.cuh")
 ARCH = ("-gencode", "arch=compute_103a,code=sm_103a")
 
 

@@ -61,6 +61,7 @@ struct bp_lb {
   int32_t cap_batch = 0;
   int64_t *d_tile_start = nullptr;
   int64_t *d_ptile_start = nullptr;  // prefix-kernel tile table
+  int64_t *d_ctile_start = nullptr;  // cluster-kernel unit table
   int64_t *d_vtile_start = nullptr;  // VB2-kernel tile table
   int32_t prefix_on = 1;             // batched modes: BP_ALGO_PREFIX (default) or DIRECT
   int32_t plain_prefix_on = 1;       // plain modes
@@ -69,6 +70,13 @@ struct bp_lb {
   int32_t *d_gscratch = nullptr;
   int64_t gscratch_ctas = 0;
   bool gscratch_failed = false;
+  // tables too large for one CTA but within a cluster's shared memory go to
+  // the cluster kernel (bp_lb_set_cluster_tables, or the batched autotuners;
+  // default off); its resident clusters per launch, cached per mode and
+  // shared-memory size
+  int32_t cluster_on = 0;
+  int cl_clusters[3] = {0, 0, 0};
+  size_t cl_smem[3] = {0, 0, 0};
   // batched modes send VB2 (c <= 65535) to the VB2 kernel; the plain path
   // keeps it in the direct kernel (one launch fewer per check)
   int32_t vb2_on = 1;
@@ -85,6 +93,7 @@ struct bp_lb {
   int32_t prefix_ctas = 0;
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_cjoin = nullptr;  // the cluster kernel's end on the side stream
   uint32_t dff_off = 0;  // DFFs left out of the bound (bit d), default none
   // VB2's parameter cap of Sec. 4 (bp_lb_set_vb2_cap): off by default; when
   // on, vb2cap_kernel writes each instance's last VB2 parameter here
@@ -101,7 +110,7 @@ struct bp_lb {
   bool timing = false;
   unsigned long long *d_work_count = nullptr;  // 4 counters (EvalArgs::work_count)
   std::vector<cudaEvent_t> ev_pool;
-  std::vector<std::array<cudaEvent_t, 6>> ev_pending;
+  std::vector<std::array<cudaEvent_t, 8>> ev_pending;
   size_t ev_next = 0;
   unsigned long long *d_keys = nullptr;
   unsigned int *d_done = nullptr;
@@ -166,6 +175,7 @@ int grow_batch(bp_lb *h, int32_t B) {
   int32_t cap = std::max<int32_t>(B, 1024);
   cudaFree(h->d_tile_start);
   cudaFree(h->d_ptile_start);
+  cudaFree(h->d_ctile_start);
   cudaFree(h->d_vtile_start);
   cudaFree(h->d_keys);
   cudaFree(h->d_done);
@@ -175,12 +185,14 @@ int grow_batch(bp_lb *h, int32_t B) {
   h->d_vb2hi = nullptr;
   h->d_tile_start = nullptr;
   h->d_ptile_start = nullptr;
+  h->d_ctile_start = nullptr;
   h->d_vtile_start = nullptr;
   h->d_keys = nullptr;
   h->d_done = nullptr;
   h->cap_batch = 0;
   BP_CHECK(cudaMalloc(&h->d_tile_start, sizeof(int64_t) * ((size_t)cap + 1)));
   BP_CHECK(cudaMalloc(&h->d_ptile_start, sizeof(int64_t) * ((size_t)cap + 1)));
+  BP_CHECK(cudaMalloc(&h->d_ctile_start, sizeof(int64_t) * ((size_t)cap + 1)));
   BP_CHECK(cudaMalloc(&h->d_vtile_start, sizeof(int64_t) * ((size_t)cap + 1)));
   BP_CHECK(cudaMalloc(&h->d_keys, sizeof(unsigned long long) * (size_t)cap));
   BP_CHECK(cudaMalloc(&h->d_done, sizeof(unsigned int) * (size_t)cap));
@@ -211,6 +223,36 @@ int launch_prefix(int mode, unsigned grid, size_t smem, cudaStream_t st, EvalArg
                                       dim3(kPrefixNT), args, smem, st));
 }
 
+// Dynamic shared memory of the cluster kernel: a table slice, then (search
+// nodes) the bin loads.
+size_t cluster_smem(int mode, int64_t max_bins) {
+  return (size_t)kSliceBytes + (mode == kSrcNodes ? sizeof(uint32_t) * (size_t)max_bins : 0);
+}
+
+// Clusters of the cluster kernel resident at once at `smem` bytes per CTA.
+int cluster_slots(bp_lb *h, int mode, size_t smem) {
+  if (h->cl_smem[mode] == smem && h->cl_clusters[mode] > 0) return h->cl_clusters[mode];
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(kClusterCtas * h->num_sms));
+  cfg.blockDim = dim3(kPrefixNT);
+  cfg.dynamicSmemBytes = smem;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, (const void *)cluster_fn(mode), &cfg) != cudaSuccess)
+    return 0;
+  h->cl_smem[mode] = smem;
+  h->cl_clusters[mode] = n;
+  return n;
+}
+
+// The cluster kernel over `clusters` clusters (the grid is kClusterCtas times
+// that; the kernel's cluster shape is compiled in).
+int launch_cluster(int mode, unsigned clusters, size_t smem, cudaStream_t st, EvalArgs &A) {
+  void *args[] = {&A};
+  return cuda_status(cudaLaunchKernel((const void *)cluster_fn(mode),
+                                      dim3(clusters * (unsigned)kClusterCtas), dim3(kPrefixNT),
+                                      args, smem, st));
+}
+
 // The prefix_on bits for a call whose prefix kernel runs `ctas` CTAs: the
 // global-table bit only when the scratch covers them (allocated on first use;
 // if that fails, tables stay in shared memory).
@@ -227,7 +269,8 @@ int32_t prefix_bits(bp_lb *h, bool on, int64_t ctas) {
       h->gscratch_failed = true;
     }
   }
-  return kPrefixShared | ((h->d_gscratch && ctas <= h->gscratch_ctas) ? kPrefixGlobal : 0);
+  return kPrefixShared | ((h->d_gscratch && ctas <= h->gscratch_ctas) ? kPrefixGlobal : 0) |
+         (h->cluster_on ? kPrefixCluster : 0);
 }
 
 // VB2's cap (vb2cap_kernel) of the A.B instances into hi[0 .. A.B).
@@ -273,6 +316,8 @@ int launch_batch(bp_lb *h, EvalArgs A, size_t smem, cudaStream_t st) {
   A.ptile_start = h->d_ptile_start;
   A.pwork = h->d_work + 1;
   A.plpt = kPrefixLPTBatch;
+  A.ctile_start = h->d_ctile_start;
+  A.cwork = h->d_work + 4;
   A.vb2_on = h->vb2_on;
   A.verdict = h->verdict;
   A.prune = h->prune;
@@ -288,7 +333,7 @@ int launch_batch(bp_lb *h, EvalArgs A, size_t smem, cudaStream_t st) {
   const int occ = occupancy(h, MODE, smem);
   if (occ <= 0) return BP_ECUDA;
   plan_kernel<MODE><<<1, 1024, 0, st>>>(A, shape_lpt(shape), h->d_tile_start, h->d_ptile_start,
-                                        h->d_vtile_start);
+                                        h->d_vtile_start, h->d_ctile_start);
   BP_CHECK(cudaGetLastError());
   if (h->vb2_cap) {
     // each instance's last VB2 parameter under the cap, before any VB2 tile
@@ -296,8 +341,10 @@ int launch_batch(bp_lb *h, EvalArgs A, size_t smem, cudaStream_t st) {
     BP_CHECK_STATUS(launch_vb2cap(h, MODE, A, h->d_vb2hi, st));
   }
   // Timing events: [0] before the prefix kernel, [1] after it, [2] before the
-  // VB2 kernel, [3] after it, [4] before the generic kernel, [5] after it.
-  std::array<cudaEvent_t, 6> ev = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  // VB2 kernel, [3] after it, [4] before the generic kernel, [5] after it,
+  // [6] before the cluster kernel, [7] after it.
+  std::array<cudaEvent_t, 8> ev = {nullptr, nullptr, nullptr, nullptr,
+                                   nullptr, nullptr, nullptr, nullptr};
   if (h->timing)
     for (auto &e : ev)
       if (!(e = next_event(h))) return BP_ECUDA;
@@ -316,10 +363,27 @@ int launch_batch(bp_lb *h, EvalArgs A, size_t smem, cudaStream_t st) {
   // (fork after the plan, join before returning), so capturable in a graph.
   const bool overlap = h->prefix_ctas > 0 && h->vb2_on;
   cudaStream_t ps_st = overlap ? h->side : st;
-  if (overlap) {
+  // The cluster kernel runs on the side stream, beside the prefix and VB2
+  // kernels (where it finds no unit -- no instance with tables of its size --
+  // its launch then costs the caller's stream nothing); the generic kernel
+  // waits for it, since it publishes the instance sums that the generic
+  // kernel's VB2 tiles are pruned with.  With overlap it simply leads the
+  // side stream's sequence.
+  const bool cl = (A.prefix_on & kPrefixCluster) != 0;
+  const bool cl_side = cl && !overlap;
+  if (overlap || cl_side) {
     BP_CHECK(cudaEventRecord(h->ev_fork, st));
     BP_CHECK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
   }
+  if (h->timing) BP_CHECK(cudaEventRecord(ev[6], h->side));
+  if (cl) {
+    const size_t cs = cluster_smem(MODE, A.max_bins);
+    const int nc = cluster_slots(h, MODE, cs);
+    if (nc <= 0) return BP_ECUDA;
+    BP_CHECK_STATUS(launch_cluster(MODE, (unsigned)nc, cs, h->side, A));
+  }
+  if (h->timing) BP_CHECK(cudaEventRecord(ev[7], h->side));
+  if (cl_side) BP_CHECK(cudaEventRecord(h->ev_cjoin, h->side));
   if (h->timing) BP_CHECK(cudaEventRecord(ev[0], ps_st));
   if (h->prefix_on) {
     const int pc = overlap ? std::min(pocc, (int)h->prefix_ctas) : pocc;
@@ -349,8 +413,12 @@ int launch_batch(bp_lb *h, EvalArgs A, size_t smem, cudaStream_t st) {
                               dim3(kVb2NT), args, vs, st));
   }
   if (h->timing) BP_CHECK(cudaEventRecord(ev[3], st));
-  if (overlap) BP_CHECK(cudaStreamWaitEvent(st, h->ev_join, 0));
-  else BP_CHECK_STATUS(generic(st));
+  if (overlap) {
+    BP_CHECK(cudaStreamWaitEvent(st, h->ev_join, 0));
+  } else {
+    if (cl_side) BP_CHECK(cudaStreamWaitEvent(st, h->ev_cjoin, 0));
+    BP_CHECK_STATUS(generic(st));
+  }
   if (h->timing) h->ev_pending.push_back(ev);
   return BP_OK;
 }
@@ -386,9 +454,27 @@ int autotune(bp_lb *h, int mode, int32_t reps, cudaStream_t st, float *ms_out,
       best = s;
     }
   }
+  h->shape[mode] = best;
+  // then, with that shape, cluster tables switched: the faster setting stays
+  if (st_all == BP_OK) {
+    const int32_t keep = h->cluster_on;
+    h->cluster_on = !keep;
+    st_all = call();
+    float ms = 0.f;
+    if (st_all == BP_OK) {
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < reps && st_all == BP_OK; ++r) st_all = call();
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) st_all = BP_ECUDA;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= reps;
+    }
+    // switched only for a clear gain (the setting costs a launch when it
+    // finds nothing to do, and ties are noise)
+    if (st_all != BP_OK || ms > 0.97f * best_ms) h->cluster_on = keep;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  h->shape[mode] = best;
   if (best_out) *best_out = best;
   return st_all;
 }
@@ -434,6 +520,9 @@ int bp_lb_create(int64_t capacity, int64_t max_items, bp_lb_t **out) {
       break;
     if ((st = cuda_status(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming))) != BP_OK)
       break;
+    if ((st = cuda_status(cudaEventCreateWithFlags(&h->ev_cjoin, cudaEventDisableTiming))) !=
+        BP_OK)
+      break;
     if ((st = cuda_status(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming))) != BP_OK)
       break;
     const size_t nb = sizeof(int32_t) * (size_t)max_items;
@@ -445,7 +534,7 @@ int bp_lb_create(int64_t capacity, int64_t max_items, bp_lb_t **out) {
     if ((st = cuda_status(cudaMallocHost(&h->h_out, sizeof(PlainOut)))) != BP_OK) break;
     if ((st = cuda_status(cudaMalloc(&h->d_key1, sizeof(unsigned long long)))) != BP_OK) break;
     if ((st = cuda_status(cudaMalloc(&h->d_done1, sizeof(unsigned int)))) != BP_OK) break;
-    if ((st = cuda_status(cudaMalloc(&h->d_work, 4 * sizeof(unsigned long long)))) != BP_OK) break;
+    if ((st = cuda_status(cudaMalloc(&h->d_work, 8 * sizeof(unsigned long long)))) != BP_OK) break;
     if ((st = cuda_status(cudaMalloc(&h->d_vb2hi1, sizeof(int64_t)))) != BP_OK) break;
     if ((st = cuda_status(cudaMalloc(&h->d_rkey, sizeof(unsigned long long)))) != BP_OK) break;
     if ((st = cuda_status(cudaMalloc(&h->d_rdone, sizeof(unsigned int)))) != BP_OK) break;
@@ -455,12 +544,17 @@ int bp_lb_create(int64_t capacity, int64_t max_items, bp_lb_t **out) {
     if ((st = cuda_status(cudaMemset(h->d_rdone, 0, sizeof(unsigned int)))) != BP_OK) break;
     if ((st = cuda_status(cudaMemset(h->d_key1, 0, sizeof(unsigned long long)))) != BP_OK) break;
     if ((st = cuda_status(cudaMemset(h->d_done1, 0, sizeof(unsigned int)))) != BP_OK) break;
-    if ((st = cuda_status(cudaMemset(h->d_work, 0, 4 * sizeof(unsigned long long)))) != BP_OK)
+    if ((st = cuda_status(cudaMemset(h->d_work, 0, 8 * sizeof(unsigned long long)))) != BP_OK)
       break;
-    for (int mode = 0; mode < 3 && st == BP_OK; ++mode)
+    for (int mode = 0; mode < 3 && st == BP_OK; ++mode) {
       st = cuda_status(cudaFuncSetAttribute((const void *)prefix_fn(mode),
                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)prefix_smem(mode, kMaxNodeBins)));
+      if (st == BP_OK)
+        st = cuda_status(cudaFuncSetAttribute((const void *)cluster_fn(mode),
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)cluster_smem(mode, kMaxNodeBins)));
+    }
     if (st != BP_OK) break;
     // the plain node path may use the full on-chip bin table
     const size_t smem_nodes = eval_smem<kSrcNodes>(kMaxNodeBins);
@@ -527,6 +621,7 @@ int bp_lb_destroy(bp_lb_t *h) {
   if (h->side) cudaStreamDestroy(h->side);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->ev_cjoin) cudaEventDestroy(h->ev_cjoin);
   delete h;
   return BP_OK;
 }
@@ -576,12 +671,13 @@ static EvalArgs plain_args(bp_lb *h, int64_t n, int64_t bins, int mode) {
   A.prefix_on = prefix_bits(h, h->plain_prefix_on != 0, 0);
   if (A.prefix_on & kPrefixGlobal) {
     const int64_t pt = route_tiles(kRoutePrefix, h->capacity, A.plpt, sb, A.prefix_on, 0, A.dff_off);
-    if (pt > h->gscratch_ctas) A.prefix_on = kPrefixShared;
+    if (pt > h->gscratch_ctas) A.prefix_on &= ~kPrefixGlobal;
   }
   A.gscratch = h->d_gscratch;
   A.single_tiles = route_tiles(kRouteDirect, h->capacity, shape_lpt(h->shape[mode]), sb,
                                A.prefix_on, 0, A.dff_off);
   A.single_ptiles = route_tiles(kRoutePrefix, h->capacity, A.plpt, sb, A.prefix_on, 0, A.dff_off);
+  A.single_ctiles = route_tiles(kRouteCluster, h->capacity, A.plpt, sb, A.prefix_on, 0, A.dff_off);
   A.single_vtiles = 0;
   A.single_c = h->capacity;
   A.single_k = bins;
@@ -606,11 +702,15 @@ int bp_lb_eval(bp_lb_t *h, const int32_t *sizes, int64_t n, int64_t bins, int64_
   }
   EvalArgs A = plain_args(h, n, bins, kModePlainRagged);
   A.sizes = h->d_items;
-  if (A.single_ptiles + A.single_tiles == 0) return plain_empty(out_bound, out_argmax);
+  if (A.single_ptiles + A.single_tiles + A.single_ctiles == 0)
+    return plain_empty(out_bound, out_argmax);
   if (h->vb2_cap) {
     A.vb2_hi = h->d_vb2hi1;
     BP_CHECK_STATUS(launch_vb2cap(h, kSrcRaggedI32, A, h->d_vb2hi1, h->stream));
   }
+  if (A.single_ctiles > 0)
+    BP_CHECK_STATUS(launch_cluster(kSrcRaggedI32, (unsigned)A.single_ctiles,
+                                   cluster_smem(kSrcRaggedI32, 0), h->stream, A));
   if (A.single_ptiles > 0)
     BP_CHECK_STATUS(launch_prefix(kSrcRaggedI32, (unsigned)A.single_ptiles,
                                   prefix_smem(kSrcRaggedI32, 0), h->stream, A));
@@ -636,11 +736,15 @@ int bp_lb_eval_node(bp_lb_t *h, const int32_t *w, const int32_t *assign, int64_t
   A.base_sizes = h->d_items;
   A.assign = h->d_assign;
   A.max_bins = (int32_t)bins;
-  if (A.single_ptiles + A.single_tiles == 0) return plain_empty(out_bound, out_argmax);
+  if (A.single_ptiles + A.single_tiles + A.single_ctiles == 0)
+    return plain_empty(out_bound, out_argmax);
   if (h->vb2_cap) {
     A.vb2_hi = h->d_vb2hi1;
     BP_CHECK_STATUS(launch_vb2cap(h, kSrcNodes, A, h->d_vb2hi1, h->stream));
   }
+  if (A.single_ctiles > 0)
+    BP_CHECK_STATUS(launch_cluster(kSrcNodes, (unsigned)A.single_ctiles,
+                                   cluster_smem(kSrcNodes, bins), h->stream, A));
   if (A.single_ptiles > 0)
     BP_CHECK_STATUS(launch_prefix(kSrcNodes, (unsigned)A.single_ptiles, prefix_smem(kSrcNodes, bins),
                                   h->stream, A));
@@ -891,6 +995,15 @@ int bp_lb_get_pruning(bp_lb_t *h) {
   return h->prune;
 }
 
+int bp_lb_set_cluster_tables(bp_lb_t *h, int32_t on) {
+  if (!h) return BP_EINVAL;
+  if (on != 0 && on != 1) return BP_ERANGE;
+  h->cluster_on = on;
+  return BP_OK;
+}
+
+int bp_lb_get_cluster_tables(bp_lb_t *h) { return h ? h->cluster_on : -1; }
+
 int bp_lb_set_overlap(bp_lb_t *h, int32_t prefix_ctas_per_sm) {
   if (!h) return BP_EINVAL;
   if (prefix_ctas_per_sm < 0 || prefix_ctas_per_sm > 8) return BP_ERANGE;
@@ -933,27 +1046,42 @@ int bp_lb_kernel_work(bp_lb_t *h, int64_t *out4) {
   return BP_OK;
 }
 
-int bp_lb_kernel_times(bp_lb_t *h, double *ms_prefix, double *ms_vb2, double *ms_direct,
-                       int64_t *calls) {
+int bp_lb_kernel_times4(bp_lb_t *h, double *out_ms4, int64_t *calls) {
   if (!h) return BP_EINVAL;
-  double p = 0.0, v = 0.0, d = 0.0;
+  double p = 0.0, v = 0.0, d = 0.0, cl = 0.0;
   for (const auto &ev : h->ev_pending) {
     BP_CHECK(cudaEventSynchronize(ev[3]));
     BP_CHECK(cudaEventSynchronize(ev[5]));
-    float a = 0.f, b = 0.f, e = 0.f;
+    float a = 0.f, b = 0.f, e = 0.f, f = 0.f;
     BP_CHECK(cudaEventElapsedTime(&a, ev[0], ev[1]));
     BP_CHECK(cudaEventElapsedTime(&b, ev[2], ev[3]));
     BP_CHECK(cudaEventElapsedTime(&e, ev[4], ev[5]));
+    BP_CHECK(cudaEventElapsedTime(&f, ev[6], ev[7]));
     p += a;
     v += b;
     d += e;
+    cl += f;
   }
-  if (ms_prefix) *ms_prefix = p;
-  if (ms_vb2) *ms_vb2 = v;
-  if (ms_direct) *ms_direct = d;
+  if (out_ms4) {
+    out_ms4[0] = cl;
+    out_ms4[1] = p;
+    out_ms4[2] = v;
+    out_ms4[3] = d;
+  }
   if (calls) *calls = (int64_t)h->ev_pending.size();
   h->ev_pending.clear();
   h->ev_next = 0;
+  return BP_OK;
+}
+
+int bp_lb_kernel_times(bp_lb_t *h, double *ms_prefix, double *ms_vb2, double *ms_direct,
+                       int64_t *calls) {
+  double ms[4];
+  const int st = bp_lb_kernel_times4(h, ms, calls);
+  if (st != BP_OK) return st;
+  if (ms_prefix) *ms_prefix = ms[1];
+  if (ms_vb2) *ms_vb2 = ms[2];
+  if (ms_direct) *ms_direct = ms[3];
   return BP_OK;
 }
 

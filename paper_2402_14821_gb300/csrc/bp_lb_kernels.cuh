@@ -108,6 +108,12 @@ struct EvalArgs {
   int32_t windowed;
   uint32_t g_lo, g_hi;
   int64_t *out_key;
+  // The cluster kernel's unit table (tables in a cluster's distributed shared
+  // memory, prefix_home 3): [B+1] exclusive prefix of units per instance, or
+  // nullptr (single instance: single_ctiles units), and its work counter.
+  const int64_t *ctile_start;
+  int64_t single_ctiles;
+  unsigned long long *cwork;
 };
 
 // Shared-memory budget of the prefix-count tables (bytes; 48 KB lets four
@@ -134,25 +140,48 @@ BPLB_HD int64_t prefix_table_bytes(int d, int64_t c) {
 }
 
 // prefix_on bits: the prefix-count kernel is on (its tables in shared
-// memory where they fit), and its tables may also live in a global-memory
+// memory where they fit), its tables may also live in a global-memory
 // scratch of kGlobalTableInts int32 per CTA (L2-resident; for capacities up
-// to about 2^20).
+// to about 2^20), and tables too large for one CTA but within
+// kClusterTableInts may be spread over the shared memory of a thread-block
+// cluster of kClusterCtas CTAs (the cluster kernel), kSliceInts int32 each:
+// entry x lives in CTA x >> kSliceShift of the cluster.
 constexpr int32_t kPrefixShared = 1;
 constexpr int32_t kPrefixGlobal = 2;
+constexpr int32_t kPrefixCluster = 4;
 constexpr int64_t kGlobalTableInts = int64_t(1) << 20;
+constexpr int kClusterCtas = 8;
+constexpr int kSliceShift = 14;
+constexpr int64_t kSliceInts = int64_t(1) << kSliceShift;
+constexpr int64_t kClusterTableInts = kClusterCtas * kSliceInts;
 
-// Where the prefix-count kernel keeps the tables of DFF d of an instance with
-// capacity c whose reduced sizes sum to at most sum_bound: 0 nowhere (the
-// direct kernels evaluate it), 1 shared memory, 2 the global scratch.  The
+// Where the prefix-count tables of DFF d of an instance with capacity c
+// whose reduced sizes sum to at most sum_bound live: 0 nowhere (the direct
+// kernels evaluate it), 1 one CTA's shared memory, 2 the global scratch (both
+// the prefix kernel), 3 a cluster's shared memory (the cluster kernel).  The
 // sums must fit 32 bits; FS1's count sum, at most 101 sum_bound / c, too.
+BPLB_HD int table_home(int64_t bytes, int32_t on) {
+  if (bytes <= kPrefixSmemBytes) return 1;
+  if ((on & kPrefixCluster) && bytes <= 4 * kClusterTableInts) return 3;
+  if ((on & kPrefixGlobal) && bytes <= 4 * kGlobalTableInts) return 2;
+  return 0;
+}
+
 BPLB_HD int prefix_home(int d, int64_t c, int64_t sum_bound, int32_t on) {
   if (!(on & kPrefixShared) || sum_bound >= (int64_t(1) << 31)) return 0;
   if (d == kFS1 && sum_bound >= (int64_t(1) << 25) * c) return 0;  // sum_bound / c >= 2^25
   const int64_t bytes = prefix_table_bytes(d, c);
   if (bytes == 0) return 0;
-  if (bytes <= kPrefixSmemBytes) return 1;
-  if ((on & kPrefixGlobal) && bytes <= 4 * kGlobalTableInts) return 2;
-  return 0;
+  return table_home(bytes, on);
+}
+
+// The routing functions (prefix_home, prefix_u_merged and what calls them)
+// depend on an instance's sum bound only through these three thresholds, so
+// that instances of one capacity and class route alike (the routing caches
+// of the planning and prefix kernels key on it).
+BPLB_HD int route_class(int64_t c, int64_t sum_bound) {
+  return (sum_bound < (int64_t(1) << 31) ? 1 : 0) | (sum_bound < (int64_t(1) << 25) * c ? 2 : 0) |
+         (sum_bound < (int64_t(1) << 15) * c ? 4 : 0);
 }
 
 BPLB_HD bool prefix_handles(int d, int64_t c, int64_t sum_bound, int32_t on) {
@@ -170,7 +199,9 @@ constexpr int64_t kVb2TilesPerSm = 24;
 // Which kernel evaluates DFF d of an instance: the prefix-count kernel
 // (prefix_handles), the VB2 kernel (VB2 on its fixed-point path), or the
 // generic direct kernel; none when the DFF is left out (dff_off).
-enum : int { kRouteNone = -1, kRouteDirect = 0, kRoutePrefix = 1, kRouteVb2 = 2 };
+// kRouteCluster only selects what route_tiles counts: the prefix-routed
+// units whose tables are a cluster's (prefix_home 3).
+enum : int { kRouteNone = -1, kRouteDirect = 0, kRoutePrefix = 1, kRouteVb2 = 2, kRouteCluster = 3 };
 
 BPLB_HD int dff_kernel(int d, int64_t c, int64_t sum_bound, int32_t prefix_on, int32_t vb2_on,
                        uint32_t dff_off) {
@@ -180,13 +211,10 @@ BPLB_HD int dff_kernel(int d, int64_t c, int64_t sum_bound, int32_t prefix_on, i
   return kRouteDirect;
 }
 
-// Where the u group's tables (E plus packed counts, 8 bytes per u) live: 1
-// shared memory, 2 the global scratch, 0 neither.
+// Where the u group's tables (E plus packed counts, 8 bytes per u) live
+// (prefix_home's numbering).
 BPLB_HD int prefix_u_home(int64_t c, int32_t on) {
-  const int64_t bytes = 8 * ((c - 1) / 2 + 2);
-  if (bytes <= kPrefixSmemBytes) return 1;
-  if ((on & kPrefixGlobal) && bytes <= 4 * kGlobalTableInts) return 2;
-  return 0;
+  return table_home(8 * ((c - 1) / 2 + 2), on);
 }
 
 // MT, RAD2 and CCM1 share one prefix-kernel tile per instance (the u group:
@@ -226,30 +254,38 @@ BPLB_HD bool prefix_w_merged(int64_t c, int64_t sum_bound, int32_t prefix_on, in
          dff_kernel(kBJ1, c, sum_bound, prefix_on, vb2_on, dff_off) == kRoutePrefix;
 }
 
-// Prefix-kernel tiles of DFF d (routed there): one when its tables are in the
-// global scratch (built once per tile, so the tile takes the whole range),
-// else ceil(count / lpt).
+// Tiles of DFF d routed to the prefix-count tables: one when its tables are in
+// the global scratch or a cluster's shared memory (built once per tile, so
+// the tile takes the whole range), else ceil(count / lpt).
 BPLB_HD int64_t prefix_dff_tiles(int d, int64_t c, int64_t sum_bound, int32_t on, int64_t lpt) {
   const int64_t pc = param_count(d, c);
   if (pc == 0) return 0;
-  return prefix_home(d, c, sum_bound, on) == 2 ? 1 : tile_count(pc, lpt);
+  return prefix_home(d, c, sum_bound, on) >= 2 ? 1 : tile_count(pc, lpt);
 }
 
 // Tiles of one kernel for an instance: lpt parameters each, DFFs in paper
-// order; on the prefix kernel the u group, when merged, is one tile, and FS1
-// rides on BJ1's first tile when prefix_w_merged.
+// order; with the prefix-count tables the u group, when merged, is one tile,
+// and FS1 rides on BJ1's first tile when prefix_w_merged.  kRoutePrefix
+// counts the prefix kernel's tiles (tables in a CTA's shared memory or the
+// global scratch), kRouteCluster the cluster kernel's (prefix_home 3).
 BPLB_HD int64_t route_tiles(int route, int64_t c, int64_t lpt, int64_t sum_bound, int32_t prefix_on,
                             int32_t vb2_on, uint32_t dff_off) {
-  const bool pre = route == kRoutePrefix;
+  const bool cl = route == kRouteCluster;
+  const bool pre = route == kRoutePrefix || cl;
   const bool merged = pre && prefix_u_merged(c, sum_bound, prefix_on, vb2_on, dff_off, lpt);
   const bool wmerged = pre && prefix_w_merged(c, sum_bound, prefix_on, vb2_on, dff_off);
-  int64_t t = merged ? 1 : 0;
+  int64_t t = (merged && (prefix_u_home(c, prefix_on) == 3) == cl) ? 1 : 0;
   for (int d = 0; d < kNumDff; ++d) {
     if (merged && (d == kMT || d == kRAD2 || d == kCCM1)) continue;
     if (wmerged && d == kFS1) continue;
-    if (dff_kernel(d, c, sum_bound, prefix_on, vb2_on, dff_off) != route) continue;
-    t += route == kRoutePrefix ? prefix_dff_tiles(d, c, sum_bound, prefix_on, lpt)
-                               : tile_count(param_count(d, c), lpt);
+    if (dff_kernel(d, c, sum_bound, prefix_on, vb2_on, dff_off) != (pre ? kRoutePrefix : route))
+      continue;
+    if (!pre) {
+      t += tile_count(param_count(d, c), lpt);
+    } else if ((prefix_home(d, c, sum_bound, prefix_on) == 3) == cl) {
+      t += cl ? (param_count(d, c) > 0 ? 1 : 0)
+              : prefix_dff_tiles(d, c, sum_bound, prefix_on, lpt);
+    }
   }
   return t;
 }
@@ -279,15 +315,17 @@ __device__ __forceinline__ bool slot_decided(const unsigned long long *slot, int
 // start on x's 16-byte boundaries (the first and last groups may be partial:
 // their entries inside [0, n) are read one at a time); y, when given, is read
 // alongside when it has the same 16-byte phase as x, else every entry is read
-// on its own.  f has one call site, so a large f is compiled once.
-template <int NT, bool ONE, class F>
-__device__ __forceinline__ void for_items_vec(const int32_t *x, const int32_t *y, int64_t n, F f) {
+// on its own.  f has one call site, so a large f is compiled once.  With
+// PARTS > 1 the groups are dealt over PARTS CTAs, this one being `part`.
+template <int NT, bool ONE, int PARTS = 1, class F>
+__device__ __forceinline__ void for_items_vec(const int32_t *x, const int32_t *y, int64_t n, F f,
+                                              uint32_t part = 0u) {
   const int64_t px = (int64_t)((reinterpret_cast<uintptr_t>(x) >> 2) & 3u);
   const int64_t py = ONE ? px : (int64_t)((reinterpret_cast<uintptr_t>(y) >> 2) & 3u);
   const bool vec = px == py;
   const int64_t ph = vec ? px : 0;  // x's offset (entries) within its 16-byte line
   const int64_t ngroups = (n + ph + 3) >> 2;
-  for (int64_t g = threadIdx.x; g < ngroups; g += NT) {
+  for (int64_t g = (int64_t)part * NT + threadIdx.x; g < ngroups; g += (int64_t)PARTS * NT) {
     const int64_t base = 4 * g - ph;  // entry index of the group's first value
     int4 vx = make_int4(0, 0, 0, 0), vy = vx;
     if (vec && base >= 0 && base + 3 < n) {
@@ -436,19 +474,20 @@ __device__ __forceinline__ int64_t plan_scan(int64_t v, int64_t *s_warp, int64_t
 
 // plan_kernel: one block.  Validates every instance and writes the tile
 // tables of the direct kernel (tile_start[0..B]), of the prefix kernel
-// (ptile_start[0..B]) and of the VB2 kernel (vtile_start[0..B]); an invalid
-// instance gets no tiles and an error result.  Clears keys/done and resets
+// (ptile_start[0..B]), of the cluster kernel (ctile_start[0..B]) and of the
+// VB2 kernel (vtile_start[0..B]); an invalid instance gets no tiles and an
+// error result.  Clears keys/done and resets
 // the work counters.  Each thread takes kPlanPerThread consecutive instances
 // (their tile counts summed locally, so that one block scan per quantity
 // covers 1024 kPlanPerThread instances: the scans' barriers are most of the
 // kernel's time) and keeps its last instance's routing, reused while the
-// capacity and stream length repeat (every node of a search-node batch).
+// capacity and route class repeat (every node of a search-node batch).
 constexpr int kPlanPerThread = 4;
 
 template <int MODE>
 __global__ void __launch_bounds__(1024)
     plan_kernel(EvalArgs A, int64_t lpt, int64_t *tile_start, int64_t *ptile_start,
-                int64_t *vtile_start) {
+                int64_t *vtile_start, int64_t *ctile_start) {
   constexpr int K = kPlanPerThread;
   __shared__ int64_t s_warp[32];
   __shared__ int64_t s_carry[3];
@@ -456,13 +495,20 @@ __global__ void __launch_bounds__(1024)
     s_carry[0] = s_carry[1] = s_carry[2] = 0;
     *A.work = 0ull;
     if (A.pwork) *A.pwork = 0ull;
+    if (A.cwork) *A.cwork = 0ull;
     if (A.vwork) *A.vwork = 0ull;
   }
   __syncthreads();
   // one pass over the instances: validate, count the direct and prefix tiles
-  // and VB2's parameters (kept in vtile_start[b] until the VB2 tile length is
+  // and VB2's parameters (kept in vtile_start[b], low 32 bits, with the
+  // instance's other tiles in the high 32, until the VB2 tile length is
   // known: VB2's parameters of the whole batch over the target tile count)
-  int64_t rc_c = -1, rc_L = -1, rc_t = 0, rc_p = 0, rc_v = 0;  // routing of (rc_c, rc_L)
+  // routing of capacity rc_c and route class rc_k; rc_p packs the prefix
+  // kernel's tiles (low 32 bits) and the cluster kernel's units (high),
+  // scanned together: a handful of each per instance, so neither field of a
+  // batch's sum reaches 2^32
+  int64_t rc_c = -1, rc_t = 0, rc_p = 0, rc_v = 0;
+  int rc_k = -1;
   for (int64_t b0 = 0; b0 < A.B; b0 += (int64_t)blockDim.x * K) {
     const int64_t bt = b0 + (int64_t)threadIdx.x * K;  // this thread's first instance
     int64_t tiles[K], ptiles[K], pvs[K];
@@ -473,7 +519,6 @@ __global__ void __launch_bounds__(1024)
       tiles[j] = ptiles[j] = pvs[j] = 0;
       if (b < A.B) {
         A.keys[b] = 0ull;
-        A.done[b] = 0u;
         if (A.isums) A.isums[8 * b + 7] = 0;
         bool ok;
         int64_t c, L;
@@ -494,15 +539,19 @@ __global__ void __launch_bounds__(1024)
           ok = c >= 1 && c <= kMaxCapacity && L >= 0 && L <= kMaxItems && A.bins[b] >= 0;
         }
         if (ok) {
-          if (c != rc_c || L != rc_L) {
+          const int rk = route_class(c, L * c);
+          if (c != rc_c || rk != rc_k) {
             rc_t = route_tiles(kRouteDirect, c, lpt, L * c, A.prefix_on, A.vb2_on, A.dff_off);
             rc_p = route_tiles(kRoutePrefix, c, A.plpt, L * c, A.prefix_on, A.vb2_on, A.dff_off);
+            if (ctile_start != nullptr && (A.prefix_on & kPrefixCluster))
+              rc_p += route_tiles(kRouteCluster, c, A.plpt, L * c, A.prefix_on, A.vb2_on,
+                                  A.dff_off) << 32;
             rc_v = (vtile_start != nullptr &&
                     dff_kernel(kVB2, c, L * c, A.prefix_on, A.vb2_on, A.dff_off) == kRouteVb2)
                        ? param_count(kVB2, c)
                        : 0;
             rc_c = c;
-            rc_L = L;
+            rc_k = rk;
           }
           tiles[j] = rc_t;
           ptiles[j] = rc_p;
@@ -525,8 +574,14 @@ __global__ void __launch_bounds__(1024)
       const int64_t b = bt + j;
       if (b < A.B) {
         tile_start[b] = e0;
-        if (ptile_start) ptile_start[b] = e1;
-        if (vtile_start) vtile_start[b] = pvs[j];
+        if (ptile_start) ptile_start[b] = e1 & 0xFFFFFFFFll;
+        if (ctile_start) ctile_start[b] = e1 >> 32;
+        // the finished-tile counter starts at minus the instance's tiles
+        // (instance_tiles); with a VB2 table, completed below once VB2's tile
+        // length is known
+        const int64_t tot = tiles[j] + (ptiles[j] & 0xFFFFFFFFll) + (ptiles[j] >> 32);
+        if (vtile_start) vtile_start[b] = pvs[j] | (tot << 32);
+        else A.done[b] = 0u - (uint32_t)tot;
       }
       e0 += tiles[j];
       e1 += ptiles[j];
@@ -551,23 +606,30 @@ __global__ void __launch_bounds__(1024)
     for (int64_t b0 = 0; b0 < A.B; b0 += (int64_t)blockDim.x * K) {
       const int64_t bt = b0 + (int64_t)threadIdx.x * K;
       int64_t vt[K];
+      uint32_t tot[K];
       int64_t sv = 0;
 #pragma unroll
       for (int j = 0; j < K; ++j) {
-        vt[j] = bt + j < A.B ? tile_count(vtile_start[bt + j], vlpt) : 0;
+        const int64_t pv = bt + j < A.B ? vtile_start[bt + j] : 0;
+        vt[j] = tile_count(pv & 0xFFFFFFFFll, vlpt);
+        tot[j] = (uint32_t)(pv >> 32);
         sv += vt[j];
       }
       int64_t e2 = plan_scan(sv, s_warp, &s_carry[2]);
 #pragma unroll
       for (int j = 0; j < K; ++j) {
-        if (bt + j < A.B) vtile_start[bt + j] = e2;
+        if (bt + j < A.B) {
+          vtile_start[bt + j] = e2;
+          A.done[bt + j] = 0u - (tot[j] + (uint32_t)vt[j]);
+        }
         e2 += vt[j];
       }
     }
   }
   if (threadIdx.x == 0) {
     tile_start[A.B] = s_carry[0];
-    if (ptile_start) ptile_start[A.B] = s_carry[1];
+    if (ptile_start) ptile_start[A.B] = s_carry[1] & 0xFFFFFFFFll;
+    if (ctile_start) ctile_start[A.B] = s_carry[1] >> 32;
     if (vtile_start) vtile_start[A.B] = s_carry[2];
   }
 }
@@ -623,13 +685,12 @@ __device__ __forceinline__ int64_t sum_bound(const InstView &I) {
   return stream_len<MODE>(I) * I.c;
 }
 
-// Tiles of instance b over all kernels (the finished-tile ticket target).
+// The finished-tile ticket target of instance b: a single instance's tiles
+// over all kernels; 0 in a batch, whose plan kernel presets each instance's
+// counter to minus its tiles, so that the last tile's ticket is 2^32 - 1.
 __device__ __forceinline__ int64_t instance_tiles(const EvalArgs &A, int64_t b) {
-  if (!A.tile_start) return A.single_tiles + A.single_ptiles + A.single_vtiles;
-  int64_t nt = A.tile_start[b + 1] - A.tile_start[b];
-  if (A.ptile_start) nt += A.ptile_start[b + 1] - A.ptile_start[b];
-  if (A.vtile_start) nt += A.vtile_start[b + 1] - A.vtile_start[b];
-  return nt;
+  if (!A.tile_start) return A.single_tiles + A.single_ptiles + A.single_vtiles + A.single_ctiles;
+  return 0;
 }
 
 // Block max of the threads' keys, one atomicMax into the instance's slot, and
@@ -653,7 +714,7 @@ __device__ void fold_and_finalize(const EvalArgs &A, int64_t b, unsigned long lo
     if (m && !err) atomicMax(&A.keys[b], m);
     __threadfence();
     const unsigned int ticket = atomicAdd(&A.done[b], 1u);
-    if ((int64_t)ticket == ntiles - 1) {
+    if (ntiles > 0 ? (int64_t)ticket == ntiles - 1 : ticket == 0xFFFFFFFFu) {
       __threadfence();
       const unsigned long long key = atomicExch(&A.keys[b], 0ull);
       A.done[b] = 0u;
@@ -872,15 +933,19 @@ __device__ __forceinline__ bool vb2_range_may_exceed(int64_t l0, int64_t l1, int
 }
 
 // Whether a VB2 tile [l0, l1] of instance b can be skipped before anything is
-// staged, from the instance's class counts and sums that the prefix kernel
-// published (EvalArgs::isums, flag 1) and the instance's cut: k in verdict
-// mode, else from its best key so far (vb2_cut).  Thread 0 only.
+// staged: VB2 was evaluated on the instance's u-group table (the prefix or
+// cluster kernel published flag 2), or the instance's class counts and sums
+// that they published (EvalArgs::isums, flag 1) and its cut -- k in verdict
+// mode, else from its best key so far (vb2_cut) -- show that no parameter of
+// the tile can change the result.  Thread 0 only.
 __device__ __forceinline__ bool vb2_tile_pruned(const EvalArgs &A, int64_t b, int64_t c, int64_t k,
                                                 int64_t L, int64_t l0, int64_t l1,
                                                 uint32_t gbase) {
   if (A.isums == nullptr || !(A.verdict || A.prune) || l1 < l0) return false;
   const volatile long long *is = A.isums + 8 * b;
-  if (is[7] != 1) return false;
+  const long long flag = is[7];
+  if (flag == 2) return true;
+  if (flag != 1) return false;
   __threadfence();
   const int64_t cut = A.verdict ? k : (int64_t)vb2_cut(&A.keys[b], gbase);
   if (cut < 0) return false;

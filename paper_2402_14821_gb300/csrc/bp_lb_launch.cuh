@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include "bp_lb_kernels.cuh"
+#include "bp_lb_cluster.cuh"
 #include "bp_lb_prefix.cuh"
 #include "bp_lb_vb2.cuh"
 
@@ -39,7 +40,7 @@ using EvalFn = void (*)(EvalArgs);
 
 // Host stubs of the instantiated kernels, one table per input mode; shape -1
 // is the prefix-count kernel of that mode, shape -2 - s the VB2 kernel with
-// shape s's VT.
+// shape s's VT, kClusterShape the cluster kernel.
 EvalFn eval_fn_ragged_i32(int shape);
 EvalFn eval_fn_ragged_i64(int shape);
 EvalFn eval_fn_nodes(int shape);
@@ -52,7 +53,10 @@ inline EvalFn eval_fn(int shape, int mode) {
   }
 }
 
+constexpr int kClusterShape = -1000;
+
 inline EvalFn prefix_fn(int mode) { return eval_fn(-1, mode); }
+inline EvalFn cluster_fn(int mode) { return eval_fn(kClusterShape, mode); }
 inline EvalFn vb2_fn(int shape, int mode) { return eval_fn(-2 - shape, mode); }
 
 }  // namespace bplb
@@ -61,6 +65,7 @@ inline EvalFn vb2_fn(int shape, int mode) { return eval_fn(-2 - shape, mode); }
 #define BPLB_INSTANTIATE_MODE(NAME, MODE)                                          \
   namespace bplb {                                                                 \
   EvalFn NAME(int shape) {                                                         \
+    if (shape == kClusterShape) return cluster_kernel<MODE>;                       \
     if (shape <= -2) {                                                             \
       switch (kShapes[-2 - shape].vt) {                                            \
         case 2: return vb2_kernel<MODE, 2>;                                        \

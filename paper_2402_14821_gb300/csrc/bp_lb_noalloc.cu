@@ -139,7 +139,7 @@ extern "C" int bp_lb_eval_batch_noalloc(int32_t B, const int64_t *d_offsets,
   // work counter of the B instances before the evaluation kernel runs.
   plan_kernel<kSrcRaggedI32><<<1, 1024, 0, s>>>(A, shape_lpt(shape),
                                                 reinterpret_cast<int64_t *>(scratch + kOffTiles),
-                                                nullptr, nullptr);
+                                                nullptr, nullptr, nullptr);
   if (cudaGetLastError() != cudaSuccess) return BP_ECUDA;
   void *args[] = {&A};
   if (cudaLaunchKernel(fn, dim3((unsigned)(nd.sms * nd.occ)), dim3(kShapes[shape].nt), args,

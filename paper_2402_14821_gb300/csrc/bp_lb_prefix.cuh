@@ -77,10 +77,12 @@ struct PrefixShared {
   int dec_d, dec_home, dec_fs1, dec_umask;
   long long dec_lam0, dec_lam_end;
   // thread 0's routing of the last decoded instance, reused while the next
-  // tiles' instances have the same capacity and stream bound (every node of a
-  // search-node batch does): the u group merged, FS1 with BJ1, the u group's
-  // members and table home, and per DFF its prefix tiles and table home
-  long long rc_c, rc_sb;
+  // tiles' instances have the same capacity and route class (route_class;
+  // every node of a search-node batch does): the u group merged, FS1 with
+  // BJ1, the u group's members and table home, and per DFF its prefix tiles
+  // and table home
+  long long rc_c;
+  int rc_k;
   int rc_merged, rc_wmerged, rc_umask, rc_uhome;
   int rc_nt[kNumDff], rc_home[kNumDff];
   int vb2_mode;  // vb2_table_plan of this u-group tile, with its cut and last l
@@ -110,8 +112,11 @@ __device__ __forceinline__ uint32_t block_sum_after(uint32_t v, uint32_t *wtot) 
 // [t per, t per + per) with per odd (consecutive lanes then hit distinct
 // banks); the values entering each segment from above come from block sums
 // of the segment totals (TWICE: also of the once-scanned segments' sums).
+// n_in, nn_in: what enters a[n - 1] from entries past n (a table scanned in
+// parts, the cluster kernel): their sum, and (TWICE) their once-scanned sum.
 template <bool TWICE>
-__device__ void suffix_scan(int32_t *a, int n, PrefixShared &S) {
+__device__ void suffix_scan(int32_t *a, int n, PrefixShared &S, uint32_t n_in = 0u,
+                            uint32_t nn_in = 0u) {
   const int per = ((n + kPrefixNT - 1) / kPrefixNT) | 1;
   const int s0 = min(n, (int)threadIdx.x * per), s1 = min(n, s0 + per);
   uint32_t h = 0, m = 0;
@@ -120,9 +125,9 @@ __device__ void suffix_scan(int32_t *a, int n, PrefixShared &S) {
     h += v;
     if (TWICE) m += v * (uint32_t)(i - s0 + 1);  // this segment's part of the twice-scanned a[s0]
   }
-  const uint32_t n_after = block_sum_after(h, S.wtot[0]);
+  const uint32_t n_after = block_sum_after(h, S.wtot[0]) + n_in;
   uint32_t nn_after = 0;
-  if (TWICE) nn_after = block_sum_after(m + (uint32_t)(s1 - s0) * n_after, S.wtot[1]);
+  if (TWICE) nn_after = block_sum_after(m + (uint32_t)(s1 - s0) * n_after, S.wtot[1]) + nn_in;
   uint32_t nr = n_after, nnr = nn_after;
   for (int i = s1 - 1; i >= s0; --i) {
     nr += (uint32_t)a[i];
@@ -140,13 +145,15 @@ __device__ void suffix_scan(int32_t *a, int n, PrefixShared &S) {
 // u, high 16 bits: big items at u), each word then rewritten as
 // (N'(x) mod 2^16) | (Ns(x) << 16) with N' = Ns - Nb.  Every lane's total is
 // at most the stream length (< 2^15 on this path), so the packed sums never
-// carry from one lane into the other.
-__device__ __forceinline__ void packed_count_scan(uint32_t *a, int n, PrefixShared &S) {
+// carry from one lane into the other.  n_in: the packed sum of the entries
+// past n (a table scanned in parts).
+__device__ __forceinline__ void packed_count_scan(uint32_t *a, int n, PrefixShared &S,
+                                                  uint32_t n_in = 0u) {
   const int per = ((n + kPrefixNT - 1) / kPrefixNT) | 1;
   const int s0 = min(n, (int)threadIdx.x * per), s1 = min(n, s0 + per);
   uint32_t h = 0;
   for (int i = s0; i < s1; ++i) h += a[i];
-  uint32_t run = block_sum_after(h, S.wtot[0]);
+  uint32_t run = block_sum_after(h, S.wtot[0]) + n_in;
   for (int i = s1 - 1; i >= s0; --i) {
     run += a[i];
     const uint32_t ns = run & 0xFFFFu, nb = run >> 16;
@@ -155,24 +162,174 @@ __device__ __forceinline__ void packed_count_scan(uint32_t *a, int n, PrefixShar
   __syncthreads();
 }
 
+// ---- distributed shared memory of a thread-block cluster ---------------------
+// Addresses are 32-bit shared-window addresses: smem_addr of a variable of
+// this CTA, cluster_map of that to the same variable in CTA `rank` of the
+// cluster (mapa); ld/st/red .shared::cluster then reach any CTA's shared
+// memory.  cluster_barrier: every thread of every CTA of the cluster arrives
+// (release) and waits (acquire), so that writes before it, local or remote,
+// are seen by all reads after it.
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint32_t cluster_map(uint32_t a, uint32_t rank) {
+  uint32_t r;
+  asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ int32_t dsm_ld(uint32_t a) {
+  int32_t v;
+  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ int32_t dsm_ld_s16(uint32_t a) {
+  int32_t v;
+  asm volatile("ld.shared::cluster.s16 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ int4 dsm_ld4(uint32_t a) {
+  int4 v;
+  asm volatile("ld.shared::cluster.v4.s32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(a));
+  return v;
+}
+__device__ __forceinline__ unsigned long long dsm_ld64(uint32_t a) {
+  unsigned long long v;
+  asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void dsm_st(uint32_t a, int32_t v) {
+  asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void dsm_st64(uint32_t a, unsigned long long v) {
+  asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+}
+__device__ __forceinline__ void dsm_red_add(uint32_t a, uint32_t v) {
+  asm volatile("red.shared::cluster.add.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void dsm_red_add64(uint32_t a, unsigned long long v) {
+  asm volatile("red.shared::cluster.add.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+}
+__device__ __forceinline__ void dsm_red_or(uint32_t a, uint32_t v) {
+  asm volatile("red.shared::cluster.or.b32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile(
+      "barrier.cluster.arrive.release;\n\t"
+      "barrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// ---- table access and thread teams --------------------------------------------
+// The evaluators below read a table through an accessor: LocalTab, a plain
+// pointer (one CTA's shared memory, or its slice of the global scratch), or
+// ClusterTab, a table spread over the shared memory of the CTAs of a
+// thread-block cluster (the cluster kernel, bp_lb_cluster.cuh).
+// Each gives ld (int32 entry), lo16 (the low 16 bits of an entry,
+// sign-extended), ldu (unsigned entry), ld4 (four entries from an entry x
+// with phase(x) == 0: one 16-byte load), st, and at(o) (the table starting at
+// entry o).  kDeep: the table's loads have a long latency (another CTA's
+// shared memory), so that the lookup loops keep more of them in flight.
+struct LocalTab {
+  static constexpr bool kDeep = false;
+  int32_t *p;
+  __device__ __forceinline__ int32_t ld(uint32_t x) const { return p[x]; }
+  __device__ __forceinline__ int32_t lo16(uint32_t x) const {
+    return (int32_t)reinterpret_cast<const int16_t *>(p)[2u * x];
+  }
+  __device__ __forceinline__ uint32_t ldu(uint32_t x) const {
+    return reinterpret_cast<const uint32_t *>(p)[x];
+  }
+  __device__ __forceinline__ int4 ld4(uint32_t x) const {
+    return *reinterpret_cast<const int4 *>(p + x);
+  }
+  __device__ __forceinline__ void st(uint32_t x, int32_t v) const { p[x] = v; }
+  // word offset of entry x within its 16-byte line
+  __device__ __forceinline__ uint32_t phase(uint32_t x) const {
+    return (uint32_t)(((reinterpret_cast<uintptr_t>(p) >> 2) + x) & 3u);
+  }
+  __device__ __forceinline__ LocalTab at(uint32_t o) const { return LocalTab{p + o}; }
+};
+
+// Entry x of a cluster table lives in CTA x >> kSliceShift of the cluster, at
+// word x & (kSliceInts - 1) of its slice; every CTA's slice starts at the same
+// shared-memory offset sbase (16-byte aligned), so mapa finds it.  off: the
+// cluster-table entry of this table's entry 0.  Every entry the evaluators
+// touch lies below the table's length (at most kClusterTableInts); the CTA
+// index is clamped all the same, so that no access can leave the cluster.
+struct ClusterTab {
+  static constexpr bool kDeep = true;
+  uint32_t sbase, off;
+  __device__ __forceinline__ uint32_t addr(uint32_t x) const {
+    const uint32_t e = off + x;
+    return cluster_map(sbase + ((e & (uint32_t)(kSliceInts - 1)) << 2),
+                       min(e >> kSliceShift, (uint32_t)(kClusterCtas - 1)));
+  }
+  __device__ __forceinline__ int32_t ld(uint32_t x) const { return dsm_ld(addr(x)); }
+  __device__ __forceinline__ int32_t lo16(uint32_t x) const { return dsm_ld_s16(addr(x)); }
+  __device__ __forceinline__ uint32_t ldu(uint32_t x) const { return (uint32_t)dsm_ld(addr(x)); }
+  __device__ __forceinline__ int4 ld4(uint32_t x) const { return dsm_ld4(addr(x)); }
+  __device__ __forceinline__ void st(uint32_t x, int32_t v) const { dsm_st(addr(x), v); }
+  __device__ __forceinline__ void add(uint32_t x, int32_t v) const {
+    dsm_red_add(addr(x), (uint32_t)v);
+  }
+  __device__ __forceinline__ uint32_t phase(uint32_t x) const { return (off + x) & 3u; }
+  __device__ __forceinline__ ClusterTab at(uint32_t o) const { return ClusterTab{sbase, off + o}; }
+};
+
+// The threads that share one table's parameters: PARTS CTAs of kPrefixNT
+// threads (one CTA, or the CTAs of a cluster), this CTA being number part.
+// Loops deal parameters over tid() < kThreads (warps over warp() < kWarps)
+// exactly as one CTA's loops deal them over threadIdx.x; sync() is the
+// team's barrier.
+template <int PARTS>
+struct Team {
+  static constexpr uint32_t kParts = PARTS;
+  static constexpr uint32_t kThreads = PARTS * kPrefixNT;
+  static constexpr uint32_t kWarps = PARTS * kPrefixWarps;
+  uint32_t part;
+  __device__ __forceinline__ uint32_t tid() const { return part * kPrefixNT + threadIdx.x; }
+  __device__ __forceinline__ uint32_t warp() const {
+    return part * kPrefixWarps + (threadIdx.x >> 5);
+  }
+  __device__ __forceinline__ void sync() const {
+    if constexpr (PARTS == 1) __syncthreads();
+    else cluster_barrier();
+  }
+};
+using CtaTeam = Team<1>;
+
 // N' at x: an int32 table (CCM1's own tile) or the low 16 bits of a packed
 // count word (the u-group tile, packed_count_scan).
-template <bool PACKED>
-__device__ __forceinline__ int32_t np_at(const int32_t *T, uint32_t x) {
-  return PACKED ? (int32_t)reinterpret_cast<const int16_t *>(T)[2u * x] : T[x];
+template <bool PACKED, class Tab>
+__device__ __forceinline__ int32_t np_at(const Tab &T, uint32_t x) {
+  return PACKED ? T.lo16(x) : T.ld(x);
 }
 
 // Strided lookup blocks b0, b0 + bs, ... of one parameter (D = CCM1 or BJ1):
 // block b is the multiple x = (b + 1) l <= X, its term N'(x) (CCM1, X = U) or
 // D(x) at entry 1 + x (BJ1, X = c).  Unrolled by two with explicit bounds (no
 // trip-count division).
-template <int D, bool PACKED>
-__device__ __forceinline__ uint32_t block_terms(const int32_t *T, uint32_t X, uint32_t l,
+template <int D, bool PACKED, class Tab>
+__device__ __forceinline__ uint32_t block_terms(const Tab &T, uint32_t X, uint32_t l,
                                                 uint32_t b0, uint32_t bs) {
   constexpr uint32_t OFF = (D == kBJ1) ? 1u : 0u;
   const uint32_t step = bs * l;
   uint32_t acc = 0;
   uint32_t x = (b0 + 1u) * l;
+  if constexpr (Tab::kDeep) {  // eight terms in flight (x + 7 step <= X < 2^21, no wrap)
+    for (; x + 7u * step <= X; x += 8u * step) {
+      uint32_t s8 = 0;
+#pragma unroll
+      for (uint32_t e = 0; e < 8u; ++e) s8 += (uint32_t)np_at<PACKED>(T, x + e * step + OFF);
+      acc += s8;
+    }
+  }
   for (; x + step <= X; x += 2u * step)
     acc += (uint32_t)np_at<PACKED>(T, x + OFF) + (uint32_t)np_at<PACKED>(T, x + step + OFF);
   if (x <= X) acc += (uint32_t)np_at<PACKED>(T, x + OFF);
@@ -181,8 +338,8 @@ __device__ __forceinline__ uint32_t block_terms(const int32_t *T, uint32_t X, ui
 
 // Sum of the terms at the first m multiples of l: N'(i l) (CCM1) or D(i l)
 // at entry 1 + i l (BJ1), i = 1 .. m; unrolled by four.
-template <int D, bool PACKED>
-__device__ __forceinline__ uint32_t harmonic_sum(const int32_t *T, uint32_t l, uint32_t m) {
+template <int D, bool PACKED, class Tab>
+__device__ __forceinline__ uint32_t harmonic_sum(const Tab &T, uint32_t l, uint32_t m) {
   constexpr uint32_t OFF = (D == kBJ1) ? 1u : 0u;
   const uint32_t l2 = 2u * l;
   if (m <= 3u) {
@@ -192,6 +349,14 @@ __device__ __forceinline__ uint32_t harmonic_sum(const int32_t *T, uint32_t l, u
     return acc;
   }
   uint32_t acc = 0, x = l + OFF, i = 0;
+  if constexpr (Tab::kDeep) {  // eight terms in flight
+    for (; i + 8u <= m; i += 8u, x += 4u * l2) {
+      uint32_t s8 = 0;
+#pragma unroll
+      for (uint32_t e = 0; e < 8u; ++e) s8 += (uint32_t)np_at<PACKED>(T, x + e * l);
+      acc += s8;
+    }
+  }
   for (; i + 4u <= m; i += 4u, x += 2u * l2)
     acc += (uint32_t)np_at<PACKED>(T, x) + (uint32_t)np_at<PACKED>(T, x + l) +
            (uint32_t)np_at<PACKED>(T, x + l2) + (uint32_t)np_at<PACKED>(T, x + l2 + l);
@@ -201,13 +366,14 @@ __device__ __forceinline__ uint32_t harmonic_sum(const int32_t *T, uint32_t l, u
 
 // NN -> D in place (file comment): D(x) = NN(c + 1 - x) - NN(1 + x) at entry
 // 1 + x, x in [0, c]; the pair (x, c - x) owns entries 1 + x and c + 1 - x.
-__device__ __forceinline__ void nn_to_d(int32_t *T, uint32_t c32) {
-  for (uint32_t x = threadIdx.x; 2u * x <= c32; x += kPrefixNT) {
-    const int32_t a = T[1u + x], b = T[c32 + 1u - x];
-    T[1u + x] = b - a;
-    T[c32 + 1u - x] = a - b;
+// The caller synchronises the team before the entries are read.
+template <class Team, class Tab>
+__device__ __forceinline__ void nn_to_d(const Tab &T, uint32_t c32, Team tm) {
+  for (uint32_t x = tm.tid(); 2u * x <= c32; x += Team::kThreads) {
+    const int32_t a = T.ld(1u + x), b = T.ld(c32 + 1u - x);
+    T.st(1u + x, b - a);
+    T.st(c32 + 1u - x, a - b);
   }
-  __syncthreads();
 }
 
 // The candidate test (file comment): divide only when S > B f, or for the
@@ -263,51 +429,46 @@ __device__ __forceinline__ bool prune_ccm1(const PrefixEval &x, uint32_t l, uint
   return lS <= 2 * (int64_t)q * l * x.L1;
 }
 
-// Word offset of p within its 16-byte line (0..3): entry e of a table at p
-// starts a 16-byte load iff (word_phase(p) + e) % 4 == 0.
-__device__ __forceinline__ uint32_t word_phase(const int32_t *p) {
-  return (uint32_t)((reinterpret_cast<uintptr_t>(p) >> 2) & 3u);
-}
-
-// First l >= l0 with (phase + l) % 4 == 0.
+// First l >= l0 with (phase + l) % 4 == 0: entry e of a table starts a
+// 16-byte load iff (phase(0) + e) % 4 == 0.
 __device__ __forceinline__ uint32_t aligned_from(uint32_t l0, uint32_t phase) {
   return l0 + ((4u - ((phase + l0) & 3u)) & 3u);
 }
 
 // MT: S(l) = E(l) + TB + sumw_big + n_half (c/2) + n_full c, f = c; one lookup.
-__device__ __forceinline__ void eval_mt(const int32_t *E, int64_t lam0, int64_t lam_end,
-                                        int64_t c, PrefixEval &x) {
+template <class Team, class Tab>
+__device__ __forceinline__ void eval_mt(const Tab &E, int64_t lam0, int64_t lam_end,
+                                        int64_t c, PrefixEval &x, Team tm) {
   int64_t lo_d, hi_d;
   param_range(kMT, c, lo_d, hi_d);
   const uint32_t gofs = flat_index(kMT, lo_d, c) - (uint32_t)lo_d;
   const uint32_t kS = x.TB + x.sumw_big + x.n_half * (x.c32 / 2u) + x.n_full * x.c32;
   const uint32_t l0 = (uint32_t)lam0, le = (uint32_t)lam_end;
-  if (l0 == 0u && threadIdx.x == 0 && !x.best) x.best = make_key((int64_t)x.B, gofs);  // l = 0: L1
-  for (uint32_t l = l0 + threadIdx.x; l < le; l += kPrefixNT)
-    try_key((uint32_t)E[min(l, x.U + 1u)] + kS, x.c32, gofs + l, x.B, x.best);
+  if (l0 == 0u && tm.tid() == 0 && !x.best) x.best = make_key((int64_t)x.B, gofs);  // l = 0: L1
+  for (uint32_t l = l0 + tm.tid(); l < le; l += Team::kThreads)
+    try_key((uint32_t)E.ld(min(l, x.U + 1u)) + kS, x.c32, gofs + l, x.B, x.best);
 }
 
 // RAD2: n1 = N'(l), n2s = Ns(y), n2b = Ns(y) - N'(y), y = c - 2l + 1; f = c.
-template <bool PACKED>
-__device__ __forceinline__ void eval_rad2(const int32_t *T0, const int32_t *T1, int64_t lam0,
-                                          int64_t lam_end, int64_t c, PrefixEval &x) {
+template <bool PACKED, class Team, class Tab>
+__device__ __forceinline__ void eval_rad2(const Tab &T0, const Tab &T1, int64_t lam0,
+                                          int64_t lam_end, int64_t c, PrefixEval &x, Team tm) {
   int64_t lo_d, hi_d;
   param_range(kRAD2, c, lo_d, hi_d);
   const uint32_t gofs = flat_index(kRAD2, lo_d, c) - (uint32_t)lo_d;
   const uint32_t A3 = x.c32 / 3u, B2 = x.c32 / 2u;
   const uint32_t kS = x.n_big * x.c32 + x.n_half * B2 + x.n_full * x.c32;
-  for (uint32_t l = (uint32_t)lam0 + threadIdx.x; l < (uint32_t)lam_end; l += kPrefixNT) {
+  for (uint32_t l = (uint32_t)lam0 + tm.tid(); l < (uint32_t)lam_end; l += Team::kThreads) {
     const uint32_t y = min(x.c32 - 2u * l + 1u, x.U + 1u);
     uint32_t n1, n2s, npy;
     if (PACKED) {
-      const uint32_t *P = reinterpret_cast<const uint32_t *>(T1);
       n1 = (uint32_t)np_at<true>(T1, l);
-      n2s = P[y] >> 16;
+      n2s = T1.ldu(y) >> 16;
       npy = (uint32_t)np_at<true>(T1, y);
     } else {
-      n1 = (uint32_t)T0[l];
-      n2s = (uint32_t)T1[y];
-      npy = (uint32_t)T0[y];
+      n1 = (uint32_t)T0.ld(l);
+      n2s = (uint32_t)T1.ld(y);
+      npy = (uint32_t)T0.ld(y);
     }
     const uint32_t n2b = n2s - npy;
     try_key(A3 * n1 + (B2 - A3) * n2s - (x.c32 - A3 - B2) * n2b + kS, x.c32, gofs + l, x.B, x.best);
@@ -316,27 +477,27 @@ __device__ __forceinline__ void eval_rad2(const int32_t *T0, const int32_t *T1, 
 
 // FS1 from the w-domain table (file comment).  Its terms (l', j), j in
 // [1, l'] -- 5150 of them for l in [1, 100] -- are cut into equal runs, one per
-// thread.  A run walks j (and on to the next l' where one ends) with an
-// incremental quotient j c = q l' + r, so that ceil(j c / l') = q + [r > 0]
-// and the multiples of the divisibility sum are exactly the terms with r = 0
-// (w = j c / l'); it adds its count and multiples' sums per parameter into
-// shared memory, after which thread l - lo forms S(l) in 64 bits and keeps
-// the key (the first parameters its thread meets).  With c < 2^20 on this path
-// every j c fits 32 bits; the count sum, at most 101 (sum w) / c, is below 2^32
-// by prefix_home, and the multiples' sum is at most sum w.
+// thread of the team.  A run walks j (and on to the next l' where one ends)
+// with an incremental quotient j c = q l' + r, so that ceil(j c / l') = q +
+// [r > 0] and the multiples of the divisibility sum are exactly the terms with
+// r = 0 (w = j c / l'); it adds its count and multiples' sums per parameter
+// into shared memory (fs1_accumulate), after which thread l - lo of one CTA
+// forms S(l) in 64 bits and keeps the key (fs1_finish; the first parameters
+// its thread meets).  With c < 2^20 on this path every j c fits 32 bits; the
+// count sum, at most 101 (sum w) / c, is below 2^32 by prefix_home, and the
+// multiples' sum is at most sum w.
 __device__ __forceinline__ uint32_t tri(uint32_t m) { return m * (m + 1u) / 2u; }
 
-__device__ __forceinline__ void eval_fs1(const int32_t *T, int64_t c, PrefixEval &x,
-                                         PrefixShared &S) {
+template <class Team, class Tab>
+__device__ __forceinline__ void fs1_accumulate(const Tab &T, int64_t c, PrefixShared &S, Team tm) {
   int64_t lo_d, hi_d;
   param_range(kFS1, c, lo_d, hi_d);
   const uint32_t lo = (uint32_t)lo_d, hi = (uint32_t)hi_d;
-  const uint32_t gofs = flat_index(kFS1, lo_d, c) - lo;
-  const uint32_t c32 = x.c32;
+  const uint32_t c32 = (uint32_t)c;
   const uint32_t base = tri(lo);  // term index of (l' = lo + 1, j = 1), plus base
   const uint32_t total = tri(hi + 1u) - base;
-  const uint32_t per = (total + kPrefixNT - 1) / kPrefixNT;
-  uint32_t p = threadIdx.x * per;
+  const uint32_t per = (total + Team::kThreads - 1) / Team::kThreads;
+  uint32_t p = tm.tid() * per;
   const uint32_t pe = min(total, p + per);
   if (p < pe) {
     // the run's first term: l = the largest m with tri(m) <= p + base
@@ -362,10 +523,10 @@ __device__ __forceinline__ void eval_fs1(const int32_t *T, int64_t c, PrefixEval
       uint32_t cnt = 0, dv = 0;
       for (;;) {
         const uint32_t xj = q + (r != 0u);  // in [1, c]
-        const int32_t nx = T[xj] - T[xj + 1u];
+        const int32_t nx = T.ld(xj) - T.ld(xj + 1u);
         cnt += (uint32_t)nx;
         if (r == 0u) {  // c divides xj l': xj's items map to xj l
-          const int32_t nx1 = (xj < c32) ? T[xj + 1u] - T[xj + 2u] : 0;  // N(c + 1) = 0
+          const int32_t nx1 = (xj < c32) ? T.ld(xj + 1u) - T.ld(xj + 2u) : 0;  // N(c + 1) = 0
           dv += xj * (uint32_t)(nx - nx1);
         }
         if (j == jend) break;
@@ -384,7 +545,16 @@ __device__ __forceinline__ void eval_fs1(const int32_t *T, int64_t c, PrefixEval
       j = 1u;
     }
   }
-  __syncthreads();
+}
+
+// FS1's keys from the sums fs1_accumulate left in S (after the team's
+// barrier): thread l - lo takes parameter l.
+__device__ __forceinline__ void fs1_finish(int64_t c, PrefixEval &x, const PrefixShared &S) {
+  int64_t lo_d, hi_d;
+  param_range(kFS1, c, lo_d, hi_d);
+  const uint32_t lo = (uint32_t)lo_d, hi = (uint32_t)hi_d;
+  const uint32_t gofs = flat_index(kFS1, lo_d, c) - lo;
+  const uint32_t c32 = x.c32;
   if (threadIdx.x <= hi - lo) {
     const uint32_t l = lo + threadIdx.x;
     const uint64_t Sv = (uint64_t)c32 * S.fs1_cnt[threadIdx.x] - S.fs1_dv[threadIdx.x];
@@ -399,10 +569,11 @@ __device__ __forceinline__ void eval_fs1(const int32_t *T, int64_t c, PrefixEval
 }
 
 // CCM1 / BJ1: the lookups of parameter l fall like X / l, so heavy parameters
-// are shared by the CTA, medium ones by a warp, the rest take a thread each.
-template <int D, bool PACKED>
-__device__ void eval_harmonic(const int32_t *T0, int64_t lam0, int64_t lam_end, int64_t c,
-                              PrefixEval &x, PrefixShared &S) {
+// are shared by the CTA (or by every CTA of the team), medium ones by a warp,
+// the rest take a thread each.
+template <int D, bool PACKED, class Team, class Tab>
+__device__ void eval_harmonic(const Tab &T0, int64_t lam0, int64_t lam_end, int64_t c,
+                              PrefixEval &x, PrefixShared &S, Team tm) {
   const int tid = threadIdx.x;
   const uint32_t c32 = x.c32, U = x.U;
   int64_t lo_d, hi_d;
@@ -414,7 +585,9 @@ __device__ void eval_harmonic(const int32_t *T0, int64_t lam0, int64_t lam_end, 
   const uint32_t X = (D == kCCM1) ? U : c32;
   const int64_t cta_end = max(lam0, min(lam_end, min((int64_t)(X / kCtaBlocks) + 1, lam0 + kMaxHeavy)));
   const int64_t warp_end = max(cta_end, min(lam_end, (int64_t)(X / kWarpBlocks) + 1));
-  const int lane = (int)lane_id(), warp = tid >> 5;
+  const int lane = (int)lane_id();
+  const uint32_t gwarp = tm.warp(), gtid = tm.tid();
+  constexpr uint32_t W = Team::kWarps;
   auto finish = [&](uint32_t l, uint32_t q, uint32_t acc) {
     uint32_t Sv, f;
     if (D == kCCM1) {
@@ -435,7 +608,32 @@ __device__ void eval_harmonic(const int32_t *T0, int64_t lam0, int64_t lam_end, 
   };
   constexpr uint32_t kPruned = 0xFFFFFFFFu;  // heavy_cm marker (cm < l otherwise)
   const int ncta = (int)(cta_end - lam0);
-  if (ncta > 0) {
+  if constexpr (Team::kParts > 1) {
+    // a team of several CTAs shares every heavy parameter: each CTA adds
+    // its blocks' sum into CTA 0's heavy_acc (zeroed by the caller before the
+    // team's last barrier), and CTA 0's thread i finishes parameter i
+    if (ncta > 0) {
+      if (tid < ncta) {
+        const uint32_t l = (uint32_t)(lam0 + tid);
+        const uint32_t q = c32 / l, cm = c32 - q * l;
+        S.heavy_cm[tid] = pruned(l, q, cm) ? kPruned : cm;
+      }
+      __syncthreads();
+      for (int i = 0; i < ncta; ++i) {
+        const uint32_t l = (uint32_t)(lam0 + i);
+        const uint32_t cm = S.heavy_cm[i];
+        if (cm == kPruned || (D == kBJ1 && cm == 0u)) continue;  // BJ1, cm = 0: S = sum w
+        const uint32_t part = __reduce_add_sync(
+            0xFFFFFFFFu, block_terms<D, PACKED>(T0, X, l, gtid, Team::kThreads));
+        if (lane == 0 && part != 0u) dsm_red_add(cluster_map(smem_addr(&S.heavy_acc[i]), 0), part);
+      }
+      tm.sync();
+      if (tm.part == 0u && tid < ncta && S.heavy_cm[tid] != kPruned) {
+        const uint32_t l = (uint32_t)(lam0 + tid);
+        finish(l, c32 / l, S.heavy_acc[tid]);
+      }
+    }
+  } else if (ncta > 0) {
     if (tid < ncta) {
       const uint32_t l = (uint32_t)(lam0 + tid);
       const uint32_t q = c32 / l, cm = c32 - q * l;
@@ -459,15 +657,15 @@ __device__ void eval_harmonic(const int32_t *T0, int64_t lam0, int64_t lam_end, 
   }
 
   // ---- parameters shared by one warp --------------------------------------------
-  // Round i gives warp w the parameter cta_end + 8 i + w (i even) or + 7 - w
-  // (i odd); lane t of a batch of 32 rounds owns the t-th one: it computes
-  // its quotient, broadcasts cm, and keeps the warp's sum.
+  // Round i gives warp w (of the team's W) the parameter cta_end + W i + w (i
+  // even) or + W - 1 - w (i odd); lane t of a batch of 32 rounds owns the t-th
+  // one: it computes its quotient, broadcasts cm, and keeps the warp's sum.
   {
     const int64_t nwarp = warp_end - cta_end;
-    const int64_t rounds = (nwarp + kPrefixWarps - 1) / kPrefixWarps;
+    const int64_t rounds = (nwarp + W - 1) / W;
     for (int64_t r0 = 0; r0 < rounds; r0 += 32) {
       const int64_t ri = r0 + lane;
-      const int64_t my_l = cta_end + ri * kPrefixWarps + ((ri & 1) ? kPrefixWarps - 1 - warp : warp);
+      const int64_t my_l = cta_end + ri * W + ((ri & 1) ? W - 1 - gwarp : gwarp);
       const bool in_range = ri < rounds && my_l < warp_end;
       const uint32_t ml = in_range ? (uint32_t)my_l : 1u;
       const uint32_t mq = c32 / ml;
@@ -490,8 +688,8 @@ __device__ void eval_harmonic(const int32_t *T0, int64_t lam0, int64_t lam_end, 
 
   // ---- one thread per run of kRun parameters -----------------------------------------
   // Warp blocks of 32 kRun consecutive lambdas from warp_end on; round i gives
-  // warp w the block i kPrefixWarps + w (i even) or + kPrefixWarps - 1 - w (i
-  // odd), so that the warps' loads balance, and lane t of it the lambdas
+  // warp w the block i W + w (i even) or + W - 1 - w (i odd), so that the
+  // warps' loads balance, and lane t of it the lambdas
   // base + t + 32 k, k < kRun: a thread's parameters increase, and at each
   // step the warp reads consecutive lambdas' terms.  One division per run for
   // q = floor(c / l) and m = floor(X / l) (the number of terms), decrements
@@ -506,8 +704,8 @@ __device__ void eval_harmonic(const int32_t *T0, int64_t lam0, int64_t lam_end, 
     // BJ1's l > c / 2 (q = 1) are taken below, four at a time
     const uint32_t lq1 = (D == kBJ1) ? max((uint32_t)warp_end, min(le, c32 / 2u + 1u)) : le;
     bool odd = false;
-    for (uint32_t r0 = (uint32_t)warp_end; r0 < lq1; r0 += kBlock * kPrefixWarps, odd = !odd) {
-      const uint32_t wb = odd ? (uint32_t)(kPrefixWarps - 1 - warp) : (uint32_t)warp;
+    for (uint32_t r0 = (uint32_t)warp_end; r0 < lq1; r0 += kBlock * W, odd = !odd) {
+      const uint32_t wb = odd ? W - 1u - gwarp : gwarp;
       const uint32_t l0 = r0 + wb * kBlock + (uint32_t)lane;
       if (l0 >= lq1) continue;
       uint32_t q = c32 / l0, m = (D == kCCM1) ? U / l0 : 0u;
@@ -532,20 +730,20 @@ __device__ void eval_harmonic(const int32_t *T0, int64_t lam0, int64_t lam_end, 
     // f = 2l - c.  Parameters from la (entry 1 + la 16-byte aligned) go four
     // to a thread per step, one 16-byte load each; the few before la one each.
     if (D == kBJ1 && lq1 < le) {
-      const uint32_t la = min(le, aligned_from(lq1, word_phase(T0 + 1)));  // T0 + 1 + la aligned
-      if (lq1 + (uint32_t)tid < la) {
-        const uint32_t l = lq1 + (uint32_t)tid;
-        try_key((uint32_t)T0[1u + l], 2u * l - c32, gofs + l, x.B, x.best);
+      const uint32_t la = min(le, aligned_from(lq1, T0.phase(1)));  // entry 1 + la aligned
+      if (lq1 + gtid < la) {
+        const uint32_t l = lq1 + gtid;
+        try_key((uint32_t)T0.ld(1u + l), 2u * l - c32, gofs + l, x.B, x.best);
       }
-      for (uint32_t l = la + 4u * (uint32_t)tid; l < le; l += 4u * kPrefixNT) {
+      for (uint32_t l = la + 4u * gtid; l < le; l += 4u * Team::kThreads) {
         if (l + 3u < le) {
-          const int4 v = *reinterpret_cast<const int4 *>(T0 + 1u + l);
+          const int4 v = T0.ld4(1u + l);
           try_key((uint32_t)v.x, 2u * l - c32, gofs + l, x.B, x.best);
           try_key((uint32_t)v.y, 2u * l + 2u - c32, gofs + l + 1u, x.B, x.best);
           try_key((uint32_t)v.z, 2u * l + 4u - c32, gofs + l + 2u, x.B, x.best);
           try_key((uint32_t)v.w, 2u * l + 6u - c32, gofs + l + 3u, x.B, x.best);
         } else {
-          for (uint32_t e = l; e < le; ++e) try_key((uint32_t)T0[1u + e], 2u * e - c32, gofs + e, x.B, x.best);
+          for (uint32_t e = l; e < le; ++e) try_key((uint32_t)T0.ld(1u + e), 2u * e - c32, gofs + e, x.B, x.best);
         }
       }
     }
@@ -562,16 +760,17 @@ __device__ void eval_harmonic(const int32_t *T0, int64_t lam0, int64_t lam_end, 
 // are l <= lmax.  Returns 0 (VB2 stays with its kernel), 1 (evaluate l in
 // [2, lmax] here) or 2 (no VB2 parameter can matter); the cut kk is k in
 // verdict mode, else L1 (MT in the bound), clamped to the stream length.
-constexpr int64_t kVb2TableTerms = 1 << 16;  // lookups per tile at most
+// `budget`: the most lookups the tile takes on (kVb2TableTerms per CTA of
+// its team).
+constexpr int64_t kVb2TableTerms = 1 << 16;  // lookups per CTA at most
 
 template <int MODE>
 __device__ __forceinline__ int vb2_table_plan(const EvalArgs &A, const InstView &I,
                                               const PrefixShared &S, uint32_t L1,
-                                              int64_t vb2_cap_hi, int64_t &kk, int64_t &lmax) {
+                                              int64_t vb2_cap_hi, int64_t budget, int64_t &kk,
+                                              int64_t &lmax) {
   const int64_t c = I.c;
-  if (!(A.prune || A.verdict) || ((A.dff_off >> kVB2) & 1u) || !A.vb2_on || c > kVb2FixedCap ||
-      c < 2)
-    return 0;
+  if (!(A.prune || A.verdict) || ((A.dff_off >> kVB2) & 1u) || !A.vb2_on || c < 2) return 0;
   const int64_t cut = A.verdict ? I.k : ((A.dff_off & 1u) ? -1 : (int64_t)L1);
   if (cut < 0) return 0;
   kk = min(cut, stream_len<MODE>(I));
@@ -589,7 +788,7 @@ __device__ __forceinline__ int vb2_table_plan(const EvalArgs &A, const InstView 
     if (lmax < 2) return 2;
   }
   const int64_t U = (c - 1) / 2;
-  return (U * lmax * lmax / (2 * c) + lmax <= kVb2TableTerms) ? 1 : 0;
+  return (U * lmax * lmax / (2 * c) + lmax <= budget) ? 1 : 0;
 }
 
 // VB2's parameters l in [2, lmax] from the packed count table T (entry x:
@@ -600,16 +799,17 @@ __device__ __forceinline__ int vb2_table_plan(const EvalArgs &A, const InstView 
 // j c = q l + r (no division but c / l per parameter).  Every l in the range
 // is evaluated exactly (the range is a relaxation of the parameters that can
 // matter; the others only cost their lookups).
-__device__ __forceinline__ void eval_vb2_table(const int32_t *T, int64_t c, PrefixEval &x,
-                                               const PrefixShared &S, int64_t lmax) {
+template <class Team, class Tab>
+__device__ __forceinline__ void eval_vb2_table(const Tab &T, int64_t c, PrefixEval &x,
+                                               const PrefixShared &S, int64_t lmax, Team tm) {
   const uint32_t c32 = x.c32, U = x.U;
   const uint32_t gofs = flat_index(kVB2, 2, c) - 2u;
   const int64_t ns = S.sums[0], nb = S.sums[1];
   const int64_t K = 2 * nb + S.sums[2] + 2 * S.sums[3];
   const uint32_t n = (uint32_t)lmax - 1u;  // parameters 2 .. lmax
   bool odd = false;
-  for (uint32_t r0 = 0; r0 < n; r0 += kPrefixNT, odd = !odd) {
-    const uint32_t p = r0 + (odd ? (uint32_t)(kPrefixNT - 1) - threadIdx.x : threadIdx.x);
+  for (uint32_t r0 = 0; r0 < n; r0 += Team::kThreads, odd = !odd) {
+    const uint32_t p = r0 + (odd ? Team::kThreads - 1u - tm.tid() : tm.tid());
     if (p >= n) continue;
     const uint32_t l = 2u + p;
     const uint32_t cq = c32 / l, cr = c32 - cq * l;
@@ -632,6 +832,85 @@ __device__ __forceinline__ void eval_vb2_table(const int32_t *T, int64_t c, Pref
       x.best = make_key((int64_t)lb, gofs + l);
     }
   }
+}
+
+// A team of several CTAs: every CTA but 0 adds its FS1 sums into CTA 0's
+// (after the CTA's barrier; the team's barrier follows).
+template <class Team>
+__device__ __forceinline__ void fs1_gather(PrefixShared &S, Team tm) {
+  if (tm.part != 0u && threadIdx.x < kFs1Params) {
+    const uint32_t t = threadIdx.x;
+    if (S.fs1_cnt[t] != 0u) dsm_red_add(cluster_map(smem_addr(&S.fs1_cnt[t]), 0), S.fs1_cnt[t]);
+    if (S.fs1_dv[t] != 0u) dsm_red_add(cluster_map(smem_addr(&S.fs1_dv[t]), 0), S.fs1_dv[t]);
+  }
+}
+
+// Evaluates the parameters of a built tile (prefix_tile; the cluster kernel):
+// D's parameters [lam0, lam_end) -- after FS1's when with_fs1 (D = BJ1) --
+// or the u group's members in umask, with the team's threads; returns the
+// thread's best key.  The instance sums are in S.sums, the tables T0 (and T1)
+// complete.  A team of several CTAs gathers FS1's sums in CTA 0 (fs1_gather),
+// which forms FS1's bounds.
+template <int D, class Team, class Tab>
+__device__ __forceinline__ unsigned long long prefix_evaluate(const EvalArgs &A, const Tab &T0,
+                                                              const Tab &T1, int64_t c,
+                                                              int64_t lam0, int64_t lam_end,
+                                                              bool with_fs1, uint32_t umask,
+                                                              PrefixShared &S, Team tm) {
+  const uint32_t c32 = (uint32_t)c;
+  // all below 2^31 on this path (prefix_handles); the sums S(l) below 2^32,
+  // evaluated in wrapping 32-bit arithmetic
+  PrefixEval x;
+  x.c32 = c32;
+  x.U = (uint32_t)((c - 1) / 2);
+  x.n_big = (uint32_t)S.sums[1];
+  x.n_half = (uint32_t)S.sums[2];
+  x.n_full = (uint32_t)S.sums[3];
+  x.sumw_big = (uint32_t)S.sums[4];
+  x.sumw = (uint32_t)S.sums[5];
+  x.TB = (uint32_t)S.sums[6];
+  // L1 (MT's bound at l = 0) when MT is part of the bound, else no floor
+  x.L1 = x.sumw / c32 + (x.sumw % c32 != 0u);
+  x.B = (A.dff_off & 1u) ? 0u : x.L1;
+  x.prune = A.prune && !(A.dff_off & 1u);
+  x.best = 0ull;
+
+  if (D == kBJ1 && with_fs1) {  // FS1 precedes BJ1 in paper order
+    fs1_accumulate(T0, c, S, tm);
+    __syncthreads();
+    if constexpr (Team::kParts > 1) {
+      fs1_gather(S, tm);
+      tm.sync();
+    }
+    if (tm.part == 0u) fs1_finish(c, x, S);
+  }
+  if (D == kBJ1 && lam0 < lam_end) {  // FS1's lookups are done
+    nn_to_d(T0, c32, tm);
+    tm.sync();
+  }
+  if (D == kMT) eval_mt(T0, lam0, lam_end, c, x, tm);
+  if (D == kRAD2) eval_rad2<false>(T0, T1, lam0, lam_end, c, x, tm);
+  if (D == kCCM1 || D == kBJ1) eval_harmonic<D, false>(T0, lam0, lam_end, c, x, S, tm);
+  if (D == kPrefixU) {
+    // the members in paper order, so that each thread meets its parameters in
+    // increasing flattened index
+    auto member = [&](int d) { return ((umask >> d) & 1u) != 0u; };
+    int64_t lo, hi;
+    if (member(kMT)) {
+      param_range(kMT, c, lo, hi);
+      eval_mt(T0, lo, hi + 1, c, x, tm);
+    }
+    if (member(kRAD2)) {
+      param_range(kRAD2, c, lo, hi);
+      eval_rad2<true>(T0, T1, lo, hi + 1, c, x, tm);
+    }
+    if (member(kCCM1)) {
+      param_range(kCCM1, c, lo, hi);
+      eval_harmonic<kCCM1, true>(T1, lo, hi + 1, c, x, S, tm);
+    }
+    if (S.vb2_mode == 1) eval_vb2_table(T1, c, x, S, S.vb2_lmax, tm);
+  }
+  return x.best;
 }
 
 // Builds the table(s) of D (a DFF, or kPrefixU for the merged u group) for
@@ -755,7 +1034,8 @@ __device__ __forceinline__ unsigned long long prefix_tile(const EvalArgs &A, con
     if (D == kPrefixU && !S.err) {
       const uint32_t sw32 = (uint32_t)S.sums[5];
       const int64_t vhi = A.vb2_hi != nullptr ? A.vb2_hi[b] : c;
-      mode = vb2_table_plan<MODE>(A, I, S, sw32 / c32 + (sw32 % c32 != 0u), vhi, kk, lmax);
+      mode = vb2_table_plan<MODE>(A, I, S, sw32 / c32 + (sw32 % c32 != 0u), vhi, kVb2TableTerms,
+                                  kk, lmax);
     }
     S.vb2_mode = mode;
     S.vb2_kk = kk;
@@ -776,54 +1056,15 @@ __device__ __forceinline__ unsigned long long prefix_tile(const EvalArgs &A, con
   }
   if (S.err) return 0ull;
 
-  // all below 2^31 on this path (prefix_handles); the sums S(l) below 2^32,
-  // evaluated in wrapping 32-bit arithmetic
-  PrefixEval x;
-  x.c32 = c32;
-  x.U = U;
-  x.n_big = (uint32_t)S.sums[1];
-  x.n_half = (uint32_t)S.sums[2];
-  x.n_full = (uint32_t)S.sums[3];
-  x.sumw_big = (uint32_t)S.sums[4];
-  x.sumw = (uint32_t)S.sums[5];
-  x.TB = (uint32_t)S.sums[6];
-  // L1 (MT's bound at l = 0) when MT is part of the bound, else no floor
-  x.L1 = x.sumw / c32 + (x.sumw % c32 != 0u);
-  x.B = (A.dff_off & 1u) ? 0u : x.L1;
-  x.prune = A.prune && !(A.dff_off & 1u);
-  x.best = 0ull;
-
-  if (D == kBJ1 && with_fs1) eval_fs1(T0, c, x, S);  // FS1 precedes BJ1 in paper order
-  if (D == kBJ1 && lam0 < lam_end) nn_to_d(T0, c32);   // FS1's lookups are done
-  if (D == kMT) eval_mt(T0, lam0, lam_end, c, x);
-  if (D == kRAD2) eval_rad2<false>(T0, T1, lam0, lam_end, c, x);
-  if (D == kCCM1 || D == kBJ1) eval_harmonic<D, false>(T0, lam0, lam_end, c, x, S);
-  if (D == kPrefixU) {
-    // the members in paper order, so that each thread meets its parameters in
-    // increasing flattened index
-    auto member = [&](int d) { return ((umask >> d) & 1u) != 0u; };
-    int64_t lo, hi;
-    if (member(kMT)) {
-      param_range(kMT, c, lo, hi);
-      eval_mt(T0, lo, hi + 1, c, x);
-    }
-    if (member(kRAD2)) {
-      param_range(kRAD2, c, lo, hi);
-      eval_rad2<true>(T0, T1, lo, hi + 1, c, x);
-    }
-    if (member(kCCM1)) {
-      param_range(kCCM1, c, lo, hi);
-      eval_harmonic<kCCM1, true>(T1, lo, hi + 1, c, x, S);
-    }
-    if (S.vb2_mode == 1) eval_vb2_table(T1, c, x, S, S.vb2_lmax);
-  }
-  return x.best;
+  return prefix_evaluate<D>(A, LocalTab{T0}, LocalTab{T1}, c, lam0, lam_end, with_fs1, umask, S,
+                            CtaTeam{0u});
 }
 
 // Persistent kernel over the prefix tile table (instance, DFF in {MT, RAD2,
 // FS1, CCM1, BJ1} routed here by prefix_handles or the merged u group, A.plpt
 // consecutive lambdas -- all of them when the tables are in the global
-// scratch; FS1 with BJ1's first tile when prefix_w_merged).
+// scratch; FS1 with BJ1's first tile when prefix_w_merged).  Tables of a
+// cluster's size (prefix_home 3) are the cluster kernel's (bp_lb_cluster.cuh).
 template <int MODE>
 __global__ void __launch_bounds__(kPrefixNT, 4) prefix_kernel(EvalArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -847,7 +1088,8 @@ __global__ void __launch_bounds__(kPrefixNT, 4) prefix_kernel(EvalArgs A) {
       int64_t rem = t - t0;
       int d = 0;
       const int64_t sb = sum_bound<MODE>(I);
-      if (I.c != S.rc_c || sb != S.rc_sb) {  // route this instance (tile counts as route_tiles)
+      const int rk = route_class(I.c, sb);
+      if (I.c != S.rc_c || rk != S.rc_k) {  // route this instance (tile counts as route_tiles)
         const bool merged = prefix_u_merged(I.c, sb, A.prefix_on, A.vb2_on, A.dff_off, A.plpt);
         const bool wmerged = prefix_w_merged(I.c, sb, A.prefix_on, A.vb2_on, A.dff_off);
         int umask = 0;
@@ -855,17 +1097,18 @@ __global__ void __launch_bounds__(kPrefixNT, 4) prefix_kernel(EvalArgs A) {
           const bool pre = dff_kernel(e, I.c, sb, A.prefix_on, A.vb2_on, A.dff_off) == kRoutePrefix;
           const bool member = merged && (e == kMT || e == kRAD2 || e == kCCM1);
           if (member && param_count(e, I.c) > 0 && pre) umask |= 1 << e;
-          S.rc_nt[e] = (pre && !member && !(wmerged && e == kFS1))
+          S.rc_home[e] = prefix_home(e, I.c, sb, A.prefix_on);
+          // units whose tables are a cluster's go to the cluster kernel
+          S.rc_nt[e] = (pre && !member && !(wmerged && e == kFS1) && S.rc_home[e] != 3)
                            ? (int)prefix_dff_tiles(e, I.c, sb, A.prefix_on, A.plpt)
                            : 0;
-          S.rc_home[e] = prefix_home(e, I.c, sb, A.prefix_on);
         }
-        S.rc_merged = merged;
+        S.rc_merged = merged && prefix_u_home(I.c, A.prefix_on) != 3;
         S.rc_wmerged = wmerged;
         S.rc_umask = umask;
         S.rc_uhome = prefix_u_home(I.c, A.prefix_on);
         S.rc_c = I.c;
-        S.rc_sb = sb;
+        S.rc_k = rk;
       }
       const bool merged = S.rc_merged != 0, wmerged = S.rc_wmerged != 0;
       if (merged && rem == 0) {
