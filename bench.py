@@ -442,8 +442,7 @@ def main():
     barrier()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    B.bp_lb_set_kernel_timing(h, True)   # events around each kernel of a step, on its stream
-    B.bp_lb_kernel_times(h)
+    # the steps as a user runs them (no per-kernel events between the kernels)
     with ClockSampler(torch.cuda.current_device()) as clk:
         barrier()
         for e0, e1 in ev:
@@ -453,6 +452,21 @@ def main():
             e1.record(stream)
         barrier()
     step_ms = np.array([e0.elapsed_time(e1) for e0, e1 in ev])
+    # the same steps again with events around each kernel, on its stream, for
+    # the per-kernel times of the roofline (they separate the kernels, so this
+    # pass's steps are a little longer)
+    B.bp_lb_set_kernel_timing(h, True)
+    B.bp_lb_kernel_times(h)
+    ev_k = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in range(max(3, args.steps // 3))]
+    barrier()
+    for e0, e1 in ev_k:
+        flush.zero_()
+        e0.record(stream)
+        step()
+        e1.record(stream)
+    barrier()
+    step_ms_timed = np.array([e0.elapsed_time(e1) for e0, e1 in ev_k])
     ms_cluster, ms_prefix, ms_vb2, ms_direct, n_calls = B.bp_lb_kernel_times4(h)
     cluster_used = B.bp_lb_get_cluster_tables(h) == 1
     kwork = B.bp_lb_kernel_work(h)        # VB2 pairs and parameters actually evaluated
@@ -644,6 +658,7 @@ def main():
                      "kernel": kernel_name + ", its own CUDA-event time per launch",
                      "prefix_kernel_ms": t_prefix, "vb2_kernel_ms": t_vb2,
                      "direct_kernel_ms": t_direct, "cluster_kernel_ms": t_cluster,
+                     "kernel_events_pass_ms_per_step": float(step_ms_timed.mean()),
                      "prefix_kernel_frac": frac["prefix"], "vb2_kernel_frac": frac["vb2"],
                      "direct_kernel_frac": frac["direct"]},
         "launch_shape": {"chosen": shape, "nt_t_g_minb": list(B.bp_lb_launch_shape_info(shape)),

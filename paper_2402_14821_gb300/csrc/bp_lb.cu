@@ -164,10 +164,29 @@ int occupancy(bp_lb *h, int mode, size_t smem) {
   return blocks;
 }
 
-int launch_eval(int shape, int mode, unsigned grid, size_t smem, cudaStream_t st, EvalArgs &A) {
+// One launch of fn; with pdl, with programmatic stream serialization (the
+// kernel may be scheduled while the previous one in the stream finishes, and
+// waits for it itself: pdl_wait).
+int launch_fn(const void *fn, unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+              EvalArgs &A, bool pdl) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = pdl ? at : nullptr;
+  cfg.numAttrs = pdl ? 1u : 0u;
   void *args[] = {&A};
-  return cuda_status(cudaLaunchKernel((const void *)eval_fn(shape, mode), dim3(grid),
-                                      dim3(kShapes[shape].nt), args, smem, st));
+  return cuda_status(cudaLaunchKernelExC(&cfg, fn, args));
+}
+
+int launch_eval(int shape, int mode, unsigned grid, size_t smem, cudaStream_t st, EvalArgs &A,
+                bool pdl = false) {
+  return launch_fn((const void *)eval_fn(shape, mode), grid, (unsigned)kShapes[shape].nt, smem, st,
+                   A, pdl);
 }
 
 int grow_batch(bp_lb *h, int32_t B) {
@@ -217,10 +236,9 @@ size_t prefix_smem(int mode, int64_t max_bins) {
   return (size_t)kPrefixSmemBytes + (mode == kSrcNodes ? sizeof(uint32_t) * (size_t)max_bins : 0);
 }
 
-int launch_prefix(int mode, unsigned grid, size_t smem, cudaStream_t st, EvalArgs &A) {
-  void *args[] = {&A};
-  return cuda_status(cudaLaunchKernel((const void *)prefix_fn(mode), dim3(grid),
-                                      dim3(kPrefixNT), args, smem, st));
+int launch_prefix(int mode, unsigned grid, size_t smem, cudaStream_t st, EvalArgs &A,
+                  bool pdl = false) {
+  return launch_fn((const void *)prefix_fn(mode), grid, kPrefixNT, smem, st, A, pdl);
 }
 
 // Dynamic shared memory of the cluster kernel: a table slice, then (search
@@ -384,15 +402,21 @@ int launch_batch(bp_lb *h, EvalArgs A, size_t smem, cudaStream_t st) {
   }
   if (h->timing) BP_CHECK(cudaEventRecord(ev[7], h->side));
   if (cl_side) BP_CHECK(cudaEventRecord(h->ev_cjoin, h->side));
+  // Serial order on the caller's stream with nothing between the kernels:
+  // programmatic dependent launch (pdl_wait), so that each kernel is
+  // scheduled while the one before it finishes.  Per-kernel timing events
+  // sit between the kernels, so timed calls launch them plainly.
+  const bool pdl = !overlap && !cl_side && !h->timing;
   if (h->timing) BP_CHECK(cudaEventRecord(ev[0], ps_st));
   if (h->prefix_on) {
     const int pc = overlap ? std::min(pocc, (int)h->prefix_ctas) : pocc;
-    BP_CHECK_STATUS(launch_prefix(MODE, (unsigned)(h->num_sms * pc), ps, ps_st, A));
+    BP_CHECK_STATUS(launch_prefix(MODE, (unsigned)(h->num_sms * pc), ps, ps_st, A, pdl));
   }
   if (h->timing) BP_CHECK(cudaEventRecord(ev[1], ps_st));
   auto generic = [&](cudaStream_t gs) -> int {
     if (h->timing) BP_CHECK(cudaEventRecord(ev[4], gs));
-    BP_CHECK_STATUS(launch_eval(shape, MODE, (unsigned)(h->num_sms * occ), smem, gs, A));
+    BP_CHECK_STATUS(launch_eval(shape, MODE, (unsigned)(h->num_sms * occ), smem, gs, A,
+                                pdl && gs == st));
     if (h->timing) BP_CHECK(cudaEventRecord(ev[5], gs));
     return BP_OK;
   };
@@ -408,9 +432,8 @@ int launch_batch(bp_lb *h, EvalArgs A, size_t smem, cudaStream_t st) {
     BP_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &vocc, (const void *)vb2_fn(shape, MODE), kVb2NT, vs));
     if (vocc <= 0) return BP_ECUDA;
-    void *args[] = {&A};
-    BP_CHECK(cudaLaunchKernel((const void *)vb2_fn(shape, MODE), dim3((unsigned)(h->num_sms * vocc)),
-                              dim3(kVb2NT), args, vs, st));
+    BP_CHECK_STATUS(launch_fn((const void *)vb2_fn(shape, MODE), (unsigned)(h->num_sms * vocc),
+                              kVb2NT, vs, st, A, pdl));
   }
   if (h->timing) BP_CHECK(cudaEventRecord(ev[3], st));
   if (overlap) {

@@ -301,6 +301,18 @@ struct InstView {
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
+// Programmatic dependent launch (the batched calls launch the prefix, VB2
+// and generic kernels with programmatic stream serialization): a kernel
+// waits for the grid before it in the stream to complete, its writes
+// visible, before it reads anything that grid wrote (pdl_wait), and lets the
+// grid after it be scheduled early (pdl_release), so that launch latency
+// overlaps the previous kernel's tail.  Without the launch attribute both
+// are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Verdict mode (Alg. 2's early exit): an instance is decided once its result
 // slot holds a bound above k -- it is infeasible whatever the remaining
 // parameters give.  Read by one thread; the caller broadcasts the answer.
@@ -491,6 +503,7 @@ __global__ void __launch_bounds__(1024)
   constexpr int K = kPlanPerThread;
   __shared__ int64_t s_warp[32];
   __shared__ int64_t s_carry[3];
+  pdl_release();  // the prefix kernel's CTAs may be scheduled now; they wait for this grid
   if (threadIdx.x == 0) {
     s_carry[0] = s_carry[1] = s_carry[2] = 0;
     *A.work = 0ull;
@@ -1427,6 +1440,7 @@ __global__ void __launch_bounds__(NT, MINB) eval_kernel(EvalArgs A) {
   float *s_a = reinterpret_cast<float *>(smem_raw + sizeof(uint32_t) * kListTop);
   uint32_t *s_load = reinterpret_cast<uint32_t *>(smem_raw + 2 * sizeof(uint32_t) * kListTop);
 
+  pdl_wait();
   const int64_t total = A.tile_start ? A.tile_start[A.B] : A.single_tiles;
   work_count_begin(A, S);
   tile_first(A.tile_start, A.B, total, A.work, cur);

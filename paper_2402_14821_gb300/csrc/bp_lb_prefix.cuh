@@ -1073,6 +1073,8 @@ __global__ void __launch_bounds__(kPrefixNT, 4) prefix_kernel(EvalArgs A) {
   int32_t *stab = reinterpret_cast<int32_t *>(smem_raw);
   uint32_t *s_load = reinterpret_cast<uint32_t *>(smem_raw + kPrefixSmemBytes);
 
+  pdl_wait();
+  pdl_release();
   const int64_t total = A.ptile_start ? A.ptile_start[A.B] : A.single_ptiles;
   if (threadIdx.x == 0) S.rc_c = -1;  // no routing cached yet
   tile_first(A.ptile_start, A.B, total, A.pwork, cur);

@@ -35,6 +35,8 @@ __global__ void __launch_bounds__(kVb2NT, vb2_minb(VT)) vb2_kernel(EvalArgs A) {
   uint32_t *s_items = reinterpret_cast<uint32_t *>(smem_raw);
   uint32_t *s_load = reinterpret_cast<uint32_t *>(smem_raw + kVb2ListBytes);
 
+  pdl_wait();
+  pdl_release();
   const int64_t total = A.vtile_start ? A.vtile_start[A.B] : A.single_vtiles;
   const int64_t vlpt = A.vlpt != nullptr ? (int64_t)*A.vlpt : kVb2LPT;
   work_count_begin(A, S);
