@@ -329,15 +329,16 @@ def main():
     ap.add_argument("--dff-mask", type=int, default=63, help="large: DFFs in the bound (bits)")
     ap.add_argument("--no-prune", action="store_true", help="large: pruning off (all the work)")
     ap.add_argument("--large-dtypes", default="int32,int64", help="large: size types")
-    ap.add_argument("--no-cluster", action="store_true",
-                    help="every handle with cluster tables off (bp_lb_set_cluster_tables): "
-                         "prefix tables of 48-512 KB in the global scratch instead")
+    ap.add_argument("--cluster", choices=("auto", "on", "off"), default="auto",
+                    help="cluster tables (bp_lb_set_cluster_tables) of every handle: auto = the "
+                         "handle's default, switched by the autotuner where one runs; on / off "
+                         "forced, also after autotuning")
     ap.add_argument("--records", default="hard,large",
                     help="secondary records of the benchmark line (comma-separated: hard, large; "
                          "'none' for the search-node step alone, e.g. under a profiler)")
     args = ap.parse_args()
     global CLUSTER_TABLES
-    CLUSTER_TABLES = not args.no_cluster
+    CLUSTER_TABLES = args.cluster
     if args.workload != "search":
         return run_sweep(args)
 
@@ -423,6 +424,7 @@ def main():
         shape, shape_ms = B.bp_lb_autotune_nodes(h, max_bins=max_bins, out_bound=out_b,
                                                  out_argmax=out_a, out_feasible=out_f, reps=2,
                                                  stream=stream, **t_in)
+        cluster_setting(B, h)
 
     def step():
         B.bp_lb_eval_nodes(h, max_bins=max_bins, out_bound=out_b, out_argmax=out_a,
@@ -680,13 +682,19 @@ def main():
 # ---------------------------------------------------------------------------
 # secondary workloads (not the benchmark line): large instances, ragged batch
 # ---------------------------------------------------------------------------
-CLUSTER_TABLES = True
+CLUSTER_TABLES = "auto"
+
+
+def cluster_setting(B, h):
+    """Applies the run's forced cluster-table setting (none under auto)."""
+    if CLUSTER_TABLES != "auto":
+        B.bp_lb_set_cluster_tables(h, CLUSTER_TABLES == "on")
 
 
 def new_handle(B, c, max_items):
     """A handle with the run's cluster-table setting."""
     h = B.bp_lb_create(c, max_items)
-    B.bp_lb_set_cluster_tables(h, CLUSTER_TABLES)
+    cluster_setting(B, h)
     return h
 
 
@@ -777,6 +785,7 @@ def hard_nodes_record(B, stream, flush, steps, peak_ops, shape=-1):
         else:
             shape, _ = B.bp_lb_autotune_nodes(h, max_bins=mb, out_bound=ob, out_argmax=oa,
                                               out_feasible=of, reps=2, stream=stream, **t_in)
+            cluster_setting(B, h)
         step = lambda: B.bp_lb_eval_nodes(h, max_bins=mb, out_bound=ob, out_argmax=oa,
                                           out_feasible=of, stream=stream, **t_in)
         res = {}
@@ -838,6 +847,7 @@ def large_record(B, stream, flush, peak_ops, cases=LARGE_CASES, steps=3):
             ob = torch.empty(rg.count, dtype=torch.int64, device="cuda")
             oa = B.argmax_tensor(rg.count)
             shape, _ = B.bp_lb_autotune_batch(h, *t, ob, oa, reps=1, stream=stream)
+            cluster_setting(B, h)
             step = lambda: B.bp_lb_eval_batch(h, *t, ob, oa, stream=stream)
             step()
             B.bp_lb_set_kernel_timing(h, True)
@@ -1026,6 +1036,7 @@ def run_sweep(args):
                                                  else B.MODE_RAGGED_I64, shape)
                     else:
                         shape, _ = B.bp_lb_autotune_batch(h, *t, ob, oa, reps=1)
+                        cluster_setting(B, h)
                     step = lambda: B.bp_lb_eval_batch(h, *t, ob, oa, stream=stream)
                     step()
                     B.bp_lb_set_kernel_timing(h, True)
@@ -1118,6 +1129,7 @@ def run_sweep(args):
             B.bp_lb_reserve(h, nd.count)
             shape, shape_ms = B.bp_lb_autotune_nodes(h, max_bins=mb, out_bound=ob, out_argmax=oa,
                                                      out_feasible=of, reps=1, **t_in)
+            cluster_setting(B, h)
             direct = lambda: B.bp_lb_eval_nodes(h, max_bins=mb, out_bound=ob, out_argmax=oa,
                                                 out_feasible=of, stream=stream, **t_in)
             # capture the whole batch (planning + persistent evaluation) in a CUDA graph

@@ -515,7 +515,8 @@ int bp_lb_get_launch_shape(bp_lb_t *h, int32_t mode);
  * for the mode and writes it to *best_shape (may be NULL), and the mean
  * milliseconds per call of every shape to ms_per_shape[0 .. num shapes) (may
  * be NULL); then times the batch with that shape and cluster tables switched
- * (bp_lb_set_cluster_tables) and keeps the faster setting.  The output buffers receive the batch's results.  Synchronises
+ * (bp_lb_set_cluster_tables) and keeps the setting 3% faster or more, never
+ * leaving them on for a batch with no instance whose tables are of their size.  The output buffers receive the batch's results.  Synchronises
  * the stream (not capturable).  Arguments as for bp_lb_eval_batch(_i64)
  * (sizes_are_i64 selects the size type) and bp_lb_eval_nodes.
  * Errors: as those calls, and BP_EINVAL for B < 1 or reps < 1. */

@@ -449,8 +449,8 @@ int launch_batch(bp_lb *h, EvalArgs A, size_t smem, cudaStream_t st) {
 // Times `reps` calls of `call` per launch shape with CUDA events on `st`,
 // leaves the fastest shape set for `mode`.
 template <class F>
-int autotune(bp_lb *h, int mode, int32_t reps, cudaStream_t st, float *ms_out,
-                    int32_t *best_out, F call) {
+int autotune(bp_lb *h, int mode, int32_t B, int32_t reps, cudaStream_t st, float *ms_out,
+             int32_t *best_out, F call) {
   if (reps < 1) return BP_EINVAL;
   cudaEvent_t e0, e1;
   BP_CHECK(cudaEventCreate(&e0));
@@ -479,12 +479,23 @@ int autotune(bp_lb *h, int mode, int32_t reps, cudaStream_t st, float *ms_out,
   }
   h->shape[mode] = best;
   // then, with that shape, cluster tables switched: the faster setting stays
+  // (on only when the batch has units for the cluster kernel: the planner's
+  // count of them, read back after a call with them on)
   if (st_all == BP_OK) {
     const int32_t keep = h->cluster_on;
     h->cluster_on = !keep;
     st_all = call();
     float ms = 0.f;
-    if (st_all == BP_OK) {
+    bool no_units = false;
+    if (st_all == BP_OK && h->cluster_on) {
+      int64_t units = 0;
+      if (cudaMemcpyAsync(&units, h->d_ctile_start + B, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                          st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess)
+        st_all = BP_ECUDA;
+      no_units = units == 0;
+    }
+    if (st_all == BP_OK && !no_units) {
       cudaEventRecord(e0, st);
       for (int r = 0; r < reps && st_all == BP_OK; ++r) st_all = call();
       cudaEventRecord(e1, st);
@@ -494,7 +505,7 @@ int autotune(bp_lb *h, int mode, int32_t reps, cudaStream_t st, float *ms_out,
     }
     // switched only for a clear gain (the setting costs a launch when it
     // finds nothing to do, and ties are noise)
-    if (st_all != BP_OK || ms > 0.97f * best_ms) h->cluster_on = keep;
+    if (st_all != BP_OK || no_units || ms > 0.97f * best_ms) h->cluster_on = keep;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1177,7 +1188,7 @@ int bp_lb_autotune_batch(bp_lb_t *h, int32_t B, const int64_t *d_offsets, const 
                          int32_t reps, float *ms_per_shape, int32_t *best_shape, void *stream) {
   if (!h || B < 1) return BP_EINVAL;
   const int mode = sizes_are_i64 ? kSrcRaggedI64 : kSrcRaggedI32;
-  return autotune(h, mode, reps, (cudaStream_t)stream, ms_per_shape, best_shape, [&]() {
+  return autotune(h, mode, B, reps, (cudaStream_t)stream, ms_per_shape, best_shape, [&]() {
     return sizes_are_i64
                ? bp_lb_eval_batch_i64(h, B, d_offsets, (const int64_t *)d_sizes, d_capacity, d_bins,
                                       d_out_bound, d_out_argmax, d_out_feasible, stream)
@@ -1193,7 +1204,7 @@ int bp_lb_autotune_nodes(bp_lb_t *h, int32_t B, int32_t num_base, const int64_t 
                          int64_t *d_out_bound, bp_argmax_t *d_out_argmax, uint8_t *d_out_feasible,
                          int32_t reps, float *ms_per_shape, int32_t *best_shape, void *stream) {
   if (!h || B < 1) return BP_EINVAL;
-  return autotune(h, kSrcNodes, reps, (cudaStream_t)stream, ms_per_shape, best_shape, [&]() {
+  return autotune(h, kSrcNodes, B, reps, (cudaStream_t)stream, ms_per_shape, best_shape, [&]() {
     return bp_lb_eval_nodes(h, B, num_base, d_base_offsets, d_base_sizes, d_base_capacity,
                             d_node_base, d_assign_offsets, d_assign, d_bins, max_bins, d_out_bound,
                             d_out_argmax, d_out_feasible, stream);
