@@ -241,10 +241,11 @@ int launch_prefix(int mode, unsigned grid, size_t smem, cudaStream_t st, EvalArg
   return launch_fn((const void *)prefix_fn(mode), grid, kPrefixNT, smem, st, A, pdl);
 }
 
-// Dynamic shared memory of the cluster kernel: a table slice, then (search
-// nodes) the bin loads.
+// Dynamic shared memory of the cluster kernel: a table slice, the
+// per-parameter accumulators, then (search nodes) the bin loads.
 size_t cluster_smem(int mode, int64_t max_bins) {
-  return (size_t)kSliceBytes + (mode == kSrcNodes ? sizeof(uint32_t) * (size_t)max_bins : 0);
+  return (size_t)(kSliceBytes + kOwnBytes) +
+         (mode == kSrcNodes ? sizeof(uint32_t) * (size_t)max_bins : 0);
 }
 
 // Clusters of the cluster kernel resident at once at `smem` bytes per CTA.

@@ -103,7 +103,8 @@ __device__ __forceinline__ unsigned long long cluster_unit(const EvalArgs &A, co
   const uint32_t c32 = (uint32_t)c;
   const uint32_t U = (uint32_t)((c - 1) / 2);
   const uint32_t nU = U + 2u, nW = c32 + 2u;
-  const ClusterTab T0{smem_addr(slice), 0u};
+  uint32_t *acc = reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(slice) + kSliceBytes);
+  const ClusterTab T0{smem_addr(slice), 0u, slice, acc};
   const ClusterTab T1 = T0.at(nU);  // Ns (RAD2), packed small/big counts (u group)
   const uint32_t nT0 = (D == kBJ1) ? nW : nU;
   const uint32_t nzero = (D == kRAD2 || D == kPrefixU) ? 2u * nU : nT0;
@@ -125,8 +126,8 @@ __device__ __forceinline__ unsigned long long cluster_unit(const EvalArgs &A, co
   if (rank == 0u) {
     if (tid < 8) C.sums[tid] = 0;
     if (tid == 0) C.err = 0;
-    for (int i = tid; i < kMaxHeavy; i += kPrefixNT) S.heavy_acc[i] = 0u;  // eval_harmonic's
   }
+  for (uint32_t i = tid; i < kOwnPerCta; i += kPrefixNT) acc[i] = 0u;  // cluster_harmonic's
   if (D == kBJ1 && with_fs1 && tid < kFs1Params) {
     // FS1's parameters l = tid + 1 (l' = tid + 2), in every CTA
     const uint32_t lp = (uint32_t)tid + 2u, cq = c32 / lp;
@@ -332,7 +333,9 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kPrefixNT
   __shared__ unsigned long long s_t;
   __shared__ long long s_b;
   int32_t *slice = reinterpret_cast<int32_t *>(smem_raw);
-  uint32_t *s_load = reinterpret_cast<uint32_t *>(smem_raw + kSliceBytes);
+  // dynamic shared memory: the table slice, cluster_harmonic's accumulators,
+  // the bin loads (search nodes)
+  uint32_t *s_load = reinterpret_cast<uint32_t *>(smem_raw + kSliceBytes + kOwnBytes);
   const int tid = threadIdx.x;
   const ClusterTeam tm{cluster_rank()};
   const unsigned long long total =

@@ -265,6 +265,8 @@ struct LocalTab {
 struct ClusterTab {
   static constexpr bool kDeep = true;
   uint32_t sbase, off;
+  const int32_t *lslice;  // this CTA's slice, for reads of its own entries
+  uint32_t *acc;          // this CTA's per-parameter accumulators (cluster_harmonic)
   __device__ __forceinline__ uint32_t addr(uint32_t x) const {
     const uint32_t e = off + x;
     return cluster_map(sbase + ((e & (uint32_t)(kSliceInts - 1)) << 2),
@@ -279,7 +281,9 @@ struct ClusterTab {
     dsm_red_add(addr(x), (uint32_t)v);
   }
   __device__ __forceinline__ uint32_t phase(uint32_t x) const { return (off + x) & 3u; }
-  __device__ __forceinline__ ClusterTab at(uint32_t o) const { return ClusterTab{sbase, off + o}; }
+  __device__ __forceinline__ ClusterTab at(uint32_t o) const {
+    return ClusterTab{sbase, off + o, lslice, acc};
+  }
 };
 
 // The threads that share one table's parameters: PARTS CTAs of kPrefixNT
@@ -569,8 +573,8 @@ __device__ __forceinline__ void fs1_finish(int64_t c, PrefixEval &x, const Prefi
 }
 
 // CCM1 / BJ1: the lookups of parameter l fall like X / l, so heavy parameters
-// are shared by the CTA (or by every CTA of the team), medium ones by a warp,
-// the rest take a thread each.
+// are shared by the CTA, medium ones by a warp, the rest take a thread each.
+// (A cluster's tables take cluster_harmonic instead.)
 template <int D, bool PACKED, class Team, class Tab>
 __device__ void eval_harmonic(const Tab &T0, int64_t lam0, int64_t lam_end, int64_t c,
                               PrefixEval &x, PrefixShared &S, Team tm) {
@@ -608,32 +612,7 @@ __device__ void eval_harmonic(const Tab &T0, int64_t lam0, int64_t lam_end, int6
   };
   constexpr uint32_t kPruned = 0xFFFFFFFFu;  // heavy_cm marker (cm < l otherwise)
   const int ncta = (int)(cta_end - lam0);
-  if constexpr (Team::kParts > 1) {
-    // a team of several CTAs shares every heavy parameter: each CTA adds
-    // its blocks' sum into CTA 0's heavy_acc (zeroed by the caller before the
-    // team's last barrier), and CTA 0's thread i finishes parameter i
-    if (ncta > 0) {
-      if (tid < ncta) {
-        const uint32_t l = (uint32_t)(lam0 + tid);
-        const uint32_t q = c32 / l, cm = c32 - q * l;
-        S.heavy_cm[tid] = pruned(l, q, cm) ? kPruned : cm;
-      }
-      __syncthreads();
-      for (int i = 0; i < ncta; ++i) {
-        const uint32_t l = (uint32_t)(lam0 + i);
-        const uint32_t cm = S.heavy_cm[i];
-        if (cm == kPruned || (D == kBJ1 && cm == 0u)) continue;  // BJ1, cm = 0: S = sum w
-        const uint32_t part = __reduce_add_sync(
-            0xFFFFFFFFu, block_terms<D, PACKED>(T0, X, l, gtid, Team::kThreads));
-        if (lane == 0 && part != 0u) dsm_red_add(cluster_map(smem_addr(&S.heavy_acc[i]), 0), part);
-      }
-      tm.sync();
-      if (tm.part == 0u && tid < ncta && S.heavy_cm[tid] != kPruned) {
-        const uint32_t l = (uint32_t)(lam0 + tid);
-        finish(l, c32 / l, S.heavy_acc[tid]);
-      }
-    }
-  } else if (ncta > 0) {
+  if (ncta > 0) {
     if (tid < ncta) {
       const uint32_t l = (uint32_t)(lam0 + tid);
       const uint32_t q = c32 / l, cm = c32 - q * l;
@@ -747,6 +726,122 @@ __device__ void eval_harmonic(const Tab &T0, int64_t lam0, int64_t lam_end, int6
         }
       }
     }
+  }
+}
+
+// Quotient n / l for n < 2^21, l >= 1: a float estimate (error below one) and
+// one correction.
+__device__ __forceinline__ uint32_t small_div(uint32_t n, uint32_t l) {
+  uint32_t q = (uint32_t)((float)n * __frcp_rn((float)l));
+  if (q * l > n) --q;
+  else if ((q + 1u) * l <= n) ++q;
+  return q;
+}
+
+constexpr uint32_t kOwnChunk = 8192;                       // parameters per chunk
+constexpr uint32_t kOwnPerCta = kOwnChunk / kClusterCtas;  // accumulators per CTA
+constexpr int64_t kOwnBytes = 4 * (int64_t)kOwnPerCta;
+
+// CCM1 / BJ1 with the cluster's table: S(l) = sum_{i=1}^{m} T(i l + OFF) (m =
+// floor(U / l) for CCM1, q = floor(c / l) for BJ1, OFF = 1 for BJ1) is the
+// sum over the CTAs of the terms whose entry lies in each CTA's own slice,
+// read there from local shared memory; each CTA adds its partial sum into the
+// accumulator of the parameter's owner (red.shared::cluster), and after a
+// cluster barrier the owner forms the bound.  Parameters go in chunks of
+// kOwnChunk, owner of parameter cb + j the CTA j / kOwnPerCta, its thread
+// j % kPrefixNT (increasing within a thread, as the key rule wants).
+// Parameters of one warp-sized local run or more (l <= kSliceInts / 32) are
+// shared by a warp, the rest take a thread each.
+template <int D, bool PACKED, class Team>
+__device__ void cluster_harmonic(const ClusterTab &T, int64_t lam0, int64_t lam_end, int64_t c,
+                                 PrefixEval &x, Team tm) {
+  constexpr uint32_t OFF = (D == kBJ1) ? 1u : 0u;
+  const int32_t *slice = T.lslice;
+  uint32_t *acc_own = T.acc;
+  const uint32_t off = T.off;
+  const int tid = threadIdx.x;
+  const uint32_t rank = tm.part;
+  const uint32_t c32 = x.c32, U = x.U;
+  const uint32_t X = (D == kCCM1) ? U : c32;
+  int64_t lo_d, hi_d;
+  param_range(D, c, lo_d, hi_d);
+  const uint32_t gofs = flat_index(D, lo_d, c) - (uint32_t)lo_d;
+  const uint32_t kS = (D == kCCM1) ? 2u * x.n_big + x.n_half + 2u * x.n_full : x.sumw;
+  // this CTA's entries of the table: table indices [ta, tb)
+  const uint32_t s0 = rank << kSliceShift;
+  const uint32_t s1 = s0 + (uint32_t)kSliceInts;
+  const uint32_t ta = s0 > off ? s0 - off : 0u;
+  const uint32_t tb = s1 > off ? min(s1 - off, X + OFF + 1u) : 0u;
+  auto tv = [&](uint32_t t) -> uint32_t {  // table entry t, local
+    const uint32_t e = off + t - s0;
+    return PACKED ? (uint32_t)(int32_t)reinterpret_cast<const int16_t *>(slice)[2u * e]
+                  : (uint32_t)slice[e];
+  };
+  auto pruned = [&](uint32_t l, uint32_t q, uint32_t cm) {
+    return D == kBJ1 ? prune_bj1(x, cm) : prune_ccm1(x, l, q, kS);
+  };
+  // terms i in [1, m] with entry i l + OFF in [ta, tb): i in [ilo, ihi]
+  auto local_range = [&](uint32_t l, uint32_t m, uint32_t &ilo, uint32_t &ihi) {
+    ilo = ta > OFF ? small_div(ta - OFF + l - 1u, l) : 1u;
+    if (ilo < 1u) ilo = 1u;
+    ihi = tb > OFF + 1u ? min(m, small_div(tb - 1u - OFF, l)) : 0u;
+  };
+  const uint32_t lheavy = (uint32_t)(kSliceInts / 32);
+  const int lane = (int)lane_id(), warp = tid >> 5;
+  for (int64_t cb = lam0; cb < lam_end; cb += kOwnChunk) {
+    const uint32_t ce = (uint32_t)min(lam_end, cb + (int64_t)kOwnChunk);
+    const uint32_t c0 = (uint32_t)cb;
+    // ---- partial sums of this CTA's terms into the owners' accumulators ----
+    const uint32_t hend = min(ce, max(c0, lheavy + 1u));  // warp-shared parameters [c0, hend)
+    for (uint32_t l = c0 + (uint32_t)warp; l < hend; l += kPrefixWarps) {
+      const uint32_t q = c32 / l, cm = c32 - q * l;
+      if (pruned(l, q, cm) || (D == kBJ1 && cm == 0u)) continue;
+      const uint32_t m = (D == kCCM1) ? U / l : q;
+      uint32_t ilo, ihi;
+      local_range(l, m, ilo, ihi);
+      uint32_t s = 0;
+      for (uint32_t i = ilo + (uint32_t)lane; i <= ihi; i += 32u) s += tv(i * l + OFF);
+      s = __reduce_add_sync(0xFFFFFFFFu, s);
+      if (lane == 0 && s != 0u) {
+        const uint32_t j = l - c0;
+        dsm_red_add(cluster_map(smem_addr(&acc_own[j % kOwnPerCta]), j / kOwnPerCta), s);
+      }
+    }
+    for (uint32_t l = hend + (uint32_t)tid; l < ce; l += kPrefixNT) {
+      const uint32_t q = small_div(c32, l), cm = c32 - q * l;
+      if (pruned(l, q, cm) || (D == kBJ1 && cm == 0u)) continue;
+      const uint32_t m = (D == kCCM1) ? small_div(U, l) : q;
+      // no term in this CTA's entries: the first lies past them or the last before
+      if (m == 0u || l + OFF >= tb || m * l + OFF < ta) continue;
+      uint32_t ilo, ihi;
+      local_range(l, m, ilo, ihi);
+      uint32_t s = 0;
+      for (uint32_t i = ilo; i <= ihi; ++i) s += tv(i * l + OFF);
+      if (s != 0u) {
+        const uint32_t j = l - c0;
+        dsm_red_add(cluster_map(smem_addr(&acc_own[j % kOwnPerCta]), j / kOwnPerCta), s);
+      }
+    }
+    cluster_barrier();  // every partial in its owner
+    // ---- the owner forms the bounds of its parameters ----------------------------
+    for (uint32_t j = rank * kOwnPerCta + (uint32_t)tid; j < (rank + 1u) * kOwnPerCta; j += kPrefixNT) {
+      const uint32_t l = c0 + j;
+      const uint32_t acc = acc_own[j - rank * kOwnPerCta];
+      acc_own[j - rank * kOwnPerCta] = 0u;
+      if (l >= ce) continue;
+      const uint32_t q = small_div(c32, l), cm = c32 - q * l;
+      if (pruned(l, q, cm)) continue;
+      uint32_t Sv, f;
+      if (D == kCCM1) {
+        Sv = 2u * acc + q * kS;
+        f = 2u * q;
+      } else {
+        Sv = cm == 0u ? kS : acc;
+        f = q * (l - cm);
+      }
+      try_key(Sv, f, gofs + l, x.B, x.best);
+    }
+    cluster_barrier();  // accumulators cleared before the next chunk's sums
   }
 }
 
@@ -890,7 +985,10 @@ __device__ __forceinline__ unsigned long long prefix_evaluate(const EvalArgs &A,
   }
   if (D == kMT) eval_mt(T0, lam0, lam_end, c, x, tm);
   if (D == kRAD2) eval_rad2<false>(T0, T1, lam0, lam_end, c, x, tm);
-  if (D == kCCM1 || D == kBJ1) eval_harmonic<D, false>(T0, lam0, lam_end, c, x, S, tm);
+  if (D == kCCM1 || D == kBJ1) {
+    if constexpr (Team::kParts > 1) cluster_harmonic<D, false>(T0, lam0, lam_end, c, x, tm);
+    else eval_harmonic<D, false>(T0, lam0, lam_end, c, x, S, tm);
+  }
   if (D == kPrefixU) {
     // the members in paper order, so that each thread meets its parameters in
     // increasing flattened index
@@ -906,7 +1004,8 @@ __device__ __forceinline__ unsigned long long prefix_evaluate(const EvalArgs &A,
     }
     if (member(kCCM1)) {
       param_range(kCCM1, c, lo, hi);
-      eval_harmonic<kCCM1, true>(T1, lo, hi + 1, c, x, S, tm);
+      if constexpr (Team::kParts > 1) cluster_harmonic<kCCM1, true>(T1, lo, hi + 1, c, x, tm);
+      else eval_harmonic<kCCM1, true>(T1, lo, hi + 1, c, x, S, tm);
     }
     if (S.vb2_mode == 1) eval_vb2_table(T1, c, x, S, S.vb2_lmax, tm);
   }
