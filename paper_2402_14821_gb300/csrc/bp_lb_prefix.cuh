@@ -807,7 +807,10 @@ __device__ void cluster_harmonic(const ClusterTab &T, int64_t lam0, int64_t lam_
         dsm_red_add(cluster_map(smem_addr(&acc_own[j % kOwnPerCta]), j / kOwnPerCta), s);
       }
     }
-    for (uint32_t l = hend + (uint32_t)tid; l < ce; l += kPrefixNT) {
+    // parameters up to a slice's length: each thread its own, every CTA
+    // its slice's terms of it
+    const uint32_t lsl = min(ce, max(hend, (uint32_t)kSliceInts + 1u));
+    for (uint32_t l = hend + (uint32_t)tid; l < lsl; l += kPrefixNT) {
       const uint32_t q = small_div(c32, l), cm = c32 - q * l;
       if (pruned(l, q, cm) || (D == kBJ1 && cm == 0u)) continue;
       const uint32_t m = (D == kCCM1) ? small_div(U, l) : q;
@@ -820,6 +823,24 @@ __device__ void cluster_harmonic(const ClusterTab &T, int64_t lam0, int64_t lam_
       if (s != 0u) {
         const uint32_t j = l - c0;
         dsm_red_add(cluster_map(smem_addr(&acc_own[j % kOwnPerCta]), j / kOwnPerCta), s);
+      }
+    }
+    // parameters longer than a slice: at most one multiple i l of each in
+    // this CTA's entries, so the CTA walks i and, for each, the parameters
+    // with i l + OFF in its entries -- only those -- one term each (whether
+    // pruned or not: the owner decides)
+    if (lsl < ce && tb > ta && tb > OFF + 1u) {
+      const uint32_t imax = (tb - 1u - OFF) / lsl;
+      for (uint32_t i = 1u; i <= imax; ++i) {
+        const uint32_t l0 = max(lsl, ta > OFF ? (ta - OFF + i - 1u) / i : 0u);
+        const uint32_t l1 = min(min(ce - 1u, (tb - 1u - OFF) / i), X / i);
+        for (uint32_t l = l0 + (uint32_t)tid; l <= l1; l += kPrefixNT) {
+          const uint32_t s = tv(i * l + OFF);
+          if (s != 0u) {
+            const uint32_t j = l - c0;
+            dsm_red_add(cluster_map(smem_addr(&acc_own[j % kOwnPerCta]), j / kOwnPerCta), s);
+          }
+        }
       }
     }
     cluster_barrier();  // every partial in its owner
