@@ -42,7 +42,8 @@ struct ClusterShared {
   long long sums[8];                     // the instance sums (PrefixShared::sums)
   uint32_t tot[kClusterCtas][3];         // per CTA: H, M of its part of T0, H of T1's
   uint32_t ltot[kClusterCtas][3];        // this CTA's copy of tot
-  unsigned long long key[kClusterCtas];  // per CTA: its best key
+  unsigned long long key[kClusterCtas];   // per CTA: its best key
+  unsigned long long team[kClusterCtas];  // per CTA: its best key so far (late_vb2_plan)
 };
 
 // The part [a, e) (slice-local entries) of this CTA's slice that cluster
@@ -104,7 +105,7 @@ __device__ __forceinline__ unsigned long long cluster_unit(const EvalArgs &A, co
   const uint32_t U = (uint32_t)((c - 1) / 2);
   const uint32_t nU = U + 2u, nW = c32 + 2u;
   uint32_t *acc = reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(slice) + kSliceBytes);
-  const ClusterTab T0{smem_addr(slice), 0u, slice, acc};
+  const ClusterTab T0{smem_addr(slice), 0u, slice, acc, C.team};
   const ClusterTab T1 = T0.at(nU);  // Ns (RAD2), packed small/big counts (u group)
   const uint32_t nT0 = (D == kBJ1) ? nW : nU;
   const uint32_t nzero = (D == kRAD2 || D == kPrefixU) ? 2u * nU : nT0;
@@ -281,7 +282,7 @@ __device__ __forceinline__ unsigned long long cluster_unit(const EvalArgs &A, co
   cluster_barrier();  // the tables complete
 
   // ---- 4. lookups ------------------------------------------------------------------
-  return prefix_evaluate<D>(A, T0, T1, c, lam0, lam_end, with_fs1, umask, S, tm);
+  return prefix_evaluate<MODE, D>(A, I, b, T0, T1, c, lam0, lam_end, with_fs1, umask, S, tm);
 }
 
 // The unit of the cluster kernel's table entry t - t0 of instance I (the

@@ -265,8 +265,9 @@ struct LocalTab {
 struct ClusterTab {
   static constexpr bool kDeep = true;
   uint32_t sbase, off;
-  const int32_t *lslice;  // this CTA's slice, for reads of its own entries
-  uint32_t *acc;          // this CTA's per-parameter accumulators (cluster_harmonic)
+  const int32_t *lslice;     // this CTA's slice, for reads of its own entries
+  uint32_t *acc;             // this CTA's per-parameter accumulators (cluster_harmonic)
+  unsigned long long *team;  // kClusterCtas keys: team_max_key's gathering point (CTA 0)
   __device__ __forceinline__ uint32_t addr(uint32_t x) const {
     const uint32_t e = off + x;
     return cluster_map(sbase + ((e & (uint32_t)(kSliceInts - 1)) << 2),
@@ -282,7 +283,7 @@ struct ClusterTab {
   }
   __device__ __forceinline__ uint32_t phase(uint32_t x) const { return (off + x) & 3u; }
   __device__ __forceinline__ ClusterTab at(uint32_t o) const {
-    return ClusterTab{sbase, off + o, lslice, acc};
+    return ClusterTab{sbase, off + o, lslice, acc, team};
   }
 };
 
@@ -880,6 +881,7 @@ __device__ void cluster_harmonic(const ClusterTab &T, int64_t lam0, int64_t lam_
 // its team).
 constexpr int64_t kVb2TableTerms = 1 << 16;  // lookups per CTA at most
 
+// L1 may be any cut known from keys already found (late_vb2_plan).
 template <int MODE>
 __device__ __forceinline__ int vb2_table_plan(const EvalArgs &A, const InstView &I,
                                               const PrefixShared &S, uint32_t L1,
@@ -961,14 +963,75 @@ __device__ __forceinline__ void fs1_gather(PrefixShared &S, Team tm) {
   }
 }
 
+// The largest of the team's threads' keys, returned to every thread (team
+// barriers inside; warp_key, and for a cluster team[0 .. kClusterCtas) in
+// every CTA, as scratch).
+template <class Team>
+__device__ __forceinline__ unsigned long long team_max_key(unsigned long long key, PrefixShared &S,
+                                                           unsigned long long *team, Team tm) {
+  key = warp_max_u64(key);
+  if (lane_id() == 0) S.warp_key[threadIdx.x >> 5] = key;
+  __syncthreads();
+  unsigned long long m = 0ull;
+  for (int w = 0; w < kPrefixWarps; ++w) m = S.warp_key[w] > m ? S.warp_key[w] : m;
+  if constexpr (Team::kParts > 1) {
+    if (threadIdx.x == 0) dsm_st64(cluster_map(smem_addr(&team[tm.part]), 0), m);
+    tm.sync();
+    if (threadIdx.x < Team::kParts)
+      S.warp_key[threadIdx.x] = dsm_ld64(cluster_map(smem_addr(&team[threadIdx.x]), 0));
+    __syncthreads();
+    m = 0ull;
+    for (uint32_t r = 0; r < Team::kParts; ++r) m = S.warp_key[r] > m ? S.warp_key[r] : m;
+  }
+  __syncthreads();  // warp_key free again
+  return m;
+}
+
+// The u group's second VB2 plan, after MT, RAD2 and CCM1: the cut of the keys
+// found so far -- the team's best over those three (their indices precede
+// VB2's) and the instance's slot -- often leaves only a few small VB2
+// parameters, which the tile then takes on the count table (S.vb2_mode 9;
+// 10: none can matter), flagging the instance's sums so (2) before any VB2
+// tile reads them.  The slot's key joins the team's maximum through thread 0
+// of each CTA, so that every CTA of a cluster plans from the same key.  Only
+// the cluster kernel's u-group units plan twice: in the prefix kernel the
+// extra code, idle on the search-node step (whose first plan takes VB2), cost
+// that step 1.5% (hard nodes gained 9%).
+template <int MODE, class Team>
+__device__ __forceinline__ void late_vb2_plan(const EvalArgs &A, const InstView &I, int64_t b,
+                                           int64_t c, unsigned long long best, uint32_t L1,
+                                           PrefixShared &S, unsigned long long *team, Team tm) {
+  unsigned long long mine = best;
+  if (threadIdx.x == 0) {
+    const unsigned long long sk = *reinterpret_cast<const volatile unsigned long long *>(&A.keys[b]);
+    mine = sk > mine ? sk : mine;
+  }
+  const unsigned long long kt = team_max_key(mine, S, team, tm);
+  if (threadIdx.x == 0) {
+    // vb2_cut's rule: a key before VB2's index wins ties, one after loses
+    const uint32_t gv = flat_index(kVB2, 2, c);
+    const int64_t cut =
+        kt ? (int64_t)(kt >> 32) - ((0xFFFFFFFFu - (uint32_t)kt) < gv ? 0 : 1) : -1;
+    int64_t kk = 0, lmax = 0;
+    const int64_t vhi = A.vb2_hi != nullptr ? A.vb2_hi[b] : c;
+    // the cut in place of L1 (MT in the bound: the caller's condition)
+    const int mode = vb2_table_plan<MODE>(A, I, S, (uint32_t)max(cut, (int64_t)L1), vhi,
+                                          Team::kParts * kVb2TableTerms, kk, lmax);
+    S.vb2_mode = mode == 0 ? 0 : 8 + mode;  // 9, 10: planned late (9: evaluate)
+    S.vb2_lmax = lmax;
+  }
+  __syncthreads();
+}
+
 // Evaluates the parameters of a built tile (prefix_tile; the cluster kernel):
 // D's parameters [lam0, lam_end) -- after FS1's when with_fs1 (D = BJ1) --
 // or the u group's members in umask, with the team's threads; returns the
 // thread's best key.  The instance sums are in S.sums, the tables T0 (and T1)
 // complete.  A team of several CTAs gathers FS1's sums in CTA 0 (fs1_gather),
 // which forms FS1's bounds.
-template <int D, class Team, class Tab>
-__device__ __forceinline__ unsigned long long prefix_evaluate(const EvalArgs &A, const Tab &T0,
+template <int MODE, int D, class Team, class Tab>
+__device__ __forceinline__ unsigned long long prefix_evaluate(const EvalArgs &A, const InstView &I,
+                                                              int64_t b, const Tab &T0,
                                                               const Tab &T1, int64_t c,
                                                               int64_t lam0, int64_t lam_end,
                                                               bool with_fs1, uint32_t umask,
@@ -1028,7 +1091,19 @@ __device__ __forceinline__ unsigned long long prefix_evaluate(const EvalArgs &A,
       if constexpr (Team::kParts > 1) cluster_harmonic<kCCM1, true>(T1, lo, hi + 1, c, x, tm);
       else eval_harmonic<kCCM1, true>(T1, lo, hi + 1, c, x, S, tm);
     }
-    if (S.vb2_mode == 1) eval_vb2_table(T1, c, x, S, S.vb2_lmax, tm);
+    // VB2 stayed with its kernel at the first plan (cut L1): plan again with
+    // the cut of the keys found so far (late_vb2_plan; cluster units)
+    if constexpr (Team::kParts > 1) {
+      if (S.vb2_mode == 0 && A.isums != nullptr && !A.verdict && A.prune && A.vb2_on &&
+          !((A.dff_off >> kVB2) & 1u) && !(A.dff_off & 1u))
+        late_vb2_plan<MODE>(A, I, b, c, x.best, x.L1, S, T1.team, tm);
+    }
+    if (S.vb2_mode == 1 || (Team::kParts > 1 && S.vb2_mode == 9))
+      eval_vb2_table(T1, c, x, S, S.vb2_lmax, tm);
+    if (Team::kParts > 1 && S.vb2_mode >= 9 && tm.part == 0u && threadIdx.x == 0) {
+      __threadfence();  // VB2's keys are this tile's, folded with them
+      A.isums[8 * b + 7] = 2;
+    }
   }
   return x.best;
 }
@@ -1176,8 +1251,8 @@ __device__ __forceinline__ unsigned long long prefix_tile(const EvalArgs &A, con
   }
   if (S.err) return 0ull;
 
-  return prefix_evaluate<D>(A, LocalTab{T0}, LocalTab{T1}, c, lam0, lam_end, with_fs1, umask, S,
-                            CtaTeam{0u});
+  return prefix_evaluate<MODE, D>(A, I, b, LocalTab{T0}, LocalTab{T1}, c, lam0, lam_end, with_fs1,
+                                  umask, S, CtaTeam{0u});
 }
 
 // Persistent kernel over the prefix tile table (instance, DFF in {MT, RAD2,

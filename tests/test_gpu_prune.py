@@ -202,3 +202,67 @@ def test_vb2_on_count_table(cudalib, orc):
                 assert np.array_equal(np.asarray(x), np.asarray(y))
     finally:
         cudalib.bp_lb_destroy(h)
+
+
+def _late_mode(w, c, cut):
+    """The second VB2 plan of a cluster's u-group unit (late_vb2_plan),
+    restated: the first plan's test with the cut of the keys already found."""
+    w = np.asarray(w, dtype=np.int64)
+    w = w[w > 0]
+    small = w[2 * w < c]
+    big = w[(2 * w > c) & (w < c)]
+    nh, nf = int(np.sum(2 * w == c)), int(np.sum(w == c))
+    ns, nb = len(small), len(big)
+    kk = min(cut, len(w))
+    K = 2 * nb + nh + 2 * nf
+    D = int(small.sum()) - int((c - big).sum())
+    alpha = 2 * D - c * (2 * kk - K)
+    beta = 2 * ns * (c - 1) + c * (2 * kk - K) - c * (2 * ns - 2 * nb + 1) + 2
+    if alpha >= 0:
+        return 2 if alpha * c + beta <= 0 else 0
+    if 2 * alpha + beta <= 0:
+        return 2
+    return 1
+
+
+@pytest.mark.parametrize("cluster", [False, True])
+def test_vb2_late_plan(cudalib, orc, cluster):
+    """Instances whose MT / RAD2 / CCM1 bounds lie above L1, so that the
+    u-group's first VB2 plan (cut L1) leaves VB2 to its kernel and a
+    cluster unit's second plan (cut from the keys found) takes it on the
+    count table: bound and argmax equal the oracle's with pruning on and
+    off, with cluster tables on (c = 30000 and 100000 take clusters) and off
+    (one plan), and with MT left out of the bound (no second plan)."""
+    import concurrent.futures as cf
+    rng = np.random.default_rng(91)
+    inst, caps = [], []
+    for c, n in ((3000, 800), (3000, 3000), (30000, 1500), (30000, 3000), (100000, 2000),
+                 (100000, 3000)):
+        inst.append(rng.integers(1, c + 1, size=n))
+        caps.append(c)
+    rg = I.ragged_from_list(inst, caps)
+    rg.bins = np.zeros(rg.count, np.int64)
+    with cf.ThreadPoolExecutor(6) as ex:
+        want = list(ex.map(lambda j: orc.lb(inst[j], caps[j], 0), range(rg.count)))
+        ucut = list(ex.map(lambda j: max(orc.lb_dff(d, inst[j], caps[j])[0] for d in (0, 1, 3)),
+                           range(rg.count)))
+    want = tuple(np.array(x) for x in zip(*want))
+    late = [_late_mode(inst[j], caps[j], ucut[j]) for j in range(rg.count)]
+    assert sum(m != 0 for m in late) >= 3, late
+    h = cudalib.bp_lb_create(150, 1 << 16)
+    try:
+        cudalib.bp_lb_set_cluster_tables(h, cluster)
+        for got in both(cudalib, h, rg):
+            for x, y in zip(got, want):
+                assert np.array_equal(np.asarray(x), np.asarray(y))
+        cudalib.bp_lb_set_dff_mask(h, 0b111110)   # MT left out: VB2 planned once
+        b, d, lam, _ = run_batch(cudalib, h, rg)
+        for j in range(rg.count):
+            best = (0, -1, -1)
+            for dd in (1, 2, 3, 4, 5):
+                lf, l = orc.lb_dff(dd, inst[j], caps[j])
+                if lf >= 0 and (best[1] < 0 or lf > best[0]):
+                    best = (lf, dd, l)
+            assert (b[j], d[j], lam[j]) == best, j
+    finally:
+        cudalib.bp_lb_destroy(h)
