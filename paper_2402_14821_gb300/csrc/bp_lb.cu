@@ -401,7 +401,10 @@ int launch_batch(bp_lb *h, EvalArgs A, size_t smem, cudaStream_t st) {
     if (nc <= 0) return BP_ECUDA;
     BP_CHECK_STATUS(launch_cluster(MODE, (unsigned)nc, cs, h->side, A));
   }
-  if (h->timing) BP_CHECK(cudaEventRecord(ev[7], h->side));
+  if (h->timing) {
+    if (cl) BP_CHECK(cudaEventRecord(ev[7], h->side));
+    else ev[7] = ev[6];  // no cluster kernel: no time
+  }
   if (cl_side) BP_CHECK(cudaEventRecord(h->ev_cjoin, h->side));
   // Serial order on the caller's stream with nothing between the kernels:
   // programmatic dependent launch (pdl_wait), so that each kernel is
