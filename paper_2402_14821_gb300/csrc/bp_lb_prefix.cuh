@@ -880,6 +880,11 @@ __device__ void cluster_harmonic(const ClusterTab &T, int64_t lam0, int64_t lam_
 // `budget`: the most lookups the tile takes on (kVb2TableTerms per CTA of
 // its team).
 constexpr int64_t kVb2TableTerms = 1 << 16;  // lookups per CTA at most
+// A cluster unit's second plan (late_vb2_plan; cluster_vb2, local lookups,
+// most of them in the three or four CTAs that hold the count table): above
+// about 2^21 lookups the unit takes longer than the generic kernel's VB2
+// tiles, which spread over every SM.
+constexpr int64_t kClusterVb2Terms = 1 << 21;
 
 // L1 may be any cut known from keys already found (late_vb2_plan).
 template <int MODE>
@@ -952,6 +957,134 @@ __device__ __forceinline__ void eval_vb2_table(const Tab &T, int64_t c, PrefixEv
   }
 }
 
+// VB2 from a cluster's packed count table by owner-computes, as
+// cluster_harmonic does CCM1 and BJ1: parameter l's terms are the entries
+// floor(j c / l) + 1 <= U, j = 0, 1, ... (eval_vb2_table), increasing with j,
+// so those in this CTA's slice are the terms of one run of j, which the CTA
+// walks from its first with the incremental quotient.  With t0 the slice's
+// first table index, that first j is j0 = ceil((t0 - 1) l / c), and j0 c =
+// (t0 - 1) l + d with 0 <= d < c gives floor(j0 c / l) = t0 - 1 +
+// floor(d / l).  Parameters of about 80 terms a slice or more (l >=
+// kVb2WarpMin) take a warp, whose lane t walks j0 + t, j0 + t + 32, ...; the
+// others a thread each.  Each CTA adds its partial sums into the owners'
+// accumulators (chunks of kOwnChunk parameters, owner of parameter cb + j the
+// CTA j / kOwnPerCta), and the owner forms the bounds as eval_vb2_table
+// does.  The accumulators hold wrapping 32-bit sums of the signed counts.
+constexpr uint32_t kVb2WarpMin = 512;
+
+// Quotient n / l for n < 2^24 and a quotient below 2^21: the float estimate
+// is within one of it, so one correction each way.
+__device__ __forceinline__ uint32_t est_div(uint32_t n, uint32_t l) {
+  uint32_t q = (uint32_t)((float)n * __frcp_rn((float)l));
+  if (q * l > n) --q;
+  else if ((q + 1u) * l <= n) ++q;
+  return q;
+}
+
+template <class Team>
+__device__ void cluster_vb2(const ClusterTab &T, int64_t c, PrefixEval &x, const PrefixShared &S,
+                            int64_t lmax, Team tm) {
+  const int16_t *lo16 = reinterpret_cast<const int16_t *>(T.lslice);
+  uint32_t *acc_own = T.acc;
+  const uint32_t off = T.off;
+  const int tid = threadIdx.x;
+  const uint32_t rank = tm.part;
+  const uint32_t c32 = x.c32, U = x.U;
+  const uint32_t gofs = flat_index(kVB2, 2, c) - 2u;
+  const int64_t ns = S.sums[0], nb = S.sums[1];
+  const int64_t K = 2 * nb + S.sums[2] + 2 * S.sums[3];
+  // this CTA's table indices [ta, tb) within the terms' [1, U]
+  const uint32_t s0 = rank << kSliceShift;
+  const uint32_t s1 = s0 + (uint32_t)kSliceInts;
+  const uint32_t ta = max(s0 > off ? s0 - off : 0u, 1u);
+  const uint32_t tb = s1 > off ? min(s1 - off, U + 1u) : 0u;
+  const bool local = ta < tb;
+  const float inv_c = 1.0f / (float)c32;
+  // d of parameter l (file comment); j0 from a float estimate, corrected
+  // against the exact 64-bit products (the estimate is within one of it)
+  auto first_d = [&](uint32_t l) -> uint32_t {
+    const uint64_t P = (uint64_t)(ta - 1u) * l;
+    uint64_t j0 = (uint64_t)((float)(ta - 1u) * (float)l * inv_c);
+    if (j0 * c32 < P) ++j0;
+    if (j0 * c32 < P) ++j0;
+    if (j0 > 0u && (j0 - 1u) * c32 >= P) --j0;
+    if (j0 > 0u && (j0 - 1u) * c32 >= P) --j0;
+    return (uint32_t)(j0 * c32 - P);
+  };
+  auto tv = [&](uint32_t t) -> uint32_t {  // N'(t), from this CTA's slice
+    return (uint32_t)(int32_t)lo16[2u * (off + t - s0)];
+  };
+  auto add_owner = [&](uint32_t j, uint32_t s) {
+    dsm_red_add(cluster_map(smem_addr(&acc_own[j % kOwnPerCta]), j / kOwnPerCta), s);
+  };
+  const int lane = (int)lane_id(), warp = tid >> 5;
+  const uint32_t lend = (uint32_t)lmax + 1u;  // parameters [2, lmax]
+  for (uint32_t cb = 2u; cb < lend; cb += kOwnChunk) {
+    const uint32_t ce = min(lend, cb + kOwnChunk);
+    // ---- partial sums of this CTA's terms into the owners' accumulators ----
+    const uint32_t wbeg = min(ce, max(cb, kVb2WarpMin));  // thread parameters [cb, wbeg)
+    if (local) {
+      const uint32_t n = wbeg - cb;
+      bool odd = false;
+      for (uint32_t r0 = 0; r0 < n; r0 += kPrefixNT, odd = !odd) {
+        const uint32_t p = r0 + (odd ? kPrefixNT - 1u - (uint32_t)tid : (uint32_t)tid);
+        if (p >= n) continue;
+        const uint32_t l = cb + p;
+        const uint32_t d = first_d(l);
+        const uint32_t dq = est_div(d, l);
+        uint32_t q = ta - 1u + dq, r = d - dq * l;
+        const uint32_t cq = est_div(c32, l), cr = c32 - cq * l;
+        uint32_t s = 0;
+        while (q + 1u < tb) {
+          s += tv(q + 1u);
+          q += cq;
+          r += cr;
+          if (r >= l) {
+            r -= l;
+            ++q;
+          }
+        }
+        if (s != 0u) add_owner(l - cb, s);
+      }
+      const uint32_t c32x = 32u * c32;
+      for (uint32_t l = wbeg + (uint32_t)warp; l < ce; l += kPrefixWarps) {
+        const uint32_t dt = first_d(l) + (uint32_t)lane * c32;  // < 32 c < 2^24
+        const uint32_t dq = est_div(dt, l);
+        uint32_t q = ta - 1u + dq, r = dt - dq * l;
+        const uint32_t cq = est_div(c32x, l), cr = c32x - cq * l;
+        uint32_t s = 0;
+        while (q + 1u < tb) {
+          s += tv(q + 1u);
+          q += cq;
+          r += cr;
+          if (r >= l) {
+            r -= l;
+            ++q;
+          }
+        }
+        s = __reduce_add_sync(0xFFFFFFFFu, s);
+        if (lane == 0 && s != 0u) add_owner(l - cb, s);
+      }
+    }
+    cluster_barrier();  // every partial in its owner
+    // ---- the owner forms the bounds of its parameters ----------------------------
+    for (uint32_t j = rank * kOwnPerCta + (uint32_t)tid; j < (rank + 1u) * kOwnPerCta; j += kPrefixNT) {
+      const uint32_t l = cb + j;
+      const int32_t acc = (int32_t)acc_own[j - rank * kOwnPerCta];
+      acc_own[j - rank * kOwnPerCta] = 0u;
+      if (l >= ce) continue;
+      const int64_t Sv = 2 * ((int64_t)acc - ns + nb) + (int64_t)(l - 1u) * K;  // >= 0
+      const uint64_t f = 2u * (l - 1u);
+      if ((uint64_t)x.B * f < (uint64_t)Sv || (x.best == 0ull && x.B == 0u)) {
+        const uint32_t lb = (uint32_t)(((uint64_t)Sv + f - 1u) / f);
+        x.B = max(x.B, lb);
+        x.best = make_key((int64_t)lb, gofs + l);
+      }
+    }
+    cluster_barrier();  // accumulators cleared before the next chunk's sums
+  }
+}
+
 // A team of several CTAs: every CTA but 0 adds its FS1 sums into CTA 0's
 // (after the CTA's barrier; the team's barrier follows).
 template <class Team>
@@ -989,10 +1122,11 @@ __device__ __forceinline__ unsigned long long team_max_key(unsigned long long ke
 
 // The u group's second VB2 plan, after MT, RAD2 and CCM1: the cut of the keys
 // found so far -- the team's best over those three (their indices precede
-// VB2's) and the instance's slot -- often leaves only a few small VB2
-// parameters, which the tile then takes on the count table (S.vb2_mode 9;
-// 10: none can matter), flagging the instance's sums so (2) before any VB2
-// tile reads them.  The slot's key joins the team's maximum through thread 0
+// VB2's) and the instance's slot -- often leaves only VB2 parameters up to
+// a few thousand, which the unit then takes on the count table (S.vb2_mode 9;
+// 10: none can matter; cluster_vb2, within kClusterVb2Terms lookups),
+// flagging the instance's sums so (2) before any VB2 tile reads them.  The
+// slot's key joins the team's maximum through thread 0
 // of each CTA, so that every CTA of a cluster plans from the same key.  Only
 // the cluster kernel's u-group units plan twice: in the prefix kernel the
 // extra code, idle on the search-node step (whose first plan takes VB2), cost
@@ -1016,7 +1150,7 @@ __device__ __forceinline__ void late_vb2_plan(const EvalArgs &A, const InstView 
     const int64_t vhi = A.vb2_hi != nullptr ? A.vb2_hi[b] : c;
     // the cut in place of L1 (MT in the bound: the caller's condition)
     const int mode = vb2_table_plan<MODE>(A, I, S, (uint32_t)max(cut, (int64_t)L1), vhi,
-                                          Team::kParts * kVb2TableTerms, kk, lmax);
+                                          kClusterVb2Terms, kk, lmax);
     S.vb2_mode = mode == 0 ? 0 : 8 + mode;  // 9, 10: planned late (9: evaluate)
     S.vb2_lmax = lmax;
   }
@@ -1098,8 +1232,10 @@ __device__ __forceinline__ unsigned long long prefix_evaluate(const EvalArgs &A,
           !((A.dff_off >> kVB2) & 1u) && !(A.dff_off & 1u))
         late_vb2_plan<MODE>(A, I, b, c, x.best, x.L1, S, T1.team, tm);
     }
-    if (S.vb2_mode == 1 || (Team::kParts > 1 && S.vb2_mode == 9))
-      eval_vb2_table(T1, c, x, S, S.vb2_lmax, tm);
+    if (S.vb2_mode == 1 || (Team::kParts > 1 && S.vb2_mode == 9)) {
+      if constexpr (Team::kParts > 1) cluster_vb2(T1, c, x, S, S.vb2_lmax, tm);
+      else eval_vb2_table(T1, c, x, S, S.vb2_lmax, tm);
+    }
     if (Team::kParts > 1 && S.vb2_mode >= 9 && tm.part == 0u && threadIdx.x == 0) {
       __threadfence();  // VB2's keys are this tile's, folded with them
       A.isums[8 * b + 7] = 2;

@@ -202,3 +202,53 @@ def test_cluster_invalid_instances(cudalib, orc):
                 assert tuple(x[i] for x in got) == oracle_node(orc, nd, i), i
     finally:
         cudalib.bp_lb_destroy(h)
+
+
+def _late_lmax(w, c, cut, budget=1 << 21):
+    """The last VB2 parameter of a cluster u-group unit's second plan
+    (late_vb2_plan with the cut of MT, RAD2 and CCM1), restated from the
+    plan's linear test; None when the plan leaves VB2 to its kernel."""
+    w = np.asarray(w, dtype=np.int64)
+    w = w[w > 0]
+    small, big = w[2 * w < c], w[(2 * w > c) & (w < c)]
+    nh, nf = int(np.sum(2 * w == c)), int(np.sum(w == c))
+    ns, nb = len(small), len(big)
+    kk = min(cut, len(w))
+    K = 2 * nb + nh + 2 * nf
+    D = int(small.sum()) - int((c - big).sum())
+    alpha = 2 * D - c * (2 * kk - K)
+    beta = 2 * ns * (c - 1) + c * (2 * kk - K) - c * (2 * ns - 2 * nb + 1) + 2
+    if alpha >= 0 or 2 * alpha + beta <= 0:
+        return None
+    lmax = min(c, (beta - 1) // (-alpha))
+    U = (c - 1) // 2
+    return lmax if U * lmax * lmax // (2 * c) + lmax <= budget else None
+
+
+def test_cluster_vb2_long_parameters(cudalib, orc):
+    """Sizes uniform over [1, c] at c = 10^5, n = 10^4: the cut of MT, RAD2
+    and CCM1 leaves VB2 parameters up to 1 000-2 800 on the cluster's count
+    table (cluster_vb2: a thread per parameter below 512, a warp per
+    parameter above, each CTA summing the terms in its own slice) and up to
+    4 800-6 000 (beyond the second plan's budget) to the generic kernel;
+    bound and argmax equal the oracle's, and the same with cluster tables
+    off."""
+    c = 100_000
+    full = I.large_instances("uniform_full", c, count=64, n=10_000, seed=2, dtype=np.int32)
+    pick = [21, 25, 45, 55, 56, 0]
+    inst = [np.asarray(full.instance(j)) for j in pick]
+    rg = I.ragged_from_list(inst, [c] * len(pick))
+    rg.bins = np.zeros(rg.count, np.int64)
+    with cf.ThreadPoolExecutor(len(pick)) as ex:
+        want = list(ex.map(lambda w: orc.lb(w, c, 0), inst))
+        ucut = list(ex.map(lambda w: max(orc.lb_dff(d, w, c)[0] for d in (0, 1, 3)), inst))
+    lm = [_late_lmax(w, c, u) for w, u in zip(inst, ucut)]
+    assert sum(1 for x in lm if x is not None and x >= 1000) >= 3, lm
+    want = tuple(np.array(x) for x in zip(*want))
+    h = cluster_handle(cudalib)
+    try:
+        assert_same(run_batch(cudalib, h, rg), want, "cluster tables on")
+        cudalib.bp_lb_set_cluster_tables(h, False)
+        assert_same(run_batch(cudalib, h, rg), want, "cluster tables off")
+    finally:
+        cudalib.bp_lb_destroy(h)
