@@ -496,6 +496,26 @@ __device__ __forceinline__ int64_t plan_scan(int64_t v, int64_t *s_warp, int64_t
 // capacity and route class repeat (every node of a search-node batch).
 constexpr int kPlanPerThread = 4;
 
+// Stores a thread's K consecutive entries v[0..K) of out (from entry wb +
+// K lane, wb the warp's first) so that each store instruction of the warp
+// writes 32 consecutive entries: the warp's 32 K entries are transposed with
+// shuffles (entry e of the block is lane e / K's v[e % K]).  Whole warps.
+template <int K, typename T>
+__device__ __forceinline__ void plan_store(T *out, int64_t wb, const T (&v)[K], int64_t B) {
+  const int lane = (int)lane_id();
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const int e = 32 * i + lane;
+    T x = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const T y = __shfl_sync(0xFFFFFFFFu, v[k], e / K);
+      if (e % K == k) x = y;
+    }
+    if (wb + e < B) out[wb + e] = x;
+  }
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(1024)
     plan_kernel(EvalArgs A, int64_t lpt, int64_t *tile_start, int64_t *ptile_start,
@@ -524,33 +544,61 @@ __global__ void __launch_bounds__(1024)
   int rc_k = -1;
   for (int64_t b0 = 0; b0 < A.B; b0 += (int64_t)blockDim.x * K) {
     const int64_t bt = b0 + (int64_t)threadIdx.x * K;  // this thread's first instance
+    const int64_t wb = b0 + (int64_t)(threadIdx.x & ~31u) * K;  // its warp's first
     int64_t tiles[K], ptiles[K], pvs[K];
     int64_t st = 0, sp = 0, sv = 0;
+    // the K instances' inputs first, with no store in between (a store could
+    // alias them), so that their memory latencies overlap: the instance's
+    // own fields, then those of a node's base instance
+    bool okj[K];
+    int64_t cj[K], Lj[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const int64_t b = bt + j < A.B ? bt + j : A.B - 1;  // clamped: the result unused past B
+      if (MODE == kSrcNodes) {
+        const int32_t base = A.node_base[b];
+        const int64_t na = A.assign_offsets[b + 1] - A.assign_offsets[b];
+        const int64_t k = A.bins[b];
+        okj[j] = base >= 0 && base < A.num_base && na >= 0 && k >= 0 && k <= A.max_bins &&
+                 (A.bin_max == nullptr || A.bin_max_offsets[b + 1] - A.bin_max_offsets[b] == k);
+        cj[j] = base;  // the base instance until its fields are read
+        Lj[j] = na;
+      } else {
+        cj[j] = A.capacity[b];
+        Lj[j] = A.offsets[b + 1] - A.offsets[b];
+        okj[j] = A.bins[b] >= 0;
+      }
+    }
+    if (MODE == kSrcNodes) {
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        const int64_t b = bt + j < A.B ? bt + j : A.B - 1;
+        const int32_t base = okj[j] ? (int32_t)cj[j] : 0;
+        const int64_t c = okj[j] ? A.base_capacity[base] : 0;
+        const int64_t n = okj[j] ? A.base_offsets[base + 1] - A.base_offsets[base] : 0;
+        // a node's stream: its base instance's items and its bins' loads
+        okj[j] = okj[j] && n == Lj[j] && n <= kMaxItems;
+        cj[j] = c;
+        Lj[j] = n + A.bins[b];
+      }
+    }
+    // the key slots and sums flags of the pass's instances, coalesced
+    for (int i = 0; i < K; ++i) {
+      const int64_t b = b0 + threadIdx.x + (int64_t)blockDim.x * i;
+      if (b < A.B) {
+        A.keys[b] = 0ull;
+        if (A.isums) A.isums[8 * b + 7] = 0;
+      }
+    }
 #pragma unroll
     for (int j = 0; j < K; ++j) {
       const int64_t b = bt + j;
       tiles[j] = ptiles[j] = pvs[j] = 0;
       if (b < A.B) {
-        A.keys[b] = 0ull;
-        if (A.isums) A.isums[8 * b + 7] = 0;
-        bool ok;
-        int64_t c, L;
-        if (MODE == kSrcNodes) {
-          const int32_t base = A.node_base[b];
-          ok = base >= 0 && base < A.num_base;
-          c = ok ? A.base_capacity[base] : 0;
-          const int64_t n = ok ? A.base_offsets[base + 1] - A.base_offsets[base] : 0;
-          const int64_t na = A.assign_offsets[b + 1] - A.assign_offsets[b];
-          const int64_t k = A.bins[b];
-          ok = ok && c >= 1 && c <= kMaxCapacity && n >= 0 && n <= kMaxItems && na == n &&
-               k >= 0 && k <= A.max_bins &&
-               (A.bin_max == nullptr || A.bin_max_offsets[b + 1] - A.bin_max_offsets[b] == k);
-          L = n + k;
-        } else {
-          c = A.capacity[b];
-          L = A.offsets[b + 1] - A.offsets[b];
-          ok = c >= 1 && c <= kMaxCapacity && L >= 0 && L <= kMaxItems && A.bins[b] >= 0;
-        }
+        const int64_t c = cj[j], L = Lj[j];
+        // (a node's n and k were checked above)
+        const bool ok = okj[j] && c >= 1 && c <= kMaxCapacity &&
+                        (MODE == kSrcNodes || (L >= 0 && L <= kMaxItems));
         if (ok) {
           const int rk = route_class(c, L * c);
           if (c != rc_c || rk != rc_k) {
@@ -579,25 +627,41 @@ __global__ void __launch_bounds__(1024)
       sp += ptiles[j];
       sv += pvs[j];
     }
-    int64_t e0 = plan_scan(st, s_warp, &s_carry[0]);
-    int64_t e1 = plan_scan(sp, s_warp, &s_carry[1]);
+    const int64_t e0 = plan_scan(st, s_warp, &s_carry[0]);
+    const int64_t e1 = plan_scan(sp, s_warp, &s_carry[1]);
     plan_scan(sv, s_warp, &s_carry[2]);
+    int64_t v[K];
 #pragma unroll
-    for (int j = 0; j < K; ++j) {
-      const int64_t b = bt + j;
-      if (b < A.B) {
-        tile_start[b] = e0;
-        if (ptile_start) ptile_start[b] = e1 & 0xFFFFFFFFll;
-        if (ctile_start) ctile_start[b] = e1 >> 32;
-        // the finished-tile counter starts at minus the instance's tiles
-        // (instance_tiles); with a VB2 table, completed below once VB2's tile
-        // length is known
-        const int64_t tot = tiles[j] + (ptiles[j] & 0xFFFFFFFFll) + (ptiles[j] >> 32);
-        if (vtile_start) vtile_start[b] = pvs[j] | (tot << 32);
-        else A.done[b] = 0u - (uint32_t)tot;
+    for (int j = 0; j < K; ++j) v[j] = j ? v[j - 1] + tiles[j - 1] : e0;
+    plan_store(tile_start, wb, v, A.B);
+    if (ptile_start != nullptr || ctile_start != nullptr) {
+#pragma unroll
+      for (int j = 0; j < K; ++j) v[j] = j ? v[j - 1] + ptiles[j - 1] : e1;
+      if (ctile_start != nullptr) {
+        int64_t u[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) u[j] = v[j] >> 32;
+        plan_store(ctile_start, wb, u, A.B);
       }
-      e0 += tiles[j];
-      e1 += ptiles[j];
+#pragma unroll
+      for (int j = 0; j < K; ++j) v[j] &= 0xFFFFFFFFll;
+      if (ptile_start != nullptr) plan_store(ptile_start, wb, v, A.B);
+    }
+    // the finished-tile counter starts at minus the instance's tiles
+    // (instance_tiles); with a VB2 table, completed below once VB2's tile
+    // length is known
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+      v[j] = tiles[j] + (ptiles[j] & 0xFFFFFFFFll) + (ptiles[j] >> 32);
+    if (vtile_start != nullptr) {
+#pragma unroll
+      for (int j = 0; j < K; ++j) v[j] = pvs[j] | (v[j] << 32);
+      plan_store(vtile_start, wb, v, A.B);
+    } else {
+      uint32_t dn[K];
+#pragma unroll
+      for (int j = 0; j < K; ++j) dn[j] = 0u - (uint32_t)v[j];
+      plan_store(A.done, wb, dn, A.B);
     }
   }
   __syncthreads();
@@ -618,6 +682,7 @@ __global__ void __launch_bounds__(1024)
   if (vtile_start != nullptr) {
     for (int64_t b0 = 0; b0 < A.B; b0 += (int64_t)blockDim.x * K) {
       const int64_t bt = b0 + (int64_t)threadIdx.x * K;
+      const int64_t wb = b0 + (int64_t)(threadIdx.x & ~31u) * K;
       int64_t vt[K];
       uint32_t tot[K];
       int64_t sv = 0;
@@ -628,15 +693,17 @@ __global__ void __launch_bounds__(1024)
         tot[j] = (uint32_t)(pv >> 32);
         sv += vt[j];
       }
-      int64_t e2 = plan_scan(sv, s_warp, &s_carry[2]);
+      // (every read of this pass's entries precedes the scan's barriers)
+      const int64_t e2 = plan_scan(sv, s_warp, &s_carry[2]);
+      int64_t v[K];
+      uint32_t dn[K];
 #pragma unroll
       for (int j = 0; j < K; ++j) {
-        if (bt + j < A.B) {
-          vtile_start[bt + j] = e2;
-          A.done[bt + j] = 0u - (tot[j] + (uint32_t)vt[j]);
-        }
-        e2 += vt[j];
+        v[j] = j ? v[j - 1] + vt[j - 1] : e2;
+        dn[j] = 0u - (tot[j] + (uint32_t)vt[j]);
       }
+      plan_store(vtile_start, wb, v, A.B);
+      plan_store(A.done, wb, dn, A.B);
     }
   }
   if (threadIdx.x == 0) {
