@@ -453,35 +453,62 @@ __device__ __forceinline__ int64_t vb2_last(const EvalArgs &A, int64_t b, int64_
 // (exclusive scan of tiles per instance; 0 tiles and an error result for an
 // invalid one), clears keys/done and resets the work counter.
 // ---------------------------------------------------------------------------
-// Block-wide exclusive scan step of plan_kernel: returns the exclusive prefix
-// of v within this pass plus *carry, and advances *carry by the pass total.
-__device__ __forceinline__ int64_t plan_scan(int64_t v, int64_t *s_warp, int64_t *carry) {
-  int64_t x = v;
+// Block-wide exclusive scan step of plan_kernel over Q quantities at once:
+// excl[q] = the exclusive prefix of v[q] within this pass plus carry[q], and
+// carry[q] advances by the pass total (four barriers for all Q).
+template <int Q>
+__device__ __forceinline__ void plan_scan(const int64_t (&v)[Q], int64_t (*s_warp)[32],
+                                          int64_t *carry, int64_t (&excl)[Q]) {
+  const int lane = (int)lane_id(), warp = (int)(threadIdx.x >> 5);
+  const int nw = (int)(blockDim.x >> 5);
+  int64_t x[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) x[q] = v[q];
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const int64_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-    if ((int)lane_id() >= o) x += y;
-  }
-  if (lane_id() == 31) s_warp[threadIdx.x >> 5] = x;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    const int nw = blockDim.x >> 5;
-    int64_t wv = (int)threadIdx.x < nw ? s_warp[threadIdx.x] : 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int64_t y = __shfl_up_sync(0xFFFFFFFFu, wv, o);
-      if ((int)threadIdx.x >= o) wv += y;
+    for (int q = 0; q < Q; ++q) {
+      const int64_t y = __shfl_up_sync(0xFFFFFFFFu, x[q], o);
+      if (lane >= o) x[q] += y;
     }
-    s_warp[threadIdx.x] = wv;  // inclusive warp prefix
+  }
+  if (lane == 31)
+#pragma unroll
+    for (int q = 0; q < Q; ++q) s_warp[q][warp] = x[q];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      int64_t wv = lane < nw ? s_warp[q][lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xFFFFFFFFu, wv, o);
+        if (lane >= o) wv += y;
+      }
+      s_warp[q][lane] = wv;  // inclusive warp prefix
+    }
   }
   __syncthreads();
-  const int64_t warp_excl = (threadIdx.x >> 5) ? s_warp[(threadIdx.x >> 5) - 1] : 0;
-  const int64_t excl = *carry + warp_excl + x - v;
-  const int64_t total = s_warp[(blockDim.x >> 5) - 1];
+  int64_t total[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    excl[q] = carry[q] + (warp ? s_warp[q][warp - 1] : 0) + x[q] - v[q];
+    total[q] = s_warp[q][nw - 1];
+  }
   __syncthreads();
-  if (threadIdx.x == 0) *carry += total;
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int q = 0; q < Q; ++q) carry[q] += total[q];
   __syncthreads();
-  return excl;
+}
+
+// VB2's tile length: the batch's VB2 parameters over the target tile count,
+// rounded up to a multiple of 1024, within [kVb2LPT, kVb2MaxLPT].
+__device__ __forceinline__ int64_t plan_vlpt(const EvalArgs &A, int64_t vb2_params) {
+  if (A.vlpt == nullptr || !A.vb2_on) return kVb2LPT;
+  const int64_t tgt = max(A.vb2_target_tiles, (int64_t)1);
+  const int64_t want = (vb2_params + tgt - 1) / tgt;
+  return min(kVb2MaxLPT, max(kVb2LPT, (want + 1023) / 1024 * 1024));
 }
 
 // plan_kernel: one block.  Validates every instance and writes the tile
@@ -521,11 +548,14 @@ __global__ void __launch_bounds__(1024)
     plan_kernel(EvalArgs A, int64_t lpt, int64_t *tile_start, int64_t *ptile_start,
                 int64_t *vtile_start, int64_t *ctile_start) {
   constexpr int K = kPlanPerThread;
-  __shared__ int64_t s_warp[32];
-  __shared__ int64_t s_carry[3];
+  __shared__ int64_t s_warp[3][32];
+  __shared__ int64_t s_carry[4];  // direct, prefix | cluster, VB2 parameters, VB2 tiles
   pdl_release();  // the prefix kernel's CTAs may be scheduled now; they wait for this grid
+  // a batch of one pass also makes VB2's tile table in it (VB2's tile length
+  // is known after its scan); larger ones in a second pass
+  const bool one_pass = A.B <= (int64_t)blockDim.x * K;
   if (threadIdx.x == 0) {
-    s_carry[0] = s_carry[1] = s_carry[2] = 0;
+    s_carry[0] = s_carry[1] = s_carry[2] = s_carry[3] = 0;
     *A.work = 0ull;
     if (A.pwork) *A.pwork = 0ull;
     if (A.cwork) *A.cwork = 0ull;
@@ -627,9 +657,12 @@ __global__ void __launch_bounds__(1024)
       sp += ptiles[j];
       sv += pvs[j];
     }
-    const int64_t e0 = plan_scan(st, s_warp, &s_carry[0]);
-    const int64_t e1 = plan_scan(sp, s_warp, &s_carry[1]);
-    plan_scan(sv, s_warp, &s_carry[2]);
+    int64_t ex[3];
+    {
+      const int64_t sums[3] = {st, sp, sv};
+      plan_scan<3>(sums, s_warp, s_carry, ex);
+    }
+    const int64_t e0 = ex[0], e1 = ex[1];
     int64_t v[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) v[j] = j ? v[j - 1] + tiles[j - 1] : e0;
@@ -653,7 +686,29 @@ __global__ void __launch_bounds__(1024)
 #pragma unroll
     for (int j = 0; j < K; ++j)
       v[j] = tiles[j] + (ptiles[j] & 0xFFFFFFFFll) + (ptiles[j] >> 32);
-    if (vtile_start != nullptr) {
+    if (vtile_start != nullptr && one_pass) {
+      // VB2's tiles now: the counter completed, the VB2 tile table written
+      const int64_t vlpt = plan_vlpt(A, s_carry[2]);
+      int64_t vt[K];
+      int64_t svt = 0;
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        vt[j] = tile_count(pvs[j], vlpt);
+        svt += vt[j];
+      }
+      int64_t e2[1];
+      {
+        const int64_t sums[1] = {svt};
+        plan_scan<1>(sums, s_warp, &s_carry[3], e2);
+      }
+      uint32_t dn[K];
+#pragma unroll
+      for (int j = 0; j < K; ++j) dn[j] = 0u - (uint32_t)(v[j] + vt[j]);
+      plan_store(A.done, wb, dn, A.B);
+#pragma unroll
+      for (int j = 0; j < K; ++j) v[j] = j ? v[j - 1] + vt[j - 1] : e2[0];
+      plan_store(vtile_start, wb, v, A.B);
+    } else if (vtile_start != nullptr) {
 #pragma unroll
       for (int j = 0; j < K; ++j) v[j] = pvs[j] | (v[j] << 32);
       plan_store(vtile_start, wb, v, A.B);
@@ -665,21 +720,11 @@ __global__ void __launch_bounds__(1024)
     }
   }
   __syncthreads();
-  int64_t vlpt = kVb2LPT;
-  if (A.vlpt != nullptr && A.vb2_on) {
-    const int64_t tgt = max(A.vb2_target_tiles, (int64_t)1);
-    const int64_t want = (s_carry[2] + tgt - 1) / tgt;
-    vlpt = min(kVb2MaxLPT, max(kVb2LPT, (want + 1023) / 1024 * 1024));
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    if (A.vlpt != nullptr) *A.vlpt = vlpt;
-    s_carry[2] = 0;
-  }
-  __syncthreads();
-  // the VB2 tile table from the kept parameter counts (each thread rereads
-  // its own entries)
-  if (vtile_start != nullptr) {
+  const int64_t vlpt = plan_vlpt(A, s_carry[2]);
+  if (threadIdx.x == 0 && A.vlpt != nullptr) *A.vlpt = vlpt;
+  // a larger batch: the VB2 tile table from the kept parameter counts (each
+  // thread rereads its own entries)
+  if (vtile_start != nullptr && !one_pass) {
     for (int64_t b0 = 0; b0 < A.B; b0 += (int64_t)blockDim.x * K) {
       const int64_t bt = b0 + (int64_t)threadIdx.x * K;
       const int64_t wb = b0 + (int64_t)(threadIdx.x & ~31u) * K;
@@ -694,12 +739,16 @@ __global__ void __launch_bounds__(1024)
         sv += vt[j];
       }
       // (every read of this pass's entries precedes the scan's barriers)
-      const int64_t e2 = plan_scan(sv, s_warp, &s_carry[2]);
+      int64_t e2[1];
+      {
+        const int64_t sums[1] = {sv};
+        plan_scan<1>(sums, s_warp, &s_carry[3], e2);
+      }
       int64_t v[K];
       uint32_t dn[K];
 #pragma unroll
       for (int j = 0; j < K; ++j) {
-        v[j] = j ? v[j - 1] + vt[j - 1] : e2;
+        v[j] = j ? v[j - 1] + vt[j - 1] : e2[0];
         dn[j] = 0u - (tot[j] + (uint32_t)vt[j]);
       }
       plan_store(vtile_start, wb, v, A.B);
@@ -710,7 +759,7 @@ __global__ void __launch_bounds__(1024)
     tile_start[A.B] = s_carry[0];
     if (ptile_start) ptile_start[A.B] = s_carry[1] & 0xFFFFFFFFll;
     if (ctile_start) ctile_start[A.B] = s_carry[1] >> 32;
-    if (vtile_start) vtile_start[A.B] = s_carry[2];
+    if (vtile_start) vtile_start[A.B] = s_carry[3];
   }
 }
 

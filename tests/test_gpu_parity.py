@@ -438,3 +438,21 @@ def test_prefix_long_stream_unmerged(cudalib, handle, orc):
             rng.integers(1, 1001, size=300)]
     rg = I.ragged_from_list(inst, [1000, 1000, 1000])
     assert_same(run_batch(cudalib, handle, rg), oracle_batch(orc, rg), "long streams")
+
+
+@pytest.mark.parametrize("count", [4095, 4096, 4097, 8193])
+def test_plan_pass_boundaries(cudalib, orc, count):
+    """Batches just below, at and above one planner pass (1024 threads x 4
+    instances; one pass also makes VB2's tile table, more take a second):
+    every instance's bound, argmax and verdict against the oracle."""
+    rng = np.random.default_rng(count)
+    caps = [int(c) for c in rng.choice([150, 151, 1000, 4999], size=count)]
+    inst = [rng.integers(1, c // 2 + 1, size=int(rng.integers(1, 30))) for c in caps]
+    rg = I.ragged_from_list(inst, caps)
+    rg.bins = rng.integers(0, 20, size=count).astype(np.int64)
+    want = oracle_batch(orc, rg)
+    h = cudalib.bp_lb_create(150, 1 << 16)
+    try:
+        assert_same(run_batch(cudalib, h, rg), want, "pass boundary %d" % count)
+    finally:
+        cudalib.bp_lb_destroy(h)
