@@ -769,6 +769,7 @@ __global__ void __launch_bounds__(1024)
 struct TileShared {
   int ns, nb, err;
   int skip;     // verdict mode: the instance was decided before this tile
+  int done_vb2;  // VB2 kernel: the instance's VB2 was evaluated on its u-group tile
   int stop[2];  // verdict mode: decided before group g (double-buffered by g & 1)
   long long kcut[2];  // VB2 pruning: the cut of group g (double-buffered by g & 1)
   int gskip[2];       // VB2 pruning: group g pruned whole

@@ -44,6 +44,30 @@ __global__ void __launch_bounds__(kVb2NT, vb2_minb(VT)) vb2_kernel(EvalArgs A) {
   while (cur.tile < total) {
     const int64_t t = cur.tile, b = cur.inst;
     const unsigned long long next = tile_claim(A.vwork);
+    // VB2 already evaluated on the instance's u-group tile (its sums flag
+    // 2): the tile only counts itself, with nothing to fold and without the
+    // instance's fields unless it is the instance's last
+    if (threadIdx.x == 0)
+      S.done_vb2 = A.isums != nullptr && (A.verdict || A.prune) &&
+                   reinterpret_cast<const volatile long long *>(A.isums)[8 * b + 7] == 2;
+    __syncthreads();
+    if (S.done_vb2) {
+      if (threadIdx.x == 32) {  // fold_and_finalize's thread, best key 0
+        __threadfence();
+        const int64_t ntiles = instance_tiles(A, b);
+        const unsigned int ticket = atomicAdd(&A.done[b], 1u);
+        if (ntiles > 0 ? (int64_t)ticket == ntiles - 1 : ticket == 0xFFFFFFFFu) {
+          __threadfence();
+          const unsigned long long key = atomicExch(&A.keys[b], 0ull);
+          A.done[b] = 0u;
+          const InstView I = resolve_instance<MODE>(A, b);
+          write_result(A, b, key, I.c, I.k);
+        }
+      }
+      if (!A.vwork) break;
+      tile_publish(A.vtile_start, A.B, total, next, cur);
+      continue;
+    }
     const InstView I = resolve_instance<MODE>(A, b);
     const int64_t t0 = A.vtile_start ? A.vtile_start[b] : 0;
     const int64_t ntiles = instance_tiles(A, b);
@@ -62,7 +86,7 @@ __global__ void __launch_bounds__(kVb2NT, vb2_minb(VT)) vb2_kernel(EvalArgs A) {
       if (!S.skip && A.isums != nullptr && (A.verdict || A.prune)) {
         const volatile long long *is = A.isums + 8 * b;
         const long long flag = is[7];
-        if (flag == 2) S.skip = 1;  // VB2 done on the prefix kernel's u-group tile
+        if (flag == 2) S.skip = 1;  // VB2 done on the u-group tile since the check above
         if (flag == 1) {
           __threadfence();
           const int64_t cut = A.verdict ? I.k : (int64_t)vb2_cut(&A.keys[b], flat_index(kVB2, lo_d, I.c));
